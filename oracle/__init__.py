@@ -1,0 +1,117 @@
+"""CPU oracle for per-edge AML pattern counts -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  It wraps ``aml_oracle.c`` (plain C + OpenMP) via
+ctypes and shares no code with the CUDA library.
+
+Columns are ``(kind, delta)`` or ``("cyc", k, delta)`` tuples with kind one of
+``deg_out, deg_in, fan_out, fan_in, gs, sg, cyc``; the definitions are the
+ones in ``aml_oracle.h`` (the paper's stage semantics, Sec. 5 and Alg. 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Iterable, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "aml_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+KINDS = {"deg_out": 0, "deg_in": 1, "fan_out": 2, "fan_in": 3, "gs": 4, "sg": 5, "cyc": 6}
+
+
+class _Col(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32), ("delta", ctypes.c_int64)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2 -fopenmp) if the .so is stale."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(os.path.join(_HERE, "aml_oracle.h"))):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-Wall", "-o", tmp, _SRC])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        lib.og_graph_new.restype = ctypes.c_void_p
+        lib.og_graph_new.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_int32]
+        lib.og_graph_free.argtypes = [ctypes.c_void_p]
+        lib.og_count_all.restype = ctypes.c_int
+        lib.og_count_all.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                     ctypes.c_void_p, ctypes.c_int32]
+        lib.og_count_edges.restype = ctypes.c_int
+        lib.og_count_edges.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.c_int32]
+        _lib = lib
+    return _lib
+
+
+def _cols(cols: Sequence[Tuple]) -> ctypes.Array:
+    arr = (_Col * len(cols))()
+    for i, c in enumerate(cols):
+        if c[0] == "cyc":
+            arr[i].kind, arr[i].k, arr[i].delta = KINDS["cyc"], int(c[1]), int(c[2])
+        else:
+            arr[i].kind, arr[i].k, arr[i].delta = KINDS[c[0]], 0, int(c[1])
+    return arr
+
+
+class OracleGraph:
+    """Host copy of the graph with (t,id)-sorted out/in rows."""
+
+    def __init__(self, src, dst, ts, n_nodes: int):
+        lib = _load()
+        self._src = np.ascontiguousarray(src, dtype=np.int32)
+        self._dst = np.ascontiguousarray(dst, dtype=np.int32)
+        self._ts = np.ascontiguousarray(ts, dtype=np.int32)
+        self.n_edges = int(self._src.shape[0])
+        self.n_nodes = int(n_nodes)
+        self._h = lib.og_graph_new(self._src.ctypes.data, self._dst.ctypes.data,
+                                   self._ts.ctypes.data, self.n_edges, self.n_nodes)
+        if not self._h:
+            raise ValueError("oracle rejected the graph (ids out of range?)")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().og_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def count_all(self, cols: Sequence[Tuple], threads: int = 0) -> np.ndarray:
+        """Canonical enumeration over the whole graph: uint32 [E, len(cols)]."""
+        out = np.zeros((self.n_edges, len(cols)), dtype=np.uint32)
+        rc = _load().og_count_all(self._h, ctypes.byref(_cols(cols)), len(cols),
+                                  out.ctypes.data, threads)
+        if rc:
+            raise ValueError(f"og_count_all failed ({rc})")
+        return out
+
+    def count_edges(self, cols: Sequence[Tuple], eids: Iterable[int],
+                    threads: int = 0) -> np.ndarray:
+        """Edge-centric query for the listed edges: uint32 [n, len(cols)]."""
+        ids = np.ascontiguousarray(np.asarray(list(eids) if not isinstance(eids, np.ndarray)
+                                              else eids, dtype=np.int64))
+        out = np.zeros((ids.shape[0], len(cols)), dtype=np.uint32)
+        rc = _load().og_count_edges(self._h, ctypes.byref(_cols(cols)), len(cols),
+                                    ids.ctypes.data, ids.shape[0], out.ctypes.data, threads)
+        if rc:
+            raise ValueError(f"og_count_edges failed ({rc})")
+        return out

@@ -1,0 +1,569 @@
+/*
+ * CPU oracle for per-edge AML pattern counts -- TEST INFRASTRUCTURE ONLY.
+ * Loaded by the tests, the smoke check and the benchmark's CPU-baseline leg;
+ * never by the product library.  Plain nested loops in the shape of the
+ * paper's per-stage loop (Alg. 1): find the window start by binary search
+ * (Find_Starting_Edge), iterate, break when the time window is exceeded,
+ * skip excluded nodes, and credit every edge of every instance found.
+ * Counts accumulate in uint64 and are clamped to 2^32-1 on output.
+ */
+#include "aml_oracle.h"
+
+#include <omp.h>
+#include <stdlib.h>
+#include <string.h>
+
+struct og_graph {
+  int64_t E;
+  int32_t N;
+  int32_t *src, *dst, *ts;
+  int64_t *out_start, *in_start; /* N+1 row offsets                         */
+  int64_t *out_list, *in_list;   /* non-loop edge ids, rows in (t,id) order  */
+  int64_t *pos_out, *pos_in;     /* position of e in its rows, -1 for loops  */
+};
+
+typedef struct { int32_t t; int64_t id; } tkey;
+
+static int cmp_tkey(const void* a, const void* b) {
+  const tkey* x = (const tkey*)a;
+  const tkey* y = (const tkey*)b;
+  if (x->t != y->t) return x->t < y->t ? -1 : 1;
+  return x->id < y->id ? -1 : (x->id > y->id ? 1 : 0);
+}
+
+/* f precedes e in the strict total order (t, id) */
+static inline int prec(const og_graph* g, int64_t f, int64_t e) {
+  return g->ts[f] < g->ts[e] || (g->ts[f] == g->ts[e] && f < e);
+}
+
+/* Find_Start: first i in [lo,hi) with t(list[i]) >= tmin */
+static int64_t find_start(const og_graph* g, const int64_t* list, int64_t lo, int64_t hi,
+                          int64_t tmin) {
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if ((int64_t)g->ts[list[mid]] < tmin) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+/* first i in [lo,hi) whose edge comes strictly after e */
+static int64_t first_after(const og_graph* g, const int64_t* list, int64_t lo, int64_t hi,
+                           int64_t e) {
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (!prec(g, e, list[mid])) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+og_graph* og_graph_new(const int32_t* src, const int32_t* dst, const int32_t* ts,
+                       int64_t E, int32_t N) {
+  if (E < 0 || N < 0) return NULL;
+  for (int64_t e = 0; e < E; ++e)
+    if (src[e] < 0 || src[e] >= N || dst[e] < 0 || dst[e] >= N) return NULL;
+  og_graph* g = (og_graph*)calloc(1, sizeof(og_graph));
+  g->E = E;
+  g->N = N;
+  size_t e4 = (size_t)(E > 0 ? E : 1) * 4, e8 = (size_t)(E > 0 ? E : 1) * 8;
+  g->src = (int32_t*)malloc(e4);
+  g->dst = (int32_t*)malloc(e4);
+  g->ts = (int32_t*)malloc(e4);
+  if (E) {
+    memcpy(g->src, src, (size_t)E * 4);
+    memcpy(g->dst, dst, (size_t)E * 4);
+    memcpy(g->ts, ts, (size_t)E * 4);
+  }
+  g->out_start = (int64_t*)calloc((size_t)N + 1, 8);
+  g->in_start = (int64_t*)calloc((size_t)N + 1, 8);
+  g->out_list = (int64_t*)malloc(e8);
+  g->in_list = (int64_t*)malloc(e8);
+  g->pos_out = (int64_t*)malloc(e8);
+  g->pos_in = (int64_t*)malloc(e8);
+
+  /* global (t, id) order of the non-loop edges */
+  tkey* ord = (tkey*)malloc(sizeof(tkey) * (size_t)(E > 0 ? E : 1));
+  int64_t nv = 0;
+  for (int64_t e = 0; e < E; ++e) {
+    g->pos_out[e] = -1;
+    g->pos_in[e] = -1;
+    if (src[e] == dst[e]) continue;
+    ord[nv].t = ts[e];
+    ord[nv].id = e;
+    ++nv;
+  }
+  qsort(ord, (size_t)nv, sizeof(tkey), cmp_tkey);
+  for (int64_t i = 0; i < nv; ++i) {
+    g->out_start[g->src[ord[i].id] + 1]++;
+    g->in_start[g->dst[ord[i].id] + 1]++;
+  }
+  for (int32_t u = 0; u < N; ++u) {
+    g->out_start[u + 1] += g->out_start[u];
+    g->in_start[u + 1] += g->in_start[u];
+  }
+  int64_t* fo = (int64_t*)malloc(((size_t)N + 1) * 8);
+  int64_t* fi = (int64_t*)malloc(((size_t)N + 1) * 8);
+  memcpy(fo, g->out_start, ((size_t)N + 1) * 8);
+  memcpy(fi, g->in_start, ((size_t)N + 1) * 8);
+  /* walking the global order keeps every row in (t, id) order */
+  for (int64_t i = 0; i < nv; ++i) {
+    int64_t e = ord[i].id;
+    int64_t p = fo[g->src[e]]++;
+    g->out_list[p] = e;
+    g->pos_out[e] = p;
+    int64_t q = fi[g->dst[e]]++;
+    g->in_list[q] = e;
+    g->pos_in[e] = q;
+  }
+  free(fo);
+  free(fi);
+  free(ord);
+  return g;
+}
+
+void og_graph_free(og_graph* g) {
+  if (!g) return;
+  free(g->src); free(g->dst); free(g->ts);
+  free(g->out_start); free(g->in_start);
+  free(g->out_list); free(g->in_list);
+  free(g->pos_out); free(g->pos_in);
+  free(g);
+}
+
+static int32_t max_row(const og_graph* g) {
+  int64_t m = 1;
+  for (int32_t u = 0; u < g->N; ++u) {
+    int64_t a = g->out_start[u + 1] - g->out_start[u];
+    int64_t b = g->in_start[u + 1] - g->in_start[u];
+    if (a > m) m = a;
+    if (b > m) m = b;
+  }
+  return (int32_t)m;
+}
+
+static int cmp_i32(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+/* ---------------- DEG / FAN (trailing window [t_e - delta, e]) ---------------- */
+
+/* window of e in its out-row (outgoing=1) or in-row: [lo, pos] */
+static void trailing_window(const og_graph* g, int64_t e, int outgoing, int64_t delta,
+                            int64_t* lo, int64_t* pos, const int64_t** list) {
+  int32_t node = outgoing ? g->src[e] : g->dst[e];
+  const int64_t* start = outgoing ? g->out_start : g->in_start;
+  *list = outgoing ? g->out_list : g->in_list;
+  *pos = outgoing ? g->pos_out[e] : g->pos_in[e];
+  *lo = find_start(g, *list, start[node], *pos + 1, (int64_t)g->ts[e] - delta);
+}
+
+/* canonical FAN: sort the window's counterparties, count distinct values */
+static uint64_t fan_sorted(const og_graph* g, int64_t e, int outgoing, int64_t delta,
+                           int32_t* buf) {
+  int64_t lo, pos;
+  const int64_t* list;
+  trailing_window(g, e, outgoing, delta, &lo, &pos, &list);
+  int64_t n = 0;
+  for (int64_t i = lo; i <= pos; ++i)
+    buf[n++] = outgoing ? g->dst[list[i]] : g->src[list[i]];
+  qsort(buf, (size_t)n, 4, cmp_i32);
+  uint64_t d = 0;
+  for (int64_t i = 0; i < n; ++i)
+    if (i == 0 || buf[i] != buf[i - 1]) ++d;
+  return d;
+}
+
+/* edge-centric FAN: mark counterparties with a per-query stamp */
+static uint64_t fan_stamp(const og_graph* g, int64_t e, int outgoing, int64_t delta,
+                          int64_t* stamp, int64_t q) {
+  int64_t lo, pos;
+  const int64_t* list;
+  trailing_window(g, e, outgoing, delta, &lo, &pos, &list);
+  uint64_t d = 0;
+  for (int64_t i = lo; i <= pos; ++i) {
+    int32_t c = outgoing ? g->dst[list[i]] : g->src[list[i]];
+    if (stamp[c] != q) { stamp[c] = q; ++d; }
+  }
+  return d;
+}
+
+static uint64_t deg(const og_graph* g, int64_t e, int outgoing, int64_t delta) {
+  int64_t lo, pos;
+  const int64_t* list;
+  trailing_window(g, e, outgoing, delta, &lo, &pos, &list);
+  return (uint64_t)(pos - lo + 1);
+}
+
+/* ---------------- canonical enumeration ---------------- */
+
+#define ACC(e, c) acc[(size_t)(e) * (size_t)ncols + (size_t)(c)]
+
+static void add(uint64_t* p, uint64_t v) {
+#pragma omp atomic
+  *p += v;
+}
+
+/* GS: each instance (a, b) found once, from its gather leg a */
+static void canon_gs(const og_graph* g, int col, int ncols, int64_t delta, uint64_t* acc,
+                     int nth) {
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nth)
+  for (int64_t a = 0; a < g->E; ++a) {
+    if (g->pos_out[a] < 0) continue;
+    int32_t x = g->src[a], h = g->dst[a];
+    int64_t hi = g->out_start[h + 1];
+    for (int64_t i = first_after(g, g->out_list, g->out_start[h], hi, a); i < hi; ++i) {
+      int64_t b = g->out_list[i];
+      if ((int64_t)g->ts[b] - g->ts[a] > delta) break;  /* break_if: window overflow */
+      if (g->dst[b] == x) continue;                       /* skip_if: y == x */
+      add(&ACC(a, col), 1);
+      add(&ACC(b, col), 1);
+    }
+  }
+}
+
+/* SG: trigger a1 = s->m1, expand m1.out -> b1 = m1->d (for_all), then the
+ * second leg from the intersection of s.out and d.in: a2 = s->m2, b2 = m2->d.
+ * Requiring m2 > m1 finds each unordered pair of legs exactly once. */
+static void canon_sg(const og_graph* g, int col, int ncols, int64_t delta, uint64_t* acc,
+                     int nth) {
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nth)
+  for (int64_t a1 = 0; a1 < g->E; ++a1) {
+    if (g->pos_out[a1] < 0) continue;
+    int32_t s = g->src[a1], m1 = g->dst[a1];
+    int64_t lo = g->ts[a1];
+    int64_t j_end = g->out_start[m1 + 1];
+    for (int64_t j = first_after(g, g->out_list, g->out_start[m1], j_end, a1); j < j_end; ++j) {
+      int64_t b1 = g->out_list[j];
+      int64_t hi = g->ts[b1];
+      if (hi - lo > delta) break;
+      int32_t d = g->dst[b1];
+      if (d == s) continue;
+      int64_t i_end = g->out_start[s + 1];
+      for (int64_t i = find_start(g, g->out_list, g->out_start[s], i_end, hi - delta); i < i_end;
+           ++i) {
+        int64_t a2 = g->out_list[i];
+        if ((int64_t)g->ts[a2] > lo + delta) break;
+        int32_t m2 = g->dst[a2];
+        if (m2 <= m1 || m2 == d) continue;
+        int64_t lo2 = lo < g->ts[a2] ? lo : g->ts[a2];
+        int64_t q_end = g->out_start[m2 + 1];
+        for (int64_t q = first_after(g, g->out_list, g->out_start[m2], q_end, a2); q < q_end; ++q) {
+          int64_t b2 = g->out_list[q];
+          if ((int64_t)g->ts[b2] > lo2 + delta) break;
+          if (g->dst[b2] != d) continue;
+          int64_t mx = hi > g->ts[b2] ? hi : g->ts[b2];
+          if (mx - lo2 > delta) continue;
+          add(&ACC(a1, col), 1);
+          add(&ACC(b1, col), 1);
+          add(&ACC(a2, col), 1);
+          add(&ACC(b2, col), 1);
+        }
+      }
+    }
+  }
+}
+
+/* CYC: depth-first from each edge taken as the cycle's earliest edge e1 =
+ * u0->u1; each hop goes to a later edge inside t(e1)+delta and to a node not
+ * yet on the path; an edge back into u0 closes a cycle of length depth+1. */
+typedef struct {
+  const og_graph* g;
+  int K;
+  const int* colmap; /* colmap[k] = column of CYC_k for this delta, or -1 */
+  int ncols;
+  uint64_t* acc;
+  int64_t tmax;
+  int64_t edges[16];
+  int32_t nodes[17];
+} cyc_ctx;
+
+static void cyc_dfs(cyc_ctx* c, int depth) {
+  const og_graph* g = c->g;
+  int ncols = c->ncols;
+  uint64_t* acc = c->acc;
+  int32_t w = c->nodes[depth];
+  int64_t end = g->out_start[w + 1];
+  for (int64_t i = first_after(g, g->out_list, g->out_start[w], end, c->edges[depth - 1]);
+       i < end; ++i) {
+    int64_t f = g->out_list[i];
+    if ((int64_t)g->ts[f] > c->tmax) break;
+    int32_t x = g->dst[f];
+    if (x == c->nodes[0]) {
+      int k = depth + 1;
+      if (k <= c->K && c->colmap[k] >= 0) {
+        for (int j = 0; j < depth; ++j) add(&ACC(c->edges[j], c->colmap[k]), 1);
+        add(&ACC(f, c->colmap[k]), 1);
+      }
+      continue;
+    }
+    if (depth + 1 >= c->K) continue;
+    int seen = 0;
+    for (int j = 1; j <= depth; ++j) seen |= (c->nodes[j] == x);
+    if (seen) continue;
+    c->edges[depth] = f;
+    c->nodes[depth + 1] = x;
+    cyc_dfs(c, depth + 1);
+  }
+}
+
+static void canon_cyc(const og_graph* g, int K, const int* colmap, int ncols, int64_t delta,
+                      uint64_t* acc, int nth) {
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nth)
+  for (int64_t e1 = 0; e1 < g->E; ++e1) {
+    if (g->pos_out[e1] < 0) continue;
+    cyc_ctx c;
+    c.g = g;
+    c.K = K;
+    c.colmap = colmap;
+    c.ncols = ncols;
+    c.acc = acc;
+    c.tmax = (int64_t)g->ts[e1] + delta;
+    c.edges[0] = e1;
+    c.nodes[0] = g->src[e1];
+    c.nodes[1] = g->dst[e1];
+    cyc_dfs(&c, 1);
+  }
+}
+
+static int check_cols(const og_col* cols, int32_t ncols) {
+  for (int i = 0; i < ncols; ++i) {
+    if (cols[i].kind < OG_DEG_OUT || cols[i].kind > OG_CYC) return -1;
+    if (cols[i].delta < 0) return -1;
+    if (cols[i].kind == OG_CYC && (cols[i].k < 2 || cols[i].k > 15)) return -1;
+  }
+  return 0;
+}
+
+static void clamp_out(const uint64_t* acc, uint32_t* out, size_t n) {
+  for (size_t i = 0; i < n; ++i) out[i] = acc[i] > 0xffffffffull ? 0xffffffffu : (uint32_t)acc[i];
+}
+
+int og_count_all(const og_graph* g, const og_col* cols, int32_t ncols, uint32_t* out,
+                 int32_t nthreads) {
+  if (!g || ncols <= 0 || check_cols(cols, ncols)) return -1;
+  int nth = nthreads > 0 ? nthreads : omp_get_max_threads();
+  size_t n = (size_t)g->E * (size_t)ncols;
+  uint64_t* acc = (uint64_t*)calloc(n ? n : 1, 8);
+  if (!acc) return -2;
+  int32_t mr = max_row(g);
+  char* done = (char*)calloc((size_t)ncols, 1);
+  for (int c = 0; c < ncols; ++c) {
+    int kind = cols[c].kind;
+    int64_t delta = cols[c].delta;
+    if (kind <= OG_FAN_IN) {
+      int outgoing = (kind == OG_DEG_OUT || kind == OG_FAN_OUT);
+      int is_fan = (kind == OG_FAN_OUT || kind == OG_FAN_IN);
+#pragma omp parallel num_threads(nth)
+      {
+        int32_t* buf = (int32_t*)malloc((size_t)mr * 4);
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t e = 0; e < g->E; ++e) {
+          if (g->pos_out[e] < 0) continue;
+          ACC(e, c) = is_fan ? fan_sorted(g, e, outgoing, delta, buf) : deg(g, e, outgoing, delta);
+        }
+        free(buf);
+      }
+    } else if (kind == OG_GS) {
+      canon_gs(g, c, ncols, delta, acc, nth);
+    } else if (kind == OG_SG) {
+      canon_sg(g, c, ncols, delta, acc, nth);
+    } else if (kind == OG_CYC && !done[c]) {
+      /* one depth-first search serves every cycle length with this delta */
+      int colmap[17];
+      for (int k = 0; k < 17; ++k) colmap[k] = -1;
+      int K = 0;
+      for (int c2 = c; c2 < ncols; ++c2) {
+        if (cols[c2].kind == OG_CYC && cols[c2].delta == delta && !done[c2]) {
+          if (colmap[cols[c2].k] < 0) {
+            colmap[cols[c2].k] = c2;
+            done[c2] = 1;
+            if (cols[c2].k > K) K = cols[c2].k;
+          }
+        }
+      }
+      canon_cyc(g, K, colmap, ncols, delta, acc, nth);
+      /* duplicate columns (same k and delta) copy the first one */
+      for (int c2 = c; c2 < ncols; ++c2)
+        if (cols[c2].kind == OG_CYC && cols[c2].delta == delta && !done[c2]) {
+          int src_c = colmap[cols[c2].k];
+          for (int64_t e = 0; e < g->E; ++e) ACC(e, c2) = ACC(e, src_c);
+          done[c2] = 1;
+        }
+    }
+  }
+  clamp_out(acc, out, n);
+  free(acc);
+  free(done);
+  return 0;
+}
+
+/* ---------------- edge-centric queries ---------------- */
+
+static uint64_t ec_gs(const og_graph* g, int64_t e, int64_t delta) {
+  uint64_t cnt = 0;
+  /* e as the gather leg a = x->h: later b = h->y, y != x */
+  int32_t x = g->src[e], h = g->dst[e];
+  int64_t end = g->out_start[h + 1];
+  for (int64_t i = first_after(g, g->out_list, g->out_start[h], end, e); i < end; ++i) {
+    int64_t b = g->out_list[i];
+    if ((int64_t)g->ts[b] - g->ts[e] > delta) break;
+    if (g->dst[b] != x) ++cnt;
+  }
+  /* e as the scatter leg b = h->y: earlier a = x->h, x != y */
+  h = g->src[e];
+  int32_t y = g->dst[e];
+  int64_t lo = find_start(g, g->in_list, g->in_start[h], g->in_start[h + 1],
+                          (int64_t)g->ts[e] - delta);
+  for (int64_t i = lo; i < g->in_start[h + 1]; ++i) {
+    int64_t a = g->in_list[i];
+    if (!prec(g, a, e)) break;
+    if (g->src[a] != y) ++cnt;
+  }
+  return cnt;
+}
+
+/* number of legs (a2 = s->m2, b2 = m2->d) with m2 != m1, a2 < b2, whose union
+ * with the leg spanning [lo, hi] spans at most delta; enumerated gather-first
+ * through d.in and m2.in (the canonical pass goes scatter-first) */
+static uint64_t ec_partners(const og_graph* g, int32_t s, int32_t d, int32_t m1, int64_t lo,
+                            int64_t hi, int64_t delta) {
+  uint64_t cnt = 0;
+  int64_t end = g->in_start[d + 1];
+  for (int64_t i = find_start(g, g->in_list, g->in_start[d], end, hi - delta); i < end; ++i) {
+    int64_t b2 = g->in_list[i];
+    int64_t tb = g->ts[b2];
+    if (tb > lo + delta) break;
+    int32_t m2 = g->src[b2];
+    if (m2 == m1) continue;
+    int64_t mx = hi > tb ? hi : tb;
+    int64_t jend = g->in_start[m2 + 1];
+    for (int64_t j = find_start(g, g->in_list, g->in_start[m2], jend, mx - delta); j < jend; ++j) {
+      int64_t a2 = g->in_list[j];
+      if (!prec(g, a2, b2)) break;
+      if (g->src[a2] != s) continue;
+      int64_t mn = lo < g->ts[a2] ? lo : g->ts[a2];
+      if (mx - mn <= delta) ++cnt;
+    }
+  }
+  return cnt;
+}
+
+static uint64_t ec_sg(const og_graph* g, int64_t e, int64_t delta) {
+  uint64_t cnt = 0;
+  /* e = s->m1 as the scatter edge of its leg */
+  int32_t s = g->src[e], m1 = g->dst[e];
+  int64_t end = g->out_start[m1 + 1];
+  for (int64_t j = first_after(g, g->out_list, g->out_start[m1], end, e); j < end; ++j) {
+    int64_t b1 = g->out_list[j];
+    if ((int64_t)g->ts[b1] - g->ts[e] > delta) break;
+    int32_t d = g->dst[b1];
+    if (d == s) continue;
+    cnt += ec_partners(g, s, d, m1, g->ts[e], g->ts[b1], delta);
+  }
+  /* e = m1->d as the gather edge of its leg */
+  m1 = g->src[e];
+  int32_t d = g->dst[e];
+  end = g->in_start[m1 + 1];
+  for (int64_t j = find_start(g, g->in_list, g->in_start[m1], end, (int64_t)g->ts[e] - delta);
+       j < end; ++j) {
+    int64_t a1 = g->in_list[j];
+    if (!prec(g, a1, e)) break;
+    int32_t s2 = g->src[a1];
+    if (s2 == d) continue;
+    cnt += ec_partners(g, s2, d, m1, g->ts[a1], g->ts[e], delta);
+  }
+  return cnt;
+}
+
+/* cycles through e = x->y: simple paths y -> ... -> x of k-1 edges inside
+ * [t_e - delta, t_e + delta]; a closed walk is a temporal cycle iff its edge
+ * sequence, read cyclically, has exactly one descent under <, and it spans
+ * at most delta */
+typedef struct {
+  const og_graph* g;
+  int k;
+  int64_t delta, tlo, thi;
+  int64_t edges[16];
+  int32_t nodes[17];
+  uint64_t cnt;
+} ec_cyc_ctx;
+
+static void ec_cyc_dfs(ec_cyc_ctx* c, int depth, int64_t mint, int64_t maxt, int ndesc) {
+  const og_graph* g = c->g;
+  int32_t w = c->nodes[depth];
+  int32_t x = c->nodes[0];
+  int64_t end = g->out_start[w + 1];
+  for (int64_t i = find_start(g, g->out_list, g->out_start[w], end, c->tlo); i < end; ++i) {
+    int64_t f = g->out_list[i];
+    int64_t tf = g->ts[f];
+    if (tf > c->thi) break;
+    int32_t z = g->dst[f];
+    int nd = ndesc + prec(g, f, c->edges[depth - 1]);
+    int64_t mn = mint < tf ? mint : tf, mx = maxt > tf ? maxt : tf;
+    if (mx - mn > c->delta) continue;
+    if (depth + 1 == c->k) {
+      if (z != x) continue;
+      nd += prec(g, c->edges[0], f);
+      if (nd == 1) c->cnt++;
+      continue;
+    }
+    if (z == x || nd > 1) continue;
+    int seen = 0;
+    for (int j = 1; j <= depth; ++j) seen |= (c->nodes[j] == z);
+    if (seen) continue;
+    c->edges[depth] = f;
+    c->nodes[depth + 1] = z;
+    ec_cyc_dfs(c, depth + 1, mn, mx, nd);
+  }
+}
+
+static uint64_t ec_cyc(const og_graph* g, int64_t e, int k, int64_t delta) {
+  ec_cyc_ctx c;
+  c.g = g;
+  c.k = k;
+  c.delta = delta;
+  c.tlo = (int64_t)g->ts[e] - delta;
+  c.thi = (int64_t)g->ts[e] + delta;
+  c.edges[0] = e;
+  c.nodes[0] = g->src[e];
+  c.nodes[1] = g->dst[e];
+  c.cnt = 0;
+  ec_cyc_dfs(&c, 1, g->ts[e], g->ts[e], 0);
+  return c.cnt;
+}
+
+int og_count_edges(const og_graph* g, const og_col* cols, int32_t ncols, const int64_t* eids,
+                   int64_t n, uint32_t* out, int32_t nthreads) {
+  if (!g || ncols <= 0 || check_cols(cols, ncols) || n < 0) return -1;
+  for (int64_t i = 0; i < n; ++i)
+    if (eids[i] < 0 || eids[i] >= g->E) return -1;
+  int nth = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel num_threads(nth)
+  {
+    int64_t* stamp = (int64_t*)malloc(((size_t)g->N + 1) * 8);
+    for (int32_t u = 0; u < g->N; ++u) stamp[u] = -1;
+    int64_t qid = 0; /* fresh stamp for every window scanned by this thread */
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t e = eids[i];
+      for (int c = 0; c < ncols; ++c) {
+        uint64_t v = 0;
+        if (g->pos_out[e] >= 0) {
+          int64_t delta = cols[c].delta;
+          switch (cols[c].kind) {
+            case OG_DEG_OUT: v = deg(g, e, 1, delta); break;
+            case OG_DEG_IN: v = deg(g, e, 0, delta); break;
+            case OG_FAN_OUT: v = fan_stamp(g, e, 1, delta, stamp, ++qid); break;
+            case OG_FAN_IN: v = fan_stamp(g, e, 0, delta, stamp, ++qid); break;
+            case OG_GS: v = ec_gs(g, e, delta); break;
+            case OG_SG: v = ec_sg(g, e, delta); break;
+            case OG_CYC: v = ec_cyc(g, e, cols[c].k, delta); break;
+          }
+        }
+        out[(size_t)i * (size_t)ncols + (size_t)c] = v > 0xffffffffull ? 0xffffffffu : (uint32_t)v;
+      }
+    }
+    free(stamp);
+  }
+  return 0;
+}
