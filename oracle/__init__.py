@@ -44,21 +44,26 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
+def load_library(path: str) -> ctypes.CDLL:
+    """Load an oracle shared library and declare its signatures."""
+    lib = ctypes.CDLL(path)
+    lib.og_graph_new.restype = ctypes.c_void_p
+    lib.og_graph_new.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_int32]
+    lib.og_graph_free.argtypes = [ctypes.c_void_p]
+    lib.og_count_all.restype = ctypes.c_int
+    lib.og_count_all.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                 ctypes.c_void_p, ctypes.c_int32]
+    lib.og_count_edges.restype = ctypes.c_int
+    lib.og_count_edges.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_int32]
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        lib.og_graph_new.restype = ctypes.c_void_p
-        lib.og_graph_new.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_int32]
-        lib.og_graph_free.argtypes = [ctypes.c_void_p]
-        lib.og_count_all.restype = ctypes.c_int
-        lib.og_count_all.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
-                                     ctypes.c_void_p, ctypes.c_int32]
-        lib.og_count_edges.restype = ctypes.c_int
-        lib.og_count_edges.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
-                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
-                                       ctypes.c_int32]
-        _lib = lib
+        _lib = load_library(build())
     return _lib
 
 
@@ -75,8 +80,8 @@ def _cols(cols: Sequence[Tuple]) -> ctypes.Array:
 class OracleGraph:
     """Host copy of the graph with (t,id)-sorted out/in rows."""
 
-    def __init__(self, src, dst, ts, n_nodes: int):
-        lib = _load()
+    def __init__(self, src, dst, ts, n_nodes: int, lib: ctypes.CDLL = None):
+        self._lib = lib = lib if lib is not None else _load()
         self._src = np.ascontiguousarray(src, dtype=np.int32)
         self._dst = np.ascontiguousarray(dst, dtype=np.int32)
         self._ts = np.ascontiguousarray(ts, dtype=np.int32)
@@ -89,7 +94,7 @@ class OracleGraph:
 
     def close(self):
         if getattr(self, "_h", None):
-            _load().og_graph_free(self._h)
+            self._lib.og_graph_free(self._h)
             self._h = None
 
     def __del__(self):
@@ -98,7 +103,7 @@ class OracleGraph:
     def count_all(self, cols: Sequence[Tuple], threads: int = 0) -> np.ndarray:
         """Canonical enumeration over the whole graph: uint32 [E, len(cols)]."""
         out = np.zeros((self.n_edges, len(cols)), dtype=np.uint32)
-        rc = _load().og_count_all(self._h, ctypes.byref(_cols(cols)), len(cols),
+        rc = self._lib.og_count_all(self._h, ctypes.byref(_cols(cols)), len(cols),
                                   out.ctypes.data, threads)
         if rc:
             raise ValueError(f"og_count_all failed ({rc})")
@@ -110,7 +115,7 @@ class OracleGraph:
         ids = np.ascontiguousarray(np.asarray(list(eids) if not isinstance(eids, np.ndarray)
                                               else eids, dtype=np.int64))
         out = np.zeros((ids.shape[0], len(cols)), dtype=np.uint32)
-        rc = _load().og_count_edges(self._h, ctypes.byref(_cols(cols)), len(cols),
+        rc = self._lib.og_count_edges(self._h, ctypes.byref(_cols(cols)), len(cols),
                                     ids.ctypes.data, ids.shape[0], out.ctypes.data, threads)
         if rc:
             raise ValueError(f"og_count_edges failed ({rc})")

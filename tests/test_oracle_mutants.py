@@ -1,0 +1,76 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case below plants one mistake (a dropped term, a flipped comparison, an
+off-by-one index, a wrong operand) in a temporary copy of the oracle's C
+source, compiles it on the CPU, and checks that the brute-force pins reject
+the mutant.  The oracle under oracle/ is never modified.
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import aml_synth
+import oracle
+from brute import brute_counts
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "aml_oracle.c")
+
+# (name, original text, mutated text) -- every original must occur exactly once
+MUTANTS = [
+    ("prec-tie-reversed", "(g->ts[f] == g->ts[e] && f < e)", "(g->ts[f] == g->ts[e] && f > e)"),
+    ("find-start-exclusive", "if ((int64_t)g->ts[list[mid]] < tmin) lo",
+     "if ((int64_t)g->ts[list[mid]] <= tmin) lo"),
+    ("deg-off-by-one", "return (uint64_t)(pos - lo + 1);", "return (uint64_t)(pos - lo);"),
+    ("fan-counts-repeats", "if (i == 0 || buf[i] != buf[i - 1]) ++d;", "++d;"),
+    ("gs-keeps-reciprocal", "      if (g->dst[b] == x) continue;                       /* skip_if: y == x */\n",
+     ""),
+    ("gs-window-open", "if ((int64_t)g->ts[b] - g->ts[a] > delta) break;  /* break_if",
+     "if ((int64_t)g->ts[b] - g->ts[a] >= delta) break;  /* break_if"),
+    ("sg-same-intermediary", "if (m2 <= m1 || m2 == d) continue;", "if (m2 < m1 || m2 == d) continue;"),
+    ("sg-span-from-leg1", "int64_t lo2 = lo < g->ts[a2] ? lo : g->ts[a2];", "int64_t lo2 = lo;"),
+    ("sg-leg-order-dropped",
+     "for (int64_t q = first_after(g, g->out_list, g->out_start[m2], q_end, a2); q < q_end; ++q) {",
+     "for (int64_t q = g->out_start[m2]; q < q_end; ++q) {"),
+    ("sg-partner-wrong-operand", "if (g->src[a2] != s) continue;", "if (g->src[a2] == s) continue;"),
+    ("cyc-credit-skips-first", "for (int j = 0; j < depth; ++j) add(",
+     "for (int j = 1; j < depth; ++j) add("),
+    ("cyc-not-simple", "for (int j = 1; j <= depth; ++j) seen |= (c->nodes[j] == x);",
+     "for (int j = 2; j <= depth; ++j) seen |= (c->nodes[j] == x);"),
+    ("ec-cyc-descents", "if (nd == 1) c->cnt++;", "if (nd <= 2) c->cnt++;"),
+]
+
+COLS = [("deg_out", 5), ("deg_in", 5), ("fan_out", 5), ("fan_in", 5), ("gs", 5), ("sg", 6),
+        ("sg", 100), ("cyc", 2, 6), ("cyc", 3, 6), ("cyc", 4, 8), ("cyc", 5, 9)]
+
+
+def _pins_reject(lib) -> bool:
+    for seed in range(80):
+        n = 3 + seed % 6
+        E = 8 + seed % 15
+        g = aml_synth.tiny_random(n, E, 10 + seed % 7, seed, self_loops=(seed % 3 == 0))
+        og = oracle.OracleGraph(g.src, g.dst, g.ts, n, lib=lib)
+        want = brute_counts(g.src, g.dst, g.ts, COLS)
+        if not np.array_equal(og.count_all(COLS, threads=1), want):
+            return True
+        if not np.array_equal(og.count_edges(COLS, np.arange(E), threads=1), want):
+            return True
+    return False
+
+
+@pytest.mark.parametrize("name,orig,mutated", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_reject_mutant(tmp_path, name, orig, mutated):
+    text = open(SRC).read()
+    assert text.count(orig) == 1, f"mutation site for {name} not unique"
+    path = tmp_path / "mutant.c"
+    path.write_text(text.replace(orig, mutated))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-I", os.path.dirname(SRC), "-o", str(so), str(path)])
+    lib = oracle.load_library(str(so))
+    assert _pins_reject(lib), f"mutant {name} survived the pins"
+
+
+def test_unmutated_oracle_passes(tmp_path):
+    assert not _pins_reject(oracle._load())
