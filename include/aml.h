@@ -1,0 +1,231 @@
+/*
+ * aml.h -- C ABI of the B300 per-edge AML pattern-counting library.
+ *
+ * The library counts, for every transaction edge of a temporal transaction
+ * graph, how many instances of each multi-stage laundering pattern the edge
+ * takes part in, and writes an E x P uint32 feature matrix (one column per
+ * pattern).  This is the mining front end of the paper's pipeline (Sec. 1,
+ * Fig. 1: "augments each transaction edge with pattern occurrence counts");
+ * patterns are given as stage programs in the paper's multi-stage framework
+ * (Sec. 5; stage configuration of Alg. 1 and Sec. 6 "Input specification").
+ *
+ * Conventions for every call:
+ *   - No C++ exception, abort or exit crosses this boundary.  Every call
+ *     returns an aml_status; on failure aml_last_error() gives a message
+ *     (thread-local, valid until the calling thread's next failing call).
+ *   - CUDA errors map to AML_ECUDA.  Kernel faults are asynchronous and
+ *     surface at aml_sync() or at the next call on the same object.
+ *   - "device pointer" = memory of the current CUDA device (cudaMalloc,
+ *     cudaMallocAsync, torch.cuda tensors); "host pointer" = ordinary or
+ *     pinned host memory.  Pointer arguments are never retained unless
+ *     stated: the library copies what it keeps.
+ *   - `stream` is a cudaStream_t passed as void*; NULL = the legacy default
+ *     stream.  Work is enqueued on it; calls return before it finishes
+ *     unless stated.
+ *   - The library owns graphs, pattern sets and its scratch memory; the
+ *     caller owns its inputs and the output matrix.
+ *   - Edge ids are input positions 0..E-1 and E < 2^31; node ids are in
+ *     [0, n_nodes).  Timestamps are int32 seconds.
+ */
+#ifndef AML_H
+#define AML_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+
+typedef int32_t aml_status;
+#define AML_OK 0
+#define AML_EINVAL 1        /* bad argument (null pointer, size, id, flag)        */
+#define AML_ENOMEM 2        /* device or host allocation failed                   */
+#define AML_ECUDA 3         /* a CUDA runtime call or kernel failed               */
+#define AML_EUNSUPPORTED 4  /* well-formed stage program no kernel implements     */
+#define AML_EUNSORTED 5     /* AML_ASSUME_SORTED given but timestamps decrease     */
+#define AML_ELATE 6         /* streamed batch older than the stream's clock        */
+#define AML_EADMIT 7        /* streamed batch refused by the memory budget         */
+#define AML_ETIMEOUT 8      /* a bounded device-side wait gave up                  */
+#define AML_EINTERNAL 9     /* internal invariant violated (device error word)     */
+
+/* Static string naming a status ("AML_OK", ...); never NULL. */
+const char* aml_status_str(aml_status s);
+/* Message of the calling thread's last failing call ("" if none); never NULL. */
+const char* aml_last_error(void);
+/* Library version as 10000*major + 100*minor + patch. */
+int32_t aml_version(void);
+
+/* ------------------------------------------------------------------- graph */
+
+/* The transaction graph (Sec. 2.3: node = account, edge = transaction with
+ * amount and time).  Built on the device: edges ordered by (timestamp, id);
+ * per-account out-lists (CSR) and in-lists (CSC) sorted by (t, id) so that
+ * every time window is a contiguous range found by binary search (Alg. 1's
+ * Find_Starting_Edge; Sec. 6 "sorted neighbor lists and binary search"), plus
+ * a second per-account order by (counterparty, t, id) for membership tests
+ * in intersections.  Self-loops (src == dst) are kept as edges but belong to
+ * no list: every pattern count of a self-loop is 0. */
+typedef struct aml_graph aml_graph;
+
+#define AML_PTR_HOST 0x0u       /* src/dst/ts/amount are host pointers            */
+#define AML_PTR_DEVICE 0x1u     /* ... are device pointers                         */
+#define AML_ASSUME_SORTED 0x2u  /* caller promises ts non-decreasing in id order;  */
+                                /* verified on the device (AML_EUNSORTED if not)   */
+
+/* Build a graph from E transactions.
+ *   src, dst : int32[E] account ids in [0, n_nodes)
+ *   ts       : int32[E] timestamps (seconds); any order unless ASSUME_SORTED
+ *   amount   : float[E] transaction amounts, or NULL (stored; no current
+ *              pattern constrains amounts)
+ *   n_edges  : E, 0 <= E < 2^31;  n_nodes: 1 <= N < 2^31
+ *   flags    : AML_PTR_* | AML_ASSUME_SORTED
+ *   stream   : stream for the copies and the build; the call synchronizes it
+ *              before returning (the graph is ready on return)
+ *   out      : receives the graph handle (unchanged on failure)
+ * Errors: AML_EINVAL (null pointers, sizes, an id outside [0, N)),
+ * AML_EUNSORTED, AML_ENOMEM, AML_ECUDA.  The inputs are copied. */
+aml_status aml_graph_create(const int32_t* src, const int32_t* dst, const int32_t* ts,
+                            const float* amount, int64_t n_edges, int32_t n_nodes,
+                            uint32_t flags, void* stream, aml_graph** out);
+
+/* Free a graph and everything cached on it (NULL is a no-op).  Synchronizes
+ * the device work previously enqueued on the graph. */
+aml_status aml_graph_destroy(aml_graph* g);
+
+typedef struct aml_graph_info {
+  int64_t n_edges;        /* E as given                                       */
+  int64_t n_list_edges;   /* edges in the lists (E minus self-loops)          */
+  int32_t n_nodes;
+  int32_t max_out_degree;
+  int32_t max_in_degree;
+  int32_t reserved;
+  int64_t device_bytes;   /* device memory held by the graph                  */
+} aml_graph_info;
+
+aml_status aml_graph_get_info(const aml_graph* g, aml_graph_info* info);
+
+/* ----------------------------------------------------------- stage programs */
+
+/* One stage of a multi-stage pattern (Sec. 5; per-stage configuration of
+ * Alg. 1: operation, input node set, output variable, skip_if / break_if
+ * constraints including the time window).  Node variables N0, N1, ... are
+ * numbered in binding order; the trigger binds N0 -> N1. */
+#define AML_OP_TRIGGER 0    /* stage 0: the anchor transaction N0 -> N1          */
+#define AML_OP_FOR_ALL 1    /* iterate the neighbours of one bound node         */
+#define AML_OP_INTERSECT 2  /* nodes in both of two neighbour sets               */
+
+#define AML_DIR_OUT 0       /* Nx.out_neigh: edges leaving Nx                    */
+#define AML_DIR_IN 1        /* Nx.in_neigh: edges entering Nx                    */
+
+#define AML_ORDER_NONE 0    /* no ordering constraint on the matched edge(s)     */
+#define AML_ORDER_AFTER 1   /* matched edge comes after the edge that reached    */
+                            /* the operand's node (causal flow of funds)         */
+#define AML_ORDER_BEFORE 2  /* ... comes before it                               */
+#define AML_ORDER_LEG 3     /* INTERSECT: a-side edge before b-side edge         */
+
+#define AML_WIN_TRAILING 0  /* edge time in [t_trigger - delta, trigger]         */
+#define AML_WIN_SPAN 1      /* all edges of an instance within delta             */
+
+typedef struct aml_stage {
+  int32_t op;        /* AML_OP_*                                                */
+  int32_t a_var;     /* first operand: node variable ...                        */
+  int32_t a_dir;     /* ... and its neighbour set (AML_DIR_*)                   */
+  int32_t b_var;     /* second operand (INTERSECT only; else -1)                */
+  int32_t b_dir;
+  int32_t out_var;   /* variable this stage binds; naming an already bound      */
+                     /* variable closes the walk onto that node                 */
+  int32_t order;     /* AML_ORDER_*                                             */
+  int32_t window;    /* AML_WIN_*                                               */
+  uint32_t skip_eq;  /* skip_if: bit i set = drop candidates equal to N_i       */
+                     /* (the paper's "differentiate", e.g. N2 != N0)            */
+} aml_stage;
+
+/* What the final stage's Postprocess reports for each trigger edge. */
+#define AML_AGG_EDGES 0      /* # matched edges (windowed degree)               */
+#define AML_AGG_DISTINCT 1   /* # distinct matched nodes (fan-in / fan-out)     */
+#define AML_AGG_INSTANCES 2  /* # pattern instances containing the edge, each   */
+                             /* instance credited to all of its edges           */
+                             /* (Sec. 5: an edge "increments counts for all     */
+                             /* pattern instances it participates in")          */
+
+typedef struct aml_pattern {
+  const aml_stage* stages;   /* read during aml_pattern_set_create only          */
+  int32_t n_stages;
+  int32_t aggregate;         /* AML_AGG_*                                        */
+  int32_t delta;             /* time window in seconds, >= 0                     */
+  int32_t reserved;          /* must be 0                                        */
+} aml_pattern;
+
+/* Pattern families the planner maps stage programs onto (one output column
+ * per pattern).  Exact semantics (e = u->v at time t_e; f < e means
+ * (t_f, f) < (t_e, e); counts saturate at 2^32-1):
+ *   DEG_OUT  #{f : src f = u, f <= e, t_f >= t_e - delta}   (DEG_IN: dst f = v)
+ *   FAN_OUT  #distinct dst f over the same edges             (FAN_IN: distinct src)
+ *   GS       gather-scatter 2-paths a = x->h, b = h->y, x != y, a < b,
+ *            t_b - t_a <= delta, counted on a and on b
+ *   SG       scatter-gather: unordered pairs of legs (s->m1->d, s->m2->d),
+ *            s != d, m1 != m2, scatter before gather in each leg, all four
+ *            edges within delta, counted on all four (Sec. 5, Fig. 4a)
+ *   CYC_k    simple directed k-cycles whose edges increase in time around the
+ *            cycle from the earliest, spanning <= delta (Sec. 5, Fig. 4b)   */
+#define AML_FAM_DEG_OUT 0
+#define AML_FAM_DEG_IN 1
+#define AML_FAM_FAN_OUT 2
+#define AML_FAM_FAN_IN 3
+#define AML_FAM_GS 4
+#define AML_FAM_SG 5
+#define AML_FAM_CYC 6
+
+typedef struct aml_pattern_set aml_pattern_set;
+
+/* Validate and plan n patterns; column j of the output is pattern j.
+ * Validation (Sec. 6: "validates operand dependencies between stages"):
+ * stage 0 is the trigger; every operand names a variable bound by an
+ * earlier stage; skip masks name bound variables; windows and orders are in
+ * range.  A valid program the planner cannot map onto a family returns
+ * AML_EUNSUPPORTED and names the stage in aml_last_error().  Host-only; no
+ * device work. */
+aml_status aml_pattern_set_create(const aml_pattern* patterns, int32_t n_patterns,
+                                  aml_pattern_set** out);
+aml_status aml_pattern_set_destroy(aml_pattern_set* ps);
+
+typedef struct aml_column_info {
+  int32_t family;   /* AML_FAM_*                          */
+  int32_t k;        /* cycle length (CYC), else 0         */
+  int32_t delta;    /* window seconds                     */
+  int32_t reserved;
+  char name[32];    /* e.g. "FAN_OUT@86400", "CYC4@604800" */
+} aml_column_info;
+
+aml_status aml_pattern_set_num_columns(const aml_pattern_set* ps, int32_t* n_cols);
+aml_status aml_pattern_set_column(const aml_pattern_set* ps, int32_t col,
+                                  aml_column_info* info);
+
+/* ------------------------------------------------------------------ mining */
+
+#define AML_MINE_HOST_OUTPUT 0x1u  /* counts is a host pointer (copied back)     */
+
+/* Count every pattern of `ps` for every edge of `g`.
+ *   counts : uint32, row-major, row e = input edge e, column j = pattern j;
+ *            element (e, j) at counts[e * ld + j].  Device pointer unless
+ *            AML_MINE_HOST_OUTPUT (then the call synchronizes `stream`).
+ *            Columns >= n_cols of each row are left untouched.
+ *   ld     : row stride in elements, ld >= n_cols
+ *   flags  : AML_MINE_* (unknown bits: AML_EINVAL)
+ * The first call for a given (graph, window) sizes the intermediate buffers
+ * and synchronizes `stream` once; later calls enqueue work only.
+ * Errors: AML_EINVAL, AML_ENOMEM, AML_ECUDA. */
+aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
+                    uint32_t flags, void* stream);
+
+/* Wait for the graph's enqueued work and report device-side errors
+ * (AML_ETIMEOUT, AML_EINTERNAL) recorded by its kernels since the last call. */
+aml_status aml_sync(aml_graph* g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AML_H */

@@ -1,0 +1,159 @@
+"""B300-native per-edge AML pattern counting (multi-stage graph mining).
+
+Thin Python layer over the C ABI of ``libaml_b300.so`` (include/aml.h):
+argument marshalling only, every step of the computation runs in the
+library's CUDA kernels.  PyTorch provides device memory and streams.
+
+    import paper_2604_12241_b300 as aml
+    g = aml.Graph(src, dst, ts, n_nodes)                 # numpy (host) or torch CUDA tensors
+    ps = aml.PatternSet(aml.patterns.standard(86400))    # stage programs -> columns
+    counts = aml.mine(g, ps)                             # torch int32 [E, P] (uint32 bits)
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import patterns  # noqa: F401
+from ._lib import (ASSUME_SORTED, MINE_HOST_OUTPUT, PTR_DEVICE, PTR_HOST, AmlError,  # noqa: F401
+                   aml_column_info, aml_graph_info, check, lib, make_patterns)
+
+__all__ = ["Graph", "PatternSet", "mine", "AmlError", "patterns"]
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(x):
+    """(pointer, is_device) of a numpy array or torch tensor (contiguous)."""
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("arrays must be contiguous")
+        return x.ctypes.data, False
+    import torch
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr(), x.is_cuda
+    raise TypeError(type(x))
+
+
+class Graph:
+    """Device-resident transaction graph (aml_graph_create)."""
+
+    def __init__(self, src, dst, ts, n_nodes: int, amount=None, assume_sorted: bool = False,
+                 stream=None):
+        L = lib()
+        if isinstance(src, np.ndarray):
+            src = np.ascontiguousarray(src, dtype=np.int32)
+            dst = np.ascontiguousarray(dst, dtype=np.int32)
+            ts = np.ascontiguousarray(ts, dtype=np.int32)
+            if amount is not None:
+                amount = np.ascontiguousarray(amount, dtype=np.float32)
+        ps, dev = _ptr(src)
+        pd, _ = _ptr(dst)
+        pt, _ = _ptr(ts)
+        pa = _ptr(amount)[0] if amount is not None else None
+        flags = (PTR_DEVICE if dev else PTR_HOST) | (ASSUME_SORTED if assume_sorted else 0)
+        n_edges = int(src.shape[0])
+        h = ctypes.c_void_p()
+        s = _stream_handle(stream)
+        check(L.aml_graph_create(ps, pd, pt, pa, n_edges, int(n_nodes), flags, s,
+                                 ctypes.byref(h)))
+        self._h = h
+        self.n_edges = n_edges
+        self.n_nodes = int(n_nodes)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = aml_graph_info()
+        check(lib().aml_graph_get_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in inf._fields_ if f != "reserved"}
+
+    def sync(self) -> None:
+        check(lib().aml_sync(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().aml_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PatternSet:
+    """Validated, planned set of stage programs (aml_pattern_set_create)."""
+
+    def __init__(self, pats: Sequence["patterns.Pattern"]):
+        arr, keep = make_patterns(pats)
+        h = ctypes.c_void_p()
+        check(lib().aml_pattern_set_create(arr, len(pats), ctypes.byref(h)))
+        self._h = h
+        self.patterns = list(pats)
+        n = ctypes.c_int32()
+        check(lib().aml_pattern_set_num_columns(h, ctypes.byref(n)))
+        self.n_cols = n.value
+        self.columns = []
+        for j in range(self.n_cols):
+            ci = aml_column_info()
+            check(lib().aml_pattern_set_column(h, j, ctypes.byref(ci)))
+            self.columns.append(dict(family=ci.family, k=ci.k, delta=ci.delta,
+                                     name=ci.name.decode()))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().aml_pattern_set_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mine(graph: Graph, pset: PatternSet, out=None, stream=None, host_output: bool = False):
+    """Per-edge counts, [E, P] (aml_mine).
+
+    Device mode (default) returns / fills a torch int32 CUDA tensor holding
+    the uint32 counts bit-for-bit (``.view(torch.uint32)`` or numpy
+    ``.view(np.uint32)`` to read them unsigned).  ``host_output=True``
+    returns a numpy uint32 array copied back by the library.
+    """
+    P = pset.n_cols
+    E = graph.n_edges
+    s = _stream_handle(stream)
+    if host_output:
+        arr = out if out is not None else np.empty((E, P), dtype=np.uint32)
+        ptr, dev = _ptr(arr)
+        if dev:
+            raise ValueError("host_output needs a host array")
+        check(lib().aml_mine(graph.handle, pset.handle, ptr, arr.shape[1], MINE_HOST_OUTPUT, s))
+        return arr
+    import torch
+    if out is None:
+        out = torch.empty((E, P), dtype=torch.int32, device="cuda")
+    ptr, dev = _ptr(out)
+    if not dev:
+        raise ValueError("device mode needs a CUDA tensor")
+    check(lib().aml_mine(graph.handle, pset.handle, ptr, out.shape[1], 0, s))
+    return out

@@ -1,0 +1,118 @@
+"""ctypes binding of libaml_b300.so (argument marshalling only).
+
+Function names match the C ABI in include/aml.h.  Every status other than
+AML_OK raises ``AmlError`` carrying aml_last_error().  There is no fallback:
+if the shared library is missing or fails to load, importing anything that
+needs it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libaml_b300.so")
+
+STATUS = {0: "AML_OK", 1: "AML_EINVAL", 2: "AML_ENOMEM", 3: "AML_ECUDA", 4: "AML_EUNSUPPORTED",
+          5: "AML_EUNSORTED", 6: "AML_ELATE", 7: "AML_EADMIT", 8: "AML_ETIMEOUT",
+          9: "AML_EINTERNAL"}
+
+PTR_HOST, PTR_DEVICE, ASSUME_SORTED = 0x0, 0x1, 0x2
+MINE_HOST_OUTPUT = 0x1
+
+
+class AmlError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class aml_stage(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("a_var", ctypes.c_int32), ("a_dir", ctypes.c_int32),
+                ("b_var", ctypes.c_int32), ("b_dir", ctypes.c_int32), ("out_var", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("window", ctypes.c_int32), ("skip_eq", ctypes.c_uint32)]
+
+
+class aml_pattern(ctypes.Structure):
+    _fields_ = [("stages", ctypes.POINTER(aml_stage)), ("n_stages", ctypes.c_int32),
+                ("aggregate", ctypes.c_int32), ("delta", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class aml_graph_info(ctypes.Structure):
+    _fields_ = [("n_edges", ctypes.c_int64), ("n_list_edges", ctypes.c_int64),
+                ("n_nodes", ctypes.c_int32), ("max_out_degree", ctypes.c_int32),
+                ("max_in_degree", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class aml_column_info(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int32), ("k", ctypes.c_int32), ("delta", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("name", ctypes.c_char * 32)]
+
+
+_VP = ctypes.c_void_p
+_SIGS = {
+    "aml_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
+    "aml_last_error": (ctypes.c_char_p, []),
+    "aml_version": (ctypes.c_int32, []),
+    "aml_graph_create": (ctypes.c_int32, [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_uint32, _VP, ctypes.POINTER(_VP)]),
+    "aml_graph_destroy": (ctypes.c_int32, [_VP]),
+    "aml_graph_get_info": (ctypes.c_int32, [_VP, ctypes.POINTER(aml_graph_info)]),
+    "aml_pattern_set_create": (ctypes.c_int32, [ctypes.POINTER(aml_pattern), ctypes.c_int32,
+                                                ctypes.POINTER(_VP)]),
+    "aml_pattern_set_destroy": (ctypes.c_int32, [_VP]),
+    "aml_pattern_set_num_columns": (ctypes.c_int32, [_VP, ctypes.POINTER(ctypes.c_int32)]),
+    "aml_pattern_set_column": (ctypes.c_int32, [_VP, ctypes.c_int32,
+                                                ctypes.POINTER(aml_column_info)]),
+    "aml_mine": (ctypes.c_int32, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_uint32, _VP]),
+    "aml_sync": (ctypes.c_int32, [_VP]),
+}
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def exported_names() -> Sequence[str]:
+    return list(_SIGS)
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "or `python -m paper_2604_12241_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status: int) -> None:
+    if status != 0:
+        raise AmlError(status, lib().aml_last_error().decode(errors="replace"))
+
+
+def make_patterns(patterns) -> tuple:
+    """ctypes aml_pattern array (and the stage arrays it points into)."""
+    keep = []
+    arr = (aml_pattern * len(patterns))()
+    for i, p in enumerate(patterns):
+        st = (aml_stage * len(p.stages))()
+        for j, s in enumerate(p.stages):
+            st[j] = aml_stage(s.op, s.a_var, s.a_dir, s.b_var, s.b_dir, s.out_var, s.order,
+                              s.window, s.skip_eq)
+        keep.append(st)
+        arr[i].stages = ctypes.cast(st, ctypes.POINTER(aml_stage))
+        arr[i].n_stages = len(p.stages)
+        arr[i].aggregate = p.aggregate
+        arr[i].delta = p.delta
+        arr[i].reserved = 0
+    return arr, keep

@@ -1,0 +1,214 @@
+// Internal declarations of the B300 AML pattern-counting library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/aml.h"
+
+namespace aml {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const std::string& msg);
+void clear_error();
+
+struct Failure {
+  aml_status status;
+  std::string msg;
+};
+
+#define AML_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t _e = (call);                                                        \
+    if (_e != cudaSuccess)                                                          \
+      throw ::aml::Failure{_e == cudaErrorMemoryAllocation ? AML_ENOMEM : AML_ECUDA, \
+                           std::string(#call) + ": " + cudaGetErrorString(_e)};     \
+  } while (0)
+
+#define AML_REQUIRE(cond, st, msg)                         \
+  do {                                                     \
+    if (!(cond)) throw ::aml::Failure{(st), (msg)};        \
+  } while (0)
+
+// Device error word bits (set with atomicOr by kernels, read by aml_sync).
+enum : uint32_t {
+  ERR_BOUNDS = 1u,    // an index left its buffer (checked builds)
+  ERR_TIMEOUT = 2u,   // a bounded wait gave up
+  ERR_UNSORTED = 4u,  // timestamps decrease although sorted was promised
+  ERR_BAD_ID = 8u,    // a node id outside [0, N)
+  ERR_OVERFLOW = 16u, // an internal counter exceeded its range
+};
+
+// ------------------------------------------------------- device allocation
+
+// Stream-ordered scratch from the device's default memory pool (kept
+// resident by a high release threshold, so steady-state calls reuse it).
+void* dalloc(size_t bytes, cudaStream_t s);
+void dfree(void* p, cudaStream_t s);
+
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  DBuf() = default;
+  DBuf(size_t count, cudaStream_t st) : n(count), s(st) {
+    p = static_cast<T*>(dalloc(count * sizeof(T) + 16, st));
+  }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    reset();
+    p = o.p; n = o.n; s = o.s; o.p = nullptr;
+    return *this;
+  }
+  ~DBuf() { reset(); }
+  void reset() {
+    if (p) dfree(p, s);
+    p = nullptr;
+  }
+};
+
+// ----------------------------------------------------------- device graph
+
+// One adjacency direction: rows = accounts, slots sorted by (t, id) inside
+// each row; the *n arrays hold the same slots re-sorted by (nbr, t, id).
+struct Adj {
+  int32_t* ptr = nullptr;   // [N+1] row offsets (row N holds nothing)
+  int32_t* nbr = nullptr;   // [Ev] counterparty of the slot's edge
+  int32_t* t = nullptr;     // [Ev] timestamp
+  int32_t* eid = nullptr;   // [Ev] edge id
+  int32_t* prev = nullptr;  // [Ev] previous slot of the same row with the same nbr, or -1
+  int32_t* next = nullptr;  // [Ev] next such slot, or INT32_MAX
+  int32_t* nnbr = nullptr;  // [Ev] (nbr, t, id)-sorted copy: counterparty
+  int32_t* nt = nullptr;    //                               timestamp
+  int32_t* neid = nullptr;  //                               edge id
+  int32_t* pos = nullptr;   // [E] slot of edge e in this direction, -1 for self-loops
+};
+
+struct LegCache {
+  int64_t n_legs = -1;      // temporal 2-paths with s != d in the window (GS instances)
+  int64_t* off = nullptr;   // [E+1] first leg of each edge (owned by the graph)
+};
+
+}  // namespace aml
+
+struct aml_graph {
+  int64_t E = 0;
+  int64_t Ev = 0;  // list edges
+  int32_t N = 0;
+  int32_t max_out = 0, max_in = 0;
+  int32_t* src = nullptr;
+  int32_t* dst = nullptr;
+  int32_t* ts = nullptr;
+  float* amount = nullptr;
+  aml::Adj out, in;
+  uint32_t* err = nullptr;  // device error word
+  int64_t bytes = 0;
+  std::vector<void*> allocs;
+  std::map<int32_t, aml::LegCache> legs;  // per window
+  cudaStream_t last_stream = nullptr;
+  int device = 0;
+};
+
+namespace aml {
+
+// ------------------------------------------------------------ primitives
+
+// Exclusive (inclusive=false) or inclusive prefix sum of n values.
+void scan_i32(const int32_t* in, int32_t* out, int64_t n, bool inclusive, cudaStream_t s);
+void scan_i64(const int64_t* in, int64_t* out, int64_t n, bool inclusive, cudaStream_t s);
+// Exclusive scan of int32 counts into int64 offsets; total written to *total_dev.
+void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs by key bits [0, nbits).
+// Sorted result ends in (keys, vals); tmp buffers must hold n elements.
+void radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
+                    int64_t n, int nbits, cudaStream_t s);
+void radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_tmp, uint32_t* vals_tmp,
+                    int64_t n, int nbits, cudaStream_t s);
+
+void iota_i32(int32_t* out, int64_t n, cudaStream_t s);
+
+inline int bits_for(uint64_t max_value) {
+  int b = 1;
+  while (b < 64 && (max_value >> b) != 0) ++b;
+  return b;
+}
+
+inline unsigned grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+// ------------------------------------------------------ pattern planning
+
+struct Column {
+  int32_t family;  // AML_FAM_*
+  int32_t k;       // cycle length
+  int32_t delta;
+};
+
+}  // namespace aml
+
+struct aml_pattern_set {
+  std::vector<aml::Column> cols;
+};
+
+// ---------------------------------------------------------------- helpers
+
+namespace aml {
+
+__device__ __forceinline__ bool before(int32_t tf, int32_t f, int32_t te, int32_t e) {
+  return tf < te || (tf == te && f < e);
+}
+
+// first i in [lo, hi) with t[i] >= tmin (int64 bound so t - delta cannot wrap)
+__device__ __forceinline__ int32_t lower_t(const int32_t* __restrict__ t, int32_t lo, int32_t hi,
+                                           int64_t tmin) {
+  while (lo < hi) {
+    int32_t mid = (int32_t)(((uint32_t)lo + (uint32_t)hi) >> 1);
+    if ((int64_t)__ldg(t + mid) < tmin) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// first i in [lo, hi) with t[i] > tmax
+__device__ __forceinline__ int32_t upper_t(const int32_t* __restrict__ t, int32_t lo, int32_t hi,
+                                           int64_t tmax) {
+  while (lo < hi) {
+    int32_t mid = (int32_t)(((uint32_t)lo + (uint32_t)hi) >> 1);
+    if ((int64_t)__ldg(t + mid) <= tmax) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// first i in [lo, hi) whose edge (t[i], id[i]) comes strictly after (te, e)
+__device__ __forceinline__ int32_t after_edge(const int32_t* __restrict__ t,
+                                              const int32_t* __restrict__ id, int32_t lo,
+                                              int32_t hi, int32_t te, int32_t e) {
+  while (lo < hi) {
+    int32_t mid = (int32_t)(((uint32_t)lo + (uint32_t)hi) >> 1);
+    int32_t tm = __ldg(t + mid);
+    if (tm < te || (tm == te && __ldg(id + mid) <= e)) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// first i in [lo, hi) with nbr[i] >= x
+__device__ __forceinline__ int32_t lower_nbr(const int32_t* __restrict__ nbr, int32_t lo,
+                                             int32_t hi, int32_t x) {
+  while (lo < hi) {
+    int32_t mid = (int32_t)(((uint32_t)lo + (uint32_t)hi) >> 1);
+    if (__ldg(nbr + mid) < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+}  // namespace aml

@@ -1,0 +1,76 @@
+// Kernel-parameter structs shared by the mining kernels and their host code.
+#pragma once
+
+#include "aml_internal.cuh"
+
+namespace aml {
+
+constexpr int MAX_COLS = 64;    // columns per pattern set
+constexpr int MAX_DELTAS = 16;  // distinct windows per pattern set
+constexpr int MAX_CYCLE = 8;    // longest cycle
+
+// Read-only view of a device graph, passed by value to kernels.
+struct GraphView {
+  int64_t E;
+  int32_t N;
+  const int32_t *src, *dst, *ts;
+  const int32_t *optr, *onbr, *ot, *oeid, *oprev, *onext, *onnbr, *ont, *oneid, *opos;
+  const int32_t *iptr, *inbr, *it, *ieid, *iprev, *inext, *innbr, *int_, *ineid, *ipos;
+};
+
+inline GraphView view_of(const aml_graph* g) {
+  GraphView v;
+  v.E = g->E;
+  v.N = g->N;
+  v.src = g->src; v.dst = g->dst; v.ts = g->ts;
+  v.optr = g->out.ptr; v.onbr = g->out.nbr; v.ot = g->out.t; v.oeid = g->out.eid;
+  v.oprev = g->out.prev; v.onext = g->out.next; v.onnbr = g->out.nnbr; v.ont = g->out.nt;
+  v.oneid = g->out.neid; v.opos = g->out.pos;
+  v.iptr = g->in.ptr; v.inbr = g->in.nbr; v.it = g->in.t; v.ieid = g->in.eid;
+  v.iprev = g->in.prev; v.inext = g->in.next; v.innbr = g->in.nnbr; v.int_ = g->in.nt;
+  v.ineid = g->in.neid; v.ipos = g->in.pos;
+  return v;
+}
+
+struct ColDesc {
+  int32_t family;
+  int32_t k;
+  int32_t delta;
+  int32_t didx;      // index of the column's window in the per-window tables
+  int32_t acc_slot;  // accumulator column (SG, CYC), else -1
+};
+
+struct AssembleParams {
+  GraphView g;
+  ColDesc cols[MAX_COLS];
+  int32_t ncols;
+  const int32_t* S_out[MAX_DELTAS];
+  const int32_t* S_in[MAX_DELTAS];
+  const unsigned long long* acc;
+  uint32_t* counts;
+  int64_t ld;
+};
+
+struct CycleSlots {
+  int32_t slot[MAX_CYCLE + 1];  // accumulator column of CYC_k, or -1
+};
+
+__global__ void k_fan_delta(const int32_t* ptr, const int32_t* t, const int32_t* eid,
+                            const int32_t* prev, const int32_t* next, const int32_t* row_of,
+                            int64_t Ev, int32_t delta, int32_t* D);
+__global__ void k_leg_count(GraphView g, int32_t delta, int32_t* L);
+__global__ void k_leg_emit(GraphView g, int32_t delta, const int64_t* off, int32_t* la,
+                           int32_t* lb, uint64_t* key, int64_t n_nodes,
+                           unsigned long long* acc_cyc2);
+__global__ void k_sg_group(const uint64_t* key, const uint32_t* idx, int64_t n, const int32_t* la,
+                           const int32_t* lb, const int32_t* dst, const int32_t* ts,
+                           int32_t delta, unsigned long long* acc);
+__global__ void k_cycles(GraphView g, int32_t delta, int K, const int32_t* la, const int32_t* lb,
+                         int64_t n_legs, CycleSlots slots, unsigned long long* acc);
+__global__ void k_assemble(AssembleParams P);
+
+// Host pipeline: enqueue a full mine of `ps` on `g` into device `counts`.
+void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
+                cudaStream_t s);
+
+}  // namespace aml

@@ -1,0 +1,170 @@
+// Stage-program validation and planning (host only).
+//
+// A pattern is a chain of stages (Sec. 5); each stage applies an operation
+// (for_all, intersection) to neighbour sets of node variables bound by
+// earlier stages, with skip_if (node inequality) and time constraints
+// (Alg. 1's per-stage configuration).  The planner first validates operand
+// dependencies (Sec. 6), then maps the program onto one of the families the
+// kernels implement by comparing it, stage by stage, with that family's
+// canonical programs; a valid program that matches none is reported as
+// unsupported rather than run approximately.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "aml_internal.cuh"
+
+namespace aml {
+
+namespace {
+
+aml_stage st(int op, int a_var, int a_dir, int b_var, int b_dir, int out_var, int order,
+             int window, uint32_t skip) {
+  aml_stage s;
+  s.op = op; s.a_var = a_var; s.a_dir = a_dir; s.b_var = b_var; s.b_dir = b_dir;
+  s.out_var = out_var; s.order = order; s.window = window; s.skip_eq = skip;
+  return s;
+}
+
+aml_stage trigger() { return st(AML_OP_TRIGGER, 0, AML_DIR_OUT, -1, 0, 1, 0, 0, 0); }
+
+uint32_t bits_upto(int n) { return n >= 32 ? 0xffffffffu : ((1u << (n + 1)) - 1u); }
+
+struct Template {
+  int family;
+  int k;
+  int aggregate;
+  std::vector<aml_stage> stages;
+};
+
+std::vector<Template> templates() {
+  std::vector<Template> t;
+  const int O = AML_DIR_OUT, I = AML_DIR_IN;
+  const int F = AML_OP_FOR_ALL, X = AML_OP_INTERSECT;
+  const int TR = AML_WIN_TRAILING, SP = AML_WIN_SPAN;
+  // windowed degree / fan: the trigger's own neighbourhood over the trailing window
+  t.push_back({AML_FAM_DEG_OUT, 0, AML_AGG_EDGES, {trigger(), st(F, 0, O, -1, 0, 2, 0, TR, 0)}});
+  t.push_back({AML_FAM_FAN_OUT, 0, AML_AGG_DISTINCT, {trigger(), st(F, 0, O, -1, 0, 2, 0, TR, 0)}});
+  t.push_back({AML_FAM_DEG_IN, 0, AML_AGG_EDGES, {trigger(), st(F, 1, I, -1, 0, 2, 0, TR, 0)}});
+  t.push_back({AML_FAM_FAN_IN, 0, AML_AGG_DISTINCT, {trigger(), st(F, 1, I, -1, 0, 2, 0, TR, 0)}});
+  // gather-scatter: N0 -> N1 -> N2 (later), N2 != N0; or the mirrored N2 -> N0 -> N1
+  t.push_back({AML_FAM_GS, 0, AML_AGG_INSTANCES,
+               {trigger(), st(F, 1, O, -1, 0, 2, AML_ORDER_AFTER, SP, 1u << 0)}});
+  t.push_back({AML_FAM_GS, 0, AML_AGG_INSTANCES,
+               {trigger(), st(F, 0, I, -1, 0, 2, AML_ORDER_BEFORE, SP, 1u << 1)}});
+  // scatter-gather, trigger = scatter edge: N1.out -> N2, then N0.out ∩ N2.in -> N3
+  t.push_back({AML_FAM_SG, 0, AML_AGG_INSTANCES,
+               {trigger(), st(F, 1, O, -1, 0, 2, AML_ORDER_AFTER, SP, 1u << 0),
+                st(X, 0, O, 2, I, 3, AML_ORDER_LEG, SP, 1u << 1)}});
+  // scatter-gather, trigger = gather edge: N0.in -> N2, then N2.out ∩ N1.in -> N3
+  t.push_back({AML_FAM_SG, 0, AML_AGG_INSTANCES,
+               {trigger(), st(F, 0, I, -1, 0, 2, AML_ORDER_BEFORE, SP, 1u << 1),
+                st(X, 2, O, 1, I, 3, AML_ORDER_LEG, SP, 1u << 0)}});
+  // k-cycles: chain of for_all over out-neighbours, each later than the last,
+  // skipping bound nodes, closed by an edge back into N0 ...
+  for (int k = 2; k <= 15; ++k) {
+    Template c{AML_FAM_CYC, k, AML_AGG_INSTANCES, {trigger()}};
+    for (int i = 1; i <= k - 2; ++i)
+      c.stages.push_back(st(F, i, O, -1, 0, i + 1, AML_ORDER_AFTER, SP, bits_upto(i)));
+    c.stages.push_back(st(F, k - 1, O, -1, 0, 0, AML_ORDER_AFTER, SP, 0));
+    t.push_back(c);
+    // ... or, as in Sec. 6's 4-cycle, by intersecting N(k-2).out with N0.in
+    if (k >= 3) {
+      Template d{AML_FAM_CYC, k, AML_AGG_INSTANCES, {trigger()}};
+      for (int i = 1; i <= k - 3; ++i)
+        d.stages.push_back(st(F, i, O, -1, 0, i + 1, AML_ORDER_AFTER, SP, bits_upto(i)));
+      d.stages.push_back(st(X, k - 2, O, 0, I, k - 1, AML_ORDER_AFTER, SP, bits_upto(k - 2)));
+      t.push_back(d);
+    }
+  }
+  return t;
+}
+
+bool same_stage(const aml_stage& a, const aml_stage& b) {
+  if (a.op != b.op || a.out_var != b.out_var) return false;
+  if (a.op == AML_OP_TRIGGER) return true;
+  if (a.a_var != b.a_var || a.a_dir != b.a_dir || a.order != b.order || a.window != b.window ||
+      a.skip_eq != b.skip_eq)
+    return false;
+  if (a.op == AML_OP_INTERSECT && (a.b_var != b.b_var || a.b_dir != b.b_dir)) return false;
+  return true;
+}
+
+std::string where(int p, int s) {
+  char buf[64];
+  std::snprintf(buf, sizeof(buf), "pattern %d, stage %d: ", p, s);
+  return buf;
+}
+
+void validate(const aml_pattern& pat, int p) {
+  AML_REQUIRE(pat.stages != nullptr && pat.n_stages >= 1 && pat.n_stages <= 32, AML_EINVAL,
+              where(p, 0) + "a pattern needs 1..32 stages");
+  AML_REQUIRE(pat.delta >= 0, AML_EINVAL, where(p, 0) + "delta must be >= 0");
+  AML_REQUIRE(pat.reserved == 0, AML_EINVAL, where(p, 0) + "reserved field must be 0");
+  AML_REQUIRE(pat.aggregate >= AML_AGG_EDGES && pat.aggregate <= AML_AGG_INSTANCES, AML_EINVAL,
+              where(p, 0) + "unknown aggregate");
+  const aml_stage& t = pat.stages[0];
+  AML_REQUIRE(t.op == AML_OP_TRIGGER && t.out_var == 1, AML_EINVAL,
+              where(p, 0) + "stage 0 must be the trigger binding N0 -> N1");
+  int bound = 2;  // N0, N1
+  for (int s = 1; s < pat.n_stages; ++s) {
+    const aml_stage& x = pat.stages[s];
+    AML_REQUIRE(x.op == AML_OP_FOR_ALL || x.op == AML_OP_INTERSECT, AML_EINVAL,
+                where(p, s) + "op must be FOR_ALL or INTERSECT after the trigger");
+    AML_REQUIRE(x.a_var >= 0 && x.a_var < bound, AML_EINVAL,
+                where(p, s) + "first operand is not bound by an earlier stage");
+    AML_REQUIRE(x.a_dir == AML_DIR_OUT || x.a_dir == AML_DIR_IN, AML_EINVAL,
+                where(p, s) + "bad neighbour direction");
+    if (x.op == AML_OP_INTERSECT) {
+      AML_REQUIRE(x.b_var >= 0 && x.b_var < bound, AML_EINVAL,
+                  where(p, s) + "second operand is not bound by an earlier stage");
+      AML_REQUIRE(x.b_dir == AML_DIR_OUT || x.b_dir == AML_DIR_IN, AML_EINVAL,
+                  where(p, s) + "bad neighbour direction");
+    }
+    AML_REQUIRE(x.order >= AML_ORDER_NONE && x.order <= AML_ORDER_LEG, AML_EINVAL,
+                where(p, s) + "bad order");
+    AML_REQUIRE(x.window == AML_WIN_TRAILING || x.window == AML_WIN_SPAN, AML_EINVAL,
+                where(p, s) + "bad window");
+    AML_REQUIRE(bound >= 32 || (x.skip_eq >> bound) == 0, AML_EINVAL,
+                where(p, s) + "skip mask names an unbound variable");
+    AML_REQUIRE(x.out_var >= 0 && x.out_var <= bound, AML_EINVAL,
+                where(p, s) + "output variable must be new (next index) or already bound");
+    if (x.out_var == bound) {
+      ++bound;
+    } else {
+      AML_REQUIRE(s == pat.n_stages - 1, AML_EINVAL,
+                  where(p, s) + "only the last stage may close onto a bound variable");
+    }
+  }
+}
+
+}  // namespace
+
+// Maps every pattern onto a column; throws Failure on error.
+std::vector<Column> plan_patterns(const aml_pattern* pats, int n) {
+  AML_REQUIRE(pats != nullptr && n >= 1, AML_EINVAL, "need at least one pattern");
+  static const std::vector<Template> tpl = templates();
+  std::vector<Column> cols;
+  for (int p = 0; p < n; ++p) {
+    validate(pats[p], p);
+    const aml_pattern& pat = pats[p];
+    int fam = -1, k = 0;
+    for (const Template& t : tpl) {
+      if ((int)t.stages.size() != pat.n_stages || t.aggregate != pat.aggregate) continue;
+      bool ok = true;
+      for (int s = 0; s < pat.n_stages && ok; ++s) ok = same_stage(pat.stages[s], t.stages[s]);
+      if (ok) {
+        fam = t.family;
+        k = t.k;
+        break;
+      }
+    }
+    AML_REQUIRE(fam >= 0, AML_EUNSUPPORTED,
+                where(p, 0) + "valid stage program, but no implemented pattern family matches it");
+    cols.push_back(Column{fam, k, pat.delta});
+  }
+  return cols;
+}
+
+}  // namespace aml

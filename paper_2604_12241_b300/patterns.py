@@ -1,0 +1,179 @@
+"""Stage programs for the built-in pattern families (multi-stage framework).
+
+Each builder returns a ``Pattern``: a list of stages in the paper's
+multi-stage form (Sec. 5, Fig. 4; per-stage configuration of Alg. 1:
+operation, operand node sets, output variable, skip_if / time constraints)
+plus the final aggregation and the window.  ``aml_pattern_set_create`` maps
+each program onto the kernel family that evaluates it.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Sequence
+
+OP_TRIGGER, OP_FOR_ALL, OP_INTERSECT = 0, 1, 2
+DIR_OUT, DIR_IN = 0, 1
+ORDER_NONE, ORDER_AFTER, ORDER_BEFORE, ORDER_LEG = 0, 1, 2, 3
+WIN_TRAILING, WIN_SPAN = 0, 1
+AGG_EDGES, AGG_DISTINCT, AGG_INSTANCES = 0, 1, 2
+FAM_NAMES = {0: "DEG_OUT", 1: "DEG_IN", 2: "FAN_OUT", 3: "FAN_IN", 4: "GS", 5: "SG", 6: "CYC"}
+
+DAY = 86400
+WEEK = 7 * DAY
+
+
+@dataclasses.dataclass(frozen=True)
+class Stage:
+    op: int
+    a_var: int = 0
+    a_dir: int = DIR_OUT
+    b_var: int = -1
+    b_dir: int = 0
+    out_var: int = 0
+    order: int = ORDER_NONE
+    window: int = WIN_TRAILING
+    skip_eq: int = 0
+
+
+@dataclasses.dataclass(frozen=True)
+class Pattern:
+    stages: tuple
+    aggregate: int
+    delta: int
+    name: str = ""
+
+
+def _skip(*vars_: int) -> int:
+    m = 0
+    for v in vars_:
+        m |= 1 << v
+    return m
+
+
+TRIGGER = Stage(OP_TRIGGER, 0, DIR_OUT, -1, 0, 1)
+
+
+def deg_out(delta: int) -> Pattern:
+    """Edges out of N0 in the trailing window of the trigger."""
+    return Pattern((TRIGGER, Stage(OP_FOR_ALL, 0, DIR_OUT, out_var=2, window=WIN_TRAILING)),
+                   AGG_EDGES, delta, f"DEG_OUT@{delta}")
+
+
+def deg_in(delta: int) -> Pattern:
+    return Pattern((TRIGGER, Stage(OP_FOR_ALL, 1, DIR_IN, out_var=2, window=WIN_TRAILING)),
+                   AGG_EDGES, delta, f"DEG_IN@{delta}")
+
+
+def fan_out(delta: int) -> Pattern:
+    """Distinct counterparties N0 paid in the trailing window (fan-out)."""
+    return Pattern((TRIGGER, Stage(OP_FOR_ALL, 0, DIR_OUT, out_var=2, window=WIN_TRAILING)),
+                   AGG_DISTINCT, delta, f"FAN_OUT@{delta}")
+
+
+def fan_in(delta: int) -> Pattern:
+    return Pattern((TRIGGER, Stage(OP_FOR_ALL, 1, DIR_IN, out_var=2, window=WIN_TRAILING)),
+                   AGG_DISTINCT, delta, f"FAN_IN@{delta}")
+
+
+def gather_scatter(delta: int, mirrored: bool = False) -> Pattern:
+    """N0 -> N1 -> N2 with the second edge later, N2 != N0 (funds passing a hub)."""
+    if mirrored:
+        s = Stage(OP_FOR_ALL, 0, DIR_IN, out_var=2, order=ORDER_BEFORE, window=WIN_SPAN,
+                  skip_eq=_skip(1))
+    else:
+        s = Stage(OP_FOR_ALL, 1, DIR_OUT, out_var=2, order=ORDER_AFTER, window=WIN_SPAN,
+                  skip_eq=_skip(0))
+    return Pattern((TRIGGER, s), AGG_INSTANCES, delta, f"GS@{delta}")
+
+
+def scatter_gather(delta: int, trigger: str = "scatter") -> Pattern:
+    """Sec. 5's scatter-gather: trigger N0 -> N1, expand N1.out -> N2, then
+    intersect N0.out with N2.in -> N3 (another intermediary)."""
+    if trigger == "scatter":
+        stages = (TRIGGER,
+                  Stage(OP_FOR_ALL, 1, DIR_OUT, out_var=2, order=ORDER_AFTER, window=WIN_SPAN,
+                        skip_eq=_skip(0)),
+                  Stage(OP_INTERSECT, 0, DIR_OUT, 2, DIR_IN, out_var=3, order=ORDER_LEG,
+                        window=WIN_SPAN, skip_eq=_skip(1)))
+    elif trigger == "gather":
+        # the same diamond reached from a gather edge (Sec. 6's description)
+        stages = (TRIGGER,
+                  Stage(OP_FOR_ALL, 0, DIR_IN, out_var=2, order=ORDER_BEFORE, window=WIN_SPAN,
+                        skip_eq=_skip(1)),
+                  Stage(OP_INTERSECT, 2, DIR_OUT, 1, DIR_IN, out_var=3, order=ORDER_LEG,
+                        window=WIN_SPAN, skip_eq=_skip(0)))
+    else:
+        raise ValueError(trigger)
+    return Pattern(stages, AGG_INSTANCES, delta, f"SG@{delta}")
+
+
+def cycle(k: int, delta: int, closing: str = "for_all") -> Pattern:
+    """k-cycle: trigger N0 -> N1, then N_i.out -> N_{i+1} (later, new node),
+    closed by an edge back into N0 -- or, for k >= 3, by intersecting
+    N_{k-2}.out with N0.in as in Sec. 5/6's 4-cycle."""
+    if k < 2:
+        raise ValueError("k >= 2")
+    st: List[Stage] = [TRIGGER]
+    if closing == "for_all":
+        for i in range(1, k - 1):
+            st.append(Stage(OP_FOR_ALL, i, DIR_OUT, out_var=i + 1, order=ORDER_AFTER,
+                            window=WIN_SPAN, skip_eq=_skip(*range(i + 1))))
+        st.append(Stage(OP_FOR_ALL, k - 1, DIR_OUT, out_var=0, order=ORDER_AFTER,
+                        window=WIN_SPAN))
+    elif closing == "intersect":
+        if k < 3:
+            raise ValueError("intersection closing needs k >= 3")
+        for i in range(1, k - 2):
+            st.append(Stage(OP_FOR_ALL, i, DIR_OUT, out_var=i + 1, order=ORDER_AFTER,
+                            window=WIN_SPAN, skip_eq=_skip(*range(i + 1))))
+        st.append(Stage(OP_INTERSECT, k - 2, DIR_OUT, 0, DIR_IN, out_var=k - 1,
+                        order=ORDER_AFTER, window=WIN_SPAN, skip_eq=_skip(*range(k - 1))))
+    else:
+        raise ValueError(closing)
+    return Pattern(tuple(st), AGG_INSTANCES, delta, f"CYC{k}@{delta}")
+
+
+def standard(delta: int, kmax: int = 5) -> List[Pattern]:
+    """The ten per-window columns: DEG_OUT, DEG_IN, FAN_OUT, FAN_IN, GS, SG,
+    CYC_2..CYC_kmax."""
+    return ([deg_out(delta), deg_in(delta), fan_out(delta), fan_in(delta),
+             gather_scatter(delta), scatter_gather(delta)]
+            + [cycle(k, delta) for k in range(2, kmax + 1)])
+
+
+def workload_patterns(name: str) -> List[Pattern]:
+    """Column sets of the named workloads."""
+    if name == "tiny-10k":
+        return standard(DAY, 5)
+    if name in ("hi-small", "hi-medium"):
+        return standard(DAY, 5) + standard(WEEK, 5)
+    if name == "hi-large":
+        return ([fan_out(DAY), fan_in(DAY), gather_scatter(DAY), scatter_gather(DAY)]
+                + [cycle(k, DAY) for k in range(3, 7)] + [fan_out(WEEK), fan_in(WEEK)])
+    raise KeyError(name)
+
+
+def oracle_columns(patterns: Sequence[Pattern]) -> list:
+    """The oracle's column tuples for a list of built-in patterns."""
+    out = []
+    for p in patterns:
+        fam, _, rest = p.name.partition("@")
+        d = int(rest)
+        if fam.startswith("CYC"):
+            out.append(("cyc", int(fam[3:]), d))
+        else:
+            out.append((fam.lower(), d))
+    return out
+
+
+def from_oracle_columns(cols) -> List[Pattern]:
+    """Built-in patterns for oracle column tuples (inverse of oracle_columns)."""
+    make = {"deg_out": deg_out, "deg_in": deg_in, "fan_out": fan_out, "fan_in": fan_in,
+            "gs": gather_scatter, "sg": scatter_gather}
+    out = []
+    for c in cols:
+        if c[0] == "cyc":
+            out.append(cycle(int(c[1]), int(c[2])))
+        else:
+            out.append(make[c[0]](int(c[1])))
+    return out
