@@ -225,6 +225,28 @@ aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, i
  * (AML_ETIMEOUT, AML_EINTERNAL) recorded by its kernels since the last call. */
 aml_status aml_sync(aml_graph* g);
 
+/* --------------------------------------------------------------- profiling */
+
+/* Number of kernels the library has launched in this process (all devices,
+ * all threads).  The difference across a region counts its launches. */
+aml_status aml_launch_count(int64_t* out);
+
+/* Start (on != 0) or stop timing every kernel launch with a pair of CUDA
+ * events recorded on the launching stream.  Launches during stream capture
+ * are not timed.  Costs two event records per launch while on. */
+aml_status aml_profile_enable(int32_t on);
+
+typedef struct aml_kernel_stat {
+  char name[40];       /* kernel name, e.g. "k_assemble"                     */
+  int64_t launches;    /* timed launches                                     */
+  double total_ms;     /* summed event-to-event time of those launches       */
+} aml_kernel_stat;
+
+/* Wait for the recorded events, fold them into per-kernel totals and copy up
+ * to `cap` totals into `stats` (may be NULL); *n_out receives the number of
+ * distinct kernels.  reset != 0 clears the totals afterwards. */
+aml_status aml_profile_read(aml_kernel_stat* stats, int32_t cap, int32_t* n_out, int32_t reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -48,6 +48,11 @@ class aml_graph_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class aml_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
 class aml_column_info(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int32), ("k", ctypes.c_int32), ("delta", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("name", ctypes.c_char * 32)]
@@ -70,6 +75,10 @@ _SIGS = {
                                                 ctypes.POINTER(aml_column_info)]),
     "aml_mine": (ctypes.c_int32, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_uint32, _VP]),
     "aml_sync": (ctypes.c_int32, [_VP]),
+    "aml_launch_count": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_int64)]),
+    "aml_profile_enable": (ctypes.c_int32, [ctypes.c_int32]),
+    "aml_profile_read": (ctypes.c_int32, [ctypes.POINTER(aml_kernel_stat), ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
 }
 
 _lib: Optional[ctypes.CDLL] = None
@@ -116,3 +125,22 @@ def make_patterns(patterns) -> tuple:
         arr[i].delta = p.delta
         arr[i].reserved = 0
     return arr, keep
+
+
+def launch_count() -> int:
+    n = ctypes.c_int64()
+    check(lib().aml_launch_count(ctypes.byref(n)))
+    return n.value
+
+
+def profile_enable(on: bool) -> None:
+    check(lib().aml_profile_enable(1 if on else 0))
+
+
+def profile_read(reset: bool = True) -> dict:
+    """{kernel name: (launches, total_ms)} of the timed launches so far."""
+    n = ctypes.c_int32()
+    check(lib().aml_profile_read(None, 0, ctypes.byref(n), 0))
+    arr = (aml_kernel_stat * max(1, n.value))()
+    check(lib().aml_profile_read(arr, n.value, ctypes.byref(n), 1 if reset else 0))
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(n.value)}

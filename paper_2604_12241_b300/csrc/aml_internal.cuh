@@ -92,9 +92,13 @@ struct Adj {
   int32_t* pos = nullptr;   // [E] slot of edge e in this direction, -1 for self-loops
 };
 
+// Sizes that depend only on the graph and a window, learned on the first
+// mine that needs them (one host synchronization) and reused to size the
+// buffers of later mines; the contents are recomputed by every mine.
 struct LegCache {
-  int64_t n_legs = -1;      // temporal 2-paths with s != d in the window (GS instances)
-  int64_t* off = nullptr;   // [E+1] first leg of each edge (owned by the graph)
+  int64_t n_legs = -1;  // temporal 2-paths with s != d in the window (GS instances)
+  int64_t n_front[16] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+                        // cycle-search frontier sizes by level (index = path length)
 };
 
 }  // namespace aml

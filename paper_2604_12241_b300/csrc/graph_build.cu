@@ -11,6 +11,7 @@
 #include <cstring>
 
 #include "aml_internal.cuh"
+#include "profile.cuh"
 
 namespace aml {
 
@@ -27,7 +28,8 @@ __global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __res
   if (bits && (threadIdx.x & 31) == __ffs(__activemask()) - 1) atomicOr(err, bits);
 }
 
-__global__ void k_time_keys(const int32_t* __restrict__ ts, int64_t E, uint32_t* __restrict__ keys) {
+__global__ void k_time_keys(const int32_t* __restrict__ ts, int64_t E,
+                            uint32_t* __restrict__ keys) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < E) keys[i] = (uint32_t)ts[i] ^ 0x80000000u;  // signed order as unsigned
 }
@@ -108,7 +110,8 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
   if (i < n) p[i] = v;
 }
 
-__global__ void k_max_degree(const int32_t* __restrict__ ptr, int32_t N, int32_t* __restrict__ out) {
+__global__ void k_max_degree(const int32_t* __restrict__ ptr, int32_t N,
+                             int32_t* __restrict__ out) {
   int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
   int32_t d = (u < N) ? ptr[u + 1] - ptr[u] : 0;
   d = __reduce_max_sync(0xffffffffu, d);
@@ -141,10 +144,12 @@ static void build_direction(aml_graph* g, Adj& a, const int32_t* row_of, const i
   const int B = 256;
   // rows by account, (t, id) order inside each row (stable sort of the time order)
   AML_CUDA(cudaMemcpyAsync(perm.p, time_perm, E * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-  k_row_keys<<<grid_for(E, B), B, 0, s>>>(perm.p, row_of, other, E, N, keys.p);
+  AML_LAUNCH("k_row_keys", s,
+             k_row_keys<<<grid_for(E, B), B, 0, s>>>(perm.p, row_of, other, E, N, keys.p));
   radix_sort_u32(keys.p, perm.p, ktmp.p, vtmp.p, E, nbits, s);
   a.ptr = ga.get<int32_t>((size_t)N + 1);
-  k_row_ptr<<<grid_for((int64_t)N + 1, B), B, 0, s>>>(keys.p, E, N, a.ptr);
+  AML_LAUNCH("k_row_ptr", s,
+             k_row_ptr<<<grid_for((int64_t)N + 1, B), B, 0, s>>>(keys.p, E, N, a.ptr));
   int64_t Ev = g->Ev;
   a.nbr = ga.get<int32_t>(Ev);
   a.t = ga.get<int32_t>(Ev);
@@ -157,17 +162,21 @@ static void build_direction(aml_graph* g, Adj& a, const int32_t* row_of, const i
   a.pos = ga.get<int32_t>(E);
   AML_CUDA(cudaMemsetAsync(a.pos, 0xff, (E ? E : 1) * sizeof(int32_t), s));
   AML_CUDA(cudaMemsetAsync(a.prev, 0xff, (Ev ? Ev : 1) * sizeof(int32_t), s));
-  k_fill_i32<<<grid_for(Ev, B), B, 0, s>>>(a.next, Ev, INT32_MAX);
-  k_fill_slots<<<grid_for(Ev, B), B, 0, s>>>(perm.p, Ev, other, g->ts, a.nbr, a.t, a.eid, a.pos);
+  AML_LAUNCH("k_fill_i32", s, k_fill_i32<<<grid_for(Ev, B), B, 0, s>>>(a.next, Ev, INT32_MAX));
+  AML_LAUNCH("k_fill_slots", s,
+             k_fill_slots<<<grid_for(Ev, B), B, 0, s>>>(
+                 perm.p, Ev, other, g->ts, a.nbr, a.t, a.eid, a.pos));
   // (account, counterparty, t, id) order: stable sort by counterparty, then by account
-  k_nbr_keys<<<grid_for(E, B), B, 0, s>>>(perm.p, row_of, other, E, N, keys.p);
+  AML_LAUNCH("k_nbr_keys", s,
+             k_nbr_keys<<<grid_for(E, B), B, 0, s>>>(perm.p, row_of, other, E, N, keys.p));
   radix_sort_u32(keys.p, perm.p, ktmp.p, vtmp.p, E, nbits, s);
-  k_row_keys<<<grid_for(E, B), B, 0, s>>>(perm.p, row_of, other, E, N, keys.p);
+  AML_LAUNCH("k_row_keys", s,
+             k_row_keys<<<grid_for(E, B), B, 0, s>>>(perm.p, row_of, other, E, N, keys.p));
   radix_sort_u32(keys.p, perm.p, ktmp.p, vtmp.p, E, nbits, s);
-  k_fill_nbr_order<<<grid_for(Ev, B), B, 0, s>>>(perm.p, Ev, row_of, other, g->ts, a.pos, a.nnbr,
-                                                 a.nt, a.neid, a.prev, a.next);
-  k_max_degree<<<grid_for(N, B), B, 0, s>>>(a.ptr, N, max_deg_dev);
-  AML_CUDA(cudaGetLastError());
+  AML_LAUNCH("k_fill_nbr_order", s,
+             k_fill_nbr_order<<<grid_for(Ev, B), B, 0, s>>>(
+                 perm.p, Ev, row_of, other, g->ts, a.pos, a.nnbr, a.nt, a.neid, a.prev, a.next));
+  AML_LAUNCH("k_max_degree", s, k_max_degree<<<grid_for(N, B), B, 0, s>>>(a.ptr, N, max_deg_dev));
 }
 
 __global__ void k_count_loops(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
@@ -207,9 +216,10 @@ aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts
     AML_CUDA(cudaMemsetAsync(scal.p, 0, 32, s));
     const int B = 256;
     if (E) {
-      k_validate<<<grid_for(E, B), B, 0, s>>>(g->src, g->dst, g->ts, E, N, g->err);
-      k_count_loops<<<grid_for(E, B), B, 0, s>>>(g->src, g->dst, E, scal.p);
-      AML_CUDA(cudaGetLastError());
+      AML_LAUNCH("k_validate", s,
+                 k_validate<<<grid_for(E, B), B, 0, s>>>(g->src, g->dst, g->ts, E, N, g->err));
+      AML_LAUNCH("k_count_loops", s,
+                 k_count_loops<<<grid_for(E, B), B, 0, s>>>(g->src, g->dst, E, scal.p));
     }
     uint32_t err = 0;
     unsigned long long hs[4];
@@ -227,7 +237,7 @@ aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts
     iota_i32(reinterpret_cast<int32_t*>(tperm.p), E, s);
     if (err & ERR_UNSORTED) {
       DBuf<uint32_t> keys(E, s), ktmp(E, s), vtmp(E, s);
-      k_time_keys<<<grid_for(E, B), B, 0, s>>>(g->ts, E, keys.p);
+      AML_LAUNCH("k_time_keys", s, k_time_keys<<<grid_for(E, B), B, 0, s>>>(g->ts, E, keys.p));
       radix_sort_u32(keys.p, tperm.p, ktmp.p, vtmp.p, E, 32, s);
     }
     int nbits = bits_for((uint64_t)N);  // keys range over [0, N]

@@ -24,21 +24,27 @@ namespace aml {
 // next(r) <= p-1.  So R is a per-row prefix sum of per-slot deltas: one pass
 // plus one scan, O(list length) in total.
 
-__global__ void __launch_bounds__(256) k_fan_delta(const int32_t* __restrict__ ptr,
-                                                   const int32_t* __restrict__ t,
-                                                   const int32_t* __restrict__ eid,
-                                                   const int32_t* __restrict__ prev,
-                                                   const int32_t* __restrict__ next,
-                                                   const int32_t* __restrict__ row_of, int64_t Ev,
-                                                   int32_t delta, int32_t* __restrict__ D) {
+// Per slot p of one direction: the start lb(p) of its trailing window (so
+// DEG = p - lb(p) + 1) and, when FAN is wanted, the repeat delta above.
+__global__ void __launch_bounds__(256) k_window_slots(const int32_t* __restrict__ ptr,
+                                                      const int32_t* __restrict__ t,
+                                                      const int32_t* __restrict__ eid,
+                                                      const int32_t* __restrict__ prev,
+                                                      const int32_t* __restrict__ next,
+                                                      const int32_t* __restrict__ row_of,
+                                                      int64_t Ev, int32_t delta,
+                                                      int32_t* __restrict__ lb,
+                                                      int32_t* __restrict__ D) {
   int64_t p64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p64 >= Ev) return;
   int32_t p = (int32_t)p64;
   int32_t rs = __ldg(ptr + __ldg(row_of + __ldg(eid + p)));
+  int32_t tp = __ldg(t + p);
+  int32_t lbp = lower_t(t, rs, p + 1, (int64_t)tp - delta);
+  lb[p] = lbp;
+  if (!D) return;
   int32_t d = 0;
   if (p > rs) {
-    int32_t tp = __ldg(t + p);
-    int32_t lbp = lower_t(t, rs, p + 1, (int64_t)tp - delta);
     // lb(p-1) <= min(lb(p), p-1): search only up to there
     int32_t lbq = lower_t(t, rs, min(lbp + 1, p), (int64_t)__ldg(t + p - 1) - delta);
     d = (__ldg(prev + p) >= lbp) ? 1 : 0;
@@ -116,13 +122,25 @@ __global__ void __launch_bounds__(256) k_leg_count(GraphView g, int32_t delta,
   L[a] = (g.src[a] == g.dst[a]) ? 0 : legs_from(g, a, delta);
 }
 
+// legs ending with each edge, by binary search (when no legs are emitted)
+__global__ void __launch_bounds__(256) k_gs_into(GraphView g, int32_t delta,
+                                                 int32_t* __restrict__ gs_in) {
+  int64_t b64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b64 >= g.E) return;
+  int32_t b = (int32_t)b64;
+  gs_in[b] = (g.src[b] == g.dst[b]) ? 0 : legs_into(g, b, delta);
+}
+
 // Writes every leg (a, b) of edge a at off[a]...; reciprocal edges b = h->x
-// inside the window close 2-cycles (a, b) and are credited directly.
+// inside the window close 2-cycles (a, b) and are credited directly.  With
+// gs_in, also counts the legs ending with each edge (the scatter side of GS).
 __global__ void __launch_bounds__(256) k_leg_emit(GraphView g, int32_t delta,
                                                   const int64_t* __restrict__ off,
-                                                  int32_t* __restrict__ la, int32_t* __restrict__ lb,
+                                                  int32_t* __restrict__ la,
+                                                  int32_t* __restrict__ lb,
                                                   uint64_t* __restrict__ key, int64_t n_nodes,
-                                                  unsigned long long* __restrict__ acc_cyc2) {
+                                                  unsigned long long* __restrict__ acc_cyc2,
+                                                  int32_t* __restrict__ gs_in) {
   int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a64 >= g.E) return;
   int32_t a = (int32_t)a64;
@@ -145,6 +163,7 @@ __global__ void __launch_bounds__(256) k_leg_emit(GraphView g, int32_t delta,
     la[o] = a;
     lb[o] = b;
     if (key) key[o] = (uint64_t)x * (uint64_t)n_nodes + (uint64_t)y;
+    if (gs_in) atomicAdd(gs_in + b, 1);
     ++o;
   }
   if (n_cyc2) atomicAdd(acc_cyc2 + a, n_cyc2);
@@ -194,96 +213,163 @@ __global__ void __launch_bounds__(256) k_sg_group(const uint64_t* __restrict__ k
 
 // ---------------------------------------------------------------- cycles
 //
-// Depth-first search from every leg (e1, e2) taken as the first two edges
-// of a cycle (e1 is its earliest edge): every hop takes a later edge inside
-// t(e1) + delta to a node not yet on the path; an edge back into u0 closes a
-// cycle of length depth+1.  At the last level only closing edges can count,
-// so they are found by binary search in the (nbr, t, id) copy instead of a
-// window scan (the closing intersection of Sec. 6's cycle example).
+// Every cycle is enumerated once, from its earliest edge e1 = u0->u1, as a
+// path of later edges that returns to u0 within t(e1) + delta (the cycle
+// program of Sec. 5 / Fig. 4b: trigger, for_all expansions, and a closing
+// intersection with N0.in).  The closing edges of e1 are the slots of u0's
+// in-list after e1 and inside the window: one contiguous range B1, found
+// per mine.  The paths are then extended level by level (all paths of j
+// edges, then all of j+1), so a hub's large window is split over many
+// threads instead of being walked by one.  On the way every path
+//   * stops at once when B1 is empty (no cycle can start at e1),
+//   * is bounded by the latest edge of B1 (a cycle's intermediate edges all
+//     precede its closing edge), and
+//   * closes at its end node w by matching w against B1 -- a scan of B1 when
+//     it is short, two binary searches in u0's (nbr, t, id) in-list otherwise
+//     (the degree-ordered intersection of Sec. 6).
 
-__device__ __forceinline__ void credit_cycle(unsigned long long* acc, int64_t E, int slot,
-                                             const int32_t* edges, int n,
-                                             unsigned long long c) {
-  unsigned long long* col = acc + (int64_t)slot * E;
-  for (int j = 0; j < n; ++j) atomicAdd(col + edges[j], c);
+// B1 of every edge a = u0 -> u1: slots of in(u0) after a with t <= t_a + delta
+__global__ void __launch_bounds__(256) k_close_range(GraphView g, int32_t delta,
+                                                     int2* __restrict__ rng) {
+  int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a64 >= g.E) return;
+  int32_t a = (int32_t)a64;
+  int32_t u0 = g.src[a];
+  int2 r = make_int2(0, 0);
+  if (u0 != g.dst[a]) {
+    int32_t is = g.iptr[u0], ie = g.iptr[u0 + 1];
+    int32_t ta = g.ts[a];
+    r.x = after_edge(g.it, g.ieid, is, ie, ta, a);
+    r.y = upper_t(g.it, r.x, ie, (int64_t)ta + delta);
+  }
+  rng[a] = r;
 }
 
-__global__ void __launch_bounds__(128) k_cycles(GraphView g, int32_t delta, int K,
-                                                const int32_t* __restrict__ la,
-                                                const int32_t* __restrict__ lb, int64_t n_legs,
-                                                CycleSlots slots,
-                                                unsigned long long* __restrict__ acc) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_legs) return;
-  int32_t edges[MAX_CYCLE];
-  int32_t nodes[MAX_CYCLE];
-  int32_t cur[MAX_CYCLE], end[MAX_CYCLE];
-  edges[0] = la[i];
-  edges[1] = lb[i];
+constexpr int32_t CLOSE_SCAN_MAX = 48;  // B1 longer than this: binary search
+
+// Rebuilds the path of frontier element i at level j (j edges):
+// edges[0..j-1] and nodes[0..j] (nodes[0] = u0 = src of the anchor).
+__device__ __forceinline__ void cyc_path(const GraphView& g, const CycFrontier& F, int j,
+                                         int64_t i, int32_t* edges, int32_t* nodes) {
+  int64_t idx = i;
+  for (int lev = j; lev >= 3; --lev) {
+    const int32_t q = F.slot[lev][idx];
+    edges[lev - 1] = __ldg(g.oeid + q);
+    nodes[lev] = __ldg(g.onbr + q);
+    idx = F.par[lev][idx];
+  }
+  edges[0] = F.la[idx];
+  edges[1] = F.lb[idx];
   nodes[0] = g.src[edges[0]];
   nodes[1] = g.dst[edges[0]];
   nodes[2] = g.dst[edges[1]];
-  const int32_t u0 = nodes[0];
-  const int64_t tmax = (int64_t)g.ts[edges[0]] + delta;
-  int L = 2;  // edges on the path; current node nodes[L]
-  // opening a level: the window after the last edge, or the closing lookup
-  auto open = [&](int lev) -> bool {
-    int32_t w = nodes[lev];
-    int32_t last = edges[lev - 1];
-    int32_t tl = g.ts[last];
-    int32_t ws = g.optr[w], we = g.optr[w + 1];
-    if (lev == K - 1) {
-      // only closing edges matter here
-      // tl >= t(e1), so tmax - tl <= delta fits in int32
-      int32_t c = pair_after(g.onnbr, g.ont, g.oneid, ws, we, u0, tl, last,
-                             (int32_t)(tmax - tl));
-      if (c > 0 && slots.slot[K] >= 0) {
-        credit_cycle(acc, g.E, slots.slot[K], edges, lev, (unsigned long long)c);
-        int32_t r0 = lower_nbr(g.onnbr, ws, we, u0);
-        int32_t r1 = lower_nbr(g.onnbr, r0, we, u0 + 1);
-        int32_t b0 = after_edge(g.ont, g.oneid, r0, r1, tl, last);
-        int32_t b1 = upper_t(g.ont, b0, r1, tmax);
-        unsigned long long* col = acc + (int64_t)slots.slot[K] * g.E;
-        for (int32_t q = b0; q < b1; ++q) atomicAdd(col + __ldg(g.oneid + q), 1ull);
+}
+
+// One level of the cycle search.  Element i of level j is a path of j
+// increasing edges from the anchor e1; the kernel checks that its last hop
+// is admissible (new node, before the latest closing edge), credits the
+// cycles of length j+1 that close from its end node through B1, and reports
+// the window of later hops its children will take.
+__global__ void __launch_bounds__(256) k_cyc_level(GraphView g, int32_t delta, int K, int j,
+                                                   CycFrontier F, int64_t n,
+                                                   const int2* __restrict__ close_rng,
+                                                   CycleSlots slots,
+                                                   unsigned long long* __restrict__ acc,
+                                                   int32_t* __restrict__ cnt,
+                                                   int32_t* __restrict__ q0_out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool has_next = j + 1 <= K - 1;
+  if (has_next) cnt[i] = 0;
+  int32_t edges[MAX_CYCLE];
+  int32_t nodes[MAX_CYCLE + 1];
+  cyc_path(g, F, j, i, edges, nodes);
+  const int2 cr = close_rng[edges[0]];
+  if (cr.x >= cr.y) return;  // e1 starts no cycle
+  const int32_t t_cl = __ldg(g.it + cr.y - 1), id_cl = __ldg(g.ieid + cr.y - 1);
+  const int32_t last = edges[j - 1], tl = g.ts[last];
+  if (!before(tl, last, t_cl, id_cl)) return;  // nothing can close after it
+  const int32_t u0 = nodes[0], w = nodes[j];
+  if (j >= 3) {  // the hop into w must reach a new node
+    if (w == u0) return;
+    for (int m = 1; m < j; ++m)
+      if (nodes[m] == w) return;
+  }
+  // cycles of length j+1: edges w -> u0 in B1 after `last`
+  const int k = j + 1;
+  if (k <= K && slots.slot[k] >= 0) {
+    unsigned long long* col = acc + (int64_t)slots.slot[k] * g.E;
+    unsigned long long c = 0;
+    if (cr.y - cr.x <= CLOSE_SCAN_MAX) {
+      for (int32_t q = cr.x; q < cr.y; ++q) {
+        if (__ldg(g.inbr + q) != w) continue;
+        const int32_t cid = __ldg(g.ieid + q);
+        if (!before(tl, last, __ldg(g.it + q), cid)) continue;
+        atomicAdd(col + cid, 1ull);
+        ++c;
       }
-      return false;
-    }
-    cur[lev] = after_edge(g.ot, g.oeid, ws, we, tl, last);
-    end[lev] = upper_t(g.ot, cur[lev], we, tmax);
-    return true;
-  };
-  if (!open(L)) return;
-  while (L >= 2) {
-    if (cur[L] >= end[L]) {
-      --L;
-      continue;
-    }
-    int32_t q = cur[L]++;
-    int32_t x = __ldg(g.onbr + q);
-    int32_t f = __ldg(g.oeid + q);
-    if (x == u0) {
-      int k = L + 1;
-      if (slots.slot[k] >= 0) {
-        edges[L] = f;
-        credit_cycle(acc, g.E, slots.slot[k], edges, k, 1ull);
+    } else {
+      const int32_t in_s = g.iptr[u0], in_e = g.iptr[u0 + 1];
+      const int32_t r0 = lower_nbr(g.innbr, in_s, in_e, w);
+      if (r0 < in_e && __ldg(g.innbr + r0) == w) {
+        const int32_t r1 = lower_nbr(g.innbr, r0, in_e, w + 1);
+        const int32_t b0 = after_edge(g.int_, g.ineid, r0, r1, tl, last);
+        const int32_t b1 = upper_t(g.int_, b0, r1, (int64_t)g.ts[edges[0]] + delta);
+        for (int32_t q = b0; q < b1; ++q) atomicAdd(col + __ldg(g.ineid + q), 1ull);
+        c = (unsigned long long)(b1 - b0);
       }
-      continue;
     }
-    if (L + 1 >= K) continue;
-    bool seen = false;
-    for (int j = 1; j <= L; ++j) seen |= (nodes[j] == x);
-    if (seen) continue;
-    edges[L] = f;
-    nodes[L + 1] = x;
-    if (open(L + 1)) ++L;
+    if (c)
+      for (int m = 0; m < j; ++m) atomicAdd(col + edges[m], c);
+  }
+  if (has_next) {
+    const int32_t ws = g.optr[w], we = g.optr[w + 1];
+    const int32_t q0 = after_edge(g.ot, g.oeid, ws, we, tl, last);
+    const int32_t q1 = upper_t(g.ot, q0, we, t_cl);
+    cnt[i] = q1 - q0;
+    q0_out[i] = q0;
+  }
+}
+
+// Writes the children (parent, slot) of every element at off[i]...; short
+// windows are written by their own lane, long ones by the whole warp.
+__global__ void __launch_bounds__(256) k_cyc_emit(int64_t n, const int32_t* __restrict__ cnt,
+                                                  const int32_t* __restrict__ q0,
+                                                  const int64_t* __restrict__ off,
+                                                  int32_t* __restrict__ par,
+                                                  int32_t* __restrict__ slot) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int32_t c = i < n ? cnt[i] : 0;
+  const int64_t o = c ? off[i] : 0;
+  const int32_t b = c ? q0[i] : 0;
+  const bool own = c <= 32;
+  if (own)
+    for (int32_t k = 0; k < c; ++k) {
+      par[o + k] = (int32_t)i;
+      slot[o + k] = b + k;
+    }
+  unsigned heavy = __ballot_sync(0xffffffffu, !own);
+  while (heavy) {
+    const int src = __ffs(heavy) - 1;
+    heavy &= heavy - 1;
+    const int64_t hi = __shfl_sync(0xffffffffu, i, src);
+    const int32_t hc = __shfl_sync(0xffffffffu, c, src);
+    const int64_t ho = __shfl_sync(0xffffffffu, o, src);
+    const int32_t hb = __shfl_sync(0xffffffffu, b, src);
+    for (int32_t k = lane; k < hc; k += 32) {
+      par[ho + k] = (int32_t)hi;
+      slot[ho + k] = hb + k;
+    }
   }
 }
 
 // -------------------------------------------------------------- assemble
 //
-// One thread per edge writes the edge's whole output row: DEG and FAN from
-// the window bounds and the repeat prefix sums, GS from binary searches, SG
-// and CYC from the 64-bit accumulators, all saturated to 32 bits.
+// One thread per edge writes the edge's whole output row from values the
+// earlier kernels left in slot or edge order: DEG = pos - lb(pos) + 1, FAN =
+// DEG - repeats (prefix-sum difference), GS = legs starting + legs ending at
+// the edge, SG and CYC from the 64-bit accumulators; saturated to 32 bits.
 
 __global__ void __launch_bounds__(256) k_assemble(AssembleParams P) {
   int64_t e64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -296,37 +382,31 @@ __global__ void __launch_bounds__(256) k_assemble(AssembleParams P) {
     for (int c = 0; c < P.ncols; ++c) row[c] = 0u;
     return;
   }
-  int32_t te = g.ts[e];
   int32_t po = g.opos[e], pi = g.ipos[e];
   int32_t os = g.optr[u], is = g.iptr[v];
   for (int c = 0; c < P.ncols; ++c) {
     const ColDesc cd = P.cols[c];
+    const int w = cd.didx;
     uint64_t val = 0;
     switch (cd.family) {
       case AML_FAM_DEG_OUT:
+        val = (uint64_t)(po - P.lb_out[w][po] + 1);
+        break;
       case AML_FAM_FAN_OUT: {
-        int32_t lb = lower_t(g.ot, os, po + 1, (int64_t)te - cd.delta);
-        val = (uint64_t)(po - lb + 1);
-        if (cd.family == AML_FAM_FAN_OUT) {
-          const int32_t* S = P.S_out[cd.didx];
-          int32_t rep = S[po] - (os > 0 ? S[os - 1] : 0);
-          val -= (uint64_t)rep;
-        }
+        const int32_t* S = P.S_out[w];
+        val = (uint64_t)(po - P.lb_out[w][po] + 1 - (S[po] - (os > 0 ? S[os - 1] : 0)));
         break;
       }
       case AML_FAM_DEG_IN:
+        val = (uint64_t)(pi - P.lb_in[w][pi] + 1);
+        break;
       case AML_FAM_FAN_IN: {
-        int32_t lb = lower_t(g.it, is, pi + 1, (int64_t)te - cd.delta);
-        val = (uint64_t)(pi - lb + 1);
-        if (cd.family == AML_FAM_FAN_IN) {
-          const int32_t* S = P.S_in[cd.didx];
-          int32_t rep = S[pi] - (is > 0 ? S[is - 1] : 0);
-          val -= (uint64_t)rep;
-        }
+        const int32_t* S = P.S_in[w];
+        val = (uint64_t)(pi - P.lb_in[w][pi] + 1 - (S[pi] - (is > 0 ? S[is - 1] : 0)));
         break;
       }
       case AML_FAM_GS:
-        val = (uint64_t)legs_from(g, e, cd.delta) + (uint64_t)legs_into(g, e, cd.delta);
+        val = (uint64_t)(P.off[w][e + 1] - P.off[w][e]) + (uint64_t)P.gs_in[w][e];
         break;
       default:  // accumulated families
         val = P.acc[(int64_t)cd.acc_slot * g.E + e];

@@ -44,8 +44,12 @@ struct AssembleParams {
   GraphView g;
   ColDesc cols[MAX_COLS];
   int32_t ncols;
-  const int32_t* S_out[MAX_DELTAS];
+  const int32_t* lb_out[MAX_DELTAS];  // window start per out-slot
+  const int32_t* lb_in[MAX_DELTAS];   // window start per in-slot
+  const int32_t* S_out[MAX_DELTAS];   // repeat prefix sums per out-slot (FAN)
   const int32_t* S_in[MAX_DELTAS];
+  const int64_t* off[MAX_DELTAS];     // leg offsets per edge (GS gather side)
+  const int32_t* gs_in[MAX_DELTAS];   // legs ending with each edge (GS scatter side)
   const unsigned long long* acc;
   uint32_t* counts;
   int64_t ld;
@@ -55,18 +59,33 @@ struct CycleSlots {
   int32_t slot[MAX_CYCLE + 1];  // accumulator column of CYC_k, or -1
 };
 
-__global__ void k_fan_delta(const int32_t* ptr, const int32_t* t, const int32_t* eid,
-                            const int32_t* prev, const int32_t* next, const int32_t* row_of,
-                            int64_t Ev, int32_t delta, int32_t* D);
+// Frontier of the level-by-level cycle search: level 2 is the legs (la, lb);
+// element i of level j >= 3 extends element par[j][i] of level j-1 by the
+// out-slot slot[j][i].
+struct CycFrontier {
+  const int32_t* la;
+  const int32_t* lb;
+  const int32_t* par[MAX_CYCLE + 1];
+  const int32_t* slot[MAX_CYCLE + 1];
+};
+
+__global__ void k_window_slots(const int32_t* ptr, const int32_t* t, const int32_t* eid,
+                               const int32_t* prev, const int32_t* next, const int32_t* row_of,
+                               int64_t Ev, int32_t delta, int32_t* lb, int32_t* D);
 __global__ void k_leg_count(GraphView g, int32_t delta, int32_t* L);
+__global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);
 __global__ void k_leg_emit(GraphView g, int32_t delta, const int64_t* off, int32_t* la,
                            int32_t* lb, uint64_t* key, int64_t n_nodes,
-                           unsigned long long* acc_cyc2);
+                           unsigned long long* acc_cyc2, int32_t* gs_in);
 __global__ void k_sg_group(const uint64_t* key, const uint32_t* idx, int64_t n, const int32_t* la,
                            const int32_t* lb, const int32_t* dst, const int32_t* ts,
                            int32_t delta, unsigned long long* acc);
-__global__ void k_cycles(GraphView g, int32_t delta, int K, const int32_t* la, const int32_t* lb,
-                         int64_t n_legs, CycleSlots slots, unsigned long long* acc);
+__global__ void k_close_range(GraphView g, int32_t delta, int2* rng);
+__global__ void k_cyc_level(GraphView g, int32_t delta, int K, int j, CycFrontier F, int64_t n,
+                            const int2* close_rng, CycleSlots slots, unsigned long long* acc,
+                            int32_t* cnt, int32_t* q0_out);
+__global__ void k_cyc_emit(int64_t n, const int32_t* cnt, const int32_t* q0, const int64_t* off,
+                           int32_t* par, int32_t* slot);
 __global__ void k_assemble(AssembleParams P);
 
 // Host pipeline: enqueue a full mine of `ps` on `g` into device `counts`.

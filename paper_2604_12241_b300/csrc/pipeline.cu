@@ -1,11 +1,21 @@
 // Host side of a mine: plans the per-window work and enqueues the kernels.
+//
+// Per window delta, in order:
+//   1. window starts (and FAN repeat deltas + scan) of the out- and in-slots;
+//   2. legs: count per edge, scan to offsets, emit (a, b) pairs, crediting
+//      2-cycles and counting the legs that end at each edge;
+//   3. SG: sort legs by (s, d), count partner legs inside each run;
+//   4. CYC_3..K: closing ranges, then the legs extended level by level;
+// and finally one pass writes every output row.  All of it is enqueued on
+// the caller's stream; only the first mine of a (graph, window) pair waits
+// once for the number of legs, to size the leg buffers.
 #include <algorithm>
 #include <climits>
 #include <cstring>
-#include <set>
 
 #include "aml_internal.cuh"
 #include "mine.cuh"
+#include "profile.cuh"
 
 namespace aml {
 
@@ -13,40 +23,16 @@ namespace {
 
 struct WindowPlan {
   int32_t delta = 0;
-  bool fan_out = false, fan_in = false, sg = false;
+  bool deg_out = false, deg_in = false, fan_out = false, fan_in = false;
+  bool gs = false, sg = false;
   int sg_slot = -1;
   CycleSlots cyc;
   int K = 0;  // longest cycle wanted
-  bool needs_legs() const { return sg || K >= 2; }
+  bool emit_legs() const { return sg || K >= 2; }
+  bool needs_off() const { return gs || emit_legs(); }
 };
 
 }  // namespace
-
-// Leg offsets of a window depend only on the graph, so they are computed on
-// the first mine that needs them and kept with the graph.
-static LegCache& leg_offsets(aml_graph* g, const GraphView& gv, int32_t delta, cudaStream_t s) {
-  LegCache& lc = g->legs[delta];
-  if (lc.n_legs >= 0) return lc;
-  const int64_t E = g->E;
-  DBuf<int32_t> L(E + 1, s);
-  k_leg_count<<<grid_for(E, 256), 256, 0, s>>>(gv, delta, L.p);
-  AML_CUDA(cudaGetLastError());
-  AML_CUDA(cudaMemsetAsync(L.p + E, 0, sizeof(int32_t), s));
-  void* off = nullptr;
-  AML_CUDA(cudaMalloc(&off, (size_t)(E + 1) * sizeof(int64_t)));
-  g->allocs.push_back(off);
-  g->bytes += (E + 1) * 8;
-  scan_i32_to_i64(L.p, static_cast<int64_t*>(off), E + 1, s);
-  int64_t total = 0;
-  AML_CUDA(cudaMemcpyAsync(&total, static_cast<int64_t*>(off) + E, sizeof(int64_t),
-                           cudaMemcpyDeviceToHost, s));
-  AML_CUDA(cudaStreamSynchronize(s));
-  AML_REQUIRE(total < (int64_t)UINT32_MAX, AML_EUNSUPPORTED,
-              "more than 2^32 temporal 2-paths in one window");
-  lc.off = static_cast<int64_t*>(off);
-  lc.n_legs = total;
-  return lc;
-}
 
 void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
                 cudaStream_t s) {
@@ -77,8 +63,11 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     WindowPlan& wp = wins[didx];
     ColDesc cd{col.family, col.k, col.delta, didx, -1};
     switch (col.family) {
+      case AML_FAM_DEG_OUT: wp.deg_out = true; break;
+      case AML_FAM_DEG_IN: wp.deg_in = true; break;
       case AML_FAM_FAN_OUT: wp.fan_out = true; break;
       case AML_FAM_FAN_IN: wp.fan_in = true; break;
+      case AML_FAM_GS: wp.gs = true; break;
       case AML_FAM_SG:
         if (wp.sg_slot < 0) wp.sg_slot = n_acc++;
         wp.sg = true;
@@ -103,50 +92,126 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   if (n_acc) AML_CUDA(cudaMemsetAsync(acc.p, 0, (size_t)n_acc * E * 8, s));
   P.acc = acc.p;
 
-  std::vector<DBuf<int32_t>> fan_bufs;
-  fan_bufs.reserve(2 * wins.size());
+  std::vector<DBuf<int32_t>> keep32;   // per-window buffers read by k_assemble
+  std::vector<DBuf<int64_t>> keep64;
+  keep32.reserve(8 * wins.size());
+  keep64.reserve(wins.size());
   const int B = 256;
+  const int64_t Ev = g->Ev;
   for (size_t w = 0; w < wins.size(); ++w) {
     WindowPlan& wp = wins[w];
+    // 1. trailing windows of both directions
     for (int dir = 0; dir < 2; ++dir) {
-      bool want = dir == 0 ? wp.fan_out : wp.fan_in;
-      if (!want || g->Ev == 0) continue;
+      bool fan = dir == 0 ? wp.fan_out : wp.fan_in;
+      bool deg = dir == 0 ? wp.deg_out : wp.deg_in;
+      if (!(fan || deg) || Ev == 0) continue;
       const Adj& a = dir == 0 ? g->out : g->in;
-      fan_bufs.emplace_back((size_t)g->Ev, s);
-      int32_t* D = fan_bufs.back().p;
-      k_fan_delta<<<grid_for(g->Ev, B), B, 0, s>>>(a.ptr, a.t, a.eid, a.prev, a.next,
-                                                   dir == 0 ? g->src : g->dst, g->Ev, wp.delta, D);
-      AML_CUDA(cudaGetLastError());
-      scan_i32(D, D, g->Ev, true, s);
+      keep32.emplace_back((size_t)Ev, s);
+      int32_t* lbp = keep32.back().p;
+      int32_t* D = nullptr;
+      if (fan) {
+        keep32.emplace_back((size_t)Ev, s);
+        D = keep32.back().p;
+      }
+      AML_LAUNCH("k_window_slots", s,
+                 k_window_slots<<<grid_for(Ev, B), B, 0, s>>>(
+                     a.ptr, a.t, a.eid, a.prev, a.next, dir == 0 ? g->src : g->dst, Ev,
+                     wp.delta, lbp, D));
+      if (fan) scan_i32(D, D, Ev, true, s);
+      (dir == 0 ? P.lb_out : P.lb_in)[w] = lbp;
       (dir == 0 ? P.S_out : P.S_in)[w] = D;
     }
-    if (!wp.needs_legs()) continue;
-    LegCache& lc = leg_offsets(g, gv, wp.delta, s);
+    if (!wp.needs_off()) continue;
+    // 2. legs
+    DBuf<int32_t> L(E + 1, s);
+    AML_LAUNCH("k_leg_count", s, k_leg_count<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, L.p));
+    AML_CUDA(cudaMemsetAsync(L.p + E, 0, sizeof(int32_t), s));
+    keep64.emplace_back((size_t)(E + 1), s);
+    int64_t* off = keep64.back().p;
+    scan_i32_to_i64(L.p, off, E + 1, s);
+    P.off[w] = off;
+    int32_t* gs_in = nullptr;
+    if (wp.gs) {
+      keep32.emplace_back((size_t)E, s);
+      gs_in = keep32.back().p;
+      P.gs_in[w] = gs_in;
+    }
+    if (!wp.emit_legs()) {
+      AML_LAUNCH("k_gs_into", s, k_gs_into<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, gs_in));
+      continue;
+    }
+    LegCache& lc = g->legs[wp.delta];
+    if (lc.n_legs < 0) {
+      int64_t total = 0;
+      AML_CUDA(cudaMemcpyAsync(&total, off + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      AML_CUDA(cudaStreamSynchronize(s));
+      AML_REQUIRE(total < (int64_t)UINT32_MAX, AML_EUNSUPPORTED,
+                  "more than 2^32 temporal 2-paths in one window");
+      lc.n_legs = total;
+    }
     const int64_t nl = lc.n_legs;
+    if (gs_in) AML_CUDA(cudaMemsetAsync(gs_in, 0, (size_t)E * 4, s));
     DBuf<int32_t> la(nl, s), lb(nl, s);
     DBuf<uint64_t> key(wp.sg ? nl : 0, s);
-    unsigned long long* acc2 = wp.cyc.slot[2] >= 0 ? acc.p + (int64_t)wp.cyc.slot[2] * E : nullptr;
-    k_leg_emit<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, lc.off, la.p, lb.p,
-                                            wp.sg ? key.p : nullptr, g->N, acc2);
-    AML_CUDA(cudaGetLastError());
+    unsigned long long* acc2 =
+        wp.cyc.slot[2] >= 0 ? acc.p + (int64_t)wp.cyc.slot[2] * E : nullptr;
+    AML_LAUNCH("k_leg_emit", s,
+               k_leg_emit<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, off, la.p, lb.p,
+                                                       wp.sg ? key.p : nullptr, g->N, acc2,
+                                                       gs_in));
+    // 3. scatter-gather
     if (wp.sg && nl > 1) {
       DBuf<uint32_t> idx(nl, s), itmp(nl, s);
       DBuf<uint64_t> ktmp(nl, s);
       iota_i32(reinterpret_cast<int32_t*>(idx.p), nl, s);
       uint64_t max_key = (uint64_t)g->N * (uint64_t)g->N;
       radix_sort_u64(key.p, idx.p, ktmp.p, itmp.p, nl, bits_for(max_key), s);
-      k_sg_group<<<grid_for(nl, B), B, 0, s>>>(key.p, idx.p, nl, la.p, lb.p, g->dst, g->ts,
-                                               wp.delta, acc.p + (int64_t)wp.sg_slot * E);
-      AML_CUDA(cudaGetLastError());
+      AML_LAUNCH("k_sg_group", s,
+                 k_sg_group<<<grid_for(nl, B), B, 0, s>>>(key.p, idx.p, nl, la.p, lb.p, g->dst,
+                                                          g->ts, wp.delta,
+                                                          acc.p + (int64_t)wp.sg_slot * E));
     }
+    // 4. cycles of length >= 3, level by level from the legs
     if (wp.K >= 3 && nl > 0) {
-      k_cycles<<<grid_for(nl, 128), 128, 0, s>>>(gv, wp.delta, wp.K, la.p, lb.p, nl, wp.cyc,
-                                                  acc.p);
-      AML_CUDA(cudaGetLastError());
+      DBuf<int2> crng(E, s);
+      AML_LAUNCH("k_close_range", s,
+                 k_close_range<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, crng.p));
+      CycFrontier F;
+      std::memset(&F, 0, sizeof(F));
+      F.la = la.p;
+      F.lb = lb.p;
+      std::vector<DBuf<int32_t>> front;  // par/slot of levels >= 3
+      front.reserve(2 * MAX_CYCLE);
+      int64_t n = nl;
+      for (int j = 2; j <= wp.K - 1 && n > 0; ++j) {
+        const bool has_next = j + 1 <= wp.K - 1;
+        DBuf<int32_t> cnt(has_next ? n + 1 : 0, s), q0(has_next ? n : 0, s);
+        AML_LAUNCH("k_cyc_level", s,
+                   k_cyc_level<<<grid_for(n, B), B, 0, s>>>(gv, wp.delta, wp.K, j, F, n, crng.p,
+                                                            wp.cyc, acc.p, cnt.p, q0.p));
+        if (!has_next) break;
+        DBuf<int64_t> foff(n + 1, s);
+        AML_CUDA(cudaMemsetAsync(cnt.p + n, 0, sizeof(int32_t), s));
+        scan_i32_to_i64(cnt.p, foff.p, n + 1, s);
+        int64_t& nn = lc.n_front[j + 1];
+        if (nn < 0) {
+          AML_CUDA(cudaMemcpyAsync(&nn, foff.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+          AML_CUDA(cudaStreamSynchronize(s));
+          AML_REQUIRE(nn < (int64_t)INT32_MAX, AML_EUNSUPPORTED, "cycle frontier too large");
+        }
+        front.emplace_back((size_t)nn, s);
+        int32_t* par = front.back().p;
+        front.emplace_back((size_t)nn, s);
+        int32_t* slot = front.back().p;
+        AML_LAUNCH("k_cyc_emit", s,
+                   k_cyc_emit<<<grid_for(n, B), B, 0, s>>>(n, cnt.p, q0.p, foff.p, par, slot));
+        F.par[j + 1] = par;
+        F.slot[j + 1] = slot;
+        n = nn;
+      }
     }
   }
-  k_assemble<<<grid_for(E, B), B, 0, s>>>(P);
-  AML_CUDA(cudaGetLastError());
+  AML_LAUNCH("k_assemble", s, k_assemble<<<grid_for(E, B), B, 0, s>>>(P));
 }
 
 }  // namespace aml

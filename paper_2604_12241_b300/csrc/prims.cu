@@ -3,6 +3,7 @@
 #include <set>
 
 #include "aml_internal.cuh"
+#include "profile.cuh"
 
 namespace aml {
 
@@ -43,8 +44,7 @@ __global__ void k_iota(int32_t* out, int64_t n) {
 
 void iota_i32(int32_t* out, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
-  k_iota<<<grid_for(n, 256), 256, 0, s>>>(out, n);
-  AML_CUDA(cudaGetLastError());
+  AML_LAUNCH("k_iota", s, k_iota<<<grid_for(n, 256), 256, 0, s>>>(out, n));
 }
 
 // ------------------------------------------------------------- prefix sum
@@ -139,16 +139,17 @@ static void scan_impl(const Tin* in, Tacc* out, int64_t n, bool inclusive, cudaS
   if (n <= 0) return;
   int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nb == 1) {
-    k_tile_scan<Tin, Tacc><<<1, SCAN_BLOCK, 0, s>>>(in, out, n, nullptr, inclusive);
-    AML_CUDA(cudaGetLastError());
+    AML_LAUNCH("k_tile_scan", s,
+               k_tile_scan<Tin, Tacc><<<1, SCAN_BLOCK, 0, s>>>(in, out, n, nullptr, inclusive));
     return;
   }
   DBuf<Tacc> part(nb, s);
-  k_tile_reduce<Tin, Tacc><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, n, part.p);
-  AML_CUDA(cudaGetLastError());
+  AML_LAUNCH("k_tile_reduce", s,
+             k_tile_reduce<Tin, Tacc><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, n, part.p));
   scan_impl<Tacc, Tacc>(part.p, part.p, nb, false, s);
-  k_tile_scan<Tin, Tacc><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, out, n, part.p, inclusive);
-  AML_CUDA(cudaGetLastError());
+  AML_LAUNCH("k_tile_scan", s,
+             k_tile_scan<Tin, Tacc><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(
+                 in, out, n, part.p, inclusive));
 }
 
 void scan_i32(const int32_t* in, int32_t* out, int64_t n, bool inclusive, cudaStream_t s) {
@@ -247,11 +248,10 @@ static void radix_impl(K* keys, uint32_t* vals, K* keys_tmp, uint32_t* vals_tmp,
   K* kb = keys_tmp;
   uint32_t* vb = vals_tmp;
   for (int shift = 0; shift < nbits; shift += 8) {
-    k_rs_hist<K><<<nb, RS_BLOCK, 0, s>>>(ka, n, shift, hist.p, nb);
-    AML_CUDA(cudaGetLastError());
+    AML_LAUNCH("k_rs_hist", s, k_rs_hist<K><<<nb, RS_BLOCK, 0, s>>>(ka, n, shift, hist.p, nb));
     scan_i32(hist.p, hist.p, (int64_t)nb * 256, false, s);
-    k_rs_scatter<K><<<nb, RS_BLOCK, 0, s>>>(ka, va, n, shift, hist.p, nb, kb, vb);
-    AML_CUDA(cudaGetLastError());
+    AML_LAUNCH("k_rs_scatter", s,
+               k_rs_scatter<K><<<nb, RS_BLOCK, 0, s>>>(ka, va, n, shift, hist.p, nb, kb, vb));
     K* tk = ka; ka = kb; kb = tk;
     uint32_t* tv = va; va = vb; vb = tv;
   }
