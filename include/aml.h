@@ -225,6 +225,33 @@ aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, i
  * (AML_ETIMEOUT, AML_EINTERNAL) recorded by its kernels since the last call. */
 aml_status aml_sync(aml_graph* g);
 
+/* ------------------------------------------------------ allocation-free FAN */
+
+/* FAN_OUT (direction = AML_DIR_OUT) or FAN_IN (AML_DIR_IN) of every edge for
+ * one window, computed without any device memory allocation.  The paper has
+ * no counterpart of this call: it exists for callers that cannot allocate at
+ * the point of use -- code running while a CUDA stream capture is active,
+ * serving processes that reserve their whole device-memory budget up front,
+ * and latency-critical loops that cannot afford an allocator's implicit
+ * synchronization.  aml_mine allocates scratch on every call; this does not.
+ *   g      : a graph made earlier by aml_graph_create
+ *   delta  : trailing window in seconds, >= 0
+ *   out    : device uint32[E], caller-owned; out[e] = the count for edge e,
+ *            equal to aml_mine's FAN_OUT / FAN_IN column for the same window
+ *   stream : the work is enqueued on it; the call does not wait for it
+ * Limit: at most 4,194,304 non-loop edges (aml_graph_info.n_list_edges);
+ * larger graphs get AML_EINVAL.  Scratch: one fixed 32 MiB + 8 KiB __device__
+ * array, reserved on every GPU that loads the library until the process
+ * exits and shared by all calls -- calls that overlap on the GPU (concurrent
+ * streams or host threads) race on it and give wrong counts, so serialize
+ * them.  Each call writes every scratch word before reading it, so nothing
+ * from an earlier call leaks into a result.  The first call on each device
+ * resolves the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  No cudaMalloc, cudaFree or other
+ * allocating routine is called. */
+aml_status aml_fan_noalloc(const aml_graph* g, int32_t delta, int32_t direction, uint32_t* out,
+                           void* stream);
+
 /* --------------------------------------------------------------- profiling */
 
 /* Number of kernels the library has launched in this process (all devices,

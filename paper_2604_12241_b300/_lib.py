@@ -75,6 +75,7 @@ _SIGS = {
                                                 ctypes.POINTER(aml_column_info)]),
     "aml_mine": (ctypes.c_int32, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_uint32, _VP]),
     "aml_sync": (ctypes.c_int32, [_VP]),
+    "aml_fan_noalloc": (ctypes.c_int32, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
     "aml_launch_count": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_int64)]),
     "aml_profile_enable": (ctypes.c_int32, [ctypes.c_int32]),
     "aml_profile_read": (ctypes.c_int32, [ctypes.POINTER(aml_kernel_stat), ctypes.c_int32,
