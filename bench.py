@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="hi-small", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the workload (nodes, edges, hub cap) for profiling captures")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
@@ -250,9 +252,13 @@ def run_ours(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dist = Dist(ws)
-    base = aml_synth.WORKLOADS[args.workload]
-    params = dict(base)
-    params["seed"] = base["seed"] + rank * 1000     # independent replica per rank
+    params = dict(aml_synth.WORKLOADS[args.workload])
+    if args.scale != 1.0:
+        params["n_nodes"] = max(1000, int(params["n_nodes"] * args.scale))
+        params["n_edges"] = max(10_000, int(params["n_edges"] * args.scale))
+        if params.get("d_max"):
+            params["d_max"] = max(50.0, params["d_max"] * args.scale)
+    params["seed"] += rank * 1000     # independent replica per rank
     g = aml_synth.generate(name=args.workload, **params)
     pats = P.workload_patterns(args.workload)
     E, Pn = g.n_edges, len(pats)
@@ -347,6 +353,7 @@ def run_ours(args, ws, rank, local):
                 "impl": "ours",
                 "config": {"workload": WORKLOAD_TEXT[args.workload], "n_edges": E,
                            "n_nodes": g.n_nodes, "columns": Pn, "mode": "plain",
+                           "scale": args.scale,
                            "l2": "flushed between steps (256 MB write, untimed)",
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "wall_s_timed_loop": wall},

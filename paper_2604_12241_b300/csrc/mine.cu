@@ -131,83 +131,287 @@ __global__ void __launch_bounds__(256) k_gs_into(GraphView g, int32_t delta,
   gs_in[b] = (g.src[b] == g.dst[b]) ? 0 : legs_into(g, b, delta);
 }
 
+// --------------------------------------------------------- leg emission
+//
+// A leg (a, b) of a scatter-gather candidate is filed under its (source,
+// destination) pair s*N + d.  Pairs are spread over `nb` buckets by the top
+// bits of a 64-bit mix of the key (MurmurHash3's finalizer, Appleby), so a
+// bucket holds ~1.5K legs and every leg of one pair lands in one bucket.
+
+__device__ __forceinline__ uint64_t mix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+__device__ __forceinline__ uint32_t bucket_of(uint64_t key, int bucket_bits) {
+  return bucket_bits ? (uint32_t)(mix64(key) >> (64 - bucket_bits)) : 0u;
+}
+
+// bucket histogram increment, aggregated over the lanes of a warp that hit
+// the same bucket
+__device__ __forceinline__ void count_bucket(uint32_t* hist, uint32_t bkt, bool active) {
+  const unsigned act = __ballot_sync(0xffffffffu, active);
+  if (!active) return;
+  const unsigned peers = __match_any_sync(act, bkt);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(hist + bkt, (uint32_t)__popc(peers));
+}
+
+__device__ __forceinline__ void put_leg(const LegSink& S, int64_t pos, int32_t a, int32_t b,
+                                        int32_t x, int32_t h, int32_t y, int32_t ta, int32_t tb,
+                                        int64_t n_nodes) {
+  if (S.la) {
+    S.la[pos] = a;
+    S.lb[pos] = b;
+  }
+  if (S.rec) {
+    LegRec r;
+    r.key = (uint64_t)x * (uint64_t)n_nodes + (uint64_t)y;
+    r.lo = ta;
+    r.hi = tb;
+    r.m = h;
+    r.a = a;
+    r.b = b;
+    r.pad = 0;
+    S.rec[pos] = r;
+  }
+}
+
 // Writes every leg (a, b) of edge a at off[a]...; reciprocal edges b = h->x
 // inside the window close 2-cycles (a, b) and are credited directly.  With
-// gs_in, also counts the legs ending with each edge (the scatter side of GS).
+// gs_in, also counts the legs ending with each edge (the scatter side of GS);
+// with records, also counts them into the SG buckets.  Windows of up to 32
+// slots are written by their own lane; longer ones (hub accounts) by the
+// whole warp, 32 slots at a time, with ballots keeping the output order.
 __global__ void __launch_bounds__(256) k_leg_emit(GraphView g, int32_t delta,
-                                                  const int64_t* __restrict__ off,
-                                                  int32_t* __restrict__ la,
-                                                  int32_t* __restrict__ lb,
-                                                  uint64_t* __restrict__ key, int64_t n_nodes,
+                                                  const int64_t* __restrict__ off, LegSink S,
                                                   unsigned long long* __restrict__ acc_cyc2,
                                                   int32_t* __restrict__ gs_in) {
-  int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a64 >= g.E) return;
-  int32_t a = (int32_t)a64;
-  int32_t x = g.src[a];
-  if (x == g.dst[a]) return;
-  int32_t q0, q1;
-  leg_window(g, a, q0, q1, delta);
-  int64_t o = off[a];
-  unsigned long long n_cyc2 = 0;
-  for (int32_t q = q0; q < q1; ++q) {
-    int32_t y = __ldg(g.onbr + q);
-    int32_t b = __ldg(g.oeid + q);
-    if (y == x) {
-      if (acc_cyc2) {
-        atomicAdd(acc_cyc2 + b, 1ull);
-        ++n_cyc2;
-      }
-      continue;
+  const int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  int32_t a = (int32_t)a64, x = 0, q0 = 0, q1 = 0, h = 0, ta = 0;
+  int64_t o = 0;
+  if (a64 < g.E) {
+    x = g.src[a];
+    h = g.dst[a];
+    if (x != h) {
+      leg_window(g, a, q0, q1, delta);
+      o = off[a];
+      ta = g.ts[a];
     }
-    la[o] = a;
-    lb[o] = b;
-    if (key) key[o] = (uint64_t)x * (uint64_t)n_nodes + (uint64_t)y;
-    if (gs_in) atomicAdd(gs_in + b, 1);
-    ++o;
+  }
+  const bool own = q1 - q0 <= 32;
+  // lanes with short windows walk them in lock step (one slot per round)
+  const int32_t own_len = own ? q1 - q0 : 0;
+  int32_t rounds = own_len;
+  for (int sh = 16; sh > 0; sh >>= 1)
+    rounds = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, sh));
+  unsigned long long n_cyc2 = 0;
+  for (int32_t r = 0; r < rounds; ++r) {
+    const bool in = r < own_len;
+    const int32_t q = q0 + r;
+    const int32_t y = in ? __ldg(g.onbr + q) : x;
+    const int32_t b = in ? __ldg(g.oeid + q) : 0;
+    const bool leg = in && y != x;
+    if (leg) {
+      put_leg(S, o, a, b, x, h, y, ta, __ldg(g.ot + q), g.N);
+      if (gs_in) atomicAdd(gs_in + b, 1);
+      ++o;
+    } else if (in && acc_cyc2) {
+      atomicAdd(acc_cyc2 + b, 1ull);
+      ++n_cyc2;
+    }
+    if (S.hist)
+      count_bucket(S.hist, leg ? bucket_of((uint64_t)x * (uint64_t)g.N + (uint64_t)y, S.bits) : 0u,
+                   leg);
   }
   if (n_cyc2) atomicAdd(acc_cyc2 + a, n_cyc2);
+  unsigned heavy = __ballot_sync(0xffffffffu, !own);
+  while (heavy) {
+    const int src = __ffs(heavy) - 1;
+    heavy &= heavy - 1;
+    const int32_t ha = __shfl_sync(0xffffffffu, a, src);
+    const int32_t hx = __shfl_sync(0xffffffffu, x, src);
+    const int32_t hh = __shfl_sync(0xffffffffu, h, src);
+    const int32_t hta = __shfl_sync(0xffffffffu, ta, src);
+    const int32_t hq1 = __shfl_sync(0xffffffffu, q1, src);
+    int32_t base = __shfl_sync(0xffffffffu, q0, src);
+    int64_t ho = __shfl_sync(0xffffffffu, o, src);
+    unsigned long long hc2 = 0;
+    for (; base < hq1; base += 32) {
+      const int32_t q = base + lane;
+      const bool in = q < hq1;
+      const int32_t y = in ? __ldg(g.onbr + q) : hx;
+      const int32_t b = in ? __ldg(g.oeid + q) : 0;
+      const bool leg = in && y != hx;
+      const unsigned m = __ballot_sync(0xffffffffu, leg);
+      if (leg) {
+        put_leg(S, ho + __popc(m & lt), ha, b, hx, hh, y, hta, __ldg(g.ot + q), g.N);
+        if (gs_in) atomicAdd(gs_in + b, 1);
+      } else if (in && acc_cyc2) {
+        atomicAdd(acc_cyc2 + b, 1ull);
+        ++hc2;
+      }
+      if (S.hist)
+        count_bucket(S.hist,
+                     leg ? bucket_of((uint64_t)hx * (uint64_t)g.N + (uint64_t)y, S.bits) : 0u,
+                     leg);
+      ho += __popc(m);
+    }
+    if (acc_cyc2) {
+      for (int sh = 16; sh > 0; sh >>= 1) hc2 += __shfl_down_sync(0xffffffffu, hc2, sh);
+      if (lane == 0 && hc2) atomicAdd(acc_cyc2 + ha, hc2);
+    }
+  }
 }
 
 // --------------------------------------------------------- scatter-gather
 //
-// Legs sorted by (s, d): each run of equal keys holds all legs between one
-// source and one destination.  A leg's partners are the legs of its run with
-// another intermediary whose union with it spans at most delta; each partner
-// pair is one SG instance, credited to the four edges (a leg credits its own
-// two edges once per partner, and the partner credits its two).
+// Every SG instance is two legs of one (s, d) pair with different
+// intermediaries whose four edges span at most delta; it is credited to the
+// four edges (each leg credits its own two edges once per partner leg).
+// After emission the leg records are moved into their buckets; then one
+// block per bucket groups its records by key in a shared-memory hash table
+// and counts, for every record of a group of two or more, its partners.
 
-__global__ void __launch_bounds__(256) k_sg_group(const uint64_t* __restrict__ key,
-                                                  const uint32_t* __restrict__ idx, int64_t n,
-                                                  const int32_t* __restrict__ la,
-                                                  const int32_t* __restrict__ lb,
-                                                  const int32_t* __restrict__ dst,
-                                                  const int32_t* __restrict__ ts, int32_t delta,
-                                                  unsigned long long* __restrict__ acc) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint64_t k = key[i];
-  int64_t gs = i, ge = i + 1;
-  while (gs > 0 && key[gs - 1] == k) --gs;
-  while (ge < n && key[ge] == k) ++ge;
-  if (ge - gs < 2) return;
-  uint32_t li = idx[i];
-  int32_t ai = la[li], bi = lb[li];
-  int32_t mi = dst[ai];
-  int64_t lo = ts[ai], hi = ts[bi];
-  unsigned long long c = 0;
-  for (int64_t j = gs; j < ge; ++j) {
-    if (j == i) continue;
-    uint32_t lj = idx[j];
-    int32_t aj = la[lj];
-    if (dst[aj] == mi) continue;
-    int64_t loj = ts[aj], hij = ts[lb[lj]];
-    int64_t span = max(hi, hij) - min(lo, loj);
-    c += (span <= delta) ? 1ull : 0ull;
+// SG_PART_ITEMS independent records per thread keep several cursor atomics
+// in flight at once (the kernel is bound by their latency)
+__global__ void __launch_bounds__(256) k_sg_partition(const LegRec* __restrict__ rec, int64_t n,
+                                                      int bits,
+                                                      const int64_t* __restrict__ boff,
+                                                      uint32_t* __restrict__ cursor,
+                                                      LegRec* __restrict__ out) {
+  const int64_t base = (int64_t)blockIdx.x * blockDim.x * SG_PART_ITEMS + threadIdx.x;
+  LegRec r[SG_PART_ITEMS];
+  uint32_t bkt[SG_PART_ITEMS];
+  int64_t pos[SG_PART_ITEMS];
+#pragma unroll
+  for (int k = 0; k < SG_PART_ITEMS; ++k) {
+    const int64_t i = base + (int64_t)k * blockDim.x;
+    if (i < n) {
+      r[k] = rec[i];
+      bkt[k] = bucket_of(r[k].key, bits);
+    }
   }
+#pragma unroll
+  for (int k = 0; k < SG_PART_ITEMS; ++k)
+    if (base + (int64_t)k * blockDim.x < n) pos[k] = boff[bkt[k]] + atomicAdd(cursor + bkt[k], 1u);
+#pragma unroll
+  for (int k = 0; k < SG_PART_ITEMS; ++k)
+    if (base + (int64_t)k * blockDim.x < n) out[pos[k]] = r[k];
+}
+
+
+__device__ __forceinline__ void sg_credit(unsigned long long* acc, const LegRec& r,
+                                          unsigned long long c) {
   if (c) {
-    atomicAdd(acc + ai, c);
-    atomicAdd(acc + bi, c);
+    atomicAdd(acc + r.a, c);
+    atomicAdd(acc + r.b, c);
+  }
+}
+
+__device__ __forceinline__ bool sg_partner(const LegRec& r, const LegRec& o, int32_t delta) {
+  if (o.m == r.m) return false;  // same intermediary (also the record itself)
+  const int64_t span = (int64_t)max(r.hi, o.hi) - (int64_t)min(r.lo, o.lo);
+  return span <= delta;
+}
+
+__global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ rec,
+                                                   const int64_t* __restrict__ boff,
+                                                   int32_t delta,
+                                                   unsigned long long* __restrict__ acc) {
+  extern __shared__ __align__(16) unsigned char sg_smem[];
+  unsigned long long* s_key = reinterpret_cast<unsigned long long*>(sg_smem);
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_key + SG_TAB);
+  uint32_t* s_end = s_cnt + SG_TAB;
+  uint16_t* s_slot = reinterpret_cast<uint16_t*>(s_end + SG_TAB);
+  uint16_t* s_idx = s_slot + SG_CAP;
+  const int64_t base = boff[blockIdx.x];
+  const int n = (int)(boff[blockIdx.x + 1] - base);
+  if (n < 2) return;
+  const LegRec* R = rec + base;
+  if (n > SG_CAP) {
+    // oversized bucket (a very large pair): compare every record with all
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const LegRec r = R[i];
+      unsigned long long c = 0;
+      for (int j = 0; j < n; ++j) {
+        const LegRec o = R[j];
+        if (o.key == r.key && sg_partner(r, o, delta)) ++c;
+      }
+      sg_credit(acc, r, c);
+    }
+    return;
+  }
+  for (int t = threadIdx.x; t < SG_TAB; t += blockDim.x) {
+    s_key[t] = ~0ull;
+    s_cnt[t] = 0;
+  }
+  __syncthreads();
+  // file every record under its key
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned long long key = R[i].key;
+    uint32_t h = (uint32_t)mix64(key) & (SG_TAB - 1);
+    for (int probe = 0; probe < SG_TAB; ++probe) {  // n < SG_TAB: a slot is always found
+      const unsigned long long cur = s_key[h];
+      if (cur == key) break;
+      if (cur == ~0ull) {
+        const unsigned long long old = atomicCAS(&s_key[h], ~0ull, key);
+        if (old == ~0ull || old == key) break;
+      }
+      h = (h + 1) & (SG_TAB - 1);
+    }
+    s_slot[i] = (uint16_t)h;
+    atomicAdd(&s_cnt[h], 1u);
+  }
+  __syncthreads();
+  // group starts: exclusive prefix of the slot counts (16 slots per thread)
+  {
+    constexpr int PER = SG_TAB / 256;
+    uint32_t loc[PER], sum = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      loc[k] = s_cnt[threadIdx.x * PER + k];
+      sum += loc[k];
+    }
+    __shared__ uint32_t s_wsum[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    uint32_t before = x - sum;
+    for (int w = 0; w < warp; ++w) before += s_wsum[w];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      s_end[threadIdx.x * PER + k] = before;  // becomes the end after the fill below
+      before += loc[k];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint32_t h = s_slot[i];
+    if (s_cnt[h] >= 2) s_idx[atomicAdd(&s_end[h], 1u)] = (uint16_t)i;
+  }
+  __syncthreads();
+  // partners inside each group of two or more
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint32_t h = s_slot[i];
+    const uint32_t c = s_cnt[h];
+    if (c < 2) continue;
+    const LegRec r = R[i];
+    const uint32_t gs = s_end[h] - c;
+    unsigned long long k = 0;
+    for (uint32_t j = gs; j < gs + c; ++j)
+      if (sg_partner(r, R[s_idx[j]], delta)) ++k;
+    sg_credit(acc, r, k);
   }
 }
 

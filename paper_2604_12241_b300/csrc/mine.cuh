@@ -8,6 +8,11 @@ namespace aml {
 constexpr int MAX_COLS = 64;    // columns per pattern set
 constexpr int MAX_DELTAS = 16;  // distinct windows per pattern set
 constexpr int MAX_CYCLE = 8;    // longest cycle
+constexpr int SG_CAP = 1024;    // leg records one SG bucket block groups in shared memory
+constexpr int SG_TAB = 2048;    // its hash-table slots (load <= 0.5)
+constexpr int SG_BUCKET_MEAN = 384;  // target records per SG bucket
+constexpr int SG_PART_ITEMS = 4;     // records per thread in k_sg_partition
+constexpr size_t SG_SMEM = (size_t)SG_TAB * (8 + 4 + 4) + (size_t)SG_CAP * (2 + 2);
 
 // Read-only view of a device graph, passed by value to kernels.
 struct GraphView {
@@ -55,6 +60,26 @@ struct AssembleParams {
   int64_t ld;
 };
 
+// One leg a = s->m (at time lo), b = m->d (at time hi) filed for the SG
+// grouping under key s*N + d; 32 bytes.
+struct LegRec {
+  uint64_t key;
+  int32_t lo, hi;
+  int32_t m;
+  int32_t a, b;
+  int32_t pad;
+};
+
+// Where k_leg_emit writes the legs: (a, b) arrays for the cycle search
+// and/or records + bucket histogram for the SG grouping (null = not wanted).
+struct LegSink {
+  int32_t* la;
+  int32_t* lb;
+  LegRec* rec;
+  uint32_t* hist;
+  int bits;  // log2 of the number of SG buckets
+};
+
 struct CycleSlots {
   int32_t slot[MAX_CYCLE + 1];  // accumulator column of CYC_k, or -1
 };
@@ -74,12 +99,12 @@ __global__ void k_window_slots(const int32_t* ptr, const int32_t* t, const int32
                                int64_t Ev, int32_t delta, int32_t* lb, int32_t* D);
 __global__ void k_leg_count(GraphView g, int32_t delta, int32_t* L);
 __global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);
-__global__ void k_leg_emit(GraphView g, int32_t delta, const int64_t* off, int32_t* la,
-                           int32_t* lb, uint64_t* key, int64_t n_nodes,
+__global__ void k_leg_emit(GraphView g, int32_t delta, const int64_t* off, LegSink S,
                            unsigned long long* acc_cyc2, int32_t* gs_in);
-__global__ void k_sg_group(const uint64_t* key, const uint32_t* idx, int64_t n, const int32_t* la,
-                           const int32_t* lb, const int32_t* dst, const int32_t* ts,
-                           int32_t delta, unsigned long long* acc);
+__global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, const int64_t* boff,
+                               uint32_t* cursor, LegRec* out);
+__global__ void k_sg_bucket(const LegRec* rec, const int64_t* boff, int32_t delta,
+                            unsigned long long* acc);
 __global__ void k_close_range(GraphView g, int32_t delta, int2* rng);
 __global__ void k_cyc_level(GraphView g, int32_t delta, int K, int j, CycFrontier F, int64_t n,
                             const int2* close_rng, CycleSlots slots, unsigned long long* acc,

@@ -4,7 +4,8 @@
 //   1. window starts (and FAN repeat deltas + scan) of the out- and in-slots;
 //   2. legs: count per edge, scan to offsets, emit (a, b) pairs, crediting
 //      2-cycles and counting the legs that end at each edge;
-//   3. SG: sort legs by (s, d), count partner legs inside each run;
+//   3. SG: bucket the leg records by a hash of (s, d), then per bucket group
+//      them by (s, d) in shared memory and count partner legs;
 //   4. CYC_3..K: closing ranges, then the legs extended level by level;
 // and finally one pass writes every output row.  All of it is enqueued on
 // the caller's stream; only the first mine of a (graph, window) pair waits
@@ -151,25 +152,48 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     }
     const int64_t nl = lc.n_legs;
     if (gs_in) AML_CUDA(cudaMemsetAsync(gs_in, 0, (size_t)E * 4, s));
-    DBuf<int32_t> la(nl, s), lb(nl, s);
-    DBuf<uint64_t> key(wp.sg ? nl : 0, s);
+    LegSink S{nullptr, nullptr, nullptr, nullptr, 0};
+    DBuf<int32_t> la, lb;
+    if (wp.K >= 3) {  // the cycle search starts from the (a, b) pairs
+      la = DBuf<int32_t>((size_t)nl, s);
+      lb = DBuf<int32_t>((size_t)nl, s);
+      S.la = la.p;
+      S.lb = lb.p;
+    }
+    DBuf<LegRec> rec;
+    DBuf<uint32_t> hist;
+    int64_t nb = 1;
+    if (wp.sg) {
+      while (nb * SG_BUCKET_MEAN < nl) nb <<= 1;
+      while ((1ll << S.bits) < nb) ++S.bits;
+      rec = DBuf<LegRec>((size_t)nl, s);
+      hist = DBuf<uint32_t>((size_t)nb + 1, s);
+      AML_CUDA(cudaMemsetAsync(hist.p, 0, (size_t)(nb + 1) * 4, s));
+      S.rec = rec.p;
+      S.hist = hist.p;
+    }
     unsigned long long* acc2 =
         wp.cyc.slot[2] >= 0 ? acc.p + (int64_t)wp.cyc.slot[2] * E : nullptr;
     AML_LAUNCH("k_leg_emit", s,
-               k_leg_emit<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, off, la.p, lb.p,
-                                                       wp.sg ? key.p : nullptr, g->N, acc2,
-                                                       gs_in));
-    // 3. scatter-gather
+               k_leg_emit<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, off, S, acc2, gs_in));
+    // 3. scatter-gather: bucket the leg records, group each bucket by (s, d)
     if (wp.sg && nl > 1) {
-      DBuf<uint32_t> idx(nl, s), itmp(nl, s);
-      DBuf<uint64_t> ktmp(nl, s);
-      iota_i32(reinterpret_cast<int32_t*>(idx.p), nl, s);
-      uint64_t max_key = (uint64_t)g->N * (uint64_t)g->N;
-      radix_sort_u64(key.p, idx.p, ktmp.p, itmp.p, nl, bits_for(max_key), s);
-      AML_LAUNCH("k_sg_group", s,
-                 k_sg_group<<<grid_for(nl, B), B, 0, s>>>(key.p, idx.p, nl, la.p, lb.p, g->dst,
-                                                          g->ts, wp.delta,
-                                                          acc.p + (int64_t)wp.sg_slot * E));
+      DBuf<int64_t> boff((size_t)nb + 1, s);
+      scan_i32_to_i64(reinterpret_cast<const int32_t*>(hist.p), boff.p, nb + 1, s);
+      AML_CUDA(cudaMemsetAsync(hist.p, 0, (size_t)nb * 4, s));  // now the bucket cursors
+      DBuf<LegRec> part((size_t)nl, s);
+      AML_LAUNCH("k_sg_partition", s,
+                 k_sg_partition<<<grid_for(nl, B * SG_PART_ITEMS), B, 0, s>>>(
+                     rec.p, nl, S.bits, boff.p, hist.p, part.p));
+      static bool smem_set[64] = {false};  // per device
+      if (g->device >= 64 || !smem_set[g->device]) {
+        AML_CUDA(cudaFuncSetAttribute(k_sg_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)SG_SMEM));
+        if (g->device < 64) smem_set[g->device] = true;
+      }
+      AML_LAUNCH("k_sg_bucket", s,
+                 k_sg_bucket<<<(unsigned)nb, B, SG_SMEM, s>>>(part.p, boff.p, wp.delta,
+                                                              acc.p + (int64_t)wp.sg_slot * E));
     }
     // 4. cycles of length >= 3, level by level from the legs
     if (wp.K >= 3 && nl > 0) {

@@ -208,3 +208,26 @@ def test_hi_small_invariants_and_planted(hi_small):
             assert (rows[:, c[f"SG@{DAY}"]] == m.k - 1).all()
         else:
             assert (rows[:, c[f"CYC{m.k}@{DAY}"]] == 1).all()
+
+
+def test_sg_pair_larger_than_a_bucket():
+    """One (s, d) pair with 1,440 legs (more than a shared-memory bucket
+    holds) plus background noise: exercises the oversized-bucket path."""
+    rng = np.random.default_rng(5)
+    s, d, n_mid, par = 0, 1, 40, 6
+    src, dst, ts = [], [], []
+    for m in range(2, 2 + n_mid):
+        for _ in range(par):
+            src.append(s); dst.append(m); ts.append(int(rng.integers(0, 500)))
+            src.append(m); dst.append(d); ts.append(int(rng.integers(500, 1000)))
+    n = 2 + n_mid + 30
+    for _ in range(3000):
+        a, b = rng.integers(0, n, 2)
+        if a != b:
+            src.append(int(a)); dst.append(int(b)); ts.append(int(rng.integers(0, 3000)))
+    src, dst, ts = (np.asarray(x, np.int32) for x in (src, dst, ts))
+    cols = [("sg", 1000), ("sg", 200), ("gs", 1000), ("cyc", 3, 600), ("cyc", 4, 600)]
+    want = oracle.OracleGraph(src, dst, ts, n).count_all(cols)
+    got = gpu_counts(src, dst, ts, n, P.from_oracle_columns(cols))
+    np.testing.assert_array_equal(got, want)
+    assert got[:, 0].max() > 1000
