@@ -43,7 +43,7 @@ WORKLOAD_TEXT = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="hi-small", choices=sorted(WORKLOAD_TEXT))
@@ -54,6 +54,9 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", choices=["graph", "plain"], default="graph",
+                    help="graph: the whole mine replayed as one captured CUDA graph")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -151,25 +154,37 @@ def measured_peak():
 def algorithmic_bytes(kernel: str, E: int, Ev: int, pats, n_legs: dict) -> float:
     """Bytes per launch the kernel's definition must move (no probes, no re-reads).
 
-    k_assemble, per edge: src, dst, ts (12 B); its two slot positions and two
-    row starts (16 B); per FAN column two prefix-sum values (8 B); per
-    accumulated SG/CYC column one uint64 (8 B); the output row (4 B/column).
-    k_leg_emit, per launch: src, dst, ts, leg offset of every edge (20 B/edge),
-    the (nbr, eid) slots of every leg's window (8 B per scanned slot, counted
-    as legs) and 16 B written per leg (a, b, 8-byte key).
-    k_fan_delta, per slot: t, eid, prev, next, row start (20 B) + delta (4 B).
+    n_legs: temporal 2-paths per window (= sum of the GS column / 2).  Kernels
+    launched once per window report the mean over the windows.
+      k_assemble    per edge: src, dst, ts (12 B), two slot positions and two
+                    row starts (16 B), per FAN column two prefix sums (8 B), per
+                    SG/CYC column one uint64 accumulator (8 B), the row (4 B/col)
+      k_leg_emit    per edge: src, dst, ts, leg offset (20 B); per leg: the
+                    window slot (nbr, eid, t: 12 B) and its outputs, (a, b) for
+                    the cycle search (8 B) and the 32-B SG record
+      k_sg_partition  per leg: one 32-B record read and written (64 B)
+      k_sg_bucket   per leg: one 32-B record read
+      k_window_slots  per list slot: t, eid, row, prev, next (20 B) + lb, delta (8 B)
+      k_cyc_level   per edge of the window: the anchor's closing range (8 B) and
+                    its two edges (8 B) -- the legs it starts from
     """
     P = len(pats)
     names = [p.name for p in pats]
     n_fan = sum(n.startswith("FAN") for n in names)
     n_acc = sum(n.startswith("SG") or n.startswith("CYC") for n in names)
+    legs = sum(n_legs.values()) / max(1, len(n_legs))
     if kernel == "k_assemble":
         return E * (12 + 16 + 8 * n_fan + 8 * n_acc + 4 * P)
     if kernel == "k_leg_emit":
-        legs = sum(n_legs.values()) / max(1, len(n_legs))
-        return E * 20 + legs * (8 + 16)
-    if kernel == "k_fan_delta":
-        return Ev * 24
+        return E * 20 + legs * (12 + 8 + 32)
+    if kernel == "k_sg_partition":
+        return legs * 64
+    if kernel == "k_sg_bucket":
+        return legs * 32
+    if kernel == "k_window_slots":
+        return Ev * 28
+    if kernel == "k_cyc_level":
+        return legs * 16
     return float("nan")
 
 
@@ -269,36 +284,53 @@ def run_ours(args, ws, rank, local):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB L2
     stream = torch.cuda.current_stream()
 
+    tune_info = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        best, best_ms = aml.autotune(graph, ps, repeats=3)
+        tune_info = {"tuning": best, "best_ms": best_ms, "seconds": time.perf_counter() - t0}
+    use_graph = args.mode == "graph"
     for _ in range(max(3, args.warmup)):
-        aml.mine(graph, ps, out=out)
+        aml.mine(graph, ps, out=out, use_graph=use_graph)
     torch.cuda.synchronize()
     graph.sync()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    def timed(steps, graph_mode, profile):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        dist.barrier()
+        torch.cuda.synchronize()
+        l0 = _lib.launch_count()
+        if profile:
+            _lib.profile_read(reset=True)
+            _lib.profile_enable(True)
+        w0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()                     # evict L2 between steps (not timed)
+            ev[k][0].record(stream)
+            aml.mine(graph, ps, out=out, stream=stream, use_graph=graph_mode)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        dist.barrier()
+        if profile:
+            _lib.profile_enable(False)
+        launches = _lib.launch_count() - l0
+        graph.sync()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        prof = _lib.profile_read(reset=True) if profile else {}
+        return ms, wall, launches, prof
+
+    # headline: the chosen mode, clocks sampled during the timed region
     clocks = ClockSampler(local)
-    _lib.profile_read(reset=True)
-    dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    launches0 = _lib.launch_count()
-    _lib.profile_enable(True)
-    wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()                     # evict L2 between steps (not timed)
-        ev[k][0].record(stream)
-        aml.mine(graph, ps, out=out, stream=stream)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    dist.barrier()
-    _lib.profile_enable(False)
-    launches = _lib.launch_count() - launches0
+    dev_ms, wall, launches, _ = timed(args.steps, use_graph, False)
     clk = clocks.stop()
-    graph.sync()
-    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
-    prof = _lib.profile_read(reset=True)
     dev_ms_max = dist.max(dev_ms)
+    # per-kernel CUDA-event times come from a plain-mode pass (events cannot be
+    # recorded between the kernels of a replayed graph)
+    prof_steps = max(3, min(args.steps, 10))
+    plain_ms, _, plain_launches, prof = timed(prof_steps, False, True)
 
     # end to end through the public API: pinned host inputs -> graph build ->
     # mine -> counts copied back to pinned host memory, every step
@@ -335,16 +367,21 @@ def run_ours(args, ws, rank, local):
         # dominant kernel of the timed region, from its own CUDA events
         dom = max(prof.items(), key=lambda kv: kv[1][1])
         dom_name, (dom_n, dom_ms) = dom
-        n_legs = {}
+        n_legs = {}   # each leg is one GS instance, counted on its two edges
+        for j, p in enumerate(pats):
+            if p.name.startswith("GS@"):
+                n_legs[p.name] = float(out[:, j].to(torch.int64).sum().item()) / 2
         peak, peak_src = measured_peak()
         alg = algorithmic_bytes(dom_name, E, info["n_list_edges"], pats, n_legs)
         achieved = alg / (dom_ms / dom_n / 1000.0) / 1e9 if alg == alg else None
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                 "traffic": None, "peak_source": peak_src,
-                "launch_ms": dom_ms / dom_n, "share_of_step": dom_ms / dev_ms,
-                "algorithmic_bytes_per_launch": alg}
-        kernels = {k: {"launches": n, "ms": round(ms, 4), "share": round(ms / dev_ms, 4)}
+                "launch_ms": dom_ms / dom_n, "share_of_step": dom_ms / plain_ms,
+                "algorithmic_bytes_per_launch": alg, "timed_in": "plain-mode profiled pass",
+                "legs_per_window": n_legs}
+        kernels = {k: {"launches": n, "ms_per_step": round(ms / prof_steps, 4),
+                       "share": round(ms / plain_ms, 4)}
                    for k, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
         line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": max(3, args.warmup),
@@ -352,12 +389,15 @@ def run_ours(args, ws, rank, local):
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "impl": "ours",
                 "config": {"workload": WORKLOAD_TEXT[args.workload], "n_edges": E,
-                           "n_nodes": g.n_nodes, "columns": Pn, "mode": "plain",
+                           "n_nodes": g.n_nodes, "columns": Pn, "mode": args.mode,
+                           "autotune": tune_info,
                            "scale": args.scale,
                            "l2": "flushed between steps (256 MB write, untimed)",
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "wall_s_timed_loop": wall},
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clk,
+                "plain_ms_per_step": plain_ms / prof_steps,
+                "plain_gpu_launches_per_step": plain_launches / prof_steps,
                 "kernels": kernels}
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g, pats, args.cpu_seconds)

@@ -207,6 +207,12 @@ aml_status aml_pattern_set_column(const aml_pattern_set* ps, int32_t col,
 /* ------------------------------------------------------------------ mining */
 
 #define AML_MINE_HOST_OUTPUT 0x1u  /* counts is a host pointer (copied back)     */
+#define AML_MINE_GRAPH 0x2u        /* replay the whole mine as one CUDA graph:   */
+                                   /* the first call with a given (pattern set,  */
+                                   /* counts, ld, tuning) mines normally and     */
+                                   /* captures the kernel sequence on a private  */
+                                   /* stream; later calls are one graph launch.  */
+                                   /* Device output only.                        */
 
 /* Count every pattern of `ps` for every edge of `g`.
  *   counts : uint32, row-major, row e = input edge e, column j = pattern j;
@@ -221,9 +227,93 @@ aml_status aml_pattern_set_column(const aml_pattern_set* ps, int32_t col,
 aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
                     uint32_t flags, void* stream);
 
+/* Runtime tunables of the mining kernels.  None of them changes any count;
+ * they trade work distribution against overhead.  Defaults: 32, 384, 48, 256. */
+typedef struct aml_tuning {
+  int32_t own_max;         /* windows up to this many slots are walked by one lane,
+                              longer ones by a whole warp (degree binning), [0, 4096] */
+  int32_t sg_bucket_mean;  /* target leg records per scatter-gather hash bucket, [16, 512] */
+  int32_t close_scan_max;  /* cycle closing ranges up to this long are scanned, longer ones
+                              binary-searched, [0, 4096]                               */
+  int32_t block;           /* threads per block of the per-edge kernels: 64, 128, 256, 512 */
+} aml_tuning;
+
+aml_status aml_graph_get_tuning(const aml_graph* g, aml_tuning* out);
+/* Replace a graph's tunables (AML_EINVAL outside the ranges above); drops
+ * the graph's captured mines. */
+aml_status aml_graph_set_tuning(aml_graph* g, const aml_tuning* t);
+
+/* Autotuner: times real mines of `ps` on `g` (median of `repeats` after one
+ * warm-up each, CUDA events on `stream`) while sweeping one tunable at a time
+ * over a fixed candidate list, keeps the fastest setting on the graph and
+ * reports it (best / best_ms may be NULL).  Synchronizes `stream`; allocates
+ * a temporary output.  The replacement for the paper's compile-time choice of
+ * evaluation plan from neighbourhood size and selectivity (Sec. 6). */
+aml_status aml_autotune(aml_graph* g, const aml_pattern_set* ps, int32_t repeats, void* stream,
+                        aml_tuning* best, float* best_ms);
+
 /* Wait for the graph's enqueued work and report device-side errors
  * (AML_ETIMEOUT, AML_EINTERNAL) recorded by its kernels since the last call. */
 aml_status aml_sync(aml_graph* g);
+
+/* --------------------------------------------------------------- streaming */
+
+/* Streaming recount (Sec. 5, "Integration with streaming analytics": each
+ * arriving transaction increments the counts of all instances it takes part
+ * in; incremental processing with localized updates).  Transactions arrive
+ * in batches whose timestamps never decrease; edges get global row ids in
+ * arrival order.  After every append, each resident row holds the count of
+ * its column over the whole history.  A batch B is recounted exactly by
+ * mining the window W of resident edges within delta_max of B twice (with and
+ * without B) and crediting the difference: the instances B creates.  Rows
+ * older than t_max - resident_window are evicted. */
+typedef struct aml_stream aml_stream;
+
+typedef struct aml_stream_batch {
+  int64_t first_row;           /* global row id of the batch's first edge        */
+  int64_t n_rows;              /* edges appended                                  */
+  int64_t rows_recounted;      /* resident rows inside the recount window W       */
+  int64_t resident_first_row;  /* oldest resident row after the append           */
+  int64_t resident_rows;
+} aml_stream_batch;
+
+typedef struct aml_stream_info {
+  int64_t resident_first_row;
+  int64_t resident_rows;
+  int64_t capacity_rows;       /* resident rows the budget allows                 */
+  int64_t final_end_row;       /* rows below this will never change again         */
+  int64_t device_bytes;        /* resident storage                                */
+  int32_t t_max;               /* latest timestamp appended                        */
+  int32_t delta_max;           /* largest window of the pattern set               */
+} aml_stream_info;
+
+/* Open a stream counting the columns of `ps` (copied) over accounts
+ * [0, n_nodes).  resident_window_s must be >= the largest pattern window.
+ * mem_budget_bytes bounds the device memory of the stream: half holds
+ * resident rows (16 + 4*P bytes each), half is the working set of one append
+ * (estimated at 512 + 16*P bytes per edge of the recount window).
+ * Errors: AML_EINVAL, AML_ENOMEM, AML_ECUDA. */
+aml_status aml_stream_open(const aml_pattern_set* ps, int32_t n_nodes, int32_t resident_window_s,
+                           size_t mem_budget_bytes, aml_stream** out);
+
+/* Append n transactions (host arrays, or device arrays with AML_PTR_DEVICE)
+ * and recount.  Synchronous: returns when every count is updated.  The batch
+ * must be non-decreasing in time (AML_EUNSORTED) and start no earlier than
+ * the latest appended timestamp (AML_ELATE); ids must be in [0, n_nodes)
+ * (AML_EINVAL).  A batch that does not fit the budget returns AML_EADMIT.
+ * On any error the stream is unchanged.  info may be NULL. */
+aml_status aml_stream_append(aml_stream* st, const int32_t* src, const int32_t* dst,
+                             const int32_t* ts, const float* amount, int64_t n, uint32_t flags,
+                             void* stream, aml_stream_batch* info);
+
+/* Copy the counts of resident rows [row0, row0 + n) into out (row-major,
+ * stride ld >= P; device pointer, or host with AML_MINE_HOST_OUTPUT, which
+ * synchronizes `stream`).  Rows outside the resident range: AML_EINVAL. */
+aml_status aml_stream_read(aml_stream* st, int64_t row0, int64_t n, uint32_t* out, int64_t ld,
+                           uint32_t flags, void* stream);
+
+aml_status aml_stream_get_info(const aml_stream* st, aml_stream_info* info);
+aml_status aml_stream_close(aml_stream* st);
 
 /* ------------------------------------------------------ allocation-free FAN */
 

@@ -17,10 +17,11 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import patterns  # noqa: F401
-from ._lib import (ASSUME_SORTED, MINE_HOST_OUTPUT, PTR_DEVICE, PTR_HOST, AmlError,  # noqa: F401
-                   aml_column_info, aml_graph_info, check, lib, make_patterns)
+from ._lib import (ASSUME_SORTED, MINE_GRAPH, MINE_HOST_OUTPUT, PTR_DEVICE, PTR_HOST,  # noqa: F401
+                   AmlError, aml_column_info, aml_graph_info, aml_stream_batch,
+                   aml_stream_info, aml_tuning, check, lib, make_patterns)
 
-__all__ = ["Graph", "PatternSet", "mine", "AmlError", "patterns"]
+__all__ = ["Graph", "PatternSet", "Stream", "mine", "autotune", "AmlError", "patterns"]
 
 
 def _stream_handle(stream) -> int:
@@ -84,6 +85,17 @@ class Graph:
     def sync(self) -> None:
         check(lib().aml_sync(self._h))
 
+    def tuning(self) -> dict:
+        t = aml_tuning()
+        check(lib().aml_graph_get_tuning(self._h, ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in t._fields_}
+
+    def set_tuning(self, **kw) -> None:
+        cur = self.tuning()
+        cur.update(kw)
+        t = aml_tuning(**cur)
+        check(lib().aml_graph_set_tuning(self._h, ctypes.byref(t)))
+
     def close(self) -> None:
         if getattr(self, "_h", None):
             lib().aml_graph_destroy(self._h)
@@ -131,13 +143,25 @@ class PatternSet:
             pass
 
 
-def mine(graph: Graph, pset: PatternSet, out=None, stream=None, host_output: bool = False):
+def autotune(graph: Graph, pset: PatternSet, repeats: int = 3, stream=None):
+    """Pick the fastest tunables for this graph and pattern set (aml_autotune);
+    returns (tuning dict, median ms of the best setting)."""
+    t = aml_tuning()
+    ms = ctypes.c_float()
+    check(lib().aml_autotune(graph.handle, pset.handle, repeats, _stream_handle(stream),
+                             ctypes.byref(t), ctypes.byref(ms)))
+    return {f: getattr(t, f) for f, _ in t._fields_}, ms.value
+
+
+def mine(graph: Graph, pset: PatternSet, out=None, stream=None, host_output: bool = False,
+         use_graph: bool = False):
     """Per-edge counts, [E, P] (aml_mine).
 
     Device mode (default) returns / fills a torch int32 CUDA tensor holding
     the uint32 counts bit-for-bit (``.view(torch.uint32)`` or numpy
     ``.view(np.uint32)`` to read them unsigned).  ``host_output=True``
-    returns a numpy uint32 array copied back by the library.
+    returns a numpy uint32 array copied back by the library.  ``use_graph``
+    replays the whole mine as one captured CUDA graph (AML_MINE_GRAPH).
     """
     P = pset.n_cols
     E = graph.n_edges
@@ -155,5 +179,57 @@ def mine(graph: Graph, pset: PatternSet, out=None, stream=None, host_output: boo
     ptr, dev = _ptr(out)
     if not dev:
         raise ValueError("device mode needs a CUDA tensor")
-    check(lib().aml_mine(graph.handle, pset.handle, ptr, out.shape[1], 0, s))
+    check(lib().aml_mine(graph.handle, pset.handle, ptr, out.shape[1],
+                         MINE_GRAPH if use_graph else 0, s))
     return out
+
+
+class Stream:
+    """Streaming recount (aml_stream_*): append time-ordered batches, read
+    full-history counts of the resident rows."""
+
+    def __init__(self, pset: PatternSet, n_nodes: int, resident_window: int,
+                 mem_budget: int = 8 << 30):
+        h = ctypes.c_void_p()
+        check(lib().aml_stream_open(pset.handle, int(n_nodes), int(resident_window),
+                                    int(mem_budget), ctypes.byref(h)))
+        self._h = h
+        self.n_cols = pset.n_cols
+
+    def append(self, src, dst, ts, amount=None, stream=None) -> dict:
+        if isinstance(src, np.ndarray):
+            src = np.ascontiguousarray(src, dtype=np.int32)
+            dst = np.ascontiguousarray(dst, dtype=np.int32)
+            ts = np.ascontiguousarray(ts, dtype=np.int32)
+            if amount is not None:
+                amount = np.ascontiguousarray(amount, dtype=np.float32)
+        ps, dev = _ptr(src)
+        info = aml_stream_batch()
+        check(lib().aml_stream_append(self._h, ps, _ptr(dst)[0], _ptr(ts)[0],
+                                      _ptr(amount)[0] if amount is not None else None,
+                                      int(src.shape[0]), PTR_DEVICE if dev else PTR_HOST,
+                                      _stream_handle(stream), ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in info._fields_}
+
+    def read(self, row0: int, n: int) -> np.ndarray:
+        out = np.empty((n, self.n_cols), dtype=np.uint32)
+        if n:
+            check(lib().aml_stream_read(self._h, int(row0), int(n), out.ctypes.data,
+                                        self.n_cols, MINE_HOST_OUTPUT, _stream_handle(None)))
+        return out
+
+    def info(self) -> dict:
+        inf = aml_stream_info()
+        check(lib().aml_stream_get_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in inf._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().aml_stream_close(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

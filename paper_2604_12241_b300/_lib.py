@@ -20,6 +20,7 @@ STATUS = {0: "AML_OK", 1: "AML_EINVAL", 2: "AML_ENOMEM", 3: "AML_ECUDA", 4: "AML
 
 PTR_HOST, PTR_DEVICE, ASSUME_SORTED = 0x0, 0x1, 0x2
 MINE_HOST_OUTPUT = 0x1
+MINE_GRAPH = 0x2
 
 
 class AmlError(RuntimeError):
@@ -53,6 +54,24 @@ class aml_kernel_stat(ctypes.Structure):
                 ("total_ms", ctypes.c_double)]
 
 
+class aml_tuning(ctypes.Structure):
+    _fields_ = [("own_max", ctypes.c_int32), ("sg_bucket_mean", ctypes.c_int32),
+                ("close_scan_max", ctypes.c_int32), ("block", ctypes.c_int32)]
+
+
+class aml_stream_batch(ctypes.Structure):
+    _fields_ = [("first_row", ctypes.c_int64), ("n_rows", ctypes.c_int64),
+                ("rows_recounted", ctypes.c_int64), ("resident_first_row", ctypes.c_int64),
+                ("resident_rows", ctypes.c_int64)]
+
+
+class aml_stream_info(ctypes.Structure):
+    _fields_ = [("resident_first_row", ctypes.c_int64), ("resident_rows", ctypes.c_int64),
+                ("capacity_rows", ctypes.c_int64), ("final_end_row", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("t_max", ctypes.c_int32),
+                ("delta_max", ctypes.c_int32)]
+
+
 class aml_column_info(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int32), ("k", ctypes.c_int32), ("delta", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("name", ctypes.c_char * 32)]
@@ -75,6 +94,19 @@ _SIGS = {
                                                 ctypes.POINTER(aml_column_info)]),
     "aml_mine": (ctypes.c_int32, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_uint32, _VP]),
     "aml_sync": (ctypes.c_int32, [_VP]),
+    "aml_graph_get_tuning": (ctypes.c_int32, [_VP, ctypes.POINTER(aml_tuning)]),
+    "aml_graph_set_tuning": (ctypes.c_int32, [_VP, ctypes.POINTER(aml_tuning)]),
+    "aml_autotune": (ctypes.c_int32, [_VP, _VP, ctypes.c_int32, _VP, ctypes.POINTER(aml_tuning),
+                                      ctypes.POINTER(ctypes.c_float)]),
+    "aml_stream_open": (ctypes.c_int32, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t,
+                                         ctypes.POINTER(_VP)]),
+    "aml_stream_append": (ctypes.c_int32, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int64,
+                                           ctypes.c_uint32, _VP,
+                                           ctypes.POINTER(aml_stream_batch)]),
+    "aml_stream_read": (ctypes.c_int32, [_VP, ctypes.c_int64, ctypes.c_int64, _VP,
+                                         ctypes.c_int64, ctypes.c_uint32, _VP]),
+    "aml_stream_get_info": (ctypes.c_int32, [_VP, ctypes.POINTER(aml_stream_info)]),
+    "aml_stream_close": (ctypes.c_int32, [_VP]),
     "aml_fan_noalloc": (ctypes.c_int32, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
     "aml_launch_count": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_int64)]),
     "aml_profile_enable": (ctypes.c_int32, [ctypes.c_int32]),

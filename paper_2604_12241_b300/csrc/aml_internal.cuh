@@ -101,6 +101,24 @@ struct LegCache {
                         // cycle-search frontier sizes by level (index = path length)
 };
 
+// Runtime tunables of the mining kernels (none changes any count).
+struct Tuning {
+  int32_t own_max = 32;          // windows up to this long are walked by one lane
+  int32_t sg_bucket_mean = 384;  // target leg records per SG bucket
+  int32_t close_scan_max = 48;   // closing ranges up to this long are scanned
+  int32_t block = 256;           // threads per block of the per-edge kernels
+};
+
+// An instantiated CUDA graph of a whole mine, replayed by AML_MINE_GRAPH.
+struct MineExec {
+  uint64_t ps_id;     // pattern set it was captured for
+  uint32_t* counts;   // output pointer baked into it
+  int64_t ld;
+  uint64_t tune_gen;  // tuning generation it was captured with
+  cudaGraphExec_t exec;
+  long long n_kernels;  // kernel launches it replays
+};
+
 }  // namespace aml
 
 struct aml_graph {
@@ -119,6 +137,10 @@ struct aml_graph {
   std::map<int32_t, aml::LegCache> legs;  // per window
   cudaStream_t last_stream = nullptr;
   int device = 0;
+  aml::Tuning tune;
+  uint64_t tune_gen = 0;
+  std::vector<aml::MineExec> execs;   // captured mines (AML_MINE_GRAPH)
+  cudaStream_t capture_stream = nullptr;
 };
 
 namespace aml {
@@ -163,6 +185,7 @@ struct Column {
 
 struct aml_pattern_set {
   std::vector<aml::Column> cols;
+  uint64_t id = 0;  // unique per process, keys captured mines
 };
 
 // ---------------------------------------------------------------- helpers

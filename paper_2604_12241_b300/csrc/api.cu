@@ -1,4 +1,5 @@
 // extern "C" entry points: argument checks, error mapping, dispatch.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -125,8 +126,10 @@ aml_status aml_pattern_set_create(const aml_pattern* patterns, int32_t n_pattern
     AML_REQUIRE(out != nullptr, AML_EINVAL, "out is NULL");
     AML_REQUIRE(n_patterns <= MAX_COLS, AML_EUNSUPPORTED, "at most 64 patterns per set");
     std::vector<Column> cols = plan_patterns(patterns, n_patterns);
+    static std::atomic<uint64_t> next_id{1};
     aml_pattern_set* ps = new aml_pattern_set();
     ps->cols = std::move(cols);
+    ps->id = next_id.fetch_add(1);
     *out = ps;
   });
 }
@@ -163,7 +166,10 @@ aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, i
                     uint32_t flags, void* stream) {
   return guarded("aml_mine", [&] {
     AML_REQUIRE(g && ps, AML_EINVAL, "NULL graph or pattern set");
-    AML_REQUIRE((flags & ~AML_MINE_HOST_OUTPUT) == 0, AML_EINVAL, "unknown flag bits");
+    AML_REQUIRE((flags & ~(AML_MINE_HOST_OUTPUT | AML_MINE_GRAPH)) == 0, AML_EINVAL,
+                "unknown flag bits");
+    AML_REQUIRE(!((flags & AML_MINE_GRAPH) && (flags & AML_MINE_HOST_OUTPUT)), AML_EINVAL,
+                "AML_MINE_GRAPH needs a device output");
     const int64_t P = (int64_t)ps->cols.size();
     AML_REQUIRE(ld >= P, AML_EINVAL, "ld must be >= the number of columns");
     AML_REQUIRE(g->E == 0 || counts != nullptr, AML_EINVAL, "counts is NULL");
@@ -176,6 +182,8 @@ aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, i
         AML_CUDA(cudaMemcpy2DAsync(counts, (size_t)ld * 4, dev.p, (size_t)P * 4, (size_t)P * 4,
                                    (size_t)g->E, cudaMemcpyDeviceToHost, s));
       AML_CUDA(cudaStreamSynchronize(s));
+    } else if (flags & AML_MINE_GRAPH) {
+      mine_graph_mode(g, ps, counts, ld, s);
     } else {
       mine_plain(g, ps, counts, ld, s);
     }

@@ -258,9 +258,13 @@ aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts
   }
 }
 
+void drop_captured_mines(aml_graph* g);
+
 void destroy_graph(aml_graph* g) {
   if (!g) return;
   cudaDeviceSynchronize();
+  drop_captured_mines(g);
+  if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
   free_graph(g);
 }
 

@@ -26,7 +26,7 @@ namespace aml {
 
 // Per slot p of one direction: the start lb(p) of its trailing window (so
 // DEG = p - lb(p) + 1) and, when FAN is wanted, the repeat delta above.
-__global__ void __launch_bounds__(256) k_window_slots(const int32_t* __restrict__ ptr,
+__global__ void __launch_bounds__(512) k_window_slots(const int32_t* __restrict__ ptr,
                                                       const int32_t* __restrict__ t,
                                                       const int32_t* __restrict__ eid,
                                                       const int32_t* __restrict__ prev,
@@ -114,7 +114,7 @@ __device__ __forceinline__ int32_t legs_into(const GraphView& g, int32_t b, int3
   return (c1 - c0) - pair_before(g.innbr, g.int_, g.ineid, hs, he, g.dst[b], tb, b, delta);
 }
 
-__global__ void __launch_bounds__(256) k_leg_count(GraphView g, int32_t delta,
+__global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
                                                    int32_t* __restrict__ L) {
   int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a64 >= g.E) return;
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) k_leg_count(GraphView g, int32_t delta,
 }
 
 // legs ending with each edge, by binary search (when no legs are emitted)
-__global__ void __launch_bounds__(256) k_gs_into(GraphView g, int32_t delta,
+__global__ void __launch_bounds__(512) k_gs_into(GraphView g, int32_t delta,
                                                  int32_t* __restrict__ gs_in) {
   int64_t b64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b64 >= g.E) return;
@@ -186,10 +186,10 @@ __device__ __forceinline__ void put_leg(const LegSink& S, int64_t pos, int32_t a
 // with records, also counts them into the SG buckets.  Windows of up to 32
 // slots are written by their own lane; longer ones (hub accounts) by the
 // whole warp, 32 slots at a time, with ballots keeping the output order.
-__global__ void __launch_bounds__(256) k_leg_emit(GraphView g, int32_t delta,
+__global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
                                                   const int64_t* __restrict__ off, LegSink S,
                                                   unsigned long long* __restrict__ acc_cyc2,
-                                                  int32_t* __restrict__ gs_in) {
+                                                  int32_t* __restrict__ gs_in, int32_t own_max) {
   const int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) k_leg_emit(GraphView g, int32_t delta,
       ta = g.ts[a];
     }
   }
-  const bool own = q1 - q0 <= 32;
+  const bool own = q1 - q0 <= own_max;
   // lanes with short windows walk them in lock step (one slot per round)
   const int32_t own_len = own ? q1 - q0 : 0;
   int32_t rounds = own_len;
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ re
 //     (the degree-ordered intersection of Sec. 6).
 
 // B1 of every edge a = u0 -> u1: slots of in(u0) after a with t <= t_a + delta
-__global__ void __launch_bounds__(256) k_close_range(GraphView g, int32_t delta,
+__global__ void __launch_bounds__(512) k_close_range(GraphView g, int32_t delta,
                                                      int2* __restrict__ rng) {
   int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a64 >= g.E) return;
@@ -449,7 +449,6 @@ __global__ void __launch_bounds__(256) k_close_range(GraphView g, int32_t delta,
   rng[a] = r;
 }
 
-constexpr int32_t CLOSE_SCAN_MAX = 48;  // B1 longer than this: binary search
 
 // Rebuilds the path of frontier element i at level j (j edges):
 // edges[0..j-1] and nodes[0..j] (nodes[0] = u0 = src of the anchor).
@@ -474,13 +473,14 @@ __device__ __forceinline__ void cyc_path(const GraphView& g, const CycFrontier& 
 // is admissible (new node, before the latest closing edge), credits the
 // cycles of length j+1 that close from its end node through B1, and reports
 // the window of later hops its children will take.
-__global__ void __launch_bounds__(256) k_cyc_level(GraphView g, int32_t delta, int K, int j,
+__global__ void __launch_bounds__(512) k_cyc_level(GraphView g, int32_t delta, int K, int j,
                                                    CycFrontier F, int64_t n,
                                                    const int2* __restrict__ close_rng,
                                                    CycleSlots slots,
                                                    unsigned long long* __restrict__ acc,
                                                    int32_t* __restrict__ cnt,
-                                                   int32_t* __restrict__ q0_out) {
+                                                   int32_t* __restrict__ q0_out,
+                                                   int32_t close_scan_max) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const bool has_next = j + 1 <= K - 1;
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(256) k_cyc_level(GraphView g, int32_t delta, i
   if (k <= K && slots.slot[k] >= 0) {
     unsigned long long* col = acc + (int64_t)slots.slot[k] * g.E;
     unsigned long long c = 0;
-    if (cr.y - cr.x <= CLOSE_SCAN_MAX) {
+    if (cr.y - cr.x <= close_scan_max) {
       for (int32_t q = cr.x; q < cr.y; ++q) {
         if (__ldg(g.inbr + q) != w) continue;
         const int32_t cid = __ldg(g.ieid + q);
@@ -537,17 +537,17 @@ __global__ void __launch_bounds__(256) k_cyc_level(GraphView g, int32_t delta, i
 
 // Writes the children (parent, slot) of every element at off[i]...; short
 // windows are written by their own lane, long ones by the whole warp.
-__global__ void __launch_bounds__(256) k_cyc_emit(int64_t n, const int32_t* __restrict__ cnt,
+__global__ void __launch_bounds__(512) k_cyc_emit(int64_t n, const int32_t* __restrict__ cnt,
                                                   const int32_t* __restrict__ q0,
                                                   const int64_t* __restrict__ off,
                                                   int32_t* __restrict__ par,
-                                                  int32_t* __restrict__ slot) {
+                                                  int32_t* __restrict__ slot, int32_t own_max) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int32_t c = i < n ? cnt[i] : 0;
   const int64_t o = c ? off[i] : 0;
   const int32_t b = c ? q0[i] : 0;
-  const bool own = c <= 32;
+  const bool own = c <= own_max;
   if (own)
     for (int32_t k = 0; k < c; ++k) {
       par[o + k] = (int32_t)i;
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(256) k_cyc_emit(int64_t n, const int32_t* __re
 // DEG - repeats (prefix-sum difference), GS = legs starting + legs ending at
 // the edge, SG and CYC from the 64-bit accumulators; saturated to 32 bits.
 
-__global__ void __launch_bounds__(256) k_assemble(AssembleParams P) {
+__global__ void __launch_bounds__(512) k_assemble(AssembleParams P) {
   int64_t e64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const GraphView& g = P.g;
   if (e64 >= g.E) return;

@@ -10,7 +10,6 @@ constexpr int MAX_DELTAS = 16;  // distinct windows per pattern set
 constexpr int MAX_CYCLE = 8;    // longest cycle
 constexpr int SG_CAP = 1024;    // leg records one SG bucket block groups in shared memory
 constexpr int SG_TAB = 2048;    // its hash-table slots (load <= 0.5)
-constexpr int SG_BUCKET_MEAN = 384;  // target records per SG bucket
 constexpr int SG_PART_ITEMS = 4;     // records per thread in k_sg_partition
 constexpr size_t SG_SMEM = (size_t)SG_TAB * (8 + 4 + 4) + (size_t)SG_CAP * (2 + 2);
 
@@ -100,7 +99,7 @@ __global__ void k_window_slots(const int32_t* ptr, const int32_t* t, const int32
 __global__ void k_leg_count(GraphView g, int32_t delta, int32_t* L);
 __global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);
 __global__ void k_leg_emit(GraphView g, int32_t delta, const int64_t* off, LegSink S,
-                           unsigned long long* acc_cyc2, int32_t* gs_in);
+                           unsigned long long* acc_cyc2, int32_t* gs_in, int32_t own_max);
 __global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, const int64_t* boff,
                                uint32_t* cursor, LegRec* out);
 __global__ void k_sg_bucket(const LegRec* rec, const int64_t* boff, int32_t delta,
@@ -108,13 +107,17 @@ __global__ void k_sg_bucket(const LegRec* rec, const int64_t* boff, int32_t delt
 __global__ void k_close_range(GraphView g, int32_t delta, int2* rng);
 __global__ void k_cyc_level(GraphView g, int32_t delta, int K, int j, CycFrontier F, int64_t n,
                             const int2* close_rng, CycleSlots slots, unsigned long long* acc,
-                            int32_t* cnt, int32_t* q0_out);
+                            int32_t* cnt, int32_t* q0_out, int32_t close_scan_max);
 __global__ void k_cyc_emit(int64_t n, const int32_t* cnt, const int32_t* q0, const int64_t* off,
-                           int32_t* par, int32_t* slot);
+                           int32_t* par, int32_t* slot, int32_t own_max);
 __global__ void k_assemble(AssembleParams P);
 
 // Host pipeline: enqueue a full mine of `ps` on `g` into device `counts`.
 void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
                 cudaStream_t s);
+// The same, replayed from a CUDA graph captured on first use.
+void mine_graph_mode(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
+                     cudaStream_t s);
+void drop_captured_mines(aml_graph* g);
 
 }  // namespace aml

@@ -97,7 +97,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   std::vector<DBuf<int64_t>> keep64;
   keep32.reserve(8 * wins.size());
   keep64.reserve(wins.size());
-  const int B = 256;
+  const Tuning tn = g->tune;
+  const int B = tn.block;
   const int64_t Ev = g->Ev;
   for (size_t w = 0; w < wins.size(); ++w) {
     WindowPlan& wp = wins[w];
@@ -164,7 +165,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     DBuf<uint32_t> hist;
     int64_t nb = 1;
     if (wp.sg) {
-      while (nb * SG_BUCKET_MEAN < nl) nb <<= 1;
+      while (nb * tn.sg_bucket_mean < nl) nb <<= 1;
       while ((1ll << S.bits) < nb) ++S.bits;
       rec = DBuf<LegRec>((size_t)nl, s);
       hist = DBuf<uint32_t>((size_t)nb + 1, s);
@@ -175,7 +176,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     unsigned long long* acc2 =
         wp.cyc.slot[2] >= 0 ? acc.p + (int64_t)wp.cyc.slot[2] * E : nullptr;
     AML_LAUNCH("k_leg_emit", s,
-               k_leg_emit<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, off, S, acc2, gs_in));
+               k_leg_emit<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, off, S, acc2, gs_in,
+                                                       tn.own_max));
     // 3. scatter-gather: bucket the leg records, group each bucket by (s, d)
     if (wp.sg && nl > 1) {
       DBuf<int64_t> boff((size_t)nb + 1, s);
@@ -183,7 +185,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       AML_CUDA(cudaMemsetAsync(hist.p, 0, (size_t)nb * 4, s));  // now the bucket cursors
       DBuf<LegRec> part((size_t)nl, s);
       AML_LAUNCH("k_sg_partition", s,
-                 k_sg_partition<<<grid_for(nl, B * SG_PART_ITEMS), B, 0, s>>>(
+                 k_sg_partition<<<grid_for(nl, 256 * SG_PART_ITEMS), 256, 0, s>>>(
                      rec.p, nl, S.bits, boff.p, hist.p, part.p));
       static bool smem_set[64] = {false};  // per device
       if (g->device >= 64 || !smem_set[g->device]) {
@@ -192,7 +194,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
         if (g->device < 64) smem_set[g->device] = true;
       }
       AML_LAUNCH("k_sg_bucket", s,
-                 k_sg_bucket<<<(unsigned)nb, B, SG_SMEM, s>>>(part.p, boff.p, wp.delta,
+                 k_sg_bucket<<<(unsigned)nb, 256, SG_SMEM, s>>>(part.p, boff.p, wp.delta,
                                                               acc.p + (int64_t)wp.sg_slot * E));
     }
     // 4. cycles of length >= 3, level by level from the legs
@@ -212,7 +214,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
         DBuf<int32_t> cnt(has_next ? n + 1 : 0, s), q0(has_next ? n : 0, s);
         AML_LAUNCH("k_cyc_level", s,
                    k_cyc_level<<<grid_for(n, B), B, 0, s>>>(gv, wp.delta, wp.K, j, F, n, crng.p,
-                                                            wp.cyc, acc.p, cnt.p, q0.p));
+                                                            wp.cyc, acc.p, cnt.p, q0.p,
+                                                            tn.close_scan_max));
         if (!has_next) break;
         DBuf<int64_t> foff(n + 1, s);
         AML_CUDA(cudaMemsetAsync(cnt.p + n, 0, sizeof(int32_t), s));
@@ -228,7 +231,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
         front.emplace_back((size_t)nn, s);
         int32_t* slot = front.back().p;
         AML_LAUNCH("k_cyc_emit", s,
-                   k_cyc_emit<<<grid_for(n, B), B, 0, s>>>(n, cnt.p, q0.p, foff.p, par, slot));
+                   k_cyc_emit<<<grid_for(n, B), B, 0, s>>>(n, cnt.p, q0.p, foff.p, par, slot,
+                                                           tn.own_max));
         F.par[j + 1] = par;
         F.slot[j + 1] = slot;
         n = nn;

@@ -66,6 +66,8 @@ LaunchScope::~LaunchScope() {
 
 long long launch_count() { return g_launches.load(); }
 
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 }  // namespace aml
 
 using namespace aml;

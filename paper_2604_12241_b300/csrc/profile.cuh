@@ -20,6 +20,7 @@ class LaunchScope {
 };
 
 long long launch_count();
+void add_launches(long long n);  // kernels launched through a replayed CUDA graph
 
 }  // namespace aml
 

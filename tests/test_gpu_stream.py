@@ -1,0 +1,88 @@
+"""Streaming recount: after every append, every resident row equals the
+count of a full mine of everything appended so far (bit-exact), for random
+batch sizes, ties across batch boundaries, and eviction; bad batches are
+refused without changing the stream."""
+import numpy as np
+import pytest
+
+import aml_synth
+import paper_2604_12241_b300 as aml
+from paper_2604_12241_b300 import patterns as P
+
+pytestmark = pytest.mark.gpu
+
+
+def full_mine(g, n, pats):
+    graph = aml.Graph(g.src[:n], g.dst[:n], g.ts[:n], g.n_nodes, assume_sorted=True)
+    out = aml.mine(graph, aml.PatternSet(pats)).cpu().numpy().view(np.uint32)
+    graph.close()
+    return out
+
+
+@pytest.mark.parametrize("window_days", [8, 30])
+def test_stream_equals_full_mine(window_days):
+    import torch
+    assert torch.cuda.is_available()
+    g = aml_synth.workload("tiny-10k")
+    pats = P.standard(P.DAY) + P.standard(P.WEEK)
+    ps = aml.PatternSet(pats)
+    st = aml.Stream(ps, g.n_nodes, resident_window=window_days * P.DAY, mem_budget=1 << 30)
+    rng = np.random.default_rng(window_days)
+    pos, n_checks = 0, 0
+    E = g.n_edges
+    while pos < E:
+        n = int(min(E - pos, rng.integers(1, 6000)))
+        info = st.append(g.src[pos:pos + n], g.dst[pos:pos + n], g.ts[pos:pos + n],
+                         g.amount[pos:pos + n])
+        assert info["first_row"] == pos and info["n_rows"] == n
+        pos += n
+        if rng.random() < 0.3 or pos == E:
+            want = full_mine(g, pos, pats)
+            r0, nr = info["resident_first_row"], info["resident_rows"]
+            np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
+            n_checks += 1
+    assert n_checks >= 3
+    inf = st.info()
+    if window_days == 8:
+        assert inf["resident_first_row"] > 0          # eviction happened
+        with pytest.raises(aml.AmlError):
+            st.read(0, 1)
+    assert inf["final_end_row"] <= inf["resident_first_row"] + inf["resident_rows"]
+    st.close()
+
+
+def test_stream_refuses_bad_batches():
+    g = aml_synth.workload("tiny-10k")
+    pats = P.standard(P.DAY)
+    ps = aml.PatternSet(pats)
+    st = aml.Stream(ps, g.n_nodes, resident_window=2 * P.DAY, mem_budget=1 << 28)
+    st.append(g.src[:1000], g.dst[:1000], g.ts[:1000])
+    # late: starts before the latest appended timestamp
+    with pytest.raises(aml.AmlError) as ei:
+        st.append(g.src[:10], g.dst[:10], g.ts[:10])
+    assert ei.value.name == "AML_ELATE"
+    # decreasing inside the batch
+    ts = g.ts[1000:1010].copy()
+    ts[5] = ts[9] + 1
+    with pytest.raises(aml.AmlError) as ei:
+        st.append(g.src[1000:1010], g.dst[1000:1010], ts)
+    assert ei.value.name == "AML_EUNSORTED"
+    # an id outside [0, n_nodes)
+    bad = g.dst[1000:1010].copy()
+    bad[3] = g.n_nodes
+    with pytest.raises(aml.AmlError) as ei:
+        st.append(g.src[1000:1010], bad, g.ts[1000:1010])
+    assert ei.value.name == "AML_EINVAL"
+    # over the budget: refused, and the stream is unchanged afterwards
+    cap = st.info()["capacity_rows"]
+    big = 1000 + cap + 10
+    if big <= g.n_edges:
+        with pytest.raises(aml.AmlError) as ei:
+            st.append(g.src[1000:big], g.dst[1000:big], g.ts[1000:big])
+        assert ei.value.name == "AML_EADMIT"
+    st.append(g.src[1000:3000], g.dst[1000:3000], g.ts[1000:3000])
+    want = full_mine(g, 3000, pats)
+    inf = st.info()
+    r0, nr = inf["resident_first_row"], inf["resident_rows"]
+    np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
+    st.close()
