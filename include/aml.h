@@ -213,6 +213,13 @@ aml_status aml_pattern_set_column(const aml_pattern_set* ps, int32_t col,
                                    /* captures the kernel sequence on a private  */
                                    /* stream; later calls are one graph launch.  */
                                    /* Device output only.                        */
+#define AML_MINE_PERSISTENT 0x4u   /* cycles by one persistent launch over       */
+                                   /* anchor edges in warp / thread queues       */
+                                   /* ordered longest-first by a degree estimate */
+#define AML_MINE_LEARNED 0x8u      /* as PERSISTENT, but the queues and their    */
+                                   /* order come from the cost model trained by  */
+                                   /* aml_cost_train for that window (degree     */
+                                   /* estimate when no model exists)            */
 
 /* Count every pattern of `ps` for every edge of `g`.
  *   counts : uint32, row-major, row e = input edge e, column j = pattern j;
@@ -251,6 +258,54 @@ aml_status aml_graph_set_tuning(aml_graph* g, const aml_tuning* t);
  * evaluation plan from neighbourhood size and selectivity (Sec. 6). */
 aml_status aml_autotune(aml_graph* g, const aml_pattern_set* ps, int32_t repeats, void* stream,
                         aml_tuning* best, float* best_ms);
+
+/* ------------------------------------------------------------- cost model */
+
+/* Learned cost binning of the persistent cycle search.  A perceptron
+ * 16 -> 64 -> 64 -> 1 (ReLU; bf16 weights, fp32 accumulation; inference on
+ * tensor cores) maps 16 cheap features of an anchor edge (first-window size,
+ * closing-range size, degrees of its nodes, second-hop degree samples, ...)
+ * to log(1 + clock64 cycles) of that anchor's search.  aml_cost_train samples
+ * up to max_samples anchors of the widest window with cycle columns,
+ * measures their cost with the persistent kernel run one anchor per lane
+ * (clock64 probe), trains the model on 80% of them with the library's own
+ * forward/backward and Adam kernels (minibatch 4096, lr 2e-3) for `epochs`
+ * epochs, and evaluates it on the other 20% against the degree estimate
+ * (the first-window size).  The model is kept with the graph and used by
+ * AML_MINE_LEARNED.  Synchronizes `stream`.  The paper's optimizer chooses
+ * evaluation plans from neighbourhood size and selectivity (Sec. 6); this is
+ * a learned replacement for that estimate, not a feature of the paper. */
+typedef struct aml_cost_report {
+  int32_t delta;               /* window the model serves                        */
+  int32_t epochs;
+  int64_t n_items;             /* anchors with cycle work in that window          */
+  int64_t n_train, n_test;
+  float final_train_mse;       /* normalized-label MSE of the last epoch          */
+  float test_log_mae;          /* mean |predicted - measured| of log(1 + cycles)  */
+  float test_spearman;         /* rank correlation, model vs measured cost        */
+  float degree_spearman;       /* rank correlation, first-window size vs cost     */
+  float warp_threshold_cycles; /* predicted cost at which an anchor gets a warp   */
+  float probe_ms;              /* time of the clock64 probe                       */
+  float total_ms;              /* whole call                                      */
+} aml_cost_report;
+
+aml_status aml_cost_train(aml_graph* g, const aml_pattern_set* ps, int64_t max_samples,
+                          int32_t epochs, uint64_t seed, void* stream, aml_cost_report* report);
+
+/* Building blocks of the cost model, on host arrays (for verification):
+ * params = 5313 floats (W1[64][16], b1[64], W2[64][64], b2[64], w3[64], b3),
+ * x = n x 16 normalized features, y = n labels.  aml_mlp_loss_grad returns
+ * the mean squared error and its gradient (forward with weights rounded to
+ * bf16, fp32 arithmetic).  aml_mlp_adam_step applies one Adam step (bias
+ * corrected, step >= 1) to params, m and v in place.  aml_mlp_predict runs
+ * the tensor-core inference on raw features; norm = 16 means, 16 inverse
+ * standard deviations, label mean, label std. */
+aml_status aml_mlp_loss_grad(const float* params, const float* x, const float* y, int64_t n,
+                             float* grad, float* loss);
+aml_status aml_mlp_adam_step(float* params, const float* grad, float* m, float* v, int32_t step,
+                             float lr, float beta1, float beta2, float eps);
+aml_status aml_mlp_predict(const float* params, const float* norm, const float* feat, int64_t n,
+                           float* out);
 
 /* Wait for the graph's enqueued work and report device-side errors
  * (AML_ETIMEOUT, AML_EINTERNAL) recorded by its kernels since the last call. */

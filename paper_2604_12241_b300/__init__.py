@@ -17,11 +17,13 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import patterns  # noqa: F401
-from ._lib import (ASSUME_SORTED, MINE_GRAPH, MINE_HOST_OUTPUT, PTR_DEVICE, PTR_HOST,  # noqa: F401
-                   AmlError, aml_column_info, aml_graph_info, aml_stream_batch,
-                   aml_stream_info, aml_tuning, check, lib, make_patterns)
+from ._lib import (ASSUME_SORTED, MINE_GRAPH, MINE_HOST_OUTPUT, MINE_LEARNED,  # noqa: F401
+                   MINE_PERSISTENT, PTR_DEVICE, PTR_HOST, AmlError, aml_column_info,
+                   aml_cost_report, aml_graph_info, aml_stream_batch, aml_stream_info,
+                   aml_tuning, check, lib, make_patterns)
 
-__all__ = ["Graph", "PatternSet", "Stream", "mine", "autotune", "AmlError", "patterns"]
+__all__ = ["Graph", "PatternSet", "Stream", "mine", "autotune", "cost_train", "AmlError",
+           "patterns"]
 
 
 def _stream_handle(stream) -> int:
@@ -153,8 +155,20 @@ def autotune(graph: Graph, pset: PatternSet, repeats: int = 3, stream=None):
     return {f: getattr(t, f) for f, _ in t._fields_}, ms.value
 
 
+def cost_train(graph: Graph, pset: PatternSet, max_samples: int = 1_000_000, epochs: int = 20,
+               seed: int = 1, stream=None) -> dict:
+    """Train the cycle-search cost model on the GPU (aml_cost_train)."""
+    r = aml_cost_report()
+    check(lib().aml_cost_train(graph.handle, pset.handle, int(max_samples), int(epochs), int(seed),
+                               _stream_handle(stream), ctypes.byref(r)))
+    return {f: getattr(r, f) for f, _ in r._fields_}
+
+
+MODES = {"plain": 0, "persistent": MINE_PERSISTENT, "learned": MINE_LEARNED}
+
+
 def mine(graph: Graph, pset: PatternSet, out=None, stream=None, host_output: bool = False,
-         use_graph: bool = False):
+         use_graph: bool = False, mode: str = "plain"):
     """Per-edge counts, [E, P] (aml_mine).
 
     Device mode (default) returns / fills a torch int32 CUDA tensor holding
@@ -162,7 +176,11 @@ def mine(graph: Graph, pset: PatternSet, out=None, stream=None, host_output: boo
     ``.view(np.uint32)`` to read them unsigned).  ``host_output=True``
     returns a numpy uint32 array copied back by the library.  ``use_graph``
     replays the whole mine as one captured CUDA graph (AML_MINE_GRAPH).
+    ``mode``: "plain" (level-by-level cycle search), "persistent" (one
+    persistent launch, degree-binned queues) or "learned" (queues from the
+    trained cost model).  All modes give identical counts.
     """
+    flags = MODES[mode]
     P = pset.n_cols
     E = graph.n_edges
     s = _stream_handle(stream)
@@ -171,7 +189,8 @@ def mine(graph: Graph, pset: PatternSet, out=None, stream=None, host_output: boo
         ptr, dev = _ptr(arr)
         if dev:
             raise ValueError("host_output needs a host array")
-        check(lib().aml_mine(graph.handle, pset.handle, ptr, arr.shape[1], MINE_HOST_OUTPUT, s))
+        check(lib().aml_mine(graph.handle, pset.handle, ptr, arr.shape[1],
+                             MINE_HOST_OUTPUT | flags, s))
         return arr
     import torch
     if out is None:
@@ -180,7 +199,7 @@ def mine(graph: Graph, pset: PatternSet, out=None, stream=None, host_output: boo
     if not dev:
         raise ValueError("device mode needs a CUDA tensor")
     check(lib().aml_mine(graph.handle, pset.handle, ptr, out.shape[1],
-                         MINE_GRAPH if use_graph else 0, s))
+                         (MINE_GRAPH if use_graph else 0) | flags, s))
     return out
 
 

@@ -21,6 +21,8 @@ STATUS = {0: "AML_OK", 1: "AML_EINVAL", 2: "AML_ENOMEM", 3: "AML_ECUDA", 4: "AML
 PTR_HOST, PTR_DEVICE, ASSUME_SORTED = 0x0, 0x1, 0x2
 MINE_HOST_OUTPUT = 0x1
 MINE_GRAPH = 0x2
+MINE_PERSISTENT = 0x4
+MINE_LEARNED = 0x8
 
 
 class AmlError(RuntimeError):
@@ -72,6 +74,15 @@ class aml_stream_info(ctypes.Structure):
                 ("delta_max", ctypes.c_int32)]
 
 
+class aml_cost_report(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_int32), ("epochs", ctypes.c_int32), ("n_items", ctypes.c_int64),
+                ("n_train", ctypes.c_int64), ("n_test", ctypes.c_int64),
+                ("final_train_mse", ctypes.c_float), ("test_log_mae", ctypes.c_float),
+                ("test_spearman", ctypes.c_float), ("degree_spearman", ctypes.c_float),
+                ("warp_threshold_cycles", ctypes.c_float), ("probe_ms", ctypes.c_float),
+                ("total_ms", ctypes.c_float)]
+
+
 class aml_column_info(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int32), ("k", ctypes.c_int32), ("delta", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("name", ctypes.c_char * 32)]
@@ -108,6 +119,12 @@ _SIGS = {
     "aml_stream_get_info": (ctypes.c_int32, [_VP, ctypes.POINTER(aml_stream_info)]),
     "aml_stream_close": (ctypes.c_int32, [_VP]),
     "aml_fan_noalloc": (ctypes.c_int32, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
+    "aml_cost_train": (ctypes.c_int32, [_VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                        _VP, ctypes.POINTER(aml_cost_report)]),
+    "aml_mlp_loss_grad": (ctypes.c_int32, [_VP, _VP, _VP, ctypes.c_int64, _VP, _VP]),
+    "aml_mlp_adam_step": (ctypes.c_int32, [_VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_float,
+                                           ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    "aml_mlp_predict": (ctypes.c_int32, [_VP, _VP, _VP, ctypes.c_int64, _VP]),
     "aml_launch_count": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_int64)]),
     "aml_profile_enable": (ctypes.c_int32, [ctypes.c_int32]),
     "aml_profile_read": (ctypes.c_int32, [ctypes.POINTER(aml_kernel_stat), ctypes.c_int32,

@@ -109,8 +109,19 @@ struct Tuning {
   int32_t block = 256;           // threads per block of the per-edge kernels
 };
 
+// Trained cost model of one window (see mlp.cu / cost.cu).
+struct CostModel {
+  int32_t delta = -1;
+  float* params = nullptr;   // device fp32 parameters, owned by the graph
+  float mean[16] = {0};      // feature normalization
+  float inv_std[16] = {0};
+  float y_mean = 0.f, y_std = 1.f;  // label (log1p cycles) normalization
+  float warp_threshold = 0.f;       // predicted cycles at which an item gets a warp
+};
+
 // An instantiated CUDA graph of a whole mine, replayed by AML_MINE_GRAPH.
 struct MineExec {
+  uint32_t flags;     // mining mode it was captured with
   uint64_t ps_id;     // pattern set it was captured for
   uint32_t* counts;   // output pointer baked into it
   int64_t ld;
@@ -140,6 +151,7 @@ struct aml_graph {
   aml::Tuning tune;
   uint64_t tune_gen = 0;
   std::vector<aml::MineExec> execs;   // captured mines (AML_MINE_GRAPH)
+  std::vector<aml::CostModel> cost_models;  // per window (aml_cost_train)
   cudaStream_t capture_stream = nullptr;
 };
 

@@ -166,8 +166,10 @@ aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, i
                     uint32_t flags, void* stream) {
   return guarded("aml_mine", [&] {
     AML_REQUIRE(g && ps, AML_EINVAL, "NULL graph or pattern set");
-    AML_REQUIRE((flags & ~(AML_MINE_HOST_OUTPUT | AML_MINE_GRAPH)) == 0, AML_EINVAL,
-                "unknown flag bits");
+    AML_REQUIRE((flags & ~(AML_MINE_HOST_OUTPUT | AML_MINE_GRAPH | AML_MINE_PERSISTENT |
+                           AML_MINE_LEARNED)) == 0,
+                AML_EINVAL, "unknown flag bits");
+    const uint32_t mode = flags & (AML_MINE_PERSISTENT | AML_MINE_LEARNED);
     AML_REQUIRE(!((flags & AML_MINE_GRAPH) && (flags & AML_MINE_HOST_OUTPUT)), AML_EINVAL,
                 "AML_MINE_GRAPH needs a device output");
     const int64_t P = (int64_t)ps->cols.size();
@@ -177,15 +179,15 @@ aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, i
     g->last_stream = s;
     if (flags & AML_MINE_HOST_OUTPUT) {
       DBuf<uint32_t> dev((size_t)(g->E * P), s);
-      mine_plain(g, ps, dev.p, P, s);
+      mine_plain(g, ps, dev.p, P, s, mode);
       if (g->E)
         AML_CUDA(cudaMemcpy2DAsync(counts, (size_t)ld * 4, dev.p, (size_t)P * 4, (size_t)P * 4,
                                    (size_t)g->E, cudaMemcpyDeviceToHost, s));
       AML_CUDA(cudaStreamSynchronize(s));
     } else if (flags & AML_MINE_GRAPH) {
-      mine_graph_mode(g, ps, counts, ld, s);
+      mine_graph_mode(g, ps, counts, ld, s, mode);
     } else {
-      mine_plain(g, ps, counts, ld, s);
+      mine_plain(g, ps, counts, ld, s, mode);
     }
   });
 }

@@ -23,9 +23,10 @@ void drop_captured_mines(aml_graph* g) {
 }
 
 void mine_graph_mode(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
-                     cudaStream_t s) {
+                     cudaStream_t s, uint32_t mode) {
   for (const MineExec& m : g->execs) {
-    if (m.ps_id == ps->id && m.counts == counts && m.ld == ld && m.tune_gen == g->tune_gen) {
+    if (m.flags == mode && m.ps_id == ps->id && m.counts == counts && m.ld == ld &&
+        m.tune_gen == g->tune_gen) {
       AML_CUDA(cudaGraphLaunch(m.exec, s));
       add_launches(m.n_kernels);
       return;
@@ -33,7 +34,7 @@ void mine_graph_mode(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, 
   }
   // this call's result comes from a plain mine, which also learns every
   // buffer size the capture needs (so the captured sequence never waits)
-  mine_plain(g, ps, counts, ld, s);
+  mine_plain(g, ps, counts, ld, s, mode);
   if (!g->capture_stream)
     AML_CUDA(cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking));
   cudaStream_t cs = g->capture_stream;
@@ -41,7 +42,7 @@ void mine_graph_mode(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, 
   const long long before = launch_count();
   AML_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   try {
-    mine_plain(g, ps, counts, ld, cs);
+    mine_plain(g, ps, counts, ld, cs, mode);
   } catch (...) {
     cudaStreamEndCapture(cs, &graph);
     if (graph) cudaGraphDestroy(graph);
@@ -52,7 +53,7 @@ void mine_graph_mode(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, 
   cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   AML_CUDA(e);
-  g->execs.push_back(MineExec{ps->id, counts, ld, g->tune_gen, exec,
+  g->execs.push_back(MineExec{mode, ps->id, counts, ld, g->tune_gen, exec,
                               (long long)(launch_count() - before)});
 }
 

@@ -113,11 +113,16 @@ __global__ void k_cyc_emit(int64_t n, const int32_t* cnt, const int32_t* q0, con
 __global__ void k_assemble(AssembleParams P);
 
 // Host pipeline: enqueue a full mine of `ps` on `g` into device `counts`.
+// mode: AML_MINE_PERSISTENT / AML_MINE_LEARNED select the cycle search.
 void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
-                cudaStream_t s);
+                cudaStream_t s, uint32_t mode = 0);
 // The same, replayed from a CUDA graph captured on first use.
 void mine_graph_mode(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
-                     cudaStream_t s);
+                     cudaStream_t s, uint32_t mode = 0);
+// Cycle search of one window by the persistent, cost-binned kernel (cost.cu).
+void cycles_persistent(aml_graph* g, const GraphView& gv, int32_t delta, int K,
+                       const CycleSlots& slots, unsigned long long* acc, bool learned,
+                       cudaStream_t s);
 void drop_captured_mines(aml_graph* g);
 
 }  // namespace aml

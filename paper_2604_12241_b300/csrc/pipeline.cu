@@ -36,7 +36,8 @@ struct WindowPlan {
 }  // namespace
 
 void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
-                cudaStream_t s) {
+                cudaStream_t s, uint32_t mode) {
+  const bool persistent = (mode & (AML_MINE_PERSISTENT | AML_MINE_LEARNED)) != 0;
   const int64_t E = g->E;
   const int ncols = (int)ps->cols.size();
   AML_REQUIRE(ncols <= MAX_COLS, AML_EUNSUPPORTED, "too many columns in one pattern set");
@@ -155,7 +156,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     if (gs_in) AML_CUDA(cudaMemsetAsync(gs_in, 0, (size_t)E * 4, s));
     LegSink S{nullptr, nullptr, nullptr, nullptr, 0};
     DBuf<int32_t> la, lb;
-    if (wp.K >= 3) {  // the cycle search starts from the (a, b) pairs
+    if (wp.K >= 3 && !persistent) {  // the level-by-level search starts from (a, b) pairs
       la = DBuf<int32_t>((size_t)nl, s);
       lb = DBuf<int32_t>((size_t)nl, s);
       S.la = la.p;
@@ -197,8 +198,10 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
                  k_sg_bucket<<<(unsigned)nb, 256, SG_SMEM, s>>>(part.p, boff.p, wp.delta,
                                                               acc.p + (int64_t)wp.sg_slot * E));
     }
-    // 4. cycles of length >= 3, level by level from the legs
-    if (wp.K >= 3 && nl > 0) {
+    // 4. cycles of length >= 3: one persistent cost-binned launch ...
+    if (wp.K >= 3 && persistent) {
+      cycles_persistent(g, gv, wp.delta, wp.K, wp.cyc, acc.p, (mode & AML_MINE_LEARNED) != 0, s);
+    } else if (wp.K >= 3 && nl > 0) {  // ... or level by level from the legs
       DBuf<int2> crng(E, s);
       AML_LAUNCH("k_close_range", s,
                  k_close_range<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, crng.p));

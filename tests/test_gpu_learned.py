@@ -1,0 +1,134 @@
+"""Cost model and persistent cycle search.
+
+* The GPU perceptron's loss and gradient equal the float64 reference (same
+  bf16-rounded weights) within fp32 accumulation error; its Adam step equals
+  the reference step; its tensor-core inference equals the reference forward
+  with bf16 activations.
+* Persistent (degree-binned) and learned-binned mining give exactly the
+  plain path's counts, with and without CUDA-graph replay.
+* Training reports sane numbers and the trained model is used.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import aml_synth
+import mlp_ref as R
+import paper_2604_12241_b300 as aml
+from paper_2604_12241_b300 import _lib, patterns as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def test_mlp_gradient_matches_fp64_reference():
+    rng = np.random.default_rng(3)
+    for n in (1, 63, 300, 5000):
+        p = _f32(R.random_params(rng))
+        x = _f32(rng.normal(0, 1, (n, R.IN)))
+        y = _f32(rng.normal(0, 1, n))
+        grad = np.zeros(R.NPARAM, np.float32)
+        loss = np.zeros(1, np.float32)
+        rc = _lib.lib().aml_mlp_loss_grad(p.ctypes.data, x.ctypes.data, y.ctypes.data, n,
+                                          grad.ctypes.data, loss.ctypes.data)
+        assert rc == 0, _lib.lib().aml_last_error()
+        want_loss, want = R.loss_grad(R.weights_bf16(p), x, y)
+        assert abs(loss[0] - want_loss) <= 1e-4 * max(1.0, want_loss)
+        scale = np.abs(want).max()
+        np.testing.assert_allclose(grad, want, rtol=0, atol=2e-4 * scale)
+
+
+def test_adam_step_matches_reference():
+    rng = np.random.default_rng(4)
+    p = _f32(rng.normal(0, 1, R.NPARAM))
+    g = _f32(rng.normal(0, 1e-2, R.NPARAM))
+    m = _f32(rng.normal(0, 1e-3, R.NPARAM))
+    v = _f32(np.abs(rng.normal(0, 1e-4, R.NPARAM)))
+    # the kernel receives float32 hyperparameters: the reference uses the same
+    # values, in float64 arithmetic
+    lr, b1, b2, eps = (float(np.float32(x)) for x in (2e-3, 0.9, 0.999, 1e-8))
+    want_p, want_m, want_v = R.adam(p.astype(np.float64), g.astype(np.float64),
+                                    m.astype(np.float64), v.astype(np.float64), 7, lr, b1, b2, eps)
+    rc = _lib.lib().aml_mlp_adam_step(p.ctypes.data, g.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                      7, ctypes.c_float(2e-3), ctypes.c_float(0.9),
+                                      ctypes.c_float(0.999), ctypes.c_float(1e-8))
+    assert rc == 0
+    np.testing.assert_allclose(m, want_m, rtol=1e-5, atol=1e-9)
+    np.testing.assert_allclose(v, want_v, rtol=1e-5, atol=1e-12)
+    np.testing.assert_allclose(p, want_p, rtol=1e-5, atol=1e-6)
+
+
+def test_tensor_core_inference_matches_reference():
+    rng = np.random.default_rng(5)
+    p = _f32(R.random_params(rng))
+    n = 1000 + 13                                   # not a multiple of the 16-item tile
+    feat = _f32(rng.normal(2, 3, (n, R.IN)))
+    mean = rng.normal(2, 0.1, R.IN)
+    inv_std = 1 / rng.uniform(2, 4, R.IN)
+    norm = _f32(np.concatenate([mean, inv_std, [0.7, 1.9]]))
+    out = np.zeros(n, np.float32)
+    rc = _lib.lib().aml_mlp_predict(p.ctypes.data, norm.ctypes.data, feat.ctypes.data, n,
+                                    out.ctypes.data)
+    assert rc == 0, _lib.lib().aml_last_error()
+    xn = ((feat - mean) * inv_std).astype(np.float32)
+    want, _ = R.forward(R.weights_bf16(p), xn, act_bf16=True)
+    want = want * 1.9 + 0.7
+    np.testing.assert_allclose(out, want, rtol=0, atol=1e-2 * np.abs(want).max())
+
+
+@pytest.fixture(scope="module")
+def week_graph():
+    g = aml_synth.workload("tiny-10k")
+    graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes, assume_sorted=True)
+    ps = aml.PatternSet(P.standard(P.DAY) + P.standard(P.WEEK) + [P.cycle(k, P.WEEK)
+                                                                  for k in (6, 7)])
+    ref = aml.mine(graph, ps).cpu().numpy()
+    return g, graph, ps, ref
+
+
+def test_persistent_and_learned_modes_are_exact(week_graph):
+    g, graph, ps, ref = week_graph
+    for mode in ("persistent", "learned"):          # learned without a model: degree fallback
+        np.testing.assert_array_equal(aml.mine(graph, ps, mode=mode).cpu().numpy(), ref)
+        np.testing.assert_array_equal(aml.mine(graph, ps, mode=mode, use_graph=True)
+                                      .cpu().numpy(), ref)
+    before = graph.tuning()
+    try:
+        for own in (0, 1, 4096):                    # everything warp / thread queued
+            graph.set_tuning(own_max=own)
+            np.testing.assert_array_equal(aml.mine(graph, ps, mode="persistent").cpu().numpy(),
+                                          ref)
+    finally:
+        graph.set_tuning(**before)
+
+
+def test_cost_training_and_learned_mining(week_graph):
+    g, graph, ps, ref = week_graph
+    rep = aml.cost_train(graph, ps, max_samples=20_000, epochs=8, seed=3)
+    assert rep["delta"] == P.WEEK and rep["n_items"] > 100
+    assert rep["n_train"] + rep["n_test"] == min(rep["n_items"], 20_000)
+    assert np.isfinite(rep["final_train_mse"]) and rep["final_train_mse"] < 1.5
+    assert -1 <= rep["test_spearman"] <= 1 and -1 <= rep["degree_spearman"] <= 1
+    assert rep["test_log_mae"] >= 0
+    np.testing.assert_array_equal(aml.mine(graph, ps, mode="learned").cpu().numpy(), ref)
+    np.testing.assert_array_equal(aml.mine(graph, ps, mode="learned", use_graph=True)
+                                  .cpu().numpy(), ref)
+
+
+def test_persistent_on_multi_tile_random_graph():
+    import oracle
+    g = aml_synth.tiny_random(300, 20_000, 3_000, 901, self_loops=True)
+    cols = [("cyc", 3, 60), ("cyc", 4, 60), ("cyc", 5, 80), ("cyc", 6, 80), ("sg", 40),
+            ("gs", 40)]
+    want = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes).count_all(cols)
+    graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes)
+    ps = aml.PatternSet(P.from_oracle_columns(cols))
+    got = aml.mine(graph, ps, mode="persistent").cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(got, want)
+    aml.cost_train(graph, ps, max_samples=5_000, epochs=3)
+    got = aml.mine(graph, ps, mode="learned").cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(got, want)
