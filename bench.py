@@ -58,6 +58,10 @@ def parse():
                     help="graph: the whole mine replayed as one captured CUDA graph")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
+    ap.add_argument("--cycle-mode", choices=["auto", "plain", "persistent", "learned"],
+                    default="auto", help="cycle search; auto = fastest measured")
+    ap.add_argument("--cost-samples", type=int, default=1_000_000)
+    ap.add_argument("--cost-epochs", type=int, default=20)
     ap.add_argument("--stream-batches", type=int, default=30)
     return ap.parse_args()
 
@@ -364,12 +368,40 @@ def run_ours(args, ws, rank, local):
         best, best_ms = aml.autotune(graph, ps, repeats=3)
         tune_info = {"tuning": best, "best_ms": best_ms, "seconds": time.perf_counter() - t0}
     use_graph = args.mode == "graph"
+    # cost model for learned binning, then each cycle-search mode timed
+    cost_report = None
+    if args.cycle_mode in ("auto", "learned"):
+        cost_report = aml.cost_train(graph, ps, max_samples=args.cost_samples,
+                                     epochs=args.cost_epochs, seed=20260003)
+
+    def mode_ms(mode, reps=10):
+        for _ in range(2):
+            aml.mine(graph, ps, out=out, use_graph=use_graph, mode=mode)
+        torch.cuda.synchronize()
+        ts_ = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            aml.mine(graph, ps, out=out, stream=stream, use_graph=use_graph, mode=mode)
+            b.record(stream)
+            b.synchronize()
+            ts_.append(a.elapsed_time(b))
+        return float(np.median(ts_))
+
+    modes = {}
+    if args.cycle_mode == "auto":
+        for m in ("plain", "persistent", "learned"):
+            modes[m] = mode_ms(m)
+        cycle_mode = min(modes, key=modes.get)
+    else:
+        cycle_mode = args.cycle_mode
     for _ in range(max(3, args.warmup)):
-        aml.mine(graph, ps, out=out, use_graph=use_graph)
+        aml.mine(graph, ps, out=out, use_graph=use_graph, mode=cycle_mode)
     torch.cuda.synchronize()
     graph.sync()
 
-    def timed(steps, graph_mode, profile):
+    def timed(steps, graph_mode, profile, mode):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
         dist.barrier()
@@ -382,7 +414,7 @@ def run_ours(args, ws, rank, local):
         for k in range(steps):
             flush.zero_()                     # evict L2 between steps (not timed)
             ev[k][0].record(stream)
-            aml.mine(graph, ps, out=out, stream=stream, use_graph=graph_mode)
+            aml.mine(graph, ps, out=out, stream=stream, use_graph=graph_mode, mode=mode)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
@@ -398,13 +430,13 @@ def run_ours(args, ws, rank, local):
     # headline: the chosen mode, clocks sampled during the timed region
     clocks = ClockSampler(local)
     clocks.start()
-    dev_ms, wall, launches, _ = timed(args.steps, use_graph, False)
+    dev_ms, wall, launches, _ = timed(args.steps, use_graph, False, cycle_mode)
     clk = clocks.stop()
     dev_ms_max = dist.max(dev_ms)
-    # per-kernel CUDA-event times come from a plain-mode pass (events cannot be
-    # recorded between the kernels of a replayed graph)
+    # per-kernel CUDA-event times come from a pass without graph replay
+    # (events cannot be recorded between the kernels of a replayed graph)
     prof_steps = max(3, min(args.steps, 10))
-    plain_ms, _, plain_launches, prof = timed(prof_steps, False, True)
+    plain_ms, _, plain_launches, prof = timed(prof_steps, False, True, cycle_mode)
 
     # end to end through the public API: pinned host inputs -> graph build ->
     # mine -> counts copied back to pinned host memory, every step
@@ -464,13 +496,15 @@ def run_ours(args, ws, rank, local):
                 "impl": "ours",
                 "config": {"workload": WORKLOAD_TEXT[args.workload], "n_edges": E,
                            "n_nodes": g.n_nodes, "columns": Pn, "mode": args.mode,
-                           "autotune": tune_info,
+                           "autotune": tune_info, "cycle_mode": cycle_mode,
+                           "cycle_modes_ms": modes or None,
                            "scale": args.scale,
                            "l2": "flushed between steps (256 MB write, untimed)",
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "wall_s_timed_loop": wall},
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clk,
                 "plain_ms_per_step": plain_ms / prof_steps,
+                "cost_model": cost_report,
                 "plain_gpu_launches_per_step": plain_launches / prof_steps,
                 "kernels": kernels}
         if ws == 1 and not args.no_cpu_baseline:

@@ -114,12 +114,50 @@ __device__ __forceinline__ int32_t legs_into(const GraphView& g, int32_t b, int3
   return (c1 - c0) - pair_before(g.innbr, g.int_, g.ineid, hs, he, g.dst[b], tb, b, delta);
 }
 
+// slot bound of the legs of a that can start a cycle: its window slots that
+// precede the latest edge of its closing range (q0 when that range is empty)
+__device__ __forceinline__ int32_t cycle_bound(const GraphView& g, const int2* crng, int32_t a,
+                                               int32_t q0, int32_t q1) {
+  const int2 cr = crng[a];
+  if (cr.x >= cr.y) return q0;
+  const int32_t t_cl = __ldg(g.it + cr.y - 1), id_cl = __ldg(g.ieid + cr.y - 1);
+  return after_edge(g.ot, g.oeid, q0, q1, t_cl, id_cl - 1);  // first slot not before it
+}
+
+// L[a]: legs from a.  With crng: L2[a] = those that can start a cycle
+// (slots before the cycle bound, minus returns to src(a) among them).
 __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
-                                                   int32_t* __restrict__ L) {
+                                                   int32_t* __restrict__ L,
+                                                   const int2* __restrict__ crng,
+                                                   int32_t* __restrict__ L2) {
   int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a64 >= g.E) return;
   int32_t a = (int32_t)a64;
-  L[a] = (g.src[a] == g.dst[a]) ? 0 : legs_from(g, a, delta);
+  if (g.src[a] == g.dst[a]) {
+    L[a] = 0;
+    if (L2) L2[a] = 0;
+    return;
+  }
+  L[a] = legs_from(g, a, delta);
+  if (!L2) return;
+  int32_t q0, q1;
+  leg_window(g, a, q0, q1, delta);
+  const int32_t qc = cycle_bound(g, crng, a, q0, q1);
+  int32_t back = 0;
+  if (qc > q0) {  // returns h -> src(a) among the slots [q0, qc)
+    const int32_t h = g.dst[a], x = g.src[a];
+    const int32_t hs = g.optr[h], he = g.optr[h + 1];
+    const int32_t r0 = lower_nbr(g.onnbr, hs, he, x);
+    if (r0 < he && __ldg(g.onnbr + r0) == x) {
+      const int32_t r1 = lower_nbr(g.onnbr, r0, he, x + 1);
+      const int2 cr = crng[a];
+      const int32_t b0 = after_edge(g.ont, g.oneid, r0, r1, g.ts[a], a);
+      const int32_t b1 = after_edge(g.ont, g.oneid, b0, r1, __ldg(g.it + cr.y - 1),
+                                    __ldg(g.ieid + cr.y - 1) - 1);
+      back = b1 - b0;
+    }
+  }
+  L2[a] = (qc - q0) - back;
 }
 
 // legs ending with each edge, by binary search (when no legs are emitted)
@@ -163,10 +201,6 @@ __device__ __forceinline__ void count_bucket(uint32_t* hist, uint32_t bkt, bool 
 __device__ __forceinline__ void put_leg(const LegSink& S, int64_t pos, int32_t a, int32_t b,
                                         int32_t x, int32_t h, int32_t y, int32_t ta, int32_t tb,
                                         int64_t n_nodes) {
-  if (S.la) {
-    S.la[pos] = a;
-    S.lb[pos] = b;
-  }
   if (S.rec) {
     LegRec r;
     r.key = (uint64_t)x * (uint64_t)n_nodes + (uint64_t)y;
@@ -204,6 +238,14 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
       ta = g.ts[a];
     }
   }
+  // legs before the cycle bound can start a cycle: they go to la/lb at
+  // off2[a] + their rank among a's legs
+  int32_t qc = q0;
+  int64_t o2 = 0;
+  if (S.la && q1 > q0) {
+    qc = cycle_bound(g, S.crng, a, q0, q1);
+    o2 = S.off2[a] - o;
+  }
   const bool own = q1 - q0 <= own_max;
   // lanes with short windows walk them in lock step (one slot per round)
   const int32_t own_len = own ? q1 - q0 : 0;
@@ -217,13 +259,18 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
     const int32_t y = in ? __ldg(g.onbr + q) : x;
     const int32_t b = in ? __ldg(g.oeid + q) : 0;
     const bool leg = in && y != x;
+    const int32_t tb = in ? __ldg(g.ot + q) : 0;
     if (leg) {
-      put_leg(S, o, a, b, x, h, y, ta, __ldg(g.ot + q), g.N);
+      put_leg(S, o, a, b, x, h, y, ta, tb, g.N);
       if (gs_in) atomicAdd(gs_in + b, 1);
       ++o;
     } else if (in && acc_cyc2) {
       atomicAdd(acc_cyc2 + b, 1ull);
       ++n_cyc2;
+    }
+    if (S.la && leg && q < qc) {
+      S.la[o2 + o - 1] = a;
+      S.lb[o2 + o - 1] = b;
     }
     if (S.hist)
       count_bucket(S.hist, leg ? bucket_of((uint64_t)x * (uint64_t)g.N + (uint64_t)y, S.bits) : 0u,
@@ -238,6 +285,8 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
     const int32_t hx = __shfl_sync(0xffffffffu, x, src);
     const int32_t hh = __shfl_sync(0xffffffffu, h, src);
     const int32_t hta = __shfl_sync(0xffffffffu, ta, src);
+    const int32_t hqc = __shfl_sync(0xffffffffu, qc, src);
+    const int64_t ho2 = __shfl_sync(0xffffffffu, o2, src);
     const int32_t hq1 = __shfl_sync(0xffffffffu, q1, src);
     int32_t base = __shfl_sync(0xffffffffu, q0, src);
     int64_t ho = __shfl_sync(0xffffffffu, o, src);
@@ -249,12 +298,18 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
       const int32_t b = in ? __ldg(g.oeid + q) : 0;
       const bool leg = in && y != hx;
       const unsigned m = __ballot_sync(0xffffffffu, leg);
+      const int32_t tb = in ? __ldg(g.ot + q) : 0;
       if (leg) {
-        put_leg(S, ho + __popc(m & lt), ha, b, hx, hh, y, hta, __ldg(g.ot + q), g.N);
+        put_leg(S, ho + __popc(m & lt), ha, b, hx, hh, y, hta, tb, g.N);
         if (gs_in) atomicAdd(gs_in + b, 1);
       } else if (in && acc_cyc2) {
         atomicAdd(acc_cyc2 + b, 1ull);
         ++hc2;
+      }
+      if (S.la && leg && q < hqc) {
+        const int64_t pos = ho2 + ho + __popc(m & lt);
+        S.la[pos] = ha;
+        S.lb[pos] = b;
       }
       if (S.hist)
         count_bucket(S.hist,

@@ -72,8 +72,10 @@ struct LegRec {
 // Where k_leg_emit writes the legs: (a, b) arrays for the cycle search
 // and/or records + bucket histogram for the SG grouping (null = not wanted).
 struct LegSink {
-  int32_t* la;
-  int32_t* lb;
+  int32_t* la;      // legs that can start a cycle (closing range not empty and the
+  int32_t* lb;      // second edge before its last closing edge), compacted
+  const int64_t* off2;  // first cycle leg of each edge (scan of k_leg_count's L2)
+  const int2* crng;     // closing ranges (needed with la)
   LegRec* rec;
   uint32_t* hist;
   int bits;  // log2 of the number of SG buckets
@@ -96,7 +98,8 @@ struct CycFrontier {
 __global__ void k_window_slots(const int32_t* ptr, const int32_t* t, const int32_t* eid,
                                const int32_t* prev, const int32_t* next, const int32_t* row_of,
                                int64_t Ev, int32_t delta, int32_t* lb, int32_t* D);
-__global__ void k_leg_count(GraphView g, int32_t delta, int32_t* L);
+__global__ void k_leg_count(GraphView g, int32_t delta, int32_t* L, const int2* crng,
+                            int32_t* L2);
 __global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);
 __global__ void k_leg_emit(GraphView g, int32_t delta, const int64_t* off, LegSink S,
                            unsigned long long* acc_cyc2, int32_t* gs_in, int32_t own_max);

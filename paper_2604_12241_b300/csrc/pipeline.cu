@@ -125,14 +125,33 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       (dir == 0 ? P.S_out : P.S_in)[w] = D;
     }
     if (!wp.needs_off()) continue;
-    // 2. legs
+    // 2. legs (and, for the level-by-level cycle search, the legs that can
+    // start a cycle: those of anchors with a closing range, before its end)
+    const bool level_cycles = wp.K >= 3 && !persistent;
+    DBuf<int2> crng;
+    DBuf<int32_t> L2;
+    DBuf<int64_t> off2;
+    if (level_cycles) {
+      crng = DBuf<int2>((size_t)E, s);
+      AML_LAUNCH("k_close_range", s,
+                 k_close_range<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, crng.p));
+      L2 = DBuf<int32_t>((size_t)E + 1, s);
+      off2 = DBuf<int64_t>((size_t)E + 1, s);
+    }
     DBuf<int32_t> L(E + 1, s);
-    AML_LAUNCH("k_leg_count", s, k_leg_count<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, L.p));
+    AML_LAUNCH("k_leg_count", s,
+               k_leg_count<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, L.p,
+                                                        level_cycles ? crng.p : nullptr,
+                                                        level_cycles ? L2.p : nullptr));
     AML_CUDA(cudaMemsetAsync(L.p + E, 0, sizeof(int32_t), s));
     keep64.emplace_back((size_t)(E + 1), s);
     int64_t* off = keep64.back().p;
     scan_i32_to_i64(L.p, off, E + 1, s);
     P.off[w] = off;
+    if (level_cycles) {
+      AML_CUDA(cudaMemsetAsync(L2.p + E, 0, sizeof(int32_t), s));
+      scan_i32_to_i64(L2.p, off2.p, E + 1, s);
+    }
     int32_t* gs_in = nullptr;
     if (wp.gs) {
       keep32.emplace_back((size_t)E, s);
@@ -154,13 +173,20 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     }
     const int64_t nl = lc.n_legs;
     if (gs_in) AML_CUDA(cudaMemsetAsync(gs_in, 0, (size_t)E * 4, s));
-    LegSink S{nullptr, nullptr, nullptr, nullptr, 0};
+    LegSink S{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
     DBuf<int32_t> la, lb;
-    if (wp.K >= 3 && !persistent) {  // the level-by-level search starts from (a, b) pairs
-      la = DBuf<int32_t>((size_t)nl, s);
-      lb = DBuf<int32_t>((size_t)nl, s);
+    if (level_cycles) {
+      int64_t& n2 = lc.n_front[2];
+      if (n2 < 0) {
+        AML_CUDA(cudaMemcpyAsync(&n2, off2.p + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        AML_CUDA(cudaStreamSynchronize(s));
+      }
+      la = DBuf<int32_t>((size_t)std::max<int64_t>(n2, 1), s);
+      lb = DBuf<int32_t>((size_t)std::max<int64_t>(n2, 1), s);
       S.la = la.p;
       S.lb = lb.p;
+      S.off2 = off2.p;
+      S.crng = crng.p;
     }
     DBuf<LegRec> rec;
     DBuf<uint32_t> hist;
@@ -201,17 +227,15 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     // 4. cycles of length >= 3: one persistent cost-binned launch ...
     if (wp.K >= 3 && persistent) {
       cycles_persistent(g, gv, wp.delta, wp.K, wp.cyc, acc.p, (mode & AML_MINE_LEARNED) != 0, s);
-    } else if (wp.K >= 3 && nl > 0) {  // ... or level by level from the legs
-      DBuf<int2> crng(E, s);
-      AML_LAUNCH("k_close_range", s,
-                 k_close_range<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, crng.p));
+    } else if (level_cycles) {  // ... or level by level from the legs
+      const int64_t n2 = lc.n_front[2];
       CycFrontier F;
       std::memset(&F, 0, sizeof(F));
       F.la = la.p;
       F.lb = lb.p;
       std::vector<DBuf<int32_t>> front;  // par/slot of levels >= 3
       front.reserve(2 * MAX_CYCLE);
-      int64_t n = nl;
+      int64_t n = n2;
       for (int j = 2; j <= wp.K - 1 && n > 0; ++j) {
         const bool has_next = j + 1 <= wp.K - 1;
         DBuf<int32_t> cnt(has_next ? n + 1 : 0, s), q0(has_next ? n : 0, s);
