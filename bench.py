@@ -330,7 +330,7 @@ def run_stream(args, rank) -> dict:
             "load_50pct": {"p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99),
                            "edges_per_s": sum(sizes2) / (sum(lat) if lat else 1),
                            "arrivals": "Poisson, batches/s = %.2f" % lam},
-            "method": "exact: window W within 7d of the batch mined with and without the batch"}
+            "method": "exact: one mine of the window W within 7d of the batch plus the batch, counting only instances whose latest edge is new"}
 
 
 # --------------------------------------------------------------------- ours

@@ -195,7 +195,9 @@ __device__ __forceinline__ void cyc_close(const CycPersist& A, int L, const int3
     const int32_t r0 = lower_nbr(g.innbr, in_s, in_e, w);
     if (r0 < in_e && __ldg(g.innbr + r0) == w) {
       const int32_t r1 = lower_nbr(g.innbr, r0, in_e, w + 1);
-      const int32_t b0 = after_edge(g.int_, g.ineid, r0, r1, tl, last);
+      int32_t b0 = after_edge(g.int_, g.ineid, r0, r1, tl, last);
+      // delta counting: only new closing edges (the scan branch's range already is)
+      if (g.new_from > 0) b0 = after_edge(g.int_, g.ineid, b0, r1, g.t_new, g.new_from - 1);
       const int32_t b1 = upper_t(g.int_, b0, r1, (int64_t)g.ts[edges[0]] + A.delta);
       for (int32_t q = b0; q < b1; ++q) atomicAdd(col + __ldg(g.ineid + q), 1ull);
       c = (unsigned long long)(b1 - b0);

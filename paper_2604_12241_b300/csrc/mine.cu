@@ -126,19 +126,39 @@ __device__ __forceinline__ int32_t cycle_bound(const GraphView& g, const int2* c
 
 // L[a]: legs from a.  With crng: L2[a] = those that can start a cycle
 // (slots before the cycle bound, minus returns to src(a) among them).
+// With L_new (delta counting): L_new[a] = legs from a whose second edge is new.
 __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
                                                    int32_t* __restrict__ L,
                                                    const int2* __restrict__ crng,
-                                                   int32_t* __restrict__ L2) {
+                                                   int32_t* __restrict__ L2,
+                                                   int32_t* __restrict__ L_new) {
   int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a64 >= g.E) return;
   int32_t a = (int32_t)a64;
   if (g.src[a] == g.dst[a]) {
     L[a] = 0;
     if (L2) L2[a] = 0;
+    if (L_new) L_new[a] = 0;
     return;
   }
   L[a] = legs_from(g, a, delta);
+  if (L_new) {
+    int32_t q0, q1;
+    leg_window(g, a, q0, q1, delta);
+    const int32_t qn = after_edge(g.ot, g.oeid, q0, q1, g.t_new, g.new_from - 1);
+    int32_t back = 0;
+    const int32_t h = g.dst[a], x = g.src[a];
+    const int32_t hs = g.optr[h], he = g.optr[h + 1];
+    const int32_t r0 = lower_nbr(g.onnbr, hs, he, x);
+    if (qn < q1 && r0 < he && __ldg(g.onnbr + r0) == x) {
+      const int32_t r1 = lower_nbr(g.onnbr, r0, he, x + 1);
+      const int32_t b0 = after_edge(g.ont, g.oneid, r0, r1, g.ts[a], a);
+      const int32_t bn = after_edge(g.ont, g.oneid, b0, r1, g.t_new, g.new_from - 1);
+      const int32_t b1 = upper_t(g.ont, bn, r1, (int64_t)g.ts[a] + delta);
+      back = b1 - bn;
+    }
+    L_new[a] = (q1 - qn) - back;
+  }
   if (!L2) return;
   int32_t q0, q1;
   leg_window(g, a, q0, q1, delta);
@@ -166,7 +186,8 @@ __global__ void __launch_bounds__(512) k_gs_into(GraphView g, int32_t delta,
   int64_t b64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b64 >= g.E) return;
   int32_t b = (int32_t)b64;
-  gs_in[b] = (g.src[b] == g.dst[b]) ? 0 : legs_into(g, b, delta);
+  // delta counting: a leg (a, b) is new iff b is new
+  gs_in[b] = (g.src[b] == g.dst[b] || b < g.new_from) ? 0 : legs_into(g, b, delta);
 }
 
 // --------------------------------------------------------- leg emission
@@ -262,9 +283,9 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
     const int32_t tb = in ? __ldg(g.ot + q) : 0;
     if (leg) {
       put_leg(S, o, a, b, x, h, y, ta, tb, g.N);
-      if (gs_in) atomicAdd(gs_in + b, 1);
+      if (gs_in && b >= g.new_from) atomicAdd(gs_in + b, 1);
       ++o;
-    } else if (in && acc_cyc2) {
+    } else if (in && acc_cyc2 && b >= g.new_from) {
       atomicAdd(acc_cyc2 + b, 1ull);
       ++n_cyc2;
     }
@@ -301,8 +322,8 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
       const int32_t tb = in ? __ldg(g.ot + q) : 0;
       if (leg) {
         put_leg(S, ho + __popc(m & lt), ha, b, hx, hh, y, hta, tb, g.N);
-        if (gs_in) atomicAdd(gs_in + b, 1);
-      } else if (in && acc_cyc2) {
+        if (gs_in && b >= g.new_from) atomicAdd(gs_in + b, 1);
+      } else if (in && acc_cyc2 && b >= g.new_from) {
         atomicAdd(acc_cyc2 + b, 1ull);
         ++hc2;
       }
@@ -378,7 +399,8 @@ __device__ __forceinline__ bool sg_partner(const LegRec& r, const LegRec& o, int
 __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ rec,
                                                    const int64_t* __restrict__ boff,
                                                    int32_t delta,
-                                                   unsigned long long* __restrict__ acc) {
+                                                   unsigned long long* __restrict__ acc,
+                                                   int32_t new_from) {
   extern __shared__ __align__(16) unsigned char sg_smem[];
   unsigned long long* s_key = reinterpret_cast<unsigned long long*>(sg_smem);
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_key + SG_TAB);
@@ -396,7 +418,7 @@ __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ re
       unsigned long long c = 0;
       for (int j = 0; j < n; ++j) {
         const LegRec o = R[j];
-        if (o.key == r.key && sg_partner(r, o, delta)) ++c;
+        if (o.key == r.key && sg_partner(r, o, delta) && max(r.b, o.b) >= new_from) ++c;
       }
       sg_credit(acc, r, c);
     }
@@ -464,8 +486,11 @@ __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ re
     const LegRec r = R[i];
     const uint32_t gs = s_end[h] - c;
     unsigned long long k = 0;
-    for (uint32_t j = gs; j < gs + c; ++j)
-      if (sg_partner(r, R[s_idx[j]], delta)) ++k;
+    for (uint32_t j = gs; j < gs + c; ++j) {
+      const LegRec& o = R[s_idx[j]];
+      // delta counting: the pair's latest edge is one of its two gather edges
+      if (sg_partner(r, o, delta) && max(r.b, o.b) >= new_from) ++k;
+    }
     sg_credit(acc, r, k);
   }
 }
@@ -500,6 +525,8 @@ __global__ void __launch_bounds__(512) k_close_range(GraphView g, int32_t delta,
     int32_t ta = g.ts[a];
     r.x = after_edge(g.it, g.ieid, is, ie, ta, a);
     r.y = upper_t(g.it, r.x, ie, (int64_t)ta + delta);
+    // delta counting: a cycle is new iff its closing (latest) edge is new
+    if (g.new_from > 0) r.x = after_edge(g.it, g.ieid, r.x, r.y, g.t_new, g.new_from - 1);
   }
   rng[a] = r;
 }
@@ -572,7 +599,9 @@ __global__ void __launch_bounds__(512) k_cyc_level(GraphView g, int32_t delta, i
       const int32_t r0 = lower_nbr(g.innbr, in_s, in_e, w);
       if (r0 < in_e && __ldg(g.innbr + r0) == w) {
         const int32_t r1 = lower_nbr(g.innbr, r0, in_e, w + 1);
-        const int32_t b0 = after_edge(g.int_, g.ineid, r0, r1, tl, last);
+        int32_t b0 = after_edge(g.int_, g.ineid, r0, r1, tl, last);
+        // delta counting: only new closing edges (the scan branch's range already is)
+        if (g.new_from > 0) b0 = after_edge(g.int_, g.ineid, b0, r1, g.t_new, g.new_from - 1);
         const int32_t b1 = upper_t(g.int_, b0, r1, (int64_t)g.ts[edges[0]] + delta);
         for (int32_t q = b0; q < b1; ++q) atomicAdd(col + __ldg(g.ineid + q), 1ull);
         c = (unsigned long long)(b1 - b0);
@@ -664,9 +693,12 @@ __global__ void __launch_bounds__(512) k_assemble(AssembleParams P) {
         val = (uint64_t)(pi - P.lb_in[w][pi] + 1 - (S[pi] - (is > 0 ? S[is - 1] : 0)));
         break;
       }
-      case AML_FAM_GS:
-        val = (uint64_t)(P.off[w][e + 1] - P.off[w][e]) + (uint64_t)P.gs_in[w][e];
+      case AML_FAM_GS: {
+        const int32_t from =
+            P.gs_from[w] ? P.gs_from[w][e] : (int32_t)(P.off[w][e + 1] - P.off[w][e]);
+        val = (uint64_t)from + (uint64_t)P.gs_in[w][e];
         break;
+      }
       default:  // accumulated families
         val = P.acc[(int64_t)cd.acc_slot * g.E + e];
         break;

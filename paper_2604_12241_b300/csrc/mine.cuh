@@ -17,6 +17,11 @@ constexpr size_t SG_SMEM = (size_t)SG_TAB * (8 + 4 + 4) + (size_t)SG_CAP * (2 + 
 struct GraphView {
   int64_t E;
   int32_t N;
+  // Delta counting: when new_from > 0, only instances whose latest edge has
+  // id >= new_from are counted (edges new_from.. are the latest in (t, id)
+  // order, the first of them at time t_new).  0 counts every instance.
+  int32_t new_from;
+  int32_t t_new;
   const int32_t *src, *dst, *ts;
   const int32_t *optr, *onbr, *ot, *oeid, *oprev, *onext, *onnbr, *ont, *oneid, *opos;
   const int32_t *iptr, *inbr, *it, *ieid, *iprev, *inext, *innbr, *int_, *ineid, *ipos;
@@ -26,6 +31,8 @@ inline GraphView view_of(const aml_graph* g) {
   GraphView v;
   v.E = g->E;
   v.N = g->N;
+  v.new_from = 0;
+  v.t_new = 0;
   v.src = g->src; v.dst = g->dst; v.ts = g->ts;
   v.optr = g->out.ptr; v.onbr = g->out.nbr; v.ot = g->out.t; v.oeid = g->out.eid;
   v.oprev = g->out.prev; v.onext = g->out.next; v.onnbr = g->out.nnbr; v.ont = g->out.nt;
@@ -53,6 +60,7 @@ struct AssembleParams {
   const int32_t* S_out[MAX_DELTAS];   // repeat prefix sums per out-slot (FAN)
   const int32_t* S_in[MAX_DELTAS];
   const int64_t* off[MAX_DELTAS];     // leg offsets per edge (GS gather side)
+  const int32_t* gs_from[MAX_DELTAS]; // delta counting: legs from each edge that are new
   const int32_t* gs_in[MAX_DELTAS];   // legs ending with each edge (GS scatter side)
   const unsigned long long* acc;
   uint32_t* counts;
@@ -99,14 +107,14 @@ __global__ void k_window_slots(const int32_t* ptr, const int32_t* t, const int32
                                const int32_t* prev, const int32_t* next, const int32_t* row_of,
                                int64_t Ev, int32_t delta, int32_t* lb, int32_t* D);
 __global__ void k_leg_count(GraphView g, int32_t delta, int32_t* L, const int2* crng,
-                            int32_t* L2);
+                            int32_t* L2, int32_t* L_new);
 __global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);
 __global__ void k_leg_emit(GraphView g, int32_t delta, const int64_t* off, LegSink S,
                            unsigned long long* acc_cyc2, int32_t* gs_in, int32_t own_max);
 __global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, const int64_t* boff,
                                uint32_t* cursor, LegRec* out);
 __global__ void k_sg_bucket(const LegRec* rec, const int64_t* boff, int32_t delta,
-                            unsigned long long* acc);
+                            unsigned long long* acc, int32_t new_from);
 __global__ void k_close_range(GraphView g, int32_t delta, int2* rng);
 __global__ void k_cyc_level(GraphView g, int32_t delta, int K, int j, CycFrontier F, int64_t n,
                             const int2* close_rng, CycleSlots slots, unsigned long long* acc,
@@ -117,8 +125,9 @@ __global__ void k_assemble(AssembleParams P);
 
 // Host pipeline: enqueue a full mine of `ps` on `g` into device `counts`.
 // mode: AML_MINE_PERSISTENT / AML_MINE_LEARNED select the cycle search.
+// new_from / t_new: delta counting (see GraphView); 0 counts everything.
 void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
-                cudaStream_t s, uint32_t mode = 0);
+                cudaStream_t s, uint32_t mode = 0, int32_t new_from = 0, int32_t t_new = 0);
 // The same, replayed from a CUDA graph captured on first use.
 void mine_graph_mode(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
                      cudaStream_t s, uint32_t mode = 0);

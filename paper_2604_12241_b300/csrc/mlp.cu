@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(256) k_mlp_infer(MlpDevice M, const float* __r
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
     const int hn = nt * 8 + g;
-    w1b[nt][0] = pack_bf16(s_w[MLP_W1 + hn * MLP_IN + 2 * c], s_w[MLP_W1 + hn * MLP_IN + 2 * c + 1]);
+    w1b[nt][0] =
+        pack_bf16(s_w[MLP_W1 + hn * MLP_IN + 2 * c], s_w[MLP_W1 + hn * MLP_IN + 2 * c + 1]);
     w1b[nt][1] = pack_bf16(s_w[MLP_W1 + hn * MLP_IN + 2 * c + 8],
                            s_w[MLP_W1 + hn * MLP_IN + 2 * c + 9]);
   }

@@ -36,13 +36,15 @@ struct WindowPlan {
 }  // namespace
 
 void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
-                cudaStream_t s, uint32_t mode) {
+                cudaStream_t s, uint32_t mode, int32_t new_from, int32_t t_new) {
   const bool persistent = (mode & (AML_MINE_PERSISTENT | AML_MINE_LEARNED)) != 0;
   const int64_t E = g->E;
   const int ncols = (int)ps->cols.size();
   AML_REQUIRE(ncols <= MAX_COLS, AML_EUNSUPPORTED, "too many columns in one pattern set");
   if (E == 0) return;
   GraphView gv = view_of(g);
+  gv.new_from = new_from;
+  gv.t_new = t_new;
 
   // windows and accumulator columns
   std::vector<WindowPlan> wins;
@@ -139,10 +141,16 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       off2 = DBuf<int64_t>((size_t)E + 1, s);
     }
     DBuf<int32_t> L(E + 1, s);
+    int32_t* L_new = nullptr;
+    if (new_from > 0 && wp.gs) {
+      keep32.emplace_back((size_t)E, s);
+      L_new = keep32.back().p;
+      P.gs_from[w] = L_new;
+    }
     AML_LAUNCH("k_leg_count", s,
                k_leg_count<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, L.p,
                                                         level_cycles ? crng.p : nullptr,
-                                                        level_cycles ? L2.p : nullptr));
+                                                        level_cycles ? L2.p : nullptr, L_new));
     AML_CUDA(cudaMemsetAsync(L.p + E, 0, sizeof(int32_t), s));
     keep64.emplace_back((size_t)(E + 1), s);
     int64_t* off = keep64.back().p;
@@ -222,7 +230,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       }
       AML_LAUNCH("k_sg_bucket", s,
                  k_sg_bucket<<<(unsigned)nb, 256, SG_SMEM, s>>>(part.p, boff.p, wp.delta,
-                                                              acc.p + (int64_t)wp.sg_slot * E));
+                                                              acc.p + (int64_t)wp.sg_slot * E,
+                                                              new_from));
     }
     // 4. cycles of length >= 3: one persistent cost-binned launch ...
     if (wp.K >= 3 && persistent) {

@@ -4,15 +4,17 @@
 // pattern instances it participates in"; incremental processing with
 // localized updates instead of full recomputation).
 //
-// Why two mines of a window suffice.  A batch B arrives after every resident
+// Why one mine of a window suffices.  A batch B arrives after every resident
 // edge in the (t, id) order.  Let W be the resident edges with
 // t >= t_min(B) - delta_max.  An instance that contains a batch edge spans at
-// most delta_max, so all its edges lie in W u B; an instance inside W u B
-// that contains no batch edge lies inside W.  Hence, column by column,
-//   instances created by B = mine(W u B) - mine(W),
-// credited to the rows of W (added to their stored counts) and giving the
-// batch rows their counts outright.  Trailing-window columns (DEG, FAN) of
-// old rows never change: later edges are outside their windows.
+// most delta_max, so all its edges lie in W u B; and it contains a batch
+// edge iff its latest edge is one.  So mining W u B while counting only the
+// instances whose latest edge is a batch edge (delta counting: the closing
+// edge of a cycle, the later gather edge of a scatter-gather pair, the second
+// edge of a gather-scatter pair) yields exactly the instances B creates:
+// added to the stored counts of the rows of W, and the full counts of the
+// batch rows.  Trailing-window columns (DEG, FAN) of old rows never change:
+// later edges are outside their windows.
 //
 // Resident rows live in device arrays compacted on demand; rows older than
 // t_now - resident_window are evicted.  resident_window >= delta_max keeps
@@ -57,26 +59,24 @@ struct aml_stream {
 
 namespace aml {
 
-// Per-resident-edge working set of one append: two device graphs of the
-// window (about 90 B/edge each) plus the mine's scratch and its output.
+// Per-resident-edge working set of one append: the device graph of the
+// window (about 90 B/edge) plus the mine's scratch and its output.
 static int64_t ws_per_edge(int P) { return 512 + 16 * (int64_t)P; }
 
-__global__ void k_stream_apply(uint32_t* __restrict__ counts, const uint32_t* __restrict__ with_b,
-                               const uint32_t* __restrict__ without_b, int64_t n_w, int64_t n_b,
-                               int P, uint64_t inst_mask) {
+// delta: the new-instance counts of the window's rows (old rows first)
+__global__ void k_stream_apply(uint32_t* __restrict__ counts, const uint32_t* __restrict__ delta,
+                               int64_t n_w, int64_t n_b, int P, uint64_t inst_mask) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_w + n_b) return;
   uint32_t* row = counts + r * P;
-  const uint32_t* a = with_b + r * P;
+  const uint32_t* a = delta + r * P;
   if (r >= n_w) {  // a batch row: its counts outright
     for (int c = 0; c < P; ++c) row[c] = a[c];
     return;
   }
-  const uint32_t* b = without_b + r * P;
   for (int c = 0; c < P; ++c) {
     if (!((inst_mask >> c) & 1ull)) continue;
-    const int64_t d = (int64_t)a[c] - (int64_t)b[c];
-    const uint64_t v = (uint64_t)row[c] + (uint64_t)(d > 0 ? d : 0);
+    const uint64_t v = (uint64_t)row[c] + (uint64_t)a[c];
     row[c] = v > 0xffffffffull ? 0xffffffffu : (uint32_t)v;
   }
 }
@@ -112,11 +112,14 @@ static void compact(aml_stream* st, cudaStream_t s) {
   st->lo = 0;
 }
 
-static void mine_window(aml_stream* st, int64_t w0, int64_t n, uint32_t* out, cudaStream_t s) {
+// mines rows [w0, w0 + n) counting only instances whose latest edge is at
+// local id >= new_from (the batch, first edge at time t_new)
+static void mine_window(aml_stream* st, int64_t w0, int64_t n, int32_t new_from, int32_t t_new,
+                        uint32_t* out, cudaStream_t s) {
   aml_graph* g = build_graph(st->src + w0, st->dst + w0, st->ts + w0, st->amt + w0, n, st->N,
                              AML_PTR_DEVICE | AML_ASSUME_SORTED, s);
   try {
-    mine_plain(g, &st->ps, out, st->P, s);
+    mine_plain(g, &st->ps, out, st->P, s, 0, new_from, t_new);
     AML_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
     destroy_graph(g);
@@ -240,15 +243,12 @@ aml_status aml_stream_append(aml_stream* st, const int32_t* src, const int32_t* 
     if (amount) AML_CUDA(cudaMemcpyAsync(st->amt + at, amount, n * 4, kind, s));
     else AML_CUDA(cudaMemsetAsync(st->amt + at, 0, n * 4, s));
     std::memcpy(st->hts.data() + at, ht.data(), n * 4);
-    // recount: mine(W u B) and mine(W), apply the difference
-    DBuf<uint32_t> with_b((size_t)(n_w + n) * st->P, s);
-    mine_window(st, w0, n_w + n, with_b.p, s);
-    DBuf<uint32_t> without_b((size_t)std::max<int64_t>(n_w, 1) * st->P, s);
-    if (n_w > 0) mine_window(st, w0, n_w, without_b.p, s);
+    // recount: one delta-counting mine of W u B, added to the window's rows
+    DBuf<uint32_t> delta((size_t)(n_w + n) * st->P, s);
+    mine_window(st, w0, n_w + n, (int32_t)n_w, t_first, delta.p, s);
     AML_LAUNCH("k_stream_apply", s,
                k_stream_apply<<<grid_for(n_w + n, 256), 256, 0, s>>>(
-                   st->counts + w0 * st->P, with_b.p, without_b.p, n_w, n, st->P,
-                   st->inst_mask));
+                   st->counts + w0 * st->P, delta.p, n_w, n, st->P, st->inst_mask));
     AML_CUDA(cudaStreamSynchronize(s));
     st->hi = at + n;
     st->any = true;
