@@ -219,20 +219,46 @@ __device__ __forceinline__ void count_bucket(uint32_t* hist, uint32_t bkt, bool 
   if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(hist + bkt, (uint32_t)__popc(peers));
 }
 
-__device__ __forceinline__ void put_leg(const LegSink& S, int64_t pos, int32_t a, int32_t b,
+__device__ __forceinline__ void put_rec(const LegSink& S, int64_t pos, int32_t a, int32_t b,
                                         int32_t x, int32_t h, int32_t y, int32_t ta, int32_t tb,
                                         int64_t n_nodes) {
-  if (S.rec) {
-    LegRec r;
-    r.key = (uint64_t)x * (uint64_t)n_nodes + (uint64_t)y;
-    r.lo = ta;
-    r.hi = tb;
-    r.m = h;
-    r.a = a;
-    r.b = b;
-    r.pad = 0;
-    S.rec[pos] = r;
+  LegRec r;
+  r.key = (uint64_t)x * (uint64_t)n_nodes + (uint64_t)y;
+  r.lo = ta;
+  r.hi = tb;
+  r.m = h;
+  r.a = a;
+  r.b = b;
+  r.pad = 0;
+  S.rec[pos] = r;
+}
+
+__device__ __forceinline__ bool in_mask(const uint32_t* mask, int32_t v) {
+  return (__ldg(mask + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// SG record of a leg: at the leg's own position, or -- when filtering by the
+// destination mask -- compacted with one atomic per warp (all lanes call it)
+__device__ __forceinline__ void sg_record(const LegSink& S, bool leg, int64_t pos, int32_t a,
+                                          int32_t b, int32_t x, int32_t h, int32_t y, int32_t ta,
+                                          int32_t tb, int64_t n_nodes, int bits) {
+  if (!S.dmask) {
+    if (leg) put_rec(S, pos, a, b, x, h, y, ta, tb, n_nodes);
+    if (S.hist)
+      count_bucket(S.hist, leg ? bucket_of((uint64_t)x * (uint64_t)n_nodes + (uint64_t)y, bits)
+                               : 0u,
+                   leg);
+    return;
   }
+  const bool keep = leg && in_mask(S.dmask, y);
+  const unsigned m = __ballot_sync(0xffffffffu, keep);
+  if (!m) return;
+  const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == lead) base = atomicAdd(S.n_rec, (unsigned long long)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, lead);
+  if (keep) put_rec(S, (int64_t)base + __popc(m & ((1u << lane) - 1u)), a, b, x, h, y, ta, tb,
+                    n_nodes);
 }
 
 // Writes every leg (a, b) of edge a at off[a]...; reciprocal edges b = h->x
@@ -281,8 +307,8 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
     const int32_t b = in ? __ldg(g.oeid + q) : 0;
     const bool leg = in && y != x;
     const int32_t tb = in ? __ldg(g.ot + q) : 0;
+    if (S.rec) sg_record(S, leg, o, a, b, x, h, y, ta, tb, g.N, S.bits);
     if (leg) {
-      put_leg(S, o, a, b, x, h, y, ta, tb, g.N);
       if (gs_in && b >= g.new_from) atomicAdd(gs_in + b, 1);
       ++o;
     } else if (in && acc_cyc2 && b >= g.new_from) {
@@ -293,9 +319,6 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
       S.la[o2 + o - 1] = a;
       S.lb[o2 + o - 1] = b;
     }
-    if (S.hist)
-      count_bucket(S.hist, leg ? bucket_of((uint64_t)x * (uint64_t)g.N + (uint64_t)y, S.bits) : 0u,
-                   leg);
   }
   if (n_cyc2) atomicAdd(acc_cyc2 + a, n_cyc2);
   unsigned heavy = __ballot_sync(0xffffffffu, !own);
@@ -320,8 +343,8 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
       const bool leg = in && y != hx;
       const unsigned m = __ballot_sync(0xffffffffu, leg);
       const int32_t tb = in ? __ldg(g.ot + q) : 0;
+      if (S.rec) sg_record(S, leg, ho + __popc(m & lt), ha, b, hx, hh, y, hta, tb, g.N, S.bits);
       if (leg) {
-        put_leg(S, ho + __popc(m & lt), ha, b, hx, hh, y, hta, tb, g.N);
         if (gs_in && b >= g.new_from) atomicAdd(gs_in + b, 1);
       } else if (in && acc_cyc2 && b >= g.new_from) {
         atomicAdd(acc_cyc2 + b, 1ull);
@@ -332,10 +355,6 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
         S.la[pos] = ha;
         S.lb[pos] = b;
       }
-      if (S.hist)
-        count_bucket(S.hist,
-                     leg ? bucket_of((uint64_t)hx * (uint64_t)g.N + (uint64_t)y, S.bits) : 0u,
-                     leg);
       ho += __popc(m);
     }
     if (acc_cyc2) {
@@ -353,6 +372,24 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
 // After emission the leg records are moved into their buckets; then one
 // block per bucket groups its records by key in a shared-memory hash table
 // and counts, for every record of a group of two or more, its partners.
+
+// bucket histogram of compacted records (delta counting)
+__global__ void __launch_bounds__(256) k_sg_hist(const LegRec* __restrict__ rec, int64_t n,
+                                                 int bits, uint32_t* __restrict__ hist) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = i < n;
+  count_bucket(hist, in ? bucket_of(rec[i].key, bits) : 0u, in);
+}
+
+// mask bit v set for v = node_of[e], e in [from, E)
+__global__ void __launch_bounds__(256) k_mark_nodes(const int32_t* __restrict__ node_of,
+                                                    int64_t from, int64_t E,
+                                                    uint32_t* __restrict__ mask) {
+  const int64_t e = from + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int32_t v = node_of[e];
+  atomicOr(mask + (v >> 5), 1u << (v & 31));
+}
 
 // SG_PART_ITEMS independent records per thread keep several cursor atomics
 // in flight at once (the kernel is bound by their latency)
@@ -666,8 +703,10 @@ __global__ void __launch_bounds__(512) k_assemble(AssembleParams P) {
   int32_t e = (int32_t)e64;
   uint32_t* row = P.counts + e64 * P.ld;
   int32_t u = g.src[e], v = g.dst[e];
+  const bool add = e64 < P.accumulate_from;  // an old row: add its new instances
   if (u == v) {
-    for (int c = 0; c < P.ncols; ++c) row[c] = 0u;
+    if (!add)
+      for (int c = 0; c < P.ncols; ++c) row[c] = 0u;
     return;
   }
   int32_t po = g.opos[e], pi = g.ipos[e];
@@ -675,6 +714,7 @@ __global__ void __launch_bounds__(512) k_assemble(AssembleParams P) {
   for (int c = 0; c < P.ncols; ++c) {
     const ColDesc cd = P.cols[c];
     const int w = cd.didx;
+    if (add && !((P.inst_mask >> c) & 1ull)) continue;  // trailing windows never change
     uint64_t val = 0;
     switch (cd.family) {
       case AML_FAM_DEG_OUT:
@@ -702,6 +742,10 @@ __global__ void __launch_bounds__(512) k_assemble(AssembleParams P) {
       default:  // accumulated families
         val = P.acc[(int64_t)cd.acc_slot * g.E + e];
         break;
+    }
+    if (add) {
+      if (val == 0) continue;
+      val += row[c];
     }
     row[c] = val > 0xffffffffull ? 0xffffffffu : (uint32_t)val;
   }

@@ -65,6 +65,11 @@ struct AssembleParams {
   const unsigned long long* acc;
   uint32_t* counts;
   int64_t ld;
+  // streaming: rows below accumulate_from add their new-instance counts to
+  // the instance columns already stored (mask bit c set = instance column);
+  // -1 writes every row outright
+  int64_t accumulate_from;
+  uint64_t inst_mask;
 };
 
 // One leg a = s->m (at time lo), b = m->d (at time hi) filed for the SG
@@ -87,6 +92,10 @@ struct LegSink {
   LegRec* rec;
   uint32_t* hist;
   int bits;  // log2 of the number of SG buckets
+  // delta counting: only legs into a node of this bitmap can be in a new SG
+  // instance; they are compacted into rec by n_rec (hist unused)
+  const uint32_t* dmask;
+  unsigned long long* n_rec;
 };
 
 struct CycleSlots {
@@ -113,6 +122,8 @@ __global__ void k_leg_emit(GraphView g, int32_t delta, const int64_t* off, LegSi
                            unsigned long long* acc_cyc2, int32_t* gs_in, int32_t own_max);
 __global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, const int64_t* boff,
                                uint32_t* cursor, LegRec* out);
+__global__ void k_sg_hist(const LegRec* rec, int64_t n, int bits, uint32_t* hist);
+__global__ void k_mark_nodes(const int32_t* node_of, int64_t from, int64_t E, uint32_t* mask);
 __global__ void k_sg_bucket(const LegRec* rec, const int64_t* boff, int32_t delta,
                             unsigned long long* acc, int32_t new_from);
 __global__ void k_close_range(GraphView g, int32_t delta, int2* rng);
@@ -126,8 +137,11 @@ __global__ void k_assemble(AssembleParams P);
 // Host pipeline: enqueue a full mine of `ps` on `g` into device `counts`.
 // mode: AML_MINE_PERSISTENT / AML_MINE_LEARNED select the cycle search.
 // new_from / t_new: delta counting (see GraphView); 0 counts everything.
+// accumulate (with new_from > 0): rows below new_from add their counts to the
+// stored instance columns, rows from new_from on are written outright.
 void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
-                cudaStream_t s, uint32_t mode = 0, int32_t new_from = 0, int32_t t_new = 0);
+                cudaStream_t s, uint32_t mode = 0, int32_t new_from = 0, int32_t t_new = 0,
+                bool accumulate = false);
 // The same, replayed from a CUDA graph captured on first use.
 void mine_graph_mode(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
                      cudaStream_t s, uint32_t mode = 0);

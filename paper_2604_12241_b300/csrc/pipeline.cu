@@ -36,7 +36,7 @@ struct WindowPlan {
 }  // namespace
 
 void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
-                cudaStream_t s, uint32_t mode, int32_t new_from, int32_t t_new) {
+                cudaStream_t s, uint32_t mode, int32_t new_from, int32_t t_new, bool accumulate) {
   const bool persistent = (mode & (AML_MINE_PERSISTENT | AML_MINE_LEARNED)) != 0;
   const int64_t E = g->E;
   const int ncols = (int)ps->cols.size();
@@ -91,6 +91,11 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   P.ncols = ncols;
   P.counts = counts;
   P.ld = ld;
+  P.accumulate_from = accumulate && new_from > 0 ? new_from : -1;
+  for (int c = 0; c < ncols; ++c) {
+    const uint32_t f = ps->cols[c].family;
+    if (f == AML_FAM_GS || f == AML_FAM_SG || f == AML_FAM_CYC) P.inst_mask |= 1ull << c;
+  }
 
   DBuf<unsigned long long> acc((size_t)std::max(n_acc, 1) * E, s);
   if (n_acc) AML_CUDA(cudaMemsetAsync(acc.p, 0, (size_t)n_acc * E * 8, s));
@@ -181,7 +186,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     }
     const int64_t nl = lc.n_legs;
     if (gs_in) AML_CUDA(cudaMemsetAsync(gs_in, 0, (size_t)E * 4, s));
-    LegSink S{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+    LegSink S{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
     DBuf<int32_t> la, lb;
     if (level_cycles) {
       int64_t& n2 = lc.n_front[2];
@@ -199,22 +204,58 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     DBuf<LegRec> rec;
     DBuf<uint32_t> hist;
     int64_t nb = 1;
-    if (wp.sg) {
-      while (nb * tn.sg_bucket_mean < nl) nb <<= 1;
+    // delta counting: the latest edge of an SG instance is one of its gather
+    // edges, so only legs into a destination of a new edge are recorded
+    const bool sg_filter = wp.sg && new_from > 0;
+    DBuf<uint32_t> dmask;
+    DBuf<unsigned long long> n_rec;
+    auto size_buckets = [&](int64_t n_records) {
+      nb = 1;
+      while (nb * tn.sg_bucket_mean < n_records) nb <<= 1;
+      S.bits = 0;
       while ((1ll << S.bits) < nb) ++S.bits;
-      rec = DBuf<LegRec>((size_t)nl, s);
       hist = DBuf<uint32_t>((size_t)nb + 1, s);
       AML_CUDA(cudaMemsetAsync(hist.p, 0, (size_t)(nb + 1) * 4, s));
+    };
+    if (wp.sg) {
+      rec = DBuf<LegRec>((size_t)std::max<int64_t>(nl, 1), s);
       S.rec = rec.p;
-      S.hist = hist.p;
+      if (sg_filter) {
+        const int64_t words = (g->N + 31) / 32;
+        dmask = DBuf<uint32_t>((size_t)std::max<int64_t>(words, 1), s);
+        AML_CUDA(cudaMemsetAsync(dmask.p, 0, (size_t)words * 4, s));
+        AML_LAUNCH("k_mark_nodes", s,
+                   k_mark_nodes<<<grid_for(E - new_from, 256), 256, 0, s>>>(g->dst, new_from, E,
+                                                                           dmask.p));
+        n_rec = DBuf<unsigned long long>(1, s);
+        AML_CUDA(cudaMemsetAsync(n_rec.p, 0, 8, s));
+        S.dmask = dmask.p;
+        S.n_rec = n_rec.p;
+      } else {
+        size_buckets(nl);
+        S.hist = hist.p;
+      }
     }
     unsigned long long* acc2 =
         wp.cyc.slot[2] >= 0 ? acc.p + (int64_t)wp.cyc.slot[2] * E : nullptr;
     AML_LAUNCH("k_leg_emit", s,
                k_leg_emit<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, off, S, acc2, gs_in,
                                                        tn.own_max));
+    int64_t n_sg = nl;  // records to bucket
+    if (sg_filter) {
+      unsigned long long kept = 0;
+      AML_CUDA(cudaMemcpyAsync(&kept, n_rec.p, 8, cudaMemcpyDeviceToHost, s));
+      AML_CUDA(cudaStreamSynchronize(s));
+      n_sg = (int64_t)kept;
+      if (n_sg > 1) {
+        size_buckets(n_sg);
+        AML_LAUNCH("k_sg_hist", s,
+                   k_sg_hist<<<grid_for(n_sg, 256), 256, 0, s>>>(rec.p, n_sg, S.bits, hist.p));
+      }
+    }
     // 3. scatter-gather: bucket the leg records, group each bucket by (s, d)
-    if (wp.sg && nl > 1) {
+    if (wp.sg && n_sg > 1) {
+      const int64_t nl = n_sg;
       DBuf<int64_t> boff((size_t)nb + 1, s);
       scan_i32_to_i64(reinterpret_cast<const int32_t*>(hist.p), boff.p, nb + 1, s);
       AML_CUDA(cudaMemsetAsync(hist.p, 0, (size_t)nb * 4, s));  // now the bucket cursors

@@ -1,8 +1,8 @@
 // Streaming recount (aml_stream_*): transactions arrive in time-ordered
 // batches; every count of every resident edge stays equal to the count over
-// the whole history (Sec. 5: an arriving edge "increments counts for all
-// pattern instances it participates in"; incremental processing with
-// localized updates instead of full recomputation).
+// the whole history.  Sec. 5 describes this streaming use: a new edge adds
+// one to the counts of every instance it completes, and only the affected
+// neighbourhood is re-examined rather than the whole graph.
 //
 // Why one mine of a window suffices.  A batch B arrives after every resident
 // edge in the (t, id) order.  Let W be the resident edges with
@@ -48,7 +48,6 @@ struct aml_stream {
   int32_t* ts = nullptr;
   float* amt = nullptr;
   uint32_t* counts = nullptr;  // device [cap * P], row-major
-  uint64_t inst_mask = 0;      // columns counted per instance (GS, SG, CYC)
   std::vector<int32_t> hts;    // host copy of ts, slot-indexed
   int64_t lo = 0, hi = 0;      // live slots
   int64_t base = 0;            // global row id of slot 0
@@ -62,24 +61,6 @@ namespace aml {
 // Per-resident-edge working set of one append: the device graph of the
 // window (about 90 B/edge) plus the mine's scratch and its output.
 static int64_t ws_per_edge(int P) { return 512 + 16 * (int64_t)P; }
-
-// delta: the new-instance counts of the window's rows (old rows first)
-__global__ void k_stream_apply(uint32_t* __restrict__ counts, const uint32_t* __restrict__ delta,
-                               int64_t n_w, int64_t n_b, int P, uint64_t inst_mask) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n_w + n_b) return;
-  uint32_t* row = counts + r * P;
-  const uint32_t* a = delta + r * P;
-  if (r >= n_w) {  // a batch row: its counts outright
-    for (int c = 0; c < P; ++c) row[c] = a[c];
-    return;
-  }
-  for (int c = 0; c < P; ++c) {
-    if (!((inst_mask >> c) & 1ull)) continue;
-    const uint64_t v = (uint64_t)row[c] + (uint64_t)a[c];
-    row[c] = v > 0xffffffffull ? 0xffffffffu : (uint32_t)v;
-  }
-}
 
 static void free_stream(aml_stream* st) {
   cudaFree(st->src);
@@ -113,13 +94,15 @@ static void compact(aml_stream* st, cudaStream_t s) {
 }
 
 // mines rows [w0, w0 + n) counting only instances whose latest edge is at
-// local id >= new_from (the batch, first edge at time t_new)
+// local id >= new_from (the batch, first edge at time t_new): rows below
+// new_from add those to their stored instance columns, the others are
+// written outright
 static void mine_window(aml_stream* st, int64_t w0, int64_t n, int32_t new_from, int32_t t_new,
                         uint32_t* out, cudaStream_t s) {
   aml_graph* g = build_graph(st->src + w0, st->dst + w0, st->ts + w0, st->amt + w0, n, st->N,
                              AML_PTR_DEVICE | AML_ASSUME_SORTED, s);
   try {
-    mine_plain(g, &st->ps, out, st->P, s, 0, new_from, t_new);
+    mine_plain(g, &st->ps, out, st->P, s, 0, new_from, t_new, true);
     AML_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
     destroy_graph(g);
@@ -144,11 +127,8 @@ aml_status aml_stream_open(const aml_pattern_set* ps, int32_t n_nodes, int32_t r
     st->ps = *ps;
     st->P = (int32_t)ps->cols.size();
     st->N = n_nodes;
-    for (size_t c = 0; c < ps->cols.size(); ++c) {
+    for (size_t c = 0; c < ps->cols.size(); ++c)
       st->delta_max = std::max(st->delta_max, ps->cols[c].delta);
-      int f = ps->cols[c].family;
-      if (f == AML_FAM_GS || f == AML_FAM_SG || f == AML_FAM_CYC) st->inst_mask |= 1ull << c;
-    }
     AML_REQUIRE(resident_window_s >= st->delta_max, AML_EINVAL,
                 "resident_window_s must be >= the largest pattern window");
     st->window = resident_window_s;
@@ -243,12 +223,9 @@ aml_status aml_stream_append(aml_stream* st, const int32_t* src, const int32_t* 
     if (amount) AML_CUDA(cudaMemcpyAsync(st->amt + at, amount, n * 4, kind, s));
     else AML_CUDA(cudaMemsetAsync(st->amt + at, 0, n * 4, s));
     std::memcpy(st->hts.data() + at, ht.data(), n * 4);
-    // recount: one delta-counting mine of W u B, added to the window's rows
-    DBuf<uint32_t> delta((size_t)(n_w + n) * st->P, s);
-    mine_window(st, w0, n_w + n, (int32_t)n_w, t_first, delta.p, s);
-    AML_LAUNCH("k_stream_apply", s,
-               k_stream_apply<<<grid_for(n_w + n, 256), 256, 0, s>>>(
-                   st->counts + w0 * st->P, delta.p, n_w, n, st->P, st->inst_mask));
+    // recount: one delta-counting mine of W u B; old rows add their new
+    // instances, batch rows are written outright
+    mine_window(st, w0, n_w + n, (int32_t)n_w, t_first, st->counts + w0 * st->P, s);
     AML_CUDA(cudaStreamSynchronize(s));
     st->hi = at + n;
     st->any = true;
