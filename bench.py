@@ -167,9 +167,9 @@ def algorithmic_bytes(kernel: str, E: int, Ev: int, pats, n_legs: dict) -> float
                     SG/CYC column one uint64 accumulator (8 B), the row (4 B/col)
       k_leg_emit    per edge: src, dst, ts, leg offset (20 B); per leg: the
                     window slot (nbr, eid, t: 12 B) and its outputs, (a, b) for
-                    the cycle search (8 B) and the 32-B SG record
-      k_sg_partition  per leg: one 32-B record read and written (64 B)
-      k_sg_bucket   per leg: one 32-B record read
+                    the cycle search (8 B) and the 16-B SG record
+      k_sg_partition  per leg: one 16-B record read and written (32 B)
+      k_sg_bucket   per leg: one 16-B record read
       k_window_slots  per list slot: t, eid, row, prev, next (20 B) + lb, delta (8 B)
       k_cyc_level   per edge of the window: the anchor's closing range (8 B) and
                     its two edges (8 B) -- the legs it starts from
@@ -182,11 +182,11 @@ def algorithmic_bytes(kernel: str, E: int, Ev: int, pats, n_legs: dict) -> float
     if kernel == "k_assemble":
         return E * (12 + 16 + 8 * n_fan + 8 * n_acc + 4 * P)
     if kernel == "k_leg_emit":
-        return E * 20 + legs * (12 + 8 + 32)
+        return E * 20 + legs * (12 + 8 + 16)
     if kernel == "k_sg_partition":
-        return legs * 64
-    if kernel == "k_sg_bucket":
         return legs * 32
+    if kernel == "k_sg_bucket":
+        return legs * 16
     if kernel == "k_window_slots":
         return Ev * 28
     if kernel == "k_cyc_level":

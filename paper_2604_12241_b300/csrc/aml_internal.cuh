@@ -174,6 +174,10 @@ void radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_tmp, uint32_t
 
 void iota_i32(int32_t* out, int64_t n, cudaStream_t s);
 
+// Reads and clears the primitives' device error word (ERR_* bits) of the
+// current device; synchronous.
+uint32_t take_prims_errors();
+
 inline int bits_for(uint64_t max_value) {
   int b = 1;
   while (b < 64 && (max_value >> b) != 0) ++b;

@@ -127,51 +127,58 @@ __device__ __forceinline__ int32_t cycle_bound(const GraphView& g, const int2* c
 // L[a]: legs from a.  With crng: L2[a] = those that can start a cycle
 // (slots before the cycle bound, minus returns to src(a) among them).
 // With L_new (delta counting): L_new[a] = legs from a whose second edge is new.
+// qwin[a] = a's window slots [q0, q1) in dst(a)'s out-list and, with crng,
+// qcb[a] = its cycle bound, kept for the emission.
 __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
                                                    int32_t* __restrict__ L,
                                                    const int2* __restrict__ crng,
                                                    int32_t* __restrict__ L2,
-                                                   int32_t* __restrict__ L_new) {
+                                                   int32_t* __restrict__ L_new,
+                                                   int2* __restrict__ qwin,
+                                                   int32_t* __restrict__ qcb) {
   int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a64 >= g.E) return;
   int32_t a = (int32_t)a64;
-  if (g.src[a] == g.dst[a]) {
+  const int32_t x = g.src[a], h = g.dst[a];
+  if (x == h) {
     L[a] = 0;
-    if (L2) L2[a] = 0;
+    qwin[a] = make_int2(0, 0);
+    if (L2) {
+      L2[a] = 0;
+      qcb[a] = 0;
+    }
     if (L_new) L_new[a] = 0;
     return;
   }
-  L[a] = legs_from(g, a, delta);
+  int32_t q0, q1;
+  leg_window(g, a, q0, q1, delta);
+  qwin[a] = make_int2(q0, q1);
+  const int32_t ta = g.ts[a];
+  const int32_t hs = g.optr[h], he = g.optr[h + 1];
+  L[a] = (q1 - q0) - pair_after(g.onnbr, g.ont, g.oneid, hs, he, x, ta, a, delta);
   if (L_new) {
-    int32_t q0, q1;
-    leg_window(g, a, q0, q1, delta);
     const int32_t qn = after_edge(g.ot, g.oeid, q0, q1, g.t_new, g.new_from - 1);
     int32_t back = 0;
-    const int32_t h = g.dst[a], x = g.src[a];
-    const int32_t hs = g.optr[h], he = g.optr[h + 1];
     const int32_t r0 = lower_nbr(g.onnbr, hs, he, x);
     if (qn < q1 && r0 < he && __ldg(g.onnbr + r0) == x) {
       const int32_t r1 = lower_nbr(g.onnbr, r0, he, x + 1);
-      const int32_t b0 = after_edge(g.ont, g.oneid, r0, r1, g.ts[a], a);
+      const int32_t b0 = after_edge(g.ont, g.oneid, r0, r1, ta, a);
       const int32_t bn = after_edge(g.ont, g.oneid, b0, r1, g.t_new, g.new_from - 1);
-      const int32_t b1 = upper_t(g.ont, bn, r1, (int64_t)g.ts[a] + delta);
+      const int32_t b1 = upper_t(g.ont, bn, r1, (int64_t)ta + delta);
       back = b1 - bn;
     }
     L_new[a] = (q1 - qn) - back;
   }
   if (!L2) return;
-  int32_t q0, q1;
-  leg_window(g, a, q0, q1, delta);
   const int32_t qc = cycle_bound(g, crng, a, q0, q1);
+  qcb[a] = qc;
   int32_t back = 0;
   if (qc > q0) {  // returns h -> src(a) among the slots [q0, qc)
-    const int32_t h = g.dst[a], x = g.src[a];
-    const int32_t hs = g.optr[h], he = g.optr[h + 1];
     const int32_t r0 = lower_nbr(g.onnbr, hs, he, x);
     if (r0 < he && __ldg(g.onnbr + r0) == x) {
       const int32_t r1 = lower_nbr(g.onnbr, r0, he, x + 1);
       const int2 cr = crng[a];
-      const int32_t b0 = after_edge(g.ont, g.oneid, r0, r1, g.ts[a], a);
+      const int32_t b0 = after_edge(g.ont, g.oneid, r0, r1, ta, a);
       const int32_t b1 = after_edge(g.ont, g.oneid, b0, r1, __ldg(g.it + cr.y - 1),
                                     __ldg(g.ieid + cr.y - 1) - 1);
       back = b1 - b0;
@@ -224,12 +231,8 @@ __device__ __forceinline__ void put_rec(const LegSink& S, int64_t pos, int32_t a
                                         int64_t n_nodes) {
   LegRec r;
   r.key = (uint64_t)x * (uint64_t)n_nodes + (uint64_t)y;
-  r.lo = ta;
-  r.hi = tb;
-  r.m = h;
   r.a = a;
   r.b = b;
-  r.pad = 0;
   S.rec[pos] = r;
 }
 
@@ -267,7 +270,8 @@ __device__ __forceinline__ void sg_record(const LegSink& S, bool leg, int64_t po
 // with records, also counts them into the SG buckets.  Windows of up to 32
 // slots are written by their own lane; longer ones (hub accounts) by the
 // whole warp, 32 slots at a time, with ballots keeping the output order.
-__global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
+__global__ void __launch_bounds__(512) k_leg_emit(GraphView g, const int2* __restrict__ qwin,
+                                                  const int32_t* __restrict__ qcb,
                                                   const int64_t* __restrict__ off, LegSink S,
                                                   unsigned long long* __restrict__ acc_cyc2,
                                                   int32_t* __restrict__ gs_in, int32_t own_max) {
@@ -280,7 +284,9 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
     x = g.src[a];
     h = g.dst[a];
     if (x != h) {
-      leg_window(g, a, q0, q1, delta);
+      const int2 w = qwin[a];
+      q0 = w.x;
+      q1 = w.y;
       o = off[a];
       ta = g.ts[a];
     }
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, int32_t delta,
   int32_t qc = q0;
   int64_t o2 = 0;
   if (S.la && q1 > q0) {
-    qc = cycle_bound(g, S.crng, a, q0, q1);
+    qc = qcb[a];
     o2 = S.off2[a] - o;
   }
   const bool own = q1 - q0 <= own_max;
@@ -427,23 +433,35 @@ __device__ __forceinline__ void sg_credit(unsigned long long* acc, const LegRec&
   }
 }
 
-__device__ __forceinline__ bool sg_partner(const LegRec& r, const LegRec& o, int32_t delta) {
-  if (o.m == r.m) return false;  // same intermediary (also the record itself)
-  const int64_t span = (int64_t)max(r.hi, o.hi) - (int64_t)min(r.lo, o.lo);
-  return span <= delta;
+// (intermediary, scatter time, gather time, gather edge) of a leg
+__device__ __forceinline__ int4 leg_info(const LegRec& r, const int32_t* dst, const int32_t* ts) {
+  return make_int4(__ldg(dst + r.a), __ldg(ts + r.a), __ldg(ts + r.b), r.b);
+}
+
+// two legs of one (s, d) key form an SG instance: different intermediaries
+// (which also excludes the leg itself) and all four edges within delta;
+// delta counting keeps the pairs whose latest edge -- one of the two gather
+// edges -- is new
+__device__ __forceinline__ bool sg_partner(const int4& r, const int4& o, int32_t delta,
+                                           int32_t new_from) {
+  if (o.x == r.x) return false;
+  const int64_t span = (int64_t)max(r.z, o.z) - (int64_t)min(r.y, o.y);
+  return span <= delta && max(r.w, o.w) >= new_from;
 }
 
 __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ rec,
                                                    const int64_t* __restrict__ boff,
-                                                   int32_t delta,
+                                                   int32_t delta, const int32_t* __restrict__ dst,
+                                                   const int32_t* __restrict__ ts,
                                                    unsigned long long* __restrict__ acc,
                                                    int32_t new_from) {
   extern __shared__ __align__(16) unsigned char sg_smem[];
-  unsigned long long* s_key = reinterpret_cast<unsigned long long*>(sg_smem);
+  int4* s_grp = reinterpret_cast<int4*>(sg_smem);  // leg_info of grouped legs, by group
+  unsigned long long* s_key = reinterpret_cast<unsigned long long*>(s_grp + SG_CAP);
+  uint32_t* s_cur = reinterpret_cast<uint32_t*>(s_key);  // group cursors, once keys are filed
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_key + SG_TAB);
-  uint32_t* s_end = s_cnt + SG_TAB;
-  uint16_t* s_slot = reinterpret_cast<uint16_t*>(s_end + SG_TAB);
-  uint16_t* s_idx = s_slot + SG_CAP;
+  uint16_t* s_slot = reinterpret_cast<uint16_t*>(s_cnt + SG_TAB);
+  uint16_t* s_pos = s_slot + SG_CAP;
   const int64_t base = boff[blockIdx.x];
   const int n = (int)(boff[blockIdx.x + 1] - base);
   if (n < 2) return;
@@ -452,16 +470,20 @@ __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ re
     // oversized bucket (a very large pair): compare every record with all
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const LegRec r = R[i];
+      const int4 ri = leg_info(r, dst, ts);
       unsigned long long c = 0;
       for (int j = 0; j < n; ++j) {
         const LegRec o = R[j];
-        if (o.key == r.key && sg_partner(r, o, delta) && max(r.b, o.b) >= new_from) ++c;
+        if (o.key == r.key && sg_partner(ri, leg_info(o, dst, ts), delta, new_from)) ++c;
       }
       sg_credit(acc, r, c);
     }
     return;
   }
-  for (int t = threadIdx.x; t < SG_TAB; t += blockDim.x) {
+  // a table of at least twice the records (load <= 0.5), 256 slots or more
+  int tab = 256;
+  while (tab < 2 * n) tab <<= 1;
+  for (int t = threadIdx.x; t < tab; t += blockDim.x) {
     s_key[t] = ~0ull;
     s_cnt[t] = 0;
   }
@@ -469,30 +491,34 @@ __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ re
   // file every record under its key
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const unsigned long long key = R[i].key;
-    uint32_t h = (uint32_t)mix64(key) & (SG_TAB - 1);
-    for (int probe = 0; probe < SG_TAB; ++probe) {  // n < SG_TAB: a slot is always found
+    uint32_t h = (uint32_t)mix64(key) & (uint32_t)(tab - 1);
+    for (int probe = 0; probe < tab; ++probe) {  // n < tab: a slot is always found
       const unsigned long long cur = s_key[h];
       if (cur == key) break;
       if (cur == ~0ull) {
         const unsigned long long old = atomicCAS(&s_key[h], ~0ull, key);
         if (old == ~0ull || old == key) break;
       }
-      h = (h + 1) & (SG_TAB - 1);
+      h = (h + 1) & (uint32_t)(tab - 1);
     }
     s_slot[i] = (uint16_t)h;
     atomicAdd(&s_cnt[h], 1u);
   }
   __syncthreads();
-  // group starts: exclusive prefix of the slot counts (16 slots per thread)
+  // group starts: exclusive prefix of the counts of slots holding two or
+  // more records (tab / 256 slots per thread); they overwrite the keys,
+  // which are no longer read
+  __shared__ uint32_t s_wsum[8];
   {
-    constexpr int PER = SG_TAB / 256;
-    uint32_t loc[PER], sum = 0;
+    constexpr int PER_MAX = SG_TAB / 256;
+    const int per = tab >> 8;
+    uint32_t loc[PER_MAX], sum = 0;
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      loc[k] = s_cnt[threadIdx.x * PER + k];
+    for (int k = 0; k < PER_MAX; ++k) {
+      const uint32_t c = k < per ? s_cnt[threadIdx.x * per + k] : 0u;
+      loc[k] = c >= 2 ? c : 0u;
       sum += loc[k];
     }
-    __shared__ uint32_t s_wsum[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = sum;
     for (int o = 1; o < 32; o <<= 1) {
@@ -504,31 +530,40 @@ __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ re
     uint32_t before = x - sum;
     for (int w = 0; w < warp; ++w) before += s_wsum[w];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      s_end[threadIdx.x * PER + k] = before;  // becomes the end after the fill below
-      before += loc[k];
+    for (int k = 0; k < PER_MAX; ++k)
+      if (k < per) {
+        s_cur[threadIdx.x * per + k] = before;  // becomes the group's end after the fill
+        before += loc[k];
+      }
+  }
+  __syncthreads();
+  uint32_t n_grouped = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) n_grouped += s_wsum[w];
+  if (n_grouped == 0) return;
+  // the legs of groups of two or more, group by group: their data, slot and
+  // record index
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint32_t h = s_slot[i];
+    if (s_cnt[h] >= 2) {
+      const uint32_t pos = atomicAdd(&s_cur[h], 1u);
+      s_grp[pos] = leg_info(R[i], dst, ts);
+      s_pos[pos] = (uint16_t)i;
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const uint32_t h = s_slot[i];
-    if (s_cnt[h] >= 2) s_idx[atomicAdd(&s_end[h], 1u)] = (uint16_t)i;
-  }
-  __syncthreads();
-  // partners inside each group of two or more
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  // partners inside each group; consecutive threads take consecutive group
+  // members, so a warp's threads mostly walk the same group
+  for (uint32_t p = threadIdx.x; p < n_grouped; p += blockDim.x) {
+    const int i = s_pos[p];
     const uint32_t h = s_slot[i];
     const uint32_t c = s_cnt[h];
-    if (c < 2) continue;
-    const LegRec r = R[i];
-    const uint32_t gs = s_end[h] - c;
+    const int4 own = s_grp[p];
+    const uint32_t end = s_cur[h];
     unsigned long long k = 0;
-    for (uint32_t j = gs; j < gs + c; ++j) {
-      const LegRec& o = R[s_idx[j]];
-      // delta counting: the pair's latest edge is one of its two gather edges
-      if (sg_partner(r, o, delta) && max(r.b, o.b) >= new_from) ++k;
-    }
-    sg_credit(acc, r, k);
+    for (uint32_t j = end - c; j < end; ++j)
+      if (sg_partner(own, s_grp[j], delta, new_from)) ++k;
+    if (k) sg_credit(acc, R[i], k);
   }
 }
 
@@ -691,63 +726,81 @@ __global__ void __launch_bounds__(512) k_cyc_emit(int64_t n, const int32_t* __re
 
 // -------------------------------------------------------------- assemble
 //
-// One thread per edge writes the edge's whole output row from values the
+// One thread per edge computes the edge's whole output row from values the
 // earlier kernels left in slot or edge order: DEG = pos - lb(pos) + 1, FAN =
 // DEG - repeats (prefix-sum difference), GS = legs starting + legs ending at
 // the edge, SG and CYC from the 64-bit accumulators; saturated to 32 bits.
+// The block's rows are staged in shared memory (odd row stride: no bank
+// conflicts) and stored column-contiguous, so the stores coalesce.
 
-__global__ void __launch_bounds__(512) k_assemble(AssembleParams P) {
-  int64_t e64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const GraphView& g = P.g;
-  if (e64 >= g.E) return;
-  int32_t e = (int32_t)e64;
-  uint32_t* row = P.counts + e64 * P.ld;
-  int32_t u = g.src[e], v = g.dst[e];
-  const bool add = e64 < P.accumulate_from;  // an old row: add its new instances
-  if (u == v) {
-    if (!add)
-      for (int c = 0; c < P.ncols; ++c) row[c] = 0u;
-    return;
+__device__ __forceinline__ uint64_t assemble_value(const AssembleParams& P, const ColDesc cd,
+                                                   int32_t e, int32_t po, int32_t pi, int32_t os,
+                                                   int32_t is) {
+  const int w = cd.didx;
+  switch (cd.family) {
+    case AML_FAM_DEG_OUT:
+      return (uint64_t)(po - P.lb_out[w][po] + 1);
+    case AML_FAM_FAN_OUT: {
+      const int32_t* S = P.S_out[w];
+      return (uint64_t)(po - P.lb_out[w][po] + 1 - (S[po] - (os > 0 ? S[os - 1] : 0)));
+    }
+    case AML_FAM_DEG_IN:
+      return (uint64_t)(pi - P.lb_in[w][pi] + 1);
+    case AML_FAM_FAN_IN: {
+      const int32_t* S = P.S_in[w];
+      return (uint64_t)(pi - P.lb_in[w][pi] + 1 - (S[pi] - (is > 0 ? S[is - 1] : 0)));
+    }
+    case AML_FAM_GS: {
+      const int32_t from =
+          P.gs_from[w] ? P.gs_from[w][e] : (int32_t)(P.off[w][e + 1] - P.off[w][e]);
+      return (uint64_t)from + (uint64_t)P.gs_in[w][e];
+    }
+    default:  // accumulated families
+      return P.acc[(int64_t)cd.acc_slot * P.g.E + e];
   }
-  int32_t po = g.opos[e], pi = g.ipos[e];
-  int32_t os = g.optr[u], is = g.iptr[v];
-  for (int c = 0; c < P.ncols; ++c) {
-    const ColDesc cd = P.cols[c];
-    const int w = cd.didx;
-    if (add && !((P.inst_mask >> c) & 1ull)) continue;  // trailing windows never change
-    uint64_t val = 0;
-    switch (cd.family) {
-      case AML_FAM_DEG_OUT:
-        val = (uint64_t)(po - P.lb_out[w][po] + 1);
-        break;
-      case AML_FAM_FAN_OUT: {
-        const int32_t* S = P.S_out[w];
-        val = (uint64_t)(po - P.lb_out[w][po] + 1 - (S[po] - (os > 0 ? S[os - 1] : 0)));
-        break;
-      }
-      case AML_FAM_DEG_IN:
-        val = (uint64_t)(pi - P.lb_in[w][pi] + 1);
-        break;
-      case AML_FAM_FAN_IN: {
-        const int32_t* S = P.S_in[w];
-        val = (uint64_t)(pi - P.lb_in[w][pi] + 1 - (S[pi] - (is > 0 ? S[is - 1] : 0)));
-        break;
-      }
-      case AML_FAM_GS: {
-        const int32_t from =
-            P.gs_from[w] ? P.gs_from[w][e] : (int32_t)(P.off[w][e + 1] - P.off[w][e]);
-        val = (uint64_t)from + (uint64_t)P.gs_in[w][e];
-        break;
-      }
-      default:  // accumulated families
-        val = P.acc[(int64_t)cd.acc_slot * g.E + e];
-        break;
+}
+
+__global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
+  extern __shared__ uint32_t s_rows[];
+  const GraphView& g = P.g;
+  const int nc = P.ncols, rs = nc | 1;
+  const int64_t e0 = (int64_t)blockIdx.x * ASM_BLOCK;
+  const int nrows = g.E - e0 < ASM_BLOCK ? (int)(g.E - e0) : ASM_BLOCK;
+  const int tot = nrows * nc;
+  if (e0 < P.accumulate_from) {  // old rows keep what they hold
+    for (int i = threadIdx.x; i < tot; i += ASM_BLOCK) {
+      const int r = i / nc, c = i - r * nc;
+      s_rows[r * rs + c] = P.counts[(e0 + r) * P.ld + c];
     }
-    if (add) {
-      if (val == 0) continue;
-      val += row[c];
+    __syncthreads();
+  }
+  if ((int)threadIdx.x < nrows) {
+    const int64_t e64 = e0 + threadIdx.x;
+    const int32_t e = (int32_t)e64;
+    uint32_t* row = s_rows + threadIdx.x * rs;
+    const bool add = e64 < P.accumulate_from;  // an old row: add its new instances
+    const int32_t u = g.src[e], v = g.dst[e];
+    if (u == v) {
+      if (!add)
+        for (int c = 0; c < nc; ++c) row[c] = 0u;
+    } else {
+      const int32_t po = g.opos[e], pi = g.ipos[e];
+      const int32_t os = g.optr[u], is = g.iptr[v];
+      for (int c = 0; c < nc; ++c) {
+        if (add && !((P.inst_mask >> c) & 1ull)) continue;  // trailing windows never change
+        uint64_t val = assemble_value(P, P.cols[c], e, po, pi, os, is);
+        if (add) {
+          if (val == 0) continue;
+          val += row[c];
+        }
+        row[c] = val > 0xffffffffull ? 0xffffffffu : (uint32_t)val;
+      }
     }
-    row[c] = val > 0xffffffffull ? 0xffffffffu : (uint32_t)val;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < tot; i += ASM_BLOCK) {
+    const int r = i / nc, c = i - r * nc;
+    P.counts[(e0 + r) * P.ld + c] = s_rows[r * rs + c];
   }
 }
 

@@ -11,7 +11,10 @@ constexpr int MAX_CYCLE = 8;    // longest cycle
 constexpr int SG_CAP = 1024;    // leg records one SG bucket block groups in shared memory
 constexpr int SG_TAB = 2048;    // its hash-table slots (load <= 0.5)
 constexpr int SG_PART_ITEMS = 4;     // records per thread in k_sg_partition
-constexpr size_t SG_SMEM = (size_t)SG_TAB * (8 + 4 + 4) + (size_t)SG_CAP * (2 + 2);
+constexpr int ASM_BLOCK = 128;       // rows per k_assemble block
+// k_sg_bucket: group data, hash keys (later group cursors), slot counts,
+// each record's slot and group position
+constexpr size_t SG_SMEM = (size_t)SG_CAP * 16 + (size_t)SG_TAB * (8 + 4) + (size_t)SG_CAP * (2 + 2);
 
 // Read-only view of a device graph, passed by value to kernels.
 struct GraphView {
@@ -72,14 +75,12 @@ struct AssembleParams {
   uint64_t inst_mask;
 };
 
-// One leg a = s->m (at time lo), b = m->d (at time hi) filed for the SG
-// grouping under key s*N + d; 32 bytes.
-struct LegRec {
+// One leg a = s->m, b = m->d filed for the SG grouping under key s*N + d;
+// 16 bytes (m and the two times are read back from the edges only for the
+// legs that share their key with another leg).
+struct __align__(16) LegRec {
   uint64_t key;
-  int32_t lo, hi;
-  int32_t m;
   int32_t a, b;
-  int32_t pad;
 };
 
 // Where k_leg_emit writes the legs: (a, b) arrays for the cycle search
@@ -116,16 +117,18 @@ __global__ void k_window_slots(const int32_t* ptr, const int32_t* t, const int32
                                const int32_t* prev, const int32_t* next, const int32_t* row_of,
                                int64_t Ev, int32_t delta, int32_t* lb, int32_t* D);
 __global__ void k_leg_count(GraphView g, int32_t delta, int32_t* L, const int2* crng,
-                            int32_t* L2, int32_t* L_new);
+                            int32_t* L2, int32_t* L_new, int2* qwin, int32_t* qcb);
 __global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);
-__global__ void k_leg_emit(GraphView g, int32_t delta, const int64_t* off, LegSink S,
-                           unsigned long long* acc_cyc2, int32_t* gs_in, int32_t own_max);
+__global__ void k_leg_emit(GraphView g, const int2* qwin, const int32_t* qcb, const int64_t* off,
+                           LegSink S, unsigned long long* acc_cyc2, int32_t* gs_in,
+                           int32_t own_max);
 __global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, const int64_t* boff,
                                uint32_t* cursor, LegRec* out);
 __global__ void k_sg_hist(const LegRec* rec, int64_t n, int bits, uint32_t* hist);
 __global__ void k_mark_nodes(const int32_t* node_of, int64_t from, int64_t E, uint32_t* mask);
 __global__ void k_sg_bucket(const LegRec* rec, const int64_t* boff, int32_t delta,
-                            unsigned long long* acc, int32_t new_from);
+                            const int32_t* dst, const int32_t* ts, unsigned long long* acc,
+                            int32_t new_from);
 __global__ void k_close_range(GraphView g, int32_t delta, int2* rng);
 __global__ void k_cyc_level(GraphView g, int32_t delta, int K, int j, CycFrontier F, int64_t n,
                             const int2* close_rng, CycleSlots slots, unsigned long long* acc,

@@ -152,10 +152,13 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       L_new = keep32.back().p;
       P.gs_from[w] = L_new;
     }
+    DBuf<int2> qwin((size_t)E, s);
+    DBuf<int32_t> qcb(level_cycles ? (size_t)E : 0, s);
     AML_LAUNCH("k_leg_count", s,
                k_leg_count<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, L.p,
                                                         level_cycles ? crng.p : nullptr,
-                                                        level_cycles ? L2.p : nullptr, L_new));
+                                                        level_cycles ? L2.p : nullptr, L_new,
+                                                        qwin.p, qcb.p));
     AML_CUDA(cudaMemsetAsync(L.p + E, 0, sizeof(int32_t), s));
     keep64.emplace_back((size_t)(E + 1), s);
     int64_t* off = keep64.back().p;
@@ -239,7 +242,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     unsigned long long* acc2 =
         wp.cyc.slot[2] >= 0 ? acc.p + (int64_t)wp.cyc.slot[2] * E : nullptr;
     AML_LAUNCH("k_leg_emit", s,
-               k_leg_emit<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, off, S, acc2, gs_in,
+               k_leg_emit<<<grid_for(E, B), B, 0, s>>>(gv, qwin.p, qcb.p, off, S, acc2, gs_in,
                                                        tn.own_max));
     int64_t n_sg = nl;  // records to bucket
     if (sg_filter) {
@@ -270,7 +273,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
         if (g->device < 64) smem_set[g->device] = true;
       }
       AML_LAUNCH("k_sg_bucket", s,
-                 k_sg_bucket<<<(unsigned)nb, 256, SG_SMEM, s>>>(part.p, boff.p, wp.delta,
+                 k_sg_bucket<<<(unsigned)nb, 256, SG_SMEM, s>>>(part.p, boff.p, wp.delta, gv.dst,
+                                                              gv.ts,
                                                               acc.p + (int64_t)wp.sg_slot * E,
                                                               new_from));
     }
@@ -316,7 +320,9 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       }
     }
   }
-  AML_LAUNCH("k_assemble", s, k_assemble<<<grid_for(E, B), B, 0, s>>>(P));
+  AML_LAUNCH("k_assemble", s,
+             k_assemble<<<grid_for(E, ASM_BLOCK), ASM_BLOCK,
+                          (size_t)ASM_BLOCK * (ncols | 1) * sizeof(uint32_t), s>>>(P));
 }
 
 }  // namespace aml

@@ -49,13 +49,25 @@ void iota_i32(int32_t* out, int64_t n, cudaStream_t s) {
 
 // ------------------------------------------------------------- prefix sum
 //
-// Three-phase scan: per-tile totals, scan of the totals (recursively), and
-// a per-tile scan seeded with its tile's offset.  Tiles are staged through
-// shared memory so global loads and stores stay coalesced.
+// Tiles of SCAN_TILE values are staged through shared memory so global loads
+// and stores stay coalesced; one tile is scanned by k_tile_scan, more by the
+// single-pass k_scan_lookback below.
 
 constexpr int SCAN_BLOCK = 256;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+// Shared-memory index of tile element i with one pad element per 128 bytes:
+// thread t then reads its SCAN_ITEMS consecutive elements without bank
+// conflicts (t * SCAN_ITEMS alone maps a warp onto 4 banks).
+template <typename T>
+__device__ __forceinline__ int spad(int i) {
+  return i + (i >> (sizeof(T) == 8 ? 4 : 5));
+}
+template <typename T>
+constexpr int scan_smem_elems() {
+  return SCAN_TILE + SCAN_TILE / (sizeof(T) == 8 ? 16 : 32);
+}
 
 template <typename T>
 __device__ T block_exclusive_sum(T v, T* total) {
@@ -87,35 +99,21 @@ __device__ T block_exclusive_sum(T v, T* total) {
 }
 
 template <typename Tin, typename Tacc>
-__global__ void __launch_bounds__(SCAN_BLOCK) k_tile_reduce(const Tin* __restrict__ in, int64_t n,
-                                                            Tacc* __restrict__ partial) {
-  int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-  Tacc sum = 0;
-  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_BLOCK) {
-    int64_t j = base + i;
-    if (j < n) sum += (Tacc)in[j];
-  }
-  Tacc tot;
-  block_exclusive_sum<Tacc>(sum, &tot);
-  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
-}
-
-template <typename Tin, typename Tacc>
 __global__ void __launch_bounds__(SCAN_BLOCK) k_tile_scan(const Tin* __restrict__ in, Tacc* out,
                                                           int64_t n, const Tacc* tile_off,
                                                           bool inclusive) {
-  __shared__ Tacc s[SCAN_TILE];
+  __shared__ Tacc s[scan_smem_elems<Tacc>()];
   int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
   for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_BLOCK) {
     int64_t j = base + i;
-    s[i] = j < n ? (Tacc)in[j] : Tacc(0);
+    s[spad<Tacc>(i)] = j < n ? (Tacc)in[j] : Tacc(0);
   }
   __syncthreads();
   Tacc loc[SCAN_ITEMS];
   Tacc sum = 0;
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
-    loc[k] = s[threadIdx.x * SCAN_ITEMS + k];
+    loc[k] = s[spad<Tacc>(threadIdx.x * SCAN_ITEMS + k)];
     sum += loc[k];
   }
   Tacc tot;
@@ -124,32 +122,153 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_tile_scan(const Tin* __restrict_
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
     Tacc v = loc[k];
-    s[threadIdx.x * SCAN_ITEMS + k] = inclusive ? run + v : run;
+    s[spad<Tacc>(threadIdx.x * SCAN_ITEMS + k)] = inclusive ? run + v : run;
     run += v;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_BLOCK) {
     int64_t j = base + i;
-    if (j < n) out[j] = s[i];
+    if (j < n) out[j] = s[spad<Tacc>(i)];
+  }
+}
+
+// Single-pass scan with decoupled look-back (Merrill & Garland, "Single-pass
+// Parallel Prefix Scan with Decoupled Look-back", 2016).  Tiles take their
+// index from an atomic counter in launch order, so every tile a tile waits
+// for is already running and publishes its total before it looks back
+// itself: the waits always end.  Status word per tile: 2 flag bits (0 = not
+// yet, AGG = the tile's own total, PRE = its inclusive prefix) over a 62-bit
+// two's-complement value, written and read as one relaxed 64-bit word.  The
+// wait is bounded all the same: past the limit the tile records ERR_TIMEOUT
+// in the primitives' error word and goes on (its results are then wrong and
+// the call that reads the word fails).
+
+constexpr unsigned long long LB_AGG = 1ull << 62;
+constexpr unsigned long long LB_PRE = 2ull << 62;
+constexpr unsigned long long LB_FLAGS = 3ull << 62;
+constexpr uint32_t LB_SPIN_LIMIT = 1u << 22;
+
+__device__ uint32_t g_prims_err = 0;
+
+__device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long long w) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+__device__ __forceinline__ unsigned long long lb_load(const unsigned long long* p) {
+  unsigned long long w;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+  return w;
+}
+template <typename T>
+__device__ __forceinline__ unsigned long long lb_pack(unsigned long long flag, T v) {
+  return flag | ((unsigned long long)(long long)v & ~LB_FLAGS);
+}
+__device__ __forceinline__ long long lb_value(unsigned long long w) {
+  return (long long)(w << 2) >> 2;
+}
+
+// status: nb + 1 zeroed words (the last one is the tile counter)
+template <typename Tin, typename Tacc>
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_lookback(const Tin* __restrict__ in,
+                                                              Tacc* out, int64_t n, int64_t nb,
+                                                              bool inclusive,
+                                                              unsigned long long* status) {
+  __shared__ Tacc s[scan_smem_elems<Tacc>()];
+  __shared__ int64_t s_tile;
+  __shared__ Tacc s_prefix;
+  if (threadIdx.x == 0)
+    s_tile = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(status + nb), 1ull);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t base = tile * SCAN_TILE;
+  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_BLOCK) {
+    const int64_t j = base + i;
+    s[spad<Tacc>(i)] = j < n ? (Tacc)in[j] : Tacc(0);
+  }
+  __syncthreads();
+  Tacc loc[SCAN_ITEMS];
+  Tacc sum = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    loc[k] = s[spad<Tacc>(threadIdx.x * SCAN_ITEMS + k)];
+    sum += loc[k];
+  }
+  Tacc tot;
+  Tacc run = block_exclusive_sum<Tacc>(sum, &tot);
+  if (threadIdx.x < 32) {  // warp 0 publishes the total and looks back
+    const int lane = threadIdx.x;
+    Tacc prefix = 0;
+    if (tile == 0) {
+      if (lane == 0) lb_store(status, lb_pack(LB_PRE, tot));
+    } else {
+      if (lane == 0) lb_store(status + tile, lb_pack(LB_AGG, tot));
+      int64_t j = tile - 1;  // newest predecessor not yet added
+      uint32_t spins = 0;
+      while (true) {
+        const int64_t idx = j - lane;
+        const unsigned long long w = idx >= 0 ? lb_load(status + idx) : LB_PRE;
+        const unsigned long long flag = w & LB_FLAGS;
+        const unsigned pre = __ballot_sync(0xffffffffu, flag == LB_PRE);
+        const unsigned wait = __ballot_sync(0xffffffffu, flag == 0);
+        const int first = pre ? __ffs(pre) : 32;  // lanes [0, first) are needed
+        const unsigned need = first == 32 ? 0xffffffffu : (1u << first) - 1u;
+        if (wait & need) {
+          if (++spins > LB_SPIN_LIMIT) {
+            if (lane == 0) atomicOr(&g_prims_err, (uint32_t)ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        Tacc v = ((need >> lane) & 1u) ? (Tacc)lb_value(w) : Tacc(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        prefix += v;
+        if (pre) break;
+        j -= 32;
+      }
+      if (lane == 0) lb_store(status + tile, lb_pack(LB_PRE, prefix + tot));
+    }
+    if (lane == 0) s_prefix = prefix;
+  }
+  __syncthreads();
+  run += s_prefix;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const Tacc v = loc[k];
+    s[spad<Tacc>(threadIdx.x * SCAN_ITEMS + k)] = inclusive ? run + v : run;
+    run += v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_BLOCK) {
+    const int64_t j = base + i;
+    if (j < n) out[j] = s[spad<Tacc>(i)];
   }
 }
 
 template <typename Tin, typename Tacc>
 static void scan_impl(const Tin* in, Tacc* out, int64_t n, bool inclusive, cudaStream_t s) {
   if (n <= 0) return;
-  int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nb == 1) {
     AML_LAUNCH("k_tile_scan", s,
                k_tile_scan<Tin, Tacc><<<1, SCAN_BLOCK, 0, s>>>(in, out, n, nullptr, inclusive));
     return;
   }
-  DBuf<Tacc> part(nb, s);
-  AML_LAUNCH("k_tile_reduce", s,
-             k_tile_reduce<Tin, Tacc><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, n, part.p));
-  scan_impl<Tacc, Tacc>(part.p, part.p, nb, false, s);
-  AML_LAUNCH("k_tile_scan", s,
-             k_tile_scan<Tin, Tacc><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(
-                 in, out, n, part.p, inclusive));
+  DBuf<unsigned long long> status((size_t)nb + 1, s);
+  AML_CUDA(cudaMemsetAsync(status.p, 0, (size_t)(nb + 1) * 8, s));
+  AML_LAUNCH("k_scan_lookback", s,
+             k_scan_lookback<Tin, Tacc><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, out, n, nb,
+                                                                            inclusive, status.p));
+}
+
+uint32_t take_prims_errors() {
+  uint32_t err = 0;
+  AML_CUDA(cudaMemcpyFromSymbol(&err, g_prims_err, 4));
+  if (err) {
+    const uint32_t zero = 0;
+    AML_CUDA(cudaMemcpyToSymbol(g_prims_err, &zero, 4));
+  }
+  return err;
 }
 
 void scan_i32(const int32_t* in, int32_t* out, int64_t n, bool inclusive, cudaStream_t s) {

@@ -23,6 +23,7 @@
 // budget is refused (AML_EADMIT) before any state changes.
 #include <algorithm>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "aml_internal.cuh"
@@ -104,6 +105,12 @@ static void mine_window(aml_stream* st, int64_t w0, int64_t n, int32_t new_from,
   try {
     mine_plain(g, &st->ps, out, st->P, s, 0, new_from, t_new, true);
     AML_CUDA(cudaStreamSynchronize(s));
+    uint32_t err = take_prims_errors();
+    uint32_t gerr = 0;
+    AML_CUDA(cudaMemcpy(&gerr, g->err, 4, cudaMemcpyDeviceToHost));
+    err |= gerr;
+    AML_REQUIRE(!(err & ERR_TIMEOUT), AML_ETIMEOUT, "a bounded device wait gave up");
+    AML_REQUIRE(err == 0, AML_EINTERNAL, "device error word set (" + std::to_string(err) + ")");
   } catch (...) {
     destroy_graph(g);
     throw;
