@@ -81,6 +81,7 @@ struct DBuf {
 // each row; the *n arrays hold the same slots re-sorted by (nbr, t, id).
 struct Adj {
   int32_t* ptr = nullptr;   // [N+1] row offsets (row N holds nothing)
+  int32_t* rstart = nullptr;  // [Ev] first slot of the slot's row
   int32_t* nbr = nullptr;   // [Ev] counterparty of the slot's edge
   int32_t* t = nullptr;     // [Ev] timestamp
   int32_t* eid = nullptr;   // [Ev] edge id
@@ -173,10 +174,6 @@ void radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_tmp, uint32_t
                     int64_t n, int nbits, cudaStream_t s);
 
 void iota_i32(int32_t* out, int64_t n, cudaStream_t s);
-
-// Reads and clears the primitives' device error word (ERR_* bits) of the
-// current device; synchronous.
-uint32_t take_prims_errors();
 
 inline int bits_for(uint64_t max_value) {
   int b = 1;

@@ -53,12 +53,10 @@ static const char* family_name(int f) {
 // Reads and clears the graph's device error word (the graph's stream must
 // be idle or synchronized by the caller).
 static void check_device_errors(aml_graph* g) {
-  uint32_t err = take_prims_errors();
-  uint32_t gerr = 0;
-  AML_CUDA(cudaMemcpy(&gerr, g->err, 4, cudaMemcpyDeviceToHost));
-  if (gerr) AML_CUDA(cudaMemset(g->err, 0, 4));
-  err |= gerr;
+  uint32_t err = 0;
+  AML_CUDA(cudaMemcpy(&err, g->err, 4, cudaMemcpyDeviceToHost));
   if (!err) return;
+  AML_CUDA(cudaMemset(g->err, 0, 4));
   AML_REQUIRE(!(err & ERR_TIMEOUT), AML_ETIMEOUT, "a bounded device wait gave up");
   AML_REQUIRE(false, AML_EINTERNAL, "device error word set (" + std::to_string(err) + ")");
 }

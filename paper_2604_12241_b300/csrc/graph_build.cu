@@ -69,10 +69,12 @@ __global__ void k_row_ptr(const uint32_t* __restrict__ keys, int64_t n, int32_t 
   ptr[u] = (int32_t)lo;
 }
 
-__global__ void k_fill_slots(const uint32_t* __restrict__ perm, int64_t Ev,
+__global__ void k_fill_slots(const uint32_t* __restrict__ perm, const uint32_t* __restrict__ keys,
+                             const int32_t* __restrict__ ptr, int64_t Ev,
                              const int32_t* __restrict__ other, const int32_t* __restrict__ ts,
                              int32_t* __restrict__ nbr, int32_t* __restrict__ t,
-                             int32_t* __restrict__ eid, int32_t* __restrict__ pos) {
+                             int32_t* __restrict__ eid, int32_t* __restrict__ pos,
+                             int32_t* __restrict__ rstart) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= Ev) return;
   int32_t e = (int32_t)perm[p];
@@ -80,6 +82,7 @@ __global__ void k_fill_slots(const uint32_t* __restrict__ perm, int64_t Ev,
   t[p] = ts[e];
   eid[p] = e;
   pos[e] = (int32_t)p;
+  rstart[p] = ptr[keys[p]];  // keys: the sorted row of every slot
 }
 
 // fills the (nbr, t, id) copy and links consecutive same-counterparty slots
@@ -160,12 +163,13 @@ static void build_direction(aml_graph* g, Adj& a, const int32_t* row_of, const i
   a.nt = ga.get<int32_t>(Ev);
   a.neid = ga.get<int32_t>(Ev);
   a.pos = ga.get<int32_t>(E);
+  a.rstart = ga.get<int32_t>(Ev);
   AML_CUDA(cudaMemsetAsync(a.pos, 0xff, (E ? E : 1) * sizeof(int32_t), s));
   AML_CUDA(cudaMemsetAsync(a.prev, 0xff, (Ev ? Ev : 1) * sizeof(int32_t), s));
   AML_LAUNCH("k_fill_i32", s, k_fill_i32<<<grid_for(Ev, B), B, 0, s>>>(a.next, Ev, INT32_MAX));
   AML_LAUNCH("k_fill_slots", s,
              k_fill_slots<<<grid_for(Ev, B), B, 0, s>>>(
-                 perm.p, Ev, other, g->ts, a.nbr, a.t, a.eid, a.pos));
+                 perm.p, keys.p, a.ptr, Ev, other, g->ts, a.nbr, a.t, a.eid, a.pos, a.rstart));
   // (account, counterparty, t, id) order: stable sort by counterparty, then by account
   AML_LAUNCH("k_nbr_keys", s,
              k_nbr_keys<<<grid_for(E, B), B, 0, s>>>(perm.p, row_of, other, E, N, keys.p));

@@ -24,24 +24,28 @@ namespace aml {
 // next(r) <= p-1.  So R is a per-row prefix sum of per-slot deltas: one pass
 // plus one scan, O(list length) in total.
 
-// Per slot p of one direction: the start lb(p) of its trailing window (so
-// DEG = p - lb(p) + 1) and, when FAN is wanted, the repeat delta above.
-__global__ void __launch_bounds__(512) k_window_slots(const int32_t* __restrict__ ptr,
+// Per slot p of one direction: DEG(p) = p - lb(p) + 1, lb(p) the start of
+// its trailing window, and, when FAN is wanted, the repeat delta above.
+// deg_s: DEG per slot; df: (DEG, 0) stored at the slot's edge id (the
+// DEG-only case: no FAN pass follows).  Each output may be null.
+__global__ void __launch_bounds__(512) k_window_slots(const int32_t* __restrict__ rstart,
                                                       const int32_t* __restrict__ t,
                                                       const int32_t* __restrict__ eid,
                                                       const int32_t* __restrict__ prev,
                                                       const int32_t* __restrict__ next,
-                                                      const int32_t* __restrict__ row_of,
                                                       int64_t Ev, int32_t delta,
-                                                      int32_t* __restrict__ lb,
-                                                      int32_t* __restrict__ D) {
+                                                      int32_t* __restrict__ deg_s,
+                                                      int32_t* __restrict__ D,
+                                                      int2* __restrict__ df) {
   int64_t p64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p64 >= Ev) return;
   int32_t p = (int32_t)p64;
-  int32_t rs = __ldg(ptr + __ldg(row_of + __ldg(eid + p)));
-  int32_t tp = __ldg(t + p);
-  int32_t lbp = lower_t(t, rs, p + 1, (int64_t)tp - delta);
-  lb[p] = lbp;
+  const int32_t rs = __ldg(rstart + p);
+  const int32_t tp = __ldg(t + p);
+  const int32_t lbp = lower_t(t, rs, p + 1, (int64_t)tp - delta);
+  const int32_t deg = p - lbp + 1;
+  if (deg_s) deg_s[p] = deg;
+  if (df) df[__ldg(eid + p)] = make_int2(deg, 0);
   if (!D) return;
   int32_t d = 0;
   if (p > rs) {
@@ -51,6 +55,22 @@ __global__ void __launch_bounds__(512) k_window_slots(const int32_t* __restrict_
     for (int32_t r = lbq; r < lbp; ++r) d -= (__ldg(next + r) <= p - 1) ? 1 : 0;
   }
   D[p] = d;
+}
+
+// (DEG, FAN) of every slot, stored at its edge id: FAN = DEG - R(p), R(p) =
+// S[p] - S[rs - 1] with S the inclusive prefix sum of the repeat deltas and
+// rs the first slot of p's row
+__global__ void __launch_bounds__(512) k_slot_fan(const int32_t* __restrict__ rstart,
+                                                  const int32_t* __restrict__ eid,
+                                                  const int32_t* __restrict__ deg_s,
+                                                  const int32_t* __restrict__ S, int64_t Ev,
+                                                  int2* __restrict__ df) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Ev) return;
+  const int32_t rs = rstart[p];
+  const int32_t deg = deg_s[p];
+  const int32_t rep = S[p] - (rs > 0 ? __ldg(S + rs - 1) : 0);
+  df[eid[p]] = make_int2(deg, deg - rep);
 }
 
 // ------------------------------------------------------------------ legs
@@ -727,29 +747,24 @@ __global__ void __launch_bounds__(512) k_cyc_emit(int64_t n, const int32_t* __re
 // -------------------------------------------------------------- assemble
 //
 // One thread per edge computes the edge's whole output row from values the
-// earlier kernels left in slot or edge order: DEG = pos - lb(pos) + 1, FAN =
-// DEG - repeats (prefix-sum difference), GS = legs starting + legs ending at
-// the edge, SG and CYC from the 64-bit accumulators; saturated to 32 bits.
+// earlier kernels left in edge order: DEG and FAN per window and direction,
+// GS = legs starting + legs ending at the edge, SG and CYC from the 64-bit
+// accumulators; saturated to 32 bits.
 // The block's rows are staged in shared memory (odd row stride: no bank
 // conflicts) and stored column-contiguous, so the stores coalesce.
 
 __device__ __forceinline__ uint64_t assemble_value(const AssembleParams& P, const ColDesc cd,
-                                                   int32_t e, int32_t po, int32_t pi, int32_t os,
-                                                   int32_t is) {
+                                                   int32_t e) {
   const int w = cd.didx;
   switch (cd.family) {
     case AML_FAM_DEG_OUT:
-      return (uint64_t)(po - P.lb_out[w][po] + 1);
-    case AML_FAM_FAN_OUT: {
-      const int32_t* S = P.S_out[w];
-      return (uint64_t)(po - P.lb_out[w][po] + 1 - (S[po] - (os > 0 ? S[os - 1] : 0)));
-    }
+      return (uint64_t)P.df_out[w][e].x;
+    case AML_FAM_FAN_OUT:
+      return (uint64_t)P.df_out[w][e].y;
     case AML_FAM_DEG_IN:
-      return (uint64_t)(pi - P.lb_in[w][pi] + 1);
-    case AML_FAM_FAN_IN: {
-      const int32_t* S = P.S_in[w];
-      return (uint64_t)(pi - P.lb_in[w][pi] + 1 - (S[pi] - (is > 0 ? S[is - 1] : 0)));
-    }
+      return (uint64_t)P.df_in[w][e].x;
+    case AML_FAM_FAN_IN:
+      return (uint64_t)P.df_in[w][e].y;
     case AML_FAM_GS: {
       const int32_t from =
           P.gs_from[w] ? P.gs_from[w][e] : (int32_t)(P.off[w][e + 1] - P.off[w][e]);
@@ -784,11 +799,9 @@ __global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
       if (!add)
         for (int c = 0; c < nc; ++c) row[c] = 0u;
     } else {
-      const int32_t po = g.opos[e], pi = g.ipos[e];
-      const int32_t os = g.optr[u], is = g.iptr[v];
       for (int c = 0; c < nc; ++c) {
         if (add && !((P.inst_mask >> c) & 1ull)) continue;  // trailing windows never change
-        uint64_t val = assemble_value(P, P.cols[c], e, po, pi, os, is);
+        uint64_t val = assemble_value(P, P.cols[c], e);
         if (add) {
           if (val == 0) continue;
           val += row[c];

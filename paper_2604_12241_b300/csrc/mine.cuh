@@ -58,10 +58,8 @@ struct AssembleParams {
   GraphView g;
   ColDesc cols[MAX_COLS];
   int32_t ncols;
-  const int32_t* lb_out[MAX_DELTAS];  // window start per out-slot
-  const int32_t* lb_in[MAX_DELTAS];   // window start per in-slot
-  const int32_t* S_out[MAX_DELTAS];   // repeat prefix sums per out-slot (FAN)
-  const int32_t* S_in[MAX_DELTAS];
+  const int2* df_out[MAX_DELTAS];  // (DEG_OUT, FAN_OUT) per edge
+  const int2* df_in[MAX_DELTAS];   // (DEG_IN, FAN_IN) per edge
   const int64_t* off[MAX_DELTAS];     // leg offsets per edge (GS gather side)
   const int32_t* gs_from[MAX_DELTAS]; // delta counting: legs from each edge that are new
   const int32_t* gs_in[MAX_DELTAS];   // legs ending with each edge (GS scatter side)
@@ -113,9 +111,11 @@ struct CycFrontier {
   const int32_t* slot[MAX_CYCLE + 1];
 };
 
-__global__ void k_window_slots(const int32_t* ptr, const int32_t* t, const int32_t* eid,
-                               const int32_t* prev, const int32_t* next, const int32_t* row_of,
-                               int64_t Ev, int32_t delta, int32_t* lb, int32_t* D);
+__global__ void k_window_slots(const int32_t* rstart, const int32_t* t, const int32_t* eid,
+                               const int32_t* prev, const int32_t* next, int64_t Ev,
+                               int32_t delta, int32_t* deg_s, int32_t* D, int2* df);
+__global__ void k_slot_fan(const int32_t* rstart, const int32_t* eid, const int32_t* deg_s,
+                           const int32_t* S, int64_t Ev, int2* df);
 __global__ void k_leg_count(GraphView g, int32_t delta, int32_t* L, const int2* crng,
                             int32_t* L2, int32_t* L_new, int2* qwin, int32_t* qcb);
 __global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(NA_BLOCK) k_na_tile_scan(int32_t* __restrict__
 
 // FAN(e) = DEG(e) - repeats(e) for every edge, 0 for self-loops
 __global__ void __launch_bounds__(NA_BLOCK) k_na_fan_rows(GraphView g, int dir,
-                                                          const int32_t* __restrict__ lb,
+                                                          const int32_t* __restrict__ deg,
                                                           const int32_t* __restrict__ S,
                                                           uint32_t* __restrict__ out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(NA_BLOCK) k_na_fan_rows(GraphView g, int dir,
   const int32_t p = dir == AML_DIR_OUT ? g.opos[e] : g.ipos[e];
   const int32_t rs = dir == AML_DIR_OUT ? g.optr[u] : g.iptr[v];
   const int32_t rep = S[p] - (rs > 0 ? S[rs - 1] : 0);
-  out[e] = (uint32_t)(p - lb[p] + 1 - rep);
+  out[e] = (uint32_t)(deg[p] - rep);
 }
 
 }  // namespace
@@ -157,7 +157,7 @@ extern "C" aml_status aml_fan_noalloc(const aml_graph* g, int32_t delta, int32_t
     if (g->E == 0) return AML_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int32_t* base = scratch_for_current_device();
-    int32_t* lb = base;
+    int32_t* deg = base;
     int32_t* D = base + NA_MAX_SLOTS;
     int32_t* part = base + 2 * NA_MAX_SLOTS;
     const GraphView gv = view_of(g);
@@ -167,8 +167,7 @@ extern "C" aml_status aml_fan_noalloc(const aml_graph* g, int32_t delta, int32_t
     // nothing left over from an earlier call is ever read
     if (Ev > 0) {
       k_window_slots<<<grid_for(Ev, NA_BLOCK), NA_BLOCK, 0, s>>>(
-          a.ptr, a.t, a.eid, a.prev, a.next, direction == AML_DIR_OUT ? g->src : g->dst, Ev,
-          delta, lb, D);
+          a.rstart, a.t, a.eid, a.prev, a.next, Ev, delta, deg, D, nullptr);
       AML_CUDA(cudaGetLastError());
       const int64_t nt = (Ev + NA_TILE - 1) / NA_TILE;
       k_na_tile_sum<<<(unsigned)nt, NA_BLOCK, 0, s>>>(D, Ev, part);
@@ -178,7 +177,7 @@ extern "C" aml_status aml_fan_noalloc(const aml_graph* g, int32_t delta, int32_t
       k_na_tile_scan<<<(unsigned)nt, NA_BLOCK, 0, s>>>(D, Ev, part, 1);
       AML_CUDA(cudaGetLastError());
     }
-    k_na_fan_rows<<<grid_for(g->E, NA_BLOCK), NA_BLOCK, 0, s>>>(gv, direction, lb, D, out);
+    k_na_fan_rows<<<grid_for(g->E, NA_BLOCK), NA_BLOCK, 0, s>>>(gv, direction, deg, D, out);
     AML_CUDA(cudaGetLastError());
     return AML_OK;
   } catch (const Failure& f) {

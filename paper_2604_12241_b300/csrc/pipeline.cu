@@ -103,6 +103,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
 
   std::vector<DBuf<int32_t>> keep32;   // per-window buffers read by k_assemble
   std::vector<DBuf<int64_t>> keep64;
+  std::vector<DBuf<int2>> keep_df;
+  keep_df.reserve(2 * wins.size());
   keep32.reserve(8 * wins.size());
   keep64.reserve(wins.size());
   const Tuning tn = g->tune;
@@ -110,26 +112,30 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   const int64_t Ev = g->Ev;
   for (size_t w = 0; w < wins.size(); ++w) {
     WindowPlan& wp = wins[w];
-    // 1. trailing windows of both directions
+    // 1. trailing windows of both directions: (DEG, FAN) per edge
     for (int dir = 0; dir < 2; ++dir) {
       bool fan = dir == 0 ? wp.fan_out : wp.fan_in;
       bool deg = dir == 0 ? wp.deg_out : wp.deg_in;
       if (!(fan || deg) || Ev == 0) continue;
       const Adj& a = dir == 0 ? g->out : g->in;
-      keep32.emplace_back((size_t)Ev, s);
-      int32_t* lbp = keep32.back().p;
-      int32_t* D = nullptr;
+      keep_df.emplace_back((size_t)E, s);
+      int2* df = keep_df.back().p;
+      DBuf<int32_t> deg_s, D;
       if (fan) {
-        keep32.emplace_back((size_t)Ev, s);
-        D = keep32.back().p;
+        deg_s = DBuf<int32_t>((size_t)Ev, s);
+        D = DBuf<int32_t>((size_t)Ev, s);
       }
       AML_LAUNCH("k_window_slots", s,
                  k_window_slots<<<grid_for(Ev, B), B, 0, s>>>(
-                     a.ptr, a.t, a.eid, a.prev, a.next, dir == 0 ? g->src : g->dst, Ev,
-                     wp.delta, lbp, D));
-      if (fan) scan_i32(D, D, Ev, true, s);
-      (dir == 0 ? P.lb_out : P.lb_in)[w] = lbp;
-      (dir == 0 ? P.S_out : P.S_in)[w] = D;
+                     a.rstart, a.t, a.eid, a.prev, a.next, Ev, wp.delta, deg_s.p, D.p,
+                     fan ? nullptr : df));
+      if (fan) {
+        scan_i32(D.p, D.p, Ev, true, s);
+        AML_LAUNCH("k_slot_fan", s,
+                   k_slot_fan<<<grid_for(Ev, B), B, 0, s>>>(a.rstart, a.eid, deg_s.p, D.p, Ev,
+                                                            df));
+      }
+      (dir == 0 ? P.df_out : P.df_in)[w] = df;
     }
     if (!wp.needs_off()) continue;
     // 2. legs (and, for the level-by-level cycle search, the legs that can

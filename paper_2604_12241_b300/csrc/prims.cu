@@ -1,4 +1,5 @@
 // Device primitives: stream-ordered scratch, prefix sums, stable radix sort.
+#include <algorithm>
 #include <mutex>
 #include <set>
 
@@ -132,143 +133,102 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_tile_scan(const Tin* __restrict_
   }
 }
 
-// Single-pass scan with decoupled look-back (Merrill & Garland, "Single-pass
-// Parallel Prefix Scan with Decoupled Look-back", 2016).  Tiles take their
-// index from an atomic counter in launch order, so every tile a tile waits
-// for is already running and publishes its total before it looks back
-// itself: the waits always end.  Status word per tile: 2 flag bits (0 = not
-// yet, AGG = the tile's own total, PRE = its inclusive prefix) over a 62-bit
-// two's-complement value, written and read as one relaxed 64-bit word.  The
-// wait is bounded all the same: past the limit the tile records ERR_TIMEOUT
-// in the primitives' error word and goes on (its results are then wrong and
-// the call that reads the word fails).
+// Larger inputs: reduce-then-scan over one contiguous chunk per block, with
+// about as many blocks as the GPU holds at once.  k_chunk_reduce writes each
+// chunk's total; k_chunk_scan sums the totals before its chunk (a few
+// thousand values, read by every block) and scans its chunk tile by tile,
+// carrying the running sum.  Two launches, no inter-block waits; the input
+// is read twice.
 
-constexpr unsigned long long LB_AGG = 1ull << 62;
-constexpr unsigned long long LB_PRE = 2ull << 62;
-constexpr unsigned long long LB_FLAGS = 3ull << 62;
-constexpr uint32_t LB_SPIN_LIMIT = 1u << 22;
-
-__device__ uint32_t g_prims_err = 0;
-
-__device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long long w) {
-  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
-}
-__device__ __forceinline__ unsigned long long lb_load(const unsigned long long* p) {
-  unsigned long long w;
-  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
-  return w;
-}
-template <typename T>
-__device__ __forceinline__ unsigned long long lb_pack(unsigned long long flag, T v) {
-  return flag | ((unsigned long long)(long long)v & ~LB_FLAGS);
-}
-__device__ __forceinline__ long long lb_value(unsigned long long w) {
-  return (long long)(w << 2) >> 2;
-}
-
-// status: nb + 1 zeroed words (the last one is the tile counter)
 template <typename Tin, typename Tacc>
-__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_lookback(const Tin* __restrict__ in,
-                                                              Tacc* out, int64_t n, int64_t nb,
-                                                              bool inclusive,
-                                                              unsigned long long* status) {
-  __shared__ Tacc s[scan_smem_elems<Tacc>()];
-  __shared__ int64_t s_tile;
-  __shared__ Tacc s_prefix;
-  if (threadIdx.x == 0)
-    s_tile = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(status + nb), 1ull);
-  __syncthreads();
-  const int64_t tile = s_tile;
-  const int64_t base = tile * SCAN_TILE;
-  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_BLOCK) {
-    const int64_t j = base + i;
-    s[spad<Tacc>(i)] = j < n ? (Tacc)in[j] : Tacc(0);
-  }
-  __syncthreads();
-  Tacc loc[SCAN_ITEMS];
+__global__ void __launch_bounds__(SCAN_BLOCK) k_chunk_reduce(const Tin* __restrict__ in,
+                                                             int64_t n, int64_t chunk,
+                                                             Tacc* __restrict__ partial) {
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
   Tacc sum = 0;
-#pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    loc[k] = s[spad<Tacc>(threadIdx.x * SCAN_ITEMS + k)];
-    sum += loc[k];
-  }
+  for (int64_t j = lo + threadIdx.x; j < hi; j += SCAN_BLOCK) sum += (Tacc)in[j];
   Tacc tot;
-  Tacc run = block_exclusive_sum<Tacc>(sum, &tot);
-  if (threadIdx.x < 32) {  // warp 0 publishes the total and looks back
-    const int lane = threadIdx.x;
-    Tacc prefix = 0;
-    if (tile == 0) {
-      if (lane == 0) lb_store(status, lb_pack(LB_PRE, tot));
-    } else {
-      if (lane == 0) lb_store(status + tile, lb_pack(LB_AGG, tot));
-      int64_t j = tile - 1;  // newest predecessor not yet added
-      uint32_t spins = 0;
-      while (true) {
-        const int64_t idx = j - lane;
-        const unsigned long long w = idx >= 0 ? lb_load(status + idx) : LB_PRE;
-        const unsigned long long flag = w & LB_FLAGS;
-        const unsigned pre = __ballot_sync(0xffffffffu, flag == LB_PRE);
-        const unsigned wait = __ballot_sync(0xffffffffu, flag == 0);
-        const int first = pre ? __ffs(pre) : 32;  // lanes [0, first) are needed
-        const unsigned need = first == 32 ? 0xffffffffu : (1u << first) - 1u;
-        if (wait & need) {
-          if (++spins > LB_SPIN_LIMIT) {
-            if (lane == 0) atomicOr(&g_prims_err, (uint32_t)ERR_TIMEOUT);
-            break;
-          }
-          __nanosleep(32);
-          continue;
-        }
-        Tacc v = ((need >> lane) & 1u) ? (Tacc)lb_value(w) : Tacc(0);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        prefix += v;
-        if (pre) break;
-        j -= 32;
-      }
-      if (lane == 0) lb_store(status + tile, lb_pack(LB_PRE, prefix + tot));
+  block_exclusive_sum<Tacc>(sum, &tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+template <typename Tin, typename Tacc>
+__global__ void __launch_bounds__(SCAN_BLOCK) k_chunk_scan(const Tin* __restrict__ in, Tacc* out,
+                                                           int64_t n, int64_t chunk,
+                                                           const Tacc* __restrict__ partial,
+                                                           bool inclusive) {
+  __shared__ Tacc s[scan_smem_elems<Tacc>()];
+  // offset of this chunk: the totals of the chunks before it
+  Tacc pre = 0;
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += SCAN_BLOCK) pre += partial[b];
+  Tacc carry;
+  block_exclusive_sum<Tacc>(pre, &carry);
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  for (int64_t base = lo; base < hi; base += SCAN_TILE) {
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_BLOCK) {
+      const int64_t j = base + i;
+      s[spad<Tacc>(i)] = j < hi ? (Tacc)in[j] : Tacc(0);
     }
-    if (lane == 0) s_prefix = prefix;
-  }
-  __syncthreads();
-  run += s_prefix;
+    __syncthreads();
+    Tacc loc[SCAN_ITEMS];
+    Tacc sum = 0;
 #pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    const Tacc v = loc[k];
-    s[spad<Tacc>(threadIdx.x * SCAN_ITEMS + k)] = inclusive ? run + v : run;
-    run += v;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      loc[k] = s[spad<Tacc>(threadIdx.x * SCAN_ITEMS + k)];
+      sum += loc[k];
+    }
+    Tacc tot;
+    Tacc run = carry + block_exclusive_sum<Tacc>(sum, &tot);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      const Tacc v = loc[k];
+      s[spad<Tacc>(threadIdx.x * SCAN_ITEMS + k)] = inclusive ? run + v : run;
+      run += v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_BLOCK) {
+      const int64_t j = base + i;
+      if (j < hi) out[j] = s[spad<Tacc>(i)];
+    }
+    carry += tot;
+    __syncthreads();  // s is refilled by the next tile
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_BLOCK) {
-    const int64_t j = base + i;
-    if (j < n) out[j] = s[spad<Tacc>(i)];
-  }
+}
+
+// blocks the GPU holds at once (8 scan blocks per SM), per device
+static int64_t resident_scan_blocks() {
+  static int64_t cached[64] = {0};
+  int dev = 0;
+  AML_CUDA(cudaGetDevice(&dev));
+  if (dev < 64 && cached[dev]) return cached[dev];
+  int sms = 0;
+  AML_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t v = 8 * (int64_t)std::max(sms, 1);
+  if (dev < 64) cached[dev] = v;
+  return v;
 }
 
 template <typename Tin, typename Tacc>
 static void scan_impl(const Tin* in, Tacc* out, int64_t n, bool inclusive, cudaStream_t s) {
   if (n <= 0) return;
-  const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-  if (nb == 1) {
+  if (n <= SCAN_TILE) {
     AML_LAUNCH("k_tile_scan", s,
                k_tile_scan<Tin, Tacc><<<1, SCAN_BLOCK, 0, s>>>(in, out, n, nullptr, inclusive));
     return;
   }
-  DBuf<unsigned long long> status((size_t)nb + 1, s);
-  AML_CUDA(cudaMemsetAsync(status.p, 0, (size_t)(nb + 1) * 8, s));
-  AML_LAUNCH("k_scan_lookback", s,
-             k_scan_lookback<Tin, Tacc><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, out, n, nb,
-                                                                            inclusive, status.p));
-}
-
-uint32_t take_prims_errors() {
-  uint32_t err = 0;
-  AML_CUDA(cudaMemcpyFromSymbol(&err, g_prims_err, 4));
-  if (err) {
-    const uint32_t zero = 0;
-    AML_CUDA(cudaMemcpyToSymbol(g_prims_err, &zero, 4));
-  }
-  return err;
+  const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  const int64_t nblk0 = std::min<int64_t>(tiles, resident_scan_blocks());
+  const int64_t chunk = (tiles + nblk0 - 1) / nblk0 * SCAN_TILE;  // whole tiles per block
+  const int64_t nblk = (n + chunk - 1) / chunk;
+  DBuf<Tacc> part((size_t)nblk, s);
+  AML_LAUNCH("k_chunk_reduce", s,
+             k_chunk_reduce<Tin, Tacc><<<(unsigned)nblk, SCAN_BLOCK, 0, s>>>(in, n, chunk,
+                                                                             part.p));
+  AML_LAUNCH("k_chunk_scan", s,
+             k_chunk_scan<Tin, Tacc><<<(unsigned)nblk, SCAN_BLOCK, 0, s>>>(in, out, n, chunk,
+                                                                           part.p, inclusive));
 }
 
 void scan_i32(const int32_t* in, int32_t* out, int64_t n, bool inclusive, cudaStream_t s) {

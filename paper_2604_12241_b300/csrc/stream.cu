@@ -105,10 +105,8 @@ static void mine_window(aml_stream* st, int64_t w0, int64_t n, int32_t new_from,
   try {
     mine_plain(g, &st->ps, out, st->P, s, 0, new_from, t_new, true);
     AML_CUDA(cudaStreamSynchronize(s));
-    uint32_t err = take_prims_errors();
-    uint32_t gerr = 0;
-    AML_CUDA(cudaMemcpy(&gerr, g->err, 4, cudaMemcpyDeviceToHost));
-    err |= gerr;
+    uint32_t err = 0;
+    AML_CUDA(cudaMemcpy(&err, g->err, 4, cudaMemcpyDeviceToHost));
     AML_REQUIRE(!(err & ERR_TIMEOUT), AML_ETIMEOUT, "a bounded device wait gave up");
     AML_REQUIRE(err == 0, AML_EINTERNAL, "device error word set (" + std::to_string(err) + ")");
   } catch (...) {
