@@ -105,7 +105,7 @@ struct LegCache {
 // Runtime tunables of the mining kernels (none changes any count).
 struct Tuning {
   int32_t own_max = 32;          // windows up to this long are walked by one lane
-  int32_t sg_bucket_mean = 384;  // target leg records per SG bucket
+  int32_t sg_bucket_mean = 192;  // target leg records per SG bucket
   int32_t close_scan_max = 48;   // closing ranges up to this long are scanned
   int32_t block = 256;           // threads per block of the per-edge kernels
 };
@@ -175,6 +175,9 @@ void radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_tmp, uint32_t
 
 void iota_i32(int32_t* out, int64_t n, cudaStream_t s);
 
+// Multiprocessors of the current device (cached per device).
+int sm_count();
+
 inline int bits_for(uint64_t max_value) {
   int b = 1;
   while (b < 64 && (max_value >> b) != 0) ++b;
@@ -217,6 +220,22 @@ __device__ __forceinline__ int32_t lower_t(const int32_t* __restrict__ t, int32_
     if ((int64_t)__ldg(t + mid) < tmin) lo = mid + 1; else hi = mid;
   }
   return lo;
+}
+
+// first index in [lo, p] with t >= tmin, given t[p] >= tmin and t sorted:
+// gallops back from p, then bisects (cost grows with the distance, not with
+// the length of the range)
+__device__ __forceinline__ int32_t lower_t_back(const int32_t* __restrict__ t, int32_t lo,
+                                                int32_t p, int64_t tmin) {
+  int32_t hi = p;  // t[hi] >= tmin
+  int32_t step = 1;
+  while (true) {
+    const int32_t idx = hi - step;
+    if (idx < lo) return lower_t(t, lo, hi, tmin);
+    if ((int64_t)__ldg(t + idx) < tmin) return lower_t(t, idx + 1, hi, tmin);
+    hi = idx;
+    step <<= 1;
+  }
 }
 
 // first i in [lo, hi) with t[i] > tmax

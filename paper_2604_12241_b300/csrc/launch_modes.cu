@@ -59,7 +59,7 @@ void mine_graph_mode(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, 
 
 static void check_tuning(const aml_tuning& t) {
   AML_REQUIRE(t.own_max >= 0 && t.own_max <= 4096, AML_EINVAL, "own_max must be in [0, 4096]");
-  AML_REQUIRE(t.sg_bucket_mean >= 16 && t.sg_bucket_mean <= SG_CAP / 2, AML_EINVAL,
+  AML_REQUIRE(t.sg_bucket_mean >= 16 && t.sg_bucket_mean <= 512, AML_EINVAL,
               "sg_bucket_mean must be in [16, 512]");
   AML_REQUIRE(t.close_scan_max >= 0 && t.close_scan_max <= 4096, AML_EINVAL,
               "close_scan_max must be in [0, 4096]");
@@ -117,7 +117,7 @@ void autotune(aml_graph* g, const aml_pattern_set* ps, int reps, cudaStream_t s,
   float best_ms = time_mines(g, ps, out.p, P, reps, s);
   const std::vector<int> blocks = {128, 256, 512};
   const std::vector<int> owns = {8, 16, 32, 64};
-  const std::vector<int> buckets = {128, 256, 384, 512};
+  const std::vector<int> buckets = {96, 128, 192, 256};
   const std::vector<int> scans = {16, 48, 128};
   auto sweep = [&](int aml_tuning::*field, const std::vector<int>& cands) {
     for (int v : cands) {

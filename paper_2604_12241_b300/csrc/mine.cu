@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(512) k_window_slots(const int32_t* __restrict_
   int32_t p = (int32_t)p64;
   const int32_t rs = __ldg(rstart + p);
   const int32_t tp = __ldg(t + p);
-  const int32_t lbp = lower_t(t, rs, p + 1, (int64_t)tp - delta);
+  const int32_t lbp = lower_t_back(t, rs, p, (int64_t)tp - delta);
   const int32_t deg = p - lbp + 1;
   if (deg_s) deg_s[p] = deg;
   if (df) df[__ldg(eid + p)] = make_int2(deg, 0);
@@ -55,22 +55,6 @@ __global__ void __launch_bounds__(512) k_window_slots(const int32_t* __restrict_
     for (int32_t r = lbq; r < lbp; ++r) d -= (__ldg(next + r) <= p - 1) ? 1 : 0;
   }
   D[p] = d;
-}
-
-// (DEG, FAN) of every slot, stored at its edge id: FAN = DEG - R(p), R(p) =
-// S[p] - S[rs - 1] with S the inclusive prefix sum of the repeat deltas and
-// rs the first slot of p's row
-__global__ void __launch_bounds__(512) k_slot_fan(const int32_t* __restrict__ rstart,
-                                                  const int32_t* __restrict__ eid,
-                                                  const int32_t* __restrict__ deg_s,
-                                                  const int32_t* __restrict__ S, int64_t Ev,
-                                                  int2* __restrict__ df) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= Ev) return;
-  const int32_t rs = rstart[p];
-  const int32_t deg = deg_s[p];
-  const int32_t rep = S[p] - (rs > 0 ? __ldg(S + rs - 1) : 0);
-  df[eid[p]] = make_int2(deg, deg - rep);
 }
 
 // ------------------------------------------------------------------ legs
@@ -469,123 +453,158 @@ __device__ __forceinline__ bool sg_partner(const int4& r, const int4& o, int32_t
   return span <= delta && max(r.w, o.w) >= new_from;
 }
 
+// Groups one bucket's records by key in a shared-memory hash table and
+// credits every leg of a group of two or more with its partners.  CAP
+// records at most; tab = a power of two >= 2n.  The thread that files a key
+// first leads its group: once the counts are known it reserves the group's
+// range of the group array with one block atomic, so no scan over the
+// table is needed.  Then the grouped legs' data are filed group by group
+// and consecutive threads take consecutive group members (a warp's threads
+// mostly walk the same group).
+template <int CAP, int TAB>
+struct SgSmem {
+  int4 grp[CAP];                 // leg_info of grouped legs, by group
+  unsigned long long key[TAB];   // filed keys; later (as uint32) group cursors
+  uint32_t cnt[TAB];             // records per slot
+  uint16_t slot[CAP];            // each record's slot
+  uint16_t pos[CAP];             // record index of each group-array entry
+  uint32_t n_grouped;
+};
+
+template <int CAP, int TAB>
+__device__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRec* __restrict__ R, int n,
+                                int32_t delta, const int32_t* __restrict__ dst,
+                                const int32_t* __restrict__ ts,
+                                unsigned long long* __restrict__ acc, int32_t new_from) {
+  constexpr int PER = (CAP + 255) / 256;  // records per thread (blocks of 256)
+  uint32_t* cur = reinterpret_cast<uint32_t*>(S.key);
+  int tab = 64;
+  while (tab < 2 * n) tab <<= 1;
+  for (int t = threadIdx.x; t < tab; t += blockDim.x) {
+    S.key[t] = ~0ull;
+    S.cnt[t] = 0;
+  }
+  if (threadIdx.x == 0) S.n_grouped = 0;
+  __syncthreads();
+  // file every record under its key; remember which keys this thread filed
+  uint32_t lead = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int i = threadIdx.x + k * (int)blockDim.x;
+    if (i >= n) break;
+    const unsigned long long key = R[i].key;
+    uint32_t h = (uint32_t)mix64(key) & (uint32_t)(tab - 1);
+    for (int probe = 0; probe < tab; ++probe) {  // n < tab: a slot is always found
+      const unsigned long long cur_key = S.key[h];
+      if (cur_key == key) break;
+      if (cur_key == ~0ull) {
+        const unsigned long long old = atomicCAS(&S.key[h], ~0ull, key);
+        if (old == ~0ull) {
+          lead |= 1u << k;
+          break;
+        }
+        if (old == key) break;
+      }
+      h = (h + 1) & (uint32_t)(tab - 1);
+    }
+    S.slot[i] = (uint16_t)h;
+    atomicAdd(&S.cnt[h], 1u);
+  }
+  __syncthreads();
+  // group leaders reserve their group's range (keys are no longer read)
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int i = threadIdx.x + k * (int)blockDim.x;
+    if (i >= n) break;
+    if ((lead >> k) & 1u) {
+      const uint32_t h = S.slot[i];
+      const uint32_t c = S.cnt[h];
+      if (c >= 2) cur[h] = atomicAdd(&S.n_grouped, c);
+    }
+  }
+  __syncthreads();
+  const uint32_t n_grouped = S.n_grouped;
+  if (n_grouped == 0) return;
+  // the grouped legs' data, group by group (cursor ends at the group's end)
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint32_t h = S.slot[i];
+    if (S.cnt[h] >= 2) {
+      const uint32_t at = atomicAdd(&cur[h], 1u);
+      S.grp[at] = leg_info(R[i], dst, ts);
+      S.pos[at] = (uint16_t)i;
+    }
+  }
+  __syncthreads();
+  for (uint32_t p = threadIdx.x; p < n_grouped; p += blockDim.x) {
+    const int i = S.pos[p];
+    const uint32_t h = S.slot[i];
+    const uint32_t c = S.cnt[h];
+    const int4 own = S.grp[p];
+    const uint32_t end = cur[h];
+    unsigned long long k = 0;
+    for (uint32_t j = end - c; j < end; ++j)
+      if (sg_partner(own, S.grp[j], delta, new_from)) ++k;
+    if (k) sg_credit(acc, R[i], k);
+  }
+}
+
+// One block per bucket of up to SG_CAP records; larger buckets are listed
+// in overflow (count at overflow[0]) for k_sg_bucket_big.
 __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ rec,
                                                    const int64_t* __restrict__ boff,
                                                    int32_t delta, const int32_t* __restrict__ dst,
                                                    const int32_t* __restrict__ ts,
                                                    unsigned long long* __restrict__ acc,
-                                                   int32_t new_from) {
-  extern __shared__ __align__(16) unsigned char sg_smem[];
-  int4* s_grp = reinterpret_cast<int4*>(sg_smem);  // leg_info of grouped legs, by group
-  unsigned long long* s_key = reinterpret_cast<unsigned long long*>(s_grp + SG_CAP);
-  uint32_t* s_cur = reinterpret_cast<uint32_t*>(s_key);  // group cursors, once keys are filed
-  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_key + SG_TAB);
-  uint16_t* s_slot = reinterpret_cast<uint16_t*>(s_cnt + SG_TAB);
-  uint16_t* s_pos = s_slot + SG_CAP;
+                                                   int32_t new_from,
+                                                   uint32_t* __restrict__ overflow) {
+  __shared__ SgSmem<SG_CAP, SG_TAB> S;
   const int64_t base = boff[blockIdx.x];
-  const int n = (int)(boff[blockIdx.x + 1] - base);
+  const int64_t n = boff[blockIdx.x + 1] - base;
   if (n < 2) return;
-  const LegRec* R = rec + base;
   if (n > SG_CAP) {
-    // oversized bucket (a very large pair): compare every record with all
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const LegRec r = R[i];
-      const int4 ri = leg_info(r, dst, ts);
-      unsigned long long c = 0;
-      for (int j = 0; j < n; ++j) {
-        const LegRec o = R[j];
-        if (o.key == r.key && sg_partner(ri, leg_info(o, dst, ts), delta, new_from)) ++c;
-      }
-      sg_credit(acc, r, c);
-    }
+    if (threadIdx.x == 0) overflow[1 + atomicAdd(overflow, 1u)] = blockIdx.x;
     return;
   }
-  // a table of at least twice the records (load <= 0.5), 256 slots or more
-  int tab = 256;
-  while (tab < 2 * n) tab <<= 1;
-  for (int t = threadIdx.x; t < tab; t += blockDim.x) {
-    s_key[t] = ~0ull;
-    s_cnt[t] = 0;
-  }
-  __syncthreads();
-  // file every record under its key
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const unsigned long long key = R[i].key;
-    uint32_t h = (uint32_t)mix64(key) & (uint32_t)(tab - 1);
-    for (int probe = 0; probe < tab; ++probe) {  // n < tab: a slot is always found
-      const unsigned long long cur = s_key[h];
-      if (cur == key) break;
-      if (cur == ~0ull) {
-        const unsigned long long old = atomicCAS(&s_key[h], ~0ull, key);
-        if (old == ~0ull || old == key) break;
+  sg_group_bucket<SG_CAP, SG_TAB>(S, rec + base, (int)n, delta, dst, ts, acc, new_from);
+}
+
+// The listed buckets, a few blocks looping over the list (the count is read
+// on the device); buckets beyond SG_CAP_BIG compare every record with all.
+__global__ void __launch_bounds__(256) k_sg_bucket_big(const LegRec* __restrict__ rec,
+                                                       const int64_t* __restrict__ boff,
+                                                       int32_t delta,
+                                                       const int32_t* __restrict__ dst,
+                                                       const int32_t* __restrict__ ts,
+                                                       unsigned long long* __restrict__ acc,
+                                                       int32_t new_from,
+                                                       const uint32_t* __restrict__ overflow) {
+  extern __shared__ __align__(16) unsigned char sg_big_smem[];
+  auto& S = *reinterpret_cast<SgSmem<SG_CAP_BIG, SG_TAB_BIG>*>(sg_big_smem);
+  const uint32_t n_over = overflow[0];
+  for (uint32_t k = blockIdx.x; k < n_over; k += gridDim.x) {
+    const uint32_t b = overflow[1 + k];
+    const int64_t base = boff[b];
+    const int64_t n = boff[b + 1] - base;
+    const LegRec* R = rec + base;
+    if (n <= SG_CAP_BIG) {
+      sg_group_bucket<SG_CAP_BIG, SG_TAB_BIG>(S, R, (int)n, delta, dst, ts, acc, new_from);
+    } else {
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const LegRec r = R[i];
+        const int4 ri = leg_info(r, dst, ts);
+        unsigned long long c = 0;
+        for (int64_t j = 0; j < n; ++j) {
+          const LegRec o = R[j];
+          if (o.key == r.key && sg_partner(ri, leg_info(o, dst, ts), delta, new_from)) ++c;
+        }
+        sg_credit(acc, r, c);
       }
-      h = (h + 1) & (uint32_t)(tab - 1);
     }
-    s_slot[i] = (uint16_t)h;
-    atomicAdd(&s_cnt[h], 1u);
-  }
-  __syncthreads();
-  // group starts: exclusive prefix of the counts of slots holding two or
-  // more records (tab / 256 slots per thread); they overwrite the keys,
-  // which are no longer read
-  __shared__ uint32_t s_wsum[8];
-  {
-    constexpr int PER_MAX = SG_TAB / 256;
-    const int per = tab >> 8;
-    uint32_t loc[PER_MAX], sum = 0;
-#pragma unroll
-    for (int k = 0; k < PER_MAX; ++k) {
-      const uint32_t c = k < per ? s_cnt[threadIdx.x * per + k] : 0u;
-      loc[k] = c >= 2 ? c : 0u;
-      sum += loc[k];
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = sum;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_wsum[warp] = x;
-    __syncthreads();
-    uint32_t before = x - sum;
-    for (int w = 0; w < warp; ++w) before += s_wsum[w];
-#pragma unroll
-    for (int k = 0; k < PER_MAX; ++k)
-      if (k < per) {
-        s_cur[threadIdx.x * per + k] = before;  // becomes the group's end after the fill
-        before += loc[k];
-      }
-  }
-  __syncthreads();
-  uint32_t n_grouped = 0;
-#pragma unroll
-  for (int w = 0; w < 8; ++w) n_grouped += s_wsum[w];
-  if (n_grouped == 0) return;
-  // the legs of groups of two or more, group by group: their data, slot and
-  // record index
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const uint32_t h = s_slot[i];
-    if (s_cnt[h] >= 2) {
-      const uint32_t pos = atomicAdd(&s_cur[h], 1u);
-      s_grp[pos] = leg_info(R[i], dst, ts);
-      s_pos[pos] = (uint16_t)i;
-    }
-  }
-  __syncthreads();
-  // partners inside each group; consecutive threads take consecutive group
-  // members, so a warp's threads mostly walk the same group
-  for (uint32_t p = threadIdx.x; p < n_grouped; p += blockDim.x) {
-    const int i = s_pos[p];
-    const uint32_t h = s_slot[i];
-    const uint32_t c = s_cnt[h];
-    const int4 own = s_grp[p];
-    const uint32_t end = s_cur[h];
-    unsigned long long k = 0;
-    for (uint32_t j = end - c; j < end; ++j)
-      if (sg_partner(own, s_grp[j], delta, new_from)) ++k;
-    if (k) sg_credit(acc, R[i], k);
+    __syncthreads();  // the shared table is reused by the next bucket
   }
 }
+
+size_t sg_big_smem_bytes() { return sizeof(SgSmem<SG_CAP_BIG, SG_TAB_BIG>); }
 
 // ---------------------------------------------------------------- cycles
 //

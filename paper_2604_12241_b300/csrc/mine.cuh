@@ -8,13 +8,12 @@ namespace aml {
 constexpr int MAX_COLS = 64;    // columns per pattern set
 constexpr int MAX_DELTAS = 16;  // distinct windows per pattern set
 constexpr int MAX_CYCLE = 8;    // longest cycle
-constexpr int SG_CAP = 1024;    // leg records one SG bucket block groups in shared memory
-constexpr int SG_TAB = 2048;    // its hash-table slots (load <= 0.5)
+constexpr int SG_CAP = 512;        // leg records one SG bucket block groups in shared memory
+constexpr int SG_TAB = 1024;       // its hash-table slots (load <= 0.5)
+constexpr int SG_CAP_BIG = 4096;   // the same for the larger buckets (k_sg_bucket_big)
+constexpr int SG_TAB_BIG = 8192;
 constexpr int SG_PART_ITEMS = 4;     // records per thread in k_sg_partition
 constexpr int ASM_BLOCK = 128;       // rows per k_assemble block
-// k_sg_bucket: group data, hash keys (later group cursors), slot counts,
-// each record's slot and group position
-constexpr size_t SG_SMEM = (size_t)SG_CAP * 16 + (size_t)SG_TAB * (8 + 4) + (size_t)SG_CAP * (2 + 2);
 
 // Read-only view of a device graph, passed by value to kernels.
 struct GraphView {
@@ -114,8 +113,9 @@ struct CycFrontier {
 __global__ void k_window_slots(const int32_t* rstart, const int32_t* t, const int32_t* eid,
                                const int32_t* prev, const int32_t* next, int64_t Ev,
                                int32_t delta, int32_t* deg_s, int32_t* D, int2* df);
-__global__ void k_slot_fan(const int32_t* rstart, const int32_t* eid, const int32_t* deg_s,
-                           const int32_t* S, int64_t Ev, int2* df);
+// (DEG, FAN) of every edge for one window and direction, stored at the
+// edge id (self-loop entries untouched); two launches on s.
+void fan_per_edge(const Adj& a, int64_t Ev, int32_t delta, int2* df, cudaStream_t s);
 __global__ void k_leg_count(GraphView g, int32_t delta, int32_t* L, const int2* crng,
                             int32_t* L2, int32_t* L_new, int2* qwin, int32_t* qcb);
 __global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);
@@ -128,7 +128,11 @@ __global__ void k_sg_hist(const LegRec* rec, int64_t n, int bits, uint32_t* hist
 __global__ void k_mark_nodes(const int32_t* node_of, int64_t from, int64_t E, uint32_t* mask);
 __global__ void k_sg_bucket(const LegRec* rec, const int64_t* boff, int32_t delta,
                             const int32_t* dst, const int32_t* ts, unsigned long long* acc,
-                            int32_t new_from);
+                            int32_t new_from, uint32_t* overflow);
+__global__ void k_sg_bucket_big(const LegRec* rec, const int64_t* boff, int32_t delta,
+                                const int32_t* dst, const int32_t* ts, unsigned long long* acc,
+                                int32_t new_from, const uint32_t* overflow);
+size_t sg_big_smem_bytes();
 __global__ void k_close_range(GraphView g, int32_t delta, int2* rng);
 __global__ void k_cyc_level(GraphView g, int32_t delta, int K, int j, CycFrontier F, int64_t n,
                             const int2* close_rng, CycleSlots slots, unsigned long long* acc,

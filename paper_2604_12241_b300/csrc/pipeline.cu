@@ -120,20 +120,13 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       const Adj& a = dir == 0 ? g->out : g->in;
       keep_df.emplace_back((size_t)E, s);
       int2* df = keep_df.back().p;
-      DBuf<int32_t> deg_s, D;
       if (fan) {
-        deg_s = DBuf<int32_t>((size_t)Ev, s);
-        D = DBuf<int32_t>((size_t)Ev, s);
-      }
-      AML_LAUNCH("k_window_slots", s,
-                 k_window_slots<<<grid_for(Ev, B), B, 0, s>>>(
-                     a.rstart, a.t, a.eid, a.prev, a.next, Ev, wp.delta, deg_s.p, D.p,
-                     fan ? nullptr : df));
-      if (fan) {
-        scan_i32(D.p, D.p, Ev, true, s);
-        AML_LAUNCH("k_slot_fan", s,
-                   k_slot_fan<<<grid_for(Ev, B), B, 0, s>>>(a.rstart, a.eid, deg_s.p, D.p, Ev,
-                                                            df));
+        fan_per_edge(a, Ev, wp.delta, df, s);
+      } else {
+        AML_LAUNCH("k_window_slots", s,
+                   k_window_slots<<<grid_for(Ev, B), B, 0, s>>>(a.rstart, a.t, a.eid, a.prev,
+                                                                a.next, Ev, wp.delta, nullptr,
+                                                                nullptr, df));
       }
       (dir == 0 ? P.df_out : P.df_in)[w] = df;
     }
@@ -272,17 +265,24 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       AML_LAUNCH("k_sg_partition", s,
                  k_sg_partition<<<grid_for(nl, 256 * SG_PART_ITEMS), 256, 0, s>>>(
                      rec.p, nl, S.bits, boff.p, hist.p, part.p));
+      // buckets beyond SG_CAP records: listed by k_sg_bucket, grouped by
+      // k_sg_bucket_big (one large-table block per SM)
+      DBuf<uint32_t> overflow((size_t)nb + 1, s);
+      AML_CUDA(cudaMemsetAsync(overflow.p, 0, sizeof(uint32_t), s));
       static bool smem_set[64] = {false};  // per device
       if (g->device >= 64 || !smem_set[g->device]) {
-        AML_CUDA(cudaFuncSetAttribute(k_sg_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SG_SMEM));
+        AML_CUDA(cudaFuncSetAttribute(k_sg_bucket_big,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sg_big_smem_bytes()));
         if (g->device < 64) smem_set[g->device] = true;
       }
+      unsigned long long* acc_sg = acc.p + (int64_t)wp.sg_slot * E;
       AML_LAUNCH("k_sg_bucket", s,
-                 k_sg_bucket<<<(unsigned)nb, 256, SG_SMEM, s>>>(part.p, boff.p, wp.delta, gv.dst,
-                                                              gv.ts,
-                                                              acc.p + (int64_t)wp.sg_slot * E,
-                                                              new_from));
+                 k_sg_bucket<<<(unsigned)nb, 256, 0, s>>>(part.p, boff.p, wp.delta, gv.dst, gv.ts,
+                                                          acc_sg, new_from, overflow.p));
+      AML_LAUNCH("k_sg_bucket_big", s,
+                 k_sg_bucket_big<<<(unsigned)sm_count(), 256, sg_big_smem_bytes(), s>>>(
+                     part.p, boff.p, wp.delta, gv.dst, gv.ts, acc_sg, new_from, overflow.p));
     }
     // 4. cycles of length >= 3: one persistent cost-binned launch ...
     if (wp.K >= 3 && persistent) {

@@ -197,18 +197,20 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_chunk_scan(const Tin* __restrict
   }
 }
 
-// blocks the GPU holds at once (8 scan blocks per SM), per device
-static int64_t resident_scan_blocks() {
-  static int64_t cached[64] = {0};
+int sm_count() {
+  static int cached[64] = {0};
   int dev = 0;
   AML_CUDA(cudaGetDevice(&dev));
   if (dev < 64 && cached[dev]) return cached[dev];
   int sms = 0;
   AML_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int64_t v = 8 * (int64_t)std::max(sms, 1);
-  if (dev < 64) cached[dev] = v;
-  return v;
+  sms = std::max(sms, 1);
+  if (dev < 64) cached[dev] = sms;
+  return sms;
 }
+
+// blocks the GPU holds at once (8 scan blocks per SM)
+static int64_t resident_scan_blocks() { return 8 * (int64_t)sm_count(); }
 
 template <typename Tin, typename Tacc>
 static void scan_impl(const Tin* in, Tacc* out, int64_t n, bool inclusive, cudaStream_t s) {

@@ -231,3 +231,30 @@ def test_sg_pair_larger_than_a_bucket():
     got = gpu_counts(src, dst, ts, n, P.from_oracle_columns(cols))
     np.testing.assert_array_equal(got, want)
     assert got[:, 0].max() > 1000
+
+
+def test_hub_rows_span_many_chunks():
+    """Two hubs with ~6,000 out- and ~6,000 in-slots each (repeated
+    counterparties, tied timestamps) plus background: their rows cross several
+    chunks of the DEG/FAN scan, including chunks in which no row starts."""
+    rng = np.random.default_rng(11)
+    n = 400
+    src, dst, ts = [], [], []
+    for hub in (0, 1):
+        for _ in range(12_000):
+            c = int(rng.integers(2, 2 + 150 + 100 * hub))
+            t = int(rng.integers(0, 4_000))
+            if rng.random() < 0.5:
+                src.append(hub); dst.append(c)
+            else:
+                src.append(c); dst.append(hub)
+            ts.append(t)
+    for _ in range(4_000):
+        a, b = rng.integers(0, n, 2)
+        src.append(int(a)); dst.append(int(b)); ts.append(int(rng.integers(0, 4_000)))
+    src, dst, ts = (np.asarray(x, np.int32) for x in (src, dst, ts))
+    cols = [(f, w) for w in (0, 7, 60, 900, 10_000)
+            for f in ("deg_out", "deg_in", "fan_out", "fan_in")]
+    want = oracle.OracleGraph(src, dst, ts, n).count_all(cols)
+    got = gpu_counts(src, dst, ts, n, P.from_oracle_columns(cols))
+    np.testing.assert_array_equal(got, want)
