@@ -222,22 +222,6 @@ __device__ __forceinline__ int32_t lower_t(const int32_t* __restrict__ t, int32_
   return lo;
 }
 
-// first index in [lo, p] with t >= tmin, given t[p] >= tmin and t sorted:
-// gallops back from p, then bisects (cost grows with the distance, not with
-// the length of the range)
-__device__ __forceinline__ int32_t lower_t_back(const int32_t* __restrict__ t, int32_t lo,
-                                                int32_t p, int64_t tmin) {
-  int32_t hi = p;  // t[hi] >= tmin
-  int32_t step = 1;
-  while (true) {
-    const int32_t idx = hi - step;
-    if (idx < lo) return lower_t(t, lo, hi, tmin);
-    if ((int64_t)__ldg(t + idx) < tmin) return lower_t(t, idx + 1, hi, tmin);
-    hi = idx;
-    step <<= 1;
-  }
-}
-
 // first i in [lo, hi) with t[i] > tmax
 __device__ __forceinline__ int32_t upper_t(const int32_t* __restrict__ t, int32_t lo, int32_t hi,
                                            int64_t tmax) {

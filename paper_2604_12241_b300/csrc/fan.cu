@@ -8,15 +8,15 @@
 //   R(p) - R(p-1) = [prev(p) >= lb(p)] - #{r in [lb(p-1), lb(p)) : next(r) <= p-1}
 // (the window gains p and drops [lb(p-1), lb(p))), with R(row start) = 0.
 //
-// Two launches over contiguous chunks of slots (one tile each), one block per
-// chunk:
-//   k_fan_reduce: lb, DEG and the delta of every slot, and per chunk the sum
-//     of the deltas after its last row start (all of them when no row
-//     starts inside) with a flag telling whether a row starts inside;
-//   k_fan_scan: the carry into its chunk from those chunk sums (walking back
-//     to the nearest chunk where a row starts), then a segmented scan of the
-//     deltas (restarting at row starts), and (DEG, FAN) stored at the edge
-//     id of every slot.
+// Two launches over contiguous chunks of slots:
+//   k_fan_reduce (a thread per slot, a block per chunk of FAN_RBLOCK): lb,
+//     DEG and the delta of every slot, and per chunk the sum of the deltas
+//     after its last row start (all of them when no row starts inside) with
+//     a flag telling whether a row starts inside;
+//   k_fan_scan (a block per tile of FAN_TILE slots): the carry into its tile
+//     from those chunk sums (back to the nearest chunk where a row starts),
+//     then a segmented scan of the deltas (restarting at row starts), and
+//     (DEG, FAN) stored at the edge id of every slot.
 #include <algorithm>
 
 #include "aml_internal.cuh"
@@ -27,6 +27,7 @@ namespace aml {
 
 namespace {
 
+constexpr int FAN_RBLOCK = 512;  // slots per k_fan_reduce block (one each)
 constexpr int FAN_BLOCK = 256;
 constexpr int FAN_ITEMS = 8;
 constexpr int FAN_TILE = FAN_BLOCK * FAN_ITEMS;
@@ -81,46 +82,43 @@ __device__ Seg seg_scan_block(Seg x, Seg* total) {
   return r;
 }
 
-__global__ void __launch_bounds__(FAN_BLOCK) k_fan_reduce(const int32_t* __restrict__ rstart,
-                                                          const int32_t* __restrict__ t,
-                                                          const int32_t* __restrict__ prev,
-                                                          const int32_t* __restrict__ next,
-                                                          int64_t Ev, int32_t delta,
-                                                          int64_t chunk,
-                                                          int32_t* __restrict__ deg_s,
-                                                          int32_t* __restrict__ D,
-                                                          int2* __restrict__ chunk_sum) {
-  __shared__ int32_t s_sum[FAN_BLOCK / 32];
+// one slot per thread; chunks of FAN_RBLOCK slots
+__global__ void __launch_bounds__(FAN_RBLOCK) k_fan_reduce(const int32_t* __restrict__ rstart,
+                                                           const int32_t* __restrict__ t,
+                                                           const int32_t* __restrict__ prev,
+                                                           const int32_t* __restrict__ next,
+                                                           int64_t Ev, int32_t delta,
+                                                           int32_t* __restrict__ deg_s,
+                                                           int32_t* __restrict__ D,
+                                                           int2* __restrict__ chunk_sum) {
+  __shared__ int32_t s_sum[FAN_RBLOCK / 32];
   const int lane = threadIdx.x & 31;
-  const int64_t c0 = (int64_t)blockIdx.x * chunk;
-  const int64_t c1 = c0 + chunk < Ev ? c0 + chunk : Ev;
+  const int64_t c0 = (int64_t)blockIdx.x * FAN_RBLOCK;
+  const int64_t c1 = c0 + FAN_RBLOCK < Ev ? c0 + FAN_RBLOCK : Ev;
   const int32_t last_rs = rstart[c1 - 1];  // the last row start at or before the chunk's end
   const int64_t from = last_rs > c0 ? last_rs : c0;
-  int32_t u = 0;
-  for (int64_t base = c0; base < c1; base += FAN_BLOCK) {
-    const int64_t p64 = base + threadIdx.x;
-    const bool in = p64 < c1;
-    const int32_t p = (int32_t)p64;
-    int32_t rs = 0, lbp = 0;
-    if (in) {
-      rs = __ldg(rstart + p);
-      lbp = lower_t_back(t, rs, p, (int64_t)__ldg(t + p) - delta);
-      deg_s[p] = p - lbp + 1;
+  const int64_t p64 = c0 + threadIdx.x;
+  const bool in = p64 < c1;
+  const int32_t p = (int32_t)p64;
+  int32_t rs = 0, lbp = 0, u = 0;
+  if (in) {
+    rs = __ldg(rstart + p);
+    lbp = lower_t(t, rs, p + 1, (int64_t)__ldg(t + p) - delta);
+    deg_s[p] = p - lbp + 1;
+  }
+  // lb(p-1) is the lower lane's lb when that lane holds slot p-1 of the row
+  const int32_t lb_lower = __shfl_up_sync(0xffffffffu, lbp, 1);
+  if (in) {
+    int32_t d = 0;
+    if (p > rs) {
+      const int32_t lbq =
+          lane > 0 ? lb_lower
+                   : lower_t(t, rs, min(lbp + 1, p), (int64_t)__ldg(t + p - 1) - delta);
+      d = (__ldg(prev + p) >= lbp) ? 1 : 0;
+      for (int32_t r = lbq; r < lbp; ++r) d -= (__ldg(next + r) <= p - 1) ? 1 : 0;
     }
-    // lb(p-1) is the lower lane's lb when that lane holds slot p-1 of the row
-    const int32_t lb_lower = __shfl_up_sync(0xffffffffu, lbp, 1);
-    if (in) {
-      int32_t d = 0;
-      if (p > rs) {
-        const int32_t lbq =
-            lane > 0 ? lb_lower
-                     : lower_t(t, rs, min(lbp + 1, p), (int64_t)__ldg(t + p - 1) - delta);
-        d = (__ldg(prev + p) >= lbp) ? 1 : 0;
-        for (int32_t r = lbq; r < lbp; ++r) d -= (__ldg(next + r) <= p - 1) ? 1 : 0;
-      }
-      D[p] = d;
-      if (p64 >= from) u += d;
-    }
+    D[p] = d;
+    if (p64 >= from) u = d;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
@@ -128,7 +126,7 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_reduce(const int32_t* __restr
   __syncthreads();
   if (threadIdx.x == 0) {
     int32_t tot = 0;
-    for (int w = 0; w < FAN_BLOCK / 32; ++w) tot += s_sum[w];
+    for (int w = 0; w < FAN_RBLOCK / 32; ++w) tot += s_sum[w];
     chunk_sum[blockIdx.x] = make_int2(tot, last_rs >= c0 ? 1 : 0);
   }
 }
@@ -137,24 +135,32 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restric
                                                         const int32_t* __restrict__ eid,
                                                         const int32_t* __restrict__ deg_s,
                                                         const int32_t* __restrict__ D,
-                                                        int64_t Ev, int64_t chunk,
+                                                        int64_t Ev,
                                                         const int2* __restrict__ chunk_sum,
                                                         int2* __restrict__ df) {
   __shared__ int32_t s_v[FAN_SMEM];
   __shared__ uint8_t s_h[FAN_SMEM];
   __shared__ int32_t s_carry;
-  const int64_t c0 = (int64_t)blockIdx.x * chunk;
-  const int64_t c1 = c0 + chunk < Ev ? c0 + chunk : Ev;
-  if (threadIdx.x == 0) {
-    // deltas of the row running into the chunk: walk back to the nearest
-    // chunk where a row starts (chunk 0 always has one: slot 0)
+  const int64_t c0 = (int64_t)blockIdx.x * FAN_TILE;
+  const int64_t c1 = c0 + FAN_TILE < Ev ? c0 + FAN_TILE : Ev;
+  if (threadIdx.x < 32) {
+    // deltas of the row running into the tile: the sums of the reduce
+    // chunks before it back to the nearest one where a row starts (chunk 0
+    // always has one: slot 0), 32 chunks per step
+    const int lane = threadIdx.x;
     int32_t v = 0;
-    for (int64_t c = (int64_t)blockIdx.x - 1; c >= 0; --c) {
-      const int2 cs = chunk_sum[c];
-      v += cs.x;
-      if (cs.y) break;
+    for (int64_t top = c0 / FAN_RBLOCK - 1; top >= 0; top -= 32) {
+      const int64_t c = top - lane;
+      const int2 cs = c >= 0 ? chunk_sum[c] : make_int2(0, 1);
+      const unsigned starts = __ballot_sync(0xffffffffu, cs.y != 0);
+      const int first = starts ? __ffs(starts) - 1 : 31;  // lanes [0, first] count
+      int32_t x = lane <= first ? cs.x : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      v += x;
+      if (starts) break;
     }
-    s_carry = v;
+    if (lane == 0) s_carry = v;
   }
   __syncthreads();
   Seg run{0, s_carry};
@@ -201,19 +207,17 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restric
 
 void fan_per_edge(const Adj& a, int64_t Ev, int32_t delta, int2* df, cudaStream_t s) {
   if (Ev <= 0) return;
-  // one tile per chunk: many short blocks balance rows of very different
-  // cost (hub rows) across the SMs
-  const int64_t chunk = FAN_TILE;
-  const int64_t nblk = (Ev + chunk - 1) / chunk;
+  const int64_t n_red = (Ev + FAN_RBLOCK - 1) / FAN_RBLOCK;
+  const int64_t n_tiles = (Ev + FAN_TILE - 1) / FAN_TILE;
   DBuf<int32_t> deg_s((size_t)Ev, s), D((size_t)Ev, s);
-  DBuf<int2> sums((size_t)nblk, s);
+  DBuf<int2> sums((size_t)n_red, s);
   AML_LAUNCH("k_fan_reduce", s,
-             k_fan_reduce<<<(unsigned)nblk, FAN_BLOCK, 0, s>>>(a.rstart, a.t, a.prev, a.next, Ev,
-                                                               delta, chunk, deg_s.p, D.p,
-                                                               sums.p));
+             k_fan_reduce<<<(unsigned)n_red, FAN_RBLOCK, 0, s>>>(a.rstart, a.t, a.prev, a.next,
+                                                                 Ev, delta, deg_s.p, D.p,
+                                                                 sums.p));
   AML_LAUNCH("k_fan_scan", s,
-             k_fan_scan<<<(unsigned)nblk, FAN_BLOCK, 0, s>>>(a.rstart, a.eid, deg_s.p, D.p, Ev,
-                                                             chunk, sums.p, df));
+             k_fan_scan<<<(unsigned)n_tiles, FAN_BLOCK, 0, s>>>(a.rstart, a.eid, deg_s.p, D.p,
+                                                                Ev, sums.p, df));
 }
 
 }  // namespace aml

@@ -8,9 +8,11 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <type_traits>
 
 #include "aml_internal.cuh"
 #include "mine.cuh"
+#include "profile.cuh"
 
 namespace aml {
 
@@ -42,7 +44,7 @@ __global__ void __launch_bounds__(512) k_window_slots(const int32_t* __restrict_
   int32_t p = (int32_t)p64;
   const int32_t rs = __ldg(rstart + p);
   const int32_t tp = __ldg(t + p);
-  const int32_t lbp = lower_t_back(t, rs, p, (int64_t)tp - delta);
+  const int32_t lbp = lower_t(t, rs, p + 1, (int64_t)tp - delta);
   const int32_t deg = p - lbp + 1;
   if (deg_s) deg_s[p] = deg;
   if (df) df[__ldg(eid + p)] = make_int2(deg, 0);
@@ -133,13 +135,15 @@ __device__ __forceinline__ int32_t cycle_bound(const GraphView& g, const int2* c
 // With L_new (delta counting): L_new[a] = legs from a whose second edge is new.
 // qwin[a] = a's window slots [q0, q1) in dst(a)'s out-list and, with crng,
 // qcb[a] = its cycle bound, kept for the emission.
+template <int NS>
 __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
                                                    int32_t* __restrict__ L,
                                                    const int2* __restrict__ crng,
                                                    int32_t* __restrict__ L2,
                                                    int32_t* __restrict__ L_new,
                                                    int2* __restrict__ qwin,
-                                                   int32_t* __restrict__ qcb) {
+                                                   int32_t* __restrict__ qcb,
+                                                   SubWindows sub) {
   int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a64 >= g.E) return;
   int32_t a = (int32_t)a64;
@@ -147,6 +151,9 @@ __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
   if (x == h) {
     L[a] = 0;
     qwin[a] = make_int2(0, 0);
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+      if (i < sub.n && sub.gs_from[i]) sub.gs_from[i][a] = 0;
     if (L2) {
       L2[a] = 0;
       qcb[a] = 0;
@@ -160,6 +167,14 @@ __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
   const int32_t ta = g.ts[a];
   const int32_t hs = g.optr[h], he = g.optr[h + 1];
   L[a] = (q1 - q0) - pair_after(g.onnbr, g.ont, g.oneid, hs, he, x, ta, a, delta);
+  // smaller windows: the prefix of the window within their delta
+#pragma unroll
+  for (int i = 0; i < NS; ++i)
+    if (i < sub.n && sub.gs_from[i]) {
+      const int32_t di = sub.delta[i];
+      const int32_t q1i = upper_t(g.ot, q0, q1, (int64_t)ta + di);
+      sub.gs_from[i][a] = (q1i - q0) - pair_after(g.onnbr, g.ont, g.oneid, hs, he, x, ta, a, di);
+    }
   if (L_new) {
     const int32_t qn = after_edge(g.ot, g.oeid, q0, q1, g.t_new, g.new_from - 1);
     int32_t back = 0;
@@ -274,11 +289,30 @@ __device__ __forceinline__ void sg_record(const LegSink& S, bool leg, int64_t po
 // with records, also counts them into the SG buckets.  Windows of up to 32
 // slots are written by their own lane; longer ones (hub accounts) by the
 // whole warp, 32 slots at a time, with ballots keeping the output order.
+// smaller windows: GS legs ending with b, and 2-cycles (a slot returning to
+// the anchor's source), when the pair spans at most their delta
+template <int NS>
+__device__ __forceinline__ void sub_leg_credit(const SubWindows& sub, bool leg, int32_t a,
+                                               int32_t b, int32_t span) {
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    if (i >= sub.n || span > sub.delta[i]) continue;
+    if (leg) {
+      if (sub.gs_in[i]) atomicAdd(sub.gs_in[i] + b, 1);
+    } else if (sub.cyc2[i]) {
+      atomicAdd(sub.cyc2[i] + a, 1ull);
+      atomicAdd(sub.cyc2[i] + b, 1ull);
+    }
+  }
+}
+
+template <int NS>
 __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, const int2* __restrict__ qwin,
                                                   const int32_t* __restrict__ qcb,
                                                   const int64_t* __restrict__ off, LegSink S,
                                                   unsigned long long* __restrict__ acc_cyc2,
-                                                  int32_t* __restrict__ gs_in, int32_t own_max) {
+                                                  int32_t* __restrict__ gs_in, int32_t own_max,
+                                                  SubWindows sub) {
   const int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
@@ -318,6 +352,7 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, const int2* __res
     const bool leg = in && y != x;
     const int32_t tb = in ? __ldg(g.ot + q) : 0;
     if (S.rec) sg_record(S, leg, o, a, b, x, h, y, ta, tb, g.N, S.bits);
+    if (NS > 0 && in) sub_leg_credit<NS>(sub, leg, a, b, tb - ta);
     if (leg) {
       if (gs_in && b >= g.new_from) atomicAdd(gs_in + b, 1);
       ++o;
@@ -354,6 +389,7 @@ __global__ void __launch_bounds__(512) k_leg_emit(GraphView g, const int2* __res
       const unsigned m = __ballot_sync(0xffffffffu, leg);
       const int32_t tb = in ? __ldg(g.ot + q) : 0;
       if (S.rec) sg_record(S, leg, ho + __popc(m & lt), ha, b, hx, hh, y, hta, tb, g.N, S.bits);
+      if (NS > 0 && in) sub_leg_credit<NS>(sub, leg, ha, b, tb - hta);
       if (leg) {
         if (gs_in && b >= g.new_from) atomicAdd(gs_in + b, 1);
       } else if (in && acc_cyc2 && b >= g.new_from) {
@@ -442,15 +478,37 @@ __device__ __forceinline__ int4 leg_info(const LegRec& r, const int32_t* dst, co
   return make_int4(__ldg(dst + r.a), __ldg(ts + r.a), __ldg(ts + r.b), r.b);
 }
 
-// two legs of one (s, d) key form an SG instance: different intermediaries
-// (which also excludes the leg itself) and all four edges within delta;
-// delta counting keeps the pairs whose latest edge -- one of the two gather
-// edges -- is new
-__device__ __forceinline__ bool sg_partner(const int4& r, const int4& o, int32_t delta,
-                                           int32_t new_from) {
-  if (o.x == r.x) return false;
-  const int64_t span = (int64_t)max(r.z, o.z) - (int64_t)min(r.y, o.y);
-  return span <= delta && max(r.w, o.w) >= new_from;
+// two legs of one (s, d) key form an SG instance within a window when their
+// intermediaries differ (which also excludes the leg itself) and all four
+// edges lie within its delta; delta counting keeps the pairs whose latest
+// edge -- one of the two gather edges -- is new.  The span of the pair, or
+// INT64_MAX when it is no instance at all.
+__device__ __forceinline__ int64_t sg_span(const int4& r, const int4& o, int32_t new_from) {
+  if (o.x == r.x || max(r.w, o.w) < new_from) return INT64_MAX;
+  return (int64_t)max(r.z, o.z) - (int64_t)min(r.y, o.y);
+}
+
+// partners of `own` among group entries [j0, j1), per window, credited to
+// the leg's two edges
+template <int NS>
+__device__ __forceinline__ void sg_count_partners(const int4* grp, uint32_t j0, uint32_t j1,
+                                                  const int4& own, const LegRec& r,
+                                                  int32_t delta, int32_t new_from,
+                                                  unsigned long long* acc,
+                                                  const SubWindows& sub) {
+  unsigned long long k = 0, ks[NS > 0 ? NS : 1] = {};
+  for (uint32_t j = j0; j < j1; ++j) {
+    const int64_t span = sg_span(own, grp[j], new_from);
+    if (span > delta) continue;
+    ++k;
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+      if (i < sub.n && span <= sub.delta[i]) ++ks[i];
+  }
+  if (acc) sg_credit(acc, r, k);
+#pragma unroll
+  for (int i = 0; i < NS; ++i)
+    if (i < sub.n && sub.sg[i]) sg_credit(sub.sg[i], r, ks[i]);
 }
 
 // Groups one bucket's records by key in a shared-memory hash table and
@@ -471,11 +529,12 @@ struct SgSmem {
   uint32_t n_grouped;
 };
 
-template <int CAP, int TAB>
+template <int CAP, int TAB, int NS>
 __device__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRec* __restrict__ R, int n,
                                 int32_t delta, const int32_t* __restrict__ dst,
                                 const int32_t* __restrict__ ts,
-                                unsigned long long* __restrict__ acc, int32_t new_from) {
+                                unsigned long long* __restrict__ acc, int32_t new_from,
+                                const SubWindows& sub) {
   constexpr int PER = (CAP + 255) / 256;  // records per thread (blocks of 256)
   uint32_t* cur = reinterpret_cast<uint32_t*>(S.key);
   int tab = 64;
@@ -539,24 +598,22 @@ __device__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRec* __restrict__ 
     const int i = S.pos[p];
     const uint32_t h = S.slot[i];
     const uint32_t c = S.cnt[h];
-    const int4 own = S.grp[p];
     const uint32_t end = cur[h];
-    unsigned long long k = 0;
-    for (uint32_t j = end - c; j < end; ++j)
-      if (sg_partner(own, S.grp[j], delta, new_from)) ++k;
-    if (k) sg_credit(acc, R[i], k);
+    sg_count_partners<NS>(S.grp, end - c, end, S.grp[p], R[i], delta, new_from, acc, sub);
   }
 }
 
 // One block per bucket of up to SG_CAP records; larger buckets are listed
 // in overflow (count at overflow[0]) for k_sg_bucket_big.
+template <int NS>
 __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ rec,
                                                    const int64_t* __restrict__ boff,
                                                    int32_t delta, const int32_t* __restrict__ dst,
                                                    const int32_t* __restrict__ ts,
                                                    unsigned long long* __restrict__ acc,
                                                    int32_t new_from,
-                                                   uint32_t* __restrict__ overflow) {
+                                                   uint32_t* __restrict__ overflow,
+                                                   SubWindows sub) {
   __shared__ SgSmem<SG_CAP, SG_TAB> S;
   const int64_t base = boff[blockIdx.x];
   const int64_t n = boff[blockIdx.x + 1] - base;
@@ -565,11 +622,12 @@ __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ re
     if (threadIdx.x == 0) overflow[1 + atomicAdd(overflow, 1u)] = blockIdx.x;
     return;
   }
-  sg_group_bucket<SG_CAP, SG_TAB>(S, rec + base, (int)n, delta, dst, ts, acc, new_from);
+  sg_group_bucket<SG_CAP, SG_TAB, NS>(S, rec + base, (int)n, delta, dst, ts, acc, new_from, sub);
 }
 
 // The listed buckets, a few blocks looping over the list (the count is read
 // on the device); buckets beyond SG_CAP_BIG compare every record with all.
+template <int NS>
 __global__ void __launch_bounds__(256) k_sg_bucket_big(const LegRec* __restrict__ rec,
                                                        const int64_t* __restrict__ boff,
                                                        int32_t delta,
@@ -577,7 +635,8 @@ __global__ void __launch_bounds__(256) k_sg_bucket_big(const LegRec* __restrict_
                                                        const int32_t* __restrict__ ts,
                                                        unsigned long long* __restrict__ acc,
                                                        int32_t new_from,
-                                                       const uint32_t* __restrict__ overflow) {
+                                                       const uint32_t* __restrict__ overflow,
+                                                       SubWindows sub) {
   extern __shared__ __align__(16) unsigned char sg_big_smem[];
   auto& S = *reinterpret_cast<SgSmem<SG_CAP_BIG, SG_TAB_BIG>*>(sg_big_smem);
   const uint32_t n_over = overflow[0];
@@ -587,24 +646,33 @@ __global__ void __launch_bounds__(256) k_sg_bucket_big(const LegRec* __restrict_
     const int64_t n = boff[b + 1] - base;
     const LegRec* R = rec + base;
     if (n <= SG_CAP_BIG) {
-      sg_group_bucket<SG_CAP_BIG, SG_TAB_BIG>(S, R, (int)n, delta, dst, ts, acc, new_from);
+      sg_group_bucket<SG_CAP_BIG, SG_TAB_BIG, NS>(S, R, (int)n, delta, dst, ts, acc, new_from,
+                                              sub);
     } else {
       for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         const LegRec r = R[i];
         const int4 ri = leg_info(r, dst, ts);
-        unsigned long long c = 0;
+        unsigned long long c = 0, cs[NS > 0 ? NS : 1] = {};
         for (int64_t j = 0; j < n; ++j) {
           const LegRec o = R[j];
-          if (o.key == r.key && sg_partner(ri, leg_info(o, dst, ts), delta, new_from)) ++c;
+          if (o.key != r.key) continue;
+          const int64_t span = sg_span(ri, leg_info(o, dst, ts), new_from);
+          if (span > delta) continue;
+          ++c;
+#pragma unroll
+          for (int q = 0; q < NS; ++q)
+            if (q < sub.n && span <= sub.delta[q]) ++cs[q];
         }
-        sg_credit(acc, r, c);
+        if (acc) sg_credit(acc, r, c);
+#pragma unroll
+        for (int q = 0; q < NS; ++q)
+          if (q < sub.n && sub.sg[q]) sg_credit(sub.sg[q], r, cs[q]);
       }
     }
     __syncthreads();  // the shared table is reused by the next bucket
   }
 }
 
-size_t sg_big_smem_bytes() { return sizeof(SgSmem<SG_CAP_BIG, SG_TAB_BIG>); }
 
 // ---------------------------------------------------------------- cycles
 //
@@ -666,6 +734,7 @@ __device__ __forceinline__ void cyc_path(const GraphView& g, const CycFrontier& 
 // is admissible (new node, before the latest closing edge), credits the
 // cycles of length j+1 that close from its end node through B1, and reports
 // the window of later hops its children will take.
+template <int NS>
 __global__ void __launch_bounds__(512) k_cyc_level(GraphView g, int32_t delta, int K, int j,
                                                    CycFrontier F, int64_t n,
                                                    const int2* __restrict__ close_rng,
@@ -673,7 +742,7 @@ __global__ void __launch_bounds__(512) k_cyc_level(GraphView g, int32_t delta, i
                                                    unsigned long long* __restrict__ acc,
                                                    int32_t* __restrict__ cnt,
                                                    int32_t* __restrict__ q0_out,
-                                                   int32_t close_scan_max) {
+                                                   int32_t close_scan_max, SubWindows sub) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const bool has_next = j + 1 <= K - 1;
@@ -692,34 +761,60 @@ __global__ void __launch_bounds__(512) k_cyc_level(GraphView g, int32_t delta, i
     for (int m = 1; m < j; ++m)
       if (nodes[m] == w) return;
   }
-  // cycles of length j+1: edges w -> u0 in B1 after `last`
+  // cycles of length j+1: edges w -> u0 in B1 after `last`, for this window
+  // and every smaller one whose delta the closing edge keeps
   const int k = j + 1;
-  if (k <= K && slots.slot[k] >= 0) {
-    unsigned long long* col = acc + (int64_t)slots.slot[k] * g.E;
-    unsigned long long c = 0;
-    if (cr.y - cr.x <= close_scan_max) {
-      for (int32_t q = cr.x; q < cr.y; ++q) {
-        if (__ldg(g.inbr + q) != w) continue;
-        const int32_t cid = __ldg(g.ieid + q);
-        if (!before(tl, last, __ldg(g.it + q), cid)) continue;
-        atomicAdd(col + cid, 1ull);
-        ++c;
-      }
-    } else {
-      const int32_t in_s = g.iptr[u0], in_e = g.iptr[u0 + 1];
-      const int32_t r0 = lower_nbr(g.innbr, in_s, in_e, w);
-      if (r0 < in_e && __ldg(g.innbr + r0) == w) {
-        const int32_t r1 = lower_nbr(g.innbr, r0, in_e, w + 1);
-        int32_t b0 = after_edge(g.int_, g.ineid, r0, r1, tl, last);
-        // delta counting: only new closing edges (the scan branch's range already is)
-        if (g.new_from > 0) b0 = after_edge(g.int_, g.ineid, b0, r1, g.t_new, g.new_from - 1);
-        const int32_t b1 = upper_t(g.int_, b0, r1, (int64_t)g.ts[edges[0]] + delta);
-        for (int32_t q = b0; q < b1; ++q) atomicAdd(col + __ldg(g.ineid + q), 1ull);
-        c = (unsigned long long)(b1 - b0);
-      }
+  if (k <= K) {
+    constexpr int NT = 1 + NS;
+    unsigned long long* col[NT];
+    int64_t tmax[NT];
+    unsigned long long c[NT];
+    bool any = false;
+    const int64_t ta = g.ts[edges[0]];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int sl = t == 0 ? slots.slot[k] : (t - 1 < sub.n ? sub.cyc[t - 1].slot[k] : -1);
+      col[t] = sl >= 0 ? acc + (int64_t)sl * g.E : nullptr;
+      tmax[t] = ta + (t == 0 ? delta : (t - 1 < sub.n ? sub.delta[t - 1] : 0));
+      c[t] = 0;
+      any |= sl >= 0;
     }
-    if (c)
-      for (int m = 0; m < j; ++m) atomicAdd(col + edges[m], c);
+    if (any) {
+      if (cr.y - cr.x <= close_scan_max) {
+        for (int32_t q = cr.x; q < cr.y; ++q) {
+          if (__ldg(g.inbr + q) != w) continue;
+          const int32_t cid = __ldg(g.ieid + q), tq = __ldg(g.it + q);
+          if (!before(tl, last, tq, cid)) continue;
+#pragma unroll
+          for (int t = 0; t < NT; ++t)
+            if (col[t] && tq <= tmax[t]) {
+              atomicAdd(col[t] + cid, 1ull);
+              ++c[t];
+            }
+        }
+      } else {
+        const int32_t in_s = g.iptr[u0], in_e = g.iptr[u0 + 1];
+        const int32_t r0 = lower_nbr(g.innbr, in_s, in_e, w);
+        if (r0 < in_e && __ldg(g.innbr + r0) == w) {
+          const int32_t r1 = lower_nbr(g.innbr, r0, in_e, w + 1);
+          int32_t b0 = after_edge(g.int_, g.ineid, r0, r1, tl, last);
+          // delta counting: only new closing edges (the scan branch's range already is)
+          if (g.new_from > 0) b0 = after_edge(g.int_, g.ineid, b0, r1, g.t_new, g.new_from - 1);
+          const int32_t b1 = upper_t(g.int_, b0, r1, tmax[0]);
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            if (!col[t]) continue;
+            const int32_t bt = t == 0 ? b1 : upper_t(g.int_, b0, b1, tmax[t]);
+            for (int32_t q = b0; q < bt; ++q) atomicAdd(col[t] + __ldg(g.ineid + q), 1ull);
+            c[t] = (unsigned long long)(bt - b0);
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        if (c[t])
+          for (int m = 0; m < j; ++m) atomicAdd(col[t] + edges[m], c[t]);
+    }
   }
   if (has_next) {
     const int32_t ws = g.optr[w], we = g.optr[w + 1];
@@ -834,6 +929,83 @@ __global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
     const int r = i / nc, c = i - r * nc;
     P.counts[(e0 + r) * P.ld + c] = s_rows[r * rs + c];
   }
+}
+
+
+// ------------------------------------------------------------- launchers
+//
+// The kernels that count sub-windows are compiled for 0, 1, 2 and MAX_SUB
+// of them, so the per-window counters live in registers.
+
+template <typename F>
+static void nsub_dispatch(int n, F&& f) {
+  if (n <= 0)
+    f(std::integral_constant<int, 0>{});
+  else if (n == 1)
+    f(std::integral_constant<int, 1>{});
+  else if (n == 2)
+    f(std::integral_constant<int, 2>{});
+  else
+    f(std::integral_constant<int, MAX_SUB>{});
+}
+
+void launch_leg_count(unsigned grid, int block, cudaStream_t s, const GraphView& g, int32_t delta,
+                      int32_t* L, const int2* crng, int32_t* L2, int32_t* L_new, int2* qwin,
+                      int32_t* qcb, const SubWindows& sub) {
+  nsub_dispatch(sub.n, [&](auto ns) {
+    AML_LAUNCH("k_leg_count", s,
+               k_leg_count<decltype(ns)::value><<<grid, block, 0, s>>>(g, delta, L, crng, L2,
+                                                                      L_new, qwin, qcb, sub));
+  });
+}
+
+void launch_leg_emit(unsigned grid, int block, cudaStream_t s, const GraphView& g,
+                     const int2* qwin, const int32_t* qcb, const int64_t* off, const LegSink& S,
+                     unsigned long long* acc_cyc2, int32_t* gs_in, int32_t own_max,
+                     const SubWindows& sub) {
+  nsub_dispatch(sub.n, [&](auto ns) {
+    AML_LAUNCH("k_leg_emit", s,
+               k_leg_emit<decltype(ns)::value><<<grid, block, 0, s>>>(g, qwin, qcb, off, S,
+                                                                     acc_cyc2, gs_in, own_max,
+                                                                     sub));
+  });
+}
+
+void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
+                       const int64_t* boff, int32_t delta, const int32_t* dst, const int32_t* ts,
+                       unsigned long long* acc, int32_t new_from, uint32_t* overflow,
+                       const SubWindows& sub) {
+  nsub_dispatch(sub.n, [&](auto ns) {
+    constexpr int NS = decltype(ns)::value;
+    static bool smem_set[64][MAX_SUB + 1] = {};  // per device and instantiation
+    int dev = 0;
+    AML_CUDA(cudaGetDevice(&dev));
+    const size_t big = sizeof(SgSmem<SG_CAP_BIG, SG_TAB_BIG>);
+    if (dev >= 64 || !smem_set[dev][NS]) {
+      AML_CUDA(cudaFuncSetAttribute(k_sg_bucket_big<NS>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big));
+      if (dev < 64) smem_set[dev][NS] = true;
+    }
+    AML_LAUNCH("k_sg_bucket", s,
+               k_sg_bucket<NS><<<n_buckets, 256, 0, s>>>(rec, boff, delta, dst, ts, acc,
+                                                         new_from, overflow, sub));
+    AML_LAUNCH("k_sg_bucket_big", s,
+               k_sg_bucket_big<NS><<<(unsigned)sm_count(), 256, big, s>>>(
+                   rec, boff, delta, dst, ts, acc, new_from, overflow, sub));
+  });
+}
+
+void launch_cyc_level(unsigned grid, int block, cudaStream_t s, const GraphView& g,
+                      int32_t delta, int K, int j, const CycFrontier& F, int64_t n,
+                      const int2* close_rng, const CycleSlots& slots, unsigned long long* acc,
+                      int32_t* cnt, int32_t* q0_out, int32_t close_scan_max,
+                      const SubWindows& sub) {
+  nsub_dispatch(sub.n, [&](auto ns) {
+    AML_LAUNCH("k_cyc_level", s,
+               k_cyc_level<decltype(ns)::value><<<grid, block, 0, s>>>(
+                   g, delta, K, j, F, n, close_rng, slots, acc, cnt, q0_out, close_scan_max,
+                   sub));
+  });
 }
 
 }  // namespace aml

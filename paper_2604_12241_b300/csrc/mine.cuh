@@ -100,6 +100,21 @@ struct CycleSlots {
   int32_t slot[MAX_CYCLE + 1];  // accumulator column of CYC_k, or -1
 };
 
+// Smaller windows counted from the legs, SG groups and cycle paths of a
+// larger window: an instance within a smaller window is an instance of the
+// larger one whose span is that small, so each count only adds a test of
+// the span.  Null pointers / -1 slots: column not wanted.
+constexpr int MAX_SUB = 4;
+struct SubWindows {
+  int n;
+  int32_t delta[MAX_SUB];
+  int32_t* gs_from[MAX_SUB];          // GS: legs starting with each edge
+  int32_t* gs_in[MAX_SUB];            // GS: legs ending with each edge
+  unsigned long long* cyc2[MAX_SUB];  // CYC2 accumulator
+  unsigned long long* sg[MAX_SUB];    // SG accumulator
+  CycleSlots cyc[MAX_SUB];            // CYC_k accumulator slots, k >= 3
+};
+
 // Frontier of the level-by-level cycle search: level 2 is the legs (la, lb);
 // element i of level j >= 3 extends element par[j][i] of level j-1 by the
 // out-slot slot[j][i].
@@ -116,27 +131,31 @@ __global__ void k_window_slots(const int32_t* rstart, const int32_t* t, const in
 // (DEG, FAN) of every edge for one window and direction, stored at the
 // edge id (self-loop entries untouched); two launches on s.
 void fan_per_edge(const Adj& a, int64_t Ev, int32_t delta, int2* df, cudaStream_t s);
-__global__ void k_leg_count(GraphView g, int32_t delta, int32_t* L, const int2* crng,
-                            int32_t* L2, int32_t* L_new, int2* qwin, int32_t* qcb);
 __global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);
-__global__ void k_leg_emit(GraphView g, const int2* qwin, const int32_t* qcb, const int64_t* off,
-                           LegSink S, unsigned long long* acc_cyc2, int32_t* gs_in,
-                           int32_t own_max);
 __global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, const int64_t* boff,
                                uint32_t* cursor, LegRec* out);
 __global__ void k_sg_hist(const LegRec* rec, int64_t n, int bits, uint32_t* hist);
 __global__ void k_mark_nodes(const int32_t* node_of, int64_t from, int64_t E, uint32_t* mask);
-__global__ void k_sg_bucket(const LegRec* rec, const int64_t* boff, int32_t delta,
-                            const int32_t* dst, const int32_t* ts, unsigned long long* acc,
-                            int32_t new_from, uint32_t* overflow);
-__global__ void k_sg_bucket_big(const LegRec* rec, const int64_t* boff, int32_t delta,
-                                const int32_t* dst, const int32_t* ts, unsigned long long* acc,
-                                int32_t new_from, const uint32_t* overflow);
-size_t sg_big_smem_bytes();
 __global__ void k_close_range(GraphView g, int32_t delta, int2* rng);
-__global__ void k_cyc_level(GraphView g, int32_t delta, int K, int j, CycFrontier F, int64_t n,
-                            const int2* close_rng, CycleSlots slots, unsigned long long* acc,
-                            int32_t* cnt, int32_t* q0_out, int32_t close_scan_max);
+// Launchers of the kernels that also count sub-windows (instantiated for
+// the number of them in sub).
+void launch_leg_count(unsigned grid, int block, cudaStream_t s, const GraphView& g, int32_t delta,
+                      int32_t* L, const int2* crng, int32_t* L2, int32_t* L_new, int2* qwin,
+                      int32_t* qcb, const SubWindows& sub);
+void launch_leg_emit(unsigned grid, int block, cudaStream_t s, const GraphView& g,
+                     const int2* qwin, const int32_t* qcb, const int64_t* off, const LegSink& S,
+                     unsigned long long* acc_cyc2, int32_t* gs_in, int32_t own_max,
+                     const SubWindows& sub);
+// k_sg_bucket over all buckets, then k_sg_bucket_big over the overflow list
+void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
+                       const int64_t* boff, int32_t delta, const int32_t* dst, const int32_t* ts,
+                       unsigned long long* acc, int32_t new_from, uint32_t* overflow,
+                       const SubWindows& sub);
+void launch_cyc_level(unsigned grid, int block, cudaStream_t s, const GraphView& g,
+                      int32_t delta, int K, int j, const CycFrontier& F, int64_t n,
+                      const int2* close_rng, const CycleSlots& slots, unsigned long long* acc,
+                      int32_t* cnt, int32_t* q0_out, int32_t close_scan_max,
+                      const SubWindows& sub);
 __global__ void k_cyc_emit(int64_t n, const int32_t* cnt, const int32_t* q0, const int64_t* off,
                            int32_t* par, int32_t* slot, int32_t own_max);
 __global__ void k_assemble(AssembleParams P);

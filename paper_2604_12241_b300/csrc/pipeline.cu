@@ -101,6 +101,25 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   if (n_acc) AML_CUDA(cudaMemsetAsync(acc.p, 0, (size_t)n_acc * E * 8, s));
   P.acc = acc.p;
 
+  // Smaller windows whose GS/SG/CYC columns are counted from the largest
+  // leg-emitting window's pass (sub-windows; not for delta counting or the
+  // persistent cycle search, and not when they want longer cycles).
+  std::vector<int> owner(wins.size(), -1);
+  std::vector<std::vector<int>> members(wins.size());
+  if (!persistent && new_from == 0) {
+    int lw = -1;
+    for (size_t w = 0; w < wins.size(); ++w)
+      if (wins[w].emit_legs() && (lw < 0 || wins[w].delta > wins[lw].delta)) lw = (int)w;
+    for (size_t w = 0; lw >= 0 && w < wins.size(); ++w) {
+      const WindowPlan& wp = wins[w];
+      if ((int)w == lw || !wp.needs_off() || wp.delta > wins[lw].delta) continue;
+      if (wp.K >= 3 && wp.K > wins[lw].K) continue;
+      if (members[lw].size() >= (size_t)MAX_SUB) continue;
+      owner[w] = lw;
+      members[lw].push_back((int)w);
+    }
+  }
+
   std::vector<DBuf<int32_t>> keep32;   // per-window buffers read by k_assemble
   std::vector<DBuf<int64_t>> keep64;
   std::vector<DBuf<int2>> keep_df;
@@ -130,7 +149,29 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       }
       (dir == 0 ? P.df_out : P.df_in)[w] = df;
     }
-    if (!wp.needs_off()) continue;
+    if (!wp.needs_off() || owner[w] >= 0) continue;
+    // sub-windows counted from this window's legs
+    SubWindows sub;
+    std::memset(&sub, 0, sizeof(sub));
+    bool sg_any = wp.sg;
+    for (int m : members[w]) {
+      const WindowPlan& mp = wins[m];
+      const int i = sub.n++;
+      sub.delta[i] = mp.delta;
+      sub.cyc[i] = mp.cyc;
+      if (mp.gs) {
+        keep32.emplace_back((size_t)E, s);
+        sub.gs_from[i] = keep32.back().p;
+        keep32.emplace_back((size_t)E, s);
+        sub.gs_in[i] = keep32.back().p;
+        AML_CUDA(cudaMemsetAsync(sub.gs_in[i], 0, (size_t)E * 4, s));
+        P.gs_from[m] = sub.gs_from[i];
+        P.gs_in[m] = sub.gs_in[i];
+      }
+      if (mp.cyc.slot[2] >= 0) sub.cyc2[i] = acc.p + (int64_t)mp.cyc.slot[2] * E;
+      if (mp.sg) sub.sg[i] = acc.p + (int64_t)mp.sg_slot * E;
+      sg_any |= mp.sg;
+    }
     // 2. legs (and, for the level-by-level cycle search, the legs that can
     // start a cycle: those of anchors with a closing range, before its end)
     const bool level_cycles = wp.K >= 3 && !persistent;
@@ -153,11 +194,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     }
     DBuf<int2> qwin((size_t)E, s);
     DBuf<int32_t> qcb(level_cycles ? (size_t)E : 0, s);
-    AML_LAUNCH("k_leg_count", s,
-               k_leg_count<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, L.p,
-                                                        level_cycles ? crng.p : nullptr,
-                                                        level_cycles ? L2.p : nullptr, L_new,
-                                                        qwin.p, qcb.p));
+    launch_leg_count(grid_for(E, B), B, s, gv, wp.delta, L.p, level_cycles ? crng.p : nullptr,
+                     level_cycles ? L2.p : nullptr, L_new, qwin.p, qcb.p, sub);
     AML_CUDA(cudaMemsetAsync(L.p + E, 0, sizeof(int32_t), s));
     keep64.emplace_back((size_t)(E + 1), s);
     int64_t* off = keep64.back().p;
@@ -208,7 +246,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     int64_t nb = 1;
     // delta counting: the latest edge of an SG instance is one of its gather
     // edges, so only legs into a destination of a new edge are recorded
-    const bool sg_filter = wp.sg && new_from > 0;
+    const bool sg_filter = sg_any && new_from > 0;
     DBuf<uint32_t> dmask;
     DBuf<unsigned long long> n_rec;
     auto size_buckets = [&](int64_t n_records) {
@@ -219,7 +257,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       hist = DBuf<uint32_t>((size_t)nb + 1, s);
       AML_CUDA(cudaMemsetAsync(hist.p, 0, (size_t)(nb + 1) * 4, s));
     };
-    if (wp.sg) {
+    if (sg_any) {
       rec = DBuf<LegRec>((size_t)std::max<int64_t>(nl, 1), s);
       S.rec = rec.p;
       if (sg_filter) {
@@ -240,9 +278,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     }
     unsigned long long* acc2 =
         wp.cyc.slot[2] >= 0 ? acc.p + (int64_t)wp.cyc.slot[2] * E : nullptr;
-    AML_LAUNCH("k_leg_emit", s,
-               k_leg_emit<<<grid_for(E, B), B, 0, s>>>(gv, qwin.p, qcb.p, off, S, acc2, gs_in,
-                                                       tn.own_max));
+    launch_leg_emit(grid_for(E, B), B, s, gv, qwin.p, qcb.p, off, S, acc2, gs_in, tn.own_max,
+                    sub);
     int64_t n_sg = nl;  // records to bucket
     if (sg_filter) {
       unsigned long long kept = 0;
@@ -256,7 +293,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       }
     }
     // 3. scatter-gather: bucket the leg records, group each bucket by (s, d)
-    if (wp.sg && n_sg > 1) {
+    if (sg_any && n_sg > 1) {
       const int64_t nl = n_sg;
       DBuf<int64_t> boff((size_t)nb + 1, s);
       scan_i32_to_i64(reinterpret_cast<const int32_t*>(hist.p), boff.p, nb + 1, s);
@@ -269,20 +306,9 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       // k_sg_bucket_big (one large-table block per SM)
       DBuf<uint32_t> overflow((size_t)nb + 1, s);
       AML_CUDA(cudaMemsetAsync(overflow.p, 0, sizeof(uint32_t), s));
-      static bool smem_set[64] = {false};  // per device
-      if (g->device >= 64 || !smem_set[g->device]) {
-        AML_CUDA(cudaFuncSetAttribute(k_sg_bucket_big,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sg_big_smem_bytes()));
-        if (g->device < 64) smem_set[g->device] = true;
-      }
-      unsigned long long* acc_sg = acc.p + (int64_t)wp.sg_slot * E;
-      AML_LAUNCH("k_sg_bucket", s,
-                 k_sg_bucket<<<(unsigned)nb, 256, 0, s>>>(part.p, boff.p, wp.delta, gv.dst, gv.ts,
-                                                          acc_sg, new_from, overflow.p));
-      AML_LAUNCH("k_sg_bucket_big", s,
-                 k_sg_bucket_big<<<(unsigned)sm_count(), 256, sg_big_smem_bytes(), s>>>(
-                     part.p, boff.p, wp.delta, gv.dst, gv.ts, acc_sg, new_from, overflow.p));
+      unsigned long long* acc_sg = wp.sg ? acc.p + (int64_t)wp.sg_slot * E : nullptr;
+      launch_sg_buckets((unsigned)nb, s, part.p, boff.p, wp.delta, gv.dst, gv.ts, acc_sg,
+                        new_from, overflow.p, sub);
     }
     // 4. cycles of length >= 3: one persistent cost-binned launch ...
     if (wp.K >= 3 && persistent) {
@@ -299,10 +325,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       for (int j = 2; j <= wp.K - 1 && n > 0; ++j) {
         const bool has_next = j + 1 <= wp.K - 1;
         DBuf<int32_t> cnt(has_next ? n + 1 : 0, s), q0(has_next ? n : 0, s);
-        AML_LAUNCH("k_cyc_level", s,
-                   k_cyc_level<<<grid_for(n, B), B, 0, s>>>(gv, wp.delta, wp.K, j, F, n, crng.p,
-                                                            wp.cyc, acc.p, cnt.p, q0.p,
-                                                            tn.close_scan_max));
+        launch_cyc_level(grid_for(n, B), B, s, gv, wp.delta, wp.K, j, F, n, crng.p, wp.cyc,
+                         acc.p, cnt.p, q0.p, tn.close_scan_max, sub);
         if (!has_next) break;
         DBuf<int64_t> foff(n + 1, s);
         AML_CUDA(cudaMemsetAsync(cnt.p + n, 0, sizeof(int32_t), s));
