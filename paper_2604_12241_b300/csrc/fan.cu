@@ -1,5 +1,6 @@
-// DEG and FAN of every edge, one window and direction (Sec. 5: DEG and FAN
-// stages over a trailing window of the edge's own account).
+// DEG and FAN of every edge for up to FAN_MAX_W windows of one direction
+// (Sec. 5: DEG and FAN stages over a trailing window of the edge's own
+// account).
 //
 // DEG(p) = p - lb(p) + 1 for slot p of a row sorted by (t, id), lb(p) the
 // first slot of the row inside [t_p - delta, t_p].  FAN(p) = DEG(p) - R(p),
@@ -8,7 +9,9 @@
 //   R(p) - R(p-1) = [prev(p) >= lb(p)] - #{r in [lb(p-1), lb(p)) : next(r) <= p-1}
 // (the window gains p and drops [lb(p-1), lb(p))), with R(row start) = 0.
 //
-// Two launches over contiguous chunks of slots:
+// Two launches over contiguous chunks of slots, all W windows at once (the
+// windows are nested, so each lb is searched above the previous one, and
+// the W results of an edge leave in one store):
 //   k_fan_reduce (a thread per slot, a block per chunk of FAN_RBLOCK): lb,
 //     DEG and the delta of every slot, and per chunk the sum of the deltas
 //     after its last row start (all of them when no row starts inside) with
@@ -16,8 +19,9 @@
 //   k_fan_scan (a block per tile of FAN_TILE slots): the carry into its tile
 //     from those chunk sums (back to the nearest chunk where a row starts),
 //     then a segmented scan of the deltas (restarting at row starts), and
-//     (DEG, FAN) stored at the edge id of every slot.
+//     (DEG, FAN) of every window stored at the edge id of every slot.
 #include <algorithm>
+#include <type_traits>
 
 #include "aml_internal.cuh"
 #include "mine.cuh"
@@ -35,63 +39,86 @@ constexpr int FAN_SMEM = FAN_TILE + FAN_TILE / 32;  // one pad word per 32
 
 __device__ __forceinline__ int fpad(int i) { return i + (i >> 5); }
 
-// segmented-sum pair: h = a row starts in the range, v = sum of the values
-// after (and at) its last row start, or of all of them when h = 0
-struct Seg {
-  int32_t h, v;
+struct FanDeltas {
+  int32_t d[FAN_MAX_W];  // descending
 };
-__device__ __forceinline__ Seg seg_combine(Seg a, Seg b) {  // a, then b
-  return Seg{a.h | b.h, b.h ? b.v : a.v + b.v};
+
+// segmented sums: h = a row starts in the range, v[k] = sum of the values
+// after (and at) its last row start, or of all of them when h = 0
+template <int W>
+struct Seg {
+  int32_t h;
+  int32_t v[W];
+};
+template <int W>
+__device__ __forceinline__ Seg<W> seg_combine(const Seg<W>& a, const Seg<W>& b) {  // a, then b
+  Seg<W> r;
+  r.h = a.h | b.h;
+#pragma unroll
+  for (int k = 0; k < W; ++k) r.v[k] = b.h ? b.v[k] : a.v[k] + b.v[k];
+  return r;
+}
+template <int W>
+__device__ __forceinline__ Seg<W> seg_shfl_up(const Seg<W>& x, int o) {
+  Seg<W> y;
+  y.h = __shfl_up_sync(0xffffffffu, x.h, o);
+#pragma unroll
+  for (int k = 0; k < W; ++k) y.v[k] = __shfl_up_sync(0xffffffffu, x.v[k], o);
+  return y;
+}
+template <int W>
+__device__ __forceinline__ Seg<W> seg_zero() {
+  Seg<W> z;
+  z.h = 0;
+#pragma unroll
+  for (int k = 0; k < W; ++k) z.v[k] = 0;
+  return z;
 }
 
-// exclusive segmented scan of one pair per thread over the block, in thread
-// order; *total = the block's combined pair
-__device__ Seg seg_scan_block(Seg x, Seg* total) {
-  __shared__ Seg s_w[FAN_BLOCK / 32];
+// exclusive segmented scan of one value set per thread over the block, in
+// thread order; *total = the block's combined set
+template <int W>
+__device__ Seg<W> seg_scan_block(const Seg<W>& x, Seg<W>* total) {
+  __shared__ Seg<W> s_w[FAN_BLOCK / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Seg inc = x;
+  Seg<W> inc = x;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    Seg y;
-    y.h = __shfl_up_sync(0xffffffffu, inc.h, o);
-    y.v = __shfl_up_sync(0xffffffffu, inc.v, o);
+    const Seg<W> y = seg_shfl_up(inc, o);
     if (lane >= o) inc = seg_combine(y, inc);
   }
-  Seg ex;
-  ex.h = __shfl_up_sync(0xffffffffu, inc.h, 1);
-  ex.v = __shfl_up_sync(0xffffffffu, inc.v, 1);
-  if (lane == 0) ex = Seg{0, 0};
+  Seg<W> ex = seg_shfl_up(inc, 1);
+  if (lane == 0) ex = seg_zero<W>();
   if (lane == 31) s_w[warp] = inc;
   __syncthreads();
   if (warp == 0) {
-    Seg w = lane < FAN_BLOCK / 32 ? s_w[lane] : Seg{0, 0};
+    Seg<W> w = lane < FAN_BLOCK / 32 ? s_w[lane] : seg_zero<W>();
 #pragma unroll
     for (int o = 1; o < FAN_BLOCK / 32; o <<= 1) {
-      Seg y;
-      y.h = __shfl_up_sync(0xffffffffu, w.h, o);
-      y.v = __shfl_up_sync(0xffffffffu, w.v, o);
+      const Seg<W> y = seg_shfl_up(w, o);
       if (lane >= o) w = seg_combine(y, w);
     }
     if (lane < FAN_BLOCK / 32) s_w[lane] = w;  // inclusive over warps
   }
   __syncthreads();
-  const Seg before = warp ? s_w[warp - 1] : Seg{0, 0};
+  const Seg<W> before = warp ? s_w[warp - 1] : seg_zero<W>();
   *total = s_w[FAN_BLOCK / 32 - 1];
-  const Seg r = seg_combine(before, ex);
+  const Seg<W> r = seg_combine(before, ex);
   __syncthreads();  // s_w is reused by the next call
   return r;
 }
 
-// one slot per thread; chunks of FAN_RBLOCK slots
+// deg_s, D: [W][Ev]; chunk_sum: [W][n_red]
+template <int W>
 __global__ void __launch_bounds__(FAN_RBLOCK) k_fan_reduce(const int32_t* __restrict__ rstart,
                                                            const int32_t* __restrict__ t,
                                                            const int32_t* __restrict__ prev,
                                                            const int32_t* __restrict__ next,
-                                                           int64_t Ev, int32_t delta,
+                                                           int64_t Ev, FanDeltas fd,
                                                            int32_t* __restrict__ deg_s,
                                                            int32_t* __restrict__ D,
                                                            int2* __restrict__ chunk_sum) {
-  __shared__ int32_t s_sum[FAN_RBLOCK / 32];
+  __shared__ int32_t s_sum[W][FAN_RBLOCK / 32];
   const int lane = threadIdx.x & 31;
   const int64_t c0 = (int64_t)blockIdx.x * FAN_RBLOCK;
   const int64_t c1 = c0 + FAN_RBLOCK < Ev ? c0 + FAN_RBLOCK : Ev;
@@ -100,47 +127,77 @@ __global__ void __launch_bounds__(FAN_RBLOCK) k_fan_reduce(const int32_t* __rest
   const int64_t p64 = c0 + threadIdx.x;
   const bool in = p64 < c1;
   const int32_t p = (int32_t)p64;
-  int32_t rs = 0, lbp = 0, u = 0;
+  int32_t rs = 0, tp = 0, lb[W], u[W];
   if (in) {
     rs = __ldg(rstart + p);
-    lbp = lower_t(t, rs, p + 1, (int64_t)__ldg(t + p) - delta);
-    deg_s[p] = p - lbp + 1;
+    tp = __ldg(t + p);
   }
-  // lb(p-1) is the lower lane's lb when that lane holds slot p-1 of the row
-  const int32_t lb_lower = __shfl_up_sync(0xffffffffu, lbp, 1);
-  if (in) {
+  int32_t lo = rs;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    u[k] = 0;
+    lb[k] = in ? lower_t(t, lo, p + 1, (int64_t)tp - fd.d[k]) : 0;  // nested: lb grows
+    lo = lb[k];
+    if (in) deg_s[k * Ev + p] = p - lb[k] + 1;
+  }
+  const int32_t t_before = in && p > rs ? __ldg(t + p - 1) : 0;
+  const int32_t prev_p = in && p > rs ? __ldg(prev + p) : -1;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    // lb(p-1) is the lower lane's lb when that lane holds slot p-1 of the row
+    const int32_t lb_lower = __shfl_up_sync(0xffffffffu, lb[k], 1);
+    if (!in) continue;
     int32_t d = 0;
     if (p > rs) {
       const int32_t lbq =
-          lane > 0 ? lb_lower
-                   : lower_t(t, rs, min(lbp + 1, p), (int64_t)__ldg(t + p - 1) - delta);
-      d = (__ldg(prev + p) >= lbp) ? 1 : 0;
-      for (int32_t r = lbq; r < lbp; ++r) d -= (__ldg(next + r) <= p - 1) ? 1 : 0;
+          lane > 0 ? lb_lower : lower_t(t, rs, min(lb[k] + 1, p), (int64_t)t_before - fd.d[k]);
+      d = prev_p >= lb[k] ? 1 : 0;
+      for (int32_t r = lbq; r < lb[k]; ++r) d -= (__ldg(next + r) <= p - 1) ? 1 : 0;
     }
-    D[p] = d;
-    if (p64 >= from) u = d;
+    D[k * Ev + p] = d;
+    if (p64 >= from) u[k] = d;
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-  if (lane == 0) s_sum[threadIdx.x >> 5] = u;
+  for (int k = 0; k < W; ++k) {
+    int32_t x = u[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s_sum[k][threadIdx.x >> 5] = x;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < W) {
+    const int k = threadIdx.x;
     int32_t tot = 0;
-    for (int w = 0; w < FAN_RBLOCK / 32; ++w) tot += s_sum[w];
-    chunk_sum[blockIdx.x] = make_int2(tot, last_rs >= c0 ? 1 : 0);
+    for (int w = 0; w < FAN_RBLOCK / 32; ++w) tot += s_sum[k][w];
+    chunk_sum[(int64_t)k * gridDim.x + blockIdx.x] = make_int2(tot, last_rs >= c0 ? 1 : 0);
   }
 }
 
+template <int W>
+__device__ __forceinline__ void store_df(int2* __restrict__ df, int32_t e, const int2 (&v)[W]) {
+  int2* dst = df + (int64_t)e * W;
+  if constexpr (W % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < W; k += 2)
+      reinterpret_cast<int4*>(dst)[k / 2] = make_int4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
+  } else {
+#pragma unroll
+    for (int k = 0; k < W; ++k) dst[k] = v[k];
+  }
+}
+
+// df: [E][W] (DEG, FAN) pairs
+template <int W>
 __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restrict__ rstart,
                                                         const int32_t* __restrict__ eid,
                                                         const int32_t* __restrict__ deg_s,
                                                         const int32_t* __restrict__ D,
-                                                        int64_t Ev,
+                                                        int64_t Ev, int64_t n_red,
                                                         const int2* __restrict__ chunk_sum,
                                                         int2* __restrict__ df) {
-  __shared__ int32_t s_v[FAN_SMEM];
+  __shared__ int32_t s_v[W][FAN_SMEM];
   __shared__ uint8_t s_h[FAN_SMEM];
-  __shared__ int32_t s_carry;
+  __shared__ int32_t s_carry[W];
   const int64_t c0 = (int64_t)blockIdx.x * FAN_TILE;
   const int64_t c1 = c0 + FAN_TILE < Ev ? c0 + FAN_TILE : Ev;
   if (threadIdx.x < 32) {
@@ -148,54 +205,75 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restric
     // chunks before it back to the nearest one where a row starts (chunk 0
     // always has one: slot 0), 32 chunks per step
     const int lane = threadIdx.x;
-    int32_t v = 0;
+    int32_t v[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) v[k] = 0;
     for (int64_t top = c0 / FAN_RBLOCK - 1; top >= 0; top -= 32) {
       const int64_t c = top - lane;
-      const int2 cs = c >= 0 ? chunk_sum[c] : make_int2(0, 1);
-      const unsigned starts = __ballot_sync(0xffffffffu, cs.y != 0);
+      const int32_t flag = c >= 0 ? chunk_sum[c].y : 1;
+      const unsigned starts = __ballot_sync(0xffffffffu, flag != 0);
       const int first = starts ? __ffs(starts) - 1 : 31;  // lanes [0, first] count
-      int32_t x = lane <= first ? cs.x : 0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      v += x;
+      for (int k = 0; k < W; ++k) {
+        int32_t x = (c >= 0 && lane <= first) ? chunk_sum[k * n_red + c].x : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        v[k] += x;
+      }
       if (starts) break;
     }
-    if (lane == 0) s_carry = v;
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < W; ++k) s_carry[k] = v[k];
   }
   __syncthreads();
-  Seg run{0, s_carry};
+  Seg<W> run;
+  run.h = 0;
+#pragma unroll
+  for (int k = 0; k < W; ++k) run.v[k] = s_carry[k];
   for (int64_t base = c0; base < c1; base += FAN_TILE) {
     for (int i = threadIdx.x; i < FAN_TILE; i += FAN_BLOCK) {
       const int64_t p = base + i;
       const bool in = p < c1;
-      s_v[fpad(i)] = in ? D[p] : 0;
+#pragma unroll
+      for (int k = 0; k < W; ++k) s_v[k][fpad(i)] = in ? D[k * Ev + p] : 0;
       s_h[fpad(i)] = in && rstart[p] == (int32_t)p ? 1 : 0;
     }
     __syncthreads();
-    int32_t v[FAN_ITEMS];
-    uint8_t h[FAN_ITEMS];
-    Seg mine{0, 0};
+    Seg<W> mine = seg_zero<W>();
 #pragma unroll
-    for (int k = 0; k < FAN_ITEMS; ++k) {
-      const int j = fpad(threadIdx.x * FAN_ITEMS + k);
-      v[k] = s_v[j];
-      h[k] = s_h[j];
-      mine = seg_combine(mine, Seg{h[k], v[k]});
+    for (int it = 0; it < FAN_ITEMS; ++it) {
+      const int j = fpad(threadIdx.x * FAN_ITEMS + it);
+      Seg<W> x;
+      x.h = s_h[j];
+#pragma unroll
+      for (int k = 0; k < W; ++k) x.v[k] = s_v[k][j];
+      mine = seg_combine(mine, x);
     }
-    Seg tile_total;
-    const Seg ex = seg_scan_block(mine, &tile_total);
-    int32_t r = seg_combine(run, ex).v;
+    Seg<W> tile_total;
+    const Seg<W> ex = seg_scan_block(mine, &tile_total);
+    Seg<W> r = seg_combine(run, ex);
 #pragma unroll
-    for (int k = 0; k < FAN_ITEMS; ++k) {
-      r = h[k] ? v[k] : r + v[k];
-      s_v[fpad(threadIdx.x * FAN_ITEMS + k)] = r;  // R of the slot
+    for (int it = 0; it < FAN_ITEMS; ++it) {
+      const int j = fpad(threadIdx.x * FAN_ITEMS + it);
+      const bool h = s_h[j] != 0;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        r.v[k] = h ? s_v[k][j] : r.v[k] + s_v[k][j];
+        s_v[k][j] = r.v[k];  // R of the slot
+      }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < FAN_TILE; i += FAN_BLOCK) {
       const int64_t p = base + i;
       if (p < c1) {
-        const int32_t deg = deg_s[p];
-        df[eid[p]] = make_int2(deg, deg - s_v[fpad(i)]);
+        int2 v[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          const int32_t deg = deg_s[k * Ev + p];
+          v[k] = make_int2(deg, deg - s_v[k][fpad(i)]);
+        }
+        store_df<W>(df, eid[p], v);
       }
     }
     run = seg_combine(run, tile_total);
@@ -203,21 +281,38 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restric
   }
 }
 
-}  // namespace
-
-void fan_per_edge(const Adj& a, int64_t Ev, int32_t delta, int2* df, cudaStream_t s) {
-  if (Ev <= 0) return;
+template <int W>
+void fan_launch(const Adj& a, int64_t Ev, const FanDeltas& fd, int2* df, cudaStream_t s) {
   const int64_t n_red = (Ev + FAN_RBLOCK - 1) / FAN_RBLOCK;
   const int64_t n_tiles = (Ev + FAN_TILE - 1) / FAN_TILE;
-  DBuf<int32_t> deg_s((size_t)Ev, s), D((size_t)Ev, s);
-  DBuf<int2> sums((size_t)n_red, s);
+  DBuf<int32_t> deg_s((size_t)W * Ev, s), D((size_t)W * Ev, s);
+  DBuf<int2> sums((size_t)W * n_red, s);
   AML_LAUNCH("k_fan_reduce", s,
-             k_fan_reduce<<<(unsigned)n_red, FAN_RBLOCK, 0, s>>>(a.rstart, a.t, a.prev, a.next,
-                                                                 Ev, delta, deg_s.p, D.p,
-                                                                 sums.p));
+             k_fan_reduce<W><<<(unsigned)n_red, FAN_RBLOCK, 0, s>>>(
+                 a.rstart, a.t, a.prev, a.next, Ev, fd, deg_s.p, D.p, sums.p));
   AML_LAUNCH("k_fan_scan", s,
-             k_fan_scan<<<(unsigned)n_tiles, FAN_BLOCK, 0, s>>>(a.rstart, a.eid, deg_s.p, D.p,
-                                                                Ev, sums.p, df));
+             k_fan_scan<W><<<(unsigned)n_tiles, FAN_BLOCK, 0, s>>>(a.rstart, a.eid, deg_s.p, D.p,
+                                                                   Ev, n_red, sums.p, df));
+}
+
+}  // namespace
+
+void fan_per_edge(const Adj& a, int64_t Ev, int nw, const int32_t* deltas, int2* df,
+                  cudaStream_t s) {
+  AML_REQUIRE(nw >= 1 && nw <= FAN_MAX_W, AML_EINTERNAL, "fan_per_edge: window count");
+  if (Ev <= 0) return;
+  FanDeltas fd{};
+  for (int k = 0; k < nw; ++k) {
+    fd.d[k] = deltas[k];
+    AML_REQUIRE(k == 0 || deltas[k] <= deltas[k - 1], AML_EINTERNAL,
+                "fan_per_edge: windows must be in descending order");
+  }
+  switch (nw) {
+    case 1: fan_launch<1>(a, Ev, fd, df, s); break;
+    case 2: fan_launch<2>(a, Ev, fd, df, s); break;
+    case 3: fan_launch<3>(a, Ev, fd, df, s); break;
+    default: fan_launch<4>(a, Ev, fd, df, s); break;
+  }
 }
 
 }  // namespace aml

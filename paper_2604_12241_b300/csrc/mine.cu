@@ -872,13 +872,13 @@ __device__ __forceinline__ uint64_t assemble_value(const AssembleParams& P, cons
   const int w = cd.didx;
   switch (cd.family) {
     case AML_FAM_DEG_OUT:
-      return (uint64_t)P.df_out[w][e].x;
+      return (uint64_t)P.df_out[w][(int64_t)e * P.df_stride_out[w]].x;
     case AML_FAM_FAN_OUT:
-      return (uint64_t)P.df_out[w][e].y;
+      return (uint64_t)P.df_out[w][(int64_t)e * P.df_stride_out[w]].y;
     case AML_FAM_DEG_IN:
-      return (uint64_t)P.df_in[w][e].x;
+      return (uint64_t)P.df_in[w][(int64_t)e * P.df_stride_in[w]].x;
     case AML_FAM_FAN_IN:
-      return (uint64_t)P.df_in[w][e].y;
+      return (uint64_t)P.df_in[w][(int64_t)e * P.df_stride_in[w]].y;
     case AML_FAM_GS: {
       const int32_t from =
           P.gs_from[w] ? P.gs_from[w][e] : (int32_t)(P.off[w][e + 1] - P.off[w][e]);

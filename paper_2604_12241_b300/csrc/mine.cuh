@@ -57,8 +57,10 @@ struct AssembleParams {
   GraphView g;
   ColDesc cols[MAX_COLS];
   int32_t ncols;
-  const int2* df_out[MAX_DELTAS];  // (DEG_OUT, FAN_OUT) per edge
-  const int2* df_in[MAX_DELTAS];   // (DEG_IN, FAN_IN) per edge
+  const int2* df_out[MAX_DELTAS];  // (DEG_OUT, FAN_OUT) of edge e at [e * stride]
+  const int2* df_in[MAX_DELTAS];   // (DEG_IN, FAN_IN) likewise
+  int32_t df_stride_out[MAX_DELTAS];
+  int32_t df_stride_in[MAX_DELTAS];
   const int64_t* off[MAX_DELTAS];     // leg offsets per edge (GS gather side)
   const int32_t* gs_from[MAX_DELTAS]; // delta counting: legs from each edge that are new
   const int32_t* gs_in[MAX_DELTAS];   // legs ending with each edge (GS scatter side)
@@ -128,9 +130,12 @@ struct CycFrontier {
 __global__ void k_window_slots(const int32_t* rstart, const int32_t* t, const int32_t* eid,
                                const int32_t* prev, const int32_t* next, int64_t Ev,
                                int32_t delta, int32_t* deg_s, int32_t* D, int2* df);
-// (DEG, FAN) of every edge for one window and direction, stored at the
-// edge id (self-loop entries untouched); two launches on s.
-void fan_per_edge(const Adj& a, int64_t Ev, int32_t delta, int2* df, cudaStream_t s);
+// (DEG, FAN) of every edge for nw <= FAN_MAX_W windows of one direction
+// (deltas in descending order): df[e * nw + k] for window k, at the edge id
+// (self-loop entries untouched); two launches on s.
+constexpr int FAN_MAX_W = 4;
+void fan_per_edge(const Adj& a, int64_t Ev, int nw, const int32_t* deltas, int2* df,
+                  cudaStream_t s);
 __global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);
 __global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, const int64_t* boff,
                                uint32_t* cursor, LegRec* out);

@@ -129,26 +129,46 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   const Tuning tn = g->tune;
   const int B = tn.block;
   const int64_t Ev = g->Ev;
-  for (size_t w = 0; w < wins.size(); ++w) {
-    WindowPlan& wp = wins[w];
-    // 1. trailing windows of both directions: (DEG, FAN) per edge
-    for (int dir = 0; dir < 2; ++dir) {
-      bool fan = dir == 0 ? wp.fan_out : wp.fan_in;
-      bool deg = dir == 0 ? wp.deg_out : wp.deg_in;
-      if (!(fan || deg) || Ev == 0) continue;
-      const Adj& a = dir == 0 ? g->out : g->in;
-      keep_df.emplace_back((size_t)E, s);
+  // 1. trailing windows, per direction: (DEG, FAN) of every window at once
+  // when any wants FAN (groups of FAN_MAX_W, largest delta first), else DEG
+  // alone window by window
+  for (int dir = 0; dir < 2 && Ev > 0; ++dir) {
+    const Adj& a = dir == 0 ? g->out : g->in;
+    std::vector<int> ws;
+    bool any_fan = false;
+    for (size_t w = 0; w < wins.size(); ++w) {
+      const WindowPlan& wp = wins[w];
+      const bool fan = dir == 0 ? wp.fan_out : wp.fan_in;
+      const bool deg = dir == 0 ? wp.deg_out : wp.deg_in;
+      if (fan || deg) ws.push_back((int)w);
+      any_fan |= fan;
+    }
+    std::sort(ws.begin(), ws.end(), [&](int x, int y) { return wins[x].delta > wins[y].delta; });
+    const int group = any_fan ? FAN_MAX_W : 1;
+    for (size_t g0 = 0; g0 < ws.size(); g0 += group) {
+      const int nw = (int)std::min<size_t>(group, ws.size() - g0);
+      keep_df.emplace_back((size_t)E * nw, s);
       int2* df = keep_df.back().p;
-      if (fan) {
-        fan_per_edge(a, Ev, wp.delta, df, s);
+      int32_t deltas[FAN_MAX_W];
+      for (int k = 0; k < nw; ++k) {
+        const int w = ws[g0 + k];
+        deltas[k] = wins[w].delta;
+        (dir == 0 ? P.df_out : P.df_in)[w] = df + k;
+        (dir == 0 ? P.df_stride_out : P.df_stride_in)[w] = nw;
+      }
+      if (any_fan) {
+        fan_per_edge(a, Ev, nw, deltas, df, s);
       } else {
         AML_LAUNCH("k_window_slots", s,
                    k_window_slots<<<grid_for(Ev, B), B, 0, s>>>(a.rstart, a.t, a.eid, a.prev,
-                                                                a.next, Ev, wp.delta, nullptr,
+                                                                a.next, Ev, deltas[0], nullptr,
                                                                 nullptr, df));
       }
-      (dir == 0 ? P.df_out : P.df_in)[w] = df;
     }
+  }
+
+  for (size_t w = 0; w < wins.size(); ++w) {
+    WindowPlan& wp = wins[w];
     if (!wp.needs_off() || owner[w] >= 0) continue;
     // sub-windows counted from this window's legs
     SubWindows sub;
