@@ -236,20 +236,10 @@ __device__ __forceinline__ uint32_t bucket_of(uint64_t key, int bucket_bits) {
   return bucket_bits ? (uint32_t)(mix64(key) >> (64 - bucket_bits)) : 0u;
 }
 
-// bucket histogram increment, aggregated over the lanes of a warp that hit
-// the same bucket
-__device__ __forceinline__ void count_bucket(uint32_t* hist, uint32_t bkt, bool active) {
-  const unsigned act = __ballot_sync(0xffffffffu, active);
-  if (!active) return;
-  const unsigned peers = __match_any_sync(act, bkt);
-  if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(hist + bkt, (uint32_t)__popc(peers));
-}
-
-__device__ __forceinline__ void put_rec(const LegSink& S, int64_t pos, int32_t a, int32_t b,
-                                        int32_t x, int32_t h, int32_t y, int32_t ta, int32_t tb,
-                                        int64_t n_nodes) {
+__device__ __forceinline__ void put_rec(const LegSink& S, int64_t pos, uint64_t key, int32_t a,
+                                        int32_t b) {
   LegRec r;
-  r.key = (uint64_t)x * (uint64_t)n_nodes + (uint64_t)y;
+  r.key = key;
   r.a = a;
   r.b = b;
   S.rec[pos] = r;
@@ -264,12 +254,14 @@ __device__ __forceinline__ bool in_mask(const uint32_t* mask, int32_t v) {
 __device__ __forceinline__ void sg_record(const LegSink& S, bool leg, int64_t pos, int32_t a,
                                           int32_t b, int32_t x, int32_t h, int32_t y, int32_t ta,
                                           int32_t tb, int64_t n_nodes, int bits) {
+  const uint64_t key = (uint64_t)x * (uint64_t)n_nodes + (uint64_t)y;
   if (!S.dmask) {
-    if (leg) put_rec(S, pos, a, b, x, h, y, ta, tb, n_nodes);
-    if (S.hist)
-      count_bucket(S.hist, leg ? bucket_of((uint64_t)x * (uint64_t)n_nodes + (uint64_t)y, bits)
-                               : 0u,
-                   leg);
+    // buckets are many and the keys of a warp's legs differ, so the
+    // histogram takes one plain increment per leg
+    if (leg) {
+      put_rec(S, pos, key, a, b);
+      if (S.hist) atomicAdd(S.hist + bucket_of(key, bits), 1u);
+    }
     return;
   }
   const bool keep = leg && in_mask(S.dmask, y);
@@ -279,8 +271,7 @@ __device__ __forceinline__ void sg_record(const LegSink& S, bool leg, int64_t po
   unsigned long long base = 0;
   if (lane == lead) base = atomicAdd(S.n_rec, (unsigned long long)__popc(m));
   base = __shfl_sync(0xffffffffu, base, lead);
-  if (keep) put_rec(S, (int64_t)base + __popc(m & ((1u << lane) - 1u)), a, b, x, h, y, ta, tb,
-                    n_nodes);
+  if (keep) put_rec(S, (int64_t)base + __popc(m & ((1u << lane) - 1u)), key, a, b);
 }
 
 // Writes every leg (a, b) of edge a at off[a]...; reciprocal edges b = h->x
@@ -424,7 +415,7 @@ __global__ void __launch_bounds__(256) k_sg_hist(const LegRec* __restrict__ rec,
                                                  int bits, uint32_t* __restrict__ hist) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool in = i < n;
-  count_bucket(hist, in ? bucket_of(rec[i].key, bits) : 0u, in);
+  if (in) atomicAdd(hist + bucket_of(rec[i].key, bits), 1u);
 }
 
 // mask bit v set for v = node_of[e], e in [from, E)
@@ -441,7 +432,6 @@ __global__ void __launch_bounds__(256) k_mark_nodes(const int32_t* __restrict__ 
 // in flight at once (the kernel is bound by their latency)
 __global__ void __launch_bounds__(256) k_sg_partition(const LegRec* __restrict__ rec, int64_t n,
                                                       int bits,
-                                                      const int64_t* __restrict__ boff,
                                                       uint32_t* __restrict__ cursor,
                                                       LegRec* __restrict__ out) {
   const int64_t base = (int64_t)blockIdx.x * blockDim.x * SG_PART_ITEMS + threadIdx.x;
@@ -458,7 +448,7 @@ __global__ void __launch_bounds__(256) k_sg_partition(const LegRec* __restrict__
   }
 #pragma unroll
   for (int k = 0; k < SG_PART_ITEMS; ++k)
-    if (base + (int64_t)k * blockDim.x < n) pos[k] = boff[bkt[k]] + atomicAdd(cursor + bkt[k], 1u);
+    if (base + (int64_t)k * blockDim.x < n) pos[k] = atomicAdd(cursor + bkt[k], 1u);
 #pragma unroll
   for (int k = 0; k < SG_PART_ITEMS; ++k)
     if (base + (int64_t)k * blockDim.x < n) out[pos[k]] = r[k];
@@ -607,7 +597,7 @@ __device__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRec* __restrict__ 
 // in overflow (count at overflow[0]) for k_sg_bucket_big.
 template <int NS>
 __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ rec,
-                                                   const int64_t* __restrict__ boff,
+                                                   const uint32_t* __restrict__ bend,
                                                    int32_t delta, const int32_t* __restrict__ dst,
                                                    const int32_t* __restrict__ ts,
                                                    unsigned long long* __restrict__ acc,
@@ -615,8 +605,8 @@ __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ re
                                                    uint32_t* __restrict__ overflow,
                                                    SubWindows sub) {
   __shared__ SgSmem<SG_CAP, SG_TAB> S;
-  const int64_t base = boff[blockIdx.x];
-  const int64_t n = boff[blockIdx.x + 1] - base;
+  const int64_t base = blockIdx.x ? bend[blockIdx.x - 1] : 0;
+  const int64_t n = (int64_t)bend[blockIdx.x] - base;
   if (n < 2) return;
   if (n > SG_CAP) {
     if (threadIdx.x == 0) overflow[1 + atomicAdd(overflow, 1u)] = blockIdx.x;
@@ -629,7 +619,7 @@ __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ re
 // on the device); buckets beyond SG_CAP_BIG compare every record with all.
 template <int NS>
 __global__ void __launch_bounds__(256) k_sg_bucket_big(const LegRec* __restrict__ rec,
-                                                       const int64_t* __restrict__ boff,
+                                                       const uint32_t* __restrict__ bend,
                                                        int32_t delta,
                                                        const int32_t* __restrict__ dst,
                                                        const int32_t* __restrict__ ts,
@@ -642,8 +632,8 @@ __global__ void __launch_bounds__(256) k_sg_bucket_big(const LegRec* __restrict_
   const uint32_t n_over = overflow[0];
   for (uint32_t k = blockIdx.x; k < n_over; k += gridDim.x) {
     const uint32_t b = overflow[1 + k];
-    const int64_t base = boff[b];
-    const int64_t n = boff[b + 1] - base;
+    const int64_t base = b ? bend[b - 1] : 0;
+    const int64_t n = (int64_t)bend[b] - base;
     const LegRec* R = rec + base;
     if (n <= SG_CAP_BIG) {
       sg_group_bucket<SG_CAP_BIG, SG_TAB_BIG, NS>(S, R, (int)n, delta, dst, ts, acc, new_from,
@@ -972,7 +962,7 @@ void launch_leg_emit(unsigned grid, int block, cudaStream_t s, const GraphView& 
 }
 
 void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
-                       const int64_t* boff, int32_t delta, const int32_t* dst, const int32_t* ts,
+                       const uint32_t* bend, int32_t delta, const int32_t* dst, const int32_t* ts,
                        unsigned long long* acc, int32_t new_from, uint32_t* overflow,
                        const SubWindows& sub) {
   nsub_dispatch(sub.n, [&](auto ns) {
@@ -987,11 +977,11 @@ void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
       if (dev < 64) smem_set[dev][NS] = true;
     }
     AML_LAUNCH("k_sg_bucket", s,
-               k_sg_bucket<NS><<<n_buckets, 256, 0, s>>>(rec, boff, delta, dst, ts, acc,
+               k_sg_bucket<NS><<<n_buckets, 256, 0, s>>>(rec, bend, delta, dst, ts, acc,
                                                          new_from, overflow, sub));
     AML_LAUNCH("k_sg_bucket_big", s,
                k_sg_bucket_big<NS><<<(unsigned)sm_count(), 256, big, s>>>(
-                   rec, boff, delta, dst, ts, acc, new_from, overflow, sub));
+                   rec, bend, delta, dst, ts, acc, new_from, overflow, sub));
   });
 }
 

@@ -137,8 +137,10 @@ constexpr int FAN_MAX_W = 4;
 void fan_per_edge(const Adj& a, int64_t Ev, int nw, const int32_t* deltas, int2* df,
                   cudaStream_t s);
 __global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);
-__global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, const int64_t* boff,
-                               uint32_t* cursor, LegRec* out);
+// moves every record to its bucket: cursor = exclusive scan of the bucket
+// sizes on entry, the bucket ends on exit
+__global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, uint32_t* cursor,
+                               LegRec* out);
 __global__ void k_sg_hist(const LegRec* rec, int64_t n, int bits, uint32_t* hist);
 __global__ void k_mark_nodes(const int32_t* node_of, int64_t from, int64_t E, uint32_t* mask);
 __global__ void k_close_range(GraphView g, int32_t delta, int2* rng);
@@ -151,9 +153,10 @@ void launch_leg_emit(unsigned grid, int block, cudaStream_t s, const GraphView& 
                      const int2* qwin, const int32_t* qcb, const int64_t* off, const LegSink& S,
                      unsigned long long* acc_cyc2, int32_t* gs_in, int32_t own_max,
                      const SubWindows& sub);
-// k_sg_bucket over all buckets, then k_sg_bucket_big over the overflow list
+// k_sg_bucket over all buckets (bucket b = records [bend[b-1], bend[b])),
+// then k_sg_bucket_big over the overflow list
 void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
-                       const int64_t* boff, int32_t delta, const int32_t* dst, const int32_t* ts,
+                       const uint32_t* bend, int32_t delta, const int32_t* dst, const int32_t* ts,
                        unsigned long long* acc, int32_t new_from, uint32_t* overflow,
                        const SubWindows& sub);
 void launch_cyc_level(unsigned grid, int block, cudaStream_t s, const GraphView& g,

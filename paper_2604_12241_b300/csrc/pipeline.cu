@@ -315,19 +315,20 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     // 3. scatter-gather: bucket the leg records, group each bucket by (s, d)
     if (sg_any && n_sg > 1) {
       const int64_t nl = n_sg;
-      DBuf<int64_t> boff((size_t)nb + 1, s);
-      scan_i32_to_i64(reinterpret_cast<const int32_t*>(hist.p), boff.p, nb + 1, s);
-      AML_CUDA(cudaMemsetAsync(hist.p, 0, (size_t)nb * 4, s));  // now the bucket cursors
+      // bucket starts (the sizes sum to < 2^32, so the 32-bit scan is exact
+      // read as unsigned); the partition leaves the bucket ends
+      scan_i32(reinterpret_cast<const int32_t*>(hist.p), reinterpret_cast<int32_t*>(hist.p), nb,
+               false, s);
       DBuf<LegRec> part((size_t)nl, s);
       AML_LAUNCH("k_sg_partition", s,
                  k_sg_partition<<<grid_for(nl, 256 * SG_PART_ITEMS), 256, 0, s>>>(
-                     rec.p, nl, S.bits, boff.p, hist.p, part.p));
+                     rec.p, nl, S.bits, hist.p, part.p));
       // buckets beyond SG_CAP records: listed by k_sg_bucket, grouped by
       // k_sg_bucket_big (one large-table block per SM)
       DBuf<uint32_t> overflow((size_t)nb + 1, s);
       AML_CUDA(cudaMemsetAsync(overflow.p, 0, sizeof(uint32_t), s));
       unsigned long long* acc_sg = wp.sg ? acc.p + (int64_t)wp.sg_slot * E : nullptr;
-      launch_sg_buckets((unsigned)nb, s, part.p, boff.p, wp.delta, gv.dst, gv.ts, acc_sg,
+      launch_sg_buckets((unsigned)nb, s, part.p, hist.p, wp.delta, gv.dst, gv.ts, acc_sg,
                         new_from, overflow.p, sub);
     }
     // 4. cycles of length >= 3: one persistent cost-binned launch ...
