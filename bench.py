@@ -157,40 +157,57 @@ def measured_peak():
     return 6400.0, "of fallback"
 
 
-def algorithmic_bytes(kernel: str, E: int, Ev: int, pats, n_legs: dict) -> float:
+def algorithmic_bytes(kernel: str, E: int, Ev: int, pats, stats: dict) -> float:
     """Bytes per launch the kernel's definition must move (no probes, no re-reads).
 
-    n_legs: temporal 2-paths per window (= sum of the GS column / 2).  Kernels
-    launched once per window report the mean over the windows.
-      k_assemble    per edge: src, dst, ts (12 B), two slot positions and two
-                    row starts (16 B), per FAN column two prefix sums (8 B), per
-                    SG/CYC column one uint64 accumulator (8 B), the row (4 B/col)
-      k_leg_emit    per edge: src, dst, ts, leg offset (20 B); per leg: the
-                    window slot (nbr, eid, t: 12 B) and its outputs, (a, b) for
-                    the cycle search (8 B) and the 16-B SG record
+    stats: the leg pass's window sizes (aml_graph_window_stats of the largest
+    window: every smaller window is counted inside its pass): legs = temporal
+    2-paths, front[j] = cycle-search paths of j edges.  A kernel launched once
+    per level reports the mean over its launches.
+      k_assemble      per edge: src, dst (8 B); per window and direction with
+                      DEG/FAN columns one (DEG, FAN) pair (8 B); per GS column
+                      the two leg counts (8 B); per SG/CYC column one uint64
+                      accumulator (8 B); the row (4 B per column)
+      k_leg_emit      per edge: src, dst, ts, leg window, leg offset (24 B); per
+                      leg: the window slot (nbr, eid, t: 12 B) and its 16-B SG
+                      record; per cycle-capable leg its (a, b) (8 B)
       k_sg_partition  per leg: one 16-B record read and written (32 B)
-      k_sg_bucket   per leg: one 16-B record read
-      k_window_slots  per list slot: t, eid, row, prev, next (20 B) + lb, delta (8 B)
-      k_cyc_level   per edge of the window: the anchor's closing range (8 B) and
-                    its two edges (8 B) -- the legs it starts from
+      k_sg_bucket     per leg: one 16-B record read
+      k_fan_reduce    per slot: row start, t, prev (12 B), per window the DEG
+                      and delta written (8 B)
+      k_fan_scan      per slot: row start, eid (8 B), per window DEG and delta
+                      read and (DEG, FAN) written (16 B)
+      k_cyc_level     per path: its parent link and slot (8 B), its anchor's
+                      closing range (8 B), its next-hop count and start (8 B)
     """
     P = len(pats)
     names = [p.name for p in pats]
-    n_fan = sum(n.startswith("FAN") for n in names)
-    n_acc = sum(n.startswith("SG") or n.startswith("CYC") for n in names)
-    legs = sum(n_legs.values()) / max(1, len(n_legs))
+    fam = [n.split("@")[0] for n in names]
+    wins = {n.split("@")[1] for n in names}
+    n_degfan = sum(any(f.startswith(("DEG_OUT", "FAN_OUT")) and n.endswith("@" + w)
+                       for f, n in zip(fam, names)) +
+                   any(f.startswith(("DEG_IN", "FAN_IN")) and n.endswith("@" + w)
+                       for f, n in zip(fam, names)) for w in wins)
+    n_gs = sum(f == "GS" for f in fam)
+    n_acc = sum(f.startswith(("SG", "CYC")) for f in fam)
+    W = sum(1 for w in wins if any(f.startswith(("DEG_OUT", "FAN_OUT")) and n.endswith("@" + w)
+                                   for f, n in zip(fam, names)))
+    legs = float(stats.get("legs", 0))
+    front = stats.get("front", {})
     if kernel == "k_assemble":
-        return E * (12 + 16 + 8 * n_fan + 8 * n_acc + 4 * P)
+        return E * (8 + 8 * n_degfan + 8 * n_gs + 8 * n_acc + 4 * P)
     if kernel == "k_leg_emit":
-        return E * 20 + legs * (12 + 8 + 16)
+        return E * 24 + legs * (12 + 16) + front.get(2, 0) * 8
     if kernel == "k_sg_partition":
         return legs * 32
     if kernel == "k_sg_bucket":
         return legs * 16
-    if kernel == "k_window_slots":
-        return Ev * 28
-    if kernel == "k_cyc_level":
-        return legs * 16
+    if kernel == "k_fan_reduce":
+        return Ev * (12 + 8 * W)
+    if kernel == "k_fan_scan":
+        return Ev * (8 + 16 * W)
+    if kernel == "k_cyc_level" and front:
+        return 24.0 * sum(front.values()) / len(front)
     return float("nan")
 
 
@@ -473,19 +490,19 @@ def run_ours(args, ws, rank, local):
         # dominant kernel of the timed region, from its own CUDA events
         dom = max(prof.items(), key=lambda kv: kv[1][1])
         dom_name, (dom_n, dom_ms) = dom
-        n_legs = {}   # each leg is one GS instance, counted on its two edges
-        for j, p in enumerate(pats):
-            if p.name.startswith("GS@"):
-                n_legs[p.name] = float(out[:, j].to(torch.int64).sum().item()) / 2
+        # the leg pass runs on the largest window (smaller ones are counted in it)
+        big = max(int(p.name.split("@")[1]) for p in pats)
+        ws_stats = graph.window_stats(big)
+        stats = {"legs": ws_stats["n_legs"], "front": ws_stats["n_front"]}
         peak, peak_src = measured_peak()
-        alg = algorithmic_bytes(dom_name, E, info["n_list_edges"], pats, n_legs)
+        alg = algorithmic_bytes(dom_name, E, info["n_list_edges"], pats, stats)
         achieved = alg / (dom_ms / dom_n / 1000.0) / 1e9 if alg == alg else None
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                 "traffic": None, "peak_source": peak_src,
                 "launch_ms": dom_ms / dom_n, "share_of_step": dom_ms / plain_ms,
                 "algorithmic_bytes_per_launch": alg, "timed_in": "plain-mode profiled pass",
-                "legs_per_window": n_legs}
+                "leg_pass": {"delta": big, **stats}}
         kernels = {k: {"launches": n, "ms_per_step": round(ms / prof_steps, 4),
                        "share": round(ms / plain_ms, 4)}
                    for k, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])}

@@ -107,6 +107,21 @@ typedef struct aml_graph_info {
 
 aml_status aml_graph_get_info(const aml_graph* g, aml_graph_info* info);
 
+/* Work sizes of one window that earlier mines of this graph measured (no
+ * paper counterpart; for measurement and capacity planning).
+ *   delta    : the window, seconds
+ *   n_legs   : out, temporal 2-paths with distinct ends in the window (the
+ *              GS instances; also the SG leg records), -1 if no mine has
+ *              expanded this window's legs yet
+ *   n_front  : out, int64[AML_MAX_CYCLE + 1]; n_front[j] = paths of j edges
+ *              the level-by-level cycle search held (j >= 2), -1 where no
+ *              mine has built that level; entries 0 and 1 are -1
+ * A window counted inside a larger window's pass (see aml_mine) has no
+ * sizes of its own.  Both pointers must be non-NULL host pointers. */
+#define AML_MAX_CYCLE 8
+aml_status aml_graph_window_stats(const aml_graph* g, int32_t delta, int64_t* n_legs,
+                                  int64_t* n_front);
+
 /* ----------------------------------------------------------- stage programs */
 
 /* One stage of a multi-stage pattern (Sec. 5; per-stage configuration of

@@ -84,6 +84,15 @@ class Graph:
         check(lib().aml_graph_get_info(self._h, ctypes.byref(inf)))
         return {f: getattr(inf, f) for f, _ in inf._fields_ if f != "reserved"}
 
+    def window_stats(self, delta: int) -> dict:
+        """Work sizes earlier mines measured for one window
+        (aml_graph_window_stats): legs and cycle-search frontier per level."""
+        n_legs = ctypes.c_int64()
+        front = (ctypes.c_int64 * 9)()
+        check(lib().aml_graph_window_stats(self._h, int(delta), ctypes.byref(n_legs), front))
+        return {"n_legs": n_legs.value,
+                "n_front": {j: front[j] for j in range(2, 9) if front[j] >= 0}}
+
     def sync(self) -> None:
         check(lib().aml_sync(self._h))
 

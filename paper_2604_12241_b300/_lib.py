@@ -97,6 +97,9 @@ _SIGS = {
                                           ctypes.c_uint32, _VP, ctypes.POINTER(_VP)]),
     "aml_graph_destroy": (ctypes.c_int32, [_VP]),
     "aml_graph_get_info": (ctypes.c_int32, [_VP, ctypes.POINTER(aml_graph_info)]),
+    "aml_graph_window_stats": (ctypes.c_int32, [_VP, ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_int64),
+                                                ctypes.POINTER(ctypes.c_int64)]),
     "aml_pattern_set_create": (ctypes.c_int32, [ctypes.POINTER(aml_pattern), ctypes.c_int32,
                                                 ctypes.POINTER(_VP)]),
     "aml_pattern_set_destroy": (ctypes.c_int32, [_VP]),

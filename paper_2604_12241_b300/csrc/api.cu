@@ -120,6 +120,20 @@ aml_status aml_graph_get_info(const aml_graph* g, aml_graph_info* info) {
   });
 }
 
+aml_status aml_graph_window_stats(const aml_graph* g, int32_t delta, int64_t* n_legs,
+                                  int64_t* n_front) {
+  return guarded("aml_graph_window_stats", [&] {
+    AML_REQUIRE(g && n_legs && n_front, AML_EINVAL, "NULL argument");
+    static_assert(AML_MAX_CYCLE == MAX_CYCLE, "cycle limit of the ABI and the kernels");
+    *n_legs = -1;
+    for (int j = 0; j <= MAX_CYCLE; ++j) n_front[j] = -1;
+    auto it = g->legs.find(delta);
+    if (it == g->legs.end()) return;
+    *n_legs = it->second.n_legs;
+    for (int j = 2; j <= MAX_CYCLE; ++j) n_front[j] = it->second.n_front[j];
+  });
+}
+
 aml_status aml_pattern_set_create(const aml_pattern* patterns, int32_t n_patterns,
                                   aml_pattern_set** out) {
   return guarded("aml_pattern_set_create", [&] {

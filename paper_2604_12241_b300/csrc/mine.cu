@@ -298,7 +298,7 @@ __device__ __forceinline__ void sub_leg_credit(const SubWindows& sub, bool leg, 
 }
 
 template <int NS>
-__global__ void __launch_bounds__(512) k_leg_emit(GraphView g, const int2* __restrict__ qwin,
+__global__ void __launch_bounds__(512, 3) k_leg_emit(GraphView g, const int2* __restrict__ qwin,
                                                   const int32_t* __restrict__ qcb,
                                                   const int64_t* __restrict__ off, LegSink S,
                                                   unsigned long long* __restrict__ acc_cyc2,
