@@ -9,17 +9,18 @@
 //   R(p) - R(p-1) = [prev(p) >= lb(p)] - #{r in [lb(p-1), lb(p)) : next(r) <= p-1}
 // (the window gains p and drops [lb(p-1), lb(p))), with R(row start) = 0.
 //
-// Two launches over contiguous chunks of slots, all W windows at once (the
-// windows are nested, so each lb is searched above the previous one, and
-// the W results of an edge leave in one store):
-//   k_fan_reduce (a thread per slot, a block per chunk of FAN_RBLOCK): lb,
-//     DEG and the delta of every slot, and per chunk the sum of the deltas
-//     after its last row start (all of them when no row starts inside) with
-//     a flag telling whether a row starts inside;
-//   k_fan_scan (a block per tile of FAN_TILE slots): the carry into its tile
-//     from those chunk sums (back to the nearest chunk where a row starts),
-//     then a segmented scan of the deltas (restarting at row starts), and
-//     (DEG, FAN) of every window stored at the edge id of every slot.
+// Two launches over tiles of FAN_TILE consecutive slots (a block each), all
+// W windows at once (the windows are nested, so each window start is
+// searched above the previous one, and the W results of an edge leave in
+// one store):
+//   k_fan_reduce: lb, DEG and the delta of every slot (two pointers along
+//     FAN_ITEMS consecutive slots per thread), and per tile the sum of the
+//     deltas after its last row start (all of them when no row starts
+//     inside) with a flag telling whether a row starts inside;
+//   k_fan_scan: the carry into its tile from those tile sums (back to the
+//     nearest tile where a row starts), then a segmented scan of the deltas
+//     (restarting at row starts), and (DEG, FAN) of every window stored at
+//     the edge id of every slot.
 #include <algorithm>
 #include <type_traits>
 
@@ -31,7 +32,6 @@ namespace aml {
 
 namespace {
 
-constexpr int FAN_RBLOCK = 512;  // slots per k_fan_reduce block (one each)
 constexpr int FAN_BLOCK = 256;
 constexpr int FAN_ITEMS = 8;
 constexpr int FAN_TILE = FAN_BLOCK * FAN_ITEMS;
@@ -108,54 +108,69 @@ __device__ Seg<W> seg_scan_block(const Seg<W>& x, Seg<W>* total) {
   return r;
 }
 
-// deg_s, D: [W][Ev]; chunk_sum: [W][n_red]
+// deg_s, D: [W][Ev]; chunk_sum: [W][n_tiles].  Thread t of block b walks
+// the FAN_ITEMS consecutive slots from b * FAN_TILE + t * FAN_ITEMS: one
+// binary search per window for the slot before its first slot, then every
+// window start only moves forward (two pointers), and the slots it passes
+// are exactly the dropped range of the repeat delta.
 template <int W>
-__global__ void __launch_bounds__(FAN_RBLOCK) k_fan_reduce(const int32_t* __restrict__ rstart,
-                                                           const int32_t* __restrict__ t,
-                                                           const int32_t* __restrict__ prev,
-                                                           const int32_t* __restrict__ next,
-                                                           int64_t Ev, FanDeltas fd,
-                                                           int32_t* __restrict__ deg_s,
-                                                           int32_t* __restrict__ D,
-                                                           int2* __restrict__ chunk_sum) {
-  __shared__ int32_t s_sum[W][FAN_RBLOCK / 32];
+__global__ void __launch_bounds__(FAN_BLOCK) k_fan_reduce(const int32_t* __restrict__ rstart,
+                                                          const int32_t* __restrict__ t,
+                                                          const int32_t* __restrict__ prev,
+                                                          const int32_t* __restrict__ next,
+                                                          int64_t Ev, FanDeltas fd,
+                                                          int32_t* __restrict__ deg_s,
+                                                          int32_t* __restrict__ D,
+                                                          int2* __restrict__ chunk_sum) {
+  __shared__ int32_t s_sum[W][FAN_BLOCK / 32];
   const int lane = threadIdx.x & 31;
-  const int64_t c0 = (int64_t)blockIdx.x * FAN_RBLOCK;
-  const int64_t c1 = c0 + FAN_RBLOCK < Ev ? c0 + FAN_RBLOCK : Ev;
+  const int64_t c0 = (int64_t)blockIdx.x * FAN_TILE;
+  const int64_t c1 = c0 + FAN_TILE < Ev ? c0 + FAN_TILE : Ev;
   const int32_t last_rs = rstart[c1 - 1];  // the last row start at or before the chunk's end
   const int64_t from = last_rs > c0 ? last_rs : c0;
-  const int64_t p64 = c0 + threadIdx.x;
-  const bool in = p64 < c1;
-  const int32_t p = (int32_t)p64;
-  int32_t rs = 0, tp = 0, lb[W], u[W];
-  if (in) {
-    rs = __ldg(rstart + p);
-    tp = __ldg(t + p);
-  }
-  int32_t lo = rs;
+  const int64_t p0 = c0 + (int64_t)threadIdx.x * FAN_ITEMS;
+  const int64_t p1 = p0 + FAN_ITEMS < c1 ? p0 + FAN_ITEMS : c1;
+  int32_t u[W];
 #pragma unroll
-  for (int k = 0; k < W; ++k) {
-    u[k] = 0;
-    lb[k] = in ? lower_t(t, lo, p + 1, (int64_t)tp - fd.d[k]) : 0;  // nested: lb grows
-    lo = lb[k];
-    if (in) deg_s[k * Ev + p] = p - lb[k] + 1;
-  }
-  const int32_t t_before = in && p > rs ? __ldg(t + p - 1) : 0;
-  const int32_t prev_p = in && p > rs ? __ldg(prev + p) : -1;
+  for (int k = 0; k < W; ++k) u[k] = 0;
+  if (p0 < p1) {
+    // window starts of slot p0 - 1 when it lies in p0's row
+    int32_t lb[W];
+    const int32_t rs0 = __ldg(rstart + p0);
+    if (p0 > rs0) {
+      const int64_t tq = __ldg(t + p0 - 1);
+      int32_t lo = rs0;
 #pragma unroll
-  for (int k = 0; k < W; ++k) {
-    // lb(p-1) is the lower lane's lb when that lane holds slot p-1 of the row
-    const int32_t lb_lower = __shfl_up_sync(0xffffffffu, lb[k], 1);
-    if (!in) continue;
-    int32_t d = 0;
-    if (p > rs) {
-      const int32_t lbq =
-          lane > 0 ? lb_lower : lower_t(t, rs, min(lb[k] + 1, p), (int64_t)t_before - fd.d[k]);
-      d = prev_p >= lb[k] ? 1 : 0;
-      for (int32_t r = lbq; r < lb[k]; ++r) d -= (__ldg(next + r) <= p - 1) ? 1 : 0;
+      for (int k = 0; k < W; ++k) {
+        lb[k] = lower_t(t, lo, (int32_t)p0, tq - fd.d[k]);  // nested: lb grows
+        lo = lb[k];
+      }
     }
-    D[k * Ev + p] = d;
-    if (p64 >= from) u[k] = d;
+    for (int64_t p64 = p0; p64 < p1; ++p64) {
+      const int32_t p = (int32_t)p64;
+      const bool head = __ldg(rstart + p) == p;
+      const int64_t tp = __ldg(t + p);
+      const int32_t pv = head ? -1 : __ldg(prev + p);
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        int32_t d = 0;
+        if (head) {
+          lb[k] = p;
+        } else {
+          int32_t l = lb[k], gone = 0;
+          const int64_t tmin = tp - fd.d[k];
+          while (__ldg(t + l) < tmin) {  // stops at p at the latest: t[p] >= tmin
+            gone += __ldg(next + l) <= p - 1 ? 1 : 0;
+            ++l;
+          }
+          lb[k] = l;
+          d = (pv >= l ? 1 : 0) - gone;
+        }
+        deg_s[k * Ev + p] = p - lb[k] + 1;
+        D[k * Ev + p] = d;
+        if (p64 >= from) u[k] += d;
+      }
+    }
   }
 #pragma unroll
   for (int k = 0; k < W; ++k) {
@@ -168,7 +183,7 @@ __global__ void __launch_bounds__(FAN_RBLOCK) k_fan_reduce(const int32_t* __rest
   if (threadIdx.x < W) {
     const int k = threadIdx.x;
     int32_t tot = 0;
-    for (int w = 0; w < FAN_RBLOCK / 32; ++w) tot += s_sum[k][w];
+    for (int w = 0; w < FAN_BLOCK / 32; ++w) tot += s_sum[k][w];
     chunk_sum[(int64_t)k * gridDim.x + blockIdx.x] = make_int2(tot, last_rs >= c0 ? 1 : 0);
   }
 }
@@ -192,7 +207,7 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restric
                                                         const int32_t* __restrict__ eid,
                                                         const int32_t* __restrict__ deg_s,
                                                         const int32_t* __restrict__ D,
-                                                        int64_t Ev, int64_t n_red,
+                                                        int64_t Ev, int64_t n_tiles,
                                                         const int2* __restrict__ chunk_sum,
                                                         int2* __restrict__ df) {
   __shared__ int32_t s_v[W][FAN_SMEM];
@@ -201,21 +216,21 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restric
   const int64_t c0 = (int64_t)blockIdx.x * FAN_TILE;
   const int64_t c1 = c0 + FAN_TILE < Ev ? c0 + FAN_TILE : Ev;
   if (threadIdx.x < 32) {
-    // deltas of the row running into the tile: the sums of the reduce
-    // chunks before it back to the nearest one where a row starts (chunk 0
-    // always has one: slot 0), 32 chunks per step
+    // deltas of the row running into the tile: the sums of the tiles before
+    // it back to the nearest one where a row starts (tile 0 always has one:
+    // slot 0), 32 tiles per step
     const int lane = threadIdx.x;
     int32_t v[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) v[k] = 0;
-    for (int64_t top = c0 / FAN_RBLOCK - 1; top >= 0; top -= 32) {
+    for (int64_t top = (int64_t)blockIdx.x - 1; top >= 0; top -= 32) {
       const int64_t c = top - lane;
       const int32_t flag = c >= 0 ? chunk_sum[c].y : 1;
       const unsigned starts = __ballot_sync(0xffffffffu, flag != 0);
       const int first = starts ? __ffs(starts) - 1 : 31;  // lanes [0, first] count
 #pragma unroll
       for (int k = 0; k < W; ++k) {
-        int32_t x = (c >= 0 && lane <= first) ? chunk_sum[k * n_red + c].x : 0;
+        int32_t x = (c >= 0 && lane <= first) ? chunk_sum[k * n_tiles + c].x : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         v[k] += x;
@@ -283,16 +298,15 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restric
 
 template <int W>
 void fan_launch(const Adj& a, int64_t Ev, const FanDeltas& fd, int2* df, cudaStream_t s) {
-  const int64_t n_red = (Ev + FAN_RBLOCK - 1) / FAN_RBLOCK;
   const int64_t n_tiles = (Ev + FAN_TILE - 1) / FAN_TILE;
   DBuf<int32_t> deg_s((size_t)W * Ev, s), D((size_t)W * Ev, s);
-  DBuf<int2> sums((size_t)W * n_red, s);
+  DBuf<int2> sums((size_t)W * n_tiles, s);
   AML_LAUNCH("k_fan_reduce", s,
-             k_fan_reduce<W><<<(unsigned)n_red, FAN_RBLOCK, 0, s>>>(
+             k_fan_reduce<W><<<(unsigned)n_tiles, FAN_BLOCK, 0, s>>>(
                  a.rstart, a.t, a.prev, a.next, Ev, fd, deg_s.p, D.p, sums.p));
   AML_LAUNCH("k_fan_scan", s,
              k_fan_scan<W><<<(unsigned)n_tiles, FAN_BLOCK, 0, s>>>(a.rstart, a.eid, deg_s.p, D.p,
-                                                                   Ev, n_red, sums.p, df));
+                                                                   Ev, n_tiles, sums.p, df));
 }
 
 }  // namespace

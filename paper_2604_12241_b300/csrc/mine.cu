@@ -455,11 +455,12 @@ __global__ void __launch_bounds__(256) k_sg_partition(const LegRec* __restrict__
 }
 
 
-__device__ __forceinline__ void sg_credit(unsigned long long* acc, const LegRec& r,
+// c instances credited to the leg's two edges
+__device__ __forceinline__ void sg_credit(unsigned long long* acc, int32_t a, int32_t b,
                                           unsigned long long c) {
   if (c) {
-    atomicAdd(acc + r.a, c);
-    atomicAdd(acc + r.b, c);
+    atomicAdd(acc + a, c);
+    atomicAdd(acc + b, c);
   }
 }
 
@@ -482,7 +483,7 @@ __device__ __forceinline__ int64_t sg_span(const int4& r, const int4& o, int32_t
 // the leg's two edges
 template <int NS>
 __device__ __forceinline__ void sg_count_partners(const int4* grp, uint32_t j0, uint32_t j1,
-                                                  const int4& own, const LegRec& r,
+                                                  const int4& own, int32_t a,
                                                   int32_t delta, int32_t new_from,
                                                   unsigned long long* acc,
                                                   const SubWindows& sub) {
@@ -495,10 +496,10 @@ __device__ __forceinline__ void sg_count_partners(const int4* grp, uint32_t j0, 
     for (int i = 0; i < NS; ++i)
       if (i < sub.n && span <= sub.delta[i]) ++ks[i];
   }
-  if (acc) sg_credit(acc, r, k);
+  if (acc) sg_credit(acc, a, own.w, k);
 #pragma unroll
   for (int i = 0; i < NS; ++i)
-    if (i < sub.n && sub.sg[i]) sg_credit(sub.sg[i], r, ks[i]);
+    if (i < sub.n && sub.sg[i]) sg_credit(sub.sg[i], a, own.w, ks[i]);
 }
 
 // Groups one bucket's records by key in a shared-memory hash table and
@@ -512,24 +513,31 @@ __device__ __forceinline__ void sg_count_partners(const int4* grp, uint32_t j0, 
 template <int CAP, int TAB>
 struct SgSmem {
   int4 grp[CAP];                 // leg_info of grouped legs, by group
+  int32_t ga[CAP];               // the scatter edge a of each group entry
+  uint16_t gslot[CAP];           // the table slot (group) of each group entry
   unsigned long long key[TAB];   // filed keys; later (as uint32) group cursors
   uint32_t cnt[TAB];             // records per slot
-  uint16_t slot[CAP];            // each record's slot
-  uint16_t pos[CAP];             // record index of each group-array entry
   uint32_t n_grouped;
 };
 
-template <int CAP, int TAB, int NS>
+template <int CAP, int TAB, int NS, int BS>
 __device__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRec* __restrict__ R, int n,
                                 int32_t delta, const int32_t* __restrict__ dst,
                                 const int32_t* __restrict__ ts,
                                 unsigned long long* __restrict__ acc, int32_t new_from,
                                 const SubWindows& sub) {
-  constexpr int PER = (CAP + 255) / 256;  // records per thread (blocks of 256)
+  constexpr int PER = (CAP + BS - 1) / BS;  // records per thread (blocks of BS)
   uint32_t* cur = reinterpret_cast<uint32_t*>(S.key);
+  // this thread's records stay in registers from the first read on
+  LegRec r[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int i = threadIdx.x + k * BS;
+    if (i < n) r[k] = R[i];
+  }
   int tab = 64;
   while (tab < 2 * n) tab <<= 1;
-  for (int t = threadIdx.x; t < tab; t += blockDim.x) {
+  for (int t = threadIdx.x; t < tab; t += BS) {
     S.key[t] = ~0ull;
     S.cnt[t] = 0;
   }
@@ -537,66 +545,65 @@ __device__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRec* __restrict__ 
   __syncthreads();
   // file every record under its key; remember which keys this thread filed
   uint32_t lead = 0;
+  uint16_t h[PER];
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
-    const int i = threadIdx.x + k * (int)blockDim.x;
-    if (i >= n) break;
-    const unsigned long long key = R[i].key;
-    uint32_t h = (uint32_t)mix64(key) & (uint32_t)(tab - 1);
+    if (threadIdx.x + k * BS >= n) break;
+    const unsigned long long key = r[k].key;
+    uint32_t q = (uint32_t)mix64(key) & (uint32_t)(tab - 1);
     for (int probe = 0; probe < tab; ++probe) {  // n < tab: a slot is always found
-      const unsigned long long cur_key = S.key[h];
+      const unsigned long long cur_key = S.key[q];
       if (cur_key == key) break;
       if (cur_key == ~0ull) {
-        const unsigned long long old = atomicCAS(&S.key[h], ~0ull, key);
+        const unsigned long long old = atomicCAS(&S.key[q], ~0ull, key);
         if (old == ~0ull) {
           lead |= 1u << k;
           break;
         }
         if (old == key) break;
       }
-      h = (h + 1) & (uint32_t)(tab - 1);
+      q = (q + 1) & (uint32_t)(tab - 1);
     }
-    S.slot[i] = (uint16_t)h;
-    atomicAdd(&S.cnt[h], 1u);
+    h[k] = (uint16_t)q;
+    atomicAdd(&S.cnt[q], 1u);
   }
   __syncthreads();
   // group leaders reserve their group's range (keys are no longer read)
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
-    const int i = threadIdx.x + k * (int)blockDim.x;
-    if (i >= n) break;
+    if (threadIdx.x + k * BS >= n) break;
     if ((lead >> k) & 1u) {
-      const uint32_t h = S.slot[i];
-      const uint32_t c = S.cnt[h];
-      if (c >= 2) cur[h] = atomicAdd(&S.n_grouped, c);
+      const uint32_t c = S.cnt[h[k]];
+      if (c >= 2) cur[h[k]] = atomicAdd(&S.n_grouped, c);
     }
   }
   __syncthreads();
   const uint32_t n_grouped = S.n_grouped;
   if (n_grouped == 0) return;
   // the grouped legs' data, group by group (cursor ends at the group's end)
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const uint32_t h = S.slot[i];
-    if (S.cnt[h] >= 2) {
-      const uint32_t at = atomicAdd(&cur[h], 1u);
-      S.grp[at] = leg_info(R[i], dst, ts);
-      S.pos[at] = (uint16_t)i;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    if (threadIdx.x + k * BS >= n) break;
+    if (S.cnt[h[k]] >= 2) {
+      const uint32_t at = atomicAdd(&cur[h[k]], 1u);
+      S.grp[at] = leg_info(r[k], dst, ts);
+      S.ga[at] = r[k].a;
+      S.gslot[at] = h[k];
     }
   }
   __syncthreads();
-  for (uint32_t p = threadIdx.x; p < n_grouped; p += blockDim.x) {
-    const int i = S.pos[p];
-    const uint32_t h = S.slot[i];
-    const uint32_t c = S.cnt[h];
-    const uint32_t end = cur[h];
-    sg_count_partners<NS>(S.grp, end - c, end, S.grp[p], R[i], delta, new_from, acc, sub);
+  for (uint32_t p = threadIdx.x; p < n_grouped; p += BS) {
+    const uint32_t q = S.gslot[p];
+    const uint32_t c = S.cnt[q];
+    const uint32_t end = cur[q];
+    sg_count_partners<NS>(S.grp, end - c, end, S.grp[p], S.ga[p], delta, new_from, acc, sub);
   }
 }
 
 // One block per bucket of up to SG_CAP records; larger buckets are listed
 // in overflow (count at overflow[0]) for k_sg_bucket_big.
 template <int NS>
-__global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ rec,
+__global__ void __launch_bounds__(SG_BLOCK, 8) k_sg_bucket(const LegRec* __restrict__ rec,
                                                    const uint32_t* __restrict__ bend,
                                                    int32_t delta, const int32_t* __restrict__ dst,
                                                    const int32_t* __restrict__ ts,
@@ -612,7 +619,8 @@ __global__ void __launch_bounds__(256) k_sg_bucket(const LegRec* __restrict__ re
     if (threadIdx.x == 0) overflow[1 + atomicAdd(overflow, 1u)] = blockIdx.x;
     return;
   }
-  sg_group_bucket<SG_CAP, SG_TAB, NS>(S, rec + base, (int)n, delta, dst, ts, acc, new_from, sub);
+  sg_group_bucket<SG_CAP, SG_TAB, NS, SG_BLOCK>(S, rec + base, (int)n, delta, dst, ts, acc,
+                                                new_from, sub);
 }
 
 // The listed buckets, a few blocks looping over the list (the count is read
@@ -636,7 +644,7 @@ __global__ void __launch_bounds__(256) k_sg_bucket_big(const LegRec* __restrict_
     const int64_t n = (int64_t)bend[b] - base;
     const LegRec* R = rec + base;
     if (n <= SG_CAP_BIG) {
-      sg_group_bucket<SG_CAP_BIG, SG_TAB_BIG, NS>(S, R, (int)n, delta, dst, ts, acc, new_from,
+      sg_group_bucket<SG_CAP_BIG, SG_TAB_BIG, NS, 256>(S, R, (int)n, delta, dst, ts, acc, new_from,
                                               sub);
     } else {
       for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -653,10 +661,10 @@ __global__ void __launch_bounds__(256) k_sg_bucket_big(const LegRec* __restrict_
           for (int q = 0; q < NS; ++q)
             if (q < sub.n && span <= sub.delta[q]) ++cs[q];
         }
-        if (acc) sg_credit(acc, r, c);
+        if (acc) sg_credit(acc, r.a, r.b, c);
 #pragma unroll
         for (int q = 0; q < NS; ++q)
-          if (q < sub.n && sub.sg[q]) sg_credit(sub.sg[q], r, cs[q]);
+          if (q < sub.n && sub.sg[q]) sg_credit(sub.sg[q], r.a, r.b, cs[q]);
       }
     }
     __syncthreads();  // the shared table is reused by the next bucket
@@ -854,8 +862,8 @@ __global__ void __launch_bounds__(512) k_cyc_emit(int64_t n, const int32_t* __re
 // earlier kernels left in edge order: DEG and FAN per window and direction,
 // GS = legs starting + legs ending at the edge, SG and CYC from the 64-bit
 // accumulators; saturated to 32 bits.
-// The block's rows are staged in shared memory (odd row stride: no bank
-// conflicts) and stored column-contiguous, so the stores coalesce.
+// The block's rows are staged in shared memory and stored as one contiguous
+// range when the output has no padding (ld = P), so the stores coalesce.
 
 __device__ __forceinline__ uint64_t assemble_value(const AssembleParams& P, const ColDesc cd,
                                                    int32_t e) {
@@ -880,23 +888,25 @@ __device__ __forceinline__ uint64_t assemble_value(const AssembleParams& P, cons
 }
 
 __global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
-  extern __shared__ uint32_t s_rows[];
+  extern __shared__ uint32_t s_rows[];  // the block's rows, row-major
   const GraphView& g = P.g;
-  const int nc = P.ncols, rs = nc | 1;
+  const int nc = P.ncols;
   const int64_t e0 = (int64_t)blockIdx.x * ASM_BLOCK;
   const int nrows = g.E - e0 < ASM_BLOCK ? (int)(g.E - e0) : ASM_BLOCK;
   const int tot = nrows * nc;
-  if (e0 < P.accumulate_from) {  // old rows keep what they hold
+  uint32_t* out = P.counts + e0 * P.ld;
+  const bool dense = P.ld == nc;  // the block's rows are one contiguous range
+  if (e0 < P.accumulate_from) {   // old rows keep what they hold
     for (int i = threadIdx.x; i < tot; i += ASM_BLOCK) {
-      const int r = i / nc, c = i - r * nc;
-      s_rows[r * rs + c] = P.counts[(e0 + r) * P.ld + c];
+      const int r = dense ? 0 : i / nc;
+      s_rows[i] = out[dense ? i : r * P.ld + (i - r * nc)];
     }
     __syncthreads();
   }
   if ((int)threadIdx.x < nrows) {
     const int64_t e64 = e0 + threadIdx.x;
     const int32_t e = (int32_t)e64;
-    uint32_t* row = s_rows + threadIdx.x * rs;
+    uint32_t* row = s_rows + threadIdx.x * nc;
     const bool add = e64 < P.accumulate_from;  // an old row: add its new instances
     const int32_t u = g.src[e], v = g.dst[e];
     if (u == v) {
@@ -916,8 +926,8 @@ __global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
   }
   __syncthreads();
   for (int i = threadIdx.x; i < tot; i += ASM_BLOCK) {
-    const int r = i / nc, c = i - r * nc;
-    P.counts[(e0 + r) * P.ld + c] = s_rows[r * rs + c];
+    const int r = dense ? 0 : i / nc;
+    out[dense ? i : r * P.ld + (i - r * nc)] = s_rows[i];
   }
 }
 
@@ -977,7 +987,7 @@ void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
       if (dev < 64) smem_set[dev][NS] = true;
     }
     AML_LAUNCH("k_sg_bucket", s,
-               k_sg_bucket<NS><<<n_buckets, 256, 0, s>>>(rec, bend, delta, dst, ts, acc,
+               k_sg_bucket<NS><<<n_buckets, SG_BLOCK, 0, s>>>(rec, bend, delta, dst, ts, acc,
                                                          new_from, overflow, sub));
     AML_LAUNCH("k_sg_bucket_big", s,
                k_sg_bucket_big<NS><<<(unsigned)sm_count(), 256, big, s>>>(

@@ -10,6 +10,7 @@ constexpr int MAX_DELTAS = 16;  // distinct windows per pattern set
 constexpr int MAX_CYCLE = 8;    // longest cycle
 constexpr int SG_CAP = 512;        // leg records one SG bucket block groups in shared memory
 constexpr int SG_TAB = 1024;       // its hash-table slots (load <= 0.5)
+constexpr int SG_BLOCK = 256;      // threads of that block
 constexpr int SG_CAP_BIG = 4096;   // the same for the larger buckets (k_sg_bucket_big)
 constexpr int SG_TAB_BIG = 8192;
 constexpr int SG_PART_ITEMS = 4;     // records per thread in k_sg_partition
