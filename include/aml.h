@@ -420,7 +420,9 @@ aml_status aml_launch_count(int64_t* out);
 
 /* Start (on != 0) or stop timing every kernel launch with a pair of CUDA
  * events recorded on the launching stream.  Launches during stream capture
- * are not timed.  Costs two event records per launch while on. */
+ * are not timed.  Costs two event records per launch while on; mines run
+ * their kernels one after another meanwhile (no concurrent branches), so
+ * each time is the kernel's own. */
 aml_status aml_profile_enable(int32_t on);
 
 typedef struct aml_kernel_stat {

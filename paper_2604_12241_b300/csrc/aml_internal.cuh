@@ -154,6 +154,10 @@ struct aml_graph {
   std::vector<aml::MineExec> execs;   // captured mines (AML_MINE_GRAPH)
   std::vector<aml::CostModel> cost_models;  // per window (aml_cost_train)
   cudaStream_t capture_stream = nullptr;
+  // side streams and fork/join events of a mine's independent branches
+  // (created by the first full mine; captured mines use them too)
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t branch_ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace aml {

@@ -269,6 +269,10 @@ void destroy_graph(aml_graph* g) {
   cudaDeviceSynchronize();
   drop_captured_mines(g);
   if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
+  for (cudaStream_t st : g->side)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : g->branch_ev)
+    if (ev) cudaEventDestroy(ev);
   free_graph(g);
 }
 

@@ -33,6 +33,27 @@ struct WindowPlan {
   bool needs_off() const { return gs || emit_legs(); }
 };
 
+// Side streams for a mine's independent branches (DEG/FAN beside the leg
+// pass; SG beside the cycle search), created outside any capture; false if
+// they do not exist and cannot be made now (the mine then runs in order).
+bool ensure_branches(aml_graph* g, cudaStream_t s) {
+  if (g->side[1] && g->branch_ev[3]) return true;
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  AML_CUDA(cudaStreamIsCapturing(s, &st));
+  if (st != cudaStreamCaptureStatusNone) return false;
+  for (cudaStream_t& x : g->side)
+    if (!x) AML_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : g->branch_ev)
+    if (!e) AML_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return true;
+}
+
+// work enqueued on `to` from now on runs after what `from` holds so far
+void branch_wait(cudaEvent_t ev, cudaStream_t from, cudaStream_t to) {
+  AML_CUDA(cudaEventRecord(ev, from));
+  AML_CUDA(cudaStreamWaitEvent(to, ev, 0));
+}
+
 }  // namespace
 
 void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
@@ -131,9 +152,16 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   const int64_t Ev = g->Ev;
   // 1. trailing windows, per direction: (DEG, FAN) of every window at once
   // when any wants FAN (groups of FAN_MAX_W, largest delta first), else DEG
-  // alone window by window
+  // alone window by window.  Planned and allocated here, launched below.
+  struct DfJob {
+    const Adj* a;
+    int nw;
+    bool fan;
+    int32_t deltas[FAN_MAX_W];
+    int2* df;
+  };
+  std::vector<DfJob> df_jobs;
   for (int dir = 0; dir < 2 && Ev > 0; ++dir) {
-    const Adj& a = dir == 0 ? g->out : g->in;
     std::vector<int> ws;
     bool any_fan = false;
     for (size_t w = 0; w < wins.size(); ++w) {
@@ -146,26 +174,38 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     std::sort(ws.begin(), ws.end(), [&](int x, int y) { return wins[x].delta > wins[y].delta; });
     const int group = any_fan ? FAN_MAX_W : 1;
     for (size_t g0 = 0; g0 < ws.size(); g0 += group) {
-      const int nw = (int)std::min<size_t>(group, ws.size() - g0);
-      keep_df.emplace_back((size_t)E * nw, s);
-      int2* df = keep_df.back().p;
-      int32_t deltas[FAN_MAX_W];
-      for (int k = 0; k < nw; ++k) {
+      DfJob job{dir == 0 ? &g->out : &g->in, (int)std::min<size_t>(group, ws.size() - g0),
+                any_fan, {}, nullptr};
+      keep_df.emplace_back((size_t)E * job.nw, s);
+      job.df = keep_df.back().p;
+      for (int k = 0; k < job.nw; ++k) {
         const int w = ws[g0 + k];
-        deltas[k] = wins[w].delta;
-        (dir == 0 ? P.df_out : P.df_in)[w] = df + k;
-        (dir == 0 ? P.df_stride_out : P.df_stride_in)[w] = nw;
+        job.deltas[k] = wins[w].delta;
+        (dir == 0 ? P.df_out : P.df_in)[w] = job.df + k;
+        (dir == 0 ? P.df_stride_out : P.df_stride_in)[w] = job.nw;
       }
-      if (any_fan) {
-        fan_per_edge(a, Ev, nw, deltas, df, s);
-      } else {
-        AML_LAUNCH("k_window_slots", s,
-                   k_window_slots<<<grid_for(Ev, B), B, 0, s>>>(a.rstart, a.t, a.eid, a.prev,
-                                                                a.next, Ev, deltas[0], nullptr,
-                                                                nullptr, df));
-      }
+      df_jobs.push_back(job);
     }
   }
+
+  // Independent branches run on side streams (full mines only; not while
+  // kernels are timed one by one): buffers used across streams are
+  // allocated on s before the fork and freed on s after the join.
+  const bool branches = new_from == 0 && !profiling_enabled() && ensure_branches(g, s);
+  cudaStream_t s_fan = branches ? g->side[0] : s;
+  cudaStream_t s_sg = branches ? g->side[1] : s;
+  if (branches) branch_wait(g->branch_ev[0], s, s_fan);
+  for (const DfJob& job : df_jobs) {
+    if (job.fan) {
+      fan_per_edge(*job.a, Ev, job.nw, job.deltas, job.df, s_fan);
+    } else {
+      AML_LAUNCH("k_window_slots", s_fan,
+                 k_window_slots<<<grid_for(Ev, B), B, 0, s_fan>>>(
+                     job.a->rstart, job.a->t, job.a->eid, job.a->prev, job.a->next, Ev,
+                     job.deltas[0], nullptr, nullptr, job.df));
+    }
+  }
+  if (branches) AML_CUDA(cudaEventRecord(g->branch_ev[1], s_fan));  // joined before assembly
 
   for (size_t w = 0; w < wins.size(); ++w) {
     WindowPlan& wp = wins[w];
@@ -313,22 +353,26 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       }
     }
     // 3. scatter-gather: bucket the leg records, group each bucket by (s, d)
+    // (beside the cycle search: disjoint accumulator columns)
+    const bool sg_branch = branches && sg_any && n_sg > 1;
+    if (sg_branch) branch_wait(g->branch_ev[2], s, s_sg);
     if (sg_any && n_sg > 1) {
+      cudaStream_t t = sg_branch ? s_sg : s;
       const int64_t nl = n_sg;
       // bucket starts (the sizes sum to < 2^32, so the 32-bit scan is exact
       // read as unsigned); the partition leaves the bucket ends
       scan_i32(reinterpret_cast<const int32_t*>(hist.p), reinterpret_cast<int32_t*>(hist.p), nb,
-               false, s);
-      DBuf<LegRec> part((size_t)nl, s);
-      AML_LAUNCH("k_sg_partition", s,
-                 k_sg_partition<<<grid_for(nl, 256 * SG_PART_ITEMS), 256, 0, s>>>(
+               false, t);
+      DBuf<LegRec> part((size_t)nl, t);
+      AML_LAUNCH("k_sg_partition", t,
+                 k_sg_partition<<<grid_for(nl, 256 * SG_PART_ITEMS), 256, 0, t>>>(
                      rec.p, nl, S.bits, hist.p, part.p));
       // buckets beyond SG_CAP records: listed by k_sg_bucket, grouped by
       // k_sg_bucket_big (one large-table block per SM)
-      DBuf<uint32_t> overflow((size_t)nb + 1, s);
-      AML_CUDA(cudaMemsetAsync(overflow.p, 0, sizeof(uint32_t), s));
+      DBuf<uint32_t> overflow((size_t)nb + 1, t);
+      AML_CUDA(cudaMemsetAsync(overflow.p, 0, sizeof(uint32_t), t));
       unsigned long long* acc_sg = wp.sg ? acc.p + (int64_t)wp.sg_slot * E : nullptr;
-      launch_sg_buckets((unsigned)nb, s, part.p, hist.p, wp.delta, gv.dst, gv.ts, acc_sg,
+      launch_sg_buckets((unsigned)nb, t, part.p, hist.p, wp.delta, gv.dst, gv.ts, acc_sg,
                         new_from, overflow.p, sub);
     }
     // 4. cycles of length >= 3: one persistent cost-binned launch ...
@@ -370,7 +414,10 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
         n = nn;
       }
     }
+    // the window's buffers (rec, hist, ...) are freed on s after this join
+    if (sg_branch) branch_wait(g->branch_ev[3], s_sg, s);
   }
+  if (branches) AML_CUDA(cudaStreamWaitEvent(s, g->branch_ev[1], 0));
   AML_LAUNCH("k_assemble", s,
              k_assemble<<<grid_for(E, ASM_BLOCK), ASM_BLOCK,
                           (size_t)ASM_BLOCK * (ncols | 1) * sizeof(uint32_t), s>>>(P));

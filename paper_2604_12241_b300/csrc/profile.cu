@@ -64,6 +64,8 @@ LaunchScope::~LaunchScope() {
   if (cudaEventRecord(b_, s_) == cudaSuccess) g_pending.push_back({name_, a_, b_});
 }
 
+bool profiling_enabled() { return g_enabled.load(std::memory_order_relaxed); }
+
 long long launch_count() { return g_launches.load(); }
 
 void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }

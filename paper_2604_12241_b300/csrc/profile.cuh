@@ -20,6 +20,7 @@ class LaunchScope {
 };
 
 long long launch_count();
+bool profiling_enabled();  // aml_profile_enable is on
 void add_launches(long long n);  // kernels launched through a replayed CUDA graph
 
 }  // namespace aml
