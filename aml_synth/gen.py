@@ -10,17 +10,20 @@ Recipe (one call = one graph):
     count and water-filled so no expected degree exceeds ``d_max``; the two
     weight vectors are independently permuted over the ids (Chung-Lu style
     preferential attachment);
-  * each background edge draws src ~ out-weight and dst ~ (in-weight + 1);
-    self-loops are redrawn;
-  * timestamps are uniform int32 seconds over ``days`` days;
+  * each background edge draws src ~ out-weight and dst ~ (in-weight + 1)
+    independently (drawn as per-account multinomial counts dealt in random
+    order); self-loops are redrawn;
+  * timestamps are uniform int32 seconds over ``days`` days (drawn, sorted
+    and dealt in order to the randomly ordered edges: the same law);
   * amounts are lognormal(mu=6, sigma=2), float32;
   * planted motifs: scatter-gathers with 2..6 intermediaries and temporal
     cycles of length 3..5, all edges of one motif inside one 24h span with
     strictly increasing timestamps inside each leg/cycle; half of them use
     reserved fresh account ids (n_bg..n_nodes-1, touched by nothing else) and
     half reuse random background accounts;
-  * all edges are finally stably sorted by timestamp, so edge ids are
-    positions in time order (ties keep generation order).
+  * the motif edges are merged into the time order, so edge ids are
+    positions in time order (ties: background edges first, then motif
+    edges in generation order).
 """
 from __future__ import annotations
 
@@ -111,15 +114,22 @@ def generate(n_nodes: int, n_edges: int, alpha: float, d_max: Optional[float],
 
     w_out = capped_zipf_weights(n_bg, alpha, n_bg_edges, d_max, rng)
     w_in = capped_zipf_weights(n_bg, alpha, n_bg_edges, d_max, rng) + 1.0
-    c_out = np.cumsum(w_out)
+    # iid draws src ~ w_out, dst ~ w_in: per-account counts (multinomial),
+    # each column dealt in random order (a uniform shuffle of iid draws is
+    # again iid); src == dst pairs are redrawn
+    ids = np.arange(n_bg, dtype=np.int32)
+    src = np.repeat(ids, rng.multinomial(n_bg_edges, w_out / w_out.sum()))
+    rng.shuffle(src)
+    dst = np.repeat(ids, rng.multinomial(n_bg_edges, w_in / w_in.sum()))
+    rng.shuffle(dst)
     c_in = np.cumsum(w_in)
-    src = _draw(rng, c_out, n_bg_edges)
-    dst = _draw(rng, c_in, n_bg_edges)
     bad = np.nonzero(src == dst)[0]
     while bad.size:
         dst[bad] = _draw(rng, c_in, bad.size)
         bad = bad[src[bad] == dst[bad]]
-    ts = rng.integers(0, span, size=n_bg_edges, dtype=np.int64)
+    # iid uniform times, independent of the (src, dst) pairs, which are in
+    # random order: dealing the sorted times in order gives the same law
+    ts = np.sort(rng.integers(0, span, size=n_bg_edges, dtype=np.int64))
 
     # planted motifs: (src, dst, t) lists plus bookkeeping of local indices
     m_src: List[int] = []
@@ -164,19 +174,25 @@ def generate(n_nodes: int, n_edges: int, alpha: float, d_max: Optional[float],
             m_src.append(ids[j]); m_dst.append(ids[(j + 1) % k]); m_ts.append(t0 + int(offs[j]))
         plans.append(("cycle", k, bool(cyc_fresh[i]), list(range(base, base + k))))
 
-    all_src = np.concatenate([src, np.asarray(m_src, dtype=np.int32)])
-    all_dst = np.concatenate([dst, np.asarray(m_dst, dtype=np.int32)])
-    all_ts = np.concatenate([ts, np.asarray(m_ts, dtype=np.int64)])
-    order = np.argsort(all_ts, kind="stable")
-    inv = np.empty_like(order)
-    inv[order] = np.arange(order.shape[0])
-    amount = rng.lognormal(6.0, 2.0, size=order.shape[0]).astype(np.float32)
+    # merge the motif edges into the time order: after background edges of
+    # equal time, among themselves in generation order
+    m_src_a = np.asarray(m_src, dtype=np.int32)
+    m_dst_a = np.asarray(m_dst, dtype=np.int32)
+    m_ts_a = np.asarray(m_ts, dtype=np.int64)
+    mo = np.argsort(m_ts_a, kind="stable")
+    pos = np.searchsorted(ts, m_ts_a[mo], side="right")
+    final = np.empty(mo.size, dtype=np.int64)
+    final[mo] = pos + np.arange(mo.size)        # final edge id of each motif edge
+    all_src = np.insert(src, pos, m_src_a[mo])
+    all_dst = np.insert(dst, pos, m_dst_a[mo])
+    all_ts = np.insert(ts, pos, m_ts_a[mo])
+    amount = rng.lognormal(6.0, 2.0, size=all_ts.shape[0]).astype(np.float32)
     motifs = []
     for kind, k, fresh, loc in plans:
-        motifs.append(Motif(kind, k, fresh, inv[n_bg_edges + np.asarray(loc, dtype=np.int64)]))
-    g = Graph(src=np.ascontiguousarray(all_src[order]),
-              dst=np.ascontiguousarray(all_dst[order]),
-              ts=np.ascontiguousarray(all_ts[order].astype(np.int32)),
+        motifs.append(Motif(kind, k, fresh, final[np.asarray(loc, dtype=np.int64)]))
+    g = Graph(src=np.ascontiguousarray(all_src),
+              dst=np.ascontiguousarray(all_dst),
+              ts=np.ascontiguousarray(all_ts.astype(np.int32)),
               amount=amount, n_nodes=n_nodes, motifs=motifs, name=name,
               params=dict(n_nodes=n_nodes, n_edges=n_edges, alpha=alpha, d_max=d_max,
                           days=days, seed=seed, n_sg=n_sg, n_cycles=n_cycles))

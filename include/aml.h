@@ -328,15 +328,17 @@ aml_status aml_sync(aml_graph* g);
 
 /* --------------------------------------------------------------- streaming */
 
-/* Streaming recount (Sec. 5, "Integration with streaming analytics": each
- * arriving transaction increments the counts of all instances it takes part
- * in; incremental processing with localized updates).  Transactions arrive
- * in batches whose timestamps never decrease; edges get global row ids in
- * arrival order.  After every append, each resident row holds the count of
- * its column over the whole history.  A batch B is recounted exactly by
- * mining the window W of resident edges within delta_max of B twice (with and
- * without B) and crediting the difference: the instances B creates.  Rows
- * older than t_max - resident_window are evicted. */
+/* Streaming recount (Sec. 5, streaming use: a new transaction adds to the
+ * count of every instance it completes, and only its neighbourhood is
+ * re-examined).  Transactions arrive in batches whose timestamps never
+ * decrease; edges get global row ids in arrival order.  After every append,
+ * each resident row holds the count of its column over the whole history.
+ * A batch B is recounted exactly by one mine of B and the window W of
+ * resident edges at most delta_max older than B's first edge that counts
+ * only the instances whose latest edge is in B (those B creates) and adds
+ * them to the stored rows.  An append evicts the rows older than both
+ * t_max - resident_window and B's first time - delta_max (no later batch
+ * can reach them). */
 typedef struct aml_stream aml_stream;
 
 typedef struct aml_stream_batch {

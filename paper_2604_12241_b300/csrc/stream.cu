@@ -16,10 +16,11 @@
 // batch rows.  Trailing-window columns (DEG, FAN) of old rows never change:
 // later edges are outside their windows.
 //
-// Resident rows live in device arrays compacted on demand; rows older than
-// t_now - resident_window are evicted.  resident_window >= delta_max keeps
-// every instance of a resident row visible while it is counted, so resident
-// rows hold full-history counts.  A batch that would not fit the memory
+// Resident rows live in device arrays compacted on demand; an append evicts
+// the rows older than both t_now - resident_window and t_first(B) -
+// delta_max (W must stay resident while B is counted).  resident_window >=
+// delta_max keeps every instance of a resident row visible while it is
+// counted, so resident rows hold full-history counts.  A batch that would not fit the memory
 // budget is refused (AML_EADMIT) before any state changes.
 #include <algorithm>
 #include <cstring>
@@ -195,9 +196,11 @@ aml_status aml_stream_append(aml_stream* st, const int32_t* src, const int32_t* 
     }
     AML_REQUIRE(!st->any || ht[0] >= st->t_max, AML_ELATE,
                 "batch starts before the latest timestamp already appended");
-    // eviction and admission plan
+    // eviction and admission plan: rows older than the resident window go,
+    // except those the batch's recount window W still needs
     const int32_t t_first = ht[0], t_last = ht[n - 1];
-    const int64_t cutoff = (int64_t)t_last - st->window;
+    const int64_t cutoff = std::min((int64_t)t_last - st->window,
+                                    (int64_t)t_first - st->delta_max);
     const int64_t new_lo =
         std::lower_bound(st->hts.begin() + st->lo, st->hts.begin() + st->hi, cutoff,
                          [](int32_t a, int64_t b) { return (int64_t)a < b; }) -

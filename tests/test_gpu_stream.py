@@ -86,3 +86,26 @@ def test_stream_refuses_bad_batches():
     r0, nr = inf["resident_first_row"], inf["resident_rows"]
     np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
     st.close()
+
+
+def test_stream_hi_medium_shape_at_tenth_scale():
+    """The serving configuration's shape (Zipf 1.05, hubs, 20 columns, a
+    7-day resident window) at a tenth of its size: batches of log-uniform
+    size in [1e3, 1e5]; the resident rows equal a full mine at the end."""
+    g = aml_synth.workload("hi-medium", scale=0.1)
+    pats = P.workload_patterns("hi-medium")
+    ps = aml.PatternSet(pats)
+    st = aml.Stream(ps, g.n_nodes, resident_window=7 * P.DAY, mem_budget=8 << 30)
+    rng = np.random.default_rng(5)
+    pos, E = 0, g.n_edges
+    while pos < E:
+        n = int(min(E - pos, np.exp(rng.uniform(np.log(1e3), np.log(1e5)))))
+        st.append(g.src[pos:pos + n], g.dst[pos:pos + n], g.ts[pos:pos + n],
+                  g.amount[pos:pos + n])
+        pos += n
+    inf = st.info()
+    r0, nr = inf["resident_first_row"], inf["resident_rows"]
+    assert r0 > 0 and r0 + nr == E
+    want = full_mine(g, E, pats)
+    np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
+    st.close()
