@@ -105,6 +105,8 @@ typedef struct aml_graph_info {
   int64_t device_bytes;   /* device memory held by the graph                  */
 } aml_graph_info;
 
+/* Sizes of a graph.  The first call waits for the graph's build to finish
+ * (the degree maxima are read from the device then). */
 aml_status aml_graph_get_info(const aml_graph* g, aml_graph_info* info);
 
 /* Work sizes of one window that earlier mines of this graph measured (no

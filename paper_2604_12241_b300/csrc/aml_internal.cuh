@@ -137,7 +137,8 @@ struct aml_graph {
   int64_t E = 0;
   int64_t Ev = 0;  // list edges
   int32_t N = 0;
-  int32_t max_out = 0, max_in = 0;
+  int32_t max_out = -1, max_in = -1;  // -1: not read from max_deg yet
+  int32_t* max_deg = nullptr;          // device [2]: out, in
   int32_t* src = nullptr;
   int32_t* dst = nullptr;
   int32_t* ts = nullptr;

@@ -107,9 +107,17 @@ aml_status aml_graph_destroy(aml_graph* g) {
   return guarded("aml_graph_destroy", [&] { destroy_graph(g); });
 }
 
-aml_status aml_graph_get_info(const aml_graph* g, aml_graph_info* info) {
+aml_status aml_graph_get_info(const aml_graph* gc, aml_graph_info* info) {
   return guarded("aml_graph_get_info", [&] {
-    AML_REQUIRE(g && info, AML_EINVAL, "NULL argument");
+    AML_REQUIRE(gc && info, AML_EINVAL, "NULL argument");
+    aml_graph* g = const_cast<aml_graph*>(gc);  // caches the degree read below
+    if (g->max_out < 0) {
+      int32_t md[2] = {0, 0};
+      AML_CUDA(cudaStreamSynchronize(g->last_stream));
+      AML_CUDA(cudaMemcpy(md, g->max_deg, 8, cudaMemcpyDeviceToHost));
+      g->max_out = md[0];
+      g->max_in = md[1];
+    }
     std::memset(info, 0, sizeof(*info));
     info->n_edges = g->E;
     info->n_list_edges = g->Ev;
@@ -194,7 +202,10 @@ aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, i
     if (flags & AML_MINE_HOST_OUTPUT) {
       DBuf<uint32_t> dev((size_t)(g->E * P), s);
       mine_plain(g, ps, dev.p, P, s, mode);
-      if (g->E)
+      if (g->E && ld == P)  // one contiguous copy (a pitched copy moves row by row)
+        AML_CUDA(cudaMemcpyAsync(counts, dev.p, (size_t)(g->E * P) * 4, cudaMemcpyDeviceToHost,
+                                 s));
+      else if (g->E)
         AML_CUDA(cudaMemcpy2DAsync(counts, (size_t)ld * 4, dev.p, (size_t)P * 4, (size_t)P * 4,
                                    (size_t)g->E, cudaMemcpyDeviceToHost, s));
       AML_CUDA(cudaStreamSynchronize(s));

@@ -121,12 +121,14 @@ __global__ void k_max_degree(const int32_t* __restrict__ ptr, int32_t N,
   if ((threadIdx.x & 31) == 0 && d > 0) atomicMax(out, d);
 }
 
+// The graph's arrays come from the device's stream-ordered pool (no driver
+// allocation once the pool holds enough), ordered on the build stream.
 struct GraphAlloc {
   aml_graph* g;
+  cudaStream_t s;
   template <typename T>
   T* get(size_t n) {
-    void* p = nullptr;
-    AML_CUDA(cudaMalloc(&p, (n ? n : 1) * sizeof(T)));
+    void* p = dalloc((n ? n : 1) * sizeof(T), s);
     g->allocs.push_back(p);
     g->bytes += (int64_t)((n ? n : 1) * sizeof(T));
     return static_cast<T*>(p);
@@ -134,7 +136,7 @@ struct GraphAlloc {
 };
 
 static void free_graph(aml_graph* g) {
-  for (void* p : g->allocs) cudaFree(p);
+  for (void* p : g->allocs) dfree(p, 0);  // callers have synchronized
   g->allocs.clear();
   delete g;
 }
@@ -195,7 +197,7 @@ aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts
                        const float* amount, int64_t E, int32_t N, uint32_t flags,
                        cudaStream_t s) {
   aml_graph* g = new aml_graph();
-  GraphAlloc ga{g};
+  GraphAlloc ga{g, s};
   try {
     AML_CUDA(cudaGetDevice(&g->device));
     g->E = E;
@@ -245,15 +247,11 @@ aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts
       radix_sort_u32(keys.p, tperm.p, ktmp.p, vtmp.p, E, 32, s);
     }
     int nbits = bits_for((uint64_t)N);  // keys range over [0, N]
-    int32_t* maxdeg = reinterpret_cast<int32_t*>(scal.p) + 2;  // two int32 slots
-    AML_CUDA(cudaMemsetAsync(maxdeg, 0, 8, s));
-    build_direction(g, g->out, g->src, g->dst, tperm.p, E, N, nbits, s, ga, maxdeg);
-    build_direction(g, g->in, g->dst, g->src, tperm.p, E, N, nbits, s, ga, maxdeg + 1);
-    int32_t md[2];
-    AML_CUDA(cudaMemcpyAsync(md, maxdeg, 8, cudaMemcpyDeviceToHost, s));
-    AML_CUDA(cudaStreamSynchronize(s));
-    g->max_out = md[0];
-    g->max_in = md[1];
+    // maximum degrees: read when first asked for (aml_graph_get_info)
+    g->max_deg = ga.get<int32_t>(2);
+    AML_CUDA(cudaMemsetAsync(g->max_deg, 0, 8, s));
+    build_direction(g, g->out, g->src, g->dst, tperm.p, E, N, nbits, s, ga, g->max_deg);
+    build_direction(g, g->in, g->dst, g->src, tperm.p, E, N, nbits, s, ga, g->max_deg + 1);
     return g;
   } catch (...) {
     cudaStreamSynchronize(s);

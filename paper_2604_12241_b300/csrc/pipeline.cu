@@ -276,24 +276,25 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       continue;
     }
     LegCache& lc = g->legs[wp.delta];
-    if (lc.n_legs < 0) {
-      int64_t total = 0;
-      AML_CUDA(cudaMemcpyAsync(&total, off + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (lc.n_legs < 0 || (level_cycles && lc.n_front[2] < 0)) {
+      // one wait for both sizes
+      int64_t total[2] = {0, 0};
+      AML_CUDA(cudaMemcpyAsync(&total[0], off + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      if (level_cycles)
+        AML_CUDA(cudaMemcpyAsync(&total[1], off2.p + E, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
       AML_CUDA(cudaStreamSynchronize(s));
-      AML_REQUIRE(total < (int64_t)UINT32_MAX, AML_EUNSUPPORTED,
+      AML_REQUIRE(total[0] < (int64_t)UINT32_MAX, AML_EUNSUPPORTED,
                   "more than 2^32 temporal 2-paths in one window");
-      lc.n_legs = total;
+      lc.n_legs = total[0];
+      if (level_cycles) lc.n_front[2] = total[1];
     }
     const int64_t nl = lc.n_legs;
     if (gs_in) AML_CUDA(cudaMemsetAsync(gs_in, 0, (size_t)E * 4, s));
     LegSink S{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
     DBuf<int32_t> la, lb;
     if (level_cycles) {
-      int64_t& n2 = lc.n_front[2];
-      if (n2 < 0) {
-        AML_CUDA(cudaMemcpyAsync(&n2, off2.p + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        AML_CUDA(cudaStreamSynchronize(s));
-      }
+      const int64_t n2 = lc.n_front[2];
       la = DBuf<int32_t>((size_t)std::max<int64_t>(n2, 1), s);
       lb = DBuf<int32_t>((size_t)std::max<int64_t>(n2, 1), s);
       S.la = la.p;

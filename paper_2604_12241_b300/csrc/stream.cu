@@ -268,11 +268,13 @@ aml_status aml_stream_read(aml_stream* st, int64_t row0, int64_t n, uint32_t* ou
     if (n == 0) return AML_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint32_t* from = st->counts + (row0 - st->base) * st->P;
-    AML_CUDA(cudaMemcpy2DAsync(out, (size_t)ld * 4, from, (size_t)st->P * 4, (size_t)st->P * 4,
-                               (size_t)n,
-                               (flags & AML_MINE_HOST_OUTPUT) ? cudaMemcpyDeviceToHost
-                                                              : cudaMemcpyDeviceToDevice,
-                               s));
+    const cudaMemcpyKind kind =
+        (flags & AML_MINE_HOST_OUTPUT) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (ld == st->P)  // one contiguous copy (a pitched copy moves row by row)
+      AML_CUDA(cudaMemcpyAsync(out, from, (size_t)(n * st->P) * 4, kind, s));
+    else
+      AML_CUDA(cudaMemcpy2DAsync(out, (size_t)ld * 4, from, (size_t)st->P * 4,
+                                 (size_t)st->P * 4, (size_t)n, kind, s));
     if (flags & AML_MINE_HOST_OUTPUT) AML_CUDA(cudaStreamSynchronize(s));
     return AML_OK;
   } catch (const Failure& f) {
