@@ -116,7 +116,7 @@ void autotune(aml_graph* g, const aml_pattern_set* ps, int reps, cudaStream_t s,
   aml_tuning best = get_tuning(g);
   float best_ms = time_mines(g, ps, out.p, P, reps, s);
   const std::vector<int> blocks = {128, 256, 512};
-  const std::vector<int> owns = {8, 16, 32, 64};
+  const std::vector<int> owns = {16, 32, 128, 512};
   const std::vector<int> buckets = {96, 128, 192, 256};
   const std::vector<int> scans = {16, 48, 128};
   auto sweep = [&](int aml_tuning::*field, const std::vector<int>& cands) {

@@ -329,34 +329,67 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit(GraphView g, const int2* __
     o2 = S.off2[a] - o;
   }
   const bool own = q1 - q0 <= own_max;
-  // lanes with short windows walk them in lock step (one slot per round)
+  // Short windows (the lanes' own) are flattened over the warp: round r
+  // takes slots [32r, 32r + 32) of the concatenated windows, so every lane
+  // has a slot in every round but the last.  A slot's leg rank inside its
+  // anchor's window = the legs its anchor had in earlier rounds (kept by
+  // the anchor's lane) + the legs before it in this round.
+  const unsigned full = 0xffffffffu;
   const int32_t own_len = own ? q1 - q0 : 0;
-  int32_t rounds = own_len;
-  for (int sh = 16; sh > 0; sh >>= 1)
-    rounds = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, sh));
-  unsigned long long n_cyc2 = 0;
-  for (int32_t r = 0; r < rounds; ++r) {
-    const bool in = r < own_len;
-    const int32_t q = q0 + r;
-    const int32_t y = in ? __ldg(g.onbr + q) : x;
-    const int32_t b = in ? __ldg(g.oeid + q) : 0;
-    const bool leg = in && y != x;
-    const int32_t tb = in ? __ldg(g.ot + q) : 0;
-    if (S.rec) sg_record(S, leg, o, a, b, x, h, y, ta, tb, g.N, S.bits);
-    if (NS > 0 && in) sub_leg_credit<NS>(sub, leg, a, b, tb - ta);
+  int32_t incl = own_len;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int32_t y = __shfl_up_sync(full, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const int32_t excl = incl - own_len;
+  const int32_t total = __shfl_sync(full, incl, 31);
+  const int64_t c2 = o2 + o;  // first cycle-leg position of this lane's anchor
+  int32_t run = 0;            // legs of this lane's anchor in earlier rounds
+  for (int32_t base = 0; base < total; base += 32) {
+    const int32_t k = base + lane;
+    const bool in = k < total;
+    // the lane whose window holds flattened slot k: the largest s with
+    // excl_s <= k (an empty window shares the next lane's excl)
+    int src = 0;
+    for (int step = 16; step > 0; step >>= 1) {
+      const int t = src + step;
+      if (__shfl_sync(full, excl, t) <= k) src = t;
+    }
+    const int32_t sa = __shfl_sync(full, a, src);
+    const int32_t sx = __shfl_sync(full, x, src);
+    const int32_t sh = __shfl_sync(full, h, src);
+    const int32_t sta = __shfl_sync(full, ta, src);
+    const int32_t sqc = __shfl_sync(full, qc, src);
+    const int32_t sq = __shfl_sync(full, q0, src) + (k - __shfl_sync(full, excl, src));
+    const int64_t so = __shfl_sync(full, o, src);
+    const int64_t sc2 = __shfl_sync(full, c2, src);
+    const int32_t srun = __shfl_sync(full, run, src);
+    const int32_t y = in ? __ldg(g.onbr + sq) : sx;
+    const int32_t b = in ? __ldg(g.oeid + sq) : 0;
+    const int32_t tb = in ? __ldg(g.ot + sq) : 0;
+    const bool leg = in && y != sx;
+    const unsigned peers = __match_any_sync(full, in ? src : 32 + lane);
+    const unsigned lm = __ballot_sync(full, leg);
+    const int32_t rank = srun + __popc(lm & peers & lt);
+    if (S.rec) sg_record(S, leg, so + rank, sa, b, sx, sh, y, sta, tb, g.N, S.bits);
+    if (NS > 0 && in) sub_leg_credit<NS>(sub, leg, sa, b, tb - sta);
     if (leg) {
       if (gs_in && b >= g.new_from) atomicAdd(gs_in + b, 1);
-      ++o;
-    } else if (in && acc_cyc2 && b >= g.new_from) {
+      if (S.la && sq < sqc) {
+        S.la[sc2 + rank] = sa;
+        S.lb[sc2 + rank] = b;
+      }
+    } else if (in && acc_cyc2 && b >= g.new_from) {  // a return: a 2-cycle
       atomicAdd(acc_cyc2 + b, 1ull);
-      ++n_cyc2;
+      atomicAdd(acc_cyc2 + sa, 1ull);
     }
-    if (S.la && leg && q < qc) {
-      S.la[o2 + o - 1] = a;
-      S.lb[o2 + o - 1] = b;
-    }
+    // every lane's anchor adds its legs of this round (read from a lane
+    // that held one of its slots: the first, at max(excl, base) - base)
+    const int32_t cnt = __popc(lm & peers);
+    const bool mine = own_len > 0 && excl < base + 32 && incl > base;
+    const int32_t add = __shfl_sync(full, cnt, mine ? max(excl, base) - base : lane);
+    if (mine) run += add;
   }
-  if (n_cyc2) atomicAdd(acc_cyc2 + a, n_cyc2);
   unsigned heavy = __ballot_sync(0xffffffffu, !own);
   while (heavy) {
     const int src = __ffs(heavy) - 1;
