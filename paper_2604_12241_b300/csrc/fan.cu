@@ -309,10 +309,117 @@ void fan_launch(const Adj& a, int64_t Ev, const FanDeltas& fd, int2* df, cudaStr
                                                                    Ev, n_tiles, sums.p, df));
 }
 
+// ----------------------------------------------------------- batch rows
+//
+// Delta counting needs DEG/FAN only for the new edges (ids >= new_from),
+// which are the last slots of their rows (they come after every older edge
+// in the (t, id) order).  One warp per row holding new slots: the warp
+// counts the distinct counterparties of the first new slot's windows
+// directly (slots whose previous same-counterparty slot lies before the
+// window start), then one lane walks the row's remaining new slots with
+// the repeat-delta recurrence (two pointers).
+
+// first new slot of every row that has one: rows[*n_rows++]
+__global__ void __launch_bounds__(256) k_batch_rows(const int32_t* __restrict__ pos,
+                                                    const int32_t* __restrict__ rstart,
+                                                    const int32_t* __restrict__ eid,
+                                                    int64_t new_from, int64_t E,
+                                                    int32_t* __restrict__ rows,
+                                                    unsigned int* __restrict__ n_rows) {
+  const int64_t e = new_from + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int32_t p = pos[e];
+  if (p < 0) return;  // self-loop
+  if (p == rstart[p] || eid[p - 1] < new_from) rows[atomicAdd(n_rows, 1u)] = p;
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) k_fan_batch(const int32_t* __restrict__ rstart,
+                                                   const int32_t* __restrict__ t,
+                                                   const int32_t* __restrict__ eid,
+                                                   const int32_t* __restrict__ prev,
+                                                   const int32_t* __restrict__ next, int64_t Ev,
+                                                   FanDeltas fd, const int32_t* __restrict__ rows,
+                                                   const unsigned int* __restrict__ n_rows,
+                                                   int2* __restrict__ df) {
+  const int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wi >= (int64_t)*n_rows) return;  // warp-uniform
+  const int32_t p1 = rows[wi];
+  const int32_t rs = __ldg(rstart + p1);
+  const int64_t tp1 = __ldg(t + p1);
+  int32_t lb[W];
+  int32_t lo = rs;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {  // nested windows: each start above the previous
+    lb[k] = lower_t(t, lo, p1 + 1, tp1 - fd.d[k]);
+    lo = lb[k];
+  }
+  // distinct counterparties of p1's windows: slots whose previous slot of
+  // the same counterparty lies before the window start
+  int32_t c[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) c[k] = 0;
+  for (int32_t q = lb[0] + lane; q <= p1; q += 32) {
+    const int32_t pv = __ldg(prev + q);
+#pragma unroll
+    for (int k = 0; k < W; ++k) c[k] += (q >= lb[k] && pv < lb[k]) ? 1 : 0;
+  }
+#pragma unroll
+  for (int k = 0; k < W; ++k)
+    for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(0xffffffffu, c[k], o);
+  if (lane != 0) return;
+  int32_t R[W];
+  int2 v[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    const int32_t deg = p1 - lb[k] + 1;
+    R[k] = deg - c[k];
+    v[k] = make_int2(deg, c[k]);
+  }
+  store_df<W>(df, __ldg(eid + p1), v);
+  // the row's later (new) slots
+  for (int64_t p64 = p1 + 1; p64 < Ev && __ldg(rstart + p64) == rs; ++p64) {
+    const int32_t p = (int32_t)p64;
+    const int64_t tp = __ldg(t + p);
+    const int32_t pv = __ldg(prev + p);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      int32_t l = lb[k], gone = 0;
+      const int64_t tmin = tp - fd.d[k];
+      while (__ldg(t + l) < tmin) {
+        gone += __ldg(next + l) <= p - 1 ? 1 : 0;
+        ++l;
+      }
+      lb[k] = l;
+      R[k] += (pv >= l ? 1 : 0) - gone;
+      const int32_t deg = p - l + 1;
+      v[k] = make_int2(deg, deg - R[k]);
+    }
+    store_df<W>(df, __ldg(eid + p), v);
+  }
+}
+
+template <int W>
+void fan_batch_launch(const Adj& a, int64_t Ev, int64_t E, int64_t new_from,
+                      const FanDeltas& fd, int2* df, cudaStream_t s) {
+  const int64_t nb = E - new_from;
+  if (nb <= 0 || Ev <= 0) return;
+  DBuf<int32_t> rows((size_t)nb, s);
+  DBuf<unsigned int> n_rows(1, s);
+  AML_CUDA(cudaMemsetAsync(n_rows.p, 0, sizeof(unsigned int), s));
+  AML_LAUNCH("k_batch_rows", s,
+             k_batch_rows<<<grid_for(nb, 256), 256, 0, s>>>(a.pos, a.rstart, a.eid, new_from, E,
+                                                            rows.p, n_rows.p));
+  AML_LAUNCH("k_fan_batch", s,
+             k_fan_batch<W><<<grid_for(nb * 32, 256), 256, 0, s>>>(
+                 a.rstart, a.t, a.eid, a.prev, a.next, Ev, fd, rows.p, n_rows.p, df));
+}
+
 }  // namespace
 
-void fan_per_edge(const Adj& a, int64_t Ev, int nw, const int32_t* deltas, int2* df,
-                  cudaStream_t s) {
+void fan_per_edge(const Adj& a, int64_t Ev, int64_t E, int64_t new_from, int nw,
+                  const int32_t* deltas, int2* df, cudaStream_t s) {
   AML_REQUIRE(nw >= 1 && nw <= FAN_MAX_W, AML_EINTERNAL, "fan_per_edge: window count");
   if (Ev <= 0) return;
   FanDeltas fd{};
@@ -320,6 +427,15 @@ void fan_per_edge(const Adj& a, int64_t Ev, int nw, const int32_t* deltas, int2*
     fd.d[k] = deltas[k];
     AML_REQUIRE(k == 0 || deltas[k] <= deltas[k - 1], AML_EINTERNAL,
                 "fan_per_edge: windows must be in descending order");
+  }
+  if (new_from > 0) {  // the new edges only
+    switch (nw) {
+      case 1: fan_batch_launch<1>(a, Ev, E, new_from, fd, df, s); break;
+      case 2: fan_batch_launch<2>(a, Ev, E, new_from, fd, df, s); break;
+      case 3: fan_batch_launch<3>(a, Ev, E, new_from, fd, df, s); break;
+      default: fan_batch_launch<4>(a, Ev, E, new_from, fd, df, s); break;
+    }
+    return;
   }
   switch (nw) {
     case 1: fan_launch<1>(a, Ev, fd, df, s); break;

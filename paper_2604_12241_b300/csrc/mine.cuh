@@ -133,10 +133,11 @@ __global__ void k_window_slots(const int32_t* rstart, const int32_t* t, const in
                                int32_t delta, int32_t* deg_s, int32_t* D, int2* df);
 // (DEG, FAN) of every edge for nw <= FAN_MAX_W windows of one direction
 // (deltas in descending order): df[e * nw + k] for window k, at the edge id
-// (self-loop entries untouched); two launches on s.
+// (self-loop entries untouched); two launches on s.  new_from > 0: only the
+// edges e >= new_from (delta counting), the other entries untouched.
 constexpr int FAN_MAX_W = 4;
-void fan_per_edge(const Adj& a, int64_t Ev, int nw, const int32_t* deltas, int2* df,
-                  cudaStream_t s);
+void fan_per_edge(const Adj& a, int64_t Ev, int64_t E, int64_t new_from, int nw,
+                  const int32_t* deltas, int2* df, cudaStream_t s);
 __global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);
 // moves every record to its bucket: cursor = exclusive scan of the bucket
 // sizes on entry, the bucket ends on exit

@@ -197,7 +197,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   if (branches) branch_wait(g->branch_ev[0], s, s_fan);
   for (const DfJob& job : df_jobs) {
     if (job.fan) {
-      fan_per_edge(*job.a, Ev, job.nw, job.deltas, job.df, s_fan);
+      fan_per_edge(*job.a, Ev, E, new_from, job.nw, job.deltas, job.df, s_fan);
     } else {
       AML_LAUNCH("k_window_slots", s_fan,
                  k_window_slots<<<grid_for(Ev, B), B, 0, s_fan>>>(
