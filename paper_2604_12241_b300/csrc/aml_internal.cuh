@@ -175,8 +175,6 @@ void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s)
 // Sorted result ends in (keys, vals); tmp buffers must hold n elements.
 void radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
                     int64_t n, int nbits, cudaStream_t s);
-void radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_tmp, uint32_t* vals_tmp,
-                    int64_t n, int nbits, cudaStream_t s);
 
 void iota_i32(int32_t* out, int64_t n, cudaStream_t s);
 

@@ -45,17 +45,6 @@ __global__ void k_row_keys(const uint32_t* __restrict__ perm, const int32_t* __r
   keys[i] = (r == o) ? (uint32_t)N : (uint32_t)r;
 }
 
-// counterparty key of edge perm[i] (self-loops get N; their row is ignored)
-__global__ void k_nbr_keys(const uint32_t* __restrict__ perm, const int32_t* __restrict__ row_of,
-                           const int32_t* __restrict__ other, int64_t E, int32_t N,
-                           uint32_t* __restrict__ keys) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= E) return;
-  uint32_t e = perm[i];
-  int32_t r = row_of[e], o = other[e];
-  keys[i] = (r == o) ? (uint32_t)N : (uint32_t)o;
-}
-
 // ptr[u] = first i with keys[i] >= u, for u in [0, N] (one thread per row)
 __global__ void k_row_ptr(const uint32_t* __restrict__ keys, int64_t n, int32_t N,
                           int32_t* __restrict__ ptr) {
@@ -141,48 +130,57 @@ static void free_graph(aml_graph* g) {
   delete g;
 }
 
-// Build one direction.  row_of/other are src/dst (out-lists) or dst/src.
-static void build_direction(aml_graph* g, Adj& a, const int32_t* row_of, const int32_t* other,
-                            const uint32_t* time_perm, int64_t E, int32_t N, int nbits,
-                            cudaStream_t s, GraphAlloc& ga, int32_t* max_deg_dev) {
-  DBuf<uint32_t> keys(E, s), perm(E, s), ktmp(E, s), vtmp(E, s);
+// Rows of one direction (row_of/other = src/dst for out-lists, dst/src for
+// in-lists): a stable sort of the time order by row gives every row in (t, id)
+// order; perm keeps that order for the other direction's second copy.
+static void build_rows(aml_graph* g, Adj& a, const int32_t* row_of, const int32_t* other,
+                       const uint32_t* time_perm, int64_t E, int32_t N, int nbits,
+                       cudaStream_t s, GraphAlloc& ga, uint32_t* perm, int32_t* max_deg_dev) {
+  DBuf<uint32_t> keys(E, s), ktmp(E, s), vtmp(E, s);
   const int B = 256;
-  // rows by account, (t, id) order inside each row (stable sort of the time order)
-  AML_CUDA(cudaMemcpyAsync(perm.p, time_perm, E * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  AML_CUDA(cudaMemcpyAsync(perm, time_perm, E * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
   AML_LAUNCH("k_row_keys", s,
-             k_row_keys<<<grid_for(E, B), B, 0, s>>>(perm.p, row_of, other, E, N, keys.p));
-  radix_sort_u32(keys.p, perm.p, ktmp.p, vtmp.p, E, nbits, s);
+             k_row_keys<<<grid_for(E, B), B, 0, s>>>(perm, row_of, other, E, N, keys.p));
+  radix_sort_u32(keys.p, perm, ktmp.p, vtmp.p, E, nbits, s);
   a.ptr = ga.get<int32_t>((size_t)N + 1);
   AML_LAUNCH("k_row_ptr", s,
              k_row_ptr<<<grid_for((int64_t)N + 1, B), B, 0, s>>>(keys.p, E, N, a.ptr));
-  int64_t Ev = g->Ev;
+  const int64_t Ev = g->Ev;
   a.nbr = ga.get<int32_t>(Ev);
   a.t = ga.get<int32_t>(Ev);
   a.eid = ga.get<int32_t>(Ev);
+  a.pos = ga.get<int32_t>(E);
+  a.rstart = ga.get<int32_t>(Ev);
+  AML_CUDA(cudaMemsetAsync(a.pos, 0xff, (E ? E : 1) * sizeof(int32_t), s));
+  AML_LAUNCH("k_fill_slots", s,
+             k_fill_slots<<<grid_for(Ev, B), B, 0, s>>>(
+                 perm, keys.p, a.ptr, Ev, other, g->ts, a.nbr, a.t, a.eid, a.pos, a.rstart));
+  AML_LAUNCH("k_max_degree", s, k_max_degree<<<grid_for(N, B), B, 0, s>>>(a.ptr, N, max_deg_dev));
+}
+
+// The (counterparty, t, id) copy of one direction's rows, and the links
+// between consecutive slots of one counterparty.  `perm` is the other
+// direction's row order, sorted by (counterparty, t, id) already: a stable
+// sort by this direction's row gives (row, counterparty, t, id).
+static void build_nbr_order(aml_graph* g, Adj& a, const int32_t* row_of,
+                            const int32_t* other, uint32_t* perm, int64_t E, int32_t N,
+                            int nbits, cudaStream_t s, GraphAlloc& ga) {
+  DBuf<uint32_t> keys(E, s), ktmp(E, s), vtmp(E, s);
+  const int B = 256;
+  const int64_t Ev = g->Ev;
   a.prev = ga.get<int32_t>(Ev);
   a.next = ga.get<int32_t>(Ev);
   a.nnbr = ga.get<int32_t>(Ev);
   a.nt = ga.get<int32_t>(Ev);
   a.neid = ga.get<int32_t>(Ev);
-  a.pos = ga.get<int32_t>(E);
-  a.rstart = ga.get<int32_t>(Ev);
-  AML_CUDA(cudaMemsetAsync(a.pos, 0xff, (E ? E : 1) * sizeof(int32_t), s));
   AML_CUDA(cudaMemsetAsync(a.prev, 0xff, (Ev ? Ev : 1) * sizeof(int32_t), s));
   AML_LAUNCH("k_fill_i32", s, k_fill_i32<<<grid_for(Ev, B), B, 0, s>>>(a.next, Ev, INT32_MAX));
-  AML_LAUNCH("k_fill_slots", s,
-             k_fill_slots<<<grid_for(Ev, B), B, 0, s>>>(
-                 perm.p, keys.p, a.ptr, Ev, other, g->ts, a.nbr, a.t, a.eid, a.pos, a.rstart));
-  // (account, counterparty, t, id) order: stable sort by counterparty, then by account
-  AML_LAUNCH("k_nbr_keys", s,
-             k_nbr_keys<<<grid_for(E, B), B, 0, s>>>(perm.p, row_of, other, E, N, keys.p));
-  radix_sort_u32(keys.p, perm.p, ktmp.p, vtmp.p, E, nbits, s);
   AML_LAUNCH("k_row_keys", s,
-             k_row_keys<<<grid_for(E, B), B, 0, s>>>(perm.p, row_of, other, E, N, keys.p));
-  radix_sort_u32(keys.p, perm.p, ktmp.p, vtmp.p, E, nbits, s);
+             k_row_keys<<<grid_for(E, B), B, 0, s>>>(perm, row_of, other, E, N, keys.p));
+  radix_sort_u32(keys.p, perm, ktmp.p, vtmp.p, E, nbits, s);
   AML_LAUNCH("k_fill_nbr_order", s,
              k_fill_nbr_order<<<grid_for(Ev, B), B, 0, s>>>(
-                 perm.p, Ev, row_of, other, g->ts, a.pos, a.nnbr, a.nt, a.neid, a.prev, a.next));
-  AML_LAUNCH("k_max_degree", s, k_max_degree<<<grid_for(N, B), B, 0, s>>>(a.ptr, N, max_deg_dev));
+                 perm, Ev, row_of, other, g->ts, a.pos, a.nnbr, a.nt, a.neid, a.prev, a.next));
 }
 
 __global__ void k_count_loops(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
@@ -250,8 +248,13 @@ aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts
     // maximum degrees: read when first asked for (aml_graph_get_info)
     g->max_deg = ga.get<int32_t>(2);
     AML_CUDA(cudaMemsetAsync(g->max_deg, 0, 8, s));
-    build_direction(g, g->out, g->src, g->dst, tperm.p, E, N, nbits, s, ga, g->max_deg);
-    build_direction(g, g->in, g->dst, g->src, tperm.p, E, N, nbits, s, ga, g->max_deg + 1);
+    DBuf<uint32_t> perm_out(E, s), perm_in(E, s);
+    build_rows(g, g->out, g->src, g->dst, tperm.p, E, N, nbits, s, ga, perm_out.p, g->max_deg);
+    build_rows(g, g->in, g->dst, g->src, tperm.p, E, N, nbits, s, ga, perm_in.p, g->max_deg + 1);
+    // (src, dst, t, id) from the in-rows' (dst, t, id) order; (dst, src, t, id)
+    // from the out-rows' (src, t, id) order
+    build_nbr_order(g, g->out, g->src, g->dst, perm_in.p, E, N, nbits, s, ga);
+    build_nbr_order(g, g->in, g->dst, g->src, perm_out.p, E, N, nbits, s, ga);
     return g;
   } catch (...) {
     cudaStreamSynchronize(s);

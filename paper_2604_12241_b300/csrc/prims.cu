@@ -245,111 +245,134 @@ void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s)
 
 // ------------------------------------------------------------ radix sort
 //
-// LSD radix sort, 8-bit digits.  Per pass: (1) every 4096-element tile
-// counts its digits; (2) digit-major exclusive scan of the counts gives each
-// (digit, tile) its output offset; (3) every tile re-reads its elements in
-// order and ranks equal digits stably: inside a warp with __match_any_sync,
-// across the block's warps with per-warp digit counts in shared memory.
+// LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits.  Per
+// pass: (1) every 4096-element tile counts its digits; (2) a digit-major
+// exclusive scan of the counts gives each (digit, tile) its output offset;
+// (3) every tile ranks its elements stably (inside a warp with
+// __match_any_sync, across the block's warps and rounds with digit counts
+// in shared memory), places them in shared memory grouped by digit, and
+// writes each digit's run out contiguously.
 
 constexpr int RS_BLOCK = 256;
 constexpr int RS_WARPS = RS_BLOCK / 32;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_BLOCK * RS_ITEMS;
 
-template <typename K>
-__global__ void __launch_bounds__(RS_BLOCK) k_rs_hist(const K* __restrict__ keys, int64_t n,
-                                                      int shift, int32_t* __restrict__ hist,
-                                                      int nblocks) {
+__global__ void __launch_bounds__(RS_BLOCK) k_rs_hist(const uint32_t* __restrict__ keys,
+                                                      int64_t n, int shift,
+                                                      int32_t* __restrict__ hist, int nblocks) {
   __shared__ int32_t h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
   int64_t base = (int64_t)blockIdx.x * RS_TILE;
   for (int i = threadIdx.x; i < RS_TILE; i += RS_BLOCK) {
     int64_t j = base + i;
-    if (j < n) atomicAdd(&h[(uint32_t)(keys[j] >> shift) & 255u], 1);
+    if (j < n) atomicAdd(&h[(keys[j] >> shift) & 255u], 1);
   }
   __syncthreads();
   hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-template <typename K>
-__global__ void __launch_bounds__(RS_BLOCK) k_rs_scatter(const K* __restrict__ keys,
+__global__ void __launch_bounds__(RS_BLOCK) k_rs_scatter(const uint32_t* __restrict__ keys,
                                                          const uint32_t* __restrict__ vals,
                                                          int64_t n, int shift,
                                                          const int32_t* __restrict__ offs,
-                                                         int nblocks, K* __restrict__ okeys,
+                                                         int nblocks, uint32_t* __restrict__ okeys,
                                                          uint32_t* __restrict__ ovals) {
-  __shared__ int32_t s_off[256];
+  __shared__ uint32_t s_key[RS_TILE];
+  __shared__ uint32_t s_val[RS_TILE];
+  __shared__ int32_t s_off[256];    // output offset of the tile's run of each digit
+  __shared__ int32_t s_start[256];  // start of each digit's run inside the tile
+  __shared__ int32_t s_done[256];   // elements of each digit placed so far
   __shared__ int32_t s_w[RS_WARPS][256];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  s_off[tid] = offs[(int64_t)tid * nblocks + blockIdx.x];
   const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  const int tile_n = n - base < RS_TILE ? (int)(n - base) : RS_TILE;
+  // the tile's digit counts and run starts (exclusive scan over the digits)
+  s_done[tid] = 0;
+  __syncthreads();
+  for (int i = tid; i < tile_n; i += RS_BLOCK) atomicAdd(&s_done[(keys[base + i] >> shift) & 255u], 1);
+  __syncthreads();
+  {
+    const int c = s_done[tid];
+    int x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[0][warp] = x;
+    __syncthreads();
+    int before = x - c;
+    for (int w = 0; w < warp; ++w) before += s_w[0][w];
+    s_start[tid] = before;
+    s_off[tid] = offs[(int64_t)tid * nblocks + blockIdx.x];
+    __syncthreads();
+    s_done[tid] = 0;
+  }
   const uint32_t lt_mask = (1u << lane) - 1u;
   for (int r = 0; r < RS_ITEMS; ++r) {
 #pragma unroll
     for (int w = 0; w < RS_WARPS; ++w) s_w[w][tid] = 0;
     __syncthreads();
-    const int64_t j = base + (int64_t)r * RS_BLOCK + tid;
-    const bool valid = j < n;
-    K key = valid ? keys[j] : K(0);
-    uint32_t val = valid ? vals[j] : 0u;
-    uint32_t digit = valid ? ((uint32_t)(key >> shift) & 255u) : 256u;
-    uint32_t peers = __match_any_sync(0xffffffffu, digit);
-    int rank = __popc(peers & lt_mask);
+    const int i = r * RS_BLOCK + tid;
+    const bool valid = i < tile_n;
+    const uint32_t key = valid ? keys[base + i] : 0u;
+    const uint32_t val = valid ? vals[base + i] : 0u;
+    const uint32_t digit = valid ? ((key >> shift) & 255u) : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+    const int rank = __popc(peers & lt_mask);
     if (valid && rank == 0) s_w[warp][digit] = __popc(peers);
     __syncthreads();
     int run = 0;
 #pragma unroll
     for (int w = 0; w < RS_WARPS; ++w) {
-      int c = s_w[w][tid];
+      const int c = s_w[w][tid];
       s_w[w][tid] = run;
       run += c;
     }
     __syncthreads();
     if (valid) {
-      int dest = s_off[digit] + s_w[warp][digit] + rank;
-      okeys[dest] = key;
-      ovals[dest] = val;
+      const int at = s_start[digit] + s_done[digit] + s_w[warp][digit] + rank;
+      s_key[at] = key;
+      s_val[at] = val;
     }
     __syncthreads();
-    s_off[tid] += run;
+    s_done[tid] += run;
   }
-}
-
-template <typename K>
-static void radix_impl(K* keys, uint32_t* vals, K* keys_tmp, uint32_t* vals_tmp, int64_t n,
-                       int nbits, cudaStream_t s) {
-  if (n <= 1 || nbits <= 0) return;
-  int64_t nb64 = (n + RS_TILE - 1) / RS_TILE;
-  AML_REQUIRE(nb64 < (1ll << 31) / 256, AML_EINVAL, "radix sort input too large");
-  int nb = (int)nb64;
-  DBuf<int32_t> hist((size_t)nb * 256, s);
-  K* ka = keys;
-  uint32_t* va = vals;
-  K* kb = keys_tmp;
-  uint32_t* vb = vals_tmp;
-  for (int shift = 0; shift < nbits; shift += 8) {
-    AML_LAUNCH("k_rs_hist", s, k_rs_hist<K><<<nb, RS_BLOCK, 0, s>>>(ka, n, shift, hist.p, nb));
-    scan_i32(hist.p, hist.p, (int64_t)nb * 256, false, s);
-    AML_LAUNCH("k_rs_scatter", s,
-               k_rs_scatter<K><<<nb, RS_BLOCK, 0, s>>>(ka, va, n, shift, hist.p, nb, kb, vb));
-    K* tk = ka; ka = kb; kb = tk;
-    uint32_t* tv = va; va = vb; vb = tv;
-  }
-  if (ka != keys) {
-    AML_CUDA(cudaMemcpyAsync(keys, ka, (size_t)n * sizeof(K), cudaMemcpyDeviceToDevice, s));
-    AML_CUDA(cudaMemcpyAsync(vals, va, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  __syncthreads();
+  // consecutive threads write consecutive elements of a digit's run
+  for (int i = tid; i < tile_n; i += RS_BLOCK) {
+    const uint32_t key = s_key[i];
+    const uint32_t digit = (key >> shift) & 255u;
+    const int dest = s_off[digit] + (i - s_start[digit]);
+    okeys[dest] = key;
+    ovals[dest] = s_val[i];
   }
 }
 
 void radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
                     int64_t n, int nbits, cudaStream_t s) {
-  radix_impl<uint32_t>(keys, vals, keys_tmp, vals_tmp, n, nbits, s);
-}
-
-void radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_tmp, uint32_t* vals_tmp,
-                    int64_t n, int nbits, cudaStream_t s) {
-  radix_impl<uint64_t>(keys, vals, keys_tmp, vals_tmp, n, nbits, s);
+  if (n <= 1 || nbits <= 0) return;
+  int64_t nb64 = (n + RS_TILE - 1) / RS_TILE;
+  AML_REQUIRE(nb64 < (1ll << 31) / 256, AML_EINVAL, "radix sort input too large");
+  int nb = (int)nb64;
+  DBuf<int32_t> hist((size_t)nb * 256, s);
+  uint32_t* ka = keys;
+  uint32_t* va = vals;
+  uint32_t* kb = keys_tmp;
+  uint32_t* vb = vals_tmp;
+  for (int shift = 0; shift < nbits; shift += 8) {
+    AML_LAUNCH("k_rs_hist", s, k_rs_hist<<<nb, RS_BLOCK, 0, s>>>(ka, n, shift, hist.p, nb));
+    scan_i32(hist.p, hist.p, (int64_t)nb * 256, false, s);
+    AML_LAUNCH("k_rs_scatter", s,
+               k_rs_scatter<<<nb, RS_BLOCK, 0, s>>>(ka, va, n, shift, hist.p, nb, kb, vb));
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  if (ka != keys) {
+    AML_CUDA(cudaMemcpyAsync(keys, ka, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    AML_CUDA(cudaMemcpyAsync(vals, va, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  }
 }
 
 }  // namespace aml
