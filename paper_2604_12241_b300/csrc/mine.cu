@@ -167,13 +167,28 @@ __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
   const int32_t ta = g.ts[a];
   const int32_t hs = g.optr[h], he = g.optr[h + 1];
   L[a] = (q1 - q0) - pair_after(g.onnbr, g.ont, g.oneid, hs, he, x, ta, a, delta);
-  // smaller windows: the prefix of the window within their delta
+  // smaller windows: the prefix of the window within their delta (delta
+  // counting: only the legs whose second edge is new)
 #pragma unroll
   for (int i = 0; i < NS; ++i)
     if (i < sub.n && sub.gs_from[i]) {
       const int32_t di = sub.delta[i];
       const int32_t q1i = upper_t(g.ot, q0, q1, (int64_t)ta + di);
-      sub.gs_from[i][a] = (q1i - q0) - pair_after(g.onnbr, g.ont, g.oneid, hs, he, x, ta, a, di);
+      if (g.new_from == 0) {
+        sub.gs_from[i][a] =
+            (q1i - q0) - pair_after(g.onnbr, g.ont, g.oneid, hs, he, x, ta, a, di);
+      } else {
+        const int32_t qn = after_edge(g.ot, g.oeid, q0, q1i, g.t_new, g.new_from - 1);
+        int32_t back = 0;
+        const int32_t r0 = lower_nbr(g.onnbr, hs, he, x);
+        if (qn < q1i && r0 < he && __ldg(g.onnbr + r0) == x) {
+          const int32_t r1 = lower_nbr(g.onnbr, r0, he, x + 1);
+          const int32_t b0 = after_edge(g.ont, g.oneid, r0, r1, ta, a);
+          const int32_t bn = after_edge(g.ont, g.oneid, b0, r1, g.t_new, g.new_from - 1);
+          back = upper_t(g.ont, bn, r1, (int64_t)ta + di) - bn;
+        }
+        sub.gs_from[i][a] = (q1i - qn) - back;
+      }
     }
   if (L_new) {
     const int32_t qn = after_edge(g.ot, g.oeid, q0, q1, g.t_new, g.new_from - 1);
@@ -281,10 +296,12 @@ __device__ __forceinline__ void sg_record(const LegSink& S, bool leg, int64_t po
 // slots are written by their own lane; longer ones (hub accounts) by the
 // whole warp, 32 slots at a time, with ballots keeping the output order.
 // smaller windows: GS legs ending with b, and 2-cycles (a slot returning to
-// the anchor's source), when the pair spans at most their delta
+// the anchor's source), when the pair spans at most their delta (delta
+// counting: when b is new)
 template <int NS>
 __device__ __forceinline__ void sub_leg_credit(const SubWindows& sub, bool leg, int32_t a,
-                                               int32_t b, int32_t span) {
+                                               int32_t b, int32_t span, int32_t new_from) {
+  if (b < new_from) return;
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
     if (i >= sub.n || span > sub.delta[i]) continue;
@@ -372,7 +389,7 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit(GraphView g, const int2* __
     const unsigned lm = __ballot_sync(full, leg);
     const int32_t rank = srun + __popc(lm & peers & lt);
     if (S.rec) sg_record(S, leg, so + rank, sa, b, sx, sh, y, sta, tb, g.N, S.bits);
-    if (NS > 0 && in) sub_leg_credit<NS>(sub, leg, sa, b, tb - sta);
+    if (NS > 0 && in) sub_leg_credit<NS>(sub, leg, sa, b, tb - sta, g.new_from);
     if (leg) {
       if (gs_in && b >= g.new_from) atomicAdd(gs_in + b, 1);
       if (S.la && sq < sqc) {
@@ -413,7 +430,7 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit(GraphView g, const int2* __
       const unsigned m = __ballot_sync(0xffffffffu, leg);
       const int32_t tb = in ? __ldg(g.ot + q) : 0;
       if (S.rec) sg_record(S, leg, ho + __popc(m & lt), ha, b, hx, hh, y, hta, tb, g.N, S.bits);
-      if (NS > 0 && in) sub_leg_credit<NS>(sub, leg, ha, b, tb - hta);
+      if (NS > 0 && in) sub_leg_credit<NS>(sub, leg, ha, b, tb - hta, g.new_from);
       if (leg) {
         if (gs_in && b >= g.new_from) atomicAdd(gs_in + b, 1);
       } else if (in && acc_cyc2 && b >= g.new_from) {

@@ -123,11 +123,11 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   P.acc = acc.p;
 
   // Smaller windows whose GS/SG/CYC columns are counted from the largest
-  // leg-emitting window's pass (sub-windows; not for delta counting or the
-  // persistent cycle search, and not when they want longer cycles).
+  // leg-emitting window's pass (sub-windows; not for the persistent cycle
+  // search, and not when they want longer cycles).
   std::vector<int> owner(wins.size(), -1);
   std::vector<std::vector<int>> members(wins.size());
-  if (!persistent && new_from == 0) {
+  if (!persistent) {
     int lw = -1;
     for (size_t w = 0; w < wins.size(); ++w)
       if (wins[w].emit_legs() && (lw < 0 || wins[w].delta > wins[lw].delta)) lw = (int)w;
