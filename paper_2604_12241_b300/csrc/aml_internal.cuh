@@ -247,6 +247,79 @@ __device__ __forceinline__ int32_t after_edge(const int32_t* __restrict__ t,
   return lo;
 }
 
+// Paired searches: two bounds of one sorted range found in lockstep.  Each
+// step issues both loads before using either, so a pair costs one chain of
+// dependent loads instead of two.
+
+// q0 = after_edge(t, id, lo, hi, te, e); q1 = first i in [q0, hi) with
+// t[i] > tmax (the window of slots after (te, e) up to tmax)
+__device__ __forceinline__ void after_edge_upto(const int32_t* __restrict__ t,
+                                                const int32_t* __restrict__ id, int32_t lo,
+                                                int32_t hi, int32_t te, int32_t e, int64_t tmax,
+                                                int32_t& q0, int32_t& q1) {
+  int32_t alo = lo, ahi = hi, blo = lo, bhi = hi;
+  while (alo < ahi || blo < bhi) {
+    const bool ao = alo < ahi, bo = blo < bhi;
+    const int32_t am = (int32_t)(((uint32_t)alo + (uint32_t)ahi) >> 1);
+    const int32_t bm = (int32_t)(((uint32_t)blo + (uint32_t)bhi) >> 1);
+    const int32_t ta = ao ? __ldg(t + am) : 0;
+    const int32_t tb = bo ? __ldg(t + bm) : 0;
+    if (ao) {
+      if (ta < te || (ta == te && __ldg(id + am) <= e)) alo = am + 1; else ahi = am;
+    }
+    if (bo) {
+      if ((int64_t)tb <= tmax) blo = bm + 1; else bhi = bm;
+    }
+  }
+  q0 = alo;
+  q1 = blo > alo ? blo : alo;  // sorted: a later bound below q0 means q0 itself
+}
+
+// c0 = lower_t(t, lo, hi, tmin); c1 = first i in [c0, hi) whose edge comes
+// strictly after (te, e) (the trailing window up to and including (te, e))
+__device__ __forceinline__ void since_upto_edge(const int32_t* __restrict__ t,
+                                                const int32_t* __restrict__ id, int32_t lo,
+                                                int32_t hi, int64_t tmin, int32_t te, int32_t e,
+                                                int32_t& c0, int32_t& c1) {
+  int32_t alo = lo, ahi = hi, blo = lo, bhi = hi;
+  while (alo < ahi || blo < bhi) {
+    const bool ao = alo < ahi, bo = blo < bhi;
+    const int32_t am = (int32_t)(((uint32_t)alo + (uint32_t)ahi) >> 1);
+    const int32_t bm = (int32_t)(((uint32_t)blo + (uint32_t)bhi) >> 1);
+    const int32_t ta = ao ? __ldg(t + am) : 0;
+    const int32_t tb = bo ? __ldg(t + bm) : 0;
+    if (ao) {
+      if ((int64_t)ta < tmin) alo = am + 1; else ahi = am;
+    }
+    if (bo) {
+      if (tb < te || (tb == te && __ldg(id + bm) <= e)) blo = bm + 1; else bhi = bm;
+    }
+  }
+  c0 = alo;
+  c1 = blo > alo ? blo : alo;
+}
+
+// [r0, r1) = the slots with nbr == x of a range sorted by nbr
+__device__ __forceinline__ void nbr_range(const int32_t* __restrict__ nbr, int32_t lo, int32_t hi,
+                                          int32_t x, int32_t& r0, int32_t& r1) {
+  int32_t alo = lo, ahi = hi, blo = lo, bhi = hi;
+  while (alo < ahi || blo < bhi) {
+    const bool ao = alo < ahi, bo = blo < bhi;
+    const int32_t am = (int32_t)(((uint32_t)alo + (uint32_t)ahi) >> 1);
+    const int32_t bm = (int32_t)(((uint32_t)blo + (uint32_t)bhi) >> 1);
+    const int32_t na = ao ? __ldg(nbr + am) : 0;
+    const int32_t nb = bo ? __ldg(nbr + bm) : 0;
+    if (ao) {
+      if (na < x) alo = am + 1; else ahi = am;
+    }
+    if (bo) {
+      if (nb <= x) blo = bm + 1; else bhi = bm;
+    }
+  }
+  r0 = alo;
+  r1 = blo;
+}
+
 // first i in [lo, hi) with nbr[i] >= x
 __device__ __forceinline__ int32_t lower_nbr(const int32_t* __restrict__ nbr, int32_t lo,
                                              int32_t hi, int32_t x) {

@@ -66,8 +66,7 @@ __device__ __forceinline__ void leg_window(const GraphView& g, int32_t a, int32_
   int32_t h = g.dst[a];
   int32_t hs = g.optr[h], he = g.optr[h + 1];
   int32_t ta = g.ts[a];
-  q0 = after_edge(g.ot, g.oeid, hs, he, ta, a);
-  q1 = upper_t(g.ot, q0, he, (int64_t)ta + delta);
+  after_edge_upto(g.ot, g.oeid, hs, he, ta, a, (int64_t)ta + delta, q0, q1);
 }
 
 // number of slots in [lo, hi) of the (nbr, t, id) copy with nbr == x and
@@ -77,11 +76,10 @@ __device__ __forceinline__ int32_t pair_after(const int32_t* __restrict__ nn,
                                               const int32_t* __restrict__ ne, int32_t lo,
                                               int32_t hi, int32_t x, int32_t te, int32_t e,
                                               int32_t delta) {
-  int32_t r0 = lower_nbr(nn, lo, hi, x);
-  if (r0 >= hi || __ldg(nn + r0) != x) return 0;
-  int32_t r1 = lower_nbr(nn, r0, hi, x + 1);
-  int32_t b0 = after_edge(nt, ne, r0, r1, te, e);
-  int32_t b1 = upper_t(nt, b0, r1, (int64_t)te + delta);
+  int32_t r0, r1, b0, b1;
+  nbr_range(nn, lo, hi, x, r0, r1);
+  if (r1 == r0) return 0;
+  after_edge_upto(nt, ne, r0, r1, te, e, (int64_t)te + delta, b0, b1);
   return b1 - b0;
 }
 
@@ -91,11 +89,10 @@ __device__ __forceinline__ int32_t pair_before(const int32_t* __restrict__ nn,
                                                const int32_t* __restrict__ ne, int32_t lo,
                                                int32_t hi, int32_t x, int32_t te, int32_t e,
                                                int32_t delta) {
-  int32_t r0 = lower_nbr(nn, lo, hi, x);
-  if (r0 >= hi || __ldg(nn + r0) != x) return 0;
-  int32_t r1 = lower_nbr(nn, r0, hi, x + 1);
-  int32_t b0 = lower_t(nt, r0, r1, (int64_t)te - delta);
-  int32_t b1 = after_edge(nt, ne, b0, r1, te, e);
+  int32_t r0, r1, b0, b1;
+  nbr_range(nn, lo, hi, x, r0, r1);
+  if (r1 == r0) return 0;
+  since_upto_edge(nt, ne, r0, r1, (int64_t)te - delta, te, e, b0, b1);
   return b1 - b0;
 }
 
@@ -115,8 +112,8 @@ __device__ __forceinline__ int32_t legs_into(const GraphView& g, int32_t b, int3
   int32_t h = g.src[b];
   int32_t hs = g.iptr[h], he = g.iptr[h + 1];
   int32_t tb = g.ts[b];
-  int32_t c0 = lower_t(g.it, hs, he, (int64_t)tb - delta);
-  int32_t c1 = after_edge(g.it, g.ieid, c0, he, tb, b);
+  int32_t c0, c1;
+  since_upto_edge(g.it, g.ieid, hs, he, (int64_t)tb - delta, tb, b, c0, c1);
   return (c1 - c0) - pair_before(g.innbr, g.int_, g.ineid, hs, he, g.dst[b], tb, b, delta);
 }
 
@@ -161,12 +158,18 @@ __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
     if (L_new) L_new[a] = 0;
     return;
   }
-  int32_t q0, q1;
-  leg_window(g, a, q0, q1, delta);
-  qwin[a] = make_int2(q0, q1);
   const int32_t ta = g.ts[a];
   const int32_t hs = g.optr[h], he = g.optr[h + 1];
-  L[a] = (q1 - q0) - pair_after(g.onnbr, g.ont, g.oneid, hs, he, x, ta, a, delta);
+  int32_t q0, q1;
+  after_edge_upto(g.ot, g.oeid, hs, he, ta, a, (int64_t)ta + delta, q0, q1);
+  qwin[a] = make_int2(q0, q1);
+  // returns h -> x inside the window: slots [b0, b1) of x's run [r0, r1) in
+  // h's (nbr, t, id) list
+  int32_t r0, r1, b0, b1;
+  nbr_range(g.onnbr, hs, he, x, r0, r1);
+  b0 = b1 = r0;
+  if (r1 > r0) after_edge_upto(g.ont, g.oneid, r0, r1, ta, a, (int64_t)ta + delta, b0, b1);
+  L[a] = (q1 - q0) - (b1 - b0);
   // smaller windows: the prefix of the window within their delta (delta
   // counting: only the legs whose second edge is new)
 #pragma unroll
@@ -175,17 +178,13 @@ __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
       const int32_t di = sub.delta[i];
       const int32_t q1i = upper_t(g.ot, q0, q1, (int64_t)ta + di);
       if (g.new_from == 0) {
-        sub.gs_from[i][a] =
-            (q1i - q0) - pair_after(g.onnbr, g.ont, g.oneid, hs, he, x, ta, a, di);
+        sub.gs_from[i][a] = (q1i - q0) - (upper_t(g.ont, b0, b1, (int64_t)ta + di) - b0);
       } else {
         const int32_t qn = after_edge(g.ot, g.oeid, q0, q1i, g.t_new, g.new_from - 1);
         int32_t back = 0;
-        const int32_t r0 = lower_nbr(g.onnbr, hs, he, x);
-        if (qn < q1i && r0 < he && __ldg(g.onnbr + r0) == x) {
-          const int32_t r1 = lower_nbr(g.onnbr, r0, he, x + 1);
-          const int32_t b0 = after_edge(g.ont, g.oneid, r0, r1, ta, a);
-          const int32_t bn = after_edge(g.ont, g.oneid, b0, r1, g.t_new, g.new_from - 1);
-          back = upper_t(g.ont, bn, r1, (int64_t)ta + di) - bn;
+        if (qn < q1i && b1 > b0) {
+          const int32_t bn = after_edge(g.ont, g.oneid, b0, b1, g.t_new, g.new_from - 1);
+          back = upper_t(g.ont, bn, b1, (int64_t)ta + di) - bn;
         }
         sub.gs_from[i][a] = (q1i - qn) - back;
       }
@@ -193,30 +192,17 @@ __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
   if (L_new) {
     const int32_t qn = after_edge(g.ot, g.oeid, q0, q1, g.t_new, g.new_from - 1);
     int32_t back = 0;
-    const int32_t r0 = lower_nbr(g.onnbr, hs, he, x);
-    if (qn < q1 && r0 < he && __ldg(g.onnbr + r0) == x) {
-      const int32_t r1 = lower_nbr(g.onnbr, r0, he, x + 1);
-      const int32_t b0 = after_edge(g.ont, g.oneid, r0, r1, ta, a);
-      const int32_t bn = after_edge(g.ont, g.oneid, b0, r1, g.t_new, g.new_from - 1);
-      const int32_t b1 = upper_t(g.ont, bn, r1, (int64_t)ta + delta);
-      back = b1 - bn;
-    }
+    if (qn < q1 && b1 > b0) back = b1 - after_edge(g.ont, g.oneid, b0, b1, g.t_new, g.new_from - 1);
     L_new[a] = (q1 - qn) - back;
   }
   if (!L2) return;
   const int32_t qc = cycle_bound(g, crng, a, q0, q1);
   qcb[a] = qc;
   int32_t back = 0;
-  if (qc > q0) {  // returns h -> src(a) among the slots [q0, qc)
-    const int32_t r0 = lower_nbr(g.onnbr, hs, he, x);
-    if (r0 < he && __ldg(g.onnbr + r0) == x) {
-      const int32_t r1 = lower_nbr(g.onnbr, r0, he, x + 1);
-      const int2 cr = crng[a];
-      const int32_t b0 = after_edge(g.ont, g.oneid, r0, r1, ta, a);
-      const int32_t b1 = after_edge(g.ont, g.oneid, b0, r1, __ldg(g.it + cr.y - 1),
-                                    __ldg(g.ieid + cr.y - 1) - 1);
-      back = b1 - b0;
-    }
+  if (qc > q0 && b1 > b0) {  // returns h -> src(a) among the slots [q0, qc)
+    const int2 cr = crng[a];
+    back = after_edge(g.ont, g.oneid, b0, b1, __ldg(g.it + cr.y - 1),
+                      __ldg(g.ieid + cr.y - 1) - 1) - b0;
   }
   L2[a] = (qc - q0) - back;
 }
@@ -750,8 +736,7 @@ __global__ void __launch_bounds__(512) k_close_range(GraphView g, int32_t delta,
   if (u0 != g.dst[a]) {
     int32_t is = g.iptr[u0], ie = g.iptr[u0 + 1];
     int32_t ta = g.ts[a];
-    r.x = after_edge(g.it, g.ieid, is, ie, ta, a);
-    r.y = upper_t(g.it, r.x, ie, (int64_t)ta + delta);
+    after_edge_upto(g.it, g.ieid, is, ie, ta, a, (int64_t)ta + delta, r.x, r.y);
     // delta counting: a cycle is new iff its closing (latest) edge is new
     if (g.new_from > 0) r.x = after_edge(g.it, g.ieid, r.x, r.y, g.t_new, g.new_from - 1);
   }
@@ -783,7 +768,7 @@ __device__ __forceinline__ void cyc_path(const GraphView& g, const CycFrontier& 
 // cycles of length j+1 that close from its end node through B1, and reports
 // the window of later hops its children will take.
 template <int NS>
-__global__ void __launch_bounds__(512) k_cyc_level(GraphView g, int32_t delta, int K, int j,
+__global__ void __launch_bounds__(512, 4) k_cyc_level(GraphView g, int32_t delta, int K, int j,
                                                    CycFrontier F, int64_t n,
                                                    const int2* __restrict__ close_rng,
                                                    CycleSlots slots,
@@ -842,13 +827,13 @@ __global__ void __launch_bounds__(512) k_cyc_level(GraphView g, int32_t delta, i
         }
       } else {
         const int32_t in_s = g.iptr[u0], in_e = g.iptr[u0 + 1];
-        const int32_t r0 = lower_nbr(g.innbr, in_s, in_e, w);
-        if (r0 < in_e && __ldg(g.innbr + r0) == w) {
-          const int32_t r1 = lower_nbr(g.innbr, r0, in_e, w + 1);
-          int32_t b0 = after_edge(g.int_, g.ineid, r0, r1, tl, last);
+        int32_t r0, r1;
+        nbr_range(g.innbr, in_s, in_e, w, r0, r1);
+        if (r1 > r0) {
+          int32_t b0, b1;
+          after_edge_upto(g.int_, g.ineid, r0, r1, tl, last, tmax[0], b0, b1);
           // delta counting: only new closing edges (the scan branch's range already is)
-          if (g.new_from > 0) b0 = after_edge(g.int_, g.ineid, b0, r1, g.t_new, g.new_from - 1);
-          const int32_t b1 = upper_t(g.int_, b0, r1, tmax[0]);
+          if (g.new_from > 0) b0 = min(after_edge(g.int_, g.ineid, b0, r1, g.t_new, g.new_from - 1), b1);
 #pragma unroll
           for (int t = 0; t < NT; ++t) {
             if (!col[t]) continue;
@@ -866,8 +851,8 @@ __global__ void __launch_bounds__(512) k_cyc_level(GraphView g, int32_t delta, i
   }
   if (has_next) {
     const int32_t ws = g.optr[w], we = g.optr[w + 1];
-    const int32_t q0 = after_edge(g.ot, g.oeid, ws, we, tl, last);
-    const int32_t q1 = upper_t(g.ot, q0, we, t_cl);
+    int32_t q0, q1;
+    after_edge_upto(g.ot, g.oeid, ws, we, tl, last, t_cl, q0, q1);
     cnt[i] = q1 - q0;
     q0_out[i] = q0;
   }
