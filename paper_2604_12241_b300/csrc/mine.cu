@@ -132,6 +132,8 @@ __device__ __forceinline__ int32_t cycle_bound(const GraphView& g, const int2* c
 // With L_new (delta counting): L_new[a] = legs from a whose second edge is new.
 // qwin[a] = a's window slots [q0, q1) in dst(a)'s out-list and, with crng,
 // qcb[a] = its cycle bound, kept for the emission.
+// Z: the accumulators the emission and later kernels add into, zeroed here
+// (element a of each) instead of by separate memsets.
 template <int NS>
 __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
                                                    int32_t* __restrict__ L,
@@ -140,10 +142,15 @@ __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
                                                    int32_t* __restrict__ L_new,
                                                    int2* __restrict__ qwin,
                                                    int32_t* __restrict__ qcb,
-                                                   SubWindows sub) {
+                                                   SubWindows sub, ZeroSink Z) {
   int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a64 >= g.E) return;
   int32_t a = (int32_t)a64;
+  for (int c = 0; c < Z.n_acc; ++c) Z.acc[(int64_t)c * g.E + a] = 0ull;
+  if (Z.gs_in) Z.gs_in[a] = 0;
+#pragma unroll
+  for (int i = 0; i < NS; ++i)
+    if (i < sub.n && sub.gs_in[i]) sub.gs_in[i][a] = 0;
   const int32_t x = g.src[a], h = g.dst[a];
   if (x == h) {
     L[a] = 0;
@@ -986,11 +993,11 @@ static void nsub_dispatch(int n, F&& f) {
 
 void launch_leg_count(unsigned grid, int block, cudaStream_t s, const GraphView& g, int32_t delta,
                       int32_t* L, const int2* crng, int32_t* L2, int32_t* L_new, int2* qwin,
-                      int32_t* qcb, const SubWindows& sub) {
+                      int32_t* qcb, const SubWindows& sub, const ZeroSink& Z) {
   nsub_dispatch(sub.n, [&](auto ns) {
     AML_LAUNCH("k_leg_count", s,
                k_leg_count<decltype(ns)::value><<<grid, block, 0, s>>>(g, delta, L, crng, L2,
-                                                                      L_new, qwin, qcb, sub));
+                                                                      L_new, qwin, qcb, sub, Z));
   });
 }
 

@@ -146,11 +146,18 @@ __global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, uint32_t*
 __global__ void k_sg_hist(const LegRec* rec, int64_t n, int bits, uint32_t* hist);
 __global__ void k_mark_nodes(const int32_t* node_of, int64_t from, int64_t E, uint32_t* mask);
 __global__ void k_close_range(GraphView g, int32_t delta, int2* rng);
+// Buffers k_leg_count zeroes per edge: n_acc accumulator columns of E
+// entries, and the GS gather-side counts (either may be absent).
+struct ZeroSink {
+  unsigned long long* acc;
+  int n_acc;
+  int32_t* gs_in;
+};
 // Launchers of the kernels that also count sub-windows (instantiated for
 // the number of them in sub).
 void launch_leg_count(unsigned grid, int block, cudaStream_t s, const GraphView& g, int32_t delta,
                       int32_t* L, const int2* crng, int32_t* L2, int32_t* L_new, int2* qwin,
-                      int32_t* qcb, const SubWindows& sub);
+                      int32_t* qcb, const SubWindows& sub, const ZeroSink& Z);
 void launch_leg_emit(unsigned grid, int block, cudaStream_t s, const GraphView& g,
                      const int2* qwin, const int32_t* qcb, const int64_t* off, const LegSink& S,
                      unsigned long long* acc_cyc2, int32_t* gs_in, int32_t own_max,

@@ -118,8 +118,10 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     if (f == AML_FAM_GS || f == AML_FAM_SG || f == AML_FAM_CYC) P.inst_mask |= 1ull << c;
   }
 
+  // zeroed by the first leg count (before any kernel adds into it), or
+  // below when no window counts legs
   DBuf<unsigned long long> acc((size_t)std::max(n_acc, 1) * E, s);
-  if (n_acc) AML_CUDA(cudaMemsetAsync(acc.p, 0, (size_t)n_acc * E * 8, s));
+  bool acc_zeroed = n_acc == 0;
   P.acc = acc.p;
 
   // Smaller windows whose GS/SG/CYC columns are counted from the largest
@@ -223,8 +225,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
         keep32.emplace_back((size_t)E, s);
         sub.gs_from[i] = keep32.back().p;
         keep32.emplace_back((size_t)E, s);
-        sub.gs_in[i] = keep32.back().p;
-        AML_CUDA(cudaMemsetAsync(sub.gs_in[i], 0, (size_t)E * 4, s));
+        sub.gs_in[i] = keep32.back().p;  // zeroed by k_leg_count
         P.gs_from[m] = sub.gs_from[i];
         P.gs_in[m] = sub.gs_in[i];
       }
@@ -254,8 +255,16 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     }
     DBuf<int2> qwin((size_t)E, s);
     DBuf<int32_t> qcb(level_cycles ? (size_t)E : 0, s);
+    int32_t* gs_in = nullptr;
+    if (wp.gs && wp.emit_legs()) {  // gather-side GS counts, added to by the emission
+      keep32.emplace_back((size_t)E, s);
+      gs_in = keep32.back().p;
+      P.gs_in[w] = gs_in;
+    }
+    ZeroSink Z{acc_zeroed ? nullptr : acc.p, acc_zeroed ? 0 : n_acc, gs_in};
+    acc_zeroed = true;
     launch_leg_count(grid_for(E, B), B, s, gv, wp.delta, L.p, level_cycles ? crng.p : nullptr,
-                     level_cycles ? L2.p : nullptr, L_new, qwin.p, qcb.p, sub);
+                     level_cycles ? L2.p : nullptr, L_new, qwin.p, qcb.p, sub, Z);
     AML_CUDA(cudaMemsetAsync(L.p + E, 0, sizeof(int32_t), s));
     keep64.emplace_back((size_t)(E + 1), s);
     int64_t* off = keep64.back().p;
@@ -265,8 +274,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       AML_CUDA(cudaMemsetAsync(L2.p + E, 0, sizeof(int32_t), s));
       scan_i32_to_i64(L2.p, off2.p, E + 1, s);
     }
-    int32_t* gs_in = nullptr;
-    if (wp.gs) {
+    if (wp.gs && !wp.emit_legs()) {  // written outright by k_gs_into
       keep32.emplace_back((size_t)E, s);
       gs_in = keep32.back().p;
       P.gs_in[w] = gs_in;
@@ -290,7 +298,6 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       if (level_cycles) lc.n_front[2] = total[1];
     }
     const int64_t nl = lc.n_legs;
-    if (gs_in) AML_CUDA(cudaMemsetAsync(gs_in, 0, (size_t)E * 4, s));
     LegSink S{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
     DBuf<int32_t> la, lb;
     if (level_cycles) {
@@ -418,6 +425,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     // the window's buffers (rec, hist, ...) are freed on s after this join
     if (sg_branch) branch_wait(g->branch_ev[3], s_sg, s);
   }
+  if (!acc_zeroed) AML_CUDA(cudaMemsetAsync(acc.p, 0, (size_t)n_acc * E * 8, s));
   if (branches) AML_CUDA(cudaStreamWaitEvent(s, g->branch_ev[1], 0));
   AML_LAUNCH("k_assemble", s,
              k_assemble<<<grid_for(E, ASM_BLOCK), ASM_BLOCK,
