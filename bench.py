@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--mode", choices=["graph", "plain"], default="graph",
                     help="graph: the whole mine replayed as one captured CUDA graph")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help='fixed tunables instead of the autotuner, e.g. '
+                         '\'{"own_max": 16, "block": 128}\' (profiling captures)')
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--cycle-mode", choices=["auto", "plain", "persistent", "learned"],
                     default="auto", help="cycle search; auto = fastest measured")
@@ -159,11 +162,15 @@ def measured_peak():
 
 # DRAM bytes per launch (read + write) from one ncu capture of hi-small at
 # full size (profiles/dram_hi_small.md), valid only for the kernel sources it
-# was taken with: KERNEL_DIGEST is their digest (kernel_digest()).
-KERNEL_DIGEST = "e57da2a54aeed338"
-MEASURED_TRAFFIC = {"k_cyc_level": 235.5e6, "k_sg_bucket": 524.6e6, "k_leg_emit": 619.6e6,
-                    "k_sg_partition": 624.3e6, "k_fan_reduce": 233.4e6, "k_fan_scan": 314.0e6,
-                    "k_leg_count": 235.5e6}
+# was taken with: KERNEL_DIGEST is the digest (kernel_digest()) of the files
+# that define the measured kernels.
+KERNEL_DIGEST = "17bc39acc67e819f"
+MEASURED_TRAFFIC = {"k_cyc_level": 268.6e6, "k_sg_bucket": 518.7e6, "k_leg_emit": 609.5e6,
+                    "k_sg_partition": 552.5e6, "k_fan_reduce": 231.7e6, "k_fan_scan": 315.1e6,
+                    "k_assemble": 1077.0e6, "k_leg_count": 699.4e6}
+
+
+TRAFFIC_SOURCES = ("aml_internal.cuh", "fan.cu", "mine.cu", "mine.cuh", "pipeline.cu", "prims.cu")
 
 
 def kernel_digest() -> str:
@@ -171,7 +178,7 @@ def kernel_digest() -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2604_12241_b300", "csrc")
-    for p in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+    for p in sorted(os.path.join(csrc, f) for f in TRAFFIC_SOURCES):
         h.update(os.path.relpath(p, ROOT).encode())
         with open(p, "rb") as f:
             h.update(f.read())
@@ -401,7 +408,10 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.current_stream()
 
     tune_info = None
-    if not args.no_autotune:
+    if args.tuning:
+        graph.set_tuning(**json.loads(args.tuning))
+        tune_info = {"tuning": graph.tuning(), "fixed": True}
+    elif not args.no_autotune:
         t0 = time.perf_counter()
         best, best_ms = aml.autotune(graph, ps, repeats=3)
         tune_info = {"tuning": best, "best_ms": best_ms, "seconds": time.perf_counter() - t0}
