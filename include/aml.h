@@ -91,8 +91,13 @@ aml_status aml_graph_create(const int32_t* src, const int32_t* dst, const int32_
                             const float* amount, int64_t n_edges, int32_t n_nodes,
                             uint32_t flags, void* stream, aml_graph** out);
 
-/* Free a graph and everything cached on it (NULL is a no-op).  Synchronizes
- * the device work previously enqueued on the graph. */
+/* Free a graph and everything cached on it (NULL is a no-op).  Waits for the
+ * work enqueued on the graph: on every stream passed to aml_graph_create,
+ * aml_mine, aml_autotune and aml_cost_train for it, and on the graph's own
+ * internal streams -- not for unrelated work elsewhere on the device, so a
+ * caller may destroy one graph while the next one's transfers and mining are
+ * in flight.  Work a caller enqueued on this graph through aml_fan_noalloc
+ * on yet another stream must be finished before the call. */
 aml_status aml_graph_destroy(aml_graph* g);
 
 typedef struct aml_graph_info {
@@ -237,11 +242,18 @@ aml_status aml_pattern_set_column(const aml_pattern_set* ps, int32_t col,
                                    /* order come from the cost model trained by  */
                                    /* aml_cost_train for that window (degree     */
                                    /* estimate when no model exists)            */
+#define AML_MINE_HOST_ASYNC 0x10u  /* with HOST_OUTPUT: counts is page-locked    */
+                                   /* host memory (cudaHostAlloc / registered),  */
+                                   /* the copy back is enqueued on `stream` and  */
+                                   /* the call returns without waiting for it:   */
+                                   /* synchronize `stream` before reading counts */
+                                   /* (pageable memory: AML_EINVAL)              */
 
 /* Count every pattern of `ps` for every edge of `g`.
  *   counts : uint32, row-major, row e = input edge e, column j = pattern j;
  *            element (e, j) at counts[e * ld + j].  Device pointer unless
- *            AML_MINE_HOST_OUTPUT (then the call synchronizes `stream`).
+ *            AML_MINE_HOST_OUTPUT (then the call synchronizes `stream`,
+ *            unless AML_MINE_HOST_ASYNC).
  *            Columns >= n_cols of each row are left untouched.
  *   ld     : row stride in elements, ld >= n_cols
  *   flags  : AML_MINE_* (unknown bits: AML_EINVAL)

@@ -17,8 +17,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import patterns  # noqa: F401
-from ._lib import (ASSUME_SORTED, MINE_GRAPH, MINE_HOST_OUTPUT, MINE_LEARNED,  # noqa: F401
-                   MINE_PERSISTENT, PTR_DEVICE, PTR_HOST, AmlError, aml_column_info,
+from ._lib import (ASSUME_SORTED, MINE_GRAPH, MINE_HOST_ASYNC, MINE_HOST_OUTPUT,  # noqa: F401
+                   MINE_LEARNED, MINE_PERSISTENT, PTR_DEVICE, PTR_HOST, AmlError, aml_column_info,
                    aml_cost_report, aml_graph_info, aml_stream_batch, aml_stream_info,
                    aml_tuning, check, lib, make_patterns)
 
@@ -177,13 +177,16 @@ MODES = {"plain": 0, "persistent": MINE_PERSISTENT, "learned": MINE_LEARNED}
 
 
 def mine(graph: Graph, pset: PatternSet, out=None, stream=None, host_output: bool = False,
-         use_graph: bool = False, mode: str = "plain"):
+         use_graph: bool = False, mode: str = "plain", host_async: bool = False):
     """Per-edge counts, [E, P] (aml_mine).
 
     Device mode (default) returns / fills a torch int32 CUDA tensor holding
     the uint32 counts bit-for-bit (``.view(torch.uint32)`` or numpy
     ``.view(np.uint32)`` to read them unsigned).  ``host_output=True``
-    returns a numpy uint32 array copied back by the library.  ``use_graph``
+    returns a numpy uint32 array copied back by the library; with
+    ``host_async=True`` the copy is only enqueued on ``stream`` (``out`` must
+    be page-locked, e.g. a pinned torch tensor's ``.numpy()``) and the caller
+    synchronizes ``stream`` before reading it.  ``use_graph``
     replays the whole mine as one captured CUDA graph (AML_MINE_GRAPH).
     ``mode``: "plain" (level-by-level cycle search), "persistent" (one
     persistent launch, degree-binned queues) or "learned" (queues from the
@@ -199,7 +202,8 @@ def mine(graph: Graph, pset: PatternSet, out=None, stream=None, host_output: boo
         if dev:
             raise ValueError("host_output needs a host array")
         check(lib().aml_mine(graph.handle, pset.handle, ptr, arr.shape[1],
-                             MINE_HOST_OUTPUT | flags, s))
+                             MINE_HOST_OUTPUT | (MINE_HOST_ASYNC if host_async else 0) | flags,
+                             s))
         return arr
     import torch
     if out is None:

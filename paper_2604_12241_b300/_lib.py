@@ -23,6 +23,7 @@ MINE_HOST_OUTPUT = 0x1
 MINE_GRAPH = 0x2
 MINE_PERSISTENT = 0x4
 MINE_LEARNED = 0x8
+MINE_HOST_ASYNC = 0x10
 
 
 class AmlError(RuntimeError):

@@ -149,6 +149,15 @@ struct aml_graph {
   std::vector<void*> allocs;
   std::map<int32_t, aml::LegCache> legs;  // per window
   cudaStream_t last_stream = nullptr;
+  // every caller stream work on this graph was enqueued on (destroy waits
+  // for these, not for the whole device)
+  std::vector<cudaStream_t> used_streams;
+  void note_stream(cudaStream_t s) {
+    last_stream = s;
+    for (cudaStream_t u : used_streams)
+      if (u == s) return;
+    used_streams.push_back(s);
+  }
   int device = 0;
   aml::Tuning tune;
   uint64_t tune_gen = 0;

@@ -189,8 +189,10 @@ aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, i
   return guarded("aml_mine", [&] {
     AML_REQUIRE(g && ps, AML_EINVAL, "NULL graph or pattern set");
     AML_REQUIRE((flags & ~(AML_MINE_HOST_OUTPUT | AML_MINE_GRAPH | AML_MINE_PERSISTENT |
-                           AML_MINE_LEARNED)) == 0,
+                           AML_MINE_LEARNED | AML_MINE_HOST_ASYNC)) == 0,
                 AML_EINVAL, "unknown flag bits");
+    AML_REQUIRE(!(flags & AML_MINE_HOST_ASYNC) || (flags & AML_MINE_HOST_OUTPUT), AML_EINVAL,
+                "AML_MINE_HOST_ASYNC needs AML_MINE_HOST_OUTPUT");
     const uint32_t mode = flags & (AML_MINE_PERSISTENT | AML_MINE_LEARNED);
     AML_REQUIRE(!((flags & AML_MINE_GRAPH) && (flags & AML_MINE_HOST_OUTPUT)), AML_EINVAL,
                 "AML_MINE_GRAPH needs a device output");
@@ -198,7 +200,13 @@ aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, i
     AML_REQUIRE(ld >= P, AML_EINVAL, "ld must be >= the number of columns");
     AML_REQUIRE(g->E == 0 || counts != nullptr, AML_EINVAL, "counts is NULL");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    g->last_stream = s;
+    g->note_stream(s);
+    if (flags & AML_MINE_HOST_ASYNC) {  // the copy must not fall back to a synchronous one
+      cudaPointerAttributes at;
+      AML_CUDA(cudaPointerGetAttributes(&at, counts));
+      AML_REQUIRE(at.type == cudaMemoryTypeHost, AML_EINVAL,
+                  "AML_MINE_HOST_ASYNC needs page-locked host memory");
+    }
     if (flags & AML_MINE_HOST_OUTPUT) {
       DBuf<uint32_t> dev((size_t)(g->E * P), s);
       mine_plain(g, ps, dev.p, P, s, mode);
@@ -208,7 +216,8 @@ aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, i
       else if (g->E)
         AML_CUDA(cudaMemcpy2DAsync(counts, (size_t)ld * 4, dev.p, (size_t)P * 4, (size_t)P * 4,
                                    (size_t)g->E, cudaMemcpyDeviceToHost, s));
-      AML_CUDA(cudaStreamSynchronize(s));
+      // the staging buffer is released in stream order after the copy
+      if (!(flags & AML_MINE_HOST_ASYNC)) AML_CUDA(cudaStreamSynchronize(s));
     } else if (flags & AML_MINE_GRAPH) {
       mine_graph_mode(g, ps, counts, ld, s, mode);
     } else {

@@ -519,11 +519,11 @@ void cost_train(aml_graph* g, const aml_pattern_set* ps, int64_t max_samples, in
   for (int i = 0; i < MLP_H * MLP_IN; ++i) p[MLP_W1 + i] = nd(rng) * std::sqrt(2.f / MLP_IN);
   for (int i = 0; i < MLP_H * MLP_H; ++i) p[MLP_W2 + i] = nd(rng) * std::sqrt(2.f / MLP_H);
   for (int i = 0; i < MLP_H; ++i) p[MLP_W3 + i] = nd(rng) * std::sqrt(1.f / MLP_H);
-  void* dparams = nullptr;
-  AML_CUDA(cudaMalloc(&dparams, MLP_NPARAM * 4));
+  void* dparams = dalloc(MLP_NPARAM * 4, s);  // kept with the graph, freed with it
   cm.params = static_cast<float*>(dparams);
   g->allocs.push_back(dparams);
-  AML_CUDA(cudaMemcpy(cm.params, p.data(), MLP_NPARAM * 4, cudaMemcpyHostToDevice));
+  AML_CUDA(cudaMemcpyAsync(cm.params, p.data(), MLP_NPARAM * 4, cudaMemcpyHostToDevice, s));
+  AML_CUDA(cudaStreamSynchronize(s));
   DBuf<float> m(MLP_NPARAM, s), v(MLP_NPARAM, s), grad(MLP_NPARAM, s), loss(1, s);
   AML_CUDA(cudaMemsetAsync(m.p, 0, MLP_NPARAM * 4, s));
   AML_CUDA(cudaMemsetAsync(v.p, 0, MLP_NPARAM * 4, s));
@@ -614,6 +614,7 @@ extern "C" aml_status aml_cost_train(aml_graph* g, const aml_pattern_set* ps, in
     AML_REQUIRE(g && ps, AML_EINVAL, "NULL graph or pattern set");
     AML_REQUIRE(max_samples >= 64 && epochs >= 1 && epochs <= 1000, AML_EINVAL,
                 "max_samples >= 64 and epochs in [1, 1000]");
+    g->note_stream(static_cast<cudaStream_t>(stream));
     cost_train(g, ps, max_samples, epochs, seed, static_cast<cudaStream_t>(stream), report);
     return AML_OK;
   } catch (const Failure& f) {

@@ -200,7 +200,7 @@ aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts
     AML_CUDA(cudaGetDevice(&g->device));
     g->E = E;
     g->N = N;
-    g->last_stream = s;
+    g->note_stream(s);
     g->src = ga.get<int32_t>(E);
     g->dst = ga.get<int32_t>(E);
     g->ts = ga.get<int32_t>(E);
@@ -267,7 +267,20 @@ void drop_captured_mines(aml_graph* g);
 
 void destroy_graph(aml_graph* g) {
   if (!g) return;
-  cudaDeviceSynchronize();
+  // wait for the work enqueued on this graph: on every stream a call was
+  // given, and on the graph's own side and capture streams (not for other
+  // work on the device, so a caller can overlap a graph's teardown with the
+  // next graph's transfers); the whole device only if one of them cannot be
+  // waited on
+  bool ok = true;
+  for (cudaStream_t st : g->used_streams) ok &= cudaStreamSynchronize(st) == cudaSuccess;
+  for (cudaStream_t st : g->side)
+    if (st) ok &= cudaStreamSynchronize(st) == cudaSuccess;
+  if (g->capture_stream) ok &= cudaStreamSynchronize(g->capture_stream) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    cudaDeviceSynchronize();
+  }
   drop_captured_mines(g);
   if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
   for (cudaStream_t st : g->side)

@@ -174,6 +174,7 @@ aml_status aml_autotune(aml_graph* g, const aml_pattern_set* ps, int32_t repeats
   try {
     AML_REQUIRE(g && ps, AML_EINVAL, "NULL graph or pattern set");
     AML_REQUIRE(repeats >= 1 && repeats <= 100, AML_EINVAL, "repeats must be in [1, 100]");
+    g->note_stream(static_cast<cudaStream_t>(stream));
     autotune(g, ps, repeats, static_cast<cudaStream_t>(stream), best, best_ms);
     return AML_OK;
   } catch (const Failure& f) {

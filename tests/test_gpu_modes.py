@@ -63,3 +63,34 @@ def test_autotune_keeps_counts(setup):
     best, ms = aml.autotune(graph, ps, repeats=2)
     assert ms > 0 and graph.tuning() == best
     np.testing.assert_array_equal(aml.mine(graph, ps).cpu().numpy(), ref)
+
+
+def test_async_host_output_and_overlapped_graphs(setup):
+    """AML_MINE_HOST_ASYNC: the copy back is only enqueued; after a stream
+    sync the pinned buffer holds the device result.  Two graphs on two
+    streams, each destroyed while the other's work is in flight (destroy
+    waits for its own streams only), give identical counts.  A pageable
+    buffer is refused."""
+    import torch
+    graph, ps, ref = setup
+    g = aml_synth.workload("tiny-10k")
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [torch.empty(ref.shape, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+            for _ in range(2)]
+    live = [None, None]
+    for k in range(5):
+        i = k % 2
+        if live[i] is not None:
+            live[i].close()
+            np.testing.assert_array_equal(outs[i], ref.view(np.uint32))
+        outs[i][:] = 0xFFFFFFFF
+        gg = aml.Graph(g.src, g.dst, g.ts, g.n_nodes, assume_sorted=True, stream=streams[i])
+        aml.mine(gg, ps, out=outs[i], host_output=True, host_async=True, stream=streams[i])
+        live[i] = gg
+    for i in range(2):
+        live[i].close()
+        np.testing.assert_array_equal(outs[i], ref.view(np.uint32))
+    with pytest.raises(aml.AmlError) as ei:
+        aml.mine(graph, ps, out=np.empty(ref.shape, dtype=np.uint32), host_output=True,
+                 host_async=True)
+    assert ei.value.name == "AML_EINVAL"
