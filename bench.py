@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--workload", default="hi-small", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (nodes, edges, hub cap) for profiling captures")
-    ap.add_argument("--e2e-steps", type=int, default=6)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -486,56 +486,71 @@ def run_ours(args, ws, rank, local):
     prof_steps = max(3, min(args.steps, 10))
     plain_ms, _, plain_launches, prof = timed(prof_steps, False, True, cycle_mode)
 
-    # end to end through the public API: pinned host inputs -> graph build ->
-    # mine -> counts copied back to pinned host memory, every step.  Two
-    # streams and two output buffers: step k's copy back (the 406 MB of
-    # counts) overlaps step k+1's upload, graph build and mine; a step's graph
-    # is destroyed (which waits for its copy) before its buffers are reused.
+    # end to end through the public API, every step: the step's inputs copied
+    # from pinned host memory to the device, graph build, mine, and the
+    # counts copied back to pinned host memory.  The copy engines run one
+    # transfer at a time, so the steps are pipelined on two streams in the
+    # order upload(k), copy back(k-1): step k's build and mine run while step
+    # k-1's 406 MB of counts travel back.  A step's graph is destroyed (which
+    # waits for its stream) before its buffers are reused.
     e2e = None
     if not args.no_e2e:
         pin = {k: torch.from_numpy(v).pin_memory() for k, v in
                (("src", g.src), ("dst", g.dst), ("ts", g.ts), ("amount", g.amount))}
-        host = {k: t.numpy() for k, t in pin.items()}
-        host_out = [torch.empty((E, Pn), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
-                    for _ in range(2)]
-        e2e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        S = [torch.cuda.Stream(), torch.cuda.Stream()]
+        dev_in = [{k: torch.empty_like(t, device="cuda") for k, t in pin.items()} for _ in range(2)]
+        dev_out = [torch.empty((E, Pn), dtype=torch.int32, device="cuda") for _ in range(2)]
+        out_pin = [torch.empty((E, Pn), dtype=torch.int32).pin_memory() for _ in range(2)]
         live = [None, None]
+
+        def copy_back(j):
+            with torch.cuda.stream(S[j]):
+                out_pin[j].copy_(dev_out[j], non_blocking=True)
 
         def e2e_step(k):
             i = k % 2
             if live[i] is not None:
                 live[i].close()
                 live[i] = None
-            gg = aml.Graph(host["src"], host["dst"], host["ts"], g.n_nodes,
-                           amount=host["amount"], assume_sorted=True, stream=e2e_streams[i])
-            aml.mine(gg, ps, out=host_out[i], host_output=True, host_async=True,
-                     stream=e2e_streams[i])
+            with torch.cuda.stream(S[i]):
+                for key, t in pin.items():
+                    dev_in[i][key].copy_(t, non_blocking=True)
+            if k > 0:
+                up = torch.cuda.Event()
+                up.record(S[i])
+                S[1 - i].wait_event(up)
+                copy_back(1 - i)
+            gg = aml.Graph(dev_in[i]["src"], dev_in[i]["dst"], dev_in[i]["ts"], g.n_nodes,
+                           amount=dev_in[i]["amount"], assume_sorted=True, stream=S[i])
+            aml.mine(gg, ps, out=dev_out[i], stream=S[i])
             live[i] = gg
 
-        def e2e_drain():
+        def e2e_finish(k_last):
+            copy_back(k_last % 2)
             for i in range(2):
                 if live[i] is not None:
                     live[i].close()
                     live[i] = None
 
         e2e_step(0)
-        e2e_drain()
+        e2e_finish(0)
         dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(args.e2e_steps):
             e2e_step(k)
-        e2e_drain()
+        e2e_finish(args.e2e_steps - 1)
         torch.cuda.synchronize()
         e2e_s = dist.max(time.perf_counter() - t0)
-        last = host_out[(args.e2e_steps - 1) % 2]
+        last = out_pin[(args.e2e_steps - 1) % 2].numpy().view(np.uint32)
         e2e = {"value": ws * E * args.e2e_steps / e2e_s, "unit": "edges/s",
                "h2d_bytes_per_step": int(E * 16), "d2h_bytes_per_step": int(E * Pn * 4),
                "steps": args.e2e_steps, "ms_per_step": 1000.0 * e2e_s / args.e2e_steps,
                "matches_device_output": bool(np.array_equal(
                    last, out.cpu().numpy().view(np.uint32))),
-               "includes": "graph build from pinned host arrays, mine, copy-back of counts; "
-                           "two streams, step k's copy back overlapping step k+1"}
+               "includes": "pinned host inputs -> device, graph build, mine, counts -> pinned "
+                           "host memory; two streams, upload(k) then copy back(k-1) while "
+                           "step k builds and mines"}
 
     line = None
     if rank == 0:

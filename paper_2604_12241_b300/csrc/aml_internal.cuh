@@ -186,6 +186,19 @@ void radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t
                     int64_t n, int nbits, cudaStream_t s);
 
 void iota_i32(int32_t* out, int64_t n, cudaStream_t s);
+// device-to-device copy by a kernel (no copy engine; see prims.cu)
+void copy_d2d(void* dst, const void* src, size_t bytes, cudaStream_t s);
+// a few small device -> host reads, then waits for `s` (and only `s`): a
+// kernel stores the bytes into mapped host memory, so the reads never queue
+// behind bulk transfers of other streams on the copy engines
+constexpr int SMALL_READ_MAX = 8;
+constexpr uint32_t SMALL_READ_BYTES = 512;
+struct SmallRead {
+  void* host;
+  const void* dev;
+  uint32_t bytes;
+};
+void read_small(const SmallRead* r, int n, cudaStream_t s);
 
 // Multiprocessors of the current device (cached per device).
 int sm_count();

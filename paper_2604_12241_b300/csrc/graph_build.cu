@@ -138,7 +138,7 @@ static void build_rows(aml_graph* g, Adj& a, const int32_t* row_of, const int32_
                        cudaStream_t s, GraphAlloc& ga, uint32_t* perm, int32_t* max_deg_dev) {
   DBuf<uint32_t> keys(E, s), ktmp(E, s), vtmp(E, s);
   const int B = 256;
-  AML_CUDA(cudaMemcpyAsync(perm, time_perm, E * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  copy_d2d(perm, time_perm, E * sizeof(uint32_t), s);
   AML_LAUNCH("k_row_keys", s,
              k_row_keys<<<grid_for(E, B), B, 0, s>>>(perm, row_of, other, E, N, keys.p));
   radix_sort_u32(keys.p, perm, ktmp.p, vtmp.p, E, nbits, s);
@@ -206,13 +206,16 @@ aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts
     g->ts = ga.get<int32_t>(E);
     g->amount = ga.get<float>(E);
     g->err = ga.get<uint32_t>(4);
-    cudaMemcpyKind kind = (flags & AML_PTR_DEVICE) ? cudaMemcpyDeviceToDevice
-                                                   : cudaMemcpyHostToDevice;
     if (E) {
-      AML_CUDA(cudaMemcpyAsync(g->src, src, E * 4, kind, s));
-      AML_CUDA(cudaMemcpyAsync(g->dst, dst, E * 4, kind, s));
-      AML_CUDA(cudaMemcpyAsync(g->ts, ts, E * 4, kind, s));
-      if (amount) AML_CUDA(cudaMemcpyAsync(g->amount, amount, E * 4, kind, s));
+      // device inputs are copied by a kernel, host inputs by the copy engine
+      auto in = [&](void* to, const void* from) {
+        if (flags & AML_PTR_DEVICE) copy_d2d(to, from, E * 4, s);
+        else AML_CUDA(cudaMemcpyAsync(to, from, E * 4, cudaMemcpyHostToDevice, s));
+      };
+      in(g->src, src);
+      in(g->dst, dst);
+      in(g->ts, ts);
+      if (amount) in(g->amount, amount);
       else AML_CUDA(cudaMemsetAsync(g->amount, 0, E * 4, s));
     }
     AML_CUDA(cudaMemsetAsync(g->err, 0, 16, s));
@@ -227,9 +230,8 @@ aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts
     }
     uint32_t err = 0;
     unsigned long long hs[4];
-    AML_CUDA(cudaMemcpyAsync(&err, g->err, 4, cudaMemcpyDeviceToHost, s));
-    AML_CUDA(cudaMemcpyAsync(hs, scal.p, 32, cudaMemcpyDeviceToHost, s));
-    AML_CUDA(cudaStreamSynchronize(s));
+    const SmallRead rd[2] = {{&err, g->err, 4}, {hs, scal.p, 32}};
+    read_small(rd, 2, s);
     AML_REQUIRE(!(err & ERR_BAD_ID), AML_EINVAL, "a node id is outside [0, n_nodes)");
     AML_REQUIRE(!((flags & AML_ASSUME_SORTED) && (err & ERR_UNSORTED)), AML_EUNSORTED,
                 "AML_ASSUME_SORTED given but timestamps decrease");

@@ -287,11 +287,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     if (lc.n_legs < 0 || (level_cycles && lc.n_front[2] < 0)) {
       // one wait for both sizes
       int64_t total[2] = {0, 0};
-      AML_CUDA(cudaMemcpyAsync(&total[0], off + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-      if (level_cycles)
-        AML_CUDA(cudaMemcpyAsync(&total[1], off2.p + E, sizeof(int64_t),
-                                 cudaMemcpyDeviceToHost, s));
-      AML_CUDA(cudaStreamSynchronize(s));
+      const SmallRead rd[2] = {{&total[0], off + E, 8}, {&total[1], off2.p + E, 8}};
+      read_small(rd, level_cycles ? 2 : 1, s);
       AML_REQUIRE(total[0] < (int64_t)UINT32_MAX, AML_EUNSUPPORTED,
                   "more than 2^32 temporal 2-paths in one window");
       lc.n_legs = total[0];
@@ -351,8 +348,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     int64_t n_sg = nl;  // records to bucket
     if (sg_filter) {
       unsigned long long kept = 0;
-      AML_CUDA(cudaMemcpyAsync(&kept, n_rec.p, 8, cudaMemcpyDeviceToHost, s));
-      AML_CUDA(cudaStreamSynchronize(s));
+      const SmallRead rd{&kept, n_rec.p, 8};
+      read_small(&rd, 1, s);
       n_sg = (int64_t)kept;
       if (n_sg > 1) {
         size_buckets(n_sg);
@@ -406,8 +403,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
         scan_i32_to_i64(cnt.p, foff.p, n + 1, s);
         int64_t& nn = lc.n_front[j + 1];
         if (nn < 0) {
-          AML_CUDA(cudaMemcpyAsync(&nn, foff.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-          AML_CUDA(cudaStreamSynchronize(s));
+          const SmallRead rd{&nn, foff.p + n, 8};
+          read_small(&rd, 1, s);
           AML_REQUIRE(nn < (int64_t)INT32_MAX, AML_EUNSUPPORTED, "cycle frontier too large");
         }
         front.emplace_back((size_t)nn, s);

@@ -1,5 +1,6 @@
 // Device primitives: stream-ordered scratch, prefix sums, stable radix sort.
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <set>
 
@@ -34,6 +35,82 @@ void* dalloc(size_t bytes, cudaStream_t s) {
 
 void dfree(void* p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
+}
+
+// ------------------------------------------- copies without the copy engines
+//
+// The copy engines run transfers one after another, so a cudaMemcpy issued
+// on one stream waits behind any bulk transfer another stream has in flight
+// (the previous batch's counts on their way back to the host, say).  The
+// device-to-device copies of graph building and the few-byte reads the host
+// waits for are therefore done by kernels, which do not queue there.
+
+template <typename T>
+__global__ void k_copy(const T* __restrict__ src, T* __restrict__ dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+void copy_d2d(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return;
+  const uintptr_t align = (uintptr_t)dst | (uintptr_t)src | (uintptr_t)bytes;
+  const unsigned grid = (unsigned)std::min<int64_t>(4 * (int64_t)sm_count(),
+                                                    ((int64_t)bytes / 16 + 255) / 256 + 1);
+  if (align % 16 == 0) {
+    AML_LAUNCH("k_copy", s, k_copy<int4><<<grid, 256, 0, s>>>(
+                                static_cast<const int4*>(src), static_cast<int4*>(dst),
+                                (int64_t)(bytes / 16)));
+  } else if (align % 4 == 0) {
+    AML_LAUNCH("k_copy", s, k_copy<int32_t><<<grid, 256, 0, s>>>(
+                                static_cast<const int32_t*>(src), static_cast<int32_t*>(dst),
+                                (int64_t)(bytes / 4)));
+  } else {
+    AML_LAUNCH("k_copy", s, k_copy<unsigned char><<<grid, 256, 0, s>>>(
+                                static_cast<const unsigned char*>(src),
+                                static_cast<unsigned char*>(dst), (int64_t)bytes));
+  }
+}
+
+struct SmallReadArgs {
+  const unsigned char* src[SMALL_READ_MAX];
+  uint32_t off[SMALL_READ_MAX];
+  uint32_t bytes[SMALL_READ_MAX];
+  unsigned char* out;  // device view of mapped host memory
+};
+
+__global__ void k_read_small(SmallReadArgs a) {
+  const int i = blockIdx.x;
+  for (uint32_t b = threadIdx.x; b < a.bytes[i]; b += blockDim.x)
+    a.out[a.off[i] + b] = a.src[i][b];
+}
+
+void read_small(const SmallRead* r, int n, cudaStream_t s) {
+  AML_REQUIRE(n >= 1 && n <= SMALL_READ_MAX, AML_EINTERNAL, "read_small: bad count");
+  // one mapped (zero-copy) host buffer per host thread, kept for the process
+  thread_local unsigned char* host = nullptr;
+  thread_local unsigned char* dev = nullptr;
+  if (!host) {
+    void* h = nullptr;
+    AML_CUDA(cudaHostAlloc(&h, SMALL_READ_BYTES, cudaHostAllocMapped | cudaHostAllocPortable));
+    void* d = nullptr;
+    AML_CUDA(cudaHostGetDevicePointer(&d, h, 0));
+    host = static_cast<unsigned char*>(h);
+    dev = static_cast<unsigned char*>(d);
+  }
+  SmallReadArgs a;
+  uint32_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    a.src[i] = static_cast<const unsigned char*>(r[i].dev);
+    a.off[i] = off;
+    a.bytes[i] = r[i].bytes;
+    off += (r[i].bytes + 15u) & ~15u;
+  }
+  AML_REQUIRE(off <= SMALL_READ_BYTES, AML_EINTERNAL, "read_small: too many bytes");
+  a.out = dev;
+  AML_LAUNCH("k_read_small", s, k_read_small<<<n, 32, 0, s>>>(a));
+  AML_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < n; ++i) std::memcpy(r[i].host, host + a.off[i], r[i].bytes);
 }
 
 // ------------------------------------------------------------------ iota
@@ -370,8 +447,8 @@ void radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t
     std::swap(va, vb);
   }
   if (ka != keys) {
-    AML_CUDA(cudaMemcpyAsync(keys, ka, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-    AML_CUDA(cudaMemcpyAsync(vals, va, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    copy_d2d(keys, ka, (size_t)n * sizeof(uint32_t), s);
+    copy_d2d(vals, va, (size_t)n * sizeof(uint32_t), s);
   }
 }
 
