@@ -37,6 +37,13 @@ WORKLOAD_TEXT = {
                  "DEG_OUT, DEG_IN, FAN_OUT, FAN_IN, GS, SG, CYC2..CYC5 at 24h and at 7d"),
     "tiny-10k": ("tiny-10k: 10,000 accounts, 100,000 transactions over 10 days, Zipf(1.2); "
                  "10 columns at 24h"),
+    "hi-medium": ("hi-medium: 2,032,095 accounts, 31,898,238 transactions over 16 days, "
+                  "out/in-degree Zipf(1.05) capped at 1e5, 0.1% edges in planted motifs; "
+                  "20 columns: DEG_OUT, DEG_IN, FAN_OUT, FAN_IN, GS, SG, CYC2..CYC5 at 24h "
+                  "and at 7d"),
+    "hi-large": ("hi-large: 2,070,980 accounts, 179,702,229 transactions over 90 days, "
+                 "Zipf(1.2) capped at 1e5, 0.05% edges in planted motifs; 10 columns: "
+                 "FAN_OUT, FAN_IN, GS, SG, CYC3..CYC6 at 24h, FAN_OUT, FAN_IN at 7d"),
 }
 
 

@@ -561,10 +561,132 @@ struct SgSmem {
   unsigned long long key[TAB];   // filed keys; later (as uint32) group cursors
   uint32_t cnt[TAB];             // records per slot
   uint32_t n_grouped;
+  uint32_t n_big;                // groups counted by sorting (sg_sorted_group)
+  uint32_t n_valid;              // legs within the window being counted there
+  uint32_t big_start[CAP / 64], big_n[CAP / 64];
 };
 
-template <int CAP, int TAB, int NS, int BS>
-__device__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRec* __restrict__ R, int n,
+// Groups of more than SG_SORT_MIN legs are counted by sorting instead of
+// comparing every pair (overflow buckets, full mines)
+constexpr uint32_t SG_SORT_MIN = 64;
+
+// ascending bitonic sort of a[0, n) and, independently, b[0, n) (n a power
+// of two), by the whole block; one barrier per stage for both
+template <typename T>
+__device__ __forceinline__ void bitonic_sort2(T* a, T* b, uint32_t n) {
+  for (uint32_t k = 2; k <= n; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const T x = a[i], y = a[l];
+          if ((x > y) == up) {
+            a[i] = y;
+            a[l] = x;
+          }
+          const T u = b[i], v = b[l];
+          if ((u > v) == up) {
+            b[i] = v;
+            b[l] = u;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// first i in [lo, hi) with a[i] >= x (upper: a[i] > x)
+template <typename T, typename K>
+__device__ __forceinline__ uint32_t bound_in(const T* a, uint32_t lo, uint32_t hi, K x,
+                                             bool upper) {
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    const K v = (K)a[mid];
+    if (v < x || (upper && v == x)) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// an int32 time as an unsigned key of the same order
+__device__ __forceinline__ unsigned long long tkey(long long t) {
+  return (unsigned long long)((uint32_t)(int32_t)t ^ 0x80000000u);
+}
+
+// Partners of every leg of one (s, d) group of c legs, grp[start, start + c),
+// without comparing all pairs.  For a window dw and the legs U whose own
+// span is within dw, a leg i of U has span(i, j) <= dw with exactly the legs
+// j of U that start at or after tb_i - dw, except those that end after
+// ta_i + dw (every such leg starts after ta_i, so it was among the former):
+// two counts in U's start and end times, sorted.  The legs of U through i's
+// own intermediary (i included) are counted the same way in U's (m, start)
+// and (m, end) keys, sorted, and subtracted.  Full mines only (no delta
+// counting).
+template <int CAP, int TAB, int NS>
+__device__ __forceinline__ void sg_sorted_group(SgSmem<CAP, TAB>& S, uint32_t start, uint32_t c,
+                                                int32_t delta,
+                                                unsigned long long* __restrict__ acc,
+                                                const SubWindows& sub) {
+  static_assert(TAB >= 2 * CAP, "the sort buffers live in the hash table's space");
+  int32_t* sa = reinterpret_cast<int32_t*>(S.key);  // start times of U
+  int32_t* sb = sa + CAP;                            // end times of U
+  unsigned long long* ka = S.key + CAP;               // (m, start) of U, then ~0
+  unsigned long long* kb = reinterpret_cast<unsigned long long*>(S.cnt);  // (m, end)
+  const int4* grp = S.grp + start;
+  uint32_t p2 = 1;
+  while (p2 < c) p2 <<= 1;
+  constexpr int NT = 1 + NS;
+#pragma unroll
+  for (int w = 0; w < NT; ++w) {
+    if (w > 0 && w - 1 >= sub.n) break;
+    unsigned long long* col = w == 0 ? acc : sub.sg[w - 1];
+    if (!col) continue;
+    const long long dw = w == 0 ? delta : sub.delta[w - 1];
+    if (threadIdx.x == 0) S.n_valid = 0;
+    __syncthreads();
+    uint32_t mine = 0;
+    for (uint32_t k = threadIdx.x; k < p2; k += blockDim.x) {
+      const int4 r = k < c ? grp[k] : make_int4(0, 0, 0, 0);
+      const bool in = k < c && (long long)r.z - r.y <= dw;
+      const unsigned long long m = (unsigned long long)(uint32_t)r.x << 32;
+      sa[k] = in ? r.y : INT32_MAX;
+      sb[k] = in ? r.z : INT32_MAX;
+      ka[k] = in ? m | tkey(r.y) : ~0ull;
+      kb[k] = in ? m | tkey(r.z) : ~0ull;
+      mine += in ? 1u : 0u;
+    }
+    if (mine) atomicAdd(&S.n_valid, mine);
+    __syncthreads();
+    bitonic_sort2(sa, sb, p2);
+    bitonic_sort2(ka, kb, p2);
+    const uint32_t nw = S.n_valid;  // |U|: the first nw entries of every array
+    for (uint32_t k = threadIdx.x; k < c; k += blockDim.x) {
+      const int4 r = grp[k];
+      if ((long long)r.z - r.y > dw) continue;
+      const long long x = (long long)r.z - dw, y = (long long)r.y + dw;
+      // legs of U with start >= x, minus those with end > y
+      const uint32_t all = (nw - bound_in<int32_t, long long>(sa, 0, nw, x, false)) -
+                           (nw - bound_in<int32_t, long long>(sb, 0, nw, y, true));
+      // the same within i's intermediary's run of the (m, time) keys
+      const unsigned long long m = (unsigned long long)(uint32_t)r.x << 32;
+      const uint32_t a0 = bound_in(ka, 0, nw, m, false);
+      const uint32_t a1 = bound_in(ka, a0, nw, m + (1ull << 32), false);
+      const uint32_t b0 = bound_in(kb, 0, nw, m, false);
+      const uint32_t b1 = bound_in(kb, b0, nw, m + (1ull << 32), false);
+      const uint32_t ge = x <= INT32_MIN ? a1 - a0
+                        : x > INT32_MAX  ? 0u
+                                         : a1 - bound_in(ka, a0, a1, m | tkey(x), false);
+      const uint32_t gt = y >= INT32_MAX ? 0u
+                        : y < INT32_MIN  ? b1 - b0
+                                         : b1 - bound_in(kb, b0, b1, m | tkey(y), true);
+      sg_credit(col, S.ga[start + k], r.w, (unsigned long long)(all - (ge - gt)));
+    }
+    __syncthreads();  // the next window rewrites the buffers
+  }
+}
+
+template <int CAP, int TAB, int NS, int BS, bool SORT_BIG = false>
+__device__ __forceinline__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRec* __restrict__ R, int n,
                                 int32_t delta, const int32_t* __restrict__ dst,
                                 const int32_t* __restrict__ ts,
                                 unsigned long long* __restrict__ acc, int32_t new_from,
@@ -584,7 +706,10 @@ __device__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRec* __restrict__ 
     S.key[t] = ~0ull;
     S.cnt[t] = 0;
   }
-  if (threadIdx.x == 0) S.n_grouped = 0;
+  if (threadIdx.x == 0) {
+    S.n_grouped = 0;
+    S.n_big = 0;
+  }
   __syncthreads();
   // file every record under its key; remember which keys this thread filed
   uint32_t lead = 0;
@@ -635,12 +760,26 @@ __device__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRec* __restrict__ 
     }
   }
   __syncthreads();
+  const bool sort_big = SORT_BIG && new_from == 0;
   for (uint32_t p = threadIdx.x; p < n_grouped; p += BS) {
     const uint32_t q = S.gslot[p];
     const uint32_t c = S.cnt[q];
     const uint32_t end = cur[q];
+    if (sort_big && c > SG_SORT_MIN) {  // listed by its first entry, counted below
+      if (p == end - c) {
+        const uint32_t k = atomicAdd(&S.n_big, 1u);
+        S.big_start[k] = end - c;
+        S.big_n[k] = c;
+      }
+      continue;
+    }
     sg_count_partners<NS>(S.grp, end - c, end, S.grp[p], S.ga[p], delta, new_from, acc, sub);
   }
+  if (!sort_big) return;
+  __syncthreads();  // the table's space becomes the sort buffers
+  const uint32_t n_big = S.n_big;
+  for (uint32_t k = 0; k < n_big; ++k)
+    sg_sorted_group<CAP, TAB, NS>(S, S.big_start[k], S.big_n[k], delta, acc, sub);
 }
 
 // One block per bucket of up to SG_CAP records; larger buckets are listed
@@ -669,7 +808,7 @@ __global__ void __launch_bounds__(SG_BLOCK, 8) k_sg_bucket(const LegRec* __restr
 // The listed buckets, a few blocks looping over the list (the count is read
 // on the device); buckets beyond SG_CAP_BIG compare every record with all.
 template <int NS>
-__global__ void __launch_bounds__(256) k_sg_bucket_big(const LegRec* __restrict__ rec,
+__global__ void __launch_bounds__(SG_BIG_BLOCK, 1) k_sg_bucket_big(const LegRec* __restrict__ rec,
                                                        const uint32_t* __restrict__ bend,
                                                        int32_t delta,
                                                        const int32_t* __restrict__ dst,
@@ -687,8 +826,8 @@ __global__ void __launch_bounds__(256) k_sg_bucket_big(const LegRec* __restrict_
     const int64_t n = (int64_t)bend[b] - base;
     const LegRec* R = rec + base;
     if (n <= SG_CAP_BIG) {
-      sg_group_bucket<SG_CAP_BIG, SG_TAB_BIG, NS, 256>(S, R, (int)n, delta, dst, ts, acc, new_from,
-                                              sub);
+      sg_group_bucket<SG_CAP_BIG, SG_TAB_BIG, NS, SG_BIG_BLOCK, true>(S, R, (int)n, delta, dst,
+                                                                      ts, acc, new_from, sub);
     } else {
       for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         const LegRec r = R[i];
@@ -1032,7 +1171,7 @@ void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
                k_sg_bucket<NS><<<n_buckets, SG_BLOCK, 0, s>>>(rec, bend, delta, dst, ts, acc,
                                                          new_from, overflow, sub));
     AML_LAUNCH("k_sg_bucket_big", s,
-               k_sg_bucket_big<NS><<<(unsigned)sm_count(), 256, big, s>>>(
+               k_sg_bucket_big<NS><<<(unsigned)sm_count(), SG_BIG_BLOCK, big, s>>>(
                    rec, bend, delta, dst, ts, acc, new_from, overflow, sub));
   });
 }

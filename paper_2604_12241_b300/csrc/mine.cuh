@@ -13,6 +13,7 @@ constexpr int SG_TAB = 1024;       // its hash-table slots (load <= 0.5)
 constexpr int SG_BLOCK = 256;      // threads of that block
 constexpr int SG_CAP_BIG = 4096;   // the same for the larger buckets (k_sg_bucket_big)
 constexpr int SG_TAB_BIG = 8192;
+constexpr int SG_BIG_BLOCK = 1024;  // threads of that block (one block per SM)
 constexpr int SG_PART_ITEMS = 4;     // records per thread in k_sg_partition
 constexpr int ASM_BLOCK = 128;       // rows per k_assemble block
 
