@@ -21,7 +21,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "aml_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-KINDS = {"deg_out": 0, "deg_in": 1, "fan_out": 2, "fan_in": 3, "gs": 4, "sg": 5, "cyc": 6}
+KINDS = {"deg_out": 0, "deg_in": 1, "fan_out": 2, "fan_in": 3, "gs": 4, "sg": 5, "cyc": 6,
+         "cycw": 7}
 
 
 class _Col(ctypes.Structure):
@@ -70,8 +71,8 @@ def _load():
 def _cols(cols: Sequence[Tuple]) -> ctypes.Array:
     arr = (_Col * len(cols))()
     for i, c in enumerate(cols):
-        if c[0] == "cyc":
-            arr[i].kind, arr[i].k, arr[i].delta = KINDS["cyc"], int(c[1]), int(c[2])
+        if c[0] in ("cyc", "cycw"):
+            arr[i].kind, arr[i].k, arr[i].delta = KINDS[c[0]], int(c[1]), int(c[2])
         else:
             arr[i].kind, arr[i].k, arr[i].delta = KINDS[c[0]], 0, int(c[1])
     return arr

@@ -265,10 +265,13 @@ static void canon_sg(const og_graph* g, int col, int ncols, int64_t delta, uint6
 
 /* CYC: depth-first from each edge taken as the cycle's earliest edge e1 =
  * u0->u1; each hop goes to a later edge inside t(e1)+delta and to a node not
- * yet on the path; an edge back into u0 closes a cycle of length depth+1. */
+ * yet on the path; an edge back into u0 closes a cycle of length depth+1.
+ * CYCW (window cycles, any time order): the same walk, but each hop only has
+ * to come after e1 (the cycle's earliest edge), not after the previous hop. */
 typedef struct {
   const og_graph* g;
   int K;
+  int window; /* CYCW: hops after e1 instead of after the previous hop */
   const int* colmap; /* colmap[k] = column of CYC_k for this delta, or -1 */
   int ncols;
   uint64_t* acc;
@@ -283,8 +286,8 @@ static void cyc_dfs(cyc_ctx* c, int depth) {
   uint64_t* acc = c->acc;
   int32_t w = c->nodes[depth];
   int64_t end = g->out_start[w + 1];
-  for (int64_t i = first_after(g, g->out_list, g->out_start[w], end, c->edges[depth - 1]);
-       i < end; ++i) {
+  int64_t after = c->window ? c->edges[0] : c->edges[depth - 1];
+  for (int64_t i = first_after(g, g->out_list, g->out_start[w], end, after); i < end; ++i) {
     int64_t f = g->out_list[i];
     if ((int64_t)g->ts[f] > c->tmax) break;
     int32_t x = g->dst[f];
@@ -307,13 +310,14 @@ static void cyc_dfs(cyc_ctx* c, int depth) {
 }
 
 static void canon_cyc(const og_graph* g, int K, const int* colmap, int ncols, int64_t delta,
-                      uint64_t* acc, int nth) {
+                      uint64_t* acc, int nth, int window) {
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nth)
   for (int64_t e1 = 0; e1 < g->E; ++e1) {
     if (g->pos_out[e1] < 0) continue;
     cyc_ctx c;
     c.g = g;
     c.K = K;
+    c.window = window;
     c.colmap = colmap;
     c.ncols = ncols;
     c.acc = acc;
@@ -327,9 +331,10 @@ static void canon_cyc(const og_graph* g, int K, const int* colmap, int ncols, in
 
 static int check_cols(const og_col* cols, int32_t ncols) {
   for (int i = 0; i < ncols; ++i) {
-    if (cols[i].kind < OG_DEG_OUT || cols[i].kind > OG_CYC) return -1;
+    if (cols[i].kind < OG_DEG_OUT || cols[i].kind > OG_CYCW) return -1;
     if (cols[i].delta < 0) return -1;
-    if (cols[i].kind == OG_CYC && (cols[i].k < 2 || cols[i].k > 15)) return -1;
+    if ((cols[i].kind == OG_CYC || cols[i].kind == OG_CYCW) && (cols[i].k < 2 || cols[i].k > 15))
+      return -1;
   }
   return 0;
 }
@@ -367,13 +372,13 @@ int og_count_all(const og_graph* g, const og_col* cols, int32_t ncols, uint32_t*
       canon_gs(g, c, ncols, delta, acc, nth);
     } else if (kind == OG_SG) {
       canon_sg(g, c, ncols, delta, acc, nth);
-    } else if (kind == OG_CYC && !done[c]) {
+    } else if ((kind == OG_CYC || kind == OG_CYCW) && !done[c]) {
       /* one depth-first search serves every cycle length with this delta */
       int colmap[17];
       for (int k = 0; k < 17; ++k) colmap[k] = -1;
       int K = 0;
       for (int c2 = c; c2 < ncols; ++c2) {
-        if (cols[c2].kind == OG_CYC && cols[c2].delta == delta && !done[c2]) {
+        if (cols[c2].kind == kind && cols[c2].delta == delta && !done[c2]) {
           if (colmap[cols[c2].k] < 0) {
             colmap[cols[c2].k] = c2;
             done[c2] = 1;
@@ -381,10 +386,10 @@ int og_count_all(const og_graph* g, const og_col* cols, int32_t ncols, uint32_t*
           }
         }
       }
-      canon_cyc(g, K, colmap, ncols, delta, acc, nth);
+      canon_cyc(g, K, colmap, ncols, delta, acc, nth, kind == OG_CYCW);
       /* duplicate columns (same k and delta) copy the first one */
       for (int c2 = c; c2 < ncols; ++c2)
-        if (cols[c2].kind == OG_CYC && cols[c2].delta == delta && !done[c2]) {
+        if (cols[c2].kind == kind && cols[c2].delta == delta && !done[c2]) {
           int src_c = colmap[cols[c2].k];
           for (int64_t e = 0; e < g->E; ++e) ACC(e, c2) = ACC(e, src_c);
           done[c2] = 1;
@@ -478,10 +483,11 @@ static uint64_t ec_sg(const og_graph* g, int64_t e, int64_t delta) {
 /* cycles through e = x->y: simple paths y -> ... -> x of k-1 edges inside
  * [t_e - delta, t_e + delta]; a closed walk is a temporal cycle iff its edge
  * sequence, read cyclically, has exactly one descent under <, and it spans
- * at most delta */
+ * at most delta (a window cycle: the span alone) */
 typedef struct {
   const og_graph* g;
   int k;
+  int window;
   int64_t delta, tlo, thi;
   int64_t edges[16];
   int32_t nodes[17];
@@ -504,10 +510,10 @@ static void ec_cyc_dfs(ec_cyc_ctx* c, int depth, int64_t mint, int64_t maxt, int
     if (depth + 1 == c->k) {
       if (z != x) continue;
       nd += prec(g, c->edges[0], f);
-      if (nd == 1) c->cnt++;
+      if (nd == 1 || c->window) c->cnt++;
       continue;
     }
-    if (z == x || nd > 1) continue;
+    if (z == x || (nd > 1 && !c->window)) continue;
     int seen = 0;
     for (int j = 1; j <= depth; ++j) seen |= (c->nodes[j] == z);
     if (seen) continue;
@@ -517,10 +523,11 @@ static void ec_cyc_dfs(ec_cyc_ctx* c, int depth, int64_t mint, int64_t maxt, int
   }
 }
 
-static uint64_t ec_cyc(const og_graph* g, int64_t e, int k, int64_t delta) {
+static uint64_t ec_cyc(const og_graph* g, int64_t e, int k, int64_t delta, int window) {
   ec_cyc_ctx c;
   c.g = g;
   c.k = k;
+  c.window = window;
   c.delta = delta;
   c.tlo = (int64_t)g->ts[e] - delta;
   c.thi = (int64_t)g->ts[e] + delta;
@@ -557,7 +564,8 @@ int og_count_edges(const og_graph* g, const og_col* cols, int32_t ncols, const i
             case OG_FAN_IN: v = fan_stamp(g, e, 0, delta, stamp, ++qid); break;
             case OG_GS: v = ec_gs(g, e, delta); break;
             case OG_SG: v = ec_sg(g, e, delta); break;
-            case OG_CYC: v = ec_cyc(g, e, cols[c].k, delta); break;
+            case OG_CYC: v = ec_cyc(g, e, cols[c].k, delta, 0); break;
+            case OG_CYCW: v = ec_cyc(g, e, cols[c].k, delta, 1); break;
           }
         }
         out[(size_t)i * (size_t)ncols + (size_t)c] = v > 0xffffffffull ? 0xffffffffu : (uint32_t)v;

@@ -15,6 +15,9 @@
  *                 scatter < gather inside each leg, span of the 4 edges <= delta, e among them}
  *   CYC_k(e)    #{k-edge simple directed cycles, <-increasing cyclically from their
  *                 <-minimum edge, span <= delta, containing e}
+ *   CYCW_k(e)   #{k-edge simple directed cycles with span <= delta, their edges in
+ *                 any time order, containing e} (Sec. 4: cycles whose edges are not
+ *                 observed in cycle order, "anticipatory" edges; window constraint only)
  * Parity with an external reference implementation: unpinned (none exists);
  * every function below is pinned by the brute-force, exact-variant,
  * planted-motif and invariant tests instead.
@@ -33,12 +36,13 @@ enum {
   OG_FAN_IN = 3,
   OG_GS = 4,
   OG_SG = 5,
-  OG_CYC = 6
+  OG_CYC = 6,
+  OG_CYCW = 7
 };
 
 typedef struct og_col {
   int32_t kind;   /* OG_* */
-  int32_t k;      /* cycle length for OG_CYC, else ignored */
+  int32_t k;      /* cycle length for OG_CYC / OG_CYCW, else ignored */
   int64_t delta;  /* window in seconds, >= 0 */
 } og_col;
 

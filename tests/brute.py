@@ -25,7 +25,7 @@ def brute_counts(src, dst, ts, cols: Sequence[Tuple]) -> np.ndarray:
     out = np.zeros((E, len(cols)), dtype=np.uint64)
     for c, col in enumerate(cols):
         kind = col[0]
-        if kind == "cyc":
+        if kind in ("cyc", "cycw"):
             k, delta = int(col[1]), int(col[2])
         else:
             delta = int(col[1])
@@ -72,6 +72,32 @@ def brute_counts(src, dst, ts, cols: Sequence[Tuple]) -> np.ndarray:
                 ok = all(dst[seq[i]] == src[seq[(i + 1) % k]] for i in range(k))
                 ok = ok and len({src[f] for f in seq}) == k
                 ok = ok and ts[seq[-1]] - ts[seq[0]] <= delta
+                if ok:
+                    for e in sub:
+                        out[e, c] += 1
+        elif kind == "cycw":
+            # any k edges that chain into one simple directed cycle (distinct
+            # sources, each edge's head the source of another, one orbit),
+            # whatever their time order, spanning at most delta
+            for sub in itertools.combinations(valid, k):
+                by_src = {src[f]: f for f in sub}
+                if len(by_src) != k:
+                    continue
+                cur, seen = sub[0], 0
+                for _ in range(k):
+                    if dst[cur] not in by_src:
+                        break
+                    cur = by_src[dst[cur]]
+                    seen += 1
+                orbit = {sub[0]}
+                f = sub[0]
+                for _ in range(k - 1):
+                    if dst[f] not in by_src:
+                        break
+                    f = by_src[dst[f]]
+                    orbit.add(f)
+                ok = seen == k and cur == sub[0] and len(orbit) == k
+                ok = ok and max(ts[f] for f in sub) - min(ts[f] for f in sub) <= delta
                 if ok:
                     for e in sub:
                         out[e, c] += 1

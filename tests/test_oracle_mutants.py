@@ -1,7 +1,7 @@
 """The oracle's pins catch plausible mistakes.
 
 Each case below plants one mistake (a dropped term, a flipped comparison, an
-off-by-one index, a wrong operand) in a temporary copy of the oracle's C
+off-by-one index, a wrong operand, an ordered hop in a window cycle) in a temporary copy of the oracle's C
 source, compiles it on the CPU, and checks that the brute-force pins reject
 the mutant.  The oracle under oracle/ is never modified.
 """
@@ -38,11 +38,16 @@ MUTANTS = [
      "for (int j = 1; j < depth; ++j) add("),
     ("cyc-not-simple", "for (int j = 1; j <= depth; ++j) seen |= (c->nodes[j] == x);",
      "for (int j = 2; j <= depth; ++j) seen |= (c->nodes[j] == x);"),
-    ("ec-cyc-descents", "if (nd == 1) c->cnt++;", "if (nd <= 2) c->cnt++;"),
+    ("ec-cyc-descents", "if (nd == 1 || c->window) c->cnt++;", "if (nd <= 2 || c->window) c->cnt++;"),
+    ("cycw-after-previous-hop", "int64_t after = c->window ? c->edges[0] : c->edges[depth - 1];",
+     "int64_t after = c->edges[depth - 1];"),
+    ("ec-cycw-prunes-descents", "if (z == x || (nd > 1 && !c->window)) continue;",
+     "if (z == x || nd > 1) continue;"),
 ]
 
 COLS = [("deg_out", 5), ("deg_in", 5), ("fan_out", 5), ("fan_in", 5), ("gs", 5), ("sg", 6),
-        ("sg", 100), ("cyc", 2, 6), ("cyc", 3, 6), ("cyc", 4, 8), ("cyc", 5, 9)]
+        ("sg", 100), ("cyc", 2, 6), ("cyc", 3, 6), ("cyc", 4, 8), ("cyc", 5, 9),
+        ("cycw", 3, 6), ("cycw", 4, 8)]
 
 
 def _pins_reject(lib) -> bool:

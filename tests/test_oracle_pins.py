@@ -6,7 +6,9 @@
   number of admissible variants matches Sec. 4's 6! = 720 orders for a
   3-intermediary scatter-gather (tests/golden/sg_orders.txt);
 * a static k-cycle under all k! timestamp permutations is a temporal cycle
-  for exactly k of them;
+  for exactly k of them, and a window cycle (any time order, Sec. 4's
+  anticipatory edges) for all of them while its span fits the window;
+* a window cycle count is never below the ordered one, and equal for k = 2;
 * planted motifs on reserved accounts have closed-form counts;
 * invariants (k | sum CYC_k, 4 | sum SG, FAN <= DEG, ...);
 * DEG and FAN recomputed with numpy searchsorted / unique.
@@ -27,7 +29,8 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 ALL_SMALL = [("deg_out", 5), ("deg_in", 5), ("fan_out", 5), ("fan_in", 5),
              ("deg_out", 0), ("fan_in", 2), ("gs", 5), ("gs", 0), ("sg", 6), ("sg", 100),
-             ("cyc", 2, 6), ("cyc", 3, 6), ("cyc", 4, 8), ("cyc", 5, 9), ("cyc", 3, 1000)]
+             ("cyc", 2, 6), ("cyc", 3, 6), ("cyc", 4, 8), ("cyc", 5, 9), ("cyc", 3, 1000),
+             ("cycw", 3, 6), ("cycw", 4, 8), ("cycw", 5, 9), ("cycw", 3, 1000)]
 
 
 def _cols_10(delta):
@@ -106,6 +109,33 @@ def test_static_cycle_under_all_time_permutations(k):
     assert hits == k
 
 
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_static_window_cycle_under_all_time_permutations(k):
+    """A window cycle ignores the order of its edges: every one of the k!
+    timestamp assignments counts once on each edge, until the span exceeds
+    the window."""
+    src = np.arange(k, dtype=np.int32)
+    dst = ((np.arange(k) + 1) % k).astype(np.int32)
+    for perm in itertools.permutations(range(k)):
+        ts = np.asarray(perm, dtype=np.int32) * 10
+        og = oracle.OracleGraph(src, dst, ts, k)
+        got = og.count_all([("cycw", j, 1000) for j in range(2, 6)])
+        assert (got[:, k - 2] == 1).all()
+        assert not np.delete(got, k - 2, axis=1).any()
+        assert not og.count_all([("cycw", k, 10 * (k - 1) - 1)]).any()
+
+
+def test_window_cycles_bound_ordered_cycles():
+    for seed in range(60):
+        g = aml_synth.tiny_random(4 + seed % 5, 30 + seed % 20, 12, 500 + seed)
+        og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
+        for d in (0, 5, 100):
+            got = og.count_all([("cyc", 2, d), ("cycw", 2, d)] +
+                               [(kind, k, d) for k in (3, 4, 5) for kind in ("cyc", "cycw")])
+            assert (got[:, 0] == got[:, 1]).all()
+            assert (got[:, 3::2] >= got[:, 2::2]).all()
+
+
 def test_boundaries_and_ties():
     # two legs exactly delta apart: the span bound is inclusive
     src = np.array([0, 1, 0, 2], np.int32)
@@ -148,7 +178,7 @@ def test_rejects_bad_ids():
 def tiny10k():
     g = aml_synth.workload("tiny-10k")
     og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
-    cols = _cols_10(DAY) + _cols_10(WEEK)
+    cols = _cols_10(DAY) + _cols_10(WEEK) + [("cycw", k, DAY) for k in (3, 4, 5)]
     return g, og, cols, og.count_all(cols)
 
 
@@ -193,8 +223,12 @@ def test_invariants(tiny10k):
         assert (got[:, c[("fan_out", d)]] <= got[:, c[("deg_out", d)]]).all()
         assert (got[:, c[("fan_in", d)]] <= got[:, c[("deg_in", d)]]).all()
         assert (got[:, c[("fan_out", d)]] >= 1).all()
+        if d == DAY:
+            for k in (3, 4, 5):
+                assert got[:, c[("cycw", k, d)]].sum() % k == 0
+                assert (got[:, c[("cycw", k, d)]] >= got[:, c[("cyc", k, d)]]).all()
     # a wider window never lowers a count
-    assert (got[:, 10:] >= got[:, :10]).all()
+    assert (got[:, 10:20] >= got[:, :10]).all()
 
 
 def test_deg_fan_against_numpy(tiny10k):
