@@ -147,6 +147,9 @@ aml_status aml_graph_window_stats(const aml_graph* g, int32_t delta, int64_t* n_
                             /* the operand's node (causal flow of funds)         */
 #define AML_ORDER_BEFORE 2  /* ... comes before it                               */
 #define AML_ORDER_LEG 3     /* INTERSECT: a-side edge before b-side edge         */
+#define AML_ORDER_AFTER_TRIGGER 4 /* matched edge comes after the trigger edge;  */
+                            /* later hops may arrive in any order among         */
+                            /* themselves (Sec. 4's anticipatory edges)         */
 
 #define AML_WIN_TRAILING 0  /* edge time in [t_trigger - delta, trigger]         */
 #define AML_WIN_SPAN 1      /* all edges of an instance within delta             */
@@ -192,7 +195,13 @@ typedef struct aml_pattern {
  *            s != d, m1 != m2, scatter before gather in each leg, all four
  *            edges within delta, counted on all four (Sec. 5, Fig. 4a)
  *   CYC_k    simple directed k-cycles whose edges increase in time around the
- *            cycle from the earliest, spanning <= delta (Sec. 5, Fig. 4b)   */
+ *            cycle from the earliest, spanning <= delta (Sec. 5, Fig. 4b)
+ *   CYCW_k   window cycles, k >= 3: simple directed k-cycles spanning <= delta
+ *            whose edges may occur in any time order (Sec. 4: funds that do
+ *            not traverse the cycle in cycle order, "anticipatory" edges).
+ *            Every hop after the trigger only has to come after the trigger
+ *            edge.  (For k = 2 the set equals CYC_2 and is planned as CYC.)
+ *            Not supported by aml_stream_open (AML_EUNSUPPORTED).        */
 #define AML_FAM_DEG_OUT 0
 #define AML_FAM_DEG_IN 1
 #define AML_FAM_FAN_OUT 2
@@ -200,6 +209,7 @@ typedef struct aml_pattern {
 #define AML_FAM_GS 4
 #define AML_FAM_SG 5
 #define AML_FAM_CYC 6
+#define AML_FAM_CYCW 7
 
 typedef struct aml_pattern_set aml_pattern_set;
 

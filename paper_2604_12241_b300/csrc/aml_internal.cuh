@@ -100,6 +100,8 @@ struct LegCache {
   int64_t n_legs = -1;  // temporal 2-paths with s != d in the window (GS instances)
   int64_t n_front[16] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
                         // cycle-search frontier sizes by level (index = path length)
+  int64_t n_wfront[16] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+                        // the same for the window-cycle search (level 1 = anchors)
 };
 
 // Runtime tunables of the mining kernels (none changes any count).

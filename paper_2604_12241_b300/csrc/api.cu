@@ -46,6 +46,7 @@ static const char* family_name(int f) {
     case AML_FAM_GS: return "GS";
     case AML_FAM_SG: return "SG";
     case AML_FAM_CYC: return "CYC";
+    case AML_FAM_CYCW: return "CYCW";
     default: return "?";
   }
 }
@@ -177,8 +178,9 @@ aml_status aml_pattern_set_column(const aml_pattern_set* ps, int32_t col, aml_co
     info->family = c.family;
     info->k = c.k;
     info->delta = c.delta;
-    if (c.family == AML_FAM_CYC)
-      std::snprintf(info->name, sizeof(info->name), "CYC%d@%d", c.k, c.delta);
+    if (c.family == AML_FAM_CYC || c.family == AML_FAM_CYCW)
+      std::snprintf(info->name, sizeof(info->name), "%s%d@%d", family_name(c.family), c.k,
+                    c.delta);
     else
       std::snprintf(info->name, sizeof(info->name), "%s@%d", family_name(c.family), c.delta);
   });

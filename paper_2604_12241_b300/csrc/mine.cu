@@ -891,21 +891,30 @@ __global__ void __launch_bounds__(512) k_close_range(GraphView g, int32_t delta,
 
 
 // Rebuilds the path of frontier element i at level j (j edges):
-// edges[0..j-1] and nodes[0..j] (nodes[0] = u0 = src of the anchor).
+// edges[0..j-1] and nodes[0..j] (nodes[0] = u0 = src of the anchor); with
+// tp, also the latest time among edges[1..j-1] (the anchor's own time when
+// j = 1).
 __device__ __forceinline__ void cyc_path(const GraphView& g, const CycFrontier& F, int j,
-                                         int64_t i, int32_t* edges, int32_t* nodes) {
+                                         int64_t i, int32_t* edges, int32_t* nodes,
+                                         int32_t* tp = nullptr) {
   int64_t idx = i;
-  for (int lev = j; lev >= 3; --lev) {
+  int32_t t_late = INT32_MIN;
+  for (int lev = j; lev > F.base; --lev) {
     const int32_t q = F.slot[lev][idx];
     edges[lev - 1] = __ldg(g.oeid + q);
     nodes[lev] = __ldg(g.onbr + q);
+    if (tp) t_late = max(t_late, __ldg(g.ot + q));
     idx = F.par[lev][idx];
   }
   edges[0] = F.la[idx];
-  edges[1] = F.lb[idx];
   nodes[0] = g.src[edges[0]];
   nodes[1] = g.dst[edges[0]];
-  nodes[2] = g.dst[edges[1]];
+  if (F.base == 2) {
+    edges[1] = F.lb[idx];
+    nodes[2] = g.dst[edges[1]];
+    if (tp) t_late = max(t_late, g.ts[edges[1]]);
+  }
+  if (tp) *tp = j == 1 ? g.ts[edges[0]] : t_late;
 }
 
 // One level of the cycle search.  Element i of level j is a path of j
@@ -913,7 +922,11 @@ __device__ __forceinline__ void cyc_path(const GraphView& g, const CycFrontier& 
 // is admissible (new node, before the latest closing edge), credits the
 // cycles of length j+1 that close from its end node through B1, and reports
 // the window of later hops its children will take.
-template <int NS>
+// WIN (window cycles): the hops only have to come after e1, in any order;
+// the frontier starts at level 1 (the anchors); a cycle closes through any
+// edge of B1, and a smaller window keeps it only when the path's latest edge
+// also lies inside it.
+template <int NS, bool WIN>
 __global__ void __launch_bounds__(512, 4) k_cyc_level(GraphView g, int32_t delta, int K, int j,
                                                    CycFrontier F, int64_t n,
                                                    const int2* __restrict__ close_rng,
@@ -928,42 +941,45 @@ __global__ void __launch_bounds__(512, 4) k_cyc_level(GraphView g, int32_t delta
   if (has_next) cnt[i] = 0;
   int32_t edges[MAX_CYCLE];
   int32_t nodes[MAX_CYCLE + 1];
-  cyc_path(g, F, j, i, edges, nodes);
+  int32_t tp = 0;
+  cyc_path(g, F, j, i, edges, nodes, WIN ? &tp : nullptr);
   const int2 cr = close_rng[edges[0]];
   if (cr.x >= cr.y) return;  // e1 starts no cycle
   const int32_t t_cl = __ldg(g.it + cr.y - 1), id_cl = __ldg(g.ieid + cr.y - 1);
   const int32_t last = edges[j - 1], tl = g.ts[last];
-  if (!before(tl, last, t_cl, id_cl)) return;  // nothing can close after it
+  if (!WIN && !before(tl, last, t_cl, id_cl)) return;  // nothing can close after it
   const int32_t u0 = nodes[0], w = nodes[j];
-  if (j >= 3) {  // the hop into w must reach a new node
+  if (j >= (WIN ? 2 : 3)) {  // the hop into w must reach a new node
     if (w == u0) return;
     for (int m = 1; m < j; ++m)
       if (nodes[m] == w) return;
   }
-  // cycles of length j+1: edges w -> u0 in B1 after `last`, for this window
-  // and every smaller one whose delta the closing edge keeps
+  const int32_t e1 = edges[0], t1 = g.ts[e1];
+  // cycles of length j+1: edges w -> u0 in B1 (after `last` unless WIN), for
+  // this window and every smaller one whose delta the cycle keeps
   const int k = j + 1;
-  if (k <= K) {
+  if (k <= K && (!WIN || j >= 2)) {
     constexpr int NT = 1 + NS;
     unsigned long long* col[NT];
     int64_t tmax[NT];
     unsigned long long c[NT];
     bool any = false;
-    const int64_t ta = g.ts[edges[0]];
+    const int64_t ta = t1;
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       const int sl = t == 0 ? slots.slot[k] : (t - 1 < sub.n ? sub.cyc[t - 1].slot[k] : -1);
       col[t] = sl >= 0 ? acc + (int64_t)sl * g.E : nullptr;
       tmax[t] = ta + (t == 0 ? delta : (t - 1 < sub.n ? sub.delta[t - 1] : 0));
+      if (WIN && tp > tmax[t]) col[t] = nullptr;  // the path already leaves window t
       c[t] = 0;
-      any |= sl >= 0;
+      any |= col[t] != nullptr;
     }
     if (any) {
       if (cr.y - cr.x <= close_scan_max) {
         for (int32_t q = cr.x; q < cr.y; ++q) {
           if (__ldg(g.inbr + q) != w) continue;
           const int32_t cid = __ldg(g.ieid + q), tq = __ldg(g.it + q);
-          if (!before(tl, last, tq, cid)) continue;
+          if (!WIN && !before(tl, last, tq, cid)) continue;
 #pragma unroll
           for (int t = 0; t < NT; ++t)
             if (col[t] && tq <= tmax[t]) {
@@ -977,7 +993,8 @@ __global__ void __launch_bounds__(512, 4) k_cyc_level(GraphView g, int32_t delta
         nbr_range(g.innbr, in_s, in_e, w, r0, r1);
         if (r1 > r0) {
           int32_t b0, b1;
-          after_edge_upto(g.int_, g.ineid, r0, r1, tl, last, tmax[0], b0, b1);
+          if (WIN) after_edge_upto(g.int_, g.ineid, r0, r1, t1, e1, tmax[0], b0, b1);
+          else after_edge_upto(g.int_, g.ineid, r0, r1, tl, last, tmax[0], b0, b1);
           // delta counting: only new closing edges (the scan branch's range already is)
           if (g.new_from > 0) b0 = min(after_edge(g.int_, g.ineid, b0, r1, g.t_new, g.new_from - 1), b1);
 #pragma unroll
@@ -998,10 +1015,29 @@ __global__ void __launch_bounds__(512, 4) k_cyc_level(GraphView g, int32_t delta
   if (has_next) {
     const int32_t ws = g.optr[w], we = g.optr[w + 1];
     int32_t q0, q1;
-    after_edge_upto(g.ot, g.oeid, ws, we, tl, last, t_cl, q0, q1);
+    if (WIN) after_edge_upto(g.ot, g.oeid, ws, we, t1, e1, (int64_t)t1 + delta, q0, q1);
+    else after_edge_upto(g.ot, g.oeid, ws, we, tl, last, t_cl, q0, q1);
     cnt[i] = q1 - q0;
     q0_out[i] = q0;
   }
+}
+
+// flag[a] = 1 when edge a's closing range is not empty (it anchors cycles)
+__global__ void __launch_bounds__(256) k_anchor_flags(const int2* __restrict__ crng, int64_t E,
+                                                      int32_t* __restrict__ flag) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < E) {
+    const int2 cr = crng[a];
+    flag[a] = cr.x < cr.y ? 1 : 0;
+  }
+}
+
+// items[off[a]] = a for every flagged a
+__global__ void __launch_bounds__(256) k_compact_ids(const int32_t* __restrict__ flag,
+                                                     const int32_t* __restrict__ off, int64_t E,
+                                                     int32_t* __restrict__ items) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < E && flag[a]) items[off[a]] = (int32_t)a;
 }
 
 // Writes the children (parent, slot) of every element at off[i]...; short
@@ -1180,12 +1216,18 @@ void launch_cyc_level(unsigned grid, int block, cudaStream_t s, const GraphView&
                       int32_t delta, int K, int j, const CycFrontier& F, int64_t n,
                       const int2* close_rng, const CycleSlots& slots, unsigned long long* acc,
                       int32_t* cnt, int32_t* q0_out, int32_t close_scan_max,
-                      const SubWindows& sub) {
+                      const SubWindows& sub, bool window_cycles) {
   nsub_dispatch(sub.n, [&](auto ns) {
-    AML_LAUNCH("k_cyc_level", s,
-               k_cyc_level<decltype(ns)::value><<<grid, block, 0, s>>>(
-                   g, delta, K, j, F, n, close_rng, slots, acc, cnt, q0_out, close_scan_max,
-                   sub));
+    if (window_cycles)
+      AML_LAUNCH("k_cyc_level_win", s,
+                 k_cyc_level<decltype(ns)::value, true><<<grid, block, 0, s>>>(
+                     g, delta, K, j, F, n, close_rng, slots, acc, cnt, q0_out, close_scan_max,
+                     sub));
+    else
+      AML_LAUNCH("k_cyc_level", s,
+                 k_cyc_level<decltype(ns)::value, false><<<grid, block, 0, s>>>(
+                     g, delta, K, j, F, n, close_rng, slots, acc, cnt, q0_out, close_scan_max,
+                     sub));
   });
 }
 

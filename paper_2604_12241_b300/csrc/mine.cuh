@@ -119,10 +119,12 @@ struct SubWindows {
   CycleSlots cyc[MAX_SUB];            // CYC_k accumulator slots, k >= 3
 };
 
-// Frontier of the level-by-level cycle search: level 2 is the legs (la, lb);
-// element i of level j >= 3 extends element par[j][i] of level j-1 by the
-// out-slot slot[j][i].
+// Frontier of the level-by-level cycle search: the base level is the legs
+// (la, lb) (base 2) or, for window cycles, the anchor edges la (base 1);
+// element i of a level j above it extends element par[j][i] of level j-1 by
+// the out-slot slot[j][i].
 struct CycFrontier {
+  int base;
   const int32_t* la;
   const int32_t* lb;
   const int32_t* par[MAX_CYCLE + 1];
@@ -147,6 +149,8 @@ __global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, uint32_t*
 __global__ void k_sg_hist(const LegRec* rec, int64_t n, int bits, uint32_t* hist);
 __global__ void k_mark_nodes(const int32_t* node_of, int64_t from, int64_t E, uint32_t* mask);
 __global__ void k_close_range(GraphView g, int32_t delta, int2* rng);
+__global__ void k_anchor_flags(const int2* crng, int64_t E, int32_t* flag);
+__global__ void k_compact_ids(const int32_t* flag, const int32_t* off, int64_t E, int32_t* items);
 // Buffers k_leg_count zeroes per edge: n_acc accumulator columns of E
 // entries, and the GS gather-side counts (either may be absent).
 struct ZeroSink {
@@ -173,7 +177,7 @@ void launch_cyc_level(unsigned grid, int block, cudaStream_t s, const GraphView&
                       int32_t delta, int K, int j, const CycFrontier& F, int64_t n,
                       const int2* close_rng, const CycleSlots& slots, unsigned long long* acc,
                       int32_t* cnt, int32_t* q0_out, int32_t close_scan_max,
-                      const SubWindows& sub);
+                      const SubWindows& sub, bool window_cycles = false);
 __global__ void k_cyc_emit(int64_t n, const int32_t* cnt, const int32_t* q0, const int64_t* off,
                            int32_t* par, int32_t* slot, int32_t own_max);
 __global__ void k_assemble(AssembleParams P);

@@ -77,6 +77,14 @@ std::vector<Template> templates() {
       d.stages.push_back(st(X, k - 2, O, 0, I, k - 1, AML_ORDER_AFTER, SP, bits_upto(k - 2)));
       t.push_back(d);
     }
+    // window cycles: every hop only after the trigger edge (the cycle's
+    // earliest edge), the hops among themselves in any order; for k = 2 the
+    // one hop is the same as an ordered one
+    Template w{k == 2 ? AML_FAM_CYC : AML_FAM_CYCW, k, AML_AGG_INSTANCES, {trigger()}};
+    for (int i = 1; i <= k - 2; ++i)
+      w.stages.push_back(st(F, i, O, -1, 0, i + 1, AML_ORDER_AFTER_TRIGGER, SP, bits_upto(i)));
+    w.stages.push_back(st(F, k - 1, O, -1, 0, 0, AML_ORDER_AFTER_TRIGGER, SP, 0));
+    t.push_back(w);
   }
   return t;
 }
@@ -122,7 +130,7 @@ void validate(const aml_pattern& pat, int p) {
       AML_REQUIRE(x.b_dir == AML_DIR_OUT || x.b_dir == AML_DIR_IN, AML_EINVAL,
                   where(p, s) + "bad neighbour direction");
     }
-    AML_REQUIRE(x.order >= AML_ORDER_NONE && x.order <= AML_ORDER_LEG, AML_EINVAL,
+    AML_REQUIRE(x.order >= AML_ORDER_NONE && x.order <= AML_ORDER_AFTER_TRIGGER, AML_EINVAL,
                 where(p, s) + "bad order");
     AML_REQUIRE(x.window == AML_WIN_TRAILING || x.window == AML_WIN_SPAN, AML_EINVAL,
                 where(p, s) + "bad window");

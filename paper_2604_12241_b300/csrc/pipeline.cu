@@ -29,6 +29,8 @@ struct WindowPlan {
   int sg_slot = -1;
   CycleSlots cyc;
   int K = 0;  // longest cycle wanted
+  CycleSlots cycw;  // window cycles
+  int Kw = 0;
   bool emit_legs() const { return sg || K >= 2; }
   bool needs_off() const { return gs || emit_legs(); }
 };
@@ -56,6 +58,67 @@ void branch_wait(cudaEvent_t ev, cudaStream_t from, cudaStream_t to) {
 
 }  // namespace
 
+// Window cycles of one window (and the smaller ones in sw): closing ranges,
+// the anchors (edges with one) as level 1, then the paths level by level.
+void window_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K,
+                         const CycleSlots& slots, const SubWindows& sw,
+                         unsigned long long* acc, cudaStream_t s) {
+  const int64_t E = g->E;
+  const Tuning tn = g->tune;
+  const int B = tn.block;
+  LegCache& lc = g->legs[delta];
+  DBuf<int2> crng((size_t)E, s);
+  AML_LAUNCH("k_close_range", s, k_close_range<<<grid_for(E, B), B, 0, s>>>(gv, delta, crng.p));
+  DBuf<int32_t> flag((size_t)E + 1, s), off((size_t)E + 1, s);
+  AML_LAUNCH("k_anchor_flags", s,
+             k_anchor_flags<<<grid_for(E, 256), 256, 0, s>>>(crng.p, E, flag.p));
+  AML_CUDA(cudaMemsetAsync(flag.p + E, 0, sizeof(int32_t), s));
+  scan_i32(flag.p, off.p, E + 1, false, s);
+  int64_t& n1 = lc.n_wfront[1];
+  if (n1 < 0) {
+    int32_t n = 0;
+    const SmallRead rd{&n, off.p + E, 4};
+    read_small(&rd, 1, s);
+    n1 = n;
+  }
+  DBuf<int32_t> anchors((size_t)std::max<int64_t>(n1, 1), s);
+  AML_LAUNCH("k_compact_ids", s,
+             k_compact_ids<<<grid_for(E, 256), 256, 0, s>>>(flag.p, off.p, E, anchors.p));
+  CycFrontier F;
+  std::memset(&F, 0, sizeof(F));
+  F.base = 1;
+  F.la = anchors.p;
+  std::vector<DBuf<int32_t>> front;  // par/slot of levels >= 2
+  front.reserve(2 * MAX_CYCLE);
+  int64_t n = n1;
+  for (int j = 1; j <= K - 1 && n > 0; ++j) {
+    const bool has_next = j + 1 <= K - 1;
+    DBuf<int32_t> cnt(has_next ? n + 1 : 0, s), q0(has_next ? n : 0, s);
+    launch_cyc_level(grid_for(n, B), B, s, gv, delta, K, j, F, n, crng.p, slots, acc, cnt.p,
+                     q0.p, tn.close_scan_max, sw, true);
+    if (!has_next) break;
+    DBuf<int64_t> foff(n + 1, s);
+    AML_CUDA(cudaMemsetAsync(cnt.p + n, 0, sizeof(int32_t), s));
+    scan_i32_to_i64(cnt.p, foff.p, n + 1, s);
+    int64_t& nn = lc.n_wfront[j + 1];
+    if (nn < 0) {
+      const SmallRead rd{&nn, foff.p + n, 8};
+      read_small(&rd, 1, s);
+      AML_REQUIRE(nn < (int64_t)INT32_MAX, AML_EUNSUPPORTED, "cycle frontier too large");
+    }
+    front.emplace_back((size_t)nn, s);
+    int32_t* par = front.back().p;
+    front.emplace_back((size_t)nn, s);
+    int32_t* slot = front.back().p;
+    AML_LAUNCH("k_cyc_emit", s,
+               k_cyc_emit<<<grid_for(n, B), B, 0, s>>>(n, cnt.p, q0.p, foff.p, par, slot,
+                                                       tn.own_max));
+    F.par[j + 1] = par;
+    F.slot[j + 1] = slot;
+    n = nn;
+  }
+}
+
 void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
                 cudaStream_t s, uint32_t mode, int32_t new_from, int32_t t_new, bool accumulate) {
   const bool persistent = (mode & (AML_MINE_PERSISTENT | AML_MINE_LEARNED)) != 0;
@@ -81,7 +144,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       AML_REQUIRE(wins.size() < (size_t)MAX_DELTAS, AML_EUNSUPPORTED, "too many windows");
       WindowPlan wp;
       wp.delta = col.delta;
-      for (int k = 0; k <= MAX_CYCLE; ++k) wp.cyc.slot[k] = -1;
+      for (int k = 0; k <= MAX_CYCLE; ++k) wp.cyc.slot[k] = wp.cycw.slot[k] = -1;
       wins.push_back(wp);
       didx = (int)wins.size() - 1;
     }
@@ -104,6 +167,13 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
         wp.K = std::max(wp.K, (int)col.k);
         cd.acc_slot = wp.cyc.slot[col.k];
         break;
+      case AML_FAM_CYCW:
+        AML_REQUIRE(col.k >= 3 && col.k <= MAX_CYCLE, AML_EUNSUPPORTED, "cycle length");
+        AML_REQUIRE(new_from == 0, AML_EUNSUPPORTED, "window cycles are not counted incrementally");
+        if (wp.cycw.slot[col.k] < 0) wp.cycw.slot[col.k] = n_acc++;
+        wp.Kw = std::max(wp.Kw, (int)col.k);
+        cd.acc_slot = wp.cycw.slot[col.k];
+        break;
       default: break;
     }
     P.cols[c] = cd;
@@ -115,7 +185,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   P.accumulate_from = accumulate && new_from > 0 ? new_from : -1;
   for (int c = 0; c < ncols; ++c) {
     const uint32_t f = ps->cols[c].family;
-    if (f == AML_FAM_GS || f == AML_FAM_SG || f == AML_FAM_CYC) P.inst_mask |= 1ull << c;
+    if (f == AML_FAM_GS || f == AML_FAM_SG || f == AML_FAM_CYC || f == AML_FAM_CYCW)
+      P.inst_mask |= 1ull << c;
   }
 
   // zeroed by the first leg count (before any kernel adds into it), or
@@ -387,6 +458,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       const int64_t n2 = lc.n_front[2];
       CycFrontier F;
       std::memset(&F, 0, sizeof(F));
+      F.base = 2;
       F.la = la.p;
       F.lb = lb.p;
       std::vector<DBuf<int32_t>> front;  // par/slot of levels >= 3
@@ -423,6 +495,29 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     if (sg_branch) branch_wait(g->branch_ev[3], s_sg, s);
   }
   if (!acc_zeroed) AML_CUDA(cudaMemsetAsync(acc.p, 0, (size_t)n_acc * E * 8, s));
+  acc_zeroed = true;
+  // window cycles: one level-by-level search per group of windows, largest
+  // delta first; its pass counts the smaller windows by span tests
+  std::vector<int> wq;
+  for (size_t w = 0; w < wins.size(); ++w)
+    if (wins[w].Kw >= 3) wq.push_back((int)w);
+  std::sort(wq.begin(), wq.end(), [&](int x, int y) { return wins[x].delta > wins[y].delta; });
+  std::vector<char> wdone(wins.size(), 0);
+  for (int w : wq) {
+    if (wdone[w]) continue;
+    wdone[w] = 1;
+    const WindowPlan& wp = wins[w];
+    SubWindows sw;
+    std::memset(&sw, 0, sizeof(sw));
+    for (int m : wq)
+      if (!wdone[m] && wins[m].Kw <= wp.Kw && sw.n < MAX_SUB) {
+        sw.delta[sw.n] = wins[m].delta;
+        sw.cyc[sw.n] = wins[m].cycw;
+        ++sw.n;
+        wdone[m] = 1;
+      }
+    window_cycle_search(g, gv, wp.delta, wp.Kw, wp.cycw, sw, acc.p, s);
+  }
   if (branches) AML_CUDA(cudaStreamWaitEvent(s, g->branch_ev[1], 0));
   AML_LAUNCH("k_assemble", s,
              k_assemble<<<grid_for(E, ASM_BLOCK), ASM_BLOCK,

@@ -13,10 +13,11 @@ from typing import List, Sequence
 
 OP_TRIGGER, OP_FOR_ALL, OP_INTERSECT = 0, 1, 2
 DIR_OUT, DIR_IN = 0, 1
-ORDER_NONE, ORDER_AFTER, ORDER_BEFORE, ORDER_LEG = 0, 1, 2, 3
+ORDER_NONE, ORDER_AFTER, ORDER_BEFORE, ORDER_LEG, ORDER_AFTER_TRIGGER = 0, 1, 2, 3, 4
 WIN_TRAILING, WIN_SPAN = 0, 1
 AGG_EDGES, AGG_DISTINCT, AGG_INSTANCES = 0, 1, 2
-FAM_NAMES = {0: "DEG_OUT", 1: "DEG_IN", 2: "FAN_OUT", 3: "FAN_IN", 4: "GS", 5: "SG", 6: "CYC"}
+FAM_NAMES = {0: "DEG_OUT", 1: "DEG_IN", 2: "FAN_OUT", 3: "FAN_IN", 4: "GS", 5: "SG", 6: "CYC",
+             7: "CYCW"}
 
 DAY = 86400
 WEEK = 7 * DAY
@@ -133,6 +134,23 @@ def cycle(k: int, delta: int, closing: str = "for_all") -> Pattern:
     return Pattern(tuple(st), AGG_INSTANCES, delta, f"CYC{k}@{delta}")
 
 
+def window_cycle(k: int, delta: int) -> Pattern:
+    """Window k-cycle (Sec. 4's cycles with anticipatory edges): trigger
+    N0 -> N1, then N_i.out -> N_{i+1} to a new node with every hop only after
+    the trigger edge (the hops among themselves in any order), closed by an
+    edge back into N0, all within delta."""
+    if k < 2:
+        raise ValueError("k >= 2")
+    st: List[Stage] = [TRIGGER]
+    for i in range(1, k - 1):
+        st.append(Stage(OP_FOR_ALL, i, DIR_OUT, out_var=i + 1, order=ORDER_AFTER_TRIGGER,
+                        window=WIN_SPAN, skip_eq=_skip(*range(i + 1))))
+    st.append(Stage(OP_FOR_ALL, k - 1, DIR_OUT, out_var=0, order=ORDER_AFTER_TRIGGER,
+                    window=WIN_SPAN))
+    return Pattern(tuple(st), AGG_INSTANCES, delta, f"CYC{k}@{delta}" if k == 2
+                   else f"CYCW{k}@{delta}")
+
+
 def standard(delta: int, kmax: int = 5) -> List[Pattern]:
     """The ten per-window columns: DEG_OUT, DEG_IN, FAN_OUT, FAN_IN, GS, SG,
     CYC_2..CYC_kmax."""
@@ -159,7 +177,9 @@ def oracle_columns(patterns: Sequence[Pattern]) -> list:
     for p in patterns:
         fam, _, rest = p.name.partition("@")
         d = int(rest)
-        if fam.startswith("CYC"):
+        if fam.startswith("CYCW"):
+            out.append(("cycw", int(fam[4:]), d))
+        elif fam.startswith("CYC"):
             out.append(("cyc", int(fam[3:]), d))
         else:
             out.append((fam.lower(), d))
@@ -174,6 +194,8 @@ def from_oracle_columns(cols) -> List[Pattern]:
     for c in cols:
         if c[0] == "cyc":
             out.append(cycle(int(c[1]), int(c[2])))
+        elif c[0] == "cycw":
+            out.append(window_cycle(int(c[1]), int(c[2])))
         else:
             out.append(make[c[0]](int(c[1])))
     return out
