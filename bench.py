@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--cost-samples", type=int, default=1_000_000)
     ap.add_argument("--cost-epochs", type=int, default=20)
     ap.add_argument("--stream-batches", type=int, default=30)
+    ap.add_argument("--no-window-cycles", action="store_true",
+                    help="skip timing the window-cycle columns (CYCW3..5 at the workload's windows)")
     return ap.parse_args()
 
 
@@ -244,6 +246,48 @@ def algorithmic_bytes(kernel: str, E: int, Ev: int, pats, stats: dict) -> float:
     if kernel == "k_cyc_level" and front:
         return 24.0 * sum(front.values()) / len(front)
     return float("nan")
+
+
+def time_window_cycles(graph, pats, E, use_graph, stream, flush, reps=5) -> dict:
+    """Mines of the window-cycle columns (CYCW3..5 at every window of the
+    workload) on the same resident graph: median of `reps` CUDA-event timed
+    mines after two warm-ups, and the kernels' shares from a profiled mine."""
+    import torch
+
+    import paper_2604_12241_b300 as aml
+    from paper_2604_12241_b300 import _lib
+    from paper_2604_12241_b300 import patterns as P
+
+    deltas = sorted({int(p.name.split("@")[1]) for p in pats})
+    wpats = [P.window_cycle(k, d) for d in deltas for k in (3, 4, 5)]
+    wps = aml.PatternSet(wpats)
+    out = torch.empty((E, len(wpats)), dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        aml.mine(graph, wps, out=out, stream=stream, use_graph=use_graph)
+    torch.cuda.synchronize()
+    ts_ = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        aml.mine(graph, wps, out=out, stream=stream, use_graph=use_graph)
+        b.record(stream)
+        b.synchronize()
+        ts_.append(a.elapsed_time(b))
+    ms = float(np.median(ts_))
+    _lib.profile_read(reset=True)
+    _lib.profile_enable(True)
+    aml.mine(graph, wps, out=out, stream=stream)
+    torch.cuda.synchronize()
+    _lib.profile_enable(False)
+    prof = _lib.profile_read(reset=True)
+    tot = sum(v[1] for v in prof.values()) or 1.0
+    counts = out.cpu().numpy().view(np.uint32)
+    return {"columns": [p.name for p in wpats], "ms_per_mine": ms, "edges_per_s": E / ms * 1e3,
+            "instances_credited": [int(x) for x in counts.astype(np.uint64).sum(axis=0)],
+            "kernels": {k: {"launches": n, "ms": round(t, 4), "share": round(t / tot, 4)}
+                        for k, (n, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])[:6]},
+            "timing": f"median of {reps} mines, CUDA events, L2 flushed between mines"}
 
 
 # --------------------------------------------------------------- reference
@@ -606,6 +650,8 @@ def run_ours(args, ws, rank, local):
                 "kernels": kernels}
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g, pats, args.cpu_seconds)
+        if not args.no_window_cycles:
+            line["window_cycles"] = time_window_cycles(graph, pats, E, use_graph, stream, flush)
     graph.close()
     if not args.no_stream:
         stream = run_stream(args, rank)
