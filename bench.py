@@ -173,10 +173,10 @@ def measured_peak():
 # full size (profiles/dram_hi_small.md), valid only for the kernel sources it
 # was taken with: KERNEL_DIGEST is the digest (kernel_digest()) of the files
 # that define the measured kernels.
-KERNEL_DIGEST = "17bc39acc67e819f"
-MEASURED_TRAFFIC = {"k_cyc_level": 268.6e6, "k_sg_bucket": 518.7e6, "k_leg_emit": 609.5e6,
-                    "k_sg_partition": 552.5e6, "k_fan_reduce": 231.7e6, "k_fan_scan": 315.1e6,
-                    "k_assemble": 1077.0e6, "k_leg_count": 699.4e6}
+KERNEL_DIGEST = "f6d36b205b5157c9"
+MEASURED_TRAFFIC = {"k_cyc_level": 266.7e6, "k_sg_bucket": 518.8e6, "k_leg_emit": 609.6e6,
+                    "k_sg_partition": 550.7e6, "k_fan_reduce": 231.2e6, "k_fan_scan": 314.8e6,
+                    "k_assemble": 1077.5e6, "k_leg_count": 698.2e6}
 
 
 TRAFFIC_SOURCES = ("aml_internal.cuh", "fan.cu", "mine.cu", "mine.cuh", "pipeline.cu", "prims.cu")
