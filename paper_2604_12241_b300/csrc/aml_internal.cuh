@@ -102,6 +102,10 @@ struct LegCache {
                         // cycle-search frontier sizes by level (index = path length)
   int64_t n_wfront[16] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
                         // the same for the window-cycle search (level 1 = anchors)
+  int64_t n_hyb[2][16] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
+                          {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
+                        // the same for the heavy anchors' legs of the hybrid cycle
+                        // search, degree-binned [0] and learned [1]
 };
 
 // Runtime tunables of the mining kernels (none changes any count).
@@ -168,8 +172,8 @@ struct aml_graph {
   cudaStream_t capture_stream = nullptr;
   // side streams and fork/join events of a mine's independent branches
   // (created by the first full mine; captured mines use them too)
-  cudaStream_t side[2] = {nullptr, nullptr};
-  cudaEvent_t branch_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t branch_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace aml {

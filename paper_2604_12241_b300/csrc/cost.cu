@@ -162,49 +162,78 @@ struct CycPersist {
   int32_t delta;
   int K;
   CycleSlots slots;
+  SubWindows sub;             // smaller windows' CYC columns (sub.cyc)
   unsigned long long* acc;
   const int2* crng;
   const int32_t* queue;       // warp items, then thread items
   const int32_t* n_warp;      // device counts of the two queues
   const int32_t* n_total;
+  const int32_t* skip;        // queue entries before the warp items (null: none)
   unsigned long long* next;   // [2] zeroed: warp-queue and thread-queue cursors
   uint32_t* probe;            // clock64 cycles per thread item, or null
   int32_t close_scan_max;
 };
 
-// cycles of length L+1 closing from nodes[L] after edges[L-1] through B1
+// cycles of length L+1 closing from nodes[L] after edges[L-1] through B1,
+// for the window and every smaller one that keeps the closing edge (an
+// ordered cycle's latest edge)
 __device__ __forceinline__ void cyc_close(const CycPersist& A, int L, const int32_t* edges,
                                           const int32_t* nodes, int2 cr) {
   const int k = L + 1;
-  if (k > A.K || A.slots.slot[k] < 0) return;
+  if (k > A.K) return;
+  constexpr int NT = 1 + MAX_SUB;
   const GraphView& g = A.g;
-  unsigned long long* col = A.acc + (int64_t)A.slots.slot[k] * g.E;
+  unsigned long long* col[NT];
+  int64_t tmax[NT];
+  unsigned long long c[NT];
+  bool any = false;
+  const int64_t ta = g.ts[edges[0]];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int sl = t == 0 ? A.slots.slot[k]
+                          : (t - 1 < A.sub.n ? A.sub.cyc[t - 1].slot[k] : -1);
+    col[t] = sl >= 0 ? A.acc + (int64_t)sl * g.E : nullptr;
+    tmax[t] = ta + (t == 0 ? A.delta : (t - 1 < A.sub.n ? A.sub.delta[t - 1] : 0));
+    c[t] = 0;
+    any |= sl >= 0;
+  }
+  if (!any) return;
   const int32_t w = nodes[L], last = edges[L - 1], tl = g.ts[last];
-  unsigned long long c = 0;
   if (cr.y - cr.x <= A.close_scan_max) {
     for (int32_t q = cr.x; q < cr.y; ++q) {
       if (__ldg(g.inbr + q) != w) continue;
-      const int32_t cid = __ldg(g.ieid + q);
-      if (!before(tl, last, __ldg(g.it + q), cid)) continue;
-      atomicAdd(col + cid, 1ull);
-      ++c;
+      const int32_t cid = __ldg(g.ieid + q), tq = __ldg(g.it + q);
+      if (!before(tl, last, tq, cid)) continue;
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        if (col[t] && tq <= tmax[t]) {
+          atomicAdd(col[t] + cid, 1ull);
+          ++c[t];
+        }
     }
   } else {
     const int32_t u0 = nodes[0];
     const int32_t in_s = g.iptr[u0], in_e = g.iptr[u0 + 1];
-    const int32_t r0 = lower_nbr(g.innbr, in_s, in_e, w);
-    if (r0 < in_e && __ldg(g.innbr + r0) == w) {
-      const int32_t r1 = lower_nbr(g.innbr, r0, in_e, w + 1);
-      int32_t b0 = after_edge(g.int_, g.ineid, r0, r1, tl, last);
+    int32_t r0, r1;
+    nbr_range(g.innbr, in_s, in_e, w, r0, r1);
+    if (r1 > r0) {
+      int32_t b0, b1;
+      after_edge_upto(g.int_, g.ineid, r0, r1, tl, last, tmax[0], b0, b1);
       // delta counting: only new closing edges (the scan branch's range already is)
-      if (g.new_from > 0) b0 = after_edge(g.int_, g.ineid, b0, r1, g.t_new, g.new_from - 1);
-      const int32_t b1 = upper_t(g.int_, b0, r1, (int64_t)g.ts[edges[0]] + A.delta);
-      for (int32_t q = b0; q < b1; ++q) atomicAdd(col + __ldg(g.ineid + q), 1ull);
-      c = (unsigned long long)(b1 - b0);
+      if (g.new_from > 0) b0 = min(after_edge(g.int_, g.ineid, b0, r1, g.t_new, g.new_from - 1), b1);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        if (!col[t]) continue;
+        const int32_t bt = t == 0 ? b1 : upper_t(g.int_, b0, b1, tmax[t]);
+        for (int32_t q = b0; q < bt; ++q) atomicAdd(col[t] + __ldg(g.ineid + q), 1ull);
+        c[t] = (unsigned long long)(bt - b0);
+      }
     }
   }
-  if (c)
-    for (int m = 0; m < L; ++m) atomicAdd(col + edges[m], c);
+#pragma unroll
+  for (int t = 0; t < NT; ++t)
+    if (c[t])
+      for (int m = 0; m < L; ++m) atomicAdd(col[t] + edges[m], c[t]);
 }
 
 // every cycle whose earliest edge is e1 and whose second edge is the
@@ -266,13 +295,14 @@ __device__ void cyc_anchor(const CycPersist& A, int32_t e1, int32_t first, int32
 __global__ void __launch_bounds__(256) k_cyc_persistent(CycPersist A) {
   const int lane = threadIdx.x & 31;
   const int64_t n_warp = *A.n_warp, n_total = *A.n_total;
+  const int32_t* queue = A.queue + (A.skip ? *A.skip : 0);
   // warp items: the whole warp splits the anchor's first window
   for (;;) {
     unsigned long long i = 0;
     if (lane == 0) i = atomicAdd(A.next, 1ull);
     i = __shfl_sync(0xffffffffu, i, 0);
     if ((int64_t)i >= n_warp) break;
-    cyc_anchor(A, A.queue[i], lane, 32);
+    cyc_anchor(A, queue[i], lane, 32);
   }
   // thread items, 32 per warp pull
   const int64_t n_thread = n_total - n_warp;
@@ -284,7 +314,7 @@ __global__ void __launch_bounds__(256) k_cyc_persistent(CycPersist A) {
     const int64_t i = (int64_t)base + lane;
     if (i < n_thread) {
       const long long t0 = clock64();
-      cyc_anchor(A, A.queue[n_warp + i], 0, 1);
+      cyc_anchor(A, queue[n_warp + i], 0, 1);
       if (A.probe) A.probe[i] = (uint32_t)min(clock64() - t0, (long long)UINT32_MAX);
     }
   }
@@ -320,58 +350,167 @@ static void cyc_items(aml_graph* g, const GraphView& gv, int32_t delta, const in
   AML_CUDA(cudaMemcpyAsync(n_items, off.p + E, 4, cudaMemcpyDeviceToDevice, s));
 }
 
-void cycles_persistent(aml_graph* g, const GraphView& gv, int32_t delta, int K,
-                       const CycleSlots& slots, unsigned long long* acc, bool learned,
-                       cudaStream_t s) {
+// The hybrid split: about the first 1/HYB_HEAVY of the anchors, in
+// descending estimated cost, are searched level by level (their work spread
+// over the GPU); the rest, whose costs are small and similar, one lane each
+// in the persistent kernel beside them.  Degree and learned binning get the
+// same budget of heavy anchors, so the estimate that ranks costs better
+// leaves the persistent launch the shorter tail.  The split takes whole cost
+// buckets, so which anchors are heavy depends on their costs only, never on
+// the order the queue was filled in (the sizes of the heavy anchors' search
+// are learned once and reused).
+constexpr int HYB_HEAVY = 64;
+
+// ends[b] = end of cost bucket b in the queue (descending cost);
+// ctl = {heavy anchors H, light anchors n - H, 0 (no warp items)}, H the
+// first bucket end at or past n / HYB_HEAVY
+__global__ void k_hyb_split(const int32_t* __restrict__ ends, const int32_t* __restrict__ n_items,
+                            int32_t* __restrict__ ctl) {
+  const int32_t n = *n_items;
+  const int32_t target = n > 0 ? (n + HYB_HEAVY - 1) / HYB_HEAVY : 0;
+  int32_t h = n;
+  for (int b = 0; b < N_BUCKETS; ++b)
+    if (ends[b] >= target) {
+      h = ends[b];
+      break;
+    }
+  ctl[0] = h;
+  ctl[1] = n - h;
+  ctl[2] = 0;
+}
+
+// the heavy legs found must be exactly the ones the buffers were sized for
+__global__ void k_check_count(const int32_t* __restrict__ total, int64_t expect,
+                              uint32_t* __restrict__ err) {
+  if (*total != expect) atomicOr(err, ERR_BOUNDS);
+}
+
+// heavy[queue[i]] = 1 for the first ctl[0] queue entries
+__global__ void __launch_bounds__(256) k_mark_heavy(const int32_t* __restrict__ queue,
+                                                    const int32_t* __restrict__ ctl, int64_t cap,
+                                                    int32_t* __restrict__ heavy) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cap && i < ctl[0]) heavy[queue[i]] = 1;
+}
+
+// flag[i] = 1 for the cycle-capable legs of heavy anchors
+__global__ void __launch_bounds__(256) k_heavy_legs(const int32_t* __restrict__ la, int64_t n,
+                                                    const int32_t* __restrict__ heavy,
+                                                    int32_t* __restrict__ flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = heavy[la[i]];
+}
+
+__global__ void __launch_bounds__(256) k_gather_legs(const int32_t* __restrict__ flag,
+                                                     const int32_t* __restrict__ off, int64_t n,
+                                                     const int32_t* __restrict__ la,
+                                                     const int32_t* __restrict__ lb,
+                                                     int32_t* __restrict__ la_h,
+                                                     int32_t* __restrict__ lb_h, int64_t cap,
+                                                     uint32_t* __restrict__ err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) {
+    if (off[i] >= cap) {  // never written past the buffers; reported instead
+      atomicOr(err, ERR_BOUNDS);
+      return;
+    }
+    la_h[off[i]] = la[i];
+    lb_h[off[i]] = lb[i];
+  }
+}
+
+void cycles_hybrid(aml_graph* g, const GraphView& gv, int32_t delta, int K,
+                   const CycleSlots& slots, const SubWindows& sub, unsigned long long* acc,
+                   const int2* crng, const int32_t* la, const int32_t* lb, bool learned,
+                   cudaStream_t s, cudaStream_t side) {
   const int64_t E = g->E;
-  DBuf<int2> crng(E, s);
-  AML_LAUNCH("k_close_range", s,
-             k_close_range<<<grid_for(E, 256), 256, 0, s>>>(gv, delta, crng.p));
+  LegCache& lc = g->legs[delta];
+  const int64_t n2 = lc.n_front[2];  // all cycle-capable legs (la, lb)
+  // anchors with cycle work and their estimated costs, one descending queue
   DBuf<int32_t> items(E, s), w2(E, s), nb(4, s), queue(E, s), hist(2 * N_BUCKETS + 1, s);
-  cyc_items(g, gv, delta, crng.p, items.p, nb.p, w2.p, s);
+  cyc_items(g, gv, delta, crng, items.p, nb.p, w2.p, s);
   DBuf<float> cost(E, s);
-  float thr = (float)g->tune.own_max;
   const CostModel* cm = nullptr;
   for (const CostModel& m : g->cost_models)
     if (m.delta == delta) cm = &m;
-  if (learned && cm) {
+  const bool model = learned && cm;
+  if (model) {
     DBuf<float> feat((size_t)E * MLP_IN, s);
     AML_LAUNCH("k_cyc_features", s,
                k_cyc_features<<<grid_for(E, 256), 256, 0, s>>>(gv, delta, K, items.p, nb.p,
-                                                               crng.p, w2.p, feat.p));
-    // inference over the device count, sized by the host bound E
+                                                               crng, w2.p, feat.p));
     mlp_infer(device_of(*cm), feat.p, E, cost.p, s, nb.p);
     AML_LAUNCH("k_expm1", s, k_expm1<<<grid_for(E, 256), 256, 0, s>>>(cost.p, nb.p));
-    thr = cm->warp_threshold;
   } else {
     AML_LAUNCH("k_gather_w2", s,
                k_gather_w2<<<grid_for(E, 256), 256, 0, s>>>(items.p, nb.p, w2.p, cost.p));
   }
+  const float no_warp = 3.0e38f;  // every item in the one (descending) queue
   AML_CUDA(cudaMemsetAsync(hist.p, 0, (2 * N_BUCKETS + 1) * 4, s));
   AML_LAUNCH("k_bin_hist", s,
-             k_bin_hist<<<grid_for(E, 256), 256, 0, s>>>(cost.p, nb.p, thr, hist.p));
-  scan_i32(hist.p, hist.p, 2 * N_BUCKETS + 1, false, s);  // hist[N_BUCKETS] = warp count
-  // hist[N_BUCKETS] is now the start of the thread queue = n_warp
-  AML_CUDA(cudaMemcpyAsync(nb.p + 1, hist.p + N_BUCKETS, 4, cudaMemcpyDeviceToDevice, s));
+             k_bin_hist<<<grid_for(E, 256), 256, 0, s>>>(cost.p, nb.p, no_warp, hist.p));
+  scan_i32(hist.p, hist.p, 2 * N_BUCKETS + 1, false, s);
   AML_LAUNCH("k_bin_scatter", s,
-             k_bin_scatter<<<grid_for(E, 256), 256, 0, s>>>(items.p, cost.p, nb.p, thr, hist.p,
-                                                            queue.p));
+             k_bin_scatter<<<grid_for(E, 256), 256, 0, s>>>(items.p, cost.p, nb.p, no_warp,
+                                                            hist.p, queue.p));
+  // the heaviest anchors' legs
+  DBuf<int32_t> ctl(4, s), heavy(E, s);
+  AML_LAUNCH("k_hyb_split", s, k_hyb_split<<<1, 1, 0, s>>>(hist.p + N_BUCKETS, nb.p, ctl.p));
+  AML_CUDA(cudaMemsetAsync(heavy.p, 0, (size_t)E * 4, s));
+  AML_LAUNCH("k_mark_heavy", s,
+             k_mark_heavy<<<grid_for(E, 256), 256, 0, s>>>(queue.p, ctl.p, E, heavy.p));
+  int64_t* cache = lc.n_hyb[model ? 1 : 0];
+  DBuf<int32_t> fl((size_t)n2 + 1, s), off((size_t)n2 + 1, s);
+  if (n2 > 0)
+    AML_LAUNCH("k_heavy_legs", s,
+               k_heavy_legs<<<grid_for(n2, 256), 256, 0, s>>>(la, n2, heavy.p, fl.p));
+  AML_CUDA(cudaMemsetAsync(fl.p + n2, 0, sizeof(int32_t), s));
+  scan_i32(fl.p, off.p, n2 + 1, false, s);
+  if (cache[2] < 0) {
+    int32_t nh = 0;
+    const SmallRead rd{&nh, off.p + n2, 4};
+    read_small(&rd, 1, s);
+    cache[2] = nh;
+  }
+  const int64_t cap = std::max<int64_t>(cache[2], 1);
+  DBuf<int32_t> la_h((size_t)cap, s), lb_h((size_t)cap, s);
+  AML_CUDA(cudaMemsetAsync(la_h.p, 0, (size_t)cap * 4, s));  // valid ids whatever happens
+  AML_CUDA(cudaMemsetAsync(lb_h.p, 0, (size_t)cap * 4, s));
+  if (n2 > 0)
+    AML_LAUNCH("k_gather_legs", s,
+               k_gather_legs<<<grid_for(n2, 256), 256, 0, s>>>(fl.p, off.p, n2, la, lb,
+                                                              la_h.p, lb_h.p, cache[2], g->err));
+  AML_LAUNCH("k_check_count", s, k_check_count<<<1, 1, 0, s>>>(off.p + n2, cache[2], g->err));
+  // the other anchors: one persistent launch beside the level-by-level search
   DBuf<unsigned long long> next(2, s);
   AML_CUDA(cudaMemsetAsync(next.p, 0, 16, s));
+  const bool fork = side != s;
+  if (fork) {
+    AML_CUDA(cudaEventRecord(g->branch_ev[4], s));
+    AML_CUDA(cudaStreamWaitEvent(side, g->branch_ev[4], 0));
+  }
   CycPersist A;
   A.g = gv;
   A.delta = delta;
   A.K = K;
   A.slots = slots;
+  A.sub = sub;
   A.acc = acc;
-  A.crng = crng.p;
+  A.crng = crng;
   A.queue = queue.p;
-  A.n_warp = nb.p + 1;
-  A.n_total = nb.p;
+  A.n_warp = ctl.p + 2;
+  A.n_total = ctl.p + 1;
+  A.skip = ctl.p;
   A.next = next.p;
   A.probe = nullptr;
   A.close_scan_max = g->tune.close_scan_max;
-  AML_LAUNCH("k_cyc_persistent", s, k_cyc_persistent<<<persistent_grid(), 256, 0, s>>>(A));
+  AML_LAUNCH("k_cyc_persistent", side,
+             k_cyc_persistent<<<persistent_grid(), 256, 0, side>>>(A));
+  level_cycle_search(g, gv, delta, K, slots, sub, acc, crng, la_h.p, lb_h.p, cache, s);
+  if (fork) {  // joined before the buffers above are released on s
+    AML_CUDA(cudaEventRecord(g->branch_ev[5], side));
+    AML_CUDA(cudaStreamWaitEvent(s, g->branch_ev[5], 0));
+  }
 }
 
 // ------------------------------------------------------------- training
@@ -458,6 +597,7 @@ void cost_train(aml_graph* g, const aml_pattern_set* ps, int64_t max_samples, in
   AML_CUDA(cudaMemsetAsync(acc.p, 0, (size_t)std::max(n_acc, 1) * E * 8, s));
   AML_CUDA(cudaMemsetAsync(next.p, 0, 16, s));
   CycPersist A;
+  std::memset(&A, 0, sizeof(A));  // no smaller windows, no skipped entries
   A.g = gv;
   A.delta = delta;
   A.K = K;
@@ -584,6 +724,11 @@ void cost_train(aml_graph* g, const aml_pattern_set* ps, int64_t max_samples, in
   for (size_t i = 0; i < g->cost_models.size(); ++i)
     if (g->cost_models[i].delta == delta) g->cost_models.erase(g->cost_models.begin() + i);
   g->cost_models.push_back(cm);
+  // a new model picks new heavy anchors: forget their frontier sizes and the
+  // mines captured with them
+  for (auto& kv : g->legs)
+    for (int j = 0; j < 16; ++j) kv.second.n_hyb[1][j] = -1;
+  drop_captured_mines(g);
   if (rep) {
     std::memset(rep, 0, sizeof(*rep));
     rep->delta = delta;

@@ -193,10 +193,18 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
 // The same, replayed from a CUDA graph captured on first use.
 void mine_graph_mode(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
                      cudaStream_t s, uint32_t mode = 0);
-// Cycle search of one window by the persistent, cost-binned kernel (cost.cu).
-void cycles_persistent(aml_graph* g, const GraphView& gv, int32_t delta, int K,
-                       const CycleSlots& slots, unsigned long long* acc, bool learned,
-                       cudaStream_t s);
+// Ordered cycles level by level from the cycle-capable legs (pipeline.cu).
+void level_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K,
+                        const CycleSlots& slots, const SubWindows& sub,
+                        unsigned long long* acc, const int2* crng, const int32_t* la,
+                        const int32_t* lb, int64_t* front_cache, cudaStream_t s);
+// Cycle search of one window split by estimated anchor cost (cost.cu): the
+// heaviest anchors' legs level by level on s, the other anchors by the
+// persistent kernel on `side` (forked from and joined back to s).
+void cycles_hybrid(aml_graph* g, const GraphView& gv, int32_t delta, int K,
+                   const CycleSlots& slots, const SubWindows& sub, unsigned long long* acc,
+                   const int2* crng, const int32_t* la, const int32_t* lb, bool learned,
+                   cudaStream_t s, cudaStream_t side);
 void drop_captured_mines(aml_graph* g);
 
 }  // namespace aml

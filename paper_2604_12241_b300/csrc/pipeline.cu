@@ -39,7 +39,7 @@ struct WindowPlan {
 // pass; SG beside the cycle search), created outside any capture; false if
 // they do not exist and cannot be made now (the mine then runs in order).
 bool ensure_branches(aml_graph* g, cudaStream_t s) {
-  if (g->side[1] && g->branch_ev[3]) return true;
+  if (g->side[2] && g->branch_ev[5]) return true;
   cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
   AML_CUDA(cudaStreamIsCapturing(s, &st));
   if (st != cudaStreamCaptureStatusNone) return false;
@@ -101,6 +101,52 @@ void window_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K
     AML_CUDA(cudaMemsetAsync(cnt.p + n, 0, sizeof(int32_t), s));
     scan_i32_to_i64(cnt.p, foff.p, n + 1, s);
     int64_t& nn = lc.n_wfront[j + 1];
+    if (nn < 0) {
+      const SmallRead rd{&nn, foff.p + n, 8};
+      read_small(&rd, 1, s);
+      AML_REQUIRE(nn < (int64_t)INT32_MAX, AML_EUNSUPPORTED, "cycle frontier too large");
+    }
+    front.emplace_back((size_t)nn, s);
+    int32_t* par = front.back().p;
+    front.emplace_back((size_t)nn, s);
+    int32_t* slot = front.back().p;
+    AML_LAUNCH("k_cyc_emit", s,
+               k_cyc_emit<<<grid_for(n, B), B, 0, s>>>(n, cnt.p, q0.p, foff.p, par, slot,
+                                                       tn.own_max));
+    F.par[j + 1] = par;
+    F.slot[j + 1] = slot;
+    n = nn;
+  }
+}
+
+// Ordered cycles of length 3..K (and the sub-windows' ones), level by level
+// from the n = front_cache[2] cycle-capable legs (la, lb); front_cache[j]
+// caches the number of paths of j edges (-1: not known yet, learned once
+// with one wait per level).
+void level_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K,
+                        const CycleSlots& slots, const SubWindows& sub,
+                        unsigned long long* acc, const int2* crng, const int32_t* la,
+                        const int32_t* lb, int64_t* front_cache, cudaStream_t s) {
+  const Tuning tn = g->tune;
+  const int B = tn.block;
+  CycFrontier F;
+  std::memset(&F, 0, sizeof(F));
+  F.base = 2;
+  F.la = la;
+  F.lb = lb;
+  std::vector<DBuf<int32_t>> front;  // par/slot of levels >= 3
+  front.reserve(2 * MAX_CYCLE);
+  int64_t n = front_cache[2];
+  for (int j = 2; j <= K - 1 && n > 0; ++j) {
+    const bool has_next = j + 1 <= K - 1;
+    DBuf<int32_t> cnt(has_next ? n + 1 : 0, s), q0(has_next ? n : 0, s);
+    launch_cyc_level(grid_for(n, B), B, s, gv, delta, K, j, F, n, crng, slots, acc, cnt.p,
+                     q0.p, tn.close_scan_max, sub);
+    if (!has_next) break;
+    DBuf<int64_t> foff(n + 1, s);
+    AML_CUDA(cudaMemsetAsync(cnt.p + n, 0, sizeof(int32_t), s));
+    scan_i32_to_i64(cnt.p, foff.p, n + 1, s);
+    int64_t& nn = front_cache[j + 1];
     if (nn < 0) {
       const SmallRead rd{&nn, foff.p + n, 8};
       read_small(&rd, 1, s);
@@ -196,11 +242,11 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   P.acc = acc.p;
 
   // Smaller windows whose GS/SG/CYC columns are counted from the largest
-  // leg-emitting window's pass (sub-windows; not for the persistent cycle
-  // search, and not when they want longer cycles).
+  // leg-emitting window's pass (sub-windows; not when they want longer
+  // cycles).
   std::vector<int> owner(wins.size(), -1);
   std::vector<std::vector<int>> members(wins.size());
-  if (!persistent) {
+  {
     int lw = -1;
     for (size_t w = 0; w < wins.size(); ++w)
       if (wins[w].emit_legs() && (lw < 0 || wins[w].delta > wins[lw].delta)) lw = (int)w;
@@ -306,7 +352,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     }
     // 2. legs (and, for the level-by-level cycle search, the legs that can
     // start a cycle: those of anchors with a closing range, before its end)
-    const bool level_cycles = wp.K >= 3 && !persistent;
+    const bool level_cycles = wp.K >= 3;
     DBuf<int2> crng;
     DBuf<int32_t> L2;
     DBuf<int64_t> off2;
@@ -451,45 +497,14 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       launch_sg_buckets((unsigned)nb, t, part.p, hist.p, wp.delta, gv.dst, gv.ts, acc_sg,
                         new_from, overflow.p, sub);
     }
-    // 4. cycles of length >= 3: one persistent cost-binned launch ...
+    // 4. cycles of length >= 3: the cost-binned hybrid (heaviest anchors
+    // level by level, the rest in one persistent launch beside them) ...
     if (wp.K >= 3 && persistent) {
-      cycles_persistent(g, gv, wp.delta, wp.K, wp.cyc, acc.p, (mode & AML_MINE_LEARNED) != 0, s);
+      cycles_hybrid(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, crng.p, la.p, lb.p,
+                    (mode & AML_MINE_LEARNED) != 0, s, branches ? g->side[2] : s);
     } else if (level_cycles) {  // ... or level by level from the legs
-      const int64_t n2 = lc.n_front[2];
-      CycFrontier F;
-      std::memset(&F, 0, sizeof(F));
-      F.base = 2;
-      F.la = la.p;
-      F.lb = lb.p;
-      std::vector<DBuf<int32_t>> front;  // par/slot of levels >= 3
-      front.reserve(2 * MAX_CYCLE);
-      int64_t n = n2;
-      for (int j = 2; j <= wp.K - 1 && n > 0; ++j) {
-        const bool has_next = j + 1 <= wp.K - 1;
-        DBuf<int32_t> cnt(has_next ? n + 1 : 0, s), q0(has_next ? n : 0, s);
-        launch_cyc_level(grid_for(n, B), B, s, gv, wp.delta, wp.K, j, F, n, crng.p, wp.cyc,
-                         acc.p, cnt.p, q0.p, tn.close_scan_max, sub);
-        if (!has_next) break;
-        DBuf<int64_t> foff(n + 1, s);
-        AML_CUDA(cudaMemsetAsync(cnt.p + n, 0, sizeof(int32_t), s));
-        scan_i32_to_i64(cnt.p, foff.p, n + 1, s);
-        int64_t& nn = lc.n_front[j + 1];
-        if (nn < 0) {
-          const SmallRead rd{&nn, foff.p + n, 8};
-          read_small(&rd, 1, s);
-          AML_REQUIRE(nn < (int64_t)INT32_MAX, AML_EUNSUPPORTED, "cycle frontier too large");
-        }
-        front.emplace_back((size_t)nn, s);
-        int32_t* par = front.back().p;
-        front.emplace_back((size_t)nn, s);
-        int32_t* slot = front.back().p;
-        AML_LAUNCH("k_cyc_emit", s,
-                   k_cyc_emit<<<grid_for(n, B), B, 0, s>>>(n, cnt.p, q0.p, foff.p, par, slot,
-                                                           tn.own_max));
-        F.par[j + 1] = par;
-        F.slot[j + 1] = slot;
-        n = nn;
-      }
+      level_cycle_search(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, crng.p, la.p, lb.p,
+                         lc.n_front, s);
     }
     // the window's buffers (rec, hist, ...) are freed on s after this join
     if (sg_branch) branch_wait(g->branch_ev[3], s_sg, s);
