@@ -245,13 +245,16 @@ aml_status aml_pattern_set_column(const aml_pattern_set* ps, int32_t col,
                                    /* captures the kernel sequence on a private  */
                                    /* stream; later calls are one graph launch.  */
                                    /* Device output only.                        */
-#define AML_MINE_PERSISTENT 0x4u   /* cycles by one persistent launch over       */
-                                   /* anchor edges in warp / thread queues       */
-                                   /* ordered longest-first by a degree estimate */
-#define AML_MINE_LEARNED 0x8u      /* as PERSISTENT, but the queues and their    */
-                                   /* order come from the cost model trained by  */
-                                   /* aml_cost_train for that window (degree     */
-                                   /* estimate when no model exists)            */
+#define AML_MINE_PERSISTENT 0x4u   /* cycles split by estimated anchor cost: the  */
+                                   /* costliest quarter of the anchors (whole    */
+                                   /* cost buckets; degree estimate = the first  */
+                                   /* window's size) level by level, the rest    */
+                                   /* one lane each in a persistent launch       */
+                                   /* beside them                                */
+#define AML_MINE_LEARNED 0x8u      /* as PERSISTENT, but the costs come from the */
+                                   /* cost model trained by aml_cost_train for   */
+                                   /* that window (degree estimate when no model */
+                                   /* exists)                                   */
 #define AML_MINE_HOST_ASYNC 0x10u  /* with HOST_OUTPUT: counts is page-locked    */
                                    /* host memory (cudaHostAlloc / registered),  */
                                    /* the copy back is enqueued on `stream` and  */

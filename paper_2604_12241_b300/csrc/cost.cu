@@ -1,15 +1,15 @@
-// Persistent cycle search with cost-binned work queues, and the learned
-// cost model that bins it.
+// Cost-binned cycle search (a persistent kernel beside the level-by-level
+// search), and the learned cost model that bins it.
 //
 // Work item = an anchor edge e1 = u0->u1 whose closing range B1 (u0's
 // in-slots after e1 inside the window) is not empty.  Its work is the
 // depth-first search of every cycle whose earliest edge is e1; the cost of
-// that search varies by orders of magnitude between anchors.  Items are put
-// in two queues: a warp queue (the warp's lanes split the anchor's first
-// window) and a thread queue (one lane per anchor), each ordered by
-// decreasing estimated cost (longest processing time first).  One persistent
-// launch (grid = SMs x resident blocks) drains the warp queue, then the
-// thread queue, pulling items with atomic counters.
+// that search varies by orders of magnitude between anchors.  The anchors
+// are ordered by decreasing estimated cost; the costliest (whole cost
+// buckets, about a quarter) are searched level by level from their legs,
+// the rest by one persistent launch (grid = SMs x resident blocks) that
+// pulls them with an atomic counter, one lane each (a warp queue, whose
+// lanes split an anchor's first window, serves the cost probe's callers).
 //
 // Estimated cost: degree binning uses the anchor's first window size (the
 // number of second edges it can take); learned binning uses the perceptron of
@@ -359,7 +359,7 @@ static void cyc_items(aml_graph* g, const GraphView& gv, int32_t delta, const in
 // buckets, so which anchors are heavy depends on their costs only, never on
 // the order the queue was filled in (the sizes of the heavy anchors' search
 // are learned once and reused).
-constexpr int HYB_HEAVY = 64;
+constexpr int HYB_HEAVY = 4;
 
 // ends[b] = end of cost bucket b in the queue (descending cost);
 // ctl = {heavy anchors H, light anchors n - H, 0 (no warp items)}, H the
