@@ -8,8 +8,9 @@
 // are ordered by decreasing estimated cost; the costliest (whole cost
 // buckets, about a quarter) are searched level by level from their legs,
 // the rest by one persistent launch (grid = SMs x resident blocks) that
-// pulls them with an atomic counter, one lane each (a warp queue, whose
-// lanes split an anchor's first window, serves the cost probe's callers).
+// pulls them with an atomic counter, one lane each.  (The kernel drains a
+// warp queue first, whose lanes split an anchor's first window; the hybrid
+// and the cost probe give it none.)
 //
 // Estimated cost: degree binning uses the anchor's first window size (the
 // number of second edges it can take); learned binning uses the perceptron of
