@@ -259,12 +259,21 @@ def time_window_cycles(graph, pats, E, use_graph, stream, flush, reps=5) -> dict
     from paper_2604_12241_b300 import patterns as P
 
     deltas = sorted({int(p.name.split("@")[1]) for p in pats})
-    wpats = [P.window_cycle(k, d) for d in deltas for k in (3, 4, 5)]
-    wps = aml.PatternSet(wpats)
-    out = torch.empty((E, len(wpats)), dtype=torch.int32, device="cuda")
-    for _ in range(2):
-        aml.mine(graph, wps, out=out, stream=stream, use_graph=use_graph)
-    torch.cuda.synchronize()
+    note = None
+    while True:
+        wpats = [P.window_cycle(k, d) for d in deltas for k in (3, 4, 5)]
+        wps = aml.PatternSet(wpats)
+        out = torch.empty((E, len(wpats)), dtype=torch.int32, device="cuda")
+        try:
+            for _ in range(2):
+                aml.mine(graph, wps, out=out, stream=stream, use_graph=use_graph)
+            torch.cuda.synchronize()
+            break
+        except aml.AmlError as err:   # e.g. more than 2^31 paths in the widest window
+            if err.name != "AML_EUNSUPPORTED" or len(deltas) == 1:
+                return {"columns": [p.name for p in wpats], "unavailable": str(err)}
+            note = f"{[p.name for p in wpats]}: {err}; timed without the widest window"
+            deltas = deltas[:-1]
     ts_ = []
     for _ in range(reps):
         flush.zero_()
@@ -287,7 +296,8 @@ def time_window_cycles(graph, pats, E, use_graph, stream, flush, reps=5) -> dict
             "instances_credited": [int(x) for x in counts.astype(np.uint64).sum(axis=0)],
             "kernels": {k: {"launches": n, "ms": round(t, 4), "share": round(t / tot, 4)}
                         for k, (n, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])[:6]},
-            "timing": f"median of {reps} mines, CUDA events, L2 flushed between mines"}
+            "timing": f"median of {reps} mines, CUDA events, L2 flushed between mines",
+            "note": note}
 
 
 # --------------------------------------------------------------- reference

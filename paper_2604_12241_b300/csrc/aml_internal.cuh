@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <exception>
 #include <stdint.h>
 
 #include <map>
@@ -70,6 +72,9 @@ struct DBuf {
   }
   ~DBuf() { reset(); }
   void reset() {
+    // released by an error part-way through enqueueing: work of a side
+    // stream may still use it, so wait for the device first
+    if (p && std::uncaught_exceptions() > 0) cudaDeviceSynchronize();
     if (p) dfree(p, s);
     p = nullptr;
   }

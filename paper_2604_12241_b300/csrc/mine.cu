@@ -633,8 +633,6 @@ __device__ __forceinline__ void sg_sorted_group(SgSmem<CAP, TAB>& S, uint32_t st
   unsigned long long* ka = S.key + CAP;               // (m, start) of U, then ~0
   unsigned long long* kb = reinterpret_cast<unsigned long long*>(S.cnt);  // (m, end)
   const int4* grp = S.grp + start;
-  uint32_t p2 = 1;
-  while (p2 < c) p2 <<= 1;
   constexpr int NT = 1 + NS;
 #pragma unroll
   for (int w = 0; w < NT; ++w) {
@@ -644,22 +642,32 @@ __device__ __forceinline__ void sg_sorted_group(SgSmem<CAP, TAB>& S, uint32_t st
     const long long dw = w == 0 ? delta : sub.delta[w - 1];
     if (threadIdx.x == 0) S.n_valid = 0;
     __syncthreads();
-    uint32_t mine = 0;
-    for (uint32_t k = threadIdx.x; k < p2; k += blockDim.x) {
-      const int4 r = k < c ? grp[k] : make_int4(0, 0, 0, 0);
-      const bool in = k < c && (long long)r.z - r.y <= dw;
+    // U compacted to the front (any order: it is sorted next), the rest of
+    // the next power of two padded with keys that sort last
+    for (uint32_t k = threadIdx.x; k < c; k += blockDim.x) {
+      const int4 r = grp[k];
+      if ((long long)r.z - r.y > dw) continue;
+      const uint32_t at = atomicAdd(&S.n_valid, 1u);
       const unsigned long long m = (unsigned long long)(uint32_t)r.x << 32;
-      sa[k] = in ? r.y : INT32_MAX;
-      sb[k] = in ? r.z : INT32_MAX;
-      ka[k] = in ? m | tkey(r.y) : ~0ull;
-      kb[k] = in ? m | tkey(r.z) : ~0ull;
-      mine += in ? 1u : 0u;
+      sa[at] = r.y;
+      sb[at] = r.z;
+      ka[at] = m | tkey(r.y);
+      kb[at] = m | tkey(r.z);
     }
-    if (mine) atomicAdd(&S.n_valid, mine);
     __syncthreads();
-    bitonic_sort2(sa, sb, p2);
-    bitonic_sort2(ka, kb, p2);
     const uint32_t nw = S.n_valid;  // |U|: the first nw entries of every array
+    if (nw < 2) continue;           // no pair within this window (uniform: nw is shared)
+    uint32_t pw = 1;
+    while (pw < nw) pw <<= 1;
+    for (uint32_t k = nw + threadIdx.x; k < pw; k += blockDim.x) {
+      sa[k] = INT32_MAX;
+      sb[k] = INT32_MAX;
+      ka[k] = ~0ull;
+      kb[k] = ~0ull;
+    }
+    __syncthreads();
+    bitonic_sort2(sa, sb, pw);
+    bitonic_sort2(ka, kb, pw);
     for (uint32_t k = threadIdx.x; k < c; k += blockDim.x) {
       const int4 r = grp[k];
       if ((long long)r.z - r.y > dw) continue;

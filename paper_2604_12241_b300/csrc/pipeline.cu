@@ -101,10 +101,13 @@ void window_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K
     AML_CUDA(cudaMemsetAsync(cnt.p + n, 0, sizeof(int32_t), s));
     scan_i32_to_i64(cnt.p, foff.p, n + 1, s);
     int64_t& nn = lc.n_wfront[j + 1];
-    if (nn < 0) {
-      const SmallRead rd{&nn, foff.p + n, 8};
+    if (nn < 0) {  // cached only once it is known to fit
+      int64_t got = 0;
+      const SmallRead rd{&got, foff.p + n, 8};
       read_small(&rd, 1, s);
-      AML_REQUIRE(nn < (int64_t)INT32_MAX, AML_EUNSUPPORTED, "cycle frontier too large");
+      AML_REQUIRE(got < (int64_t)INT32_MAX, AML_EUNSUPPORTED,
+                  "window-cycle frontier above 2^31 paths");
+      nn = got;
     }
     front.emplace_back((size_t)nn, s);
     int32_t* par = front.back().p;
@@ -147,10 +150,12 @@ void level_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K,
     AML_CUDA(cudaMemsetAsync(cnt.p + n, 0, sizeof(int32_t), s));
     scan_i32_to_i64(cnt.p, foff.p, n + 1, s);
     int64_t& nn = front_cache[j + 1];
-    if (nn < 0) {
-      const SmallRead rd{&nn, foff.p + n, 8};
+    if (nn < 0) {  // cached only once it is known to fit
+      int64_t got = 0;
+      const SmallRead rd{&got, foff.p + n, 8};
       read_small(&rd, 1, s);
-      AML_REQUIRE(nn < (int64_t)INT32_MAX, AML_EUNSUPPORTED, "cycle frontier too large");
+      AML_REQUIRE(got < (int64_t)INT32_MAX, AML_EUNSUPPORTED, "cycle frontier above 2^31 paths");
+      nn = got;
     }
     front.emplace_back((size_t)nn, s);
     int32_t* par = front.back().p;
@@ -511,6 +516,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   }
   if (!acc_zeroed) AML_CUDA(cudaMemsetAsync(acc.p, 0, (size_t)n_acc * E * 8, s));
   acc_zeroed = true;
+  if (branches) AML_CUDA(cudaStreamWaitEvent(s, g->branch_ev[1], 0));  // DEG/FAN joined
   // window cycles: one level-by-level search per group of windows, largest
   // delta first; its pass counts the smaller windows by span tests
   std::vector<int> wq;
@@ -533,7 +539,6 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       }
     window_cycle_search(g, gv, wp.delta, wp.Kw, wp.cycw, sw, acc.p, s);
   }
-  if (branches) AML_CUDA(cudaStreamWaitEvent(s, g->branch_ev[1], 0));
   AML_LAUNCH("k_assemble", s,
              k_assemble<<<grid_for(E, ASM_BLOCK), ASM_BLOCK,
                           (size_t)ASM_BLOCK * (ncols | 1) * sizeof(uint32_t), s>>>(P));
