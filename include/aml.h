@@ -381,7 +381,7 @@ typedef struct aml_stream_info {
   int64_t resident_rows;
   int64_t capacity_rows;       /* resident rows the budget allows                 */
   int64_t final_end_row;       /* rows below this will never change again         */
-  int64_t device_bytes;        /* resident storage                                */
+  int64_t device_bytes;        /* resident rows plus the kept window graph        */
   int32_t t_max;               /* latest timestamp appended                        */
   int32_t delta_max;           /* largest window of the pattern set               */
 } aml_stream_info;
@@ -412,6 +412,16 @@ aml_status aml_stream_read(aml_stream* st, int64_t row0, int64_t n, uint32_t* ou
                            uint32_t flags, void* stream);
 
 aml_status aml_stream_get_info(const aml_stream* st, aml_stream_info* info);
+
+/* Self-check of the kept window graph.  Between appends the stream keeps the
+ * graph of the last recount window and makes the next window's graph by
+ * updating it (dropping the rows that left, adding the batch) instead of
+ * rebuilding it.  This call rebuilds that window's graph from scratch and
+ * compares every array of the two; *n_mismatch = the number of differing
+ * elements (0 when they are equal or no graph is kept).  Synchronizes the
+ * device.  Errors: AML_EINVAL, AML_ENOMEM, AML_ECUDA. */
+aml_status aml_stream_check_graph(aml_stream* st, int64_t* n_mismatch);
+
 aml_status aml_stream_close(aml_stream* st);
 
 /* ------------------------------------------------------ allocation-free FAN */

@@ -255,6 +255,13 @@ class Stream:
         check(lib().aml_stream_get_info(self._h, ctypes.byref(inf)))
         return {f: getattr(inf, f) for f, _ in inf._fields_}
 
+    def check_graph(self) -> int:
+        """Elements in which the kept window graph differs from a fresh build
+        of the same window (0 when they agree)."""
+        n = ctypes.c_int64(0)
+        check(lib().aml_stream_check_graph(self._h, ctypes.byref(n)))
+        return int(n.value)
+
     def close(self) -> None:
         if getattr(self, "_h", None):
             lib().aml_stream_close(self._h)

@@ -121,6 +121,7 @@ _SIGS = {
     "aml_stream_read": (ctypes.c_int32, [_VP, ctypes.c_int64, ctypes.c_int64, _VP,
                                          ctypes.c_int64, ctypes.c_uint32, _VP]),
     "aml_stream_get_info": (ctypes.c_int32, [_VP, ctypes.POINTER(aml_stream_info)]),
+    "aml_stream_check_graph": (ctypes.c_int32, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "aml_stream_close": (ctypes.c_int32, [_VP]),
     "aml_fan_noalloc": (ctypes.c_int32, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
     "aml_cost_train": (ctypes.c_int32, [_VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,

@@ -265,6 +265,319 @@ aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts
   }
 }
 
+// ------------------------------------------------------------ sliding update
+//
+// The graph of a sliding window, made from the graph of the window before it
+// instead of from scratch.  The new window drops the old one's first `drop`
+// edges and appends `n_new` edges that are no earlier than any old edge, so
+// local ids shift down by `drop` and every row changes only at its two ends:
+// the dropped edges are a prefix of each (t, id)-ordered row (ids follow
+// time), and the new edges go after every kept slot.  Kept slots move by a
+// per-row offset (one coalesced pass); only the new edges are sorted.  In a
+// row's (counterparty, t, id) copy, a kept entry moves up past the new edges
+// with a smaller counterparty and a new entry past the kept ones with a
+// counterparty no larger than its own.  Same-counterparty links are rebuilt
+// from the new copy.  The result equals a full build of the new window.
+
+// per row: dropped prefix (first slot with id >= drop) and the new length
+__global__ void k_upd_rows(const int32_t* __restrict__ optr, const int32_t* __restrict__ oeid,
+                           int32_t drop, const int32_t* __restrict__ bptr, int32_t N,
+                           int32_t* __restrict__ cnt, int32_t* __restrict__ kdrop) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > N) return;
+  if (r == N) {
+    cnt[N] = 0;
+    return;
+  }
+  const int32_t lo = optr[r], hi = optr[r + 1];
+  int32_t a = lo, b = hi;
+  while (a < b) {
+    const int32_t mid = (int32_t)(((uint32_t)a + (uint32_t)b) >> 1);
+    if (oeid[mid] < drop) a = mid + 1; else b = mid;
+  }
+  kdrop[r] = a - lo;
+  cnt[r] = (hi - a) + (bptr[r + 1] - bptr[r]);
+}
+
+// per old row start: {new row start, dropped prefix, new edges' range in the
+// sorted batch}; read by every slot of the row through its old row start
+__global__ void k_upd_rowinfo(const int32_t* __restrict__ optr, const int32_t* __restrict__ ptr,
+                              const int32_t* __restrict__ kdrop, const int32_t* __restrict__ bptr,
+                              int32_t N, int4* __restrict__ info) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const int32_t lo = optr[r];
+  if (optr[r + 1] > lo) info[lo] = make_int4(ptr[r], kdrop[r], bptr[r], bptr[r + 1]);
+}
+
+__global__ void k_upd_keep(const int32_t* __restrict__ oeid, const int32_t* __restrict__ orstart,
+                           const int32_t* __restrict__ onbr, const int32_t* __restrict__ ot,
+                           const int4* __restrict__ info, int32_t drop, int64_t oEv,
+                           int32_t* __restrict__ nbr, int32_t* __restrict__ t,
+                           int32_t* __restrict__ eid, int32_t* __restrict__ rstart,
+                           int32_t* __restrict__ pos) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= oEv) return;
+  const int32_t e = oeid[p];
+  if (e < drop) return;
+  const int32_t rs = orstart[p];
+  const int4 ri = info[rs];
+  const int32_t q = ri.x + ((int32_t)p - rs - ri.y);
+  nbr[q] = onbr[p];
+  t[q] = ot[p];
+  eid[q] = e - drop;
+  rstart[q] = ri.x;
+  pos[e - drop] = q;
+}
+
+// new edges in (row, id) order: after the row's kept slots
+__global__ void k_upd_new(const uint32_t* __restrict__ bkey, const uint32_t* __restrict__ bperm,
+                          const int32_t* __restrict__ bptr, const int32_t* __restrict__ ptr,
+                          const int32_t* __restrict__ other, const int32_t* __restrict__ ts,
+                          int32_t b0, int64_t n, int32_t N, int32_t* __restrict__ nbr,
+                          int32_t* __restrict__ t, int32_t* __restrict__ eid,
+                          int32_t* __restrict__ rstart, int32_t* __restrict__ pos) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t r = (int32_t)bkey[i];
+  if (r >= N) return;  // a self-loop
+  const int32_t e = b0 + (int32_t)bperm[i];
+  const int32_t q = ptr[r + 1] - bptr[r + 1] + (int32_t)i;
+  nbr[q] = other[e];
+  t[q] = ts[e];
+  eid[q] = e;
+  rstart[q] = ptr[r];
+  pos[e] = q;
+}
+
+__global__ void k_upd_kept_flags(const int32_t* __restrict__ oneid, int32_t drop, int64_t oEv,
+                                 int32_t* __restrict__ flag) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p <= oEv) flag[p] = p < oEv && oneid[p] >= drop;
+}
+
+__global__ void k_upd_batch_nbr(const uint32_t* __restrict__ bperm,
+                                const int32_t* __restrict__ other, int32_t b0, int64_t n,
+                                int32_t* __restrict__ bnbr) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) bnbr[i] = other[b0 + (int32_t)bperm[i]];
+}
+
+// kept (counterparty, t, id) entries: past the row's new edges with a smaller
+// counterparty (bnbr: counterparties of the batch in (row, counterparty) order)
+__global__ void k_upd_nkeep(const int32_t* __restrict__ oneid, const int32_t* __restrict__ onnbr,
+                            const int32_t* __restrict__ ont, const int32_t* __restrict__ orstart,
+                            const int4* __restrict__ info, const int32_t* __restrict__ kept,
+                            const int32_t* __restrict__ bnbr, int32_t drop, int64_t oEv,
+                            int32_t* __restrict__ nnbr, int32_t* __restrict__ nt,
+                            int32_t* __restrict__ neid) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= oEv) return;
+  const int32_t e = oneid[p];
+  if (e < drop) return;
+  const int32_t rs = orstart[p];
+  const int4 ri = info[rs];
+  const int32_t x = onnbr[p];
+  int32_t a = ri.z, b = ri.w;  // first new edge of the row with counterparty >= x
+  while (a < b) {
+    const int32_t mid = (int32_t)(((uint32_t)a + (uint32_t)b) >> 1);
+    if (bnbr[mid] < x) a = mid + 1; else b = mid;
+  }
+  const int32_t q = ri.x + (kept[p] - kept[rs]) + (a - ri.z);
+  nnbr[q] = x;
+  nt[q] = ont[p];
+  neid[q] = e - drop;
+}
+
+// new (counterparty, t, id) entries: past the row's kept entries with a
+// counterparty <= their own
+__global__ void k_upd_nnew(const uint32_t* __restrict__ bkey, const uint32_t* __restrict__ bperm,
+                           const int32_t* __restrict__ bptr, const int32_t* __restrict__ ptr,
+                           const int32_t* __restrict__ optr, const int32_t* __restrict__ onnbr,
+                           const int32_t* __restrict__ kept, const int32_t* __restrict__ other,
+                           const int32_t* __restrict__ ts, int32_t b0, int64_t n, int32_t N,
+                           int32_t* __restrict__ nnbr, int32_t* __restrict__ nt,
+                           int32_t* __restrict__ neid) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t r = (int32_t)bkey[i];
+  if (r >= N) return;
+  const int32_t e = b0 + (int32_t)bperm[i];
+  const int32_t x = other[e];
+  const int32_t lo = optr[r];
+  int32_t a = lo, b = optr[r + 1];  // first old entry with counterparty > x
+  while (a < b) {
+    const int32_t mid = (int32_t)(((uint32_t)a + (uint32_t)b) >> 1);
+    if (onnbr[mid] <= x) a = mid + 1; else b = mid;
+  }
+  const int32_t q = ptr[r] + (kept[a] - kept[lo]) + ((int32_t)i - bptr[r]);
+  nnbr[q] = x;
+  nt[q] = ts[e];
+  neid[q] = e;
+}
+
+// consecutive entries of one row and counterparty in the (counterparty, t,
+// id) copy are consecutive same-counterparty slots
+__global__ void k_upd_links(const int32_t* __restrict__ nnbr, const int32_t* __restrict__ neid,
+                            const int32_t* __restrict__ rstart, const int32_t* __restrict__ pos,
+                            int64_t Ev, int32_t* __restrict__ prev, int32_t* __restrict__ next) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Ev || p == rstart[p] || nnbr[p] != nnbr[p - 1]) return;
+  const int32_t pe = pos[neid[p]], pf = pos[neid[p - 1]];
+  prev[pe] = pf;
+  next[pf] = pe;
+}
+
+// The sorted new edges of one direction: (row, id) order in (bkey, bperm),
+// (row, counterparty, id) order in (nkey, nperm); bptr = row offsets.
+struct BatchRows {
+  DBuf<uint32_t> bkey, bperm, nkey, nperm;
+  DBuf<int32_t> bptr, bnbr, cnt, kdrop;
+  BatchRows(int64_t n, int32_t N, cudaStream_t s)
+      : bkey(n, s), bperm(n, s), nkey(n, s), nperm(n, s), bptr((size_t)N + 1, s),
+        bnbr(n, s), cnt((size_t)N + 1, s), kdrop((size_t)N, s) {}
+};
+
+static void upd_sort_batch(BatchRows& b, const int32_t* row_of, const int32_t* other, int64_t n,
+                           int32_t N, int nbits, cudaStream_t s) {
+  const int B = 256;
+  DBuf<uint32_t> kt(n, s), vt(n, s);
+  iota_i32(reinterpret_cast<int32_t*>(b.bperm.p), n, s);
+  AML_LAUNCH("k_row_keys", s,
+             k_row_keys<<<grid_for(n, B), B, 0, s>>>(b.bperm.p, row_of, other, n, N, b.bkey.p));
+  radix_sort_u32(b.bkey.p, b.bperm.p, kt.p, vt.p, n, nbits, s);
+  AML_LAUNCH("k_row_ptr", s,
+             k_row_ptr<<<grid_for((int64_t)N + 1, B), B, 0, s>>>(b.bkey.p, n, N, b.bptr.p));
+  // by counterparty, then stably by row
+  iota_i32(reinterpret_cast<int32_t*>(b.nperm.p), n, s);
+  copy_d2d(b.nkey.p, other, (size_t)n * 4, s);
+  radix_sort_u32(b.nkey.p, b.nperm.p, kt.p, vt.p, n, nbits, s);
+  AML_LAUNCH("k_row_keys", s,
+             k_row_keys<<<grid_for(n, B), B, 0, s>>>(b.nperm.p, row_of, other, n, N, b.nkey.p));
+  radix_sort_u32(b.nkey.p, b.nperm.p, kt.p, vt.p, n, nbits, s);
+  AML_LAUNCH("k_upd_batch_nbr", s,
+             k_upd_batch_nbr<<<grid_for(n, B), B, 0, s>>>(b.nperm.p, other, 0, n, b.bnbr.p));
+}
+
+static void upd_fill(const aml_graph* o, aml_graph* g, const Adj& ao, Adj& a, BatchRows& b,
+                     const int32_t* other, int32_t drop, int64_t n_new, cudaStream_t s,
+                     GraphAlloc& ga, int32_t* max_deg_dev) {
+  const int B = 256;
+  const int64_t E = g->E, Ev = g->Ev, oEv = o->Ev;
+  const int32_t N = g->N, b0 = (int32_t)(E - n_new);
+  a.nbr = ga.get<int32_t>(Ev);
+  a.t = ga.get<int32_t>(Ev);
+  a.eid = ga.get<int32_t>(Ev);
+  a.pos = ga.get<int32_t>(E);
+  a.rstart = ga.get<int32_t>(Ev);
+  a.prev = ga.get<int32_t>(Ev);
+  a.next = ga.get<int32_t>(Ev);
+  a.nnbr = ga.get<int32_t>(Ev);
+  a.nt = ga.get<int32_t>(Ev);
+  a.neid = ga.get<int32_t>(Ev);
+  AML_CUDA(cudaMemsetAsync(a.pos, 0xff, (E ? E : 1) * sizeof(int32_t), s));
+  AML_CUDA(cudaMemsetAsync(a.prev, 0xff, (Ev ? Ev : 1) * sizeof(int32_t), s));
+  AML_LAUNCH("k_fill_i32", s, k_fill_i32<<<grid_for(Ev, B), B, 0, s>>>(a.next, Ev, INT32_MAX));
+  DBuf<int4> info(oEv ? oEv : 1, s);
+  DBuf<int32_t> kept(oEv + 1, s);
+  AML_LAUNCH("k_upd_rowinfo", s,
+             k_upd_rowinfo<<<grid_for(N, B), B, 0, s>>>(ao.ptr, a.ptr, b.kdrop.p, b.bptr.p, N,
+                                                       info.p));
+  if (oEv)
+    AML_LAUNCH("k_upd_keep", s,
+               k_upd_keep<<<grid_for(oEv, B), B, 0, s>>>(ao.eid, ao.rstart, ao.nbr, ao.t, info.p,
+                                                        drop, oEv, a.nbr, a.t, a.eid, a.rstart,
+                                                        a.pos));
+  if (n_new)
+    AML_LAUNCH("k_upd_new", s,
+               k_upd_new<<<grid_for(n_new, B), B, 0, s>>>(b.bkey.p, b.bperm.p, b.bptr.p, a.ptr,
+                                                         other, g->ts, b0, n_new, N,
+                                                         a.nbr, a.t, a.eid, a.rstart, a.pos));
+  AML_LAUNCH("k_upd_kept_flags", s,
+             k_upd_kept_flags<<<grid_for(oEv + 1, B), B, 0, s>>>(ao.neid, drop, oEv, kept.p));
+  scan_i32(kept.p, kept.p, oEv + 1, false, s);
+  if (oEv)
+    AML_LAUNCH("k_upd_nkeep", s,
+               k_upd_nkeep<<<grid_for(oEv, B), B, 0, s>>>(ao.neid, ao.nnbr, ao.nt, ao.rstart,
+                                                         info.p, kept.p, b.bnbr.p, drop, oEv,
+                                                         a.nnbr, a.nt, a.neid));
+  if (n_new)
+    AML_LAUNCH("k_upd_nnew", s,
+               k_upd_nnew<<<grid_for(n_new, B), B, 0, s>>>(b.nkey.p, b.nperm.p, b.bptr.p, a.ptr,
+                                                          ao.ptr, ao.nnbr, kept.p, other, g->ts,
+                                                          b0, n_new, N, a.nnbr, a.nt,
+                                                          a.neid));
+  AML_LAUNCH("k_upd_links", s,
+             k_upd_links<<<grid_for(Ev, B), B, 0, s>>>(a.nnbr, a.neid, a.rstart, a.pos, Ev,
+                                                      a.prev, a.next));
+  AML_LAUNCH("k_max_degree", s, k_max_degree<<<grid_for(N, B), B, 0, s>>>(a.ptr, N, max_deg_dev));
+}
+
+aml_graph* update_graph(const aml_graph* o, int64_t drop, const int32_t* src, const int32_t* dst,
+                        const int32_t* ts, const float* amount, int64_t E, cudaStream_t s) {
+  AML_REQUIRE(o && drop >= 0 && drop <= o->E && E >= o->E - drop && E < INT32_MAX,
+              AML_EINVAL, "bad sliding-window update");
+  const int64_t n_new = E - (o->E - drop);
+  aml_graph* g = new aml_graph();
+  GraphAlloc ga{g, s};
+  try {
+    AML_CUDA(cudaGetDevice(&g->device));
+    g->E = E;
+    g->N = o->N;
+    g->tune = o->tune;
+    g->note_stream(s);
+    g->src = ga.get<int32_t>(E);
+    g->dst = ga.get<int32_t>(E);
+    g->ts = ga.get<int32_t>(E);
+    g->amount = ga.get<float>(E);
+    g->err = ga.get<uint32_t>(4);
+    if (E) {
+      copy_d2d(g->src, src, E * 4, s);
+      copy_d2d(g->dst, dst, E * 4, s);
+      copy_d2d(g->ts, ts, E * 4, s);
+      if (amount) copy_d2d(g->amount, amount, E * 4, s);
+      else AML_CUDA(cudaMemsetAsync(g->amount, 0, E * 4, s));
+    }
+    AML_CUDA(cudaMemsetAsync(g->err, 0, 16, s));
+    g->max_deg = ga.get<int32_t>(2);
+    AML_CUDA(cudaMemsetAsync(g->max_deg, 0, 8, s));
+    const int32_t N = g->N, b0 = (int32_t)(E - n_new);
+    const int nbits = bits_for((uint64_t)N);
+    const int B = 256;
+    const int64_t nb = n_new ? n_new : 1;
+    BatchRows bo(nb, N, s), bi(nb, N, s);
+    if (n_new) {
+      upd_sort_batch(bo, g->src + b0, g->dst + b0, n_new, N, nbits, s);
+      upd_sort_batch(bi, g->dst + b0, g->src + b0, n_new, N, nbits, s);
+    } else {
+      AML_CUDA(cudaMemsetAsync(bo.bptr.p, 0, ((size_t)N + 1) * 4, s));
+      AML_CUDA(cudaMemsetAsync(bi.bptr.p, 0, ((size_t)N + 1) * 4, s));
+    }
+    g->out.ptr = ga.get<int32_t>((size_t)N + 1);
+    g->in.ptr = ga.get<int32_t>((size_t)N + 1);
+    AML_LAUNCH("k_upd_rows", s,
+               k_upd_rows<<<grid_for((int64_t)N + 1, B), B, 0, s>>>(
+                   o->out.ptr, o->out.eid, (int32_t)drop, bo.bptr.p, N, bo.cnt.p, bo.kdrop.p));
+    AML_LAUNCH("k_upd_rows", s,
+               k_upd_rows<<<grid_for((int64_t)N + 1, B), B, 0, s>>>(
+                   o->in.ptr, o->in.eid, (int32_t)drop, bi.bptr.p, N, bi.cnt.p, bi.kdrop.p));
+    scan_i32(bo.cnt.p, g->out.ptr, (int64_t)N + 1, false, s);
+    scan_i32(bi.cnt.p, g->in.ptr, (int64_t)N + 1, false, s);
+    int32_t ev[2] = {0, 0};
+    const SmallRead rd[2] = {{&ev[0], g->out.ptr + N, 4}, {&ev[1], g->in.ptr + N, 4}};
+    read_small(rd, 2, s);
+    AML_REQUIRE(ev[0] == ev[1], AML_EINTERNAL, "sliding update: out and in lists disagree");
+    g->Ev = ev[0];
+    upd_fill(o, g, o->out, g->out, bo, g->dst, (int32_t)drop, n_new, s, ga, g->max_deg);
+    upd_fill(o, g, o->in, g->in, bi, g->src, (int32_t)drop, n_new, s, ga, g->max_deg + 1);
+    return g;
+  } catch (...) {
+    cudaStreamSynchronize(s);
+    free_graph(g);
+    throw;
+  }
+}
+
 void drop_captured_mines(aml_graph* g);
 
 void destroy_graph(aml_graph* g) {

@@ -16,6 +16,11 @@
 // batch rows.  Trailing-window columns (DEG, FAN) of old rows never change:
 // later edges are outside their windows.
 //
+// Each append needs the graph of W u B.  Consecutive windows overlap almost
+// entirely, so the stream keeps the last window's graph and updates it (drop
+// the rows that left, add the rows that arrived) instead of sorting the whole
+// window again.
+//
 // Resident rows live in device arrays compacted on demand; an append evicts
 // the rows older than both t_now - resident_window and t_first(B) -
 // delta_max (W must stay resident while B is counted).  resident_window >=
@@ -23,6 +28,7 @@
 // counted, so resident rows hold full-history counts.  A batch that would not fit the memory
 // budget is refused (AML_EADMIT) before any state changes.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -34,6 +40,8 @@
 namespace aml {
 aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts,
                        const float* amount, int64_t E, int32_t N, uint32_t flags, cudaStream_t s);
+aml_graph* update_graph(const aml_graph* o, int64_t drop, const int32_t* src, const int32_t* dst,
+                        const int32_t* ts, const float* amount, int64_t E, cudaStream_t s);
 void destroy_graph(aml_graph* g);
 }  // namespace aml
 
@@ -56,6 +64,10 @@ struct aml_stream {
   bool any = false;
   int32_t t_max = 0;
   int device = 0;
+  // the graph of the last recount window (global rows [g_first, g_first +
+  // g->E)), kept so the next window's graph is an update of it
+  aml_graph* g = nullptr;
+  int64_t g_first = 0;
 };
 
 namespace aml {
@@ -64,7 +76,13 @@ namespace aml {
 // window (about 90 B/edge) plus the mine's scratch and its output.
 static int64_t ws_per_edge(int P) { return 512 + 16 * (int64_t)P; }
 
+static void drop_graph(aml_stream* st) {
+  if (st->g) destroy_graph(st->g);
+  st->g = nullptr;
+}
+
 static void free_stream(aml_stream* st) {
+  drop_graph(st);
   cudaFree(st->src);
   cudaFree(st->dst);
   cudaFree(st->ts);
@@ -99,10 +117,30 @@ static void compact(aml_stream* st, cudaStream_t s) {
 // local id >= new_from (the batch, first edge at time t_new): rows below
 // new_from add those to their stored instance columns, the others are
 // written outright
+//
+// The window's graph is the previous window's graph updated (its oldest rows
+// dropped, the rows after it added) when that graph starts no later than w0
+// and ends inside the new window; otherwise it is built from scratch.  The
+// old graph is released once the update is enqueued; on any failure no graph
+// is kept, so the next append builds afresh.
 static void mine_window(aml_stream* st, int64_t w0, int64_t n, int32_t new_from, int32_t t_new,
                         uint32_t* out, cudaStream_t s) {
-  aml_graph* g = build_graph(st->src + w0, st->dst + w0, st->ts + w0, st->amt + w0, n, st->N,
-                             AML_PTR_DEVICE | AML_ASSUME_SORTED, s);
+  const int64_t first = st->base + w0;
+  aml_graph* g = nullptr;
+  try {
+    aml_graph* o = st->g;
+    if (o && st->g_first <= first && first - st->g_first < o->E &&
+        st->g_first + o->E <= first + n)
+      g = update_graph(o, first - st->g_first, st->src + w0, st->dst + w0, st->ts + w0,
+                       st->amt + w0, n, s);
+    else
+      g = build_graph(st->src + w0, st->dst + w0, st->ts + w0, st->amt + w0, n, st->N,
+                      AML_PTR_DEVICE | AML_ASSUME_SORTED, s);
+  } catch (...) {
+    drop_graph(st);
+    throw;
+  }
+  drop_graph(st);
   try {
     mine_plain(g, &st->ps, out, st->P, s, 0, new_from, t_new, true);
     AML_CUDA(cudaStreamSynchronize(s));
@@ -114,7 +152,16 @@ static void mine_window(aml_stream* st, int64_t w0, int64_t n, int32_t new_from,
     destroy_graph(g);
     throw;
   }
-  destroy_graph(g);
+  st->g = g;
+  st->g_first = first;
+}
+
+__global__ void k_count_diff(const int32_t* __restrict__ a, const int32_t* __restrict__ b,
+                             int64_t n, unsigned long long* __restrict__ diff) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool d = i < n && a[i] != b[i];
+  const unsigned m = __ballot_sync(0xffffffffu, d);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(diff, (unsigned long long)__popc(m));
 }
 
 }  // namespace aml
@@ -297,7 +344,7 @@ aml_status aml_stream_get_info(const aml_stream* st, aml_stream_info* info) {
   info->capacity_rows = st->cap;
   info->t_max = st->t_max;
   info->delta_max = st->delta_max;
-  info->device_bytes = st->cap * (16 + 4 * (int64_t)st->P);
+  info->device_bytes = st->cap * (16 + 4 * (int64_t)st->P) + (st->g ? st->g->bytes : 0);
   // rows whose every instance window has closed: t_e + delta_max < t_max
   const int64_t lim = (int64_t)st->t_max - st->delta_max;
   int64_t k = std::lower_bound(st->hts.begin() + st->lo, st->hts.begin() + st->hi, lim,
@@ -305,6 +352,63 @@ aml_status aml_stream_get_info(const aml_stream* st, aml_stream_info* info) {
               st->hts.begin();
   info->final_end_row = st->any ? st->base + k : st->base + st->lo;
   return AML_OK;
+}
+
+aml_status aml_stream_check_graph(aml_stream* st, int64_t* n_mismatch) {
+  aml_graph* f = nullptr;
+  try {
+    AML_REQUIRE(st && n_mismatch, AML_EINVAL, "NULL argument");
+    *n_mismatch = 0;
+    const aml_graph* g = st->g;
+    if (!g) return AML_OK;
+    const int64_t w = st->g_first - st->base;
+    AML_REQUIRE(w >= st->lo && w + g->E <= st->hi, AML_EINTERNAL,
+                "the kept graph's rows are no longer resident");
+    cudaStream_t s = nullptr;
+    AML_CUDA(cudaDeviceSynchronize());
+    f = build_graph(st->src + w, st->dst + w, st->ts + w, st->amt + w, g->E, st->N,
+                    AML_PTR_DEVICE | AML_ASSUME_SORTED, s);
+    if (f->Ev != g->Ev) {
+      *n_mismatch = 1 + std::llabs(f->Ev - g->Ev);
+    } else {
+      DBuf<unsigned long long> diff(1, s);
+      AML_CUDA(cudaMemsetAsync(diff.p, 0, 8, s));
+      auto cmp = [&](const int32_t* a, const int32_t* b, int64_t n) {
+        if (n > 0)
+          AML_LAUNCH("k_count_diff", s,
+                     k_count_diff<<<grid_for(n, 256), 256, 0, s>>>(a, b, n, diff.p));
+      };
+      const int64_t E = g->E, Ev = g->Ev, N1 = (int64_t)g->N + 1;
+      cmp(f->src, g->src, E);
+      cmp(f->dst, g->dst, E);
+      cmp(f->ts, g->ts, E);
+      const Adj* fa[2] = {&f->out, &f->in};
+      const Adj* ga[2] = {&g->out, &g->in};
+      for (int d = 0; d < 2; ++d) {
+        cmp(fa[d]->ptr, ga[d]->ptr, N1);
+        cmp(fa[d]->pos, ga[d]->pos, E);
+        cmp(fa[d]->nbr, ga[d]->nbr, Ev);
+        cmp(fa[d]->t, ga[d]->t, Ev);
+        cmp(fa[d]->eid, ga[d]->eid, Ev);
+        cmp(fa[d]->rstart, ga[d]->rstart, Ev);
+        cmp(fa[d]->prev, ga[d]->prev, Ev);
+        cmp(fa[d]->next, ga[d]->next, Ev);
+        cmp(fa[d]->nnbr, ga[d]->nnbr, Ev);
+        cmp(fa[d]->nt, ga[d]->nt, Ev);
+        cmp(fa[d]->neid, ga[d]->neid, Ev);
+      }
+      unsigned long long h = 0;
+      AML_CUDA(cudaStreamSynchronize(s));
+      AML_CUDA(cudaMemcpy(&h, diff.p, 8, cudaMemcpyDeviceToHost));
+      *n_mismatch = (int64_t)h;
+    }
+    destroy_graph(f);
+    return AML_OK;
+  } catch (const Failure& e) {
+    if (f) destroy_graph(f);
+    set_error(std::string("aml_stream_check_graph: ") + e.msg);
+    return e.status;
+  }
 }
 
 aml_status aml_stream_close(aml_stream* st) {

@@ -1,7 +1,9 @@
 """Streaming recount: after every append, every resident row equals the
 count of a full mine of everything appended so far (bit-exact), for random
-batch sizes, ties across batch boundaries, and eviction; bad batches are
-refused without changing the stream."""
+batch sizes, ties across batch boundaries, and eviction; the window graph
+the stream updates from append to append equals a fresh build of the same
+window, array by array; bad batches are refused without changing the
+stream."""
 import numpy as np
 import pytest
 
@@ -35,6 +37,8 @@ def test_stream_equals_full_mine(window_days):
         info = st.append(g.src[pos:pos + n], g.dst[pos:pos + n], g.ts[pos:pos + n],
                          g.amount[pos:pos + n])
         assert info["first_row"] == pos and info["n_rows"] == n
+        # the window graph kept between appends equals a fresh build
+        assert st.check_graph() == 0
         pos += n
         if rng.random() < 0.3 or pos == E:
             want = full_mine(g, pos, pats)
@@ -103,9 +107,43 @@ def test_stream_hi_medium_shape_at_tenth_scale():
         st.append(g.src[pos:pos + n], g.dst[pos:pos + n], g.ts[pos:pos + n],
                   g.amount[pos:pos + n])
         pos += n
+        if rng.random() < 0.2:
+            assert st.check_graph() == 0
+    assert st.check_graph() == 0
     inf = st.info()
     r0, nr = inf["resident_first_row"], inf["resident_rows"]
     assert r0 > 0 and r0 + nr == E
     want = full_mine(g, E, pats)
     np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
+    st.close()
+
+
+def test_stream_graph_update_edge_cases():
+    """Self-loops, repeated counterparties, equal timestamps across batch
+    boundaries, single-edge batches, a batch of self-loops only, and a gap
+    longer than the window (every kept row leaves): the graph updated from
+    append to append equals a fresh build, and the counts a full mine."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(11)
+    N, E = 40, 6000
+    src = rng.integers(0, N, E).astype(np.int32)
+    dst = rng.integers(0, N, E).astype(np.int32)
+    loops = rng.random(E) < 0.05
+    dst[loops] = src[loops]
+    dst[2000:2010] = src[2000:2010]            # this batch holds self-loops only
+    ts = (np.cumsum(rng.integers(0, 3, E)) * 60).astype(np.int32)  # many equal times
+    ts[3000:] += 20 * P.DAY                    # a gap longer than every window
+    assert np.all(np.diff(ts) >= 0)
+    g = SimpleNamespace(src=src, dst=dst, ts=ts, n_nodes=N)
+    pats = P.standard(P.DAY) + P.standard(P.WEEK)
+    st = aml.Stream(aml.PatternSet(pats), N, resident_window=8 * P.DAY, mem_budget=1 << 28)
+    cuts = [0, 1, 2, 3, 700, 701, 1500, 2000, 2010, 2011, 2999, 3000, 3001, 4200, 5999, E]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        st.append(src[a:b], dst[a:b], ts[a:b])
+        assert st.check_graph() == 0, (a, b)
+        if b in (2011, 3001, E):
+            want = full_mine(g, b, pats)
+            inf = st.info()
+            r0, nr = inf["resident_first_row"], inf["resident_rows"]
+            np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
     st.close()
