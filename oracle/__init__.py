@@ -29,6 +29,20 @@ class _Col(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32), ("delta", ctypes.c_int64)]
 
 
+class _Stage(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in
+                ("op", "a_var", "a_dir", "b_var", "b_dir", "out_var", "order", "window")] + \
+               [("skip_eq", ctypes.c_uint32)]
+
+
+# stage-program vocabulary (the values of the library's ABI, restated)
+OP_TRIGGER, OP_FOR_ALL, OP_INTERSECT = 0, 1, 2
+DIR_OUT, DIR_IN = 0, 1
+ORD_NONE, ORD_AFTER, ORD_BEFORE, ORD_LEG, ORD_AFTER_TRIGGER = 0, 1, 2, 3, 4
+WIN_TRAILING, WIN_SPAN = 0, 1
+AGG_EDGES, AGG_DISTINCT, AGG_INSTANCES = 0, 1, 2
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2 -fopenmp) if the .so is stale."""
     if (not force and os.path.exists(_LIB)
@@ -54,6 +68,10 @@ def load_library(path: str) -> ctypes.CDLL:
     lib.og_count_all.restype = ctypes.c_int
     lib.og_count_all.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                  ctypes.c_void_p, ctypes.c_int32]
+    lib.og_program_count.restype = ctypes.c_int
+    lib.og_program_count.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                     ctypes.c_int32]
     lib.og_count_edges.restype = ctypes.c_int
     lib.og_count_edges.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                    ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
@@ -120,4 +138,21 @@ class OracleGraph:
                                     ids.ctypes.data, ids.shape[0], out.ctypes.data, threads)
         if rc:
             raise ValueError(f"og_count_edges failed ({rc})")
+        return out
+
+    def program_count(self, stages: Sequence[Sequence[int]], aggregate: int, delta: int,
+                      threads: int = 0) -> np.ndarray:
+        """One stage program interpreted as ``og_program_count`` defines it:
+        uint32 [E].  ``stages`` = (op, a_var, a_dir, b_var, b_dir, out_var,
+        order, window, skip_eq) tuples, stage 0 the trigger."""
+        arr = (_Stage * len(stages))()
+        for i, st in enumerate(stages):
+            for f, v in zip(("op", "a_var", "a_dir", "b_var", "b_dir", "out_var", "order",
+                             "window", "skip_eq"), st):
+                setattr(arr[i], f, int(v))
+        out = np.zeros(self.n_edges, dtype=np.uint32)
+        rc = self._lib.og_program_count(self._h, ctypes.byref(arr), len(stages), int(aggregate),
+                                        int(delta), out.ctypes.data, threads)
+        if rc:
+            raise ValueError(f"og_program_count rejected the program ({rc})")
         return out

@@ -575,3 +575,213 @@ int og_count_edges(const og_graph* g, const og_col* cols, int32_t ncols, const i
   }
   return 0;
 }
+
+/* ---------------- stage programs: the nested loop of Alg. 1, stage by stage ----------------
+ * No windows are searched: every stage walks its operand's whole neighbour
+ * list and tests each condition as the definition in aml_oracle.h states it. */
+
+#define OG_MAXST 16
+#define OG_MAXVAR (OG_MAXST + 1)
+
+typedef struct {
+  const og_graph* g;
+  const og_stage* st;
+  int n;
+  int agg;
+  int64_t delta;
+  int64_t e0;
+  int32_t node[OG_MAXVAR];
+  int64_t reach[OG_MAXVAR];
+  int64_t edges[2 * OG_MAXST]; /* e0, then each stage's edge(s) in stage order */
+  int span[2 * OG_MAXST];      /* the edge takes part in the span test */
+  int nedges;
+  uint64_t nbind;              /* EDGES */
+  int32_t* seen;               /* DISTINCT: last-stage nodes met so far */
+  int64_t nseen, capseen;
+  uint64_t* acc;               /* INSTANCES: this thread's credits, E entries */
+} pg_ctx;
+
+/* the list of node u in direction dir, and the node at the far end of edge f */
+static void pg_list(const og_graph* g, int32_t u, int dir, const int64_t** list, int64_t* lo,
+                    int64_t* hi) {
+  const int64_t* start = dir == OG_DIR_OUT ? g->out_start : g->in_start;
+  *list = dir == OG_DIR_OUT ? g->out_list : g->in_list;
+  *lo = start[u];
+  *hi = start[u + 1];
+}
+
+static int32_t pg_far(const og_graph* g, int64_t f, int dir) {
+  return dir == OG_DIR_OUT ? g->dst[f] : g->src[f];
+}
+
+static int pg_trailing_ok(const pg_ctx* c, int64_t f) {
+  const og_graph* g = c->g;
+  return (int64_t)g->ts[f] >= (int64_t)g->ts[c->e0] - c->delta && (f == c->e0 || prec(g, f, c->e0));
+}
+
+/* all conditions of the completed binding that involve more than one stage:
+ * the span set and, for instances, pairwise distinct edges */
+static void pg_complete(pg_ctx* c, int32_t x_last) {
+  const og_graph* g = c->g;
+  int64_t tmin = INT64_MAX, tmax = INT64_MIN;
+  for (int i = 0; i < c->nedges; ++i) {
+    if (!c->span[i]) continue;
+    int64_t t = g->ts[c->edges[i]];
+    if (t < tmin) tmin = t;
+    if (t > tmax) tmax = t;
+  }
+  if (tmax - tmin > c->delta) return;
+  if (c->agg == OG_AGG_EDGES) {
+    c->nbind++;
+  } else if (c->agg == OG_AGG_DISTINCT) {
+    for (int64_t i = 0; i < c->nseen; ++i)
+      if (c->seen[i] == x_last) return;
+    if (c->nseen == c->capseen) {
+      c->capseen = c->capseen ? 2 * c->capseen : 64;
+      c->seen = (int32_t*)realloc(c->seen, (size_t)c->capseen * 4);
+    }
+    c->seen[c->nseen++] = x_last;
+  } else {
+    for (int i = 0; i < c->nedges; ++i)
+      for (int j = i + 1; j < c->nedges; ++j)
+        if (c->edges[i] == c->edges[j]) return;
+    for (int i = 0; i < c->nedges; ++i) c->acc[c->edges[i]]++;
+  }
+}
+
+/* node x passes the stage's out_var and skip_eq conditions */
+static int pg_node_ok(const pg_ctx* c, const og_stage* s, int32_t x, int bound) {
+  for (int i = 0; i < bound; ++i)
+    if (((s->skip_eq >> i) & 1u) && c->node[i] == x) return 0;
+  if (s->out_var < bound && c->node[s->out_var] != x) return 0;
+  return 1;
+}
+
+static void pg_stage(pg_ctx* c, int si, int bound);
+
+static void pg_bind(pg_ctx* c, int si, int bound, int32_t x, int64_t reach_edge) {
+  const og_stage* s = &c->st[si];
+  int nb = bound;
+  if (s->out_var == bound) {
+    c->node[bound] = x;
+    c->reach[bound] = reach_edge;
+    nb = bound + 1;
+  }
+  if (si == c->n - 1) pg_complete(c, x);
+  else pg_stage(c, si + 1, nb);
+}
+
+static void pg_stage(pg_ctx* c, int si, int bound) {
+  const og_graph* g = c->g;
+  const og_stage* s = &c->st[si];
+  const int64_t* la;
+  int64_t alo, ahi;
+  pg_list(g, c->node[s->a_var], s->a_dir, &la, &alo, &ahi);
+  const int64_t ra = c->reach[s->a_var];
+  const int sp = s->window == OG_WIN_SPAN;
+  for (int64_t i = alo; i < ahi; ++i) {
+    const int64_t fa = la[i];
+    const int32_t x = pg_far(g, fa, s->a_dir);
+    if (!pg_node_ok(c, s, x, bound)) continue;
+    if (s->window == OG_WIN_TRAILING && !pg_trailing_ok(c, fa)) continue;
+    if (s->op == OG_OP_FOR_ALL) {
+      if (s->order == OG_ORD_AFTER && !prec(g, ra, fa)) continue;
+      if (s->order == OG_ORD_BEFORE && !prec(g, fa, ra)) continue;
+      if (s->order == OG_ORD_AFTER_TRIGGER && !prec(g, c->e0, fa)) continue;
+      c->edges[c->nedges] = fa;
+      c->span[c->nedges] = sp;
+      c->nedges++;
+      pg_bind(c, si, bound, x, fa);
+      c->nedges--;
+    } else {
+      const int64_t* lb;
+      int64_t blo, bhi;
+      pg_list(g, c->node[s->b_var], s->b_dir, &lb, &blo, &bhi);
+      for (int64_t j = blo; j < bhi; ++j) {
+        const int64_t fb = lb[j];
+        if (pg_far(g, fb, s->b_dir) != x) continue;
+        if (s->window == OG_WIN_TRAILING && !pg_trailing_ok(c, fb)) continue;
+        if (s->order == OG_ORD_AFTER && !(prec(g, ra, fa) && prec(g, fa, fb))) continue;
+        if (s->order == OG_ORD_BEFORE && !(prec(g, fb, fa) && prec(g, fa, ra))) continue;
+        if (s->order == OG_ORD_LEG && !prec(g, fa, fb)) continue;
+        if (s->order == OG_ORD_AFTER_TRIGGER && !(prec(g, c->e0, fa) && prec(g, c->e0, fb)))
+          continue;
+        c->edges[c->nedges] = fa;
+        c->span[c->nedges] = sp;
+        c->edges[c->nedges + 1] = fb;
+        c->span[c->nedges + 1] = sp;
+        c->nedges += 2;
+        pg_bind(c, si, bound, x, fb);
+        c->nedges -= 2;
+      }
+    }
+  }
+}
+
+static int pg_check(const og_stage* st, int32_t n, int32_t agg) {
+  if (n < 1 || n > OG_MAXST || agg < OG_AGG_EDGES || agg > OG_AGG_INSTANCES) return -1;
+  if (st[0].op != OG_OP_TRIGGER || st[0].out_var != 1) return -1;
+  int bound = 2;
+  for (int s = 1; s < n; ++s) {
+    const og_stage* x = &st[s];
+    if (x->op != OG_OP_FOR_ALL && x->op != OG_OP_INTERSECT) return -1;
+    if (x->a_var < 0 || x->a_var >= bound || (x->a_dir != OG_DIR_OUT && x->a_dir != OG_DIR_IN))
+      return -1;
+    if (x->op == OG_OP_INTERSECT &&
+        (x->b_var < 0 || x->b_var >= bound || (x->b_dir != OG_DIR_OUT && x->b_dir != OG_DIR_IN)))
+      return -1;
+    if (x->order < OG_ORD_NONE || x->order > OG_ORD_AFTER_TRIGGER) return -1;
+    if (x->op == OG_OP_FOR_ALL && x->order == OG_ORD_LEG) return -1;
+    if (x->window != OG_WIN_TRAILING && x->window != OG_WIN_SPAN) return -1;
+    if (bound < 32 && (x->skip_eq >> bound) != 0) return -1;
+    if (x->out_var < 0 || x->out_var > bound) return -1;
+    if (x->out_var == bound) ++bound;
+    else if (s != n - 1) return -1;
+  }
+  return 0;
+}
+
+int og_program_count(const og_graph* g, const og_stage* st, int32_t n, int32_t agg,
+                     int64_t delta, uint32_t* out, int32_t nthreads) {
+  if (!g || !st || !out || delta < 0 || pg_check(st, n, agg)) return -1;
+  const int64_t E = g->E;
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+  uint64_t* total = (uint64_t*)calloc((size_t)(E > 0 ? E : 1), 8);
+#pragma omp parallel num_threads(nthreads)
+  {
+    pg_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.g = g;
+    c.st = st;
+    c.n = n;
+    c.agg = agg;
+    c.delta = delta;
+    if (agg == OG_AGG_INSTANCES) c.acc = (uint64_t*)calloc((size_t)(E > 0 ? E : 1), 8);
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t e0 = 0; e0 < E; ++e0) {
+      if (g->src[e0] == g->dst[e0]) continue;
+      c.e0 = e0;
+      c.node[0] = g->src[e0];
+      c.node[1] = g->dst[e0];
+      c.reach[0] = c.reach[1] = e0;
+      c.edges[0] = e0;
+      c.span[0] = 1;
+      c.nedges = 1;
+      c.nbind = 0;
+      c.nseen = 0;
+      if (n == 1) pg_complete(&c, c.node[1]);
+      else pg_stage(&c, 1, 2);
+      if (agg == OG_AGG_EDGES) total[e0] = c.nbind;
+      else if (agg == OG_AGG_DISTINCT) total[e0] = (uint64_t)c.nseen;
+    }
+    if (agg == OG_AGG_INSTANCES) {
+#pragma omp critical
+      for (int64_t e = 0; e < E; ++e) total[e] += c.acc[e];
+      free(c.acc);
+    }
+    free(c.seen);
+  }
+  clamp_out(total, out, (size_t)E);
+  free(total);
+  return 0;
+}

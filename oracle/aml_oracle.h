@@ -64,6 +64,54 @@ int og_count_all(const og_graph* g, const og_col* cols, int32_t ncols,
 int og_count_edges(const og_graph* g, const og_col* cols, int32_t ncols,
                    const int64_t* eids, int64_t n, uint32_t* out, int32_t nthreads);
 
+/* ---------------- stage programs (Sec. 5; Alg. 1's nested loop per stage) ----------------
+ *
+ * A program is a trigger (stage 0: the edge e0 = N0 -> N1) and stages
+ * 1..n-1, each binding node variables by iterating neighbour lists.  This is
+ * the generic interpretation a program gets when no pattern family applies.
+ * reach(N0) = reach(N1) = e0; a variable bound by a stage is reached by that
+ * stage's edge (INTERSECT: its b-side edge).  A binding gives every stage:
+ *   FOR_ALL (a_var = A, a_dir): an edge f of A's list (OUT: f = A -> x,
+ *     IN: f = x -> A; self-loops are in no list); x is the stage's node.
+ *   INTERSECT (A.a_dir, B.b_dir): edges fa of A's a_dir list and fb of B's
+ *     b_dir list whose other ends are the same node x.
+ * and every stage must satisfy:
+ *   out_var  new: x binds it; already bound (last stage only): x equals it.
+ *   skip_eq  x differs from N_i for every set bit i.
+ *   order    FOR_ALL: AFTER reach(A) < f, BEFORE f < reach(A), AFTER_TRIGGER
+ *            e0 < f, NONE nothing (LEG is not defined for FOR_ALL).
+ *            INTERSECT: AFTER reach(A) < fa < fb, BEFORE fb < fa < reach(A),
+ *            LEG fa < fb, AFTER_TRIGGER e0 < fa and e0 < fb, NONE nothing.
+ *   window   TRAILING: each of the stage's edges g has t_e0 - delta <= t_g
+ *            and g <= e0.  SPAN: the stage's edges join e0 in the span set,
+ *            whose latest and earliest times differ by at most delta.
+ * Aggregate for the row of trigger e0 (self-loop triggers: 0):
+ *   EDGES      the number of bindings;
+ *   DISTINCT   the number of distinct last-stage nodes x over them;
+ *   INSTANCES  a binding whose edges (e0 and all stages') are pairwise
+ *              distinct is an instance, and adds 1 to the row of each of its
+ *              edges (credited from every trigger it is found from).
+ * Every family above is one such program; e.g. the chain of AFTER stages
+ * closing on N0 counts CYC_k, and SG's program finds each pair of legs
+ * twice (once from each scatter edge). */
+enum { OG_OP_TRIGGER = 0, OG_OP_FOR_ALL = 1, OG_OP_INTERSECT = 2 };
+enum { OG_DIR_OUT = 0, OG_DIR_IN = 1 };
+enum { OG_ORD_NONE = 0, OG_ORD_AFTER = 1, OG_ORD_BEFORE = 2, OG_ORD_LEG = 3,
+       OG_ORD_AFTER_TRIGGER = 4 };
+enum { OG_WIN_TRAILING = 0, OG_WIN_SPAN = 1 };
+enum { OG_AGG_EDGES = 0, OG_AGG_DISTINCT = 1, OG_AGG_INSTANCES = 2 };
+
+typedef struct og_stage {
+  int32_t op, a_var, a_dir, b_var, b_dir, out_var, order, window;
+  uint32_t skip_eq;
+} og_stage;
+
+/* Counts of one program for every edge: out[E] (uint32, saturated).
+ * Returns 0, or -1 for a program outside the forms defined above (at most
+ * 16 stages and 17 variables). */
+int og_program_count(const og_graph* g, const og_stage* st, int32_t n_stages,
+                     int32_t aggregate, int64_t delta, uint32_t* out, int32_t nthreads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -166,3 +166,98 @@ def admissible_orders(k: int) -> Tuple[int, int]:
         if all(pos[("a", i)] < pos[("b", i)] for i in range(k)):
             ok += 1
     return total, ok
+
+
+def brute_program(src, dst, ts, stages, aggregate: int, delta: int) -> np.ndarray:
+    """A stage program's counts by enumerating every tuple of edges for the
+    program's edge slots (one per FOR_ALL stage, two per INTERSECT stage) and
+    testing the definition on each; no neighbour lists.  uint64 [E]."""
+    src = [int(x) for x in src]
+    dst = [int(x) for x in dst]
+    ts = [int(x) for x in ts]
+    E = len(src)
+    valid = [i for i in range(E) if src[i] != dst[i]]
+    out = np.zeros(E, dtype=np.uint64)
+    body = [tuple(int(v) for v in st) for st in stages[1:]]
+    width = sum(1 if st[0] == 1 else 2 for st in body)
+
+    def far(f, u, d):  # the other end of f if f is in u's d-list (0 out, 1 in)
+        if d == 0:
+            return dst[f] if src[f] == u else None
+        return src[f] if dst[f] == u else None
+
+    def before(f, e):
+        return _prec(ts, f, e)
+
+    for e0 in valid:
+        n_bind, lasts = 0, set()
+        for tup in itertools.product(valid, repeat=width):
+            node = {0: src[e0], 1: dst[e0]}
+            reach = {0: e0, 1: e0}
+            edges, span = [e0], [e0]
+            x_last, i, ok = dst[e0], 0, True
+            for op, a, ad, b, bd, outv, order, window, skip in body:
+                if op == 1:
+                    f = tup[i]
+                    i += 1
+                    x = far(f, node[a], ad)
+                    mine, rch = [f], f
+                    if x is None:
+                        ok = False
+                    elif order == 1:
+                        ok = before(reach[a], f)
+                    elif order == 2:
+                        ok = before(f, reach[a])
+                    elif order == 4:
+                        ok = before(e0, f)
+                else:
+                    fa, fb = tup[i], tup[i + 1]
+                    i += 2
+                    x, y = far(fa, node[a], ad), far(fb, node[b], bd)
+                    mine, rch = [fa, fb], fb
+                    if x is None or y is None or x != y:
+                        ok = False
+                    elif order == 1:
+                        ok = before(reach[a], fa) and before(fa, fb)
+                    elif order == 2:
+                        ok = before(fb, fa) and before(fa, reach[a])
+                    elif order == 3:
+                        ok = before(fa, fb)
+                    elif order == 4:
+                        ok = before(e0, fa) and before(e0, fb)
+                if not ok:
+                    break
+                if any((skip >> v) & 1 and node[v] == x for v in node):
+                    ok = False
+                    break
+                if outv in node:
+                    if node[outv] != x:
+                        ok = False
+                        break
+                else:
+                    node[outv], reach[outv] = x, rch
+                if window == 0:
+                    if not all(ts[g] >= ts[e0] - delta and (g == e0 or before(g, e0))
+                               for g in mine):
+                        ok = False
+                        break
+                else:
+                    span += mine
+                edges += mine
+                x_last = x
+            if not ok:
+                continue
+            if max(ts[g] for g in span) - min(ts[g] for g in span) > delta:
+                continue
+            if aggregate == 0:
+                n_bind += 1
+            elif aggregate == 1:
+                lasts.add(x_last)
+            elif len(set(edges)) == len(edges):
+                for g in edges:
+                    out[g] += 1
+        if aggregate == 0:
+            out[e0] = n_bind
+        elif aggregate == 1:
+            out[e0] = len(lasts)
+    return out

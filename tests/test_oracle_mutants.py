@@ -13,7 +13,8 @@ import pytest
 
 import aml_synth
 import oracle
-from brute import brute_counts
+from brute import brute_counts, brute_program
+from programs import NOVEL
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "aml_oracle.c")
 
@@ -43,6 +44,21 @@ MUTANTS = [
      "int64_t after = c->edges[depth - 1];"),
     ("ec-cycw-prunes-descents", "if (z == x || (nd > 1 && !c->window)) continue;",
      "if (z == x || nd > 1) continue;"),
+]
+
+# mistakes in the generic interpretation of stage programs, caught by the
+# brute-force program pins
+PROGRAM_MUTANTS = [
+    ("prog-intersect-before-flipped",
+     "if (s->order == OG_ORD_BEFORE && !(prec(g, fb, fa) && prec(g, fa, ra))) continue;",
+     "if (s->order == OG_ORD_BEFORE && !(prec(g, fa, fb) && prec(g, fa, ra))) continue;"),
+    ("prog-trailing-admits-later", "&& (f == c->e0 || prec(g, f, c->e0));", ";"),
+    ("prog-instances-repeat-edges", "        if (c->edges[i] == c->edges[j]) return;\n", ""),
+    ("prog-closing-ignored", "  if (s->out_var < bound && c->node[s->out_var] != x) return 0;\n", ""),
+    ("prog-span-open", "if (tmax - tmin > c->delta) return;", "if (tmax - tmin >= c->delta) return;"),
+    ("prog-distinct-counts-all", "if (c->seen[i] == x_last) return;", "if (0) return;"),
+    ("prog-leg-reversed", "if (s->order == OG_ORD_LEG && !prec(g, fa, fb)) continue;",
+     "if (s->order == OG_ORD_LEG && !prec(g, fb, fa)) continue;"),
 ]
 
 COLS = [("deg_out", 5), ("deg_in", 5), ("fan_out", 5), ("fan_in", 5), ("gs", 5), ("sg", 6),
@@ -79,3 +95,32 @@ def test_pins_reject_mutant(tmp_path, name, orig, mutated):
 
 def test_unmutated_oracle_passes(tmp_path):
     assert not _pins_reject(oracle._load())
+    assert not _program_pins_reject(oracle._load())
+
+
+def _program_pins_reject(lib) -> bool:
+    for seed in range(6):
+        n = 3 + seed % 4
+        g = aml_synth.tiny_random(n, 11 + seed % 3, 8 + seed % 5, 500 + seed,
+                                  self_loops=(seed % 2 == 0))
+        og = oracle.OracleGraph(g.src, g.dst, g.ts, n, lib=lib)
+        for name in sorted(NOVEL):
+            stages, agg = NOVEL[name]
+            for delta in (0, 3, 1000):
+                want = brute_program(g.src, g.dst, g.ts, stages, agg, delta)
+                if not np.array_equal(og.program_count(stages, agg, delta, threads=1), want):
+                    return True
+    return False
+
+
+@pytest.mark.parametrize("name,orig,mutated", PROGRAM_MUTANTS, ids=[m[0] for m in PROGRAM_MUTANTS])
+def test_program_pins_reject_mutant(tmp_path, name, orig, mutated):
+    text = open(SRC).read()
+    assert text.count(orig) == 1, f"mutation site for {name} not unique"
+    path = tmp_path / "mutant.c"
+    path.write_text(text.replace(orig, mutated))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-I", os.path.dirname(SRC), "-o", str(so), str(path)])
+    lib = oracle.load_library(str(so))
+    assert _program_pins_reject(lib), f"mutant {name} survived the program pins"

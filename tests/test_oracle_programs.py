@@ -1,0 +1,79 @@
+"""Pins for the oracle's generic interpretation of stage programs
+(og_program_count), against facts that do not come from it:
+
+* brute force over raw edge tuples (tests/brute.py, brute_program) for
+  programs no pattern family matches, on tiny random graphs with ties and
+  self-loops;
+* every family's own program, interpreted generically, gives that family's
+  counts from the oracle's separate family enumerations (themselves pinned
+  by brute force): DEG/FAN through EDGES/DISTINCT, GS and CYC_k and CYCW_k
+  through INSTANCES, and SG twice over (each pair of legs is found once from
+  each scatter edge, or once from each gather edge);
+* a program with contradictory constraints counts nothing.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import aml_synth
+import oracle
+from brute import brute_program
+from paper_2604_12241_b300 import patterns as P
+from programs import NOVEL
+
+
+def _tuples(pattern):
+    return [dataclasses.astuple(s) for s in pattern.stages]
+
+
+@pytest.mark.parametrize("name", sorted(NOVEL))
+def test_program_oracle_matches_brute_force(name):
+    stages, agg = NOVEL[name]
+    width = sum(1 if s[0] == 1 else 2 for s in stages[1:])
+    n_graphs = 14 if width <= 2 else 6
+    for seed in range(n_graphs):
+        n = 3 + seed % 5
+        E = (14 if width <= 2 else 10) + seed % 5
+        g = aml_synth.tiny_random(n, E, 8 + seed % 6, 1000 + seed, self_loops=(seed % 3 == 0))
+        og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
+        for delta in (0, 3, 1000):
+            want = brute_program(g.src, g.dst, g.ts, stages, agg, delta)
+            got = og.program_count(stages, agg, delta, threads=2)
+            np.testing.assert_array_equal(got, want, err_msg=f"{name}, seed {seed}, delta {delta}")
+
+
+def test_contradictory_program_counts_nothing():
+    stages, agg = NOVEL["empty_trailing_after"]
+    g = aml_synth.tiny_random(20, 400, 50, 7)
+    og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
+    assert not og.program_count(stages, agg, 10**6).any()
+
+
+def _family_cases(delta):
+    out = [(P.deg_out(delta), ("deg_out", delta), 1), (P.deg_in(delta), ("deg_in", delta), 1),
+           (P.fan_out(delta), ("fan_out", delta), 1), (P.fan_in(delta), ("fan_in", delta), 1),
+           (P.gather_scatter(delta), ("gs", delta), 1),
+           (P.gather_scatter(delta, mirrored=True), ("gs", delta), 1),
+           (P.scatter_gather(delta), ("sg", delta), 2),
+           (P.scatter_gather(delta, trigger="gather"), ("sg", delta), 2)]
+    for k in range(2, 6):
+        out.append((P.cycle(k, delta), ("cyc", k, delta), 1))
+        if k >= 3:
+            out.append((P.cycle(k, delta, closing="intersect"), ("cyc", k, delta), 1))
+            out.append((P.window_cycle(k, delta), ("cycw", k, delta), 1))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_family_programs_interpreted_generically(seed):
+    g = aml_synth.tiny_random(25, 500, 400, 77 + seed, self_loops=(seed == 1))
+    og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
+    for delta in (30, 150):
+        cases = _family_cases(delta)
+        fam = og.count_all([c[1] for c in cases], threads=4)
+        for j, (pat, col, factor) in enumerate(cases):
+            got = og.program_count(_tuples(pat), pat.aggregate, pat.delta, threads=4)
+            np.testing.assert_array_equal(got.astype(np.uint64),
+                                          fam[:, j].astype(np.uint64) * factor,
+                                          err_msg=f"{pat.name} (seed {seed})")
