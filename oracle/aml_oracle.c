@@ -577,8 +577,10 @@ int og_count_edges(const og_graph* g, const og_col* cols, int32_t ncols, const i
 }
 
 /* ---------------- stage programs: the nested loop of Alg. 1, stage by stage ----------------
- * No windows are searched: every stage walks its operand's whole neighbour
- * list and tests each condition as the definition in aml_oracle.h states it. */
+ * Every stage walks its operand's neighbour list from the start of its time
+ * range to the end of it (the trailing window, or the span so far widened by
+ * delta) and tests each condition as the definition in aml_oracle.h states
+ * it; the span is tested again on the completed binding. */
 
 #define OG_MAXST 16
 #define OG_MAXVAR (OG_MAXST + 1)
@@ -671,16 +673,45 @@ static void pg_bind(pg_ctx* c, int si, int bound, int32_t x, int64_t reach_edge)
   else pg_stage(c, si + 1, nb);
 }
 
+/* earliest and latest time of the span set bound so far */
+static void pg_span(const pg_ctx* c, int64_t* tmin, int64_t* tmax) {
+  *tmin = INT64_MAX;
+  *tmax = INT64_MIN;
+  for (int i = 0; i < c->nedges; ++i) {
+    if (!c->span[i]) continue;
+    int64_t t = c->g->ts[c->edges[i]];
+    if (t < *tmin) *tmin = t;
+    if (t > *tmax) *tmax = t;
+  }
+}
+
+/* the times a stage's edge can have: the trailing window, or within delta
+ * of every time in the span set; Alg. 1's loop starts at the first edge in
+ * range (Find_Start) and breaks at the first one past it */
+static void pg_range(const pg_ctx* c, int window, int64_t tmin, int64_t tmax, int64_t* tl,
+                     int64_t* th) {
+  if (window == OG_WIN_TRAILING) {
+    *tl = (int64_t)c->g->ts[c->e0] - c->delta;
+    *th = c->g->ts[c->e0];
+  } else {
+    *tl = tmax - c->delta;
+    *th = tmin + c->delta;
+  }
+}
+
 static void pg_stage(pg_ctx* c, int si, int bound) {
   const og_graph* g = c->g;
   const og_stage* s = &c->st[si];
   const int64_t* la;
-  int64_t alo, ahi;
+  int64_t alo, ahi, tmin, tmax, tl, th;
   pg_list(g, c->node[s->a_var], s->a_dir, &la, &alo, &ahi);
   const int64_t ra = c->reach[s->a_var];
   const int sp = s->window == OG_WIN_SPAN;
-  for (int64_t i = alo; i < ahi; ++i) {
+  pg_span(c, &tmin, &tmax);
+  pg_range(c, s->window, tmin, tmax, &tl, &th);
+  for (int64_t i = find_start(g, la, alo, ahi, tl); i < ahi; ++i) {
     const int64_t fa = la[i];
+    if ((int64_t)g->ts[fa] > th) break;
     const int32_t x = pg_far(g, fa, s->a_dir);
     if (!pg_node_ok(c, s, x, bound)) continue;
     if (s->window == OG_WIN_TRAILING && !pg_trailing_ok(c, fa)) continue;
@@ -695,10 +726,14 @@ static void pg_stage(pg_ctx* c, int si, int bound) {
       c->nedges--;
     } else {
       const int64_t* lb;
-      int64_t blo, bhi;
+      int64_t blo, bhi, btl, bth;
       pg_list(g, c->node[s->b_var], s->b_dir, &lb, &blo, &bhi);
-      for (int64_t j = blo; j < bhi; ++j) {
+      const int64_t ta = g->ts[fa];
+      pg_range(c, s->window, sp && ta < tmin ? ta : tmin, sp && ta > tmax ? ta : tmax, &btl,
+               &bth);
+      for (int64_t j = find_start(g, lb, blo, bhi, btl); j < bhi; ++j) {
         const int64_t fb = lb[j];
+        if ((int64_t)g->ts[fb] > bth) break;
         if (pg_far(g, fb, s->b_dir) != x) continue;
         if (s->window == OG_WIN_TRAILING && !pg_trailing_ok(c, fb)) continue;
         if (s->order == OG_ORD_AFTER && !(prec(g, ra, fa) && prec(g, fa, fb))) continue;
