@@ -176,12 +176,15 @@ typedef struct aml_stage {
                              /* (Sec. 5: an edge "increments counts for all     */
                              /* pattern instances it participates in")          */
 
+#define AML_PAT_INTERPRET 0x1  /* run the program through the generic        */
+                               /* interpreter even when a family matches it    */
+
 typedef struct aml_pattern {
   const aml_stage* stages;   /* read during aml_pattern_set_create only          */
   int32_t n_stages;
   int32_t aggregate;         /* AML_AGG_*                                        */
   int32_t delta;             /* time window in seconds, >= 0                     */
-  int32_t reserved;          /* must be 0                                        */
+  int32_t flags;             /* AML_PAT_* (other bits: AML_EINVAL)               */
 } aml_pattern;
 
 /* Pattern families the planner maps stage programs onto (one output column
@@ -210,16 +213,48 @@ typedef struct aml_pattern {
 #define AML_FAM_SG 5
 #define AML_FAM_CYC 6
 #define AML_FAM_CYCW 7
+#define AML_FAM_PROGRAM 8  /* a program no family matches, interpreted (below) */
 
 typedef struct aml_pattern_set aml_pattern_set;
+
+/* Generic interpretation (AML_FAM_PROGRAM columns: programs no family
+ * matches, or given AML_PAT_INTERPRET).  Alg. 1's nested loop run as
+ * written, for every trigger edge e0 = N0 -> N1 that is not a self-loop
+ * (self-loop rows are 0).  reach(N0) = reach(N1) = e0; a variable bound by a
+ * stage is reached by that stage's edge (INTERSECT: its b-side edge).  A
+ * binding gives every stage after the trigger
+ *   FOR_ALL   an edge f of a_var's a_dir list (OUT: f = A -> x, IN: f = x -> A),
+ *   INTERSECT an edge fa of a_var's a_dir list and fb of b_var's b_dir list
+ *             with the same far end x,
+ * subject to: x binds out_var if it is new, else equals it (last stage
+ * only); x differs from every N_i whose skip_eq bit is set; the order --
+ *   FOR_ALL   AFTER reach(A) < f, BEFORE f < reach(A), AFTER_TRIGGER e0 < f,
+ *             NONE no constraint (LEG: AML_EUNSUPPORTED);
+ *   INTERSECT AFTER reach(A) < fa < fb, BEFORE fb < fa < reach(A),
+ *             LEG fa < fb, AFTER_TRIGGER e0 < fa and e0 < fb, NONE none;
+ * and the window -- TRAILING: each of the stage's edges g has
+ * t_e0 - delta <= t_g and g <= e0; SPAN: the stage's edges join e0 in the
+ * span set, whose times differ by at most delta.  The row of e0 gets
+ *   EDGES      the number of bindings,
+ *   DISTINCT   the number of distinct last-stage nodes x over them,
+ *   INSTANCES  nothing directly: every binding whose edges (e0 and all the
+ *              stages') are pairwise distinct adds 1 to the row of each of
+ *              its edges, from whichever trigger it is found.
+ * Every family is such a program; interpreted, each gives its family's
+ * counts except SG, whose pairs of legs are each found twice (from both
+ * scatter edges, or both gather edges).  Limits: at most 8 stages; one
+ * launch visits at most 2^34 candidate edges (beyond: AML_EUNSUPPORTED and
+ * the column is not written).  One thread walks each trigger's bindings
+ * depth first.  Not available to AML_MINE_GRAPH or aml_stream_open
+ * (AML_EUNSUPPORTED). */
 
 /* Validate and plan n patterns; column j of the output is pattern j.
  * Validation (Sec. 6: "validates operand dependencies between stages"):
  * stage 0 is the trigger; every operand names a variable bound by an
  * earlier stage; skip masks name bound variables; windows and orders are in
- * range.  A valid program the planner cannot map onto a family returns
- * AML_EUNSUPPORTED and names the stage in aml_last_error().  Host-only; no
- * device work. */
+ * range.  A valid program no family matches becomes an AML_FAM_PROGRAM
+ * column (generic interpretation, above), or AML_EUNSUPPORTED when it is
+ * outside the interpreter's limits.  Host-only; no device work. */
 aml_status aml_pattern_set_create(const aml_pattern* patterns, int32_t n_patterns,
                                   aml_pattern_set** out);
 aml_status aml_pattern_set_destroy(aml_pattern_set* ps);

@@ -42,7 +42,10 @@ class aml_stage(ctypes.Structure):
 class aml_pattern(ctypes.Structure):
     _fields_ = [("stages", ctypes.POINTER(aml_stage)), ("n_stages", ctypes.c_int32),
                 ("aggregate", ctypes.c_int32), ("delta", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32)]
+
+
+PAT_INTERPRET = 0x1
 
 
 class aml_graph_info(ctypes.Structure):
@@ -178,7 +181,7 @@ def make_patterns(patterns) -> tuple:
         arr[i].n_stages = len(p.stages)
         arr[i].aggregate = p.aggregate
         arr[i].delta = p.delta
-        arr[i].reserved = 0
+        arr[i].flags = PAT_INTERPRET if getattr(p, "interpret", False) else 0
     return arr, keep
 
 

@@ -231,12 +231,28 @@ struct Column {
   int32_t family;  // AML_FAM_*
   int32_t k;       // cycle length
   int32_t delta;
+  int32_t prog = -1;  // AML_FAM_PROGRAM: index into the set's programs
+};
+
+// A stage program run by the generic interpreter (program.cu): the stages
+// of an aml_pattern in a fixed-size form a kernel takes by value.
+constexpr int PROG_MAX_STAGES = 8;  // the trigger and up to 7 stages
+struct ProgStage {
+  int8_t op, a_var, a_dir, b_var, b_dir, out_var, order, window;
+  uint32_t skip;
+};
+struct Prog {
+  ProgStage st[PROG_MAX_STAGES];
+  int32_t n;      // stages, trigger included
+  int32_t agg;    // AML_AGG_*
+  int32_t delta;
 };
 
 }  // namespace aml
 
 struct aml_pattern_set {
   std::vector<aml::Column> cols;
+  std::vector<aml::Prog> progs;  // programs of the AML_FAM_PROGRAM columns
   uint64_t id = 0;  // unique per process, keys captured mines
 };
 

@@ -18,7 +18,7 @@ void clear_error() { g_last_error.clear(); }
 aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts,
                        const float* amount, int64_t E, int32_t N, uint32_t flags, cudaStream_t s);
 void destroy_graph(aml_graph* g);
-std::vector<Column> plan_patterns(const aml_pattern* pats, int n);
+std::vector<Column> plan_patterns(const aml_pattern* pats, int n, std::vector<Prog>* progs);
 
 template <typename F>
 static aml_status guarded(const char* fn, F&& body) {
@@ -47,6 +47,7 @@ static const char* family_name(int f) {
     case AML_FAM_SG: return "SG";
     case AML_FAM_CYC: return "CYC";
     case AML_FAM_CYCW: return "CYCW";
+    case AML_FAM_PROGRAM: return "PROGRAM";
     default: return "?";
   }
 }
@@ -148,10 +149,12 @@ aml_status aml_pattern_set_create(const aml_pattern* patterns, int32_t n_pattern
   return guarded("aml_pattern_set_create", [&] {
     AML_REQUIRE(out != nullptr, AML_EINVAL, "out is NULL");
     AML_REQUIRE(n_patterns <= MAX_COLS, AML_EUNSUPPORTED, "at most 64 patterns per set");
-    std::vector<Column> cols = plan_patterns(patterns, n_patterns);
+    std::vector<Prog> progs;
+    std::vector<Column> cols = plan_patterns(patterns, n_patterns, &progs);
     static std::atomic<uint64_t> next_id{1};
     aml_pattern_set* ps = new aml_pattern_set();
     ps->cols = std::move(cols);
+    ps->progs = std::move(progs);
     ps->id = next_id.fetch_add(1);
     *out = ps;
   });
@@ -181,6 +184,9 @@ aml_status aml_pattern_set_column(const aml_pattern_set* ps, int32_t col, aml_co
     if (c.family == AML_FAM_CYC || c.family == AML_FAM_CYCW)
       std::snprintf(info->name, sizeof(info->name), "%s%d@%d", family_name(c.family), c.k,
                     c.delta);
+    else if (c.family == AML_FAM_PROGRAM)  // numbered by column
+      std::snprintf(info->name, sizeof(info->name), "%s%d@%d", family_name(c.family), col,
+                    c.delta);
     else
       std::snprintf(info->name, sizeof(info->name), "%s@%d", family_name(c.family), c.delta);
   });
@@ -198,6 +204,8 @@ aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, i
     const uint32_t mode = flags & (AML_MINE_PERSISTENT | AML_MINE_LEARNED);
     AML_REQUIRE(!((flags & AML_MINE_GRAPH) && (flags & AML_MINE_HOST_OUTPUT)), AML_EINVAL,
                 "AML_MINE_GRAPH needs a device output");
+    AML_REQUIRE(!(flags & AML_MINE_GRAPH) || ps->progs.empty(), AML_EUNSUPPORTED,
+                "interpreted stage programs are not captured (AML_MINE_GRAPH)");
     const int64_t P = (int64_t)ps->cols.size();
     AML_REQUIRE(ld >= P, AML_EINVAL, "ld must be >= the number of columns");
     AML_REQUIRE(g->E == 0 || counts != nullptr, AML_EINVAL, "counts is NULL");

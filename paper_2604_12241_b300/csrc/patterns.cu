@@ -6,8 +6,8 @@
 // (Alg. 1's per-stage configuration).  The planner first validates operand
 // dependencies (Sec. 6), then maps the program onto one of the families the
 // kernels implement by comparing it, stage by stage, with that family's
-// canonical programs; a valid program that matches none is reported as
-// unsupported rather than run approximately.
+// canonical programs; a valid program that matches none is run by the
+// generic interpreter (program.cu) exactly as its stages say.
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -109,7 +109,8 @@ void validate(const aml_pattern& pat, int p) {
   AML_REQUIRE(pat.stages != nullptr && pat.n_stages >= 1 && pat.n_stages <= 32, AML_EINVAL,
               where(p, 0) + "a pattern needs 1..32 stages");
   AML_REQUIRE(pat.delta >= 0, AML_EINVAL, where(p, 0) + "delta must be >= 0");
-  AML_REQUIRE(pat.reserved == 0, AML_EINVAL, where(p, 0) + "reserved field must be 0");
+  AML_REQUIRE((pat.flags & ~AML_PAT_INTERPRET) == 0, AML_EINVAL,
+              where(p, 0) + "unknown pattern flag bits");
   AML_REQUIRE(pat.aggregate >= AML_AGG_EDGES && pat.aggregate <= AML_AGG_INSTANCES, AML_EINVAL,
               where(p, 0) + "unknown aggregate");
   const aml_stage& t = pat.stages[0];
@@ -149,8 +150,37 @@ void validate(const aml_pattern& pat, int p) {
 
 }  // namespace
 
-// Maps every pattern onto a column; throws Failure on error.
-std::vector<Column> plan_patterns(const aml_pattern* pats, int n) {
+// The generic interpreter's form of a valid program, or a Failure naming
+// why the interpreter cannot run it.
+static Prog interpretable(const aml_pattern& pat, int p) {
+  AML_REQUIRE(pat.n_stages <= PROG_MAX_STAGES, AML_EUNSUPPORTED,
+              where(p, 0) + "no family matches and the interpreter runs at most 8 stages");
+  Prog g;
+  std::memset(&g, 0, sizeof(g));
+  g.n = pat.n_stages;
+  g.agg = pat.aggregate;
+  g.delta = pat.delta;
+  for (int s = 0; s < pat.n_stages; ++s) {
+    const aml_stage& x = pat.stages[s];
+    AML_REQUIRE(!(x.op == AML_OP_FOR_ALL && x.order == AML_ORDER_LEG), AML_EUNSUPPORTED,
+                where(p, s) + "LEG order is defined for INTERSECT stages only");
+    ProgStage& q = g.st[s];
+    q.op = (int8_t)x.op;
+    q.a_var = (int8_t)x.a_var;
+    q.a_dir = (int8_t)x.a_dir;
+    q.b_var = (int8_t)(x.op == AML_OP_INTERSECT ? x.b_var : -1);
+    q.b_dir = (int8_t)(x.op == AML_OP_INTERSECT ? x.b_dir : 0);
+    q.out_var = (int8_t)x.out_var;
+    q.order = (int8_t)x.order;
+    q.window = (int8_t)x.window;
+    q.skip = s == 0 ? 0u : x.skip_eq;
+  }
+  return g;
+}
+
+// Maps every pattern onto a column (a family, else the interpreter); throws
+// Failure on error.
+std::vector<Column> plan_patterns(const aml_pattern* pats, int n, std::vector<Prog>* progs) {
   AML_REQUIRE(pats != nullptr && n >= 1, AML_EINVAL, "need at least one pattern");
   static const std::vector<Template> tpl = templates();
   std::vector<Column> cols;
@@ -159,6 +189,7 @@ std::vector<Column> plan_patterns(const aml_pattern* pats, int n) {
     const aml_pattern& pat = pats[p];
     int fam = -1, k = 0;
     for (const Template& t : tpl) {
+      if (pat.flags & AML_PAT_INTERPRET) break;
       if ((int)t.stages.size() != pat.n_stages || t.aggregate != pat.aggregate) continue;
       bool ok = true;
       for (int s = 0; s < pat.n_stages && ok; ++s) ok = same_stage(pat.stages[s], t.stages[s]);
@@ -168,8 +199,11 @@ std::vector<Column> plan_patterns(const aml_pattern* pats, int n) {
         break;
       }
     }
-    AML_REQUIRE(fam >= 0, AML_EUNSUPPORTED,
-                where(p, 0) + "valid stage program, but no implemented pattern family matches it");
+    if (fam < 0) {
+      progs->push_back(interpretable(pat, p));
+      cols.push_back(Column{AML_FAM_PROGRAM, 0, pat.delta, (int32_t)progs->size() - 1});
+      continue;
+    }
     cols.push_back(Column{fam, k, pat.delta});
   }
   return cols;

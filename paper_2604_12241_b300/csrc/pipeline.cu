@@ -186,6 +186,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   AssembleParams P;
   std::memset(&P, 0, sizeof(P));
   int n_acc = 0;
+  std::vector<std::pair<int, int>> programs;  // (accumulator slot, program)
   for (int c = 0; c < ncols; ++c) {
     const Column& col = ps->cols[c];
     int didx = -1;
@@ -224,6 +225,12 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
         if (wp.cycw.slot[col.k] < 0) wp.cycw.slot[col.k] = n_acc++;
         wp.Kw = std::max(wp.Kw, (int)col.k);
         cd.acc_slot = wp.cycw.slot[col.k];
+        break;
+      case AML_FAM_PROGRAM:
+        AML_REQUIRE(new_from == 0, AML_EUNSUPPORTED,
+                    "interpreted stage programs are not counted incrementally");
+        cd.acc_slot = n_acc++;
+        programs.emplace_back(cd.acc_slot, col.prog);
         break;
       default: break;
     }
@@ -539,6 +546,9 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       }
     window_cycle_search(g, gv, wp.delta, wp.Kw, wp.cycw, sw, acc.p, s);
   }
+  // stage programs no family implements: the generic interpreter
+  for (const auto& pr : programs)
+    run_program(gv, ps->progs[pr.second], acc.p + (int64_t)pr.first * E, s);
   AML_LAUNCH("k_assemble", s,
              k_assemble<<<grid_for(E, ASM_BLOCK), ASM_BLOCK,
                           (size_t)ASM_BLOCK * (ncols | 1) * sizeof(uint32_t), s>>>(P));

@@ -177,9 +177,12 @@ aml_status aml_stream_open(const aml_pattern_set* ps, int32_t n_nodes, int32_t r
     AML_REQUIRE(ps && out, AML_EINVAL, "NULL argument");
     AML_REQUIRE(n_nodes >= 1, AML_EINVAL, "n_nodes must be >= 1");
     st = new aml_stream();
-    for (const Column& c : ps->cols)
+    for (const Column& c : ps->cols) {
       AML_REQUIRE(c.family != AML_FAM_CYCW, AML_EUNSUPPORTED,
                   "window cycles (CYCW) are not counted incrementally");
+      AML_REQUIRE(c.family != AML_FAM_PROGRAM, AML_EUNSUPPORTED,
+                  "interpreted stage programs are not counted incrementally");
+    }
     st->ps = *ps;
     st->P = (int32_t)ps->cols.size();
     st->N = n_nodes;

@@ -17,7 +17,7 @@ ORDER_NONE, ORDER_AFTER, ORDER_BEFORE, ORDER_LEG, ORDER_AFTER_TRIGGER = 0, 1, 2,
 WIN_TRAILING, WIN_SPAN = 0, 1
 AGG_EDGES, AGG_DISTINCT, AGG_INSTANCES = 0, 1, 2
 FAM_NAMES = {0: "DEG_OUT", 1: "DEG_IN", 2: "FAN_OUT", 3: "FAN_IN", 4: "GS", 5: "SG", 6: "CYC",
-             7: "CYCW"}
+             7: "CYCW", 8: "PROGRAM"}
 
 DAY = 86400
 WEEK = 7 * DAY
@@ -42,6 +42,22 @@ class Pattern:
     aggregate: int
     delta: int
     name: str = ""
+    # run through the generic interpreter even when a family matches (a
+    # program no family matches is interpreted anyway)
+    interpret: bool = False
+
+
+def program(stages, aggregate: int, delta: int, name: str = "",
+            interpret: bool = False) -> Pattern:
+    """A pattern from (op, a_var, a_dir, b_var, b_dir, out_var, order, window,
+    skip_eq) tuples or Stage objects, stage 0 the trigger."""
+    st = tuple(s if isinstance(s, Stage) else Stage(*[int(v) for v in s]) for s in stages)
+    return Pattern(st, int(aggregate), int(delta), name, interpret)
+
+
+def interpreted(p: Pattern) -> Pattern:
+    """The same program, forced through the generic interpreter."""
+    return dataclasses.replace(p, interpret=True)
 
 
 def _skip(*vars_: int) -> int:

@@ -85,19 +85,39 @@ def test_planner_rejects_invalid_programs():
     assert _err([_raw([T, P.Stage(P.OP_FOR_ALL, 0, P.DIR_OUT, out_var=2)], agg=7)]) == "AML_EINVAL"
 
 
-def test_planner_reports_unsupported_programs():
+def test_planner_interprets_programs_no_family_matches():
     T = P.TRIGGER
-    # valid, but an in-neighbour chain is not an implemented family
+    # valid, but an in-neighbour chain is no implemented family: interpreted
     prog = _raw([T, P.Stage(P.OP_FOR_ALL, 1, P.DIR_IN, out_var=2, order=P.ORDER_AFTER,
                             window=P.WIN_SPAN)])
-    assert _err([prog]) == "AML_EUNSUPPORTED"
     # a cycle whose middle stage forgets to skip N0 is not the simple-cycle family
-    bad = P.cycle(4, 10)
-    st = list(bad.stages)
+    st = list(P.cycle(4, 10).stages)
     st[1] = P.Stage(P.OP_FOR_ALL, 1, P.DIR_OUT, out_var=2, order=P.ORDER_AFTER,
                     window=P.WIN_SPAN, skip_eq=0b10)
-    assert _err([_raw(st)]) == "AML_EUNSUPPORTED"
-    assert "no implemented pattern family" in _lib.lib().aml_last_error().decode()
+    ps = _ps([prog, _raw(st), P.interpreted(P.gather_scatter(10)), P.gather_scatter(10)])
+    fams = [c["family"] for c in ps.columns]
+    assert fams == [8, 8, 8, 4]
+    assert [c["name"] for c in ps.columns[:3]] == ["PROGRAM0@10", "PROGRAM1@10", "PROGRAM2@10"]
+
+
+def test_planner_reports_programs_beyond_the_interpreter():
+    T = P.TRIGGER
+    # LEG order is defined for INTERSECT stages only
+    leg = _raw([T, P.Stage(P.OP_FOR_ALL, 1, P.DIR_OUT, out_var=2, order=P.ORDER_LEG,
+                           window=P.WIN_SPAN)])
+    assert _err([leg]) == "AML_EUNSUPPORTED"
+    assert "LEG order" in _lib.lib().aml_last_error().decode()
+    # nine stages that are no cycle: beyond the interpreter's eight
+    chain = [T] + [P.Stage(P.OP_FOR_ALL, v, P.DIR_OUT, out_var=v + 1, window=P.WIN_SPAN)
+                   for v in range(1, 9)]
+    assert _err([_raw(chain)]) == "AML_EUNSUPPORTED"
+    assert "at most 8 stages" in _lib.lib().aml_last_error().decode()
+    # unknown pattern flag bits
+    bad = _raw([T, P.Stage(P.OP_FOR_ALL, 0, P.DIR_OUT, out_var=2)])
+    arr, keep = _lib.make_patterns([bad])
+    arr[0].flags = 0x6
+    h = ctypes.c_void_p()
+    assert _lib.lib().aml_pattern_set_create(arr, 1, ctypes.byref(h)) == 1
 
 
 def test_argument_errors_need_no_device():

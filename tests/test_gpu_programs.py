@@ -1,0 +1,115 @@
+"""The generic interpretation of stage programs on the GPU against the
+oracle's (og_program_count), bit-exact: programs no family matches, every
+family's own program forced through the interpreter, and pattern sets that
+mix interpreted and family columns; tiny random graphs with ties and
+self-loops, and the tiny-10k workload.  The interpreter's refusals
+(captured mines, streams, the work limit) are errors, not wrong counts."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import aml_synth
+import oracle
+import paper_2604_12241_b300 as aml
+from paper_2604_12241_b300 import patterns as P
+from programs import NOVEL, F, T, OUT, NONE, SPAN, EDGES
+
+pytestmark = pytest.mark.gpu
+
+
+def _tuples(pattern):
+    return [dataclasses.astuple(s) for s in pattern.stages]
+
+
+def _mine(g, pats):
+    graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes)
+    out = aml.mine(graph, aml.PatternSet(pats)).cpu().numpy().view(np.uint32)
+    graph.close()
+    return out
+
+
+def _family_programs(delta):
+    out = [P.deg_out(delta), P.fan_in(delta), P.gather_scatter(delta, mirrored=True),
+           P.scatter_gather(delta), P.scatter_gather(delta, trigger="gather")]
+    for k in (2, 3, 4):
+        out.append(P.cycle(k, delta))
+    out += [P.cycle(4, delta, closing="intersect"), P.window_cycle(3, delta)]
+    return [P.interpreted(p) for p in out]
+
+
+def test_novel_programs_are_interpreted():
+    ps = aml.PatternSet([P.program(st, agg, 5) for st, agg in NOVEL.values()])
+    assert all(c["family"] == 8 and c["name"].startswith("PROGRAM") for c in ps.columns)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_programs_match_oracle_on_tiny_graphs(seed):
+    g = aml_synth.tiny_random(4 + seed % 5, 60 + 20 * seed, 30, 300 + seed,
+                              self_loops=(seed % 2 == 0))
+    og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
+    for delta in (0, 7, 1000):
+        pats = [P.program(st, agg, delta) for st, agg in NOVEL.values()]
+        pats += _family_programs(delta)
+        got = _mine(g, pats)
+        for j, p in enumerate(pats):
+            want = og.program_count(_tuples(p), p.aggregate, p.delta, threads=4)
+            np.testing.assert_array_equal(got[:, j], want,
+                                          err_msg=f"column {j} ({p.name}), delta {delta}")
+
+
+def test_programs_match_oracle_on_tiny10k():
+    g = aml_synth.workload("tiny-10k")
+    og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
+    pats = [P.program(st, agg, P.DAY) for st, agg in NOVEL.values()]
+    pats += _family_programs(P.DAY)
+    # family columns beside the interpreted ones in the same mine
+    fam = P.standard(P.DAY)
+    got = _mine(g, pats + fam)
+    for j, p in enumerate(pats):
+        want = og.program_count(_tuples(p), p.aggregate, p.delta)
+        np.testing.assert_array_equal(got[:, j], want, err_msg=p.name or f"program {j}")
+    want_fam = og.count_all(P.oracle_columns(fam))
+    np.testing.assert_array_equal(got[:, len(pats):], want_fam)
+    # interpreted family programs reproduce their families (SG twice over)
+    names = [p.name for p in pats]
+    sg = got[:, names.index(f"SG@{P.DAY}")]
+    np.testing.assert_array_equal(sg.astype(np.uint64),
+                                  want_fam[:, 5].astype(np.uint64) * 2)
+
+
+def test_interpreted_columns_are_refused_where_unsupported():
+    import torch
+    g = aml_synth.tiny_random(10, 200, 50, 3)
+    graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes)
+    st, agg = NOVEL["path3"]
+    ps = aml.PatternSet([P.program(st, agg, 20)])
+    out = torch.zeros((g.n_edges, 1), dtype=torch.int32, device="cuda")
+    with pytest.raises(aml.AmlError) as ei:
+        aml.mine(graph, ps, out=out, use_graph=True)
+    assert ei.value.name == "AML_EUNSUPPORTED"
+    with pytest.raises(aml.AmlError) as ei:
+        aml.Stream(ps, g.n_nodes, resident_window=100)
+    assert ei.value.name == "AML_EUNSUPPORTED"
+    graph.close()
+
+
+def test_work_limit_ends_the_launch_with_an_error():
+    """Seven nested loops over ~5,000 parallel edges per node: far more than
+    2^34 candidate visits.  The launch stops at the limit and the call
+    reports it; the graph stays usable."""
+    rng = np.random.default_rng(1)
+    E, N = 20000, 4
+    src = rng.integers(0, N, E).astype(np.int32)
+    dst = ((src + 1 + rng.integers(0, N - 1, E)) % N).astype(np.int32)
+    ts = np.sort(rng.integers(0, 1000, E)).astype(np.int32)
+    graph = aml.Graph(src, dst, ts, N)
+    chain = [T] + [F(v, OUT, v + 1, NONE, SPAN) for v in range(1, 8)]
+    with pytest.raises(aml.AmlError) as ei:
+        aml.mine(graph, aml.PatternSet([P.program(chain, EDGES, 10**6)]))
+    assert ei.value.name == "AML_EUNSUPPORTED" and "limit" in str(ei.value)
+    # the graph still mines normally afterwards
+    out = aml.mine(graph, aml.PatternSet([P.deg_out(100)])).cpu().numpy().view(np.uint32)
+    og = oracle.OracleGraph(src, dst, ts, N)
+    np.testing.assert_array_equal(out[:, 0], og.count_all([("deg_out", 100)])[:, 0])
+    graph.close()
