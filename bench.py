@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--stream-batches", type=int, default=30)
     ap.add_argument("--no-window-cycles", action="store_true",
                     help="skip timing the window-cycle columns (CYCW3..5 at the workload's windows)")
+    ap.add_argument("--no-programs", action="store_true",
+                    help="skip timing stage programs run by the generic interpreter")
     return ap.parse_args()
 
 
@@ -298,6 +300,66 @@ def time_window_cycles(graph, pats, E, use_graph, stream, flush, reps=5) -> dict
                         for k, (n, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])[:6]},
             "timing": f"median of {reps} mines, CUDA events, L2 flushed between mines",
             "note": note}
+
+
+def time_programs(graph, E, stream, flush, reps=3) -> dict:
+    """Stage programs run by the generic interpreter on the resident graph
+    (24-hour window), and one family program both ways (the family's kernels
+    and the interpreter) for comparison: median of `reps` CUDA-event timed
+    mines after one warm-up."""
+    import torch
+
+    import paper_2604_12241_b300 as aml
+    from paper_2604_12241_b300 import patterns as P
+
+    D = P.DAY
+    T = P.TRIGGER
+
+    def F(a, d, out, order, skip=0, window=P.WIN_SPAN):
+        return P.Stage(P.OP_FOR_ALL, a, d, -1, 0, out, order, window, skip)
+
+    progs = {
+        # N0 -> N1 -> N2 -> N3, every hop later, within 24 hours
+        "path3": P.program([T, F(1, P.DIR_OUT, 2, P.ORDER_AFTER, 0b1),
+                            F(2, P.DIR_OUT, 3, P.ORDER_AFTER, 0b11)], P.AGG_INSTANCES, D),
+        # common counterparties of N0 and N1 (an INTERSECT stage)
+        "common_out": P.program([T, P.Stage(P.OP_INTERSECT, 0, P.DIR_OUT, 1, P.DIR_OUT, 2,
+                                            P.ORDER_NONE, P.WIN_SPAN, 0b11)],
+                                P.AGG_INSTANCES, D),
+        # distinct senders into the trigger's later receivers (DISTINCT)
+        "distinct_2hop": P.program([T, F(1, P.DIR_OUT, 2, P.ORDER_AFTER_TRIGGER, 0b1),
+                                    F(2, P.DIR_IN, 3, P.ORDER_NONE, 0, P.WIN_TRAILING)],
+                                   P.AGG_DISTINCT, D),
+        "GS@86400 interpreted": P.interpreted(P.gather_scatter(D)),
+        "GS@86400 family kernels": P.gather_scatter(D),
+        "CYC3@86400 interpreted": P.interpreted(P.cycle(3, D)),
+        "CYC3@86400 family kernels": P.cycle(3, D),
+    }
+    res = {}
+    out = torch.empty((E, 1), dtype=torch.int32, device="cuda")
+    for name, pat in progs.items():
+        ps = aml.PatternSet([pat])
+        try:
+            aml.mine(graph, ps, out=out, stream=stream)
+            torch.cuda.synchronize()
+        except aml.AmlError as err:
+            res[name] = {"unavailable": str(err)}
+            continue
+        ts_ = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            aml.mine(graph, ps, out=out, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ts_.append(a.elapsed_time(b))
+        ms = float(np.median(ts_))
+        total = int(out.cpu().numpy().view(np.uint32).astype(np.uint64).sum())
+        res[name] = {"column": ps.columns[0]["name"], "ms_per_mine": round(ms, 3),
+                     "edges_per_s": E / ms * 1e3, "sum_of_counts": total}
+    return {"programs": res, "timing": f"median of {reps} mines, CUDA events, L2 flushed "
+            "between mines; one column per mine, plain launches"}
 
 
 # --------------------------------------------------------------- reference
@@ -662,6 +724,8 @@ def run_ours(args, ws, rank, local):
             line["cpu_baseline"] = cpu_baseline(g, pats, args.cpu_seconds)
         if not args.no_window_cycles:
             line["window_cycles"] = time_window_cycles(graph, pats, E, use_graph, stream, flush)
+        if not args.no_programs:
+            line["interpreter"] = time_programs(graph, E, stream, flush)
     graph.close()
     if not args.no_stream:
         stream = run_stream(args, rank)

@@ -124,6 +124,27 @@ def scatter_gather(delta: int, trigger: str = "scatter") -> Pattern:
     return Pattern(stages, AGG_INSTANCES, delta, f"SG@{delta}")
 
 
+def scatter_gather_n(n: int, delta: int) -> Pattern:
+    """Sec. 4's "at least N" placement accounts: a scatter-gather with n
+    intermediaries, n >= 2.  Trigger N0 -> N1 (s -> m1), N1.out -> N2 (the
+    destination d, later), then n - 1 intersections of N0.out with N2.in,
+    each a further intermediary distinct from the ones before, its two edges
+    in order; all 2n edges within delta.  Run by the generic interpreter: an
+    edge's count is the number of ordered n-tuples of such legs it belongs
+    to, n! * C(k - 1, n - 1) on each edge of an isolated k-intermediary
+    scatter-gather, so it is nonzero exactly when the edge takes part in a
+    scatter-gather with at least n intermediaries."""
+    if not 2 <= n <= 7:
+        raise ValueError("n must be in [2, 7] (the interpreter runs at most 8 stages)")
+    stages = [TRIGGER, Stage(OP_FOR_ALL, 1, DIR_OUT, out_var=2, order=ORDER_AFTER,
+                             window=WIN_SPAN, skip_eq=_skip(0))]
+    for i in range(n - 1):
+        stages.append(Stage(OP_INTERSECT, 0, DIR_OUT, 2, DIR_IN, out_var=3 + i,
+                            order=ORDER_LEG, window=WIN_SPAN,
+                            skip_eq=_skip(1, *range(3, 3 + i))))
+    return Pattern(tuple(stages), AGG_INSTANCES, delta, f"SG{n}@{delta}", interpret=True)
+
+
 def cycle(k: int, delta: int, closing: str = "for_all") -> Pattern:
     """k-cycle: trigger N0 -> N1, then N_i.out -> N_{i+1} (later, new node),
     closed by an edge back into N0 -- or, for k >= 3, by intersecting

@@ -63,6 +63,7 @@ def test_programs_match_oracle_on_tiny10k():
     og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
     pats = [P.program(st, agg, P.DAY) for st, agg in NOVEL.values()]
     pats += _family_programs(P.DAY)
+    pats += [P.scatter_gather_n(n, P.DAY) for n in (3, 4)]  # "at least N" intermediaries
     # family columns beside the interpreted ones in the same mine
     fam = P.standard(P.DAY)
     got = _mine(g, pats + fam)

@@ -9,8 +9,12 @@
   by brute force): DEG/FAN through EDGES/DISTINCT, GS and CYC_k and CYCW_k
   through INSTANCES, and SG twice over (each pair of legs is found once from
   each scatter edge, or once from each gather edge);
-* a program with contradictory constraints counts nothing.
+* a program with contradictory constraints counts nothing;
+* the n-intermediary scatter-gather programs ("at least N", Sec. 4) give
+  n! * C(k - 1, n - 1) on every edge of a planted isolated k-intermediary
+  scatter-gather, and 0 when k < n.
 """
+import math
 import dataclasses
 
 import numpy as np
@@ -77,3 +81,42 @@ def test_family_programs_interpreted_generically(seed):
             np.testing.assert_array_equal(got.astype(np.uint64),
                                           fam[:, j].astype(np.uint64) * factor,
                                           err_msg=f"{pat.name} (seed {seed})")
+
+
+def test_n_intermediary_scatter_gather_closed_form():
+    g = aml_synth.workload("tiny-10k")
+    og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
+    fresh = [m for m in g.motifs if m.kind == "sg" and m.fresh]
+    assert len(fresh) >= 10 and {m.k for m in fresh} >= {2, 3, 4}
+    for n in (2, 3, 4):
+        pat = P.scatter_gather_n(n, P.DAY)
+        got = og.program_count(_tuples(pat), pat.aggregate, pat.delta)
+        for m in fresh:
+            want = math.factorial(n) * math.comb(m.k - 1, n - 1) if m.k >= n else 0
+            assert (got[m.edges] == want).all(), (n, m.k, got[m.edges])
+
+
+def test_n_intermediary_scatter_gather_brute_force():
+    """Legs s -> m -> d through four candidate intermediaries at random times
+    (some out of order, one repeated), plus noise edges."""
+    pat = P.scatter_gather_n(3, 0)
+    n_nonzero = 0
+    for seed in range(5):
+        rng = np.random.default_rng(900 + seed)
+        src, dst = [], []
+        for m in range(2, 6):
+            for _ in range(1 + (m == 2)):
+                src += [0, m]
+                dst += [m, 1]
+        for _ in range(2):
+            a, b = rng.integers(0, 6, 2)
+            src.append(int(a))
+            dst.append(int(b))
+        ts = rng.integers(0, 8, len(src))
+        og = oracle.OracleGraph(src, dst, ts, 6)
+        for delta in (3, 1000):
+            want = brute_program(src, dst, ts, _tuples(pat), pat.aggregate, delta)
+            got = og.program_count(_tuples(pat), pat.aggregate, delta, threads=2)
+            np.testing.assert_array_equal(got, want, err_msg=f"seed {seed}, delta {delta}")
+            n_nonzero += int(want.any())
+    assert n_nonzero >= 3
