@@ -5,10 +5,12 @@
 // the stage's node and testing its skip_if and time constraints, and at the
 // last stage the Postprocess that reports the binding.  One thread walks the
 // bindings of one trigger edge depth first, with an explicit stack of at
-// most seven stages.  Each stage's loop starts where its time constraints
-// allow (Find_Starting_Edge: binary searches in the operand's (t, id)-sorted
-// list for the window, the span so far and the order bound) and stops where
-// they end; an INTERSECT stage finds its b-side edges by binary search in
+// most seven stages; a trigger with more than 64 first-stage candidates is
+// queued and walked by a whole warp, lane i taking every 32nd candidate.
+// Each stage's loop starts where its time constraints allow
+// (Find_Starting_Edge: binary searches in the operand's (t, id)-sorted list
+// for the window, the span so far and the order bound) and stops where they
+// end; an INTERSECT stage finds its b-side edges by binary search in
 // the (counterparty, t, id) copy of the second operand's list.  The exact
 // conditions (ties broken by edge id, skip masks, closing onto a bound node,
 // pairwise distinct edges of an instance) are tested per candidate.
@@ -20,6 +22,7 @@
 // candidate visits and reports it, so a program with an enormous search
 // space ends with an error instead of holding the GPU.
 #include <cstring>
+#include <type_traits>
 
 #include "aml_internal.cuh"
 #include "mine.cuh"
@@ -38,9 +41,17 @@ constexpr unsigned long long SET_EMPTY = ~0ull;
 struct ProgCtl {
   unsigned long long work;  // candidate visits of the launch so far
   uint32_t stop;            // set once the limit is crossed
-  uint32_t pad;
+  uint32_t n_heavy;         // triggers left to a whole warp
   unsigned long long total; // DISTINCT: bindings counted by the first pass
+  unsigned long long next;  // next heavy trigger a warp takes
 };
+
+// A trigger whose first stage has more candidates than this is walked by a
+// whole warp (each lane takes every 32nd first-stage candidate) instead of
+// one thread, so hub triggers do not leave one lane working long after the
+// rest of the GPU is idle.
+constexpr int32_t PROG_HEAVY = 64;
+constexpr unsigned long long PROG_DEFERRED = ~0ull;
 
 // one direction's lists: (t, id) order and the (counterparty, t, id) copy
 struct ListView {
@@ -83,14 +94,16 @@ __device__ bool set_insert(unsigned long long* table, uint64_t mask, unsigned lo
   return false;  // not reached: the table holds at least twice the keys
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(PROG_BLOCK) k_program(GraphView g, Prog p,
-                                                        unsigned long long* __restrict__ out,
-                                                        unsigned long long* __restrict__ table,
-                                                        uint64_t table_mask, ProgCtl* ctl) {
-  const int64_t e64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e64 >= g.E) return;
-  const int32_t e0 = (int32_t)e64;
+// The bindings of trigger e0: returns the trigger's count (EDGES, DISTINCT),
+// or PROG_DEFERRED when a single thread (WARP false) finds the first stage
+// heavy and queues the trigger for a warp.  With WARP, lane `lane` of the
+// warp walks the first-stage candidates lane, lane + 32, ...
+template <int MODE, bool WARP>
+__device__ __forceinline__ unsigned long long walk(const GraphView& g, const Prog& p, int32_t e0,
+                                                   int lane, unsigned long long* __restrict__ out,
+                                                   unsigned long long* __restrict__ table,
+                                                   uint64_t table_mask, ProgCtl* ctl,
+                                                   int32_t* __restrict__ heavy) {
   const int32_t t0 = g.ts[e0];
   const int n = p.n;
   const int64_t delta = p.delta;
@@ -101,10 +114,7 @@ __global__ void __launch_bounds__(PROG_BLOCK) k_program(GraphView g, Prog p,
   int32_t smin[PROG_MAX_STAGES], smax[PROG_MAX_STAGES];
   node[0] = g.src[e0];
   node[1] = g.dst[e0];
-  if (node[0] == node[1]) {  // self-loops are in no list; their rows stay 0
-    if (MODE != AGG_CREDIT) out[e0] = 0;
-    return;
-  }
+  if (node[0] == node[1]) return 0;  // self-loops are in no list; their rows stay 0
   reach_e[0] = reach_e[1] = e0;
   reach_t[0] = reach_t[1] = t0;
   nb[1] = 2;
@@ -195,7 +205,8 @@ __global__ void __launch_bounds__(PROG_BLOCK) k_program(GraphView g, Prog p,
       while (cur[s] < hi[s]) {
         tick();
         if (stopped) return false;
-        const int32_t i = cur[s]++;
+        const int32_t i = cur[s];
+        cur[s] += (WARP && s == 1) ? 32 : 1;
         const int32_t f = LA.eid[i], x = LA.nbr[i], tf = LA.t[i];
         if (q.order == AML_ORDER_AFTER && !before(reach_t[A], reach_e[A], tf, f)) continue;
         if (q.order == AML_ORDER_BEFORE && !before(tf, f, reach_t[A], reach_e[A])) continue;
@@ -235,7 +246,8 @@ __global__ void __launch_bounds__(PROG_BLOCK) k_program(GraphView g, Prog p,
       if (cur[s] >= hi[s]) return false;
       tick();
       if (stopped) return false;
-      const int32_t i = cur[s]++;
+      const int32_t i = cur[s];
+      cur[s] += (WARP && s == 1) ? 32 : 1;
       const int32_t fa = LA.eid[i], x = LA.nbr[i], tfa = LA.t[i];
       bhi[s] = bcur[s] = 0;
       if (q.order == AML_ORDER_AFTER && !before(reach_t[A], reach_e[A], tfa, fa)) continue;
@@ -268,10 +280,15 @@ __global__ void __launch_bounds__(PROG_BLOCK) k_program(GraphView g, Prog p,
   };
 
   if (n == 1) {
-    complete(node[1]);
+    if (!WARP || lane == 0) complete(node[1]);
   } else {
     int s = 1;
     enter(1);
+    if (!WARP && heavy && hi[1] - cur[1] > PROG_HEAVY) {
+      heavy[atomicAdd(&ctl->n_heavy, 1u)] = e0;
+      return PROG_DEFERRED;
+    }
+    if (WARP) cur[1] += lane;
     while (s >= 1) {
       if (!next(s)) {
         if (stopped) break;
@@ -286,7 +303,45 @@ __global__ void __launch_bounds__(PROG_BLOCK) k_program(GraphView g, Prog p,
       }
     }
   }
-  if (MODE != AGG_CREDIT) out[e0] = found;
+  return found;
+}
+
+// one thread per trigger edge; heavy triggers are queued for k_program_warp
+template <int MODE>
+__global__ void __launch_bounds__(PROG_BLOCK) k_program(GraphView g, Prog p,
+                                                        unsigned long long* __restrict__ out,
+                                                        unsigned long long* __restrict__ table,
+                                                        uint64_t table_mask, ProgCtl* ctl,
+                                                        int32_t* __restrict__ heavy) {
+  const int64_t e64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e64 >= g.E) return;
+  const int32_t e0 = (int32_t)e64;
+  const unsigned long long f =
+      walk<MODE, false>(g, p, e0, 0, out, table, table_mask, ctl, heavy);
+  if (MODE != AGG_CREDIT && f != PROG_DEFERRED) out[e0] = f;
+}
+
+// the queued heavy triggers, one warp each, taken from a shared cursor by
+// resident warps
+template <int MODE>
+__global__ void __launch_bounds__(PROG_BLOCK) k_program_warp(GraphView g, Prog p,
+                                                             unsigned long long* __restrict__ out,
+                                                             unsigned long long* __restrict__ table,
+                                                             uint64_t table_mask, ProgCtl* ctl,
+                                                             const int32_t* __restrict__ heavy) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long n_heavy = ctl->n_heavy;
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(&ctl->next, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n_heavy || *(volatile uint32_t*)&ctl->stop) return;
+    const int32_t e0 = heavy[item];
+    unsigned long long f =
+        walk<MODE, true>(g, p, e0, lane, out, table, table_mask, ctl, nullptr);
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
+    if (MODE != AGG_CREDIT && lane == 0) out[e0] = f;
+  }
 }
 
 __global__ void k_sum_u64(const unsigned long long* __restrict__ v, int64_t n,
@@ -306,8 +361,10 @@ void run_program(const GraphView& gv, const Prog& p, unsigned long long* out, cu
   const int64_t E = gv.E;
   if (E == 0) return;
   DBuf<ProgCtl> ctl(1, s);
+  DBuf<int32_t> heavy((size_t)E, s);
   AML_CUDA(cudaMemsetAsync(ctl.p, 0, sizeof(ProgCtl), s));
   const unsigned grid = grid_for(E, PROG_BLOCK);
+  const unsigned warp_grid = (unsigned)sm_count() * 8;  // resident warps take the queue
   auto check_stop = [&](unsigned long long* total) {
     ProgCtl h;
     const SmallRead rd{&h, ctl.p, (uint32_t)sizeof(ProgCtl)};
@@ -316,16 +373,23 @@ void run_program(const GraphView& gv, const Prog& p, unsigned long long* out, cu
                 "interpreted stage program stopped at the limit of 2^34 candidate edges");
     if (total) *total = h.total;
   };
+  // one pass: a thread per trigger, then a warp per heavy trigger
+  auto pass = [&](auto mode, unsigned long long* table, uint64_t mask) {
+    constexpr int M = decltype(mode)::value;
+    AML_LAUNCH("k_program", s,
+               k_program<M><<<grid, PROG_BLOCK, 0, s>>>(gv, p, out, table, mask, ctl.p,
+                                                        heavy.p));
+    AML_LAUNCH("k_program_warp", s,
+               k_program_warp<M><<<warp_grid, PROG_BLOCK, 0, s>>>(gv, p, out, table, mask,
+                                                                  ctl.p, heavy.p));
+  };
   if (p.agg == AML_AGG_INSTANCES) {
-    AML_LAUNCH("k_program", s,
-               k_program<AGG_CREDIT><<<grid, PROG_BLOCK, 0, s>>>(gv, p, out, nullptr, 0, ctl.p));
+    pass(std::integral_constant<int, AGG_CREDIT>{}, nullptr, 0);
   } else if (p.agg == AML_AGG_EDGES) {
-    AML_LAUNCH("k_program", s,
-               k_program<AGG_COUNT><<<grid, PROG_BLOCK, 0, s>>>(gv, p, out, nullptr, 0, ctl.p));
+    pass(std::integral_constant<int, AGG_COUNT>{}, nullptr, 0);
   } else {
     // bindings first, to size the set of (trigger, last node) keys
-    AML_LAUNCH("k_program", s,
-               k_program<AGG_COUNT><<<grid, PROG_BLOCK, 0, s>>>(gv, p, out, nullptr, 0, ctl.p));
+    pass(std::integral_constant<int, AGG_COUNT>{}, nullptr, 0);
     AML_LAUNCH("k_sum_u64", s,
                k_sum_u64<<<grid_for(E, 256), 256, 0, s>>>(out, E, &ctl.p->total));
     unsigned long long total = 0;
@@ -337,9 +401,7 @@ void run_program(const GraphView& gv, const Prog& p, unsigned long long* out, cu
     DBuf<unsigned long long> table((size_t)size, s);
     AML_CUDA(cudaMemsetAsync(table.p, 0xff, (size_t)size * 8, s));
     AML_CUDA(cudaMemsetAsync(ctl.p, 0, sizeof(ProgCtl), s));
-    AML_LAUNCH("k_program", s,
-               k_program<AGG_SET><<<grid, PROG_BLOCK, 0, s>>>(gv, p, out, table.p, size - 1,
-                                                             ctl.p));
+    pass(std::integral_constant<int, AGG_SET>{}, table.p, size - 1);
   }
   check_stop(nullptr);
 }
