@@ -300,22 +300,34 @@ __global__ void k_upd_rows(const int32_t* __restrict__ optr, const int32_t* __re
 }
 
 // per old row start: {new row start, dropped prefix, new edges' range in the
-// sorted batch}; read by every slot of the row through its old row start
+// sorted batch}, read by every slot of the row through its old row start;
+// per row: how far its kept slots move
 __global__ void k_upd_rowinfo(const int32_t* __restrict__ optr, const int32_t* __restrict__ ptr,
                               const int32_t* __restrict__ kdrop, const int32_t* __restrict__ bptr,
-                              int32_t N, int4* __restrict__ info) {
+                              int32_t N, int4* __restrict__ info, int32_t* __restrict__ shift) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   const int32_t lo = optr[r];
+  shift[r] = ptr[r] - lo - kdrop[r];
   if (optr[r + 1] > lo) info[lo] = make_int4(ptr[r], kdrop[r], bptr[r], bptr[r + 1]);
+}
+
+// slot of every kept edge: its old slot moved by its row's shift (edge
+// order, so the reads and writes are coalesced; self-loops stay -1)
+__global__ void k_upd_pos(const int32_t* __restrict__ opos, const int32_t* __restrict__ row_of,
+                          const int32_t* __restrict__ shift, int32_t drop, int64_t n_kept,
+                          int32_t* __restrict__ pos) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_kept) return;
+  const int32_t p = opos[e + drop];
+  pos[e] = p < 0 ? -1 : p + shift[row_of[e]];
 }
 
 __global__ void k_upd_keep(const int32_t* __restrict__ oeid, const int32_t* __restrict__ orstart,
                            const int32_t* __restrict__ onbr, const int32_t* __restrict__ ot,
                            const int4* __restrict__ info, int32_t drop, int64_t oEv,
                            int32_t* __restrict__ nbr, int32_t* __restrict__ t,
-                           int32_t* __restrict__ eid, int32_t* __restrict__ rstart,
-                           int32_t* __restrict__ pos) {
+                           int32_t* __restrict__ eid, int32_t* __restrict__ rstart) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= oEv) return;
   const int32_t e = oeid[p];
@@ -327,7 +339,6 @@ __global__ void k_upd_keep(const int32_t* __restrict__ oeid, const int32_t* __re
   t[q] = ot[p];
   eid[q] = e - drop;
   rstart[q] = ri.x;
-  pos[e - drop] = q;
 }
 
 // new edges in (row, id) order: after the row's kept slots
@@ -340,8 +351,11 @@ __global__ void k_upd_new(const uint32_t* __restrict__ bkey, const uint32_t* __r
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int32_t r = (int32_t)bkey[i];
-  if (r >= N) return;  // a self-loop
   const int32_t e = b0 + (int32_t)bperm[i];
+  if (r >= N) {  // a self-loop: in no row
+    pos[e] = -1;
+    return;
+  }
   const int32_t q = ptr[r + 1] - bptr[r + 1] + (int32_t)i;
   nbr[q] = other[e];
   t[q] = ts[e];
@@ -460,8 +474,8 @@ static void upd_sort_batch(BatchRows& b, const int32_t* row_of, const int32_t* o
 }
 
 static void upd_fill(const aml_graph* o, aml_graph* g, const Adj& ao, Adj& a, BatchRows& b,
-                     const int32_t* other, int32_t drop, int64_t n_new, cudaStream_t s,
-                     GraphAlloc& ga, int32_t* max_deg_dev) {
+                     const int32_t* row_of, const int32_t* other, int32_t drop, int64_t n_new,
+                     cudaStream_t s, GraphAlloc& ga, int32_t* max_deg_dev) {
   const int B = 256;
   const int64_t E = g->E, Ev = g->Ev, oEv = o->Ev;
   const int32_t N = g->N, b0 = (int32_t)(E - n_new);
@@ -475,19 +489,21 @@ static void upd_fill(const aml_graph* o, aml_graph* g, const Adj& ao, Adj& a, Ba
   a.nnbr = ga.get<int32_t>(Ev);
   a.nt = ga.get<int32_t>(Ev);
   a.neid = ga.get<int32_t>(Ev);
-  AML_CUDA(cudaMemsetAsync(a.pos, 0xff, (E ? E : 1) * sizeof(int32_t), s));
   AML_CUDA(cudaMemsetAsync(a.prev, 0xff, (Ev ? Ev : 1) * sizeof(int32_t), s));
   AML_LAUNCH("k_fill_i32", s, k_fill_i32<<<grid_for(Ev, B), B, 0, s>>>(a.next, Ev, INT32_MAX));
   DBuf<int4> info(oEv ? oEv : 1, s);
   DBuf<int32_t> kept(oEv + 1, s);
+  int32_t* shift = b.cnt.p;  // the counts are spent: the scan made the row pointers
   AML_LAUNCH("k_upd_rowinfo", s,
              k_upd_rowinfo<<<grid_for(N, B), B, 0, s>>>(ao.ptr, a.ptr, b.kdrop.p, b.bptr.p, N,
-                                                       info.p));
+                                                       info.p, shift));
   if (oEv)
     AML_LAUNCH("k_upd_keep", s,
                k_upd_keep<<<grid_for(oEv, B), B, 0, s>>>(ao.eid, ao.rstart, ao.nbr, ao.t, info.p,
-                                                        drop, oEv, a.nbr, a.t, a.eid, a.rstart,
-                                                        a.pos));
+                                                        drop, oEv, a.nbr, a.t, a.eid, a.rstart));
+  if (b0 > 0)
+    AML_LAUNCH("k_upd_pos", s,
+               k_upd_pos<<<grid_for(b0, B), B, 0, s>>>(ao.pos, row_of, shift, drop, b0, a.pos));
   if (n_new)
     AML_LAUNCH("k_upd_new", s,
                k_upd_new<<<grid_for(n_new, B), B, 0, s>>>(b.bkey.p, b.bperm.p, b.bptr.p, a.ptr,
@@ -568,8 +584,9 @@ aml_graph* update_graph(const aml_graph* o, int64_t drop, const int32_t* src, co
     read_small(rd, 2, s);
     AML_REQUIRE(ev[0] == ev[1], AML_EINTERNAL, "sliding update: out and in lists disagree");
     g->Ev = ev[0];
-    upd_fill(o, g, o->out, g->out, bo, g->dst, (int32_t)drop, n_new, s, ga, g->max_deg);
-    upd_fill(o, g, o->in, g->in, bi, g->src, (int32_t)drop, n_new, s, ga, g->max_deg + 1);
+    upd_fill(o, g, o->out, g->out, bo, g->src, g->dst, (int32_t)drop, n_new, s, ga, g->max_deg);
+    upd_fill(o, g, o->in, g->in, bi, g->dst, g->src, (int32_t)drop, n_new, s, ga,
+             g->max_deg + 1);
     return g;
   } catch (...) {
     cudaStreamSynchronize(s);

@@ -1121,30 +1121,42 @@ __global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
   const int tot = nrows * nc;
   uint32_t* out = P.counts + e0 * P.ld;
   const bool dense = P.ld == nc;  // the block's rows are one contiguous range
-  if (e0 < P.accumulate_from) {   // old rows keep what they hold
-    for (int i = threadIdx.x; i < tot; i += ASM_BLOCK) {
-      const int r = dense ? 0 : i / nc;
-      s_rows[i] = out[dense ? i : r * P.ld + (i - r * nc)];
+  if (e0 < P.accumulate_from) {
+    // a block with old rows (streaming): an old row keeps what it holds and
+    // only its instance columns with new instances change, so the row is
+    // updated in place where a count is not zero (most rows get none); the
+    // batch rows of the one block that also holds old rows are written
+    // whole, row by row
+    if ((int)threadIdx.x < nrows) {
+      const int64_t e64 = e0 + threadIdx.x;
+      const int32_t e = (int32_t)e64;
+      uint32_t* orow = out + (int64_t)threadIdx.x * P.ld;
+      const bool add = e64 < P.accumulate_from;
+      const bool loop = g.src[e] == g.dst[e];
+      for (int c = 0; c < nc; ++c) {
+        if (add) {
+          if (loop || !((P.inst_mask >> c) & 1ull)) continue;  // trailing windows never change
+          const uint64_t val = assemble_value(P, P.cols[c], e);
+          if (val == 0) continue;
+          const uint64_t sum = val + orow[c];
+          orow[c] = sum > 0xffffffffull ? 0xffffffffu : (uint32_t)sum;
+        } else {
+          const uint64_t val = loop ? 0 : assemble_value(P, P.cols[c], e);
+          orow[c] = val > 0xffffffffull ? 0xffffffffu : (uint32_t)val;
+        }
+      }
     }
-    __syncthreads();
+    return;
   }
   if ((int)threadIdx.x < nrows) {
-    const int64_t e64 = e0 + threadIdx.x;
-    const int32_t e = (int32_t)e64;
+    const int32_t e = (int32_t)(e0 + threadIdx.x);
     uint32_t* row = s_rows + threadIdx.x * nc;
-    const bool add = e64 < P.accumulate_from;  // an old row: add its new instances
     const int32_t u = g.src[e], v = g.dst[e];
     if (u == v) {
-      if (!add)
-        for (int c = 0; c < nc; ++c) row[c] = 0u;
+      for (int c = 0; c < nc; ++c) row[c] = 0u;
     } else {
       for (int c = 0; c < nc; ++c) {
-        if (add && !((P.inst_mask >> c) & 1ull)) continue;  // trailing windows never change
-        uint64_t val = assemble_value(P, P.cols[c], e);
-        if (add) {
-          if (val == 0) continue;
-          val += row[c];
-        }
+        const uint64_t val = assemble_value(P, P.cols[c], e);
         row[c] = val > 0xffffffffull ? 0xffffffffu : (uint32_t)val;
       }
     }
