@@ -444,6 +444,186 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit(GraphView g, const int2* __
   }
 }
 
+// ---------------------------------------------- legs for delta counting
+//
+// A streaming recount counts only the instances whose latest edge is new
+// (id >= new_from; the newest edges of every list).  Of anchor a's legs
+// (a, b), b in the window [q0, q1) of dst(a)'s out-list:
+//   new legs, b in the list's new suffix [qn, q1): GS and 2-cycle credits,
+//     sub-window credits, and SG records (their destination is a batch
+//     destination by definition);
+//   old legs: only SG records into a batch destination (the other leg of
+//     the pair may be new), found in the list's marked slots (those whose
+//     counterparty is a batch destination) inside [q0, qn);
+//   the cycle legs [q0, qc), whose anchors have a new closing edge.
+// So the old part of a hub's window is walked only where it can matter.
+// Used while the marked slots are a small share of all (few batch
+// destinations); otherwise walking every window contiguously (k_leg_emit)
+// is faster than visiting most slots through the marked list.
+
+// flag of every out-list slot whose counterparty is in the mask
+__global__ void k_mark_slots(const int32_t* __restrict__ nbr, int64_t Ev,
+                             const uint32_t* __restrict__ mask, int32_t* __restrict__ flag) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p <= Ev) flag[p] = p < Ev && in_mask(mask, nbr[p]);
+}
+
+// marked slots, compacted in slot order, and each node's range of them
+__global__ void k_compact_marked(const int32_t* __restrict__ flag_scan, int64_t Ev,
+                                 int32_t* __restrict__ mslot) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < Ev && flag_scan[p + 1] != flag_scan[p]) mslot[flag_scan[p]] = (int32_t)p;
+}
+
+__global__ void k_marked_ptr(const int32_t* __restrict__ optr, const int32_t* __restrict__ flag_scan,
+                             int32_t N, int32_t* __restrict__ mptr) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u <= N) mptr[u] = flag_scan[optr[u]];
+}
+
+// first i in [lo, hi) with v[i] >= x
+__device__ __forceinline__ int32_t lower_i32(const int32_t* __restrict__ v, int32_t lo, int32_t hi,
+                                             int32_t x) {
+  while (lo < hi) {
+    const int32_t mid = (int32_t)(((uint32_t)lo + (uint32_t)hi) >> 1);
+    if (__ldg(v + mid) < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// first slot of every out-list holding a new edge (new edges are the
+// newest, so they end every list)
+__global__ void k_first_new(const int32_t* __restrict__ optr, const int32_t* __restrict__ oeid,
+                            int32_t N, int32_t new_from, int32_t* __restrict__ first_new) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < N) first_new[u] = lower_i32(oeid, optr[u], optr[u + 1], new_from);
+}
+
+// f(owner lane, position or -1) over every lane's range [lo, hi), called by
+// all 32 lanes together: ranges up to own_max long one position per lane per
+// round, longer ones by the whole warp, one owner after another
+template <typename F>
+__device__ __forceinline__ void warp_ranges(int32_t lo, int32_t hi, int32_t own_max, F&& f) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const bool own = hi - lo <= own_max;
+  int32_t q = lo;
+  while (__any_sync(full, own && q < hi)) {
+    const bool in = own && q < hi;
+    f(lane, in ? q : -1);
+    if (in) ++q;
+  }
+  unsigned heavy = __ballot_sync(full, !own && hi > lo);
+  while (heavy) {
+    const int src = __ffs(heavy) - 1;
+    heavy &= heavy - 1;
+    const int32_t hlo = __shfl_sync(full, lo, src), hhi = __shfl_sync(full, hi, src);
+    for (int32_t base = hlo; base < hhi; base += 32) f(src, base + lane < hhi ? base + lane : -1);
+  }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(512, 3) k_leg_emit_delta(
+    GraphView g, const int2* __restrict__ qwin, const int32_t* __restrict__ qcb, LegSink S,
+    unsigned long long* __restrict__ acc_cyc2, int32_t* __restrict__ gs_in, int32_t own_max,
+    SubWindows sub, const int32_t* __restrict__ first_new, const int32_t* __restrict__ mptr,
+    const int32_t* __restrict__ mslot) {
+  const unsigned full = 0xffffffffu;
+  const int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  int32_t a = (int32_t)a64, x = 0, h = 0, ta = 0, q0 = 0, q1 = 0, qn = 0, qc = 0, m0 = 0, m1 = 0;
+  int64_t c2 = 0;
+  if (a64 < g.E) {
+    x = g.src[a];
+    h = g.dst[a];
+    if (x != h) {
+      const int2 w = qwin[a];
+      q0 = qn = qc = w.x;
+      q1 = w.y;
+      if (q1 > q0) {
+        ta = g.ts[a];
+        qn = min(max(__ldg(first_new + h), q0), q1);
+        if (S.la) {
+          qc = qcb[a];
+          c2 = S.off2[a];
+        }
+        if (S.rec && qn > q0) {
+          const int32_t lo = mptr[h], hi = mptr[h + 1];
+          m0 = lower_i32(mslot, lo, hi, q0);
+          m1 = lower_i32(mslot, m0, hi, qn);
+        }
+      }
+    }
+  }
+  // new legs and returns
+  warp_ranges(qn, q1, own_max, [&](int src, int32_t q) {
+    const int32_t sa = __shfl_sync(full, a, src), sx = __shfl_sync(full, x, src);
+    const int32_t sh = __shfl_sync(full, h, src), sta = __shfl_sync(full, ta, src);
+    const bool in = q >= 0;
+    const int32_t y = in ? __ldg(g.onbr + q) : sx;
+    const int32_t b = in ? __ldg(g.oeid + q) : 0;
+    const int32_t tb = in ? __ldg(g.ot + q) : 0;
+    const bool leg = in && y != sx;
+    if (S.rec) sg_record(S, leg, 0, sa, b, sx, sh, y, sta, tb, g.N, S.bits);
+    if (NS > 0 && in) sub_leg_credit<NS>(sub, leg, sa, b, tb - sta, g.new_from);
+    if (leg) {
+      if (gs_in) atomicAdd(gs_in + b, 1);
+    } else if (in && acc_cyc2) {  // a return: a 2-cycle
+      atomicAdd(acc_cyc2 + b, 1ull);
+      atomicAdd(acc_cyc2 + sa, 1ull);
+    }
+  });
+  // old legs into a batch destination
+  if (S.rec)
+    warp_ranges(m0, m1, own_max, [&](int src, int32_t i) {
+      const int32_t sa = __shfl_sync(full, a, src), sx = __shfl_sync(full, x, src);
+      const int32_t sh = __shfl_sync(full, h, src), sta = __shfl_sync(full, ta, src);
+      const bool in = i >= 0;
+      const int32_t q = in ? __ldg(mslot + i) : 0;
+      const int32_t y = in ? __ldg(g.onbr + q) : sx;
+      const int32_t b = in ? __ldg(g.oeid + q) : 0;
+      const int32_t tb = in ? __ldg(g.ot + q) : 0;
+      sg_record(S, in && y != sx, 0, sa, b, sx, sh, y, sta, tb, g.N, S.bits);
+    });
+  if (!S.la) return;
+  // cycle legs: the legs in [q0, qc), at off2[a] + their rank
+  const bool own = qc - q0 <= own_max;
+  int32_t q = q0;
+  int64_t rank = 0;
+  while (__any_sync(full, own && q < qc)) {
+    if (own && q < qc) {
+      if (__ldg(g.onbr + q) != x) {
+        S.la[c2 + rank] = a;
+        S.lb[c2 + rank] = __ldg(g.oeid + q);
+        ++rank;
+      }
+      ++q;
+    }
+  }
+  unsigned heavy = __ballot_sync(full, !own && qc > q0);
+  while (heavy) {
+    const int src = __ffs(heavy) - 1;
+    heavy &= heavy - 1;
+    const int32_t ha = __shfl_sync(full, a, src), hx = __shfl_sync(full, x, src);
+    const int32_t hq0 = __shfl_sync(full, q0, src), hqc = __shfl_sync(full, qc, src);
+    const int64_t hc2 = __shfl_sync(full, c2, src);
+    int64_t r = 0;
+    for (int32_t base = hq0; base < hqc; base += 32) {
+      const int32_t qq = base + lane;
+      const bool in = qq < hqc;
+      const bool leg = in && __ldg(g.onbr + qq) != hx;
+      const unsigned m = __ballot_sync(full, leg);
+      if (leg) {
+        const int64_t pos = hc2 + r + __popc(m & lt);
+        S.la[pos] = ha;
+        S.lb[pos] = __ldg(g.oeid + qq);
+      }
+      r += __popc(m);
+    }
+  }
+}
+
 // --------------------------------------------------------- scatter-gather
 //
 // Every SG instance is two legs of one (s, d) pair with different
@@ -1193,6 +1373,18 @@ void launch_leg_count(unsigned grid, int block, cudaStream_t s, const GraphView&
     AML_LAUNCH("k_leg_count", s,
                k_leg_count<decltype(ns)::value><<<grid, block, 0, s>>>(g, delta, L, crng, L2,
                                                                       L_new, qwin, qcb, sub, Z));
+  });
+}
+
+void launch_leg_emit_delta(unsigned grid, int block, cudaStream_t s, const GraphView& g,
+                           const int2* qwin, const int32_t* qcb, const LegSink& S,
+                           unsigned long long* acc_cyc2, int32_t* gs_in, int32_t own_max,
+                           const SubWindows& sub, const int32_t* first_new,
+                           const int32_t* mptr, const int32_t* mslot) {
+  nsub_dispatch(sub.n, [&](auto ns) {
+    AML_LAUNCH("k_leg_emit_delta", s,
+               k_leg_emit_delta<decltype(ns)::value><<<grid, block, 0, s>>>(
+                   g, qwin, qcb, S, acc_cyc2, gs_in, own_max, sub, first_new, mptr, mslot));
   });
 }
 

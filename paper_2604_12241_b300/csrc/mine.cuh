@@ -163,6 +163,21 @@ struct ZeroSink {
 void launch_leg_count(unsigned grid, int block, cudaStream_t s, const GraphView& g, int32_t delta,
                       int32_t* L, const int2* crng, int32_t* L2, int32_t* L_new, int2* qwin,
                       int32_t* qcb, const SubWindows& sub, const ZeroSink& Z);
+// Delta counting (new_from > 0): the legs a new instance can use (mine.cu);
+// first_new = each out-list's first new slot (k_first_new); mptr/mslot =
+// each node's out-list slots whose counterparty is a batch destination
+// (k_mark_slots, k_compact_marked, k_marked_ptr).
+void launch_leg_emit_delta(unsigned grid, int block, cudaStream_t s, const GraphView& g,
+                           const int2* qwin, const int32_t* qcb, const LegSink& S,
+                           unsigned long long* acc_cyc2, int32_t* gs_in, int32_t own_max,
+                           const SubWindows& sub, const int32_t* first_new,
+                           const int32_t* mptr, const int32_t* mslot);
+__global__ void k_first_new(const int32_t* optr, const int32_t* oeid, int32_t N, int32_t new_from,
+                            int32_t* first_new);
+__global__ void k_mark_slots(const int32_t* nbr, int64_t Ev, const uint32_t* mask, int32_t* flag);
+__global__ void k_compact_marked(const int32_t* flag_scan, int64_t Ev, int32_t* mslot);
+__global__ void k_marked_ptr(const int32_t* optr, const int32_t* flag_scan, int32_t N,
+                             int32_t* mptr);
 void launch_leg_emit(unsigned grid, int block, cudaStream_t s, const GraphView& g,
                      const int2* qwin, const int32_t* qcb, const int64_t* off, const LegSink& S,
                      unsigned long long* acc_cyc2, int32_t* gs_in, int32_t own_max,

@@ -472,8 +472,43 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     }
     unsigned long long* acc2 =
         wp.cyc.slot[2] >= 0 ? acc.p + (int64_t)wp.cyc.slot[2] * E : nullptr;
-    launch_leg_emit(grid_for(E, B), B, s, gv, qwin.p, qcb.p, off, S, acc2, gs_in, tn.own_max,
-                    sub);
+    // delta counting: old legs matter only as SG legs into a batch
+    // destination, found through the out-list slots marked for it -- while
+    // those are a small share of the slots (below 40%: measured break-even
+    // on the hi-medium shape); otherwise every window is walked
+    bool delta_emit = new_from > 0;
+    DBuf<int32_t> mflag, mptr, mslot;
+    if (delta_emit && sg_filter) {
+      mflag = DBuf<int32_t>((size_t)Ev + 1, s);
+      AML_LAUNCH("k_mark_slots", s,
+                 k_mark_slots<<<grid_for(Ev + 1, 256), 256, 0, s>>>(g->out.nbr, Ev, dmask.p,
+                                                                    mflag.p));
+      scan_i32(mflag.p, mflag.p, Ev + 1, false, s);
+      int32_t n_marked = 0;
+      const SmallRead rd{&n_marked, mflag.p + Ev, 4};
+      read_small(&rd, 1, s);
+      delta_emit = (double)n_marked < 0.4 * (double)Ev;
+    }
+    if (delta_emit) {
+      DBuf<int32_t> first_new((size_t)std::max<int32_t>(g->N, 1), s);
+      AML_LAUNCH("k_first_new", s,
+                 k_first_new<<<grid_for(g->N, 256), 256, 0, s>>>(g->out.ptr, g->out.eid, g->N,
+                                                                 new_from, first_new.p));
+      if (sg_filter) {
+        mptr = DBuf<int32_t>((size_t)g->N + 1, s);
+        mslot = DBuf<int32_t>((size_t)std::max<int64_t>(Ev, 1), s);
+        AML_LAUNCH("k_compact_marked", s,
+                   k_compact_marked<<<grid_for(Ev, 256), 256, 0, s>>>(mflag.p, Ev, mslot.p));
+        AML_LAUNCH("k_marked_ptr", s,
+                   k_marked_ptr<<<grid_for((int64_t)g->N + 1, 256), 256, 0, s>>>(
+                       g->out.ptr, mflag.p, g->N, mptr.p));
+      }
+      launch_leg_emit_delta(grid_for(E, B), B, s, gv, qwin.p, qcb.p, S, acc2, gs_in,
+                            tn.own_max, sub, first_new.p, mptr.p, mslot.p);
+    } else {
+      launch_leg_emit(grid_for(E, B), B, s, gv, qwin.p, qcb.p, off, S, acc2, gs_in, tn.own_max,
+                      sub);
+    }
     int64_t n_sg = nl;  // records to bucket
     if (sg_filter) {
       unsigned long long kept = 0;

@@ -147,3 +147,33 @@ def test_stream_graph_update_edge_cases():
             r0, nr = inf["resident_first_row"], inf["resident_rows"]
             np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
     st.close()
+
+
+def test_stream_uses_both_leg_emissions():
+    """A batch with few destinations takes the delta leg emission (old legs
+    only through the marked slots of batch destinations), a batch whose
+    destinations take most slots the full walk; both recounts equal a full
+    mine."""
+    from paper_2604_12241_b300 import _lib
+    g = aml_synth.workload("hi-medium", scale=0.1)
+    pats = P.workload_patterns("hi-medium")
+    st = aml.Stream(aml.PatternSet(pats), g.n_nodes, resident_window=7 * P.DAY,
+                    mem_budget=8 << 30)
+    pos = int(np.searchsorted(g.ts, 8 * P.DAY))
+    st.append(g.src[:pos], g.dst[:pos], g.ts[:pos], g.amount[:pos])
+    seen = set()
+    for n in (50, 60000, 300, 120000, 1):
+        _lib.profile_read(reset=True)
+        _lib.profile_enable(True)
+        st.append(g.src[pos:pos + n], g.dst[pos:pos + n], g.ts[pos:pos + n],
+                  g.amount[pos:pos + n])
+        _lib.profile_enable(False)
+        seen |= {k for k in _lib.profile_read(reset=True) if k.startswith("k_leg_emit")}
+        pos += n
+    assert seen == {"k_leg_emit", "k_leg_emit_delta"}, seen
+    want = full_mine(g, pos, pats)
+    inf = st.info()
+    r0, nr = inf["resident_first_row"], inf["resident_rows"]
+    np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
+    assert st.check_graph() == 0
+    st.close()
