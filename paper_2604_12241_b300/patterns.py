@@ -145,6 +145,19 @@ def scatter_gather_n(n: int, delta: int) -> Pattern:
     return Pattern(tuple(stages), AGG_INSTANCES, delta, f"SG{n}@{delta}", interpret=True)
 
 
+def scatter_gather_nodes(delta: int) -> Pattern:
+    """The node-level scatter-gather: for each scatter edge s -> m1 (the
+    trigger), the number of distinct other intermediaries m2 that complete a
+    scatter-gather s -> m1 -> d, s -> m2 -> d with it (any d, each leg in
+    order, all four edges within delta): Sec. 5's scatter-gather program
+    with the DISTINCT aggregate over its last node, run by the generic
+    interpreter.  k - 1 on each scatter edge of an isolated k-intermediary
+    scatter-gather, 0 on its gather edges; parallel legs through the same
+    intermediary count once."""
+    p = scatter_gather(delta)
+    return Pattern(p.stages, AGG_DISTINCT, delta, f"SG_NODES@{delta}", interpret=True)
+
+
 def cycle(k: int, delta: int, closing: str = "for_all") -> Pattern:
     """k-cycle: trigger N0 -> N1, then N_i.out -> N_{i+1} (later, new node),
     closed by an edge back into N0 -- or, for k >= 3, by intersecting

@@ -64,6 +64,7 @@ def test_programs_match_oracle_on_tiny10k():
     pats = [P.program(st, agg, P.DAY) for st, agg in NOVEL.values()]
     pats += _family_programs(P.DAY)
     pats += [P.scatter_gather_n(n, P.DAY) for n in (3, 4)]  # "at least N" intermediaries
+    pats += [P.scatter_gather_nodes(P.DAY)]                      # node-level SG
     # family columns beside the interpreted ones in the same mine
     fam = P.standard(P.DAY)
     got = _mine(g, pats + fam)

@@ -96,6 +96,25 @@ def test_n_intermediary_scatter_gather_closed_form():
             assert (got[m.edges] == want).all(), (n, m.k, got[m.edges])
 
 
+def test_node_level_scatter_gather_closed_form():
+    """Distinct other intermediaries per scatter edge: k - 1 on the scatter
+    edges of a planted isolated k-SG, 0 on its gather edges, and never more
+    than the edge-level pair count of the same trigger."""
+    g = aml_synth.workload("tiny-10k")
+    og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
+    pat = P.scatter_gather_nodes(P.DAY)
+    got = og.program_count(_tuples(pat), pat.aggregate, pat.delta)
+    pairs = og.program_count(_tuples(P.scatter_gather(P.DAY)), P.AGG_EDGES, P.DAY)
+    assert (got.astype(np.int64) <= pairs.astype(np.int64)).all()
+    fresh = [m for m in g.motifs if m.kind == "sg" and m.fresh]
+    assert fresh
+    for m in fresh:
+        scatter = [e for e in m.edges if g.dst[e] != g.dst[m.edges[-1]]]
+        gather = [e for e in m.edges if e not in scatter]
+        assert len(scatter) == len(gather) == m.k
+        assert (got[scatter] == m.k - 1).all() and (got[gather] == 0).all()
+
+
 def test_n_intermediary_scatter_gather_brute_force():
     """Legs s -> m -> d through four candidate intermediaries at random times
     (some out of order, one repeated), plus noise edges."""
