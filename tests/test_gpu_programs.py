@@ -58,6 +58,32 @@ def test_programs_match_oracle_on_tiny_graphs(seed):
                                           err_msg=f"column {j} ({p.name}), delta {delta}")
 
 
+def test_programs_match_oracle_with_a_hub():
+    """A hub holding a third of the edges: its triggers have hundreds of
+    first-stage candidates and go to the warp-per-trigger walk."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(42)
+    E, N = 800, 30
+    src = rng.integers(0, N, E).astype(np.int32)
+    dst = rng.integers(0, N, E).astype(np.int32)
+    hub = rng.random(E) < 0.3
+    src[hub & (rng.random(E) < 0.5)] = 0
+    dst[hub & (src != 0)] = 0
+    ts = np.sort(rng.integers(0, 200, E)).astype(np.int32)
+    g = SimpleNamespace(src=src, dst=dst, ts=ts, n_nodes=N)
+    og = oracle.OracleGraph(src, dst, ts, N)
+    assert max(np.bincount(src, minlength=N)[0], np.bincount(dst, minlength=N)[0]) > 100
+    for delta in (50, 1000):
+        pats = [P.program(st, agg, delta) for st, agg in NOVEL.values()]
+        pats += _family_programs(delta) + [P.scatter_gather_n(3, delta),
+                                           P.scatter_gather_nodes(delta)]
+        got = _mine(g, pats)
+        for j, p in enumerate(pats):
+            want = og.program_count(_tuples(p), p.aggregate, p.delta, threads=8)
+            np.testing.assert_array_equal(got[:, j], want,
+                                          err_msg=f"column {j} ({p.name}), delta {delta}")
+
+
 def test_programs_match_oracle_on_tiny10k():
     g = aml_synth.workload("tiny-10k")
     og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
