@@ -611,69 +611,74 @@ def run_ours(args, ws, rank, local):
 
     # end to end through the public API, every step: the step's inputs copied
     # from pinned host memory to the device, graph build, mine, and the
-    # counts copied back to pinned host memory.  The copy engines run one
-    # transfer at a time, so the steps are pipelined on two streams in the
-    # order upload(k), copy back(k-1): step k's build and mine run while step
-    # k-1's 406 MB of counts travel back.  A step's graph is destroyed (which
-    # waits for its stream) before its buffers are reused.
+    # counts copied back to pinned host memory.  Transfers in one direction
+    # run one at a time, but an upload overlaps a copy back (the link is full
+    # duplex), and the 406 MB copy back of a step takes longer than the next
+    # step's upload, build and mine.  The library's calls block their host
+    # thread while they wait for sizes on the device, so the steps run on two
+    # host threads (the calls release the GIL) over a ring of three slots,
+    # each with its own stream and buffers: a step takes its slot, destroys
+    # the slot's previous graph (which waits for that step's copy back), then
+    # uploads, builds, mines and enqueues its copy back on the slot's stream.
     e2e = None
     if not args.no_e2e:
+        import threading
+        from concurrent.futures import ThreadPoolExecutor
+        R = 3
         pin = {k: torch.from_numpy(v).pin_memory() for k, v in
                (("src", g.src), ("dst", g.dst), ("ts", g.ts), ("amount", g.amount))}
-        S = [torch.cuda.Stream(), torch.cuda.Stream()]
-        dev_in = [{k: torch.empty_like(t, device="cuda") for k, t in pin.items()} for _ in range(2)]
-        dev_out = [torch.empty((E, Pn), dtype=torch.int32, device="cuda") for _ in range(2)]
-        out_pin = [torch.empty((E, Pn), dtype=torch.int32).pin_memory() for _ in range(2)]
-        live = [None, None]
+        S = [torch.cuda.Stream() for _ in range(R)]
+        dev_in = [{k: torch.empty_like(t, device="cuda") for k, t in pin.items()} for _ in range(R)]
+        dev_out = [torch.empty((E, Pn), dtype=torch.int32, device="cuda") for _ in range(R)]
+        out_pin = [torch.empty((E, Pn), dtype=torch.int32).pin_memory() for _ in range(R)]
+        live = [None] * R
+        slot_lock = [threading.Lock() for _ in range(R)]
 
-        def copy_back(j):
-            with torch.cuda.stream(S[j]):
-                out_pin[j].copy_(dev_out[j], non_blocking=True)
+        dev = torch.cuda.current_device()
 
         def e2e_step(k):
-            i = k % 2
-            if live[i] is not None:
-                live[i].close()
-                live[i] = None
-            with torch.cuda.stream(S[i]):
-                for key, t in pin.items():
-                    dev_in[i][key].copy_(t, non_blocking=True)
-            if k > 0:
-                up = torch.cuda.Event()
-                up.record(S[i])
-                S[1 - i].wait_event(up)
-                copy_back(1 - i)
-            gg = aml.Graph(dev_in[i]["src"], dev_in[i]["dst"], dev_in[i]["ts"], g.n_nodes,
-                           amount=dev_in[i]["amount"], assume_sorted=True, stream=S[i])
-            aml.mine(gg, ps, out=dev_out[i], stream=S[i])
-            live[i] = gg
+            torch.cuda.set_device(dev)  # worker threads start on device 0
+            i = k % R
+            with slot_lock[i]:
+                if live[i] is not None:
+                    live[i].close()
+                    live[i] = None
+                with torch.cuda.stream(S[i]):
+                    for key, t in pin.items():
+                        dev_in[i][key].copy_(t, non_blocking=True)
+                gg = aml.Graph(dev_in[i]["src"], dev_in[i]["dst"], dev_in[i]["ts"], g.n_nodes,
+                               amount=dev_in[i]["amount"], assume_sorted=True, stream=S[i])
+                aml.mine(gg, ps, out=dev_out[i], stream=S[i])
+                with torch.cuda.stream(S[i]):
+                    out_pin[i].copy_(dev_out[i], non_blocking=True)
+                live[i] = gg
 
-        def e2e_finish(k_last):
-            copy_back(k_last % 2)
-            for i in range(2):
+        def e2e_run(n_steps):
+            with ThreadPoolExecutor(max_workers=2) as pool:
+                for f in [pool.submit(e2e_step, k) for k in range(n_steps)]:
+                    f.result()
+            for i in range(R):
                 if live[i] is not None:
                     live[i].close()
                     live[i] = None
 
-        e2e_step(0)
-        e2e_finish(0)
+        e2e_run(R)
         dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for k in range(args.e2e_steps):
-            e2e_step(k)
-        e2e_finish(args.e2e_steps - 1)
+        e2e_run(args.e2e_steps)
         torch.cuda.synchronize()
         e2e_s = dist.max(time.perf_counter() - t0)
-        last = out_pin[(args.e2e_steps - 1) % 2].numpy().view(np.uint32)
+        last = out_pin[(args.e2e_steps - 1) % R].numpy().view(np.uint32)
         e2e = {"value": ws * E * args.e2e_steps / e2e_s, "unit": "edges/s",
                "h2d_bytes_per_step": int(E * 16), "d2h_bytes_per_step": int(E * Pn * 4),
                "steps": args.e2e_steps, "ms_per_step": 1000.0 * e2e_s / args.e2e_steps,
                "matches_device_output": bool(np.array_equal(
                    last, out.cpu().numpy().view(np.uint32))),
                "includes": "pinned host inputs -> device, graph build, mine, counts -> pinned "
-                           "host memory; two streams, upload(k) then copy back(k-1) while "
-                           "step k builds and mines"}
+                           "host memory; steps on two host threads over a ring of three "
+                           "streams, so a step's upload, build and mine overlap the previous "
+                           "step's copy back"}
 
     line = None
     if rank == 0:
