@@ -166,7 +166,24 @@ typedef struct aml_stage {
   int32_t window;    /* AML_WIN_*                                               */
   uint32_t skip_eq;  /* skip_if: bit i set = drop candidates equal to N_i       */
                      /* (the paper's "differentiate", e.g. N2 != N0)            */
+  uint32_t amount_flags;  /* AML_AMT_* constraints on the amounts of the stage's */
+                          /* edges (0: none); any makes the program interpreted */
+  float amount_min, amount_max;  /* AML_AMT_RANGE: amount_min <= amount <=       */
+                                 /* amount_max for every edge of the stage      */
+  float ratio_min, ratio_max;    /* AML_AMT_RATIO: each edge's amount within     */
+                                 /* [ratio_min, ratio_max] times the amount of   */
+                                 /* the edge before it on the walk: reach(A) for */
+                                 /* a FOR_ALL edge and an INTERSECT's a-side     */
+                                 /* edge, the a-side edge for the b-side edge    */
 } aml_stage;
+
+/* Amount constraints of a stage (edge attributes as operands, Sec. 5).  The
+ * comparisons are exact: amounts are the float32 values given to
+ * aml_graph_create, and ratio * amount is formed in double precision (the
+ * exact product of two floats).  On the trigger (stage 0) only RANGE is
+ * allowed: it selects the trigger edges. */
+#define AML_AMT_RANGE 0x1u
+#define AML_AMT_RATIO 0x2u
 
 /* What the final stage's Postprocess reports for each trigger edge. */
 #define AML_AGG_EDGES 0      /* # matched edges (windowed degree)               */

@@ -32,7 +32,13 @@ class _Col(ctypes.Structure):
 class _Stage(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int32) for f in
                 ("op", "a_var", "a_dir", "b_var", "b_dir", "out_var", "order", "window")] + \
-               [("skip_eq", ctypes.c_uint32)]
+               [("skip_eq", ctypes.c_uint32), ("amount_flags", ctypes.c_uint32)] + \
+               [(f, ctypes.c_float) for f in ("amount_min", "amount_max", "ratio_min",
+                                              "ratio_max")]
+
+
+STAGE_FIELDS = ("op", "a_var", "a_dir", "b_var", "b_dir", "out_var", "order", "window",
+                "skip_eq", "amount_flags", "amount_min", "amount_max", "ratio_min", "ratio_max")
 
 
 # stage-program vocabulary (the values of the library's ABI, restated)
@@ -41,6 +47,7 @@ DIR_OUT, DIR_IN = 0, 1
 ORD_NONE, ORD_AFTER, ORD_BEFORE, ORD_LEG, ORD_AFTER_TRIGGER = 0, 1, 2, 3, 4
 WIN_TRAILING, WIN_SPAN = 0, 1
 AGG_EDGES, AGG_DISTINCT, AGG_INSTANCES = 0, 1, 2
+AMT_RANGE, AMT_RATIO = 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -68,6 +75,7 @@ def load_library(path: str) -> ctypes.CDLL:
     lib.og_count_all.restype = ctypes.c_int
     lib.og_count_all.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                  ctypes.c_void_p, ctypes.c_int32]
+    lib.og_graph_set_amounts.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     lib.og_program_count.restype = ctypes.c_int
     lib.og_program_count.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
@@ -99,7 +107,7 @@ def _cols(cols: Sequence[Tuple]) -> ctypes.Array:
 class OracleGraph:
     """Host copy of the graph with (t,id)-sorted out/in rows."""
 
-    def __init__(self, src, dst, ts, n_nodes: int, lib: ctypes.CDLL = None):
+    def __init__(self, src, dst, ts, n_nodes: int, lib: ctypes.CDLL = None, amount=None):
         self._lib = lib = lib if lib is not None else _load()
         self._src = np.ascontiguousarray(src, dtype=np.int32)
         self._dst = np.ascontiguousarray(dst, dtype=np.int32)
@@ -110,6 +118,9 @@ class OracleGraph:
                                    self._ts.ctypes.data, self.n_edges, self.n_nodes)
         if not self._h:
             raise ValueError("oracle rejected the graph (ids out of range?)")
+        if amount is not None:
+            self._amount = np.ascontiguousarray(amount, dtype=np.float32)
+            lib.og_graph_set_amounts(self._h, self._amount.ctypes.data)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -144,12 +155,12 @@ class OracleGraph:
                       threads: int = 0) -> np.ndarray:
         """One stage program interpreted as ``og_program_count`` defines it:
         uint32 [E].  ``stages`` = (op, a_var, a_dir, b_var, b_dir, out_var,
-        order, window, skip_eq) tuples, stage 0 the trigger."""
+        order, window, skip_eq[, amount_flags, amount_min, amount_max,
+        ratio_min, ratio_max]) tuples, stage 0 the trigger."""
         arr = (_Stage * len(stages))()
         for i, st in enumerate(stages):
-            for f, v in zip(("op", "a_var", "a_dir", "b_var", "b_dir", "out_var", "order",
-                             "window", "skip_eq"), st):
-                setattr(arr[i], f, int(v))
+            for f, v in zip(STAGE_FIELDS, st):
+                setattr(arr[i], f, float(v) if f.endswith(("_min", "_max")) else int(v))
         out = np.zeros(self.n_edges, dtype=np.uint32)
         rc = self._lib.og_program_count(self._h, ctypes.byref(arr), len(stages), int(aggregate),
                                         int(delta), out.ctypes.data, threads)

@@ -17,6 +17,7 @@ struct og_graph {
   int64_t E;
   int32_t N;
   int32_t *src, *dst, *ts;
+  float* amount;                 /* for amount constraints; 0 unless set    */
   int64_t *out_start, *in_start; /* N+1 row offsets                         */
   int64_t *out_list, *in_list;   /* non-loop edge ids, rows in (t,id) order  */
   int64_t *pos_out, *pos_in;     /* position of e in its rows, -1 for loops  */
@@ -68,6 +69,7 @@ og_graph* og_graph_new(const int32_t* src, const int32_t* dst, const int32_t* ts
   g->src = (int32_t*)malloc(e4);
   g->dst = (int32_t*)malloc(e4);
   g->ts = (int32_t*)malloc(e4);
+  g->amount = (float*)calloc((size_t)(E > 0 ? E : 1), 4);
   if (E) {
     memcpy(g->src, src, (size_t)E * 4);
     memcpy(g->dst, dst, (size_t)E * 4);
@@ -120,9 +122,13 @@ og_graph* og_graph_new(const int32_t* src, const int32_t* dst, const int32_t* ts
   return g;
 }
 
+void og_graph_set_amounts(og_graph* g, const float* amount) {
+  if (g && amount && g->E) memcpy(g->amount, amount, (size_t)g->E * 4);
+}
+
 void og_graph_free(og_graph* g) {
   if (!g) return;
-  free(g->src); free(g->dst); free(g->ts);
+  free(g->src); free(g->dst); free(g->ts); free(g->amount);
   free(g->out_start); free(g->in_start);
   free(g->out_list); free(g->in_list);
   free(g->pos_out); free(g->pos_in);
@@ -661,6 +667,17 @@ static int pg_node_ok(const pg_ctx* c, const og_stage* s, int32_t x, int bound) 
 
 static void pg_stage(pg_ctx* c, int si, int bound);
 
+/* the stage's amount constraints on edge f, whose predecessor on the walk is p */
+static int pg_amount_ok(const pg_ctx* c, const og_stage* s, int64_t f, int64_t p) {
+  const double a = c->g->amount[f];
+  if ((s->amount_flags & OG_AMT_RANGE) && !(a >= s->amount_min && a <= s->amount_max)) return 0;
+  if (s->amount_flags & OG_AMT_RATIO) {
+    const double b = c->g->amount[p];
+    if (!(a >= (double)s->ratio_min * b && a <= (double)s->ratio_max * b)) return 0;
+  }
+  return 1;
+}
+
 static void pg_bind(pg_ctx* c, int si, int bound, int32_t x, int64_t reach_edge) {
   const og_stage* s = &c->st[si];
   int nb = bound;
@@ -715,6 +732,7 @@ static void pg_stage(pg_ctx* c, int si, int bound) {
     const int32_t x = pg_far(g, fa, s->a_dir);
     if (!pg_node_ok(c, s, x, bound)) continue;
     if (s->window == OG_WIN_TRAILING && !pg_trailing_ok(c, fa)) continue;
+    if (!pg_amount_ok(c, s, fa, ra)) continue;
     if (s->op == OG_OP_FOR_ALL) {
       if (s->order == OG_ORD_AFTER && !prec(g, ra, fa)) continue;
       if (s->order == OG_ORD_BEFORE && !prec(g, fa, ra)) continue;
@@ -735,6 +753,7 @@ static void pg_stage(pg_ctx* c, int si, int bound) {
         const int64_t fb = lb[j];
         if ((int64_t)g->ts[fb] > bth) break;
         if (pg_far(g, fb, s->b_dir) != x) continue;
+        if (!pg_amount_ok(c, s, fb, fa)) continue;
         if (s->window == OG_WIN_TRAILING && !pg_trailing_ok(c, fb)) continue;
         if (s->order == OG_ORD_AFTER && !(prec(g, ra, fa) && prec(g, fa, fb))) continue;
         if (s->order == OG_ORD_BEFORE && !(prec(g, fb, fa) && prec(g, fa, ra))) continue;
@@ -756,6 +775,12 @@ static void pg_stage(pg_ctx* c, int si, int bound) {
 static int pg_check(const og_stage* st, int32_t n, int32_t agg) {
   if (n < 1 || n > OG_MAXST || agg < OG_AGG_EDGES || agg > OG_AGG_INSTANCES) return -1;
   if (st[0].op != OG_OP_TRIGGER || st[0].out_var != 1) return -1;
+  for (int s = 0; s < n; ++s) {
+    const uint32_t allowed = s == 0 ? OG_AMT_RANGE : (OG_AMT_RANGE | OG_AMT_RATIO);
+    if (st[s].amount_flags & ~allowed) return -1;
+    if ((st[s].amount_flags & OG_AMT_RANGE) && !(st[s].amount_min <= st[s].amount_max)) return -1;
+    if ((st[s].amount_flags & OG_AMT_RATIO) && !(st[s].ratio_min <= st[s].ratio_max)) return -1;
+  }
   int bound = 2;
   for (int s = 1; s < n; ++s) {
     const og_stage* x = &st[s];
@@ -795,6 +820,9 @@ int og_program_count(const og_graph* g, const og_stage* st, int32_t n, int32_t a
 #pragma omp for schedule(dynamic, 64)
     for (int64_t e0 = 0; e0 < E; ++e0) {
       if (g->src[e0] == g->dst[e0]) continue;
+      if ((st[0].amount_flags & OG_AMT_RANGE) &&
+          !(g->amount[e0] >= st[0].amount_min && g->amount[e0] <= st[0].amount_max))
+        continue;  /* not a trigger */
       c.e0 = e0;
       c.node[0] = g->src[e0];
       c.node[1] = g->dst[e0];

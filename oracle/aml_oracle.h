@@ -101,10 +101,24 @@ enum { OG_ORD_NONE = 0, OG_ORD_AFTER = 1, OG_ORD_BEFORE = 2, OG_ORD_LEG = 3,
 enum { OG_WIN_TRAILING = 0, OG_WIN_SPAN = 1 };
 enum { OG_AGG_EDGES = 0, OG_AGG_DISTINCT = 1, OG_AGG_INSTANCES = 2 };
 
+/* Amount constraints (edge attributes as operands): RANGE = every edge g of
+ * the stage has amount_min <= amount(g) <= amount_max; RATIO = every edge
+ * g has ratio_min * amount(p) <= amount(g) <= ratio_max * amount(p) with p
+ * the edge before g on the walk (reach(A) for a FOR_ALL edge and an
+ * intersection's fa; fa for its fb), products in double.  On the trigger,
+ * RANGE only: it selects the trigger edges.  Amounts come from
+ * og_graph_set_amounts (all 0 otherwise). */
+enum { OG_AMT_RANGE = 1, OG_AMT_RATIO = 2 };
+
 typedef struct og_stage {
   int32_t op, a_var, a_dir, b_var, b_dir, out_var, order, window;
   uint32_t skip_eq;
+  uint32_t amount_flags;
+  float amount_min, amount_max, ratio_min, ratio_max;
 } og_stage;
+
+/* Copies the n_edges float32 amounts used by amount constraints. */
+void og_graph_set_amounts(og_graph* g, const float* amount);
 
 /* Counts of one program for every edge: out[E] (uint32, saturated).
  * Returns 0, or -1 for a program outside the forms defined above (at most

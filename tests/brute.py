@@ -168,7 +168,15 @@ def admissible_orders(k: int) -> Tuple[int, int]:
     return total, ok
 
 
-def brute_program(src, dst, ts, stages, aggregate: int, delta: int) -> np.ndarray:
+def _amount_rule(st):
+    """(flags, lo, hi, rlo, rhi) of a stage tuple, bounds as the float32 values
+    the library stores (compared in double precision)."""
+    st = tuple(st) + (0, 0.0, 0.0, 0.0, 0.0)[len(st) - 9:] if len(st) < 14 else tuple(st)
+    f32 = lambda v: float(np.float32(v))
+    return int(st[9]), f32(st[10]), f32(st[11]), f32(st[12]), f32(st[13])
+
+
+def brute_program(src, dst, ts, stages, aggregate: int, delta: int, amount=None) -> np.ndarray:
     """A stage program's counts by enumerating every tuple of edges for the
     program's edge slots (one per FOR_ALL stage, two per INTERSECT stage) and
     testing the definition on each; no neighbour lists.  uint64 [E]."""
@@ -176,10 +184,20 @@ def brute_program(src, dst, ts, stages, aggregate: int, delta: int) -> np.ndarra
     dst = [int(x) for x in dst]
     ts = [int(x) for x in ts]
     E = len(src)
+    amt = ([float(np.float32(x)) for x in amount] if amount is not None else [0.0] * E)
     valid = [i for i in range(E) if src[i] != dst[i]]
     out = np.zeros(E, dtype=np.uint64)
-    body = [tuple(int(v) for v in st) for st in stages[1:]]
+    body = [tuple(int(v) for v in st[:9]) for st in stages[1:]]
+    rules = [_amount_rule(st) for st in stages]
     width = sum(1 if st[0] == 1 else 2 for st in body)
+
+    def amount_ok(rule, g, p):
+        flags, lo, hi, rlo, rhi = rule
+        if flags & 1 and not (lo <= amt[g] <= hi):
+            return False
+        if flags & 2 and not (rlo * amt[p] <= amt[g] <= rhi * amt[p]):
+            return False
+        return True
 
     def far(f, u, d):  # the other end of f if f is in u's d-list (0 out, 1 in)
         if d == 0:
@@ -190,19 +208,21 @@ def brute_program(src, dst, ts, stages, aggregate: int, delta: int) -> np.ndarra
         return _prec(ts, f, e)
 
     for e0 in valid:
+        if not amount_ok(rules[0], e0, e0):  # the trigger's range (no ratio on it)
+            continue
         n_bind, lasts = 0, set()
         for tup in itertools.product(valid, repeat=width):
             node = {0: src[e0], 1: dst[e0]}
             reach = {0: e0, 1: e0}
             edges, span = [e0], [e0]
             x_last, i, ok = dst[e0], 0, True
-            for op, a, ad, b, bd, outv, order, window, skip in body:
+            for si, (op, a, ad, b, bd, outv, order, window, skip) in enumerate(body, 1):
                 if op == 1:
                     f = tup[i]
                     i += 1
                     x = far(f, node[a], ad)
                     mine, rch = [f], f
-                    if x is None:
+                    if x is None or not amount_ok(rules[si], f, reach[a]):
                         ok = False
                     elif order == 1:
                         ok = before(reach[a], f)
@@ -216,6 +236,9 @@ def brute_program(src, dst, ts, stages, aggregate: int, delta: int) -> np.ndarra
                     x, y = far(fa, node[a], ad), far(fb, node[b], bd)
                     mine, rch = [fa, fb], fb
                     if x is None or y is None or x != y:
+                        ok = False
+                    elif not (amount_ok(rules[si], fa, reach[a]) and
+                              amount_ok(rules[si], fb, fa)):
                         ok = False
                     elif order == 1:
                         ok = before(reach[a], fa) and before(fa, fb)

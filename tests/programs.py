@@ -56,3 +56,38 @@ NOVEL = {
     # the trigger alone
     "trigger_only": ([T], INSTANCES),
 }
+
+RANGE, RATIO = 1, 2
+
+
+def amt(stage, flags, lo=0.0, hi=0.0, rlo=0.0, rhi=0.0):
+    """A stage tuple with amount constraints (flags, range, ratio)."""
+    return tuple(stage[:9]) + (flags, lo, hi, rlo, rhi)
+
+
+# programs with amount constraints; graphs for them carry amounts
+AMOUNT_PROGRAMS = {
+    # funds passed on within the span, keeping 85-100% of the amount
+    "fee_forward": ([T, amt(F(1, OUT, 2, AFTER, SPAN, mask(0)), RATIO, rlo=0.85, rhi=1.0)],
+                    INSTANCES),
+    # trailing out-degree, counted for large triggers only
+    "large_trigger_degree": ([amt(T, RANGE, 150.0, 1e9), F(0, OUT, 2, NONE, TRAILING)], EDGES),
+    # scatter-gather whose legs pass the funds on (80-100%) and whose second
+    # scatter is 0.5-2x the first
+    "sg_fee": ([T, amt(F(1, OUT, 2, AFTER, SPAN, mask(0)), RATIO, rlo=0.8, rhi=1.0),
+                amt(X(0, OUT, 2, IN, 3, LEG, SPAN, mask(1)), RATIO, rlo=0.5, rhi=2.0)],
+               INSTANCES),
+    # 3-cycles in time order, every hop 90-100% of the hop before, amounts
+    # between 50 and 250
+    "cycle_ratio": ([T, amt(F(1, OUT, 2, AFTER, SPAN, mask(0, 1)), RATIO | RANGE, 50.0, 250.0,
+                            0.9, 1.0),
+                     amt(F(2, OUT, 0, AFTER, SPAN), RATIO | RANGE, 50.0, 250.0, 0.9, 1.0)],
+                    INSTANCES),
+    # distinct counterparties of an intersection whose edges both lie in a range
+    "distinct_range": ([T, amt(X(0, OUT, 1, IN, 2, NONE, SPAN, mask(0, 1)), RANGE, 80.0, 120.0)],
+                       DISTINCT),
+}
+
+# amounts drawn for the graphs of AMOUNT_PROGRAMS: ratio bounds fall on
+# exact pairs (85/100, 90/100, 80/100)
+AMOUNT_VALUES = (50.0, 80.0, 85.0, 90.0, 95.0, 100.0, 120.0, 150.0, 180.0, 200.0)

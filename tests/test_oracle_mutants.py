@@ -14,7 +14,7 @@ import pytest
 import aml_synth
 import oracle
 from brute import brute_counts, brute_program
-from programs import NOVEL
+from programs import AMOUNT_PROGRAMS, AMOUNT_VALUES, NOVEL
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "aml_oracle.c")
 
@@ -124,3 +124,54 @@ def test_program_pins_reject_mutant(tmp_path, name, orig, mutated):
                            "-I", os.path.dirname(SRC), "-o", str(so), str(path)])
     lib = oracle.load_library(str(so))
     assert _program_pins_reject(lib), f"mutant {name} survived the program pins"
+
+
+# mistakes in the amount constraints, caught by the amount-program pins
+AMOUNT_MUTANTS = [
+    ("amt-ratio-b-side-from-reach", "if (!pg_amount_ok(c, s, fb, fa)) continue;",
+     "if (!pg_amount_ok(c, s, fb, ra)) continue;"),
+    ("amt-range-open-below",
+     "if ((s->amount_flags & OG_AMT_RANGE) && !(a >= s->amount_min && a <= s->amount_max)) return 0;",
+     "if ((s->amount_flags & OG_AMT_RANGE) && !(a > s->amount_min && a <= s->amount_max)) return 0;"),
+    ("amt-ratio-ignored", "  if (s->amount_flags & OG_AMT_RATIO) {\n    const double b",
+     "  if (0) {\n    const double b"),
+    ("amt-trigger-range-ignored",
+     "        continue;  /* not a trigger */", "        ;  /* not a trigger */"),
+]
+
+
+def _amount_pins_reject(lib) -> bool:
+    for seed in range(8):
+        g = aml_synth.tiny_random(4, 12, 9, 3000 + seed)
+        rng = np.random.default_rng(seed)
+        src = np.concatenate([g.src, [0, 1, 2, 0, 0, 1, 2]]).astype(np.int32)
+        dst = np.concatenate([g.dst, [1, 2, 0, 1, 2, 3, 3]]).astype(np.int32)
+        ts = np.concatenate([g.ts, np.sort(rng.integers(0, 8, 3)),
+                             np.sort(rng.integers(0, 8, 2)), np.sort(rng.integers(4, 12, 2))])
+        amount = np.concatenate([rng.choice(AMOUNT_VALUES, 12), [100.0, 95.0, 90.0],
+                                 [100.0, 100.0], [95.0, 95.0]]).astype(np.float32)
+        og = oracle.OracleGraph(src, dst, ts, 4, lib=lib, amount=amount)
+        for name in sorted(AMOUNT_PROGRAMS):
+            stages, agg = AMOUNT_PROGRAMS[name]
+            for delta in (3, 1000):
+                want = brute_program(src, dst, ts, stages, agg, delta, amount=amount)
+                if not np.array_equal(og.program_count(stages, agg, delta, threads=1), want):
+                    return True
+    return False
+
+
+@pytest.mark.parametrize("name,orig,mutated", AMOUNT_MUTANTS, ids=[m[0] for m in AMOUNT_MUTANTS])
+def test_amount_pins_reject_mutant(tmp_path, name, orig, mutated):
+    text = open(SRC).read()
+    assert text.count(orig) == 1, f"mutation site for {name} not unique"
+    path = tmp_path / "mutant.c"
+    path.write_text(text.replace(orig, mutated))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-I", os.path.dirname(SRC), "-o", str(so), str(path)])
+    lib = oracle.load_library(str(so))
+    assert _amount_pins_reject(lib), f"mutant {name} survived the amount pins"
+
+
+def test_unmutated_oracle_passes_amount_pins():
+    assert not _amount_pins_reject(oracle._load())

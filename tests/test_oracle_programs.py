@@ -24,7 +24,7 @@ import aml_synth
 import oracle
 from brute import brute_program
 from paper_2604_12241_b300 import patterns as P
-from programs import NOVEL
+from programs import AMOUNT_PROGRAMS, AMOUNT_VALUES, NOVEL
 
 
 def _tuples(pattern):
@@ -139,3 +139,51 @@ def test_n_intermediary_scatter_gather_brute_force():
             np.testing.assert_array_equal(got, want, err_msg=f"seed {seed}, delta {delta}")
             n_nonzero += int(want.any())
     assert n_nonzero >= 3
+
+
+@pytest.mark.parametrize("name", sorted(AMOUNT_PROGRAMS))
+def test_amount_programs_match_brute_force(name):
+    """Amount constraints (RANGE on the trigger and stages, RATIO along the
+    walk) against the brute force, amounts from a small set so that ratio
+    bounds meet exact pairs."""
+    stages, agg = AMOUNT_PROGRAMS[name]
+    width = sum(1 if s[0] == 1 else 2 for s in stages[1:])
+    n_nonzero = 0
+    for seed in range(16):
+        n = 3 + seed % 3
+        E = (14 if width <= 2 else 10) + seed % 4
+        g = aml_synth.tiny_random(n, E, 8 + seed % 5, 2000 + seed, self_loops=(seed % 3 == 0))
+        rng = np.random.default_rng(seed)
+        # plus a triangle 0 -> 1 -> 2 -> 0 and a two-leg scatter-gather
+        # 0 -> {1, 2} -> 3 whose amounts fall off by 5% a hop, at random times
+        src = np.concatenate([g.src, [0, 1, 2, 0, 0, 1, 2]]).astype(np.int32)
+        dst = np.concatenate([g.dst, [1, 2, 0, 1, 2, 3, 3]]).astype(np.int32)
+        ts = np.concatenate([g.ts, np.sort(rng.integers(0, 8, 3)),
+                             np.sort(rng.integers(0, 8, 2)), np.sort(rng.integers(4, 12, 2))])
+        amount = np.concatenate([rng.choice(AMOUNT_VALUES, E), [100.0, 95.0, 90.0],
+                                 [100.0, 100.0], [95.0, 95.0]]).astype(np.float32)
+        n = max(n, 4)
+        og = oracle.OracleGraph(src, dst, ts, n, amount=amount)
+        for delta in (3, 1000):
+            want = brute_program(src, dst, ts, stages, agg, delta, amount=amount)
+            got = og.program_count(stages, agg, delta, threads=2)
+            np.testing.assert_array_equal(got, want, err_msg=f"{name}, seed {seed}, delta {delta}")
+            n_nonzero += int(want.any())
+    assert n_nonzero >= 2
+
+
+def test_amount_constraints_only_remove():
+    """A constrained program counts at most what the same program without the
+    constraints counts, edge by edge; with bounds that admit every amount it
+    counts the same."""
+    g = aml_synth.workload("tiny-10k")
+    og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes, amount=g.amount)
+    for name, (stages, agg) in AMOUNT_PROGRAMS.items():
+        free = [tuple(s[:9]) for s in stages]
+        loose = [tuple(s[:9]) + ((s[9], 0.0, 3.4e38, 0.0, 3.4e38) if len(s) > 9 else ())
+                 for s in stages]
+        c = og.program_count(stages, agg, P.DAY).astype(np.int64)
+        f = og.program_count(free, agg, P.DAY).astype(np.int64)
+        l = og.program_count(loose, agg, P.DAY).astype(np.int64)
+        assert (c <= f).all(), name
+        np.testing.assert_array_equal(l, f, err_msg=name)
