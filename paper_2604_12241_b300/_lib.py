@@ -36,7 +36,10 @@ class AmlError(RuntimeError):
 class aml_stage(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int32), ("a_var", ctypes.c_int32), ("a_dir", ctypes.c_int32),
                 ("b_var", ctypes.c_int32), ("b_dir", ctypes.c_int32), ("out_var", ctypes.c_int32),
-                ("order", ctypes.c_int32), ("window", ctypes.c_int32), ("skip_eq", ctypes.c_uint32)]
+                ("order", ctypes.c_int32), ("window", ctypes.c_int32), ("skip_eq", ctypes.c_uint32),
+                ("amount_flags", ctypes.c_uint32), ("amount_min", ctypes.c_float),
+                ("amount_max", ctypes.c_float), ("ratio_min", ctypes.c_float),
+                ("ratio_max", ctypes.c_float)]
 
 
 class aml_pattern(ctypes.Structure):
@@ -175,7 +178,8 @@ def make_patterns(patterns) -> tuple:
         st = (aml_stage * len(p.stages))()
         for j, s in enumerate(p.stages):
             st[j] = aml_stage(s.op, s.a_var, s.a_dir, s.b_var, s.b_dir, s.out_var, s.order,
-                              s.window, s.skip_eq)
+                              s.window, s.skip_eq, s.amount_flags, s.amount_min, s.amount_max,
+                              s.ratio_min, s.ratio_max)
         keep.append(st)
         arr[i].stages = ctypes.cast(st, ctypes.POINTER(aml_stage))
         arr[i].n_stages = len(p.stages)

@@ -240,6 +240,8 @@ constexpr int PROG_MAX_STAGES = 8;  // the trigger and up to 7 stages
 struct ProgStage {
   int8_t op, a_var, a_dir, b_var, b_dir, out_var, order, window;
   uint32_t skip;
+  uint32_t amt;              // AML_AMT_* constraints on the stage's edges
+  float amin, amax, rmin, rmax;
 };
 struct Prog {
   ProgStage st[PROG_MAX_STAGES];

@@ -211,7 +211,8 @@ void mine_graph_mode(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, 
 // Ordered cycles level by level from the cycle-capable legs (pipeline.cu).
 // The generic interpreter of stage programs (program.cu): counts of one
 // program into out[E]; waits for `s` to read the launch's status.
-void run_program(const GraphView& gv, const Prog& p, unsigned long long* out, cudaStream_t s);
+void run_program(const GraphView& gv, const float* amount, const Prog& p,
+                 unsigned long long* out, cudaStream_t s);
 
 void level_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K,
                         const CycleSlots& slots, const SubWindows& sub,

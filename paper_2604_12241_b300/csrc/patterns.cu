@@ -22,6 +22,7 @@ namespace {
 aml_stage st(int op, int a_var, int a_dir, int b_var, int b_dir, int out_var, int order,
              int window, uint32_t skip) {
   aml_stage s;
+  std::memset(&s, 0, sizeof(s));  // no amount constraints
   s.op = op; s.a_var = a_var; s.a_dir = a_dir; s.b_var = b_var; s.b_dir = b_dir;
   s.out_var = out_var; s.order = order; s.window = window; s.skip_eq = skip;
   return s;
@@ -91,6 +92,7 @@ std::vector<Template> templates() {
 
 bool same_stage(const aml_stage& a, const aml_stage& b) {
   if (a.op != b.op || a.out_var != b.out_var) return false;
+  if (a.amount_flags != b.amount_flags) return false;  // families have no amount constraints
   if (a.op == AML_OP_TRIGGER) return true;
   if (a.a_var != b.a_var || a.a_dir != b.a_dir || a.order != b.order || a.window != b.window ||
       a.skip_eq != b.skip_eq)
@@ -116,6 +118,16 @@ void validate(const aml_pattern& pat, int p) {
   const aml_stage& t = pat.stages[0];
   AML_REQUIRE(t.op == AML_OP_TRIGGER && t.out_var == 1, AML_EINVAL,
               where(p, 0) + "stage 0 must be the trigger binding N0 -> N1");
+  for (int s = 0; s < pat.n_stages; ++s) {
+    const aml_stage& x = pat.stages[s];
+    const uint32_t allowed = s == 0 ? AML_AMT_RANGE : (AML_AMT_RANGE | AML_AMT_RATIO);
+    AML_REQUIRE((x.amount_flags & ~allowed) == 0, AML_EINVAL,
+                where(p, s) + "bad amount flags (the trigger takes AML_AMT_RANGE only)");
+    AML_REQUIRE(!(x.amount_flags & AML_AMT_RANGE) || x.amount_min <= x.amount_max, AML_EINVAL,
+                where(p, s) + "amount range needs amount_min <= amount_max (no NaN)");
+    AML_REQUIRE(!(x.amount_flags & AML_AMT_RATIO) || x.ratio_min <= x.ratio_max, AML_EINVAL,
+                where(p, s) + "ratio range needs ratio_min <= ratio_max (no NaN)");
+  }
   int bound = 2;  // N0, N1
   for (int s = 1; s < pat.n_stages; ++s) {
     const aml_stage& x = pat.stages[s];
@@ -174,6 +186,11 @@ static Prog interpretable(const aml_pattern& pat, int p) {
     q.order = (int8_t)x.order;
     q.window = (int8_t)x.window;
     q.skip = s == 0 ? 0u : x.skip_eq;
+    q.amt = x.amount_flags;
+    q.amin = x.amount_min;
+    q.amax = x.amount_max;
+    q.rmin = x.ratio_min;
+    q.rmax = x.ratio_max;
   }
   return g;
 }

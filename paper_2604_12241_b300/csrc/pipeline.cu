@@ -583,7 +583,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   }
   // stage programs no family implements: the generic interpreter
   for (const auto& pr : programs)
-    run_program(gv, ps->progs[pr.second], acc.p + (int64_t)pr.first * E, s);
+    run_program(gv, g->amount, ps->progs[pr.second], acc.p + (int64_t)pr.first * E, s);
   AML_LAUNCH("k_assemble", s,
              k_assemble<<<grid_for(E, ASM_BLOCK), ASM_BLOCK,
                           (size_t)ASM_BLOCK * (ncols | 1) * sizeof(uint32_t), s>>>(P));

@@ -13,7 +13,8 @@
 // end; an INTERSECT stage finds its b-side edges by binary search in
 // the (counterparty, t, id) copy of the second operand's list.  The exact
 // conditions (ties broken by edge id, skip masks, closing onto a bound node,
-// pairwise distinct edges of an instance) are tested per candidate.
+// amount ranges and ratios, pairwise distinct edges of an instance) are
+// tested per candidate.
 //
 // Aggregates: EDGES stores the number of bindings of each trigger; DISTINCT
 // counts bindings first (to size a hash set), then stores the number of
@@ -98,8 +99,23 @@ __device__ bool set_insert(unsigned long long* table, uint64_t mask, unsigned lo
 // or PROG_DEFERRED when a single thread (WARP false) finds the first stage
 // heavy and queues the trigger for a warp.  With WARP, lane `lane` of the
 // warp walks the first-stage candidates lane, lane + 32, ...
+// the stage's amount constraints on edge f, whose predecessor on the walk
+// is edge prev; ratio * amount in double, the exact product of two floats
+__device__ __forceinline__ bool amount_ok(const ProgStage& q, const float* __restrict__ amount,
+                                          int32_t f, int32_t prev) {
+  if (!q.amt) return true;
+  const double a = __ldg(amount + f);
+  if ((q.amt & AML_AMT_RANGE) && !(a >= q.amin && a <= q.amax)) return false;
+  if (q.amt & AML_AMT_RATIO) {
+    const double b = __ldg(amount + prev);
+    if (!(a >= (double)q.rmin * b && a <= (double)q.rmax * b)) return false;
+  }
+  return true;
+}
+
 template <int MODE, bool WARP>
-__device__ __forceinline__ unsigned long long walk(const GraphView& g, const Prog& p, int32_t e0,
+__device__ __forceinline__ unsigned long long walk(const GraphView& g, const float* amount,
+                                                   const Prog& p, int32_t e0,
                                                    int lane, unsigned long long* __restrict__ out,
                                                    unsigned long long* __restrict__ table,
                                                    uint64_t table_mask, ProgCtl* ctl,
@@ -115,6 +131,7 @@ __device__ __forceinline__ unsigned long long walk(const GraphView& g, const Pro
   node[0] = g.src[e0];
   node[1] = g.dst[e0];
   if (node[0] == node[1]) return 0;  // self-loops are in no list; their rows stay 0
+  if (!amount_ok(p.st[0], amount, e0, e0)) return 0;  // not a trigger (range only)
   reach_e[0] = reach_e[1] = e0;
   reach_t[0] = reach_t[1] = t0;
   nb[1] = 2;
@@ -213,6 +230,7 @@ __device__ __forceinline__ unsigned long long walk(const GraphView& g, const Pro
         if (q.order == AML_ORDER_AFTER_TRIGGER && !before(t0, e0, tf, f)) continue;
         if (!span && before(t0, e0, tf, f)) continue;  // trailing: f <= e0
         if (!node_ok(q, s, x)) continue;
+        if (!amount_ok(q, amount, f, reach_e[A])) continue;
         if (MODE == AGG_CREDIT && used(f, s)) continue;
         ea[s] = f;
         xa[s] = x;
@@ -236,6 +254,7 @@ __device__ __forceinline__ unsigned long long walk(const GraphView& g, const Pro
         if (q.order == AML_ORDER_BEFORE && !before(tb, fb, tfa, fa)) continue;
         if (q.order == AML_ORDER_AFTER_TRIGGER && !before(t0, e0, tb, fb)) continue;
         if (!span && before(t0, e0, tb, fb)) continue;
+        if (!amount_ok(q, amount, fb, fa)) continue;
         if (MODE == AGG_CREDIT && (fb == fa || used(fb, s))) continue;
         eb[s] = fb;
         tmin = span ? min(min(smin[s], tfa), tb) : smin[s];
@@ -255,6 +274,7 @@ __device__ __forceinline__ unsigned long long walk(const GraphView& g, const Pro
       if (q.order == AML_ORDER_AFTER_TRIGGER && !before(t0, e0, tfa, fa)) continue;
       if (!span && before(t0, e0, tfa, fa)) continue;
       if (!node_ok(q, s, x)) continue;
+      if (!amount_ok(q, amount, fa, reach_e[A])) continue;
       if (MODE == AGG_CREDIT && used(fa, s)) continue;
       ea[s] = fa;
       xa[s] = x;
@@ -308,7 +328,7 @@ __device__ __forceinline__ unsigned long long walk(const GraphView& g, const Pro
 
 // one thread per trigger edge; heavy triggers are queued for k_program_warp
 template <int MODE>
-__global__ void __launch_bounds__(PROG_BLOCK) k_program(GraphView g, Prog p,
+__global__ void __launch_bounds__(PROG_BLOCK) k_program(GraphView g, const float* amount, Prog p,
                                                         unsigned long long* __restrict__ out,
                                                         unsigned long long* __restrict__ table,
                                                         uint64_t table_mask, ProgCtl* ctl,
@@ -317,14 +337,15 @@ __global__ void __launch_bounds__(PROG_BLOCK) k_program(GraphView g, Prog p,
   if (e64 >= g.E) return;
   const int32_t e0 = (int32_t)e64;
   const unsigned long long f =
-      walk<MODE, false>(g, p, e0, 0, out, table, table_mask, ctl, heavy);
+      walk<MODE, false>(g, amount, p, e0, 0, out, table, table_mask, ctl, heavy);
   if (MODE != AGG_CREDIT && f != PROG_DEFERRED) out[e0] = f;
 }
 
 // the queued heavy triggers, one warp each, taken from a shared cursor by
 // resident warps
 template <int MODE>
-__global__ void __launch_bounds__(PROG_BLOCK) k_program_warp(GraphView g, Prog p,
+__global__ void __launch_bounds__(PROG_BLOCK) k_program_warp(GraphView g, const float* amount,
+                                                             Prog p,
                                                              unsigned long long* __restrict__ out,
                                                              unsigned long long* __restrict__ table,
                                                              uint64_t table_mask, ProgCtl* ctl,
@@ -338,7 +359,7 @@ __global__ void __launch_bounds__(PROG_BLOCK) k_program_warp(GraphView g, Prog p
     if (item >= n_heavy || *(volatile uint32_t*)&ctl->stop) return;
     const int32_t e0 = heavy[item];
     unsigned long long f =
-        walk<MODE, true>(g, p, e0, lane, out, table, table_mask, ctl, nullptr);
+        walk<MODE, true>(g, amount, p, e0, lane, out, table, table_mask, ctl, nullptr);
     for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
     if (MODE != AGG_CREDIT && lane == 0) out[e0] = f;
   }
@@ -357,7 +378,8 @@ __global__ void k_sum_u64(const unsigned long long* __restrict__ v, int64_t n,
 // Counts of one interpreted program into out[E] (uint64; INSTANCES adds to
 // it, so it must hold zeros; EDGES and DISTINCT overwrite it).  Waits for
 // `s` to read the launch's status.
-void run_program(const GraphView& gv, const Prog& p, unsigned long long* out, cudaStream_t s) {
+void run_program(const GraphView& gv, const float* amount, const Prog& p,
+                 unsigned long long* out, cudaStream_t s) {
   const int64_t E = gv.E;
   if (E == 0) return;
   DBuf<ProgCtl> ctl(1, s);
@@ -377,11 +399,11 @@ void run_program(const GraphView& gv, const Prog& p, unsigned long long* out, cu
   auto pass = [&](auto mode, unsigned long long* table, uint64_t mask) {
     constexpr int M = decltype(mode)::value;
     AML_LAUNCH("k_program", s,
-               k_program<M><<<grid, PROG_BLOCK, 0, s>>>(gv, p, out, table, mask, ctl.p,
+               k_program<M><<<grid, PROG_BLOCK, 0, s>>>(gv, amount, p, out, table, mask, ctl.p,
                                                         heavy.p));
     AML_LAUNCH("k_program_warp", s,
-               k_program_warp<M><<<warp_grid, PROG_BLOCK, 0, s>>>(gv, p, out, table, mask,
-                                                                  ctl.p, heavy.p));
+               k_program_warp<M><<<warp_grid, PROG_BLOCK, 0, s>>>(gv, amount, p, out, table,
+                                                                  mask, ctl.p, heavy.p));
   };
   if (p.agg == AML_AGG_INSTANCES) {
     pass(std::integral_constant<int, AGG_CREDIT>{}, nullptr, 0);

@@ -16,6 +16,7 @@ DIR_OUT, DIR_IN = 0, 1
 ORDER_NONE, ORDER_AFTER, ORDER_BEFORE, ORDER_LEG, ORDER_AFTER_TRIGGER = 0, 1, 2, 3, 4
 WIN_TRAILING, WIN_SPAN = 0, 1
 AGG_EDGES, AGG_DISTINCT, AGG_INSTANCES = 0, 1, 2
+AMT_RANGE, AMT_RATIO = 1, 2
 FAM_NAMES = {0: "DEG_OUT", 1: "DEG_IN", 2: "FAN_OUT", 3: "FAN_IN", 4: "GS", 5: "SG", 6: "CYC",
              7: "CYCW", 8: "PROGRAM"}
 
@@ -34,6 +35,12 @@ class Stage:
     order: int = ORDER_NONE
     window: int = WIN_TRAILING
     skip_eq: int = 0
+    # amount constraints on the stage's edges (AMT_RANGE, AMT_RATIO)
+    amount_flags: int = 0
+    amount_min: float = 0.0
+    amount_max: float = 0.0
+    ratio_min: float = 0.0
+    ratio_max: float = 0.0
 
 
 @dataclasses.dataclass(frozen=True)
@@ -50,8 +57,12 @@ class Pattern:
 def program(stages, aggregate: int, delta: int, name: str = "",
             interpret: bool = False) -> Pattern:
     """A pattern from (op, a_var, a_dir, b_var, b_dir, out_var, order, window,
-    skip_eq) tuples or Stage objects, stage 0 the trigger."""
-    st = tuple(s if isinstance(s, Stage) else Stage(*[int(v) for v in s]) for s in stages)
+    skip_eq[, amount_flags, amount_min, amount_max, ratio_min, ratio_max])
+    tuples or Stage objects, stage 0 the trigger."""
+    def stage(v):
+        v = tuple(v)
+        return Stage(*[int(x) for x in v[:10]], *[float(x) for x in v[10:]])
+    st = tuple(s if isinstance(s, Stage) else stage(s) for s in stages)
     return Pattern(st, int(aggregate), int(delta), name, interpret)
 
 

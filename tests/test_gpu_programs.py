@@ -13,7 +13,7 @@ import aml_synth
 import oracle
 import paper_2604_12241_b300 as aml
 from paper_2604_12241_b300 import patterns as P
-from programs import NOVEL, F, T, OUT, NONE, SPAN, EDGES
+from programs import AMOUNT_PROGRAMS, AMOUNT_VALUES, NOVEL, F, T, OUT, NONE, SPAN, EDGES
 
 pytestmark = pytest.mark.gpu
 
@@ -23,7 +23,7 @@ def _tuples(pattern):
 
 
 def _mine(g, pats):
-    graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes)
+    graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes, amount=getattr(g, "amount", None))
     out = aml.mine(graph, aml.PatternSet(pats)).cpu().numpy().view(np.uint32)
     graph.close()
     return out
@@ -141,3 +141,46 @@ def test_work_limit_ends_the_launch_with_an_error():
     og = oracle.OracleGraph(src, dst, ts, N)
     np.testing.assert_array_equal(out[:, 0], og.count_all([("deg_out", 100)])[:, 0])
     graph.close()
+
+
+def test_amount_programs_match_oracle():
+    """Amount ranges and ratios: tiny graphs with planted motifs whose
+    amounts meet the ratio bounds exactly, and tiny-10k with its lognormal
+    amounts."""
+    from types import SimpleNamespace
+    cases = []
+    for seed in range(4):
+        base = aml_synth.tiny_random(6, 120, 40, 4000 + seed, self_loops=(seed == 1))
+        rng = np.random.default_rng(seed)
+        src = np.concatenate([base.src, [0, 1, 2, 0, 0, 1, 2]]).astype(np.int32)
+        dst = np.concatenate([base.dst, [1, 2, 0, 1, 2, 3, 3]]).astype(np.int32)
+        ts = np.concatenate([base.ts, np.sort(rng.integers(0, 20, 3)),
+                             np.sort(rng.integers(0, 20, 2)),
+                             np.sort(rng.integers(10, 30, 2))]).astype(np.int32)
+        amount = np.concatenate([rng.choice(AMOUNT_VALUES, 120), [100.0, 95.0, 90.0],
+                                 [100.0, 100.0], [95.0, 95.0]]).astype(np.float32)
+        cases.append((SimpleNamespace(src=src, dst=dst, ts=ts, n_nodes=6, amount=amount),
+                      (5, 1000)))
+    cases.append((aml_synth.workload("tiny-10k"), (P.DAY,)))
+    for g, deltas in cases:
+        og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes, amount=g.amount)
+        for delta in deltas:
+            pats = [P.program(st, agg, delta, name=n) for n, (st, agg) in AMOUNT_PROGRAMS.items()]
+            got = _mine(g, pats)
+            for j, p in enumerate(pats):
+                want = og.program_count(_tuples(p), p.aggregate, p.delta)
+                np.testing.assert_array_equal(got[:, j], want, err_msg=f"{p.name}, delta {delta}")
+
+
+def test_amount_constraints_are_validated():
+    bad = [P.program([T, F(1, OUT, 2, NONE, SPAN) + (1, 5.0, 1.0, 0.0, 0.0)], EDGES, 10),
+           P.program([T + (2, 0.0, 0.0, 0.5, 1.0), F(1, OUT, 2, NONE, SPAN)], EDGES, 10),
+           P.program([T, F(1, OUT, 2, NONE, SPAN) + (4, 0.0, 0.0, 0.0, 0.0)], EDGES, 10)]
+    for p in bad:
+        with pytest.raises(aml.AmlError) as ei:
+            aml.PatternSet([p])
+        assert ei.value.name == "AML_EINVAL"
+    # any amount constraint sends a family program to the interpreter
+    st = [dataclasses.astuple(s) for s in P.gather_scatter(10).stages]
+    st[1] = st[1][:9] + (1, 0.0, 1e9, 0.0, 0.0)
+    assert aml.PatternSet([P.program(st, P.AGG_INSTANCES, 10)]).columns[0]["family"] == 8
