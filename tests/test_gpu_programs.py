@@ -184,3 +184,18 @@ def test_amount_constraints_are_validated():
     st = [dataclasses.astuple(s) for s in P.gather_scatter(10).stages]
     st[1] = st[1][:9] + (1, 0.0, 1e9, 0.0, 0.0)
     assert aml.PatternSet([P.program(st, P.AGG_INSTANCES, 10)]).columns[0]["family"] == 8
+
+
+def test_programs_match_oracle_on_hi_small():
+    """Full size, every row: hi-small (5,078,345 edges) with its amounts, a
+    3-hop path, an intersection program, interpreted GS and an amount
+    program, in one mine as the bench runs them."""
+    g = aml_synth.workload("hi-small")
+    og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes, amount=g.amount)
+    pats = [P.program(*NOVEL["path3"], P.DAY), P.program(*NOVEL["common_out"], P.DAY),
+            P.interpreted(P.gather_scatter(P.DAY)),
+            P.program(*AMOUNT_PROGRAMS["fee_forward"], P.DAY)]
+    got = _mine(g, pats)
+    for j, p in enumerate(pats):
+        want = og.program_count(_tuples(p), p.aggregate, p.delta)
+        np.testing.assert_array_equal(got[:, j], want, err_msg=f"column {j}")
