@@ -177,3 +177,33 @@ def test_stream_uses_both_leg_emissions():
     np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
     assert st.check_graph() == 0
     st.close()
+
+
+@pytest.mark.parametrize("kind", ["no_sg", "trailing_only", "cycles_only"])
+def test_stream_column_subsets(kind):
+    """Pattern sets without scatter-gather columns (the delta leg emission
+    then walks no marked slots), with trailing-window columns only (no leg
+    pass at all), and with cycles only: the resident rows equal a full mine
+    after appends with eviction."""
+    g = aml_synth.workload("tiny-10k")
+    if kind == "no_sg":
+        pats = [p for p in P.standard(P.DAY) + P.standard(P.WEEK) if not p.name.startswith("SG")]
+    elif kind == "trailing_only":
+        pats = [P.deg_out(P.DAY), P.fan_in(P.WEEK), P.fan_out(P.DAY)]
+    else:
+        pats = [P.cycle(k, P.DAY) for k in (2, 3, 4)] + [P.cycle(3, P.WEEK)]
+    st = aml.Stream(aml.PatternSet(pats), g.n_nodes, resident_window=8 * P.DAY,
+                    mem_budget=1 << 30)
+    rng = np.random.default_rng(17)
+    pos, E = 0, g.n_edges
+    while pos < E:
+        n = int(min(E - pos, rng.integers(1, 9000)))
+        st.append(g.src[pos:pos + n], g.dst[pos:pos + n], g.ts[pos:pos + n])
+        pos += n
+    want = full_mine(g, E, pats)
+    inf = st.info()
+    r0, nr = inf["resident_first_row"], inf["resident_rows"]
+    assert r0 > 0
+    np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
+    assert st.check_graph() == 0
+    st.close()
