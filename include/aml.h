@@ -262,8 +262,8 @@ typedef struct aml_pattern_set aml_pattern_set;
  * scatter edges, or both gather edges).  Limits: at most 8 stages; one
  * launch visits at most 2^34 candidate edges (beyond: AML_EUNSUPPORTED and
  * the column is not written).  One thread walks each trigger's bindings
- * depth first.  Not available to AML_MINE_GRAPH or aml_stream_open
- * (AML_EUNSUPPORTED). */
+ * depth first (a warp when the first stage has more than 64 candidates).
+ * Not available to AML_MINE_GRAPH or aml_stream_open (AML_EUNSUPPORTED). */
 
 /* Validate and plan n patterns; column j of the output is pattern j.
  * Validation (Sec. 6: "validates operand dependencies between stages"):
