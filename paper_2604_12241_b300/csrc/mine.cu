@@ -883,11 +883,19 @@ __device__ __forceinline__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRe
   uint32_t* cur = reinterpret_cast<uint32_t*>(S.key);
   // this thread's records stay in registers from the first read on
   LegRec r[PER];
+  int any_new = 0;
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     const int i = threadIdx.x + k * BS;
-    if (i < n) r[k] = R[i];
+    if (i < n) {
+      r[k] = R[i];
+      any_new |= r[k].b >= new_from;
+    }
   }
+  // delta counting: a pair counts only with a new gather edge, and both legs
+  // of a pair share a key, hence a bucket: a bucket without new legs has
+  // nothing to count
+  if (new_from > 0 && !__syncthreads_or(any_new)) return;
   int tab = 64;
   while (tab < 2 * n) tab <<= 1;
   for (int t = threadIdx.x; t < tab; t += BS) {
