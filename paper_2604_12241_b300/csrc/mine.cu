@@ -634,11 +634,24 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit_delta(
 // and counts, for every record of a group of two or more, its partners.
 
 // bucket histogram of compacted records (delta counting)
+// (keep: only records of buckets marked in it; null: all)
 __global__ void __launch_bounds__(256) k_sg_hist(const LegRec* __restrict__ rec, int64_t n,
-                                                 int bits, uint32_t* __restrict__ hist) {
+                                                 int bits, const uint8_t* __restrict__ keep,
+                                                 uint32_t* __restrict__ hist) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in = i < n;
-  if (in) atomicAdd(hist + bucket_of(rec[i].key, bits), 1u);
+  if (i >= n) return;
+  const uint32_t q = bucket_of(rec[i].key, bits);
+  if (!keep || keep[q]) atomicAdd(hist + q, 1u);
+}
+
+// delta counting: marks the buckets holding a new leg (a leg whose gather
+// edge is new); a pair counts only with one, and both legs of a pair share
+// a key, hence a bucket, so the other buckets need not be grouped at all
+__global__ void __launch_bounds__(256) k_sg_new_buckets(const LegRec* __restrict__ rec, int64_t n,
+                                                        int bits, int32_t new_from,
+                                                        uint8_t* __restrict__ keep) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && rec[i].b >= new_from) keep[bucket_of(rec[i].key, bits)] = 1;
 }
 
 // mask bit v set for v = node_of[e], e in [from, E)
@@ -654,7 +667,7 @@ __global__ void __launch_bounds__(256) k_mark_nodes(const int32_t* __restrict__ 
 // SG_PART_ITEMS independent records per thread keep several cursor atomics
 // in flight at once (the kernel is bound by their latency)
 __global__ void __launch_bounds__(256) k_sg_partition(const LegRec* __restrict__ rec, int64_t n,
-                                                      int bits,
+                                                      int bits, const uint8_t* __restrict__ keep,
                                                       uint32_t* __restrict__ cursor,
                                                       LegRec* __restrict__ out) {
   const int64_t base = (int64_t)blockIdx.x * blockDim.x * SG_PART_ITEMS + threadIdx.x;
@@ -669,12 +682,16 @@ __global__ void __launch_bounds__(256) k_sg_partition(const LegRec* __restrict__
       bkt[k] = bucket_of(r[k].key, bits);
     }
   }
+  bool take[SG_PART_ITEMS];
 #pragma unroll
   for (int k = 0; k < SG_PART_ITEMS; ++k)
-    if (base + (int64_t)k * blockDim.x < n) pos[k] = atomicAdd(cursor + bkt[k], 1u);
+    take[k] = base + (int64_t)k * blockDim.x < n && (!keep || keep[bkt[k]]);
 #pragma unroll
   for (int k = 0; k < SG_PART_ITEMS; ++k)
-    if (base + (int64_t)k * blockDim.x < n) out[pos[k]] = r[k];
+    if (take[k]) pos[k] = atomicAdd(cursor + bkt[k], 1u);
+#pragma unroll
+  for (int k = 0; k < SG_PART_ITEMS; ++k)
+    if (take[k]) out[pos[k]] = r[k];
 }
 
 

@@ -510,6 +510,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
                       sub);
     }
     int64_t n_sg = nl;  // records to bucket
+    DBuf<uint8_t> keep_bkt;  // delta counting: the buckets holding a new leg
     if (sg_filter) {
       unsigned long long kept = 0;
       const SmallRead rd{&kept, n_rec.p, 8};
@@ -517,8 +518,14 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       n_sg = (int64_t)kept;
       if (n_sg > 1) {
         size_buckets(n_sg);
+        keep_bkt = DBuf<uint8_t>((size_t)nb, s);
+        AML_CUDA(cudaMemsetAsync(keep_bkt.p, 0, (size_t)nb, s));
+        AML_LAUNCH("k_sg_new_buckets", s,
+                   k_sg_new_buckets<<<grid_for(n_sg, 256), 256, 0, s>>>(rec.p, n_sg, S.bits,
+                                                                       new_from, keep_bkt.p));
         AML_LAUNCH("k_sg_hist", s,
-                   k_sg_hist<<<grid_for(n_sg, 256), 256, 0, s>>>(rec.p, n_sg, S.bits, hist.p));
+                   k_sg_hist<<<grid_for(n_sg, 256), 256, 0, s>>>(rec.p, n_sg, S.bits, keep_bkt.p,
+                                                                hist.p));
       }
     }
     // 3. scatter-gather: bucket the leg records, group each bucket by (s, d)
@@ -535,7 +542,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       DBuf<LegRec> part((size_t)nl, t);
       AML_LAUNCH("k_sg_partition", t,
                  k_sg_partition<<<grid_for(nl, 256 * SG_PART_ITEMS), 256, 0, t>>>(
-                     rec.p, nl, S.bits, hist.p, part.p));
+                     rec.p, nl, S.bits, keep_bkt.p, hist.p, part.p));
       // buckets beyond SG_CAP records: listed by k_sg_bucket, grouped by
       // k_sg_bucket_big (one large-table block per SM)
       DBuf<uint32_t> overflow((size_t)nb + 1, t);
