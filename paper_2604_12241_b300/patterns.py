@@ -156,6 +156,34 @@ def scatter_gather_n(n: int, delta: int) -> Pattern:
     return Pattern(tuple(stages), AGG_INSTANCES, delta, f"SG{n}@{delta}", interpret=True)
 
 
+def gather_scatter_n(n_in: int, n_out: int, delta: int) -> Pattern:
+    """Gather-scatter through a hub with at least n_in senders and n_out
+    receivers: the trigger x1 -> h is the latest gather edge, n_in - 1 earlier
+    gathers from further distinct senders, then n_out scatters after the
+    trigger to distinct receivers that are not senders; all edges within
+    delta.  Run by the generic interpreter: an edge's count is the number of
+    such bindings (ordered tuples) it belongs to, nonzero exactly when it
+    takes part in a gather-scatter of at least that size.  (1, 1) is the GS
+    program itself."""
+    if n_in < 1 or n_out < 1 or n_in + n_out > 8:
+        raise ValueError("need n_in, n_out >= 1 and n_in + n_out <= 8 (at most 8 stages)")
+    stages = [TRIGGER]
+    senders = [0]
+    for i in range(n_in - 1):  # earlier gathers: new variables 2, 3, ...
+        v = 2 + i
+        stages.append(Stage(OP_FOR_ALL, 1, DIR_IN, out_var=v, order=ORDER_BEFORE,
+                            window=WIN_SPAN, skip_eq=_skip(*senders)))
+        senders.append(v)
+    receivers = []
+    for i in range(n_out):
+        v = 1 + n_in + i
+        stages.append(Stage(OP_FOR_ALL, 1, DIR_OUT, out_var=v, order=ORDER_AFTER,
+                            window=WIN_SPAN, skip_eq=_skip(*senders, *receivers)))
+        receivers.append(v)
+    return Pattern(tuple(stages), AGG_INSTANCES, delta, f"GS{n_in}x{n_out}@{delta}",
+                   interpret=True)
+
+
 def scatter_gather_nodes(delta: int) -> Pattern:
     """The node-level scatter-gather: for each scatter edge s -> m1 (the
     trigger), the number of distinct other intermediaries m2 that complete a

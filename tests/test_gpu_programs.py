@@ -91,6 +91,7 @@ def test_programs_match_oracle_on_tiny10k():
     pats += _family_programs(P.DAY)
     pats += [P.scatter_gather_n(n, P.DAY) for n in (3, 4)]  # "at least N" intermediaries
     pats += [P.scatter_gather_nodes(P.DAY)]                      # node-level SG
+    pats += [P.gather_scatter_n(2, 2, P.DAY), P.gather_scatter_n(3, 1, P.DAY)]
     # family columns beside the interpreted ones in the same mine
     fam = P.standard(P.DAY)
     got = _mine(g, pats + fam)

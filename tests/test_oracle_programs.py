@@ -187,3 +187,44 @@ def test_amount_constraints_only_remove():
         l = og.program_count(loose, agg, P.DAY).astype(np.int64)
         assert (c <= f).all(), name
         np.testing.assert_array_equal(l, f, err_msg=name)
+
+
+@pytest.mark.parametrize("n_in,n_out", [(1, 1), (2, 1), (1, 2), (2, 2), (3, 2)])
+def test_gather_scatter_n_closed_form(n_in, n_out):
+    """A planted star, k_in senders into a hub and then k_out receivers out of
+    it, every gather before every scatter: a gather edge lies in
+    C(k_in-1, n_in-1) (n_in-1)! k_out!/(k_out-n_out)! bindings, a scatter
+    edge in C(k_in, n_in) (n_in-1)! n_out (k_out-1)!/(k_out-n_out)!."""
+    k_in, k_out, hub = 4, 3, 0
+    src = [1 + i for i in range(k_in)] + [hub] * k_out
+    dst = [hub] * k_in + [1 + k_in + i for i in range(k_out)]
+    ts = list(range(k_in + k_out))
+    og = oracle.OracleGraph(src, dst, ts, 1 + k_in + k_out)
+    pat = P.gather_scatter_n(n_in, n_out, 100)
+    got = og.program_count(_tuples(pat), pat.aggregate, pat.delta)
+    f, c = math.factorial, math.comb
+    perm = lambda n, k: f(n) // f(n - k)
+    want_g = c(k_in - 1, n_in - 1) * f(n_in - 1) * perm(k_out, n_out)
+    want_s = c(k_in, n_in) * f(n_in - 1) * n_out * perm(k_out - 1, n_out - 1)
+    assert (got[:k_in] == want_g).all() and (got[k_in:] == want_s).all(), got
+    if (n_in, n_out) == (1, 1):  # the GS program: equals the family
+        np.testing.assert_array_equal(got, og.count_all([("gs", 100)])[:, 0])
+
+
+def test_gather_scatter_n_brute_force():
+    """A hub 0 with three senders and three receivers at random times (so
+    some scatters precede some gathers), a repeated sender, and noise."""
+    pat = P.gather_scatter_n(2, 2, 0)
+    n_nonzero = 0
+    for seed in range(6):
+        rng = np.random.default_rng(5000 + seed)
+        src = [1, 2, 3, 1, 0, 0, 0] + list(rng.integers(0, 7, 3))
+        dst = [0, 0, 0, 0, 4, 5, 1] + list(rng.integers(0, 7, 3))
+        ts = list(rng.integers(0, 8, len(src)))
+        og = oracle.OracleGraph(src, dst, ts, 7)
+        for delta in (3, 1000):
+            want = brute_program(src, dst, ts, _tuples(pat), pat.aggregate, delta)
+            got = og.program_count(_tuples(pat), pat.aggregate, delta, threads=2)
+            np.testing.assert_array_equal(got, want, err_msg=f"seed {seed}, delta {delta}")
+            n_nonzero += int(want.any())
+    assert n_nonzero >= 3
