@@ -313,11 +313,12 @@ void fan_launch(const Adj& a, int64_t Ev, const FanDeltas& fd, int2* df, cudaStr
 //
 // Delta counting needs DEG/FAN only for the new edges (ids >= new_from),
 // which are the last slots of their rows (they come after every older edge
-// in the (t, id) order).  One warp per row holding new slots: the warp
-// counts the distinct counterparties of the first new slot's windows
+// in the (t, id) order).  One block per row holding new slots: its threads
+// count the distinct counterparties of the first new slot's windows
 // directly (slots whose previous same-counterparty slot lies before the
-// window start), then one lane walks the row's remaining new slots with
-// the repeat-delta recurrence (two pointers).
+// window start; a hub's window holds tens of thousands of slots), then one
+// thread walks the row's remaining new slots with the repeat-delta
+// recurrence (two pointers).
 
 // first new slot of every row that has one: rows[*n_rows++]
 __global__ void __launch_bounds__(256) k_batch_rows(const int32_t* __restrict__ pos,
@@ -333,8 +334,10 @@ __global__ void __launch_bounds__(256) k_batch_rows(const int32_t* __restrict__ 
   if (p == rstart[p] || eid[p - 1] < new_from) rows[atomicAdd(n_rows, 1u)] = p;
 }
 
+constexpr int FAN_BATCH_BLOCK = 128;
+
 template <int W>
-__global__ void __launch_bounds__(256) k_fan_batch(const int32_t* __restrict__ rstart,
+__global__ void __launch_bounds__(FAN_BATCH_BLOCK) k_fan_batch(const int32_t* __restrict__ rstart,
                                                    const int32_t* __restrict__ t,
                                                    const int32_t* __restrict__ eid,
                                                    const int32_t* __restrict__ prev,
@@ -342,9 +345,10 @@ __global__ void __launch_bounds__(256) k_fan_batch(const int32_t* __restrict__ r
                                                    FanDeltas fd, const int32_t* __restrict__ rows,
                                                    const unsigned int* __restrict__ n_rows,
                                                    int2* __restrict__ df) {
-  const int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wi >= (int64_t)*n_rows) return;  // warp-uniform
+  __shared__ int32_t s_c[FAN_BATCH_BLOCK / 32][W];
+  const int64_t wi = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (wi >= (int64_t)*n_rows) return;  // block-uniform
   const int32_t p1 = rows[wi];
   const int32_t rs = __ldg(rstart + p1);
   const int64_t tp1 = __ldg(t + p1);
@@ -360,15 +364,23 @@ __global__ void __launch_bounds__(256) k_fan_batch(const int32_t* __restrict__ r
   int32_t c[W];
 #pragma unroll
   for (int k = 0; k < W; ++k) c[k] = 0;
-  for (int32_t q = lb[0] + lane; q <= p1; q += 32) {
+  for (int32_t q = lb[0] + threadIdx.x; q <= p1; q += FAN_BATCH_BLOCK) {
     const int32_t pv = __ldg(prev + q);
 #pragma unroll
     for (int k = 0; k < W; ++k) c[k] += (q >= lb[k] && pv < lb[k]) ? 1 : 0;
   }
 #pragma unroll
-  for (int k = 0; k < W; ++k)
+  for (int k = 0; k < W; ++k) {
     for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(0xffffffffu, c[k], o);
-  if (lane != 0) return;
+    if (lane == 0) s_c[warp][k] = c[k];
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    c[k] = 0;
+    for (int w = 0; w < FAN_BATCH_BLOCK / 32; ++w) c[k] += s_c[w][k];
+  }
   int32_t R[W];
   int2 v[W];
 #pragma unroll
@@ -412,7 +424,7 @@ void fan_batch_launch(const Adj& a, int64_t Ev, int64_t E, int64_t new_from,
              k_batch_rows<<<grid_for(nb, 256), 256, 0, s>>>(a.pos, a.rstart, a.eid, new_from, E,
                                                             rows.p, n_rows.p));
   AML_LAUNCH("k_fan_batch", s,
-             k_fan_batch<W><<<grid_for(nb * 32, 256), 256, 0, s>>>(
+             k_fan_batch<W><<<(unsigned)nb, FAN_BATCH_BLOCK, 0, s>>>(
                  a.rstart, a.t, a.eid, a.prev, a.next, Ev, fd, rows.p, n_rows.p, df));
 }
 
