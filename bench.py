@@ -175,10 +175,10 @@ def measured_peak():
 # full size (profiles/dram_hi_small.md), valid only for the kernel sources it
 # was taken with: KERNEL_DIGEST is the digest (kernel_digest()) of the files
 # that define the measured kernels.
-KERNEL_DIGEST = "bba50ace3219b1d5"
-MEASURED_TRAFFIC = {"k_cyc_level": 267.2e6, "k_sg_bucket": 518.5e6, "k_leg_emit": 610.6e6,
-                    "k_sg_partition": 544.3e6, "k_fan_reduce": 230.6e6, "k_fan_scan": 314.6e6,
-                    "k_assemble": 1077.1e6, "k_leg_count": 698.1e6}
+KERNEL_DIGEST = "ebf1425e9b714bfe"
+MEASURED_TRAFFIC = {"k_cyc_level": 266.9e6, "k_sg_bucket": 518.8e6, "k_leg_emit": 610.2e6,
+                    "k_sg_partition": 543.4e6, "k_fan_reduce": 231.8e6, "k_fan_scan": 314.7e6,
+                    "k_assemble": 1076.7e6, "k_leg_count": 698.1e6}
 
 
 TRAFFIC_SOURCES = ("aml_internal.cuh", "fan.cu", "mine.cu", "mine.cuh", "pipeline.cu", "prims.cu")
