@@ -200,3 +200,18 @@ def test_programs_match_oracle_on_hi_small():
     for j, p in enumerate(pats):
         want = og.program_count(_tuples(p), p.aggregate, p.delta)
         np.testing.assert_array_equal(got[:, j], want, err_msg=f"column {j}")
+
+
+def test_programs_in_every_cycle_mode():
+    """Interpreted columns beside family columns give the same counts in the
+    plain, persistent and learned cycle modes (the interpreter runs after
+    the cycle search, whichever form it takes)."""
+    g = aml_synth.workload("tiny-10k")
+    pats = (P.standard(P.DAY) + [P.program(*NOVEL["path3"], P.DAY),
+                                 P.program(*NOVEL["distinct_2hop"], P.DAY)])
+    graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes)
+    ps = aml.PatternSet(pats)
+    outs = [aml.mine(graph, ps, mode=m).cpu().numpy() for m in ("plain", "persistent", "learned")]
+    graph.close()
+    np.testing.assert_array_equal(outs[1], outs[0])
+    np.testing.assert_array_equal(outs[2], outs[0])
