@@ -276,8 +276,9 @@ aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts
 // per-row offset (one coalesced pass); only the new edges are sorted.  In a
 // row's (counterparty, t, id) copy, a kept entry moves up past the new edges
 // with a smaller counterparty and a new entry past the kept ones with a
-// counterparty no larger than its own.  Same-counterparty links are rebuilt
-// from the new copy.  The result equals a full build of the new window.
+// counterparty no larger than its own.  Same-counterparty links move with
+// the kept slots; a new edge is linked to the entry before it in the new
+// copy.  The result equals a full build of the new window.
 
 // per row: dropped prefix (first slot with id >= drop) and the new length
 __global__ void k_upd_rows(const int32_t* __restrict__ optr, const int32_t* __restrict__ oeid,
@@ -323,22 +324,32 @@ __global__ void k_upd_pos(const int32_t* __restrict__ opos, const int32_t* __res
   pos[e] = p < 0 ? -1 : p + shift[row_of[e]];
 }
 
+// kept slots, and their same-counterparty links: the previous slot of the
+// counterparty moves with the row unless it was dropped (then no kept slot
+// precedes), the next one always moves with it (a new edge that follows is
+// linked afterwards by k_upd_new_links)
 __global__ void k_upd_keep(const int32_t* __restrict__ oeid, const int32_t* __restrict__ orstart,
                            const int32_t* __restrict__ onbr, const int32_t* __restrict__ ot,
+                           const int32_t* __restrict__ oprev, const int32_t* __restrict__ onext,
                            const int4* __restrict__ info, int32_t drop, int64_t oEv,
                            int32_t* __restrict__ nbr, int32_t* __restrict__ t,
-                           int32_t* __restrict__ eid, int32_t* __restrict__ rstart) {
+                           int32_t* __restrict__ eid, int32_t* __restrict__ rstart,
+                           int32_t* __restrict__ prev, int32_t* __restrict__ next) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= oEv) return;
   const int32_t e = oeid[p];
   if (e < drop) return;
   const int32_t rs = orstart[p];
   const int4 ri = info[rs];
-  const int32_t q = ri.x + ((int32_t)p - rs - ri.y);
+  const int32_t off = ri.x - rs - ri.y;  // the row's kept slots move by this
+  const int32_t q = (int32_t)p + off;
   nbr[q] = onbr[p];
   t[q] = ot[p];
   eid[q] = e - drop;
   rstart[q] = ri.x;
+  const int32_t pv = oprev[p], nx = onext[p];
+  prev[q] = (pv < 0 || pv - rs < ri.y) ? -1 : pv + off;
+  next[q] = nx == INT32_MAX ? INT32_MAX : nx + off;
 }
 
 // new edges in (row, id) order: after the row's kept slots
@@ -347,7 +358,8 @@ __global__ void k_upd_new(const uint32_t* __restrict__ bkey, const uint32_t* __r
                           const int32_t* __restrict__ other, const int32_t* __restrict__ ts,
                           int32_t b0, int64_t n, int32_t N, int32_t* __restrict__ nbr,
                           int32_t* __restrict__ t, int32_t* __restrict__ eid,
-                          int32_t* __restrict__ rstart, int32_t* __restrict__ pos) {
+                          int32_t* __restrict__ rstart, int32_t* __restrict__ pos,
+                          int32_t* __restrict__ prev, int32_t* __restrict__ next) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int32_t r = (int32_t)bkey[i];
@@ -362,6 +374,8 @@ __global__ void k_upd_new(const uint32_t* __restrict__ bkey, const uint32_t* __r
   eid[q] = e;
   rstart[q] = ptr[r];
   pos[e] = q;
+  prev[q] = -1;  // linked by k_upd_new_links
+  next[q] = INT32_MAX;
 }
 
 __global__ void k_upd_kept_flags(const int32_t* __restrict__ oneid, int32_t drop, int64_t oEv,
@@ -411,10 +425,11 @@ __global__ void k_upd_nnew(const uint32_t* __restrict__ bkey, const uint32_t* __
                            const int32_t* __restrict__ kept, const int32_t* __restrict__ other,
                            const int32_t* __restrict__ ts, int32_t b0, int64_t n, int32_t N,
                            int32_t* __restrict__ nnbr, int32_t* __restrict__ nt,
-                           int32_t* __restrict__ neid) {
+                           int32_t* __restrict__ neid, int32_t* __restrict__ nq) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int32_t r = (int32_t)bkey[i];
+  nq[i] = -1;
   if (r >= N) return;
   const int32_t e = b0 + (int32_t)bperm[i];
   const int32_t x = other[e];
@@ -428,16 +443,22 @@ __global__ void k_upd_nnew(const uint32_t* __restrict__ bkey, const uint32_t* __
   nnbr[q] = x;
   nt[q] = ts[e];
   neid[q] = e;
+  nq[i] = q;
 }
 
-// consecutive entries of one row and counterparty in the (counterparty, t,
-// id) copy are consecutive same-counterparty slots
-__global__ void k_upd_links(const int32_t* __restrict__ nnbr, const int32_t* __restrict__ neid,
-                            const int32_t* __restrict__ rstart, const int32_t* __restrict__ pos,
-                            int64_t Ev, int32_t* __restrict__ prev, int32_t* __restrict__ next) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= Ev || p == rstart[p] || nnbr[p] != nnbr[p - 1]) return;
-  const int32_t pe = pos[neid[p]], pf = pos[neid[p - 1]];
+// a new edge's same-counterparty link: the entry before it in the
+// (counterparty, t, id) copy, if of the same row and counterparty, is the
+// previous slot of that counterparty (kept or new)
+__global__ void k_upd_new_links(const int32_t* __restrict__ nq, int64_t n,
+                                const int32_t* __restrict__ nnbr, const int32_t* __restrict__ neid,
+                                const int32_t* __restrict__ rstart,
+                                const int32_t* __restrict__ pos, int32_t* __restrict__ prev,
+                                int32_t* __restrict__ next) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t q = nq[i];
+  if (q < 0 || q == rstart[q] || nnbr[q] != nnbr[q - 1]) return;
+  const int32_t pe = pos[neid[q]], pf = pos[neid[q - 1]];
   prev[pe] = pf;
   next[pf] = pe;
 }
@@ -489,9 +510,8 @@ static void upd_fill(const aml_graph* o, aml_graph* g, const Adj& ao, Adj& a, Ba
   a.nnbr = ga.get<int32_t>(Ev);
   a.nt = ga.get<int32_t>(Ev);
   a.neid = ga.get<int32_t>(Ev);
-  AML_CUDA(cudaMemsetAsync(a.prev, 0xff, (Ev ? Ev : 1) * sizeof(int32_t), s));
-  AML_LAUNCH("k_fill_i32", s, k_fill_i32<<<grid_for(Ev, B), B, 0, s>>>(a.next, Ev, INT32_MAX));
   DBuf<int4> info(oEv ? oEv : 1, s);
+  DBuf<int32_t> nq(n_new ? n_new : 1, s);
   DBuf<int32_t> kept(oEv + 1, s);
   int32_t* shift = b.cnt.p;  // the counts are spent: the scan made the row pointers
   AML_LAUNCH("k_upd_rowinfo", s,
@@ -499,8 +519,9 @@ static void upd_fill(const aml_graph* o, aml_graph* g, const Adj& ao, Adj& a, Ba
                                                        info.p, shift));
   if (oEv)
     AML_LAUNCH("k_upd_keep", s,
-               k_upd_keep<<<grid_for(oEv, B), B, 0, s>>>(ao.eid, ao.rstart, ao.nbr, ao.t, info.p,
-                                                        drop, oEv, a.nbr, a.t, a.eid, a.rstart));
+               k_upd_keep<<<grid_for(oEv, B), B, 0, s>>>(ao.eid, ao.rstart, ao.nbr, ao.t, ao.prev,
+                                                        ao.next, info.p, drop, oEv, a.nbr, a.t,
+                                                        a.eid, a.rstart, a.prev, a.next));
   if (b0 > 0)
     AML_LAUNCH("k_upd_pos", s,
                k_upd_pos<<<grid_for(b0, B), B, 0, s>>>(ao.pos, row_of, shift, drop, b0, a.pos));
@@ -508,7 +529,8 @@ static void upd_fill(const aml_graph* o, aml_graph* g, const Adj& ao, Adj& a, Ba
     AML_LAUNCH("k_upd_new", s,
                k_upd_new<<<grid_for(n_new, B), B, 0, s>>>(b.bkey.p, b.bperm.p, b.bptr.p, a.ptr,
                                                          other, g->ts, b0, n_new, N,
-                                                         a.nbr, a.t, a.eid, a.rstart, a.pos));
+                                                         a.nbr, a.t, a.eid, a.rstart, a.pos,
+                                                         a.prev, a.next));
   AML_LAUNCH("k_upd_kept_flags", s,
              k_upd_kept_flags<<<grid_for(oEv + 1, B), B, 0, s>>>(ao.neid, drop, oEv, kept.p));
   scan_i32(kept.p, kept.p, oEv + 1, false, s);
@@ -522,10 +544,11 @@ static void upd_fill(const aml_graph* o, aml_graph* g, const Adj& ao, Adj& a, Ba
                k_upd_nnew<<<grid_for(n_new, B), B, 0, s>>>(b.nkey.p, b.nperm.p, b.bptr.p, a.ptr,
                                                           ao.ptr, ao.nnbr, kept.p, other, g->ts,
                                                           b0, n_new, N, a.nnbr, a.nt,
-                                                          a.neid));
-  AML_LAUNCH("k_upd_links", s,
-             k_upd_links<<<grid_for(Ev, B), B, 0, s>>>(a.nnbr, a.neid, a.rstart, a.pos, Ev,
-                                                      a.prev, a.next));
+                                                          a.neid, nq.p));
+  if (n_new)
+    AML_LAUNCH("k_upd_new_links", s,
+               k_upd_new_links<<<grid_for(n_new, B), B, 0, s>>>(nq.p, n_new, a.nnbr, a.neid,
+                                                               a.rstart, a.pos, a.prev, a.next));
   AML_LAUNCH("k_max_degree", s, k_max_degree<<<grid_for(N, B), B, 0, s>>>(a.ptr, N, max_deg_dev));
 }
 
