@@ -634,24 +634,52 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit_delta(
 // and counts, for every record of a group of two or more, its partners.
 
 // bucket histogram of compacted records (delta counting)
-// (keep: only records of buckets marked in it; null: all)
+// Delta counting: a pair of legs counts only with a new gather edge, and
+// both legs of a pair share their (s, d) key, so only the records whose key
+// has a new leg need grouping.  Those keys go into an open-addressing set
+// (linear probing, at least twice the keys' slots, ~0 = empty); the
+// histogram and the partition keep only the records whose key it holds.
+__device__ __forceinline__ bool keyset_has(const KeySet& ks, uint64_t key) {
+  uint64_t h = mix64(key) & ks.mask;
+  for (uint64_t probe = 0; probe <= ks.mask; ++probe) {
+    const unsigned long long v = __ldg(ks.tab + h);
+    if (v == key) return true;
+    if (v == ~0ull) return false;
+    h = (h + 1) & ks.mask;
+  }
+  return false;
+}
+
+// new legs among the records (to size the key set)
+__global__ void __launch_bounds__(256) k_sg_count_new(const LegRec* __restrict__ rec, int64_t n,
+                                                      int32_t new_from,
+                                                      unsigned long long* __restrict__ count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned m = __ballot_sync(0xffffffffu, i < n && rec[i].b >= new_from);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(count, (unsigned long long)__popc(m));
+}
+
+__global__ void __launch_bounds__(256) k_sg_new_keys(const LegRec* __restrict__ rec, int64_t n,
+                                                     int32_t new_from, KeySet ks) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || rec[i].b < new_from) return;
+  const unsigned long long key = rec[i].key;
+  uint64_t h = mix64(key) & ks.mask;
+  for (uint64_t probe = 0; probe <= ks.mask; ++probe) {
+    const unsigned long long old = atomicCAS(ks.tab + h, ~0ull, key);
+    if (old == ~0ull || old == key) return;
+    h = (h + 1) & ks.mask;
+  }
+}
+
+// (ks.tab null: every record)
 __global__ void __launch_bounds__(256) k_sg_hist(const LegRec* __restrict__ rec, int64_t n,
-                                                 int bits, const uint8_t* __restrict__ keep,
+                                                 int bits, KeySet ks,
                                                  uint32_t* __restrict__ hist) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const uint32_t q = bucket_of(rec[i].key, bits);
-  if (!keep || keep[q]) atomicAdd(hist + q, 1u);
-}
-
-// delta counting: marks the buckets holding a new leg (a leg whose gather
-// edge is new); a pair counts only with one, and both legs of a pair share
-// a key, hence a bucket, so the other buckets need not be grouped at all
-__global__ void __launch_bounds__(256) k_sg_new_buckets(const LegRec* __restrict__ rec, int64_t n,
-                                                        int bits, int32_t new_from,
-                                                        uint8_t* __restrict__ keep) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && rec[i].b >= new_from) keep[bucket_of(rec[i].key, bits)] = 1;
+  const uint64_t key = rec[i].key;
+  if (!ks.tab || keyset_has(ks, key)) atomicAdd(hist + bucket_of(key, bits), 1u);
 }
 
 // mask bit v set for v = node_of[e], e in [from, E)
@@ -667,7 +695,7 @@ __global__ void __launch_bounds__(256) k_mark_nodes(const int32_t* __restrict__ 
 // SG_PART_ITEMS independent records per thread keep several cursor atomics
 // in flight at once (the kernel is bound by their latency)
 __global__ void __launch_bounds__(256) k_sg_partition(const LegRec* __restrict__ rec, int64_t n,
-                                                      int bits, const uint8_t* __restrict__ keep,
+                                                      int bits, KeySet ks,
                                                       uint32_t* __restrict__ cursor,
                                                       LegRec* __restrict__ out) {
   const int64_t base = (int64_t)blockIdx.x * blockDim.x * SG_PART_ITEMS + threadIdx.x;
@@ -685,7 +713,7 @@ __global__ void __launch_bounds__(256) k_sg_partition(const LegRec* __restrict__
   bool take[SG_PART_ITEMS];
 #pragma unroll
   for (int k = 0; k < SG_PART_ITEMS; ++k)
-    take[k] = base + (int64_t)k * blockDim.x < n && (!keep || keep[bkt[k]]);
+    take[k] = base + (int64_t)k * blockDim.x < n && (!ks.tab || keyset_has(ks, r[k].key));
 #pragma unroll
   for (int k = 0; k < SG_PART_ITEMS; ++k)
     if (take[k]) pos[k] = atomicAdd(cursor + bkt[k], 1u);

@@ -144,13 +144,19 @@ void fan_per_edge(const Adj& a, int64_t Ev, int64_t E, int64_t new_from, int nw,
 __global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);
 // moves every record to its bucket: cursor = exclusive scan of the bucket
 // sizes on entry, the bucket ends on exit
-__global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, const uint8_t* keep,
+// A set of SG keys (delta counting: those with a new leg); tab null = all.
+struct KeySet {
+  unsigned long long* tab;
+  uint64_t mask;  // slots - 1 (a power of two)
+};
+
+__global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, KeySet ks,
                                uint32_t* cursor,
                                LegRec* out);
-__global__ void k_sg_hist(const LegRec* rec, int64_t n, int bits, const uint8_t* keep,
-                          uint32_t* hist);
-__global__ void k_sg_new_buckets(const LegRec* rec, int64_t n, int bits, int32_t new_from,
-                                 uint8_t* keep);
+__global__ void k_sg_hist(const LegRec* rec, int64_t n, int bits, KeySet ks, uint32_t* hist);
+__global__ void k_sg_new_keys(const LegRec* rec, int64_t n, int32_t new_from, KeySet ks);
+__global__ void k_sg_count_new(const LegRec* rec, int64_t n, int32_t new_from,
+                               unsigned long long* count);
 __global__ void k_mark_nodes(const int32_t* node_of, int64_t from, int64_t E, uint32_t* mask);
 __global__ void k_close_range(GraphView g, int32_t delta, int2* rng);
 __global__ void k_anchor_flags(const int2* crng, int64_t E, int32_t* flag);

@@ -510,7 +510,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
                       sub);
     }
     int64_t n_sg = nl;  // records to bucket
-    DBuf<uint8_t> keep_bkt;  // delta counting: the buckets holding a new leg
+    DBuf<unsigned long long> key_tab;  // delta counting: the keys with a new leg
+    KeySet ks{nullptr, 0};
     if (sg_filter) {
       unsigned long long kept = 0;
       const SmallRead rd{&kept, n_rec.p, 8};
@@ -518,14 +519,24 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       n_sg = (int64_t)kept;
       if (n_sg > 1) {
         size_buckets(n_sg);
-        keep_bkt = DBuf<uint8_t>((size_t)nb, s);
-        AML_CUDA(cudaMemsetAsync(keep_bkt.p, 0, (size_t)nb, s));
-        AML_LAUNCH("k_sg_new_buckets", s,
-                   k_sg_new_buckets<<<grid_for(n_sg, 256), 256, 0, s>>>(rec.p, n_sg, S.bits,
-                                                                       new_from, keep_bkt.p));
+        // the set holds the new legs' keys: sized by their number, so it
+        // stays in L2 while every record is looked up in it
+        AML_CUDA(cudaMemsetAsync(n_rec.p, 0, 8, s));
+        AML_LAUNCH("k_sg_count_new", s,
+                   k_sg_count_new<<<grid_for(n_sg, 256), 256, 0, s>>>(rec.p, n_sg, new_from,
+                                                                     n_rec.p));
+        unsigned long long n_new_legs = 0;
+        const SmallRead rn{&n_new_legs, n_rec.p, 8};
+        read_small(&rn, 1, s);
+        uint64_t slots = 1024;
+        while (slots < 2 * (uint64_t)n_new_legs) slots <<= 1;
+        key_tab = DBuf<unsigned long long>((size_t)slots, s);
+        AML_CUDA(cudaMemsetAsync(key_tab.p, 0xff, (size_t)slots * 8, s));
+        ks = KeySet{key_tab.p, slots - 1};
+        AML_LAUNCH("k_sg_new_keys", s,
+                   k_sg_new_keys<<<grid_for(n_sg, 256), 256, 0, s>>>(rec.p, n_sg, new_from, ks));
         AML_LAUNCH("k_sg_hist", s,
-                   k_sg_hist<<<grid_for(n_sg, 256), 256, 0, s>>>(rec.p, n_sg, S.bits, keep_bkt.p,
-                                                                hist.p));
+                   k_sg_hist<<<grid_for(n_sg, 256), 256, 0, s>>>(rec.p, n_sg, S.bits, ks, hist.p));
       }
     }
     // 3. scatter-gather: bucket the leg records, group each bucket by (s, d)
@@ -542,7 +553,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       DBuf<LegRec> part((size_t)nl, t);
       AML_LAUNCH("k_sg_partition", t,
                  k_sg_partition<<<grid_for(nl, 256 * SG_PART_ITEMS), 256, 0, t>>>(
-                     rec.p, nl, S.bits, keep_bkt.p, hist.p, part.p));
+                     rec.p, nl, S.bits, ks, hist.p, part.p));
       // buckets beyond SG_CAP records: listed by k_sg_bucket, grouped by
       // k_sg_bucket_big (one large-table block per SM)
       DBuf<uint32_t> overflow((size_t)nb + 1, t);
