@@ -473,9 +473,73 @@ struct BatchRows {
         bnbr(n, s), cnt((size_t)N + 1, s), kdrop((size_t)N, s) {}
 };
 
+// A small batch (up to SMALL_SORT edges) sorted in one block: a bitonic sort
+// of (row, counterparty, index) triples in shared memory, rows as
+// k_row_keys gives them (N for a self-loop) and the counterparty 0 when only
+// (row, index) order is wanted.  The triples are unique (the index), so the
+// order equals the stable radix sorts' order.
+constexpr int SMALL_SORT = 2048;
+
+template <bool BY_NBR>
+__global__ void __launch_bounds__(SMALL_SORT / 2) k_sort_small(const int32_t* __restrict__ row_of,
+                                                               const int32_t* __restrict__ other,
+                                                               int n, int32_t N,
+                                                               uint32_t* __restrict__ key,
+                                                               uint32_t* __restrict__ perm) {
+  __shared__ uint32_t s_row[SMALL_SORT], s_nbr[SMALL_SORT], s_idx[SMALL_SORT];
+  int m = 2;
+  while (m < n) m <<= 1;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    if (i < n) {
+      const int32_t r = row_of[i], o = other[i];
+      s_row[i] = r == o ? (uint32_t)N : (uint32_t)r;
+      s_nbr[i] = BY_NBR ? (uint32_t)o : 0u;
+    } else {
+      s_row[i] = 0xffffffffu;  // padding sorts last
+      s_nbr[i] = 0xffffffffu;
+    }
+    s_idx[i] = (uint32_t)i;
+  }
+  __syncthreads();
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < m / 2; t += blockDim.x) {
+        const int i = 2 * t - (t & (j - 1));  // the lower element of a pair
+        const int l = i + j;
+        const bool up = (i & k) == 0;
+        const bool gt = s_row[i] != s_row[l] ? s_row[i] > s_row[l]
+                        : s_nbr[i] != s_nbr[l] ? s_nbr[i] > s_nbr[l] : s_idx[i] > s_idx[l];
+        if (gt == up) {
+          uint32_t x = s_row[i]; s_row[i] = s_row[l]; s_row[l] = x;
+          x = s_nbr[i]; s_nbr[i] = s_nbr[l]; s_nbr[l] = x;
+          x = s_idx[i]; s_idx[i] = s_idx[l]; s_idx[l] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    key[i] = s_row[i];
+    perm[i] = s_idx[i];
+  }
+}
+
 static void upd_sort_batch(BatchRows& b, const int32_t* row_of, const int32_t* other, int64_t n,
                            int32_t N, int nbits, cudaStream_t s) {
   const int B = 256;
+  if (n <= SMALL_SORT) {  // one block per order instead of radix passes
+    AML_LAUNCH("k_sort_small", s,
+               k_sort_small<false><<<1, SMALL_SORT / 2, 0, s>>>(row_of, other, (int)n, N,
+                                                               b.bkey.p, b.bperm.p));
+    AML_LAUNCH("k_row_ptr", s,
+               k_row_ptr<<<grid_for((int64_t)N + 1, B), B, 0, s>>>(b.bkey.p, n, N, b.bptr.p));
+    AML_LAUNCH("k_sort_small", s,
+               k_sort_small<true><<<1, SMALL_SORT / 2, 0, s>>>(row_of, other, (int)n, N,
+                                                              b.nkey.p, b.nperm.p));
+    AML_LAUNCH("k_upd_batch_nbr", s,
+               k_upd_batch_nbr<<<grid_for(n, B), B, 0, s>>>(b.nperm.p, other, 0, n, b.bnbr.p));
+    return;
+  }
   DBuf<uint32_t> kt(n, s), vt(n, s);
   iota_i32(reinterpret_cast<int32_t*>(b.bperm.p), n, s);
   AML_LAUNCH("k_row_keys", s,
