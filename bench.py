@@ -373,7 +373,7 @@ def run_reference(args, ws, rank):
     from paper_2604_12241_b300 import patterns as P
     g = aml_synth.workload(args.workload)
     pats = P.workload_patterns(args.workload)
-    cols = P.oracle_columns(pats)
+    cols = oracle.columns_from_names([p.name for p in pats])
     og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(7)
@@ -411,7 +411,7 @@ def run_reference(args, ws, rank):
 def cpu_baseline(g, pats, seconds: float) -> dict:
     import oracle
     from paper_2604_12241_b300 import patterns as P
-    cols = P.oracle_columns(pats)
+    cols = oracle.columns_from_names([p.name for p in pats])
     og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(3)

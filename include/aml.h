@@ -344,6 +344,16 @@ aml_status aml_graph_get_tuning(const aml_graph* g, aml_tuning* out);
  * the graph's captured mines. */
 aml_status aml_graph_set_tuning(aml_graph* g, const aml_tuning* t);
 
+/* Saturation bound of the counts aml_mine writes for `g` (no paper
+ * counterpart: the paper states no range for its counts).  Every column is
+ * an exact count; a count above the bound is written as the bound, never
+ * wrapped.  The bound is 2^32-1 (UINT32_MAX) from aml_graph_create on, the
+ * largest value of the uint32 output; no realistic graph gives one edge
+ * 2^32 instances, so this call exists for tests, which lower it to a few
+ * units to exercise the clamp on tiny graphs.  limit >= 1 (0: AML_EINVAL).
+ * Drops the graph's captured mines (AML_MINE_GRAPH). */
+aml_status aml_graph_set_count_limit(aml_graph* g, uint32_t limit);
+
 /* Autotuner: times real mines of `ps` on `g` (median of `repeats` after one
  * warm-up each, CUDA events on `stream`) while sweeping one tunable at a time
  * over a fixed candidate list, keeps the fastest setting on the graph and
@@ -473,6 +483,12 @@ aml_status aml_stream_get_info(const aml_stream* st, aml_stream_info* info);
  * elements (0 when they are equal or no graph is kept).  Synchronizes the
  * device.  Errors: AML_EINVAL, AML_ENOMEM, AML_ECUDA. */
 aml_status aml_stream_check_graph(aml_stream* st, int64_t* n_mismatch);
+
+/* The stream's saturation bound (as aml_graph_set_count_limit; 2^32-1 from
+ * aml_stream_open on).  It applies from the next append on: a stored count
+ * plus the instances an append adds is saturated at the bound, which keeps
+ * every stored count equal to min(full-history count, bound).  limit >= 1. */
+aml_status aml_stream_set_count_limit(aml_stream* st, uint32_t limit);
 
 aml_status aml_stream_close(aml_stream* st);
 

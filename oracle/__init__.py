@@ -84,6 +84,10 @@ def load_library(path: str) -> ctypes.CDLL:
     lib.og_count_edges.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                    ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                    ctypes.c_int32]
+    lib.og_count_all_limit.restype = ctypes.c_int
+    lib.og_count_all_limit.argtypes = lib.og_count_all.argtypes + [ctypes.c_uint32]
+    lib.og_count_edges_limit.restype = ctypes.c_int
+    lib.og_count_edges_limit.argtypes = lib.og_count_edges.argtypes + [ctypes.c_uint32]
     return lib
 
 
@@ -102,6 +106,25 @@ def _cols(cols: Sequence[Tuple]) -> ctypes.Array:
         else:
             arr[i].kind, arr[i].k, arr[i].delta = KINDS[c[0]], 0, int(c[1])
     return arr
+
+
+def columns_from_names(names: Sequence[str]) -> list:
+    """Column tuples for column names of the form FAMILY@delta (DEG_OUT@86400,
+    CYC3@86400, CYCW4@604800, ...), the names the library gives its columns."""
+    out = []
+    for name in names:
+        fam, _, rest = name.partition("@")
+        d = int(rest)
+        if fam.startswith("CYCW"):
+            out.append(("cycw", int(fam[4:]), d))
+        elif fam.startswith("CYC"):
+            out.append(("cyc", int(fam[3:]), d))
+        else:
+            kind = fam.lower()
+            if kind not in KINDS:
+                raise ValueError(f"no oracle column for {name}")
+            out.append((kind, d))
+    return out
 
 
 class OracleGraph:
@@ -130,23 +153,27 @@ class OracleGraph:
     def __del__(self):
         self.close()
 
-    def count_all(self, cols: Sequence[Tuple], threads: int = 0) -> np.ndarray:
-        """Canonical enumeration over the whole graph: uint32 [E, len(cols)]."""
+    def count_all(self, cols: Sequence[Tuple], threads: int = 0,
+                  limit: int = 0xFFFFFFFF) -> np.ndarray:
+        """Canonical enumeration over the whole graph: uint32 [E, len(cols)],
+        every count saturated at ``limit`` (2^32-1 unless a test lowers it)."""
         out = np.zeros((self.n_edges, len(cols)), dtype=np.uint32)
-        rc = self._lib.og_count_all(self._h, ctypes.byref(_cols(cols)), len(cols),
-                                  out.ctypes.data, threads)
+        rc = self._lib.og_count_all_limit(self._h, ctypes.byref(_cols(cols)), len(cols),
+                                          out.ctypes.data, threads, int(limit))
         if rc:
             raise ValueError(f"og_count_all failed ({rc})")
         return out
 
     def count_edges(self, cols: Sequence[Tuple], eids: Iterable[int],
-                    threads: int = 0) -> np.ndarray:
-        """Edge-centric query for the listed edges: uint32 [n, len(cols)]."""
+                    threads: int = 0, limit: int = 0xFFFFFFFF) -> np.ndarray:
+        """Edge-centric query for the listed edges: uint32 [n, len(cols)],
+        saturated at ``limit`` like ``count_all``."""
         ids = np.ascontiguousarray(np.asarray(list(eids) if not isinstance(eids, np.ndarray)
                                               else eids, dtype=np.int64))
         out = np.zeros((ids.shape[0], len(cols)), dtype=np.uint32)
-        rc = self._lib.og_count_edges(self._h, ctypes.byref(_cols(cols)), len(cols),
-                                    ids.ctypes.data, ids.shape[0], out.ctypes.data, threads)
+        rc = self._lib.og_count_edges_limit(self._h, ctypes.byref(_cols(cols)), len(cols),
+                                            ids.ctypes.data, ids.shape[0], out.ctypes.data,
+                                            threads, int(limit))
         if rc:
             raise ValueError(f"og_count_edges failed ({rc})")
         return out

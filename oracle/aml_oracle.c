@@ -345,13 +345,25 @@ static int check_cols(const og_col* cols, int32_t ncols) {
   return 0;
 }
 
-static void clamp_out(const uint64_t* acc, uint32_t* out, size_t n) {
-  for (size_t i = 0; i < n; ++i) out[i] = acc[i] > 0xffffffffull ? 0xffffffffu : (uint32_t)acc[i];
+/* Saturation: every exact (uint64) count above `limit` is reported as
+ * `limit` (2^32-1 unless a test lowers it to reach the clamp with tiny
+ * counts); nothing wraps. */
+static uint32_t saturate(uint64_t v, uint32_t limit) {
+  return v > (uint64_t)limit ? limit : (uint32_t)v;
+}
+
+static void clamp_out(const uint64_t* acc, uint32_t* out, size_t n, uint32_t limit) {
+  for (size_t i = 0; i < n; ++i) out[i] = saturate(acc[i], limit);
 }
 
 int og_count_all(const og_graph* g, const og_col* cols, int32_t ncols, uint32_t* out,
                  int32_t nthreads) {
-  if (!g || ncols <= 0 || check_cols(cols, ncols)) return -1;
+  return og_count_all_limit(g, cols, ncols, out, nthreads, 0xffffffffu);
+}
+
+int og_count_all_limit(const og_graph* g, const og_col* cols, int32_t ncols, uint32_t* out,
+                       int32_t nthreads, uint32_t limit) {
+  if (!g || ncols <= 0 || check_cols(cols, ncols) || limit == 0) return -1;
   int nth = nthreads > 0 ? nthreads : omp_get_max_threads();
   size_t n = (size_t)g->E * (size_t)ncols;
   uint64_t* acc = (uint64_t*)calloc(n ? n : 1, 8);
@@ -402,7 +414,7 @@ int og_count_all(const og_graph* g, const og_col* cols, int32_t ncols, uint32_t*
         }
     }
   }
-  clamp_out(acc, out, n);
+  clamp_out(acc, out, n, limit);
   free(acc);
   free(done);
   return 0;
@@ -547,7 +559,13 @@ static uint64_t ec_cyc(const og_graph* g, int64_t e, int k, int64_t delta, int w
 
 int og_count_edges(const og_graph* g, const og_col* cols, int32_t ncols, const int64_t* eids,
                    int64_t n, uint32_t* out, int32_t nthreads) {
-  if (!g || ncols <= 0 || check_cols(cols, ncols) || n < 0) return -1;
+  return og_count_edges_limit(g, cols, ncols, eids, n, out, nthreads, 0xffffffffu);
+}
+
+int og_count_edges_limit(const og_graph* g, const og_col* cols, int32_t ncols,
+                         const int64_t* eids, int64_t n, uint32_t* out, int32_t nthreads,
+                         uint32_t limit) {
+  if (!g || ncols <= 0 || check_cols(cols, ncols) || n < 0 || limit == 0) return -1;
   for (int64_t i = 0; i < n; ++i)
     if (eids[i] < 0 || eids[i] >= g->E) return -1;
   int nth = nthreads > 0 ? nthreads : omp_get_max_threads();
@@ -574,7 +592,7 @@ int og_count_edges(const og_graph* g, const og_col* cols, int32_t ncols, const i
             case OG_CYCW: v = ec_cyc(g, e, cols[c].k, delta, 1); break;
           }
         }
-        out[(size_t)i * (size_t)ncols + (size_t)c] = v > 0xffffffffull ? 0xffffffffu : (uint32_t)v;
+        out[(size_t)i * (size_t)ncols + (size_t)c] = saturate(v, limit);
       }
     }
     free(stamp);
@@ -844,7 +862,7 @@ int og_program_count(const og_graph* g, const og_stage* st, int32_t n, int32_t a
     }
     free(c.seen);
   }
-  clamp_out(total, out, (size_t)E);
+  clamp_out(total, out, (size_t)E, 0xffffffffu);
   free(total);
   return 0;
 }

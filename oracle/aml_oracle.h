@@ -64,6 +64,16 @@ int og_count_all(const og_graph* g, const og_col* cols, int32_t ncols,
 int og_count_edges(const og_graph* g, const og_col* cols, int32_t ncols,
                    const int64_t* eids, int64_t n, uint32_t* out, int32_t nthreads);
 
+/* The same two enumerations with the saturation bound as an argument:
+ * every count above `limit` (>= 1) is reported as `limit`.  The plain calls
+ * use limit = 2^32-1; tests pass small limits so that the clamp is reached
+ * on tiny graphs (no realistic graph reaches 2^32 instances of one edge). */
+int og_count_all_limit(const og_graph* g, const og_col* cols, int32_t ncols,
+                       uint32_t* out, int32_t nthreads, uint32_t limit);
+int og_count_edges_limit(const og_graph* g, const og_col* cols, int32_t ncols,
+                         const int64_t* eids, int64_t n, uint32_t* out, int32_t nthreads,
+                         uint32_t limit);
+
 /* ---------------- stage programs (Sec. 5; Alg. 1's nested loop per stage) ----------------
  *
  * A program is a trigger (stage 0: the edge e0 = N0 -> N1) and stages

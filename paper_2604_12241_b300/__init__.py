@@ -107,6 +107,10 @@ class Graph:
         t = aml_tuning(**cur)
         check(lib().aml_graph_set_tuning(self._h, ctypes.byref(t)))
 
+    def set_count_limit(self, limit: int) -> None:
+        """Saturation bound of this graph's counts (aml_graph_set_count_limit)."""
+        check(lib().aml_graph_set_count_limit(self._h, int(limit)))
+
     def close(self) -> None:
         if getattr(self, "_h", None):
             lib().aml_graph_destroy(self._h)
@@ -261,6 +265,10 @@ class Stream:
         n = ctypes.c_int64(0)
         check(lib().aml_stream_check_graph(self._h, ctypes.byref(n)))
         return int(n.value)
+
+    def set_count_limit(self, limit: int) -> None:
+        """Saturation bound of the stored counts (aml_stream_set_count_limit)."""
+        check(lib().aml_stream_set_count_limit(self._h, int(limit)))
 
     def close(self) -> None:
         if getattr(self, "_h", None):

@@ -117,6 +117,7 @@ _SIGS = {
     "aml_sync": (ctypes.c_int32, [_VP]),
     "aml_graph_get_tuning": (ctypes.c_int32, [_VP, ctypes.POINTER(aml_tuning)]),
     "aml_graph_set_tuning": (ctypes.c_int32, [_VP, ctypes.POINTER(aml_tuning)]),
+    "aml_graph_set_count_limit": (ctypes.c_int32, [_VP, ctypes.c_uint32]),
     "aml_autotune": (ctypes.c_int32, [_VP, _VP, ctypes.c_int32, _VP, ctypes.POINTER(aml_tuning),
                                       ctypes.POINTER(ctypes.c_float)]),
     "aml_stream_open": (ctypes.c_int32, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t,
@@ -129,6 +130,7 @@ _SIGS = {
     "aml_stream_get_info": (ctypes.c_int32, [_VP, ctypes.POINTER(aml_stream_info)]),
     "aml_stream_check_graph": (ctypes.c_int32, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "aml_stream_close": (ctypes.c_int32, [_VP]),
+    "aml_stream_set_count_limit": (ctypes.c_int32, [_VP, ctypes.c_uint32]),
     "aml_fan_noalloc": (ctypes.c_int32, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
     "aml_cost_train": (ctypes.c_int32, [_VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                         _VP, ctypes.POINTER(aml_cost_report)]),

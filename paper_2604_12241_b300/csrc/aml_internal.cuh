@@ -170,6 +170,9 @@ struct aml_graph {
     used_streams.push_back(s);
   }
   int device = 0;
+  // every count above this is reported as this (2^32-1; lowered only by
+  // aml_graph_set_count_limit, which tests use to reach the clamp)
+  uint32_t count_limit = 0xffffffffu;
   aml::Tuning tune;
   uint64_t tune_gen = 0;
   std::vector<aml::MineExec> execs;   // captured mines (AML_MINE_GRAPH)

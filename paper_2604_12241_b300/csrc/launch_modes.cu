@@ -169,6 +169,18 @@ aml_status aml_graph_set_tuning(aml_graph* g, const aml_tuning* t) {
   }
 }
 
+aml_status aml_graph_set_count_limit(aml_graph* g, uint32_t limit) {
+  if (!g || limit == 0) {
+    set_error("aml_graph_set_count_limit: NULL graph or a limit of 0");
+    return AML_EINVAL;
+  }
+  if (g->count_limit != limit) {
+    g->count_limit = limit;
+    drop_captured_mines(g);  // their row assembly holds the old bound
+  }
+  return AML_OK;
+}
+
 aml_status aml_autotune(aml_graph* g, const aml_pattern_set* ps, int32_t repeats, void* stream,
                         aml_tuning* best, float* best_ms) {
   try {

@@ -1319,7 +1319,10 @@ __global__ void __launch_bounds__(512) k_cyc_emit(int64_t n, const int32_t* __re
 // One thread per edge computes the edge's whole output row from values the
 // earlier kernels left in edge order: DEG and FAN per window and direction,
 // GS = legs starting + legs ending at the edge, SG and CYC from the 64-bit
-// accumulators; saturated to 32 bits.
+// accumulators; saturated at the graph's count limit (2^32-1).  A streamed
+// old row adds its new instances to the stored value and saturates the sum:
+// min(min(old, B) + new, B) = min(old + new, B), so a clamped row stays
+// exact.
 // The block's rows are staged in shared memory and stored as one contiguous
 // range when the output has no padding (ld = P), so the stores coalesce.
 
@@ -1343,6 +1346,11 @@ __device__ __forceinline__ uint64_t assemble_value(const AssembleParams& P, cons
     default:  // accumulated families
       return P.acc[(int64_t)cd.acc_slot * P.g.E + e];
   }
+}
+
+// a count above the bound is reported as the bound: saturated, never wrapped
+__device__ __forceinline__ uint32_t saturate(uint64_t v, uint32_t limit) {
+  return v > (uint64_t)limit ? limit : (uint32_t)v;
 }
 
 __global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
@@ -1371,11 +1379,9 @@ __global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
           if (loop || !((P.inst_mask >> c) & 1ull)) continue;  // trailing windows never change
           const uint64_t val = assemble_value(P, P.cols[c], e);
           if (val == 0) continue;
-          const uint64_t sum = val + orow[c];
-          orow[c] = sum > 0xffffffffull ? 0xffffffffu : (uint32_t)sum;
+          orow[c] = saturate(val + orow[c], P.limit);
         } else {
-          const uint64_t val = loop ? 0 : assemble_value(P, P.cols[c], e);
-          orow[c] = val > 0xffffffffull ? 0xffffffffu : (uint32_t)val;
+          orow[c] = loop ? 0u : saturate(assemble_value(P, P.cols[c], e), P.limit);
         }
       }
     }
@@ -1389,8 +1395,7 @@ __global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
       for (int c = 0; c < nc; ++c) row[c] = 0u;
     } else {
       for (int c = 0; c < nc; ++c) {
-        const uint64_t val = assemble_value(P, P.cols[c], e);
-        row[c] = val > 0xffffffffull ? 0xffffffffu : (uint32_t)val;
+        row[c] = saturate(assemble_value(P, P.cols[c], e), P.limit);
       }
     }
   }

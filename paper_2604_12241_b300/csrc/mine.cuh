@@ -69,6 +69,7 @@ struct AssembleParams {
   const unsigned long long* acc;
   uint32_t* counts;
   int64_t ld;
+  uint32_t limit;  // saturation bound of every count (2^32-1 unless lowered)
   // streaming: rows below accumulate_from add their new-instance counts to
   // the instance columns already stored (mask bit c set = instance column);
   // -1 writes every row outright

@@ -240,6 +240,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
   P.ncols = ncols;
   P.counts = counts;
   P.ld = ld;
+  P.limit = g->count_limit;
   P.accumulate_from = accumulate && new_from > 0 ? new_from : -1;
   for (int c = 0; c < ncols; ++c) {
     const uint32_t f = ps->cols[c].family;

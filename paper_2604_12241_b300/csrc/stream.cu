@@ -68,6 +68,7 @@ struct aml_stream {
   // g->E)), kept so the next window's graph is an update of it
   aml_graph* g = nullptr;
   int64_t g_first = 0;
+  uint32_t count_limit = 0xffffffffu;  // saturation bound of the stored counts
 };
 
 namespace aml {
@@ -142,6 +143,7 @@ static void mine_window(aml_stream* st, int64_t w0, int64_t n, int32_t new_from,
   }
   drop_graph(st);
   try {
+    g->count_limit = st->count_limit;
     mine_plain(g, &st->ps, out, st->P, s, 0, new_from, t_new, true);
     AML_CUDA(cudaStreamSynchronize(s));
     uint32_t err = 0;
@@ -412,6 +414,15 @@ aml_status aml_stream_check_graph(aml_stream* st, int64_t* n_mismatch) {
     set_error(std::string("aml_stream_check_graph: ") + e.msg);
     return e.status;
   }
+}
+
+aml_status aml_stream_set_count_limit(aml_stream* st, uint32_t limit) {
+  if (!st || limit == 0) {
+    set_error("aml_stream_set_count_limit: NULL stream or a limit of 0");
+    return AML_EINVAL;
+  }
+  st->count_limit = limit;
+  return AML_OK;
 }
 
 aml_status aml_stream_close(aml_stream* st) {

@@ -258,33 +258,3 @@ def workload_patterns(name: str) -> List[Pattern]:
         return ([fan_out(DAY), fan_in(DAY), gather_scatter(DAY), scatter_gather(DAY)]
                 + [cycle(k, DAY) for k in range(3, 7)] + [fan_out(WEEK), fan_in(WEEK)])
     raise KeyError(name)
-
-
-def oracle_columns(patterns: Sequence[Pattern]) -> list:
-    """The oracle's column tuples for a list of built-in patterns."""
-    out = []
-    for p in patterns:
-        fam, _, rest = p.name.partition("@")
-        d = int(rest)
-        if fam.startswith("CYCW"):
-            out.append(("cycw", int(fam[4:]), d))
-        elif fam.startswith("CYC"):
-            out.append(("cyc", int(fam[3:]), d))
-        else:
-            out.append((fam.lower(), d))
-    return out
-
-
-def from_oracle_columns(cols) -> List[Pattern]:
-    """Built-in patterns for oracle column tuples (inverse of oracle_columns)."""
-    make = {"deg_out": deg_out, "deg_in": deg_in, "fan_out": fan_out, "fan_in": fan_in,
-            "gs": gather_scatter, "sg": scatter_gather}
-    out = []
-    for c in cols:
-        if c[0] == "cyc":
-            out.append(cycle(int(c[1]), int(c[2])))
-        elif c[0] == "cycw":
-            out.append(window_cycle(int(c[1]), int(c[2])))
-        else:
-            out.append(make[c[0]](int(c[1])))
-    return out

@@ -135,6 +135,8 @@ def test_argument_errors_need_no_device():
                               None, ctypes.byref(h)) == 1
     assert L.aml_mine(None, None, None, 0, 0, None) == 1
     assert L.aml_sync(None) == 1
+    assert L.aml_graph_set_count_limit(None, 5) == 1
+    assert L.aml_stream_set_count_limit(None, 5) == 1
     assert L.aml_graph_destroy(None) == 0
     assert "NULL" in L.aml_last_error().decode() or L.aml_last_error() is not None
 

@@ -19,6 +19,7 @@ import aml_synth
 import mlp_ref as R
 import paper_2604_12241_b300 as aml
 from paper_2604_12241_b300 import _lib, patterns as P
+from colmap import from_oracle_columns
 
 pytestmark = pytest.mark.gpu
 
@@ -130,7 +131,7 @@ def test_persistent_on_multi_tile_random_graph():
             ("gs", 40)]
     want = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes).count_all(cols)
     graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes)
-    ps = aml.PatternSet(P.from_oracle_columns(cols))
+    ps = aml.PatternSet(from_oracle_columns(cols))
     got = aml.mine(graph, ps, mode="persistent").cpu().numpy().view(np.uint32)
     np.testing.assert_array_equal(got, want)
     aml.cost_train(graph, ps, max_samples=5_000, epochs=3)

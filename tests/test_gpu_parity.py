@@ -12,6 +12,7 @@ import aml_synth
 import oracle
 import paper_2604_12241_b300 as aml
 from paper_2604_12241_b300 import patterns as P
+from colmap import from_oracle_columns, oracle_columns
 
 pytestmark = pytest.mark.gpu
 
@@ -43,7 +44,7 @@ def gpu_counts(src, dst, ts, n_nodes, pats, assume_sorted=False, amount=None):
 
 
 def test_random_tiny_graphs():
-    pats = P.from_oracle_columns(SMALL_COLS)
+    pats = from_oracle_columns(SMALL_COLS)
     for seed in range(150):
         n = 3 + seed % 7
         E = 6 + seed % 30
@@ -63,7 +64,7 @@ def test_multi_tile_random_graphs(seed):
     cols = [("deg_out", 50), ("deg_in", 50), ("fan_out", 50), ("fan_in", 50), ("gs", 30),
             ("sg", 20), ("cyc", 2, 40), ("cyc", 3, 40), ("cyc", 4, 40), ("cyc", 5, 40)]
     want = oracle.OracleGraph(g.src, g.dst, g.ts, n).count_all(cols)
-    got = gpu_counts(g.src, g.dst, g.ts, n, P.from_oracle_columns(cols))
+    got = gpu_counts(g.src, g.dst, g.ts, n, from_oracle_columns(cols))
     np.testing.assert_array_equal(got, want)
     assert rng is not None
 
@@ -76,7 +77,7 @@ def tiny10k():
 def test_tiny10k_full_parity(tiny10k):
     g = tiny10k
     pats = P.standard(DAY) + P.standard(WEEK)
-    want = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes).count_all(P.oracle_columns(pats))
+    want = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes).count_all(oracle_columns(pats))
     got = gpu_counts(g.src, g.dst, g.ts, g.n_nodes, pats, assume_sorted=True, amount=g.amount)
     np.testing.assert_array_equal(got, want)
     assert got[:, 5].sum() > 0 and got[:, 8].sum() > 0
@@ -129,14 +130,14 @@ def test_edge_cases():
     src = np.array([0, 1, 2, 0, 1], np.int32)
     dst = np.array([1, 2, 0, 2, 0], np.int32)
     ts = np.array([-2**31, 0, 2**31 - 1, -2**31 + 5, 2**31 - 2], np.int32)
-    want = oracle.OracleGraph(src, dst, ts, 3).count_all(P.oracle_columns(big))
+    want = oracle.OracleGraph(src, dst, ts, 3).count_all(oracle_columns(big))
     np.testing.assert_array_equal(gpu_counts(src, dst, ts, 3, big), want)
     # large node ids (rows are allocated for every account)
     N = 30_000_000
     src = np.array([N - 1, 5, N - 2, N - 1], np.int32)
     dst = np.array([5, N - 2, N - 1, 5], np.int32)
     ts = np.array([1, 2, 3, 4], np.int32)
-    want = oracle.OracleGraph(src, dst, ts, N).count_all(P.oracle_columns(pats))
+    want = oracle.OracleGraph(src, dst, ts, N).count_all(oracle_columns(pats))
     np.testing.assert_array_equal(gpu_counts(src, dst, ts, N, pats), want)
 
 
@@ -153,7 +154,7 @@ def test_input_errors():
     # the same unsorted input without the promise is accepted and sorted
     out = gpu_counts(src, dst, np.array([3, 2, 1], np.int32), 3, pats)
     want = oracle.OracleGraph(src, dst, np.array([3, 2, 1], np.int32), 3).count_all(
-        P.oracle_columns(pats))
+        oracle_columns(pats))
     np.testing.assert_array_equal(out, want)
 
 
@@ -183,7 +184,7 @@ def test_hi_small_sampled_parity(hi_small):
     g, pats, got = hi_small
     ids = _sample(g, np.random.default_rng(11))
     og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
-    want = og.count_edges(P.oracle_columns(pats), ids)
+    want = og.count_edges(oracle_columns(pats), ids)
     np.testing.assert_array_equal(got[ids], want)
 
 
@@ -228,7 +229,7 @@ def test_sg_pair_larger_than_a_bucket():
     src, dst, ts = (np.asarray(x, np.int32) for x in (src, dst, ts))
     cols = [("sg", 1000), ("sg", 200), ("gs", 1000), ("cyc", 3, 600), ("cyc", 4, 600)]
     want = oracle.OracleGraph(src, dst, ts, n).count_all(cols)
-    got = gpu_counts(src, dst, ts, n, P.from_oracle_columns(cols))
+    got = gpu_counts(src, dst, ts, n, from_oracle_columns(cols))
     np.testing.assert_array_equal(got, want)
     assert got[:, 0].max() > 1000
 
@@ -256,5 +257,5 @@ def test_hub_rows_span_many_chunks():
     cols = [(f, w) for w in (0, 7, 60, 900, 10_000)
             for f in ("deg_out", "deg_in", "fan_out", "fan_in")]
     want = oracle.OracleGraph(src, dst, ts, n).count_all(cols)
-    got = gpu_counts(src, dst, ts, n, P.from_oracle_columns(cols))
+    got = gpu_counts(src, dst, ts, n, from_oracle_columns(cols))
     np.testing.assert_array_equal(got, want)

@@ -14,6 +14,7 @@ import oracle
 import paper_2604_12241_b300 as aml
 from paper_2604_12241_b300 import patterns as P
 from programs import AMOUNT_PROGRAMS, AMOUNT_VALUES, NOVEL, F, T, OUT, NONE, SPAN, EDGES
+from colmap import oracle_columns
 
 pytestmark = pytest.mark.gpu
 
@@ -98,7 +99,7 @@ def test_programs_match_oracle_on_tiny10k():
     for j, p in enumerate(pats):
         want = og.program_count(_tuples(p), p.aggregate, p.delta)
         np.testing.assert_array_equal(got[:, j], want, err_msg=p.name or f"program {j}")
-    want_fam = og.count_all(P.oracle_columns(fam))
+    want_fam = og.count_all(oracle_columns(fam))
     np.testing.assert_array_equal(got[:, len(pats):], want_fam)
     # interpreted family programs reproduce their families (SG twice over)
     names = [p.name for p in pats]

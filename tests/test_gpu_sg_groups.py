@@ -15,6 +15,7 @@ import pytest
 import oracle
 import paper_2604_12241_b300 as aml
 from paper_2604_12241_b300 import patterns as P
+from colmap import from_oracle_columns
 
 pytestmark = pytest.mark.gpu
 
@@ -59,7 +60,7 @@ def test_large_sg_groups_match_oracle(cols):
     src, dst, ts, n = hub_graph(11)
     want = oracle.OracleGraph(src, dst, ts, n).count_all(cols)
     g = aml.Graph(src, dst, ts, n)
-    ps = aml.PatternSet(P.from_oracle_columns(cols))
+    ps = aml.PatternSet(from_oracle_columns(cols))
     got = aml.mine(g, ps)
     torch.cuda.synchronize()
     g.sync()

@@ -1,15 +1,19 @@
 """Streaming recount: after every append, every resident row equals the
-count of a full mine of everything appended so far (bit-exact), for random
-batch sizes, ties across batch boundaries, and eviction; the window graph
-the stream updates from append to append equals a fresh build of the same
-window, array by array; bad batches are refused without changing the
-stream."""
+oracle's count over everything appended so far (bit-exact; the oracle's
+canonical enumeration of the prefix, or its edge-centric query on a sample
+of resident rows for the larger shapes) and the count of a full GPU mine of
+the prefix, for random batch sizes, ties across batch boundaries, and
+eviction; the window graph the stream updates from append to append equals
+a fresh build of the same window, array by array; bad batches are refused
+without changing the stream."""
 import numpy as np
 import pytest
 
 import aml_synth
+import oracle
 import paper_2604_12241_b300 as aml
 from paper_2604_12241_b300 import patterns as P
+from colmap import oracle_columns
 
 pytestmark = pytest.mark.gpu
 
@@ -21,6 +25,46 @@ def full_mine(g, n, pats):
     return out
 
 
+def oracle_prefix(g, n, pats):
+    """The oracle's counts of every edge of the first n edges."""
+    og = oracle.OracleGraph(g.src[:n], g.dst[:n], g.ts[:n], g.n_nodes)
+    return og.count_all(oracle_columns(pats))
+
+
+def check_resident(st, g, n, pats, want_gpu=None):
+    """Resident rows equal the oracle over the prefix (and a full GPU mine,
+    when given)."""
+    inf = st.info()
+    r0, nr = inf["resident_first_row"], inf["resident_rows"]
+    assert r0 + nr == n
+    got = st.read(r0, nr)
+    np.testing.assert_array_equal(got, oracle_prefix(g, n, pats)[r0:r0 + nr])
+    if want_gpu is not None:
+        np.testing.assert_array_equal(got, want_gpu[r0:r0 + nr])
+    return r0
+
+
+def check_resident_sample(st, g, n, pats, rng, n_random=3000, n_hub=600):
+    """Larger shapes: a sample of resident rows (random, the top hubs'
+    edges, the last batch's first rows) against the oracle's edge-centric
+    query over the prefix."""
+    inf = st.info()
+    r0, nr = inf["resident_first_row"], inf["resident_rows"]
+    src, dst = g.src[:n], g.dst[:n]
+    out_deg = np.bincount(src, minlength=g.n_nodes)
+    in_deg = np.bincount(dst, minlength=g.n_nodes)
+    hub = np.isin(src, np.argsort(out_deg)[-10:]) | np.isin(dst, np.argsort(in_deg)[-10:])
+    hub_rows = np.nonzero(hub[r0:])[0] + r0
+    ids = np.unique(np.concatenate([
+        rng.choice(np.arange(r0, n), min(n_random, nr), replace=False),
+        rng.choice(hub_rows, min(n_hub, hub_rows.size), replace=False),
+        np.arange(max(r0, n - 200), n), np.arange(r0, min(n, r0 + 50))]))
+    og = oracle.OracleGraph(src, dst, g.ts[:n], g.n_nodes)
+    want = og.count_edges(oracle_columns(pats), ids)
+    rows = st.read(r0, nr)[ids - r0]
+    np.testing.assert_array_equal(rows, want)
+
+
 @pytest.mark.parametrize("window_days", [8, 30])
 def test_stream_equals_full_mine(window_days):
     import torch
@@ -30,7 +74,7 @@ def test_stream_equals_full_mine(window_days):
     ps = aml.PatternSet(pats)
     st = aml.Stream(ps, g.n_nodes, resident_window=window_days * P.DAY, mem_budget=1 << 30)
     rng = np.random.default_rng(window_days)
-    pos, n_checks = 0, 0
+    pos, n_checks, evicted_checks = 0, 0, 0
     E = g.n_edges
     while pos < E:
         n = int(min(E - pos, rng.integers(1, 6000)))
@@ -41,11 +85,12 @@ def test_stream_equals_full_mine(window_days):
         assert st.check_graph() == 0
         pos += n
         if rng.random() < 0.3 or pos == E:
-            want = full_mine(g, pos, pats)
-            r0, nr = info["resident_first_row"], info["resident_rows"]
-            np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
+            r0 = check_resident(st, g, pos, pats, full_mine(g, pos, pats))
             n_checks += 1
+            evicted_checks += r0 > 0
     assert n_checks >= 3
+    if window_days == 8:
+        assert evicted_checks >= 2   # mid-stream checks after eviction too
     inf = st.info()
     if window_days == 8:
         assert inf["resident_first_row"] > 0          # eviction happened
@@ -85,10 +130,7 @@ def test_stream_refuses_bad_batches():
             st.append(g.src[1000:big], g.dst[1000:big], g.ts[1000:big])
         assert ei.value.name == "AML_EADMIT"
     st.append(g.src[1000:3000], g.dst[1000:3000], g.ts[1000:3000])
-    want = full_mine(g, 3000, pats)
-    inf = st.info()
-    r0, nr = inf["resident_first_row"], inf["resident_rows"]
-    np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
+    check_resident(st, g, 3000, pats, full_mine(g, 3000, pats))
     st.close()
 
 
@@ -101,7 +143,7 @@ def test_stream_hi_medium_shape_at_tenth_scale():
     ps = aml.PatternSet(pats)
     st = aml.Stream(ps, g.n_nodes, resident_window=7 * P.DAY, mem_budget=8 << 30)
     rng = np.random.default_rng(5)
-    pos, E = 0, g.n_edges
+    pos, E, mid = 0, g.n_edges, None
     while pos < E:
         n = int(min(E - pos, np.exp(rng.uniform(np.log(1e3), np.log(1e5)))))
         st.append(g.src[pos:pos + n], g.dst[pos:pos + n], g.ts[pos:pos + n],
@@ -109,12 +151,17 @@ def test_stream_hi_medium_shape_at_tenth_scale():
         pos += n
         if rng.random() < 0.2:
             assert st.check_graph() == 0
+        if mid is None and pos > E // 2 and st.info()["resident_first_row"] > 0:
+            check_resident_sample(st, g, pos, pats, rng)   # mid-stream, after eviction
+            mid = pos
+    assert mid is not None
     assert st.check_graph() == 0
     inf = st.info()
     r0, nr = inf["resident_first_row"], inf["resident_rows"]
     assert r0 > 0 and r0 + nr == E
     want = full_mine(g, E, pats)
     np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
+    check_resident_sample(st, g, E, pats, rng)
     st.close()
 
 
@@ -141,11 +188,9 @@ def test_stream_graph_update_edge_cases():
     for a, b in zip(cuts[:-1], cuts[1:]):
         st.append(src[a:b], dst[a:b], ts[a:b])
         assert st.check_graph() == 0, (a, b)
-        if b in (2011, 3001, E):
-            want = full_mine(g, b, pats)
-            inf = st.info()
-            r0, nr = inf["resident_first_row"], inf["resident_rows"]
-            np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
+        if b in (1, 3, 701, 2010, 2011, 3001, 4200, E):
+            check_resident(st, g, b, pats, full_mine(g, b, pats) if b in (2011, 3001, E)
+                           else None)
     st.close()
 
 
@@ -175,6 +220,7 @@ def test_stream_uses_both_leg_emissions():
     inf = st.info()
     r0, nr = inf["resident_first_row"], inf["resident_rows"]
     np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
+    check_resident_sample(st, g, pos, pats, np.random.default_rng(9))
     assert st.check_graph() == 0
     st.close()
 
@@ -200,10 +246,6 @@ def test_stream_column_subsets(kind):
         n = int(min(E - pos, rng.integers(1, 9000)))
         st.append(g.src[pos:pos + n], g.dst[pos:pos + n], g.ts[pos:pos + n])
         pos += n
-    want = full_mine(g, E, pats)
-    inf = st.info()
-    r0, nr = inf["resident_first_row"], inf["resident_rows"]
-    assert r0 > 0
-    np.testing.assert_array_equal(st.read(r0, nr), want[r0:r0 + nr])
+    assert check_resident(st, g, E, pats, full_mine(g, E, pats)) > 0
     assert st.check_graph() == 0
     st.close()

@@ -11,6 +11,7 @@ import aml_synth
 import oracle
 import paper_2604_12241_b300 as aml
 from paper_2604_12241_b300 import patterns as P
+from colmap import from_oracle_columns, oracle_columns
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +37,7 @@ def test_random_graphs_match_oracle(seed, cols):
     g = aml_synth.tiny_random(300, 20_000, 3_000, 700 + seed, self_loops=True)
     want = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes).count_all(cols)
     graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes)
-    pats = P.from_oracle_columns(cols)
+    pats = from_oracle_columns(cols)
     assert (want > 0).any(axis=0).all()
     np.testing.assert_array_equal(_mine(graph, pats), want)
     before = graph.tuning()
@@ -52,10 +53,10 @@ def test_random_graphs_match_oracle(seed, cols):
 def test_tiny10k_beside_ordered_columns():
     g = aml_synth.workload("tiny-10k")
     cols = ([("cycw", k, d) for d in (DAY, WEEK) for k in (3, 4, 5)]
-            + P.oracle_columns(P.standard(DAY)))
+            + oracle_columns(P.standard(DAY)))
     want = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes).count_all(cols)
     graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes, assume_sorted=True)
-    got = _mine(graph, P.from_oracle_columns(cols))
+    got = _mine(graph, from_oracle_columns(cols))
     np.testing.assert_array_equal(got, want)
     # planted ordered cycles on fresh accounts are window cycles too
     for m in g.motifs:

@@ -55,3 +55,26 @@ def test_fan_noalloc_refuses_graphs_above_its_limit():
     rc = _call(graph, 86400, P.DIR_OUT, out, torch.cuda.current_stream())
     assert _lib.STATUS[rc] == "AML_EINVAL"
     assert b"4,194,304" in _lib.lib().aml_last_error()
+
+
+def test_fan_noalloc_at_its_limit():
+    """A graph with exactly 4,194,304 non-loop edges: 2,048 tiles, so the
+    single-block scan of the tile totals is full, and the last tile is a
+    whole one; and one edge fewer, so the last tile is partial."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for n_edges, direction, fam in ((4_194_304, P.DIR_OUT, P.fan_out),
+                                    (4_194_303, P.DIR_IN, P.fan_in)):
+        g = aml_synth.tiny_random(50_000, n_edges, 86400 * 5, seed=78)
+        graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes)
+        assert graph.info()["n_list_edges"] == n_edges
+        ref = aml.mine(graph, aml.PatternSet([fam(P.DAY)]))[:, 0].clone()
+        out = torch.full((g.n_edges,), -1, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            out.fill_(-1)
+            assert _call(graph, P.DAY, direction, out, stream) == 0, \
+                _lib.lib().aml_last_error()
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref)
+        graph.sync()
+        graph.close()
