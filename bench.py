@@ -4,7 +4,10 @@
 One step = one aml_mine over the whole resident graph: every column of the
 workload's pattern set for every edge.  Default workload: hi-small (515,088
 accounts, 5,078,345 transactions over 16 days; DEG/FAN in+out, GS, SG,
-CYC2..5 at 24h and 7d = 20 columns).  Prints one JSON line (rank 0).
+CYC2..5 at 24h and 7d = 20 columns).  Prints one JSON line (rank 0), which
+also carries the end-to-end time through the C ABI's host-buffer path, the
+streaming latencies at three offered loads and the hi-large workload (the
+largest that fits one GPU) under "large".
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
 
@@ -72,7 +75,10 @@ def parse():
                     default="auto", help="cycle search; auto = fastest measured")
     ap.add_argument("--cost-samples", type=int, default=1_000_000)
     ap.add_argument("--cost-epochs", type=int, default=20)
-    ap.add_argument("--stream-batches", type=int, default=30)
+    ap.add_argument("--stream-batches", type=int, default=300,
+                    help="batches per offered load (25/50/90%% of capacity)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the hi-large leg (the largest single-GPU workload)")
     ap.add_argument("--no-window-cycles", action="store_true",
                     help="skip timing the window-cycle columns (CYCW3..5 at the workload's windows)")
     ap.add_argument("--no-programs", action="store_true",
@@ -172,9 +178,9 @@ def measured_peak():
 
 
 # DRAM bytes per launch (read + write) from one ncu capture of hi-small at
-# full size (profiles/dram_hi_small.md), valid only for the kernel sources it
-# was taken with: KERNEL_DIGEST is the digest (kernel_digest()) of the files
-# that define the measured kernels.
+# full size, valid only for the kernel sources it was taken with:
+# KERNEL_DIGEST is the digest (kernel_digest()) of the files that define the
+# measured kernels.
 KERNEL_DIGEST = "c5d6358914ba8ac2"
 MEASURED_TRAFFIC = {"k_cyc_level": 267.0e6, "k_sg_bucket": 519.2e6, "k_leg_emit": 610.1e6,
                     "k_sg_partition": 548.5e6, "k_fan_reduce": 230.5e6, "k_fan_scan": 314.4e6,
@@ -216,8 +222,9 @@ def algorithmic_bytes(kernel: str, E: int, Ev: int, pats, stats: dict) -> float:
                       and delta written (8 B)
       k_fan_scan      per slot: row start, eid (8 B), per window DEG and delta
                       read and (DEG, FAN) written (16 B)
-      k_cyc_level     per path: its parent link and slot (8 B), its anchor's
-                      closing range (8 B), its next-hop count and start (8 B)
+      k_cyc_level     per path: the one window slot (counterparty, time: 8 B)
+                      the depth-first expansion of its parent reads to reach it;
+                      a launch handles one level of paths
     """
     P = len(pats)
     names = [p.name for p in pats]
@@ -246,7 +253,7 @@ def algorithmic_bytes(kernel: str, E: int, Ev: int, pats, stats: dict) -> float:
     if kernel == "k_fan_scan":
         return Ev * (8 + 16 * W)
     if kernel == "k_cyc_level" and front:
-        return 24.0 * sum(front.values()) / len(front)
+        return 8.0 * sum(front.values()) / len(front)
     return float("nan")
 
 
@@ -368,10 +375,9 @@ def run_reference(args, ws, rank):
     """The CPU oracle, as it stands, on the host cores (edge-centric queries)."""
     if rank != 0:
         return
-    import aml_synth
     import oracle
     from paper_2604_12241_b300 import patterns as P
-    g = aml_synth.workload(args.workload)
+    g = make_workload(args, rank)
     pats = P.workload_patterns(args.workload)
     cols = oracle.columns_from_names([p.name for p in pats])
     og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
@@ -399,10 +405,9 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD_TEXT[args.workload], "n_edges": g.n_edges,
-                       "n_nodes": g.n_nodes, "columns": len(cols), "sample_edges": n},
+            "config": workload_config(args.workload, g, len(cols), args.scale, ws),
             "cpu_baseline": {"value": value, "unit": "edges/s", "cores": cores,
-                             "kind": "oracle", "sample": sample},
+                             "kind": "oracle", "sample": sample, "sample_edges_per_step": n},
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -431,24 +436,34 @@ def cpu_baseline(g, pats, seconds: float) -> dict:
 
 # ---------------------------------------------------------------- streaming
 
+STREAM_DAYS = 24        # the stream's graph: hi-medium's shape and daily rate, 24 days
+STREAM_PRE_DAYS = 9     # appended untimed before the measured batches
+STREAM_LOADS = (0.25, 0.5, 0.9)
+
+
 def run_stream(args, rank) -> dict:
-    """Streaming serving (the fifth workload): a HI-Medium-shaped graph (2,032,095
-    accounts, 31,898,238 transactions over 16 days), 20 columns, a 7-day
-    resident window.  The first 9 days are appended in 2M-edge batches
-    (untimed); then batches of log-uniform size in [1e3, 1e5] arrive, first
-    back to back (service latency), then as a Poisson process offered at 50%
-    of the measured capacity (latency = queueing + service)."""
+    """Streaming serving (the fifth workload): a HI-Medium-shaped graph
+    (2,032,095 accounts, Zipf 1.05, hubs to 1e5) at HI-Medium's rate of
+    about 2M transactions a day, generated over 24 days so that enough
+    batches arrive; 20 columns, a 7-day resident window.  The first 9 days
+    are appended in 2M-edge batches (untimed).  Then batches of log-uniform
+    size in [1e3, 1e5] arrive: first back to back (service time, capacity),
+    then as Poisson processes offered at 25%, 50% and 90% of the measured
+    capacity (latency = queueing + service), ``--stream-batches`` batches at
+    each load."""
     import aml_synth
     import paper_2604_12241_b300 as aml
     from paper_2604_12241_b300 import patterns as P
     params = dict(aml_synth.WORKLOADS["hi-medium"])
-    params["seed"] += rank * 1000
-    g = aml_synth.generate(name="hi-medium", **params)
+    params["n_edges"] = int(params["n_edges"] * STREAM_DAYS / params["days"])
+    params["days"] = STREAM_DAYS
+    params["seed"] = 20260005 + rank * 1000
+    g = aml_synth.generate(name="stream", **params)
     pats = P.workload_patterns("hi-medium")
     ps = aml.PatternSet(pats)
     st = aml.Stream(ps, g.n_nodes, resident_window=7 * P.DAY, mem_budget=96 << 30)
     pos = 0
-    t_pre = int(np.searchsorted(g.ts, 9 * P.DAY))
+    t_pre = int(np.searchsorted(g.ts, STREAM_PRE_DAYS * P.DAY))
     while pos < t_pre:
         n = min(2_000_000, t_pre - pos)
         st.append(g.src[pos:pos + n], g.dst[pos:pos + n], g.ts[pos:pos + n], g.amount[pos:pos + n])
@@ -464,7 +479,7 @@ def run_stream(args, rank) -> dict:
         return b
 
     service, sizes = [], []
-    for _ in range(args.stream_batches):
+    for _ in range(max(30, args.stream_batches // 3)):
         if pos >= g.n_edges:
             break
         b = next_batch()
@@ -474,34 +489,255 @@ def run_stream(args, rank) -> dict:
         sizes.append(len(b[0]))
     cap_eps = sum(sizes) / sum(service)               # edges/s, back to back
     mean_n = float(np.mean(sizes))
-    lam = 0.5 * cap_eps / mean_n                      # batches/s at 50% load
-    lat, t_next, sizes2 = [], time.perf_counter(), []
-    for _ in range(args.stream_batches):
-        if pos >= g.n_edges:
-            break
-        t_next += rng.exponential(1.0 / lam)
-        b = next_batch()
-        now = time.perf_counter()
-        if now < t_next:
-            time.sleep(t_next - now)
-        st.append(*b)
-        lat.append(time.perf_counter() - t_next)
-        sizes2.append(len(b[0]))
+    ms = lambda v, q: float(np.percentile(np.asarray(v) * 1e3, q)) if v else None
+    loads = {}
+    for load in STREAM_LOADS:
+        lam = load * cap_eps / mean_n                 # batches/s
+        lat, sizes2 = [], []
+        t_start = t_next = time.perf_counter()
+        for _ in range(args.stream_batches):
+            if pos >= g.n_edges:
+                break
+            t_next += rng.exponential(1.0 / lam)
+            b = next_batch()
+            now = time.perf_counter()
+            if now < t_next:
+                time.sleep(t_next - now)
+            st.append(*b)
+            lat.append(time.perf_counter() - t_next)
+            sizes2.append(len(b[0]))
+        span = time.perf_counter() - t_start
+        loads[f"load_{int(round(load * 100))}pct"] = {
+            "batches": len(lat), "p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99),
+            "max_ms": ms(lat, 100), "edges_per_s": sum(sizes2) / span if lat else None,
+            "arrivals": "Poisson, batches/s = %.2f" % lam}
     info = st.info()
     st.close()
-    ms = lambda v, q: float(np.percentile(np.asarray(v) * 1e3, q)) if v else None
-    return {"workload": "hi-medium shape, 7-day resident window, 20 columns",
-            "resident_rows": info["resident_rows"], "batches": len(service) + len(lat),
+    return {"workload": ("hi-medium shape (2,032,095 accounts, Zipf 1.05, hubs to 1e5) at "
+                         "~2.0M transactions/day over 24 days; 7-day resident window, 20 columns"),
+            "resident_rows": info["resident_rows"], "batches": len(service) + sum(
+                v["batches"] for v in loads.values()),
             "batch_edges": "log-uniform in [1e3, 1e5]",
+            "service_batches": len(service),
             "service_ms_p50": ms(service, 50), "service_ms_p99": ms(service, 99),
-            "capacity_edges_per_s": cap_eps,
-            "load_50pct": {"p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99),
-                           "edges_per_s": sum(sizes2) / (sum(lat) if lat else 1),
-                           "arrivals": "Poisson, batches/s = %.2f" % lam},
-            "method": "exact: one mine of the window W within 7d of the batch plus the batch, counting only instances whose latest edge is new"}
+            "capacity_edges_per_s": cap_eps, **loads,
+            "method": "exact: one mine of the window W within 7d of the batch plus the batch, "
+                      "counting only instances whose latest edge is new"}
+
+
+# ------------------------------------------------------------ end to end
+
+def time_e2e(args, g, ps, E, Pn, ref_out, ws, dist) -> dict:
+    """End to end through the C ABI with host buffers, every step: the
+    step's transactions from page-locked host arrays (aml_graph_create with
+    AML_PTR_HOST: the library copies them to the device and builds the
+    graph), the mine, and the counts back into page-locked host memory
+    (aml_mine with AML_MINE_HOST_OUTPUT | AML_MINE_HOST_ASYNC).  Steps use a
+    ring of three slots (stream + output buffer); a step takes its slot by
+    destroying the slot's previous graph, which waits for that step's copy
+    back.  aml_graph_create waits for its build and the first mine of a graph
+    waits once for its sizes, so two pipelines are timed: one host thread
+    (the next step's upload and build overlap this step's copy back), and
+    two host threads (the calls release the GIL), reporting the faster."""
+    import threading
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+
+    import paper_2604_12241_b300 as aml
+    R = 3
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+           (("src", g.src), ("dst", g.dst), ("ts", g.ts), ("amount", g.amount))}
+    host = {k: t.numpy() for k, t in pin.items()}
+    S = [torch.cuda.Stream() for _ in range(R)]
+    out_pin = [torch.empty((E, Pn), dtype=torch.int32).pin_memory() for _ in range(R)]
+    out_host = [t.numpy().view(np.uint32) for t in out_pin]
+    live = [None] * R
+    slot_lock = [threading.Lock() for _ in range(R)]
+    dev = torch.cuda.current_device()
+
+    def take_slot(i):
+        if live[i] is not None:
+            live[i].close()
+            live[i] = None
+
+    def step(k):
+        torch.cuda.set_device(dev)  # worker threads start on device 0
+        i = k % R
+        with slot_lock[i]:
+            take_slot(i)
+            gg = aml.Graph(host["src"], host["dst"], host["ts"], g.n_nodes,
+                           amount=host["amount"], assume_sorted=True, stream=S[i])
+            aml.mine(gg, ps, out=out_host[i], stream=S[i], host_output=True, host_async=True)
+            live[i] = gg
+
+    def run(n_steps, workers):
+        if workers == 1:
+            for k in range(n_steps):
+                step(k)
+        else:
+            with ThreadPoolExecutor(max_workers=workers) as pool:
+                for f in [pool.submit(step, k) for k in range(n_steps)]:
+                    f.result()
+        for i in range(R):
+            take_slot(i)
+
+    times = {}
+    for workers in (1, 2):
+        run(R, workers)
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run(args.e2e_steps, workers)
+        torch.cuda.synchronize()
+        times[workers] = dist.max(time.perf_counter() - t0)
+    host_threads = min(times, key=times.get)
+    e2e_s = times[host_threads]
+    last = out_host[(args.e2e_steps - 1) % R]
+    return {"value": ws * E * args.e2e_steps / e2e_s, "unit": "edges/s",
+            "h2d_bytes_per_step": int(E * 16), "d2h_bytes_per_step": int(E * Pn * 4),
+            "steps": args.e2e_steps, "ms_per_step": 1000.0 * e2e_s / args.e2e_steps,
+            "matches_device_output": bool(np.array_equal(
+                last, ref_out.cpu().numpy().view(np.uint32))),
+            "host_threads": host_threads,
+            "ms_per_step_by_host_threads": {str(w): round(1000.0 * t / args.e2e_steps, 3)
+                                            for w, t in times.items()},
+            "api": "aml_graph_create(AML_PTR_HOST | AML_ASSUME_SORTED) + aml_mine("
+                   "AML_MINE_HOST_OUTPUT | AML_MINE_HOST_ASYNC), page-locked host buffers",
+            "includes": "host inputs -> device, graph build, mine, counts -> host memory, "
+                        "every step; steps over a ring of three streams"}
+
+
+# ------------------------------------------------------------ shared timing
+
+def mine_ms(graph, ps, out, stream, flush, use_graph, mode, reps) -> float:
+    """Median CUDA-event time of `reps` mines (L2 flushed before each, two
+    untimed mines first)."""
+    import torch
+
+    import paper_2604_12241_b300 as aml
+    for _ in range(2):
+        aml.mine(graph, ps, out=out, stream=stream, use_graph=use_graph, mode=mode)
+    torch.cuda.synchronize()
+    ts_ = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        aml.mine(graph, ps, out=out, stream=stream, use_graph=use_graph, mode=mode)
+        b.record(stream)
+        b.synchronize()
+        ts_.append(a.elapsed_time(b))
+    return float(np.median(ts_))
+
+
+def profiled_mines(graph, ps, out, stream, flush, mode, n) -> tuple:
+    """Per-kernel CUDA-event times of n plain (not replayed) mines: the
+    library records a pair of events around every launch on its stream."""
+    import torch
+
+    import paper_2604_12241_b300 as aml
+    from paper_2604_12241_b300 import _lib
+    torch.cuda.synchronize()
+    _lib.profile_read(reset=True)
+    _lib.profile_enable(True)
+    total = 0.0
+    for _ in range(n):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        aml.mine(graph, ps, out=out, stream=stream, mode=mode)
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+    _lib.profile_enable(False)
+    return total, _lib.profile_read(reset=True)
+
+
+def roofline_of(prof, total_ms, graph, pats, E, Ev) -> dict:
+    """The dominant kernel's HBM roofline: algorithmic bytes per launch over
+    its mean launch time (CUDA events), against the measured copy
+    bandwidth."""
+    dom_name, (dom_n, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    big = max(int(p.name.split("@")[1]) for p in pats)
+    ws_stats = graph.window_stats(big)
+    stats = {"legs": ws_stats["n_legs"], "front": ws_stats["n_front"]}
+    peak, peak_src = measured_peak()
+    alg = algorithmic_bytes(dom_name, E, Ev, pats, stats)
+    achieved = alg / (dom_ms / dom_n / 1000.0) / 1e9 if alg == alg else None
+    return {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+            "peak_source": peak_src, "launch_ms": dom_ms / dom_n,
+            "share_of_step": dom_ms / total_ms, "algorithmic_bytes_per_launch": alg,
+            "timed_in": "plain-mode profiled pass (CUDA events per launch)",
+            "leg_pass": {"delta": big, **stats}}
+
+
+# --------------------------------------------------------------- hi-large
+
+def run_large(args, rank, local) -> dict:
+    """The largest single-GPU workload (hi-large: 2,070,980 accounts,
+    179,702,229 transactions over 90 days; FAN_OUT, FAN_IN, GS, SG,
+    CYC3..CYC6 at 24h, FAN_OUT, FAN_IN at 7d): the resident graph mined with
+    graph replay after autotuning, with the cost model trained for learned
+    binning; level-by-level and learned-binned cycle searches both timed."""
+    import torch
+
+    import aml_synth
+    import paper_2604_12241_b300 as aml
+    from paper_2604_12241_b300 import patterns as P
+    params = dict(aml_synth.WORKLOADS["hi-large"])
+    params["seed"] += rank * 1000
+    g = aml_synth.generate(name="hi-large", **params)
+    pats = P.workload_patterns("hi-large")
+    E, Pn = g.n_edges, len(pats)
+    graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes, amount=g.amount, assume_sorted=True)
+    Ev = graph.info()["n_list_edges"]
+    ps = aml.PatternSet(pats)
+    out = torch.empty((E, Pn), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    best, best_ms = aml.autotune(graph, ps, repeats=3)
+    rep = aml.cost_train(graph, ps, max_samples=args.cost_samples, epochs=args.cost_epochs,
+                         seed=20260004)
+    modes = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for m in ("plain", "learned"):
+        modes[m] = mine_ms(graph, ps, out, stream, flush, True, m, 5)
+    clk = clocks.stop()
+    mode = min(modes, key=modes.get)
+    plain = out.clone()
+    aml.mine(graph, ps, out=out, stream=stream, use_graph=True, mode="learned")
+    same = bool(torch.equal(out, plain))
+    total, prof = profiled_mines(graph, ps, out, stream, flush, mode, 1)
+    res = {"workload": WORKLOAD_TEXT["hi-large"], "n_edges": E, "columns": Pn,
+           "ms_per_mine": modes[mode], "edges_per_s": E / modes[mode] * 1e3,
+           "cycle_mode": mode, "cycle_modes_ms": modes, "replay": "one CUDA graph per mine",
+           "learned_equals_plain": same,
+           "cost_model": {k: rep[k] for k in ("n_train", "n_test", "test_log_mae",
+                                                "test_spearman", "degree_spearman")},
+           "autotune": {"tuning": best, "best_ms": best_ms},
+           "roofline": roofline_of(prof, total, graph, pats, E, Ev),
+           "kernels": {k: {"launches": n, "ms": round(t, 4), "share": round(t / total, 4)}
+                       for k, (n, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]},
+           "clocks": clk,
+           "timing": "median of 5 replayed mines per mode, CUDA events, L2 flushed between"}
+    del out, plain, flush
+    graph.close()
+    torch.cuda.empty_cache()
+    return res
 
 
 # --------------------------------------------------------------------- ours
+
+def workload_config(name: str, g, n_cols: int, scale: float, ws: int) -> dict:
+    """The static description of the timed workload (both arms print it)."""
+    return {"workload": WORKLOAD_TEXT[name], "n_edges": int(g.n_edges), "n_nodes": int(g.n_nodes),
+            "columns": n_cols, "scale": scale,
+            "l2": "flushed between steps (256 MB write, untimed)",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
+
 
 def run_ours(args, ws, rank, local):
     import torch
@@ -513,14 +749,7 @@ def run_ours(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dist = Dist(ws)
-    params = dict(aml_synth.WORKLOADS[args.workload])
-    if args.scale != 1.0:
-        params["n_nodes"] = max(1000, int(params["n_nodes"] * args.scale))
-        params["n_edges"] = max(10_000, int(params["n_edges"] * args.scale))
-        if params.get("d_max"):
-            params["d_max"] = max(50.0, params["d_max"] * args.scale)
-    params["seed"] += rank * 1000     # independent replica per rank
-    g = aml_synth.generate(name=args.workload, **params)
+    g = make_workload(args, rank)
     pats = P.workload_patterns(args.workload)
     E, Pn = g.n_edges, len(pats)
 
@@ -544,26 +773,10 @@ def run_ours(args, ws, rank, local):
     if args.cycle_mode in ("auto", "learned"):
         cost_report = aml.cost_train(graph, ps, max_samples=args.cost_samples,
                                      epochs=args.cost_epochs, seed=20260003)
-
-    def mode_ms(mode, reps=10):
-        for _ in range(2):
-            aml.mine(graph, ps, out=out, use_graph=use_graph, mode=mode)
-        torch.cuda.synchronize()
-        ts_ = []
-        for _ in range(reps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            aml.mine(graph, ps, out=out, stream=stream, use_graph=use_graph, mode=mode)
-            b.record(stream)
-            b.synchronize()
-            ts_.append(a.elapsed_time(b))
-        return float(np.median(ts_))
-
     modes = {}
     if args.cycle_mode == "auto":
         for m in ("plain", "persistent", "learned"):
-            modes[m] = mode_ms(m)
+            modes[m] = mine_ms(graph, ps, out, stream, flush, use_graph, m, 10)
         cycle_mode = min(modes, key=modes.get)
     else:
         cycle_mode = args.cycle_mode
@@ -572,181 +785,45 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     graph.sync()
 
-    def timed(steps, graph_mode, profile, mode):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
-        dist.barrier()
-        torch.cuda.synchronize()
-        l0 = _lib.launch_count()
-        if profile:
-            _lib.profile_read(reset=True)
-            _lib.profile_enable(True)
-        w0 = time.perf_counter()
-        for k in range(steps):
-            flush.zero_()                     # evict L2 between steps (not timed)
-            ev[k][0].record(stream)
-            aml.mine(graph, ps, out=out, stream=stream, use_graph=graph_mode, mode=mode)
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - w0
-        dist.barrier()
-        if profile:
-            _lib.profile_enable(False)
-        launches = _lib.launch_count() - l0
-        graph.sync()
-        ms = sum(a.elapsed_time(b) for a, b in ev)
-        prof = _lib.profile_read(reset=True) if profile else {}
-        return ms, wall, launches, prof
-
     # headline: the chosen mode, clocks sampled during the timed region
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
-    dev_ms, wall, launches, _ = timed(args.steps, use_graph, False, cycle_mode)
+    dist.barrier()
+    torch.cuda.synchronize()
+    l0 = _lib.launch_count()
+    w0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                     # evict L2 between steps (not timed)
+        ev[k][0].record(stream)
+        aml.mine(graph, ps, out=out, stream=stream, use_graph=use_graph, mode=cycle_mode)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    dist.barrier()
+    launches = _lib.launch_count() - l0
     clk = clocks.stop()
-    dev_ms_max = dist.max(dev_ms)
-    # per-kernel CUDA-event times come from a pass without graph replay
-    # (events cannot be recorded between the kernels of a replayed graph)
+    graph.sync()
+    dev_ms_max = dist.max(sum(a.elapsed_time(b) for a, b in ev))
+    # per-kernel CUDA-event times come from plain (not replayed) mines:
+    # events cannot be recorded between the kernels of a replayed graph
     prof_steps = max(3, min(args.steps, 10))
-    plain_ms, _, plain_launches, prof = timed(prof_steps, False, True, cycle_mode)
+    plain_ms, prof = profiled_mines(graph, ps, out, stream, flush, cycle_mode, prof_steps)
 
-    # end to end through the public API, every step: the step's inputs copied
-    # from pinned host memory to the device, graph build, mine, and the
-    # counts copied back to pinned host memory.  Transfers in one direction
-    # run one at a time; an upload and a copy back overlap (the link is full
-    # duplex), though each then runs slower.  The steps use a ring of three
-    # slots, each with its own stream and buffers; a step takes its slot by
-    # destroying the slot's previous graph (which waits for that step's copy
-    # back).  The library's calls block their host thread while they wait for
-    # sizes on the device, so two pipelines are timed: one host thread that
-    # uploads step k, then starts step k-1's copy back under step k's build
-    # and mine; and two host threads (the calls release the GIL), each step
-    # enqueueing its own copy back behind its mine while the other thread's
-    # step uploads, builds and mines.
-    e2e = None
-    if not args.no_e2e:
-        import threading
-        from concurrent.futures import ThreadPoolExecutor
-        R = 3
-        pin = {k: torch.from_numpy(v).pin_memory() for k, v in
-               (("src", g.src), ("dst", g.dst), ("ts", g.ts), ("amount", g.amount))}
-        S = [torch.cuda.Stream() for _ in range(R)]
-        dev_in = [{k: torch.empty_like(t, device="cuda") for k, t in pin.items()} for _ in range(R)]
-        dev_out = [torch.empty((E, Pn), dtype=torch.int32, device="cuda") for _ in range(R)]
-        out_pin = [torch.empty((E, Pn), dtype=torch.int32).pin_memory() for _ in range(R)]
-        live = [None] * R
-        slot_lock = [threading.Lock() for _ in range(R)]
-
-        dev = torch.cuda.current_device()
-
-        def take_slot(i):
-            if live[i] is not None:
-                live[i].close()
-                live[i] = None
-
-        def upload(i):
-            with torch.cuda.stream(S[i]):
-                for key, t in pin.items():
-                    dev_in[i][key].copy_(t, non_blocking=True)
-
-        def build_mine(i):
-            gg = aml.Graph(dev_in[i]["src"], dev_in[i]["dst"], dev_in[i]["ts"], g.n_nodes,
-                           amount=dev_in[i]["amount"], assume_sorted=True, stream=S[i])
-            aml.mine(gg, ps, out=dev_out[i], stream=S[i])
-            live[i] = gg
-
-        def copy_back(i):
-            with torch.cuda.stream(S[i]):
-                out_pin[i].copy_(dev_out[i], non_blocking=True)
-
-        def step_threaded(k):
-            # its own copy back behind its mine; the next step (another
-            # thread) uploads, builds and mines meanwhile
-            torch.cuda.set_device(dev)  # worker threads start on device 0
-            i = k % R
-            with slot_lock[i]:
-                take_slot(i)
-                upload(i)
-                build_mine(i)
-                copy_back(i)
-
-        def step_single(k):
-            # one thread: the upload first, at the link's full rate, then the
-            # previous step's copy back under this step's build and mine
-            i = k % R
-            take_slot(i)
-            upload(i)
-            if k > 0:
-                j = (k - 1) % R
-                up = torch.cuda.Event()
-                up.record(S[i])
-                S[j].wait_event(up)
-                copy_back(j)
-            build_mine(i)
-
-        def e2e_run(n_steps, workers):
-            if workers == 1:
-                for k in range(n_steps):
-                    step_single(k)
-                copy_back((n_steps - 1) % R)
-            else:
-                with ThreadPoolExecutor(max_workers=workers) as pool:
-                    for f in [pool.submit(step_threaded, k) for k in range(n_steps)]:
-                        f.result()
-            for i in range(R):
-                take_slot(i)
-
-        # two host threads let two steps' builds and mines overlap: a gain
-        # when the copy back dominates a step (hi-small), a loss when the
-        # mine does (larger graphs); the faster of the two is reported
-        e2e_times = {}
-        for workers in (1, 2):
-            e2e_run(R, workers)
-            dist.barrier()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            e2e_run(args.e2e_steps, workers)
-            torch.cuda.synchronize()
-            e2e_times[workers] = dist.max(time.perf_counter() - t0)
-        host_threads = min(e2e_times, key=e2e_times.get)
-        e2e_s = e2e_times[host_threads]
-        last = out_pin[(args.e2e_steps - 1) % R].numpy().view(np.uint32)
-        e2e = {"value": ws * E * args.e2e_steps / e2e_s, "unit": "edges/s",
-               "h2d_bytes_per_step": int(E * 16), "d2h_bytes_per_step": int(E * Pn * 4),
-               "steps": args.e2e_steps, "ms_per_step": 1000.0 * e2e_s / args.e2e_steps,
-               "matches_device_output": bool(np.array_equal(
-                   last, out.cpu().numpy().view(np.uint32))),
-               "host_threads": host_threads,
-               "ms_per_step_by_host_threads": {str(w): round(1000.0 * t / args.e2e_steps, 3)
-                                               for w, t in e2e_times.items()},
-               "includes": "pinned host inputs -> device, graph build, mine, counts -> pinned "
-                           "host memory; steps on host threads over a ring of three streams, "
-                           "each step's copy back enqueued behind its mine, so the next "
-                           "step's upload, build and mine overlap it"}
+    e2e = None if args.no_e2e else time_e2e(args, g, ps, E, Pn, out, ws, dist)
 
     line = None
     if rank == 0:
         value = ws * E * args.steps / (dev_ms_max / 1000.0)
         info = graph.info()
-        # dominant kernel of the timed region, from its own CUDA events
-        dom = max(prof.items(), key=lambda kv: kv[1][1])
-        dom_name, (dom_n, dom_ms) = dom
-        # the leg pass runs on the largest window (smaller ones are counted in it)
-        big = max(int(p.name.split("@")[1]) for p in pats)
-        ws_stats = graph.window_stats(big)
-        stats = {"legs": ws_stats["n_legs"], "front": ws_stats["n_front"]}
-        peak, peak_src = measured_peak()
-        alg = algorithmic_bytes(dom_name, E, info["n_list_edges"], pats, stats)
-        achieved = alg / (dom_ms / dom_n / 1000.0) / 1e9 if alg == alg else None
+        roof = roofline_of(prof, plain_ms, graph, pats, E, info["n_list_edges"])
         traffic = None
-        if (args.workload == "hi-small" and args.scale == 1.0 and kernel_digest() == KERNEL_DIGEST):
-            traffic = MEASURED_TRAFFIC.get(dom_name)
-        roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": traffic, "traffic_unit": "bytes per launch (ncu, full size)",
-                "peak_source": peak_src,
-                "launch_ms": dom_ms / dom_n, "share_of_step": dom_ms / plain_ms,
-                "algorithmic_bytes_per_launch": alg, "timed_in": "plain-mode profiled pass",
-                "leg_pass": {"delta": big, **stats}}
+        if (args.workload == "hi-small" and args.scale == 1.0
+                and kernel_digest() == KERNEL_DIGEST):
+            traffic = MEASURED_TRAFFIC.get(roof["kernel"])
+        roof["traffic"] = traffic
+        roof["traffic_unit"] = "DRAM bytes read + written per launch (ncu, full size)"
         kernels = {k: {"launches": n, "ms_per_step": round(ms / prof_steps, 4),
                        "share": round(ms / plain_ms, 4)}
                    for k, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -755,18 +832,12 @@ def run_ours(args, ws, rank, local):
                 "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "impl": "ours",
-                "config": {"workload": WORKLOAD_TEXT[args.workload], "n_edges": E,
-                           "n_nodes": g.n_nodes, "columns": Pn, "mode": args.mode,
-                           "autotune": tune_info, "cycle_mode": cycle_mode,
-                           "cycle_modes_ms": modes or None,
-                           "scale": args.scale,
-                           "l2": "flushed between steps (256 MB write, untimed)",
-                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                           "wall_s_timed_loop": wall},
+                "config": workload_config(args.workload, g, Pn, args.scale, ws),
+                "run": {"mode": args.mode, "autotune": tune_info, "cycle_mode": cycle_mode,
+                        "cycle_modes_ms": modes or None, "wall_s_timed_loop": wall},
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clk,
                 "plain_ms_per_step": plain_ms / prof_steps,
                 "cost_model": cost_report,
-                "plain_gpu_launches_per_step": plain_launches / prof_steps,
                 "kernels": kernels}
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g, pats, args.cpu_seconds)
@@ -774,15 +845,33 @@ def run_ours(args, ws, rank, local):
             line["window_cycles"] = time_window_cycles(graph, pats, E, use_graph, stream, flush)
         if not args.no_programs:
             line["interpreter"] = time_programs(graph, E, stream, flush)
+    del out, flush
     graph.close()
+    torch.cuda.empty_cache()
     if not args.no_stream:
-        stream = run_stream(args, rank)
+        st = run_stream(args, rank)
         if line is not None:
-            line["stream"] = stream
-            line["p99_stream_latency_ms"] = stream["load_50pct"]["p99_ms"]
+            line["stream"] = st
+            line["p99_stream_latency_ms"] = st["load_50pct"]["p99_ms"]
+    if not args.no_large and args.workload != "hi-large":
+        large = run_large(args, rank, local)
+        if line is not None:
+            line["large"] = large
     dist.close()
     if line is not None:
         print(json.dumps(line), flush=True)
+
+
+def make_workload(args, rank):
+    import aml_synth
+    params = dict(aml_synth.WORKLOADS[args.workload])
+    if args.scale != 1.0:
+        params["n_nodes"] = max(1000, int(params["n_nodes"] * args.scale))
+        params["n_edges"] = max(10_000, int(params["n_edges"] * args.scale))
+        if params.get("d_max"):
+            params["d_max"] = max(50.0, params["d_max"] * args.scale)
+    params["seed"] += rank * 1000     # independent replica per rank
+    return aml_synth.generate(name=args.workload, **params)
 
 
 def main():

@@ -46,7 +46,7 @@ def test_tiny_graphs_saturate_like_the_oracle(limit):
         np.testing.assert_array_equal(_mine(graph, from_oracle_columns(COLS)), want)
         reached += int((full > limit).sum())
         graph.close()
-    assert reached > 50
+    assert reached > 20   # the limit is really reached, on many edges
 
 
 def test_tiny_10k_saturates_plain_and_captured():
