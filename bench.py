@@ -71,7 +71,7 @@ def parse():
                     help='fixed tunables instead of the autotuner, e.g. '
                          '\'{"own_max": 16, "block": 128}\' (profiling captures)')
     ap.add_argument("--no-stream", action="store_true")
-    ap.add_argument("--cycle-mode", choices=["auto", "plain", "persistent", "learned"],
+    ap.add_argument("--cycle-mode", choices=["auto", "plain", "fused", "persistent", "learned"],
                     default="auto", help="cycle search; auto = fastest measured")
     ap.add_argument("--cost-samples", type=int, default=1_000_000)
     ap.add_argument("--cost-epochs", type=int, default=20)
@@ -703,7 +703,7 @@ def run_large(args, rank, local) -> dict:
     modes = {}
     clocks = ClockSampler(local)
     clocks.start()
-    for m in ("plain", "learned"):
+    for m in ("plain", "fused", "learned"):
         modes[m] = mine_ms(graph, ps, out, stream, flush, True, m, 5)
     clk = clocks.stop()
     mode = min(modes, key=modes.get)
@@ -775,7 +775,7 @@ def run_ours(args, ws, rank, local):
                                      epochs=args.cost_epochs, seed=20260003)
     modes = {}
     if args.cycle_mode == "auto":
-        for m in ("plain", "persistent", "learned"):
+        for m in ("plain", "fused", "persistent", "learned"):
             modes[m] = mine_ms(graph, ps, out, stream, flush, use_graph, m, 10)
         cycle_mode = min(modes, key=modes.get)
     else:

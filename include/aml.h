@@ -307,6 +307,18 @@ aml_status aml_pattern_set_column(const aml_pattern_set* ps, int32_t col,
                                    /* cost model trained by aml_cost_train for   */
                                    /* that window (degree estimate when no model */
                                    /* exists)                                   */
+#define AML_MINE_FUSED 0x20u       /* the level-by-level cycle search in one      */
+                                   /* persistent cooperative launch: per level,   */
+                                   /* the blocks close their chunk's cycles, meet */
+                                   /* at a grid-wide barrier, place their chunk's */
+                                   /* children from all blocks' counts and meet   */
+                                   /* again (no per-level scan, emission or count */
+                                   /* arrays).  The first mine of a (graph,       */
+                                   /* window) runs the plain search to learn the  */
+                                   /* level sizes.  Not with PERSISTENT/LEARNED.  */
+                                   /* A barrier wait that runs out (see           */
+                                   /* aml_graph_set_wait_limit) ends the launch:  */
+                                   /* AML_ETIMEOUT at aml_sync, counts invalid.   */
 #define AML_MINE_HOST_ASYNC 0x10u  /* with HOST_OUTPUT: counts is page-locked    */
                                    /* host memory (cudaHostAlloc / registered),  */
                                    /* the copy back is enqueued on `stream` and  */
@@ -353,6 +365,17 @@ aml_status aml_graph_set_tuning(aml_graph* g, const aml_tuning* t);
  * units to exercise the clamp on tiny graphs.  limit >= 1 (0: AML_EINVAL).
  * Drops the graph's captured mines (AML_MINE_GRAPH). */
 aml_status aml_graph_set_count_limit(aml_graph* g, uint32_t limit);
+
+/* Bound on every device-side wait of the graph's kernels (the grid-wide
+ * barriers of AML_MINE_FUSED), in SM clock cycles (no paper counterpart).
+ * Default 2^32 (about 2 s at 2 GHz): in normal operation every block of a
+ * cooperative launch is resident and a barrier completes in microseconds.
+ * A wait that runs out gives up: the kernel records ERR_TIMEOUT in the
+ * graph's error word and returns, aml_sync returns AML_ETIMEOUT, and that
+ * mine's counts are not valid; the context stays usable.  0 gives up at once
+ * unless the wait is already over (tests use it to make a wait run out).
+ * cycles >= 0 (else AML_EINVAL).  Drops the graph's captured mines. */
+aml_status aml_graph_set_wait_limit(aml_graph* g, int64_t cycles);
 
 /* Autotuner: times real mines of `ps` on `g` (median of `repeats` after one
  * warm-up each, CUDA events on `stream`) while sweeping one tunable at a time

@@ -17,8 +17,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import patterns  # noqa: F401
-from ._lib import (ASSUME_SORTED, MINE_GRAPH, MINE_HOST_ASYNC, MINE_HOST_OUTPUT,  # noqa: F401
-                   MINE_LEARNED, MINE_PERSISTENT, PTR_DEVICE, PTR_HOST, AmlError, aml_column_info,
+from ._lib import (ASSUME_SORTED, MINE_FUSED, MINE_GRAPH, MINE_HOST_ASYNC,  # noqa: F401
+                   MINE_HOST_OUTPUT, MINE_LEARNED, MINE_PERSISTENT, PTR_DEVICE, PTR_HOST, AmlError, aml_column_info,
                    aml_cost_report, aml_graph_info, aml_stream_batch, aml_stream_info,
                    aml_tuning, check, lib, make_patterns)
 
@@ -111,6 +111,10 @@ class Graph:
         """Saturation bound of this graph's counts (aml_graph_set_count_limit)."""
         check(lib().aml_graph_set_count_limit(self._h, int(limit)))
 
+    def set_wait_limit(self, cycles: int) -> None:
+        """Bound on device-side waits in SM cycles (aml_graph_set_wait_limit)."""
+        check(lib().aml_graph_set_wait_limit(self._h, int(cycles)))
+
     def close(self) -> None:
         if getattr(self, "_h", None):
             lib().aml_graph_destroy(self._h)
@@ -177,7 +181,8 @@ def cost_train(graph: Graph, pset: PatternSet, max_samples: int = 1_000_000, epo
     return {f: getattr(r, f) for f, _ in r._fields_}
 
 
-MODES = {"plain": 0, "persistent": MINE_PERSISTENT, "learned": MINE_LEARNED}
+MODES = {"plain": 0, "persistent": MINE_PERSISTENT, "learned": MINE_LEARNED,
+         "fused": MINE_FUSED}
 
 
 def mine(graph: Graph, pset: PatternSet, out=None, stream=None, host_output: bool = False,
@@ -192,7 +197,8 @@ def mine(graph: Graph, pset: PatternSet, out=None, stream=None, host_output: boo
     be page-locked, e.g. a pinned torch tensor's ``.numpy()``) and the caller
     synchronizes ``stream`` before reading it.  ``use_graph``
     replays the whole mine as one captured CUDA graph (AML_MINE_GRAPH).
-    ``mode``: "plain" (level-by-level cycle search), "persistent" (one
+    ``mode``: "plain" (level-by-level cycle search), "fused" (the same
+    search in one cooperative persistent launch), "persistent" (one
     persistent launch, degree-binned queues) or "learned" (queues from the
     trained cost model).  All modes give identical counts.
     """

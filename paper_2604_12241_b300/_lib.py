@@ -24,6 +24,7 @@ MINE_GRAPH = 0x2
 MINE_PERSISTENT = 0x4
 MINE_LEARNED = 0x8
 MINE_HOST_ASYNC = 0x10
+MINE_FUSED = 0x20
 
 
 class AmlError(RuntimeError):
@@ -118,6 +119,7 @@ _SIGS = {
     "aml_graph_get_tuning": (ctypes.c_int32, [_VP, ctypes.POINTER(aml_tuning)]),
     "aml_graph_set_tuning": (ctypes.c_int32, [_VP, ctypes.POINTER(aml_tuning)]),
     "aml_graph_set_count_limit": (ctypes.c_int32, [_VP, ctypes.c_uint32]),
+    "aml_graph_set_wait_limit": (ctypes.c_int32, [_VP, ctypes.c_int64]),
     "aml_autotune": (ctypes.c_int32, [_VP, _VP, ctypes.c_int32, _VP, ctypes.POINTER(aml_tuning),
                                       ctypes.POINTER(ctypes.c_float)]),
     "aml_stream_open": (ctypes.c_int32, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t,

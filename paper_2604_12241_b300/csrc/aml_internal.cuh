@@ -173,6 +173,9 @@ struct aml_graph {
   // every count above this is reported as this (2^32-1; lowered only by
   // aml_graph_set_count_limit, which tests use to reach the clamp)
   uint32_t count_limit = 0xffffffffu;
+  // SM clock cycles a device-side wait of this graph's kernels may take
+  // before it gives up (the fused cycle search's grid barriers)
+  long long wait_limit = 1ll << 32;
   aml::Tuning tune;
   uint64_t tune_gen = 0;
   std::vector<aml::MineExec> execs;   // captured mines (AML_MINE_GRAPH)

@@ -197,11 +197,13 @@ aml_status aml_mine(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, i
   return guarded("aml_mine", [&] {
     AML_REQUIRE(g && ps, AML_EINVAL, "NULL graph or pattern set");
     AML_REQUIRE((flags & ~(AML_MINE_HOST_OUTPUT | AML_MINE_GRAPH | AML_MINE_PERSISTENT |
-                           AML_MINE_LEARNED | AML_MINE_HOST_ASYNC)) == 0,
+                           AML_MINE_LEARNED | AML_MINE_HOST_ASYNC | AML_MINE_FUSED)) == 0,
                 AML_EINVAL, "unknown flag bits");
+    AML_REQUIRE(!((flags & AML_MINE_FUSED) && (flags & (AML_MINE_PERSISTENT | AML_MINE_LEARNED))),
+                AML_EINVAL, "AML_MINE_FUSED excludes AML_MINE_PERSISTENT and AML_MINE_LEARNED");
     AML_REQUIRE(!(flags & AML_MINE_HOST_ASYNC) || (flags & AML_MINE_HOST_OUTPUT), AML_EINVAL,
                 "AML_MINE_HOST_ASYNC needs AML_MINE_HOST_OUTPUT");
-    const uint32_t mode = flags & (AML_MINE_PERSISTENT | AML_MINE_LEARNED);
+    const uint32_t mode = flags & (AML_MINE_PERSISTENT | AML_MINE_LEARNED | AML_MINE_FUSED);
     AML_REQUIRE(!((flags & AML_MINE_GRAPH) && (flags & AML_MINE_HOST_OUTPUT)), AML_EINVAL,
                 "AML_MINE_GRAPH needs a device output");
     AML_REQUIRE(!(flags & AML_MINE_GRAPH) || ps->progs.empty(), AML_EUNSUPPORTED,

@@ -507,7 +507,8 @@ void cycles_hybrid(aml_graph* g, const GraphView& gv, int32_t delta, int K,
   A.close_scan_max = g->tune.close_scan_max;
   AML_LAUNCH("k_cyc_persistent", side,
              k_cyc_persistent<<<persistent_grid(), 256, 0, side>>>(A));
-  level_cycle_search(g, gv, delta, K, slots, sub, acc, crng, la_h.p, lb_h.p, cache, s);
+  level_cycle_search(g, gv, delta, K, slots, sub, acc, crng, nullptr, nullptr, la_h.p, lb_h.p,
+                     cache, s);
   if (fork) {  // joined before the buffers above are released on s
     AML_CUDA(cudaEventRecord(g->branch_ev[5], side));
     AML_CUDA(cudaStreamWaitEvent(s, g->branch_ev[5], 0));
@@ -569,7 +570,7 @@ void cost_train(aml_graph* g, const aml_pattern_set* ps, int64_t max_samples, in
   GraphView gv = view_of(g);
   DBuf<int2> crng(E, s);
   AML_LAUNCH("k_close_range", s,
-             k_close_range<<<grid_for(E, 256), 256, 0, s>>>(gv, delta, crng.p));
+             k_close_range<<<grid_for(E, 256), 256, 0, s>>>(gv, delta, crng.p, nullptr));
   DBuf<int32_t> items(E, s), w2(E, s), nb(4, s);
   cyc_items(g, gv, delta, crng.p, items.p, nb.p, w2.p, s);
   int32_t n_items = 0;

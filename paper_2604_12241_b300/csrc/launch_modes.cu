@@ -181,6 +181,18 @@ aml_status aml_graph_set_count_limit(aml_graph* g, uint32_t limit) {
   return AML_OK;
 }
 
+aml_status aml_graph_set_wait_limit(aml_graph* g, int64_t cycles) {
+  if (!g || cycles < 0) {
+    set_error("aml_graph_set_wait_limit: NULL graph or a negative limit");
+    return AML_EINVAL;
+  }
+  if (g->wait_limit != cycles) {
+    g->wait_limit = cycles;
+    drop_captured_mines(g);  // their launches hold the old bound
+  }
+  return AML_OK;
+}
+
 aml_status aml_autotune(aml_graph* g, const aml_pattern_set* ps, int32_t repeats, void* stream,
                         aml_tuning* best, float* best_ms) {
   try {

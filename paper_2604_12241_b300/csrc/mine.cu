@@ -118,13 +118,12 @@ __device__ __forceinline__ int32_t legs_into(const GraphView& g, int32_t b, int3
 }
 
 // slot bound of the legs of a that can start a cycle: its window slots that
-// precede the latest edge of its closing range (q0 when that range is empty)
-__device__ __forceinline__ int32_t cycle_bound(const GraphView& g, const int2* crng, int32_t a,
-                                               int32_t q0, int32_t q1) {
-  const int2 cr = crng[a];
+// precede the latest edge cl = (t, id) of its closing range (q0 when that
+// range is empty)
+__device__ __forceinline__ int32_t cycle_bound(const GraphView& g, int2 cr, int2 cl, int32_t q0,
+                                               int32_t q1) {
   if (cr.x >= cr.y) return q0;
-  const int32_t t_cl = __ldg(g.it + cr.y - 1), id_cl = __ldg(g.ieid + cr.y - 1);
-  return after_edge(g.ot, g.oeid, q0, q1, t_cl, id_cl - 1);  // first slot not before it
+  return after_edge(g.ot, g.oeid, q0, q1, cl.x, cl.y - 1);  // first slot not before it
 }
 
 // L[a]: legs from a.  With crng: L2[a] = those that can start a cycle
@@ -138,6 +137,7 @@ template <int NS>
 __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
                                                    int32_t* __restrict__ L,
                                                    const int2* __restrict__ crng,
+                                                   const int2* __restrict__ ccl,
                                                    int32_t* __restrict__ L2,
                                                    int32_t* __restrict__ L_new,
                                                    int2* __restrict__ qwin,
@@ -203,14 +203,15 @@ __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
     L_new[a] = (q1 - qn) - back;
   }
   if (!L2) return;
-  const int32_t qc = cycle_bound(g, crng, a, q0, q1);
+  const int2 cr = crng[a];
+  const int2 cl = ccl ? ccl[a]
+                      : (cr.x < cr.y ? make_int2(__ldg(g.it + cr.y - 1), __ldg(g.ieid + cr.y - 1))
+                                     : make_int2(0, 0));
+  const int32_t qc = cycle_bound(g, cr, cl, q0, q1);
   qcb[a] = qc;
   int32_t back = 0;
-  if (qc > q0 && b1 > b0) {  // returns h -> src(a) among the slots [q0, qc)
-    const int2 cr = crng[a];
-    back = after_edge(g.ont, g.oneid, b0, b1, __ldg(g.it + cr.y - 1),
-                      __ldg(g.ieid + cr.y - 1) - 1) - b0;
-  }
+  if (qc > q0 && b1 > b0)  // returns h -> src(a) among the slots [q0, qc)
+    back = after_edge(g.ont, g.oneid, b0, b1, cl.x, cl.y - 1) - b0;
   L2[a] = (qc - q0) - back;
 }
 
@@ -1112,9 +1113,13 @@ __global__ void __launch_bounds__(SG_BIG_BLOCK, 1) k_sg_bucket_big(const LegRec*
 //     it is short, two binary searches in u0's (nbr, t, id) in-list otherwise
 //     (the degree-ordered intersection of Sec. 6).
 
-// B1 of every edge a = u0 -> u1: slots of in(u0) after a with t <= t_a + delta
+// B1 of every edge a = u0 -> u1: slots of in(u0) after a with t <= t_a + delta;
+// with last, also (t, id) of B1's latest edge (any value when B1 is empty),
+// so that a path reads its anchor's closing bound in the same round of
+// loads as the range instead of after it
 __global__ void __launch_bounds__(512) k_close_range(GraphView g, int32_t delta,
-                                                     int2* __restrict__ rng) {
+                                                     int2* __restrict__ rng,
+                                                     int2* __restrict__ last) {
   int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a64 >= g.E) return;
   int32_t a = (int32_t)a64;
@@ -1128,34 +1133,65 @@ __global__ void __launch_bounds__(512) k_close_range(GraphView g, int32_t delta,
     if (g.new_from > 0) r.x = after_edge(g.it, g.ieid, r.x, r.y, g.t_new, g.new_from - 1);
   }
   rng[a] = r;
+  if (last)
+    last[a] = r.x < r.y ? make_int2(__ldg(g.it + r.y - 1), __ldg(g.ieid + r.y - 1))
+                        : make_int2(INT32_MIN, -1);
 }
 
 
+// first i in [lo, hi) with t[i] > tmax, for ranges that are usually short:
+// the first eight slots are read at once (independent loads, one round of
+// latency), and only a range longer than that is bisected further
+__device__ __forceinline__ int32_t upper_t_short(const int32_t* __restrict__ t, int32_t lo,
+                                                 int32_t hi, int64_t tmax) {
+  const int32_t n = hi - lo;
+  int32_t c = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (k < n && (int64_t)__ldg(t + lo + k) <= tmax) ++c;  // sorted: a prefix
+  if (c < 8 || n <= 8) return lo + c;
+  return upper_t(t, lo + 8, hi, tmax);
+}
+
 // Rebuilds the path of frontier element i at level j (j edges):
-// edges[0..j-1] and nodes[0..j] (nodes[0] = u0 = src of the anchor); with
-// tp, also the latest time among edges[1..j-1] (the anchor's own time when
-// j = 1).
-__device__ __forceinline__ void cyc_path(const GraphView& g, const CycFrontier& F, int j,
-                                         int64_t i, int32_t* edges, int32_t* nodes,
-                                         int32_t* tp = nullptr) {
+// edges[0..j-1] and nodes[0..j] (nodes[0] = u0 = src of the anchor), and
+// *tl = the time of its last edge (read from the slot beside its id, so it
+// costs no extra round of loads); with tp, also the latest time among
+// edges[1..j-1] (the anchor's own time when j = 1).
+// The level J and the base level (2: legs; 1: anchors, window cycles) are
+// compile-time constants, so the walk unrolls and the path stays in
+// registers.
+template <int J, int BASE>
+__device__ __forceinline__ void cyc_path(const GraphView& g, const CycFrontier& F, int64_t i,
+                                         int32_t (&edges)[J], int32_t (&nodes)[J + 1],
+                                         int32_t* tl, int32_t* tp = nullptr) {
   int64_t idx = i;
   int32_t t_late = INT32_MIN;
-  for (int lev = j; lev > F.base; --lev) {
+#pragma unroll
+  for (int lev = J; lev > BASE; --lev) {
     const int32_t q = F.slot[lev][idx];
     edges[lev - 1] = __ldg(g.oeid + q);
     nodes[lev] = __ldg(g.onbr + q);
-    if (tp) t_late = max(t_late, __ldg(g.ot + q));
+    if (tp || lev == J) {
+      const int32_t tq = __ldg(g.ot + q);
+      t_late = max(t_late, tq);
+      if (lev == J) *tl = tq;
+    }
     idx = F.par[lev][idx];
   }
   edges[0] = F.la[idx];
   nodes[0] = g.src[edges[0]];
   nodes[1] = g.dst[edges[0]];
-  if (F.base == 2) {
+  if constexpr (BASE == 2) {
     edges[1] = F.lb[idx];
     nodes[2] = g.dst[edges[1]];
-    if (tp) t_late = max(t_late, g.ts[edges[1]]);
+    const int32_t tb = g.ts[edges[1]];
+    t_late = max(t_late, tb);
+    if (J == 2) *tl = tb;
+  } else if (J == 1) {
+    *tl = g.ts[edges[0]];
   }
-  if (tp) *tp = j == 1 ? g.ts[edges[0]] : t_late;
+  if (tp) *tp = J == 1 ? g.ts[edges[0]] : t_late;
 }
 
 // One level of the cycle search.  Element i of level j is a path of j
@@ -1167,34 +1203,56 @@ __device__ __forceinline__ void cyc_path(const GraphView& g, const CycFrontier& 
 // the frontier starts at level 1 (the anchors); a cycle closes through any
 // edge of B1, and a smaller window keeps it only when the path's latest edge
 // also lies inside it.
-template <int NS, bool WIN>
-__global__ void __launch_bounds__(512, 4) k_cyc_level(GraphView g, int32_t delta, int K, int j,
-                                                   CycFrontier F, int64_t n,
-                                                   const int2* __restrict__ close_rng,
-                                                   CycleSlots slots,
-                                                   unsigned long long* __restrict__ acc,
-                                                   int32_t* __restrict__ cnt,
-                                                   int32_t* __restrict__ q0_out,
-                                                   int32_t close_scan_max, SubWindows sub) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// With ccl (the closing ranges' latest edges) and qwin (the leg window of
+// every edge: its end node's out-slots after it, up to its time + delta),
+// the window of a path's children starts at qwin[last].x with no search,
+// and ends inside qwin[last] (the latest closing edge is at most delta after
+// the anchor, hence after the path's last edge); without them (window
+// cycles, or callers that keep neither) both bounds are searched.
+// Arguments of one level of the cycle search (see cyc_item).
+struct CycLevelArgs {
+  GraphView g;
+  int32_t delta;
+  int K;
+  const int2* close_rng;
+  const int2* ccl;
+  const int2* qwin;
+  CycleSlots slots;
+  unsigned long long* acc;
+  int32_t close_scan_max;
+};
+
+// One element i of level j: closes its cycles and returns the window
+// [*q0, *q0 + count) of its children's slots (count 0: none).
+template <int NS, bool WIN, int J>
+__device__ __forceinline__ int32_t cyc_item(const CycLevelArgs& A, const CycFrontier& F,
+                                            const SubWindows& sub, int64_t i, int32_t* q0_out) {
+  constexpr int j = J;
+  const GraphView& g = A.g;
+  const int32_t delta = A.delta;
+  const int K = A.K;
   const bool has_next = j + 1 <= K - 1;
-  if (has_next) cnt[i] = 0;
-  int32_t edges[MAX_CYCLE];
-  int32_t nodes[MAX_CYCLE + 1];
-  int32_t tp = 0;
-  cyc_path(g, F, j, i, edges, nodes, WIN ? &tp : nullptr);
-  const int2 cr = close_rng[edges[0]];
-  if (cr.x >= cr.y) return;  // e1 starts no cycle
-  const int32_t t_cl = __ldg(g.it + cr.y - 1), id_cl = __ldg(g.ieid + cr.y - 1);
-  const int32_t last = edges[j - 1], tl = g.ts[last];
-  if (!WIN && !before(tl, last, t_cl, id_cl)) return;  // nothing can close after it
+  int32_t edges[J];
+  int32_t nodes[J + 1];
+  int32_t tp = 0, tl = 0;
+  cyc_path<J, WIN ? 1 : 2>(g, F, i, edges, nodes, &tl, WIN ? &tp : nullptr);
+  const int2 cr = A.close_rng[edges[0]];
+  int2 cl = A.ccl ? A.ccl[edges[0]] : make_int2(0, 0);
+  if (cr.x >= cr.y) return 0;  // e1 starts no cycle
+  if (!A.ccl) cl = make_int2(__ldg(g.it + cr.y - 1), __ldg(g.ieid + cr.y - 1));
+  const int32_t t_cl = cl.x, id_cl = cl.y;
+  const int32_t last = edges[j - 1];
+  if (!WIN && !before(tl, last, t_cl, id_cl)) return 0;  // nothing can close after it
   const int32_t u0 = nodes[0], w = nodes[j];
   if (j >= (WIN ? 2 : 3)) {  // the hop into w must reach a new node
-    if (w == u0) return;
+    if (w == u0) return 0;
+#pragma unroll
     for (int m = 1; m < j; ++m)
-      if (nodes[m] == w) return;
+      if (nodes[m] == w) return 0;
   }
+  const CycleSlots& slots = A.slots;
+  unsigned long long* acc = A.acc;
+  const int32_t close_scan_max = A.close_scan_max;
   const int32_t e1 = edges[0], t1 = g.ts[e1];
   // cycles of length j+1: edges w -> u0 in B1 (after `last` unless WIN), for
   // this window and every smaller one whose delta the cycle keeps
@@ -1249,18 +1307,270 @@ __global__ void __launch_bounds__(512, 4) k_cyc_level(GraphView g, int32_t delta
       }
 #pragma unroll
       for (int t = 0; t < NT; ++t)
-        if (c[t])
+        if (c[t]) {
+#pragma unroll
           for (int m = 0; m < j; ++m) atomicAdd(col[t] + edges[m], c[t]);
+        }
     }
   }
-  if (has_next) {
+  if (!has_next) return 0;
+  int32_t q0, q1;
+  if (!WIN && A.qwin) {
+    const int2 lw = A.qwin[last];
+    q0 = lw.x;
+    q1 = upper_t_short(g.ot, lw.x, lw.y, t_cl);
+  } else {
     const int32_t ws = g.optr[w], we = g.optr[w + 1];
-    int32_t q0, q1;
     if (WIN) after_edge_upto(g.ot, g.oeid, ws, we, t1, e1, (int64_t)t1 + delta, q0, q1);
     else after_edge_upto(g.ot, g.oeid, ws, we, tl, last, t_cl, q0, q1);
-    cnt[i] = q1 - q0;
-    q0_out[i] = q0;
   }
+  *q0_out = q0;
+  return q1 - q0;
+}
+
+template <int NS, bool WIN, int J>
+__global__ void __launch_bounds__(512, 4) k_cyc_level(CycLevelArgs A, CycFrontier F, int64_t n,
+                                                   int32_t* __restrict__ cnt,
+                                                   int32_t* __restrict__ q0_out,
+                                                   SubWindows sub) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t q0 = 0;
+  const int32_t c = cyc_item<NS, WIN, J>(A, F, sub, i, &q0);
+  if (J + 1 <= A.K - 1) {
+    cnt[i] = c;
+    if (c) q0_out[i] = q0;
+  }
+}
+
+// calls f(std::integral_constant<int, j>) for a level j in [1, MAX_CYCLE - 1]
+template <typename Fn>
+__host__ __device__ __forceinline__ void level_dispatch(int j, Fn&& f) {
+  switch (j) {
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    default: f(std::integral_constant<int, 7>{}); break;
+  }
+}
+
+template <typename F>
+static void nsub_dispatch(int n, F&& f) {
+  if (n <= 0)
+    f(std::integral_constant<int, 0>{});
+  else if (n == 1)
+    f(std::integral_constant<int, 1>{});
+  else if (n == 2)
+    f(std::integral_constant<int, 2>{});
+  else
+    f(std::integral_constant<int, MAX_SUB>{});
+}
+
+// ------------------------------------------- fused persistent cycle search
+//
+// Every level of the search above in one cooperative launch (AML_MINE_FUSED):
+// the blocks stay resident and run, per level j, (1) the elements of their
+// own contiguous chunk of level j (cyc_item), (2) after a grid-wide barrier,
+// the prefix of their chunk's child count from all blocks' sums, and (3) the
+// children of their chunk at their final positions, then a second barrier
+// before level j+1 reads them.  It replaces per level the separate level,
+// scan and emission launches and the count/offset arrays between them.  Each
+// barrier wait is bounded by P.wait_limit SM cycles: a wait that runs out
+// sets ERR_TIMEOUT in the graph's error word and the block returns (the
+// others then run out at their next barrier), so a stalled launch ends with
+// an error status instead of holding the GPU.  A cooperative launch keeps
+// every block resident, so in normal operation no wait runs out.
+
+constexpr int FUSED_BLOCK = 512;
+
+// Sense-reversing grid barrier: the last block to arrive resets the count
+// and advances the generation the others wait on.  False if the wait ran out.
+__device__ bool grid_wait(GridBarrier* bar, long long limit, uint32_t* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* gen = &bar->gen;
+    const unsigned int g0 = *gen;
+    __threadfence();
+    if (atomicAdd(&bar->count, 1u) + 1u == gridDim.x) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g0) {
+        if (clock64() - t0 > limit) {
+          atomicOr(err, ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// sum over the block (every thread gets it)
+__device__ __forceinline__ long long fused_block_sum(long long v, long long* s_w) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) s_w[warp] = v;
+  __syncthreads();
+  long long t = 0;
+  for (int w = 0; w < FUSED_BLOCK / 32; ++w) t += s_w[w];
+  return t;
+}
+
+// exclusive prefix over the block in thread order; *total = the block's sum
+__device__ __forceinline__ long long fused_block_excl(long long v, long long* s_w,
+                                                      long long* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  long long before = 0, t = 0;
+  for (int w = 0; w < FUSED_BLOCK / 32; ++w) {
+    if (w < warp) before += s_w[w];
+    t += s_w[w];
+  }
+  *total = t;
+  return before + x - v;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(FUSED_BLOCK, 3) k_cyc_fused(CycLevelArgs A, FusedCycles P,
+                                                            SubWindows sub) {
+  __shared__ long long s_w[FUSED_BLOCK / 32];
+  const int lane = threadIdx.x & 31;
+  const unsigned G = gridDim.x;
+  CycFrontier F = P.F;
+  int64_t n = P.n2;
+  for (int j = 2; j <= A.K - 1 && n > 0; ++j) {
+    const bool has_next = j + 1 <= A.K - 1;
+    const int64_t C = (n + G - 1) / G;
+    const int64_t c0 = min(n, (int64_t)blockIdx.x * C), c1 = min(n, c0 + C);
+    long long mine = 0;
+    level_dispatch(j, [&](auto jc) {
+      constexpr int JJ = decltype(jc)::value < 2 ? 2 : decltype(jc)::value;
+      for (int64_t i = c0 + threadIdx.x; i < c1; i += FUSED_BLOCK) {
+        int32_t q0 = 0;
+        const int32_t c = cyc_item<NS, false, JJ>(A, F, sub, i, &q0);
+        if (has_next) {
+          P.cnt[i] = c;
+          P.q0[i] = q0;
+          mine += c;
+        }
+      }
+    });
+    if (!has_next) break;
+    mine = fused_block_sum(mine, s_w);
+    if (threadIdx.x == 0) P.bsum[blockIdx.x] = mine;
+    if (!grid_wait(P.bar, P.wait_limit, P.err)) return;
+    // this chunk's first child position and the level's total
+    long long before = 0, total = 0;
+    for (unsigned b = threadIdx.x; b < G; b += FUSED_BLOCK) {
+      const long long v = __ldcg(P.bsum + b);
+      total += v;
+      if (b < blockIdx.x) before += v;
+    }
+    before = fused_block_sum(before, s_w);
+    total = fused_block_sum(total, s_w);
+    if (total > P.cap[j + 1]) {  // cannot happen for the sizes the capacity came from
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(P.err, ERR_OVERFLOW);
+      return;  // every block sees the same total and leaves here
+    }
+    int32_t* par = P.par[j + 1];
+    int32_t* slot = P.slot[j + 1];
+    long long run = before;
+    for (int64_t t0 = c0; t0 < c1; t0 += FUSED_BLOCK) {
+      const int64_t i = t0 + threadIdx.x;
+      const int32_t c = i < c1 ? __ldcg(P.cnt + i) : 0;
+      const int32_t b = c ? __ldcg(P.q0 + i) : 0;
+      long long tile = 0;
+      const long long o = run + fused_block_excl(c, s_w, &tile);
+      const bool own = c <= P.own_max;  // short child lists by the lane, long ones by the warp
+      if (own)
+        for (int32_t k = 0; k < c; ++k) {
+          par[o + k] = (int32_t)i;
+          slot[o + k] = b + k;
+        }
+      unsigned heavy = __ballot_sync(0xffffffffu, !own);
+      while (heavy) {
+        const int src = __ffs(heavy) - 1;
+        heavy &= heavy - 1;
+        const int64_t hi = __shfl_sync(0xffffffffu, i, src);
+        const int32_t hc = __shfl_sync(0xffffffffu, c, src);
+        const long long ho = __shfl_sync(0xffffffffu, o, src);
+        const int32_t hb = __shfl_sync(0xffffffffu, b, src);
+        for (int32_t k = lane; k < hc; k += 32) {
+          par[ho + k] = (int32_t)hi;
+          slot[ho + k] = hb + k;
+        }
+      }
+      run += tile;
+    }
+    if (!grid_wait(P.bar, P.wait_limit, P.err)) return;
+    F.par[j + 1] = par;
+    F.slot[j + 1] = slot;
+    n = total;
+  }
+}
+
+template <int NS>
+static void fused_smem_blocks(int* per_sm) {
+  AML_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_cyc_fused<NS>, FUSED_BLOCK,
+                                                         0));
+}
+
+int fused_cycle_grid(int n_sub) {
+  static int cached[64][MAX_SUB + 1] = {};
+  int dev = 0;
+  AML_CUDA(cudaGetDevice(&dev));
+  int per_sm = 0;
+  const int key = n_sub <= 0 ? 0 : n_sub == 1 ? 1 : n_sub == 2 ? 2 : MAX_SUB;
+  if (dev < 64 && cached[dev][key]) return cached[dev][key];
+  nsub_dispatch(n_sub, [&](auto ns) { fused_smem_blocks<decltype(ns)::value>(&per_sm); });
+  AML_REQUIRE(per_sm >= 1, AML_EUNSUPPORTED, "the fused cycle kernel cannot be resident");
+  const int grid = per_sm * sm_count();
+  if (dev < 64) cached[dev][key] = grid;
+  return grid;
+}
+
+void launch_cyc_fused(int grid, cudaStream_t s, const GraphView& g, int32_t delta, int K,
+                      const int2* close_rng, const int2* ccl, const int2* qwin,
+                      const CycleSlots& slots, unsigned long long* acc, int32_t close_scan_max,
+                      const FusedCycles& P, const SubWindows& sub) {
+  const CycLevelArgs A{g, delta, K, close_rng, ccl, qwin, slots, acc, close_scan_max};
+  nsub_dispatch(sub.n, [&](auto ns) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(FUSED_BLOCK);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    AML_LAUNCH("k_cyc_fused", s,
+               AML_CUDA(cudaLaunchKernelEx(&cfg, k_cyc_fused<decltype(ns)::value>, A, P, sub)));
+  });
 }
 
 // flag[a] = 1 when edge a's closing range is not empty (it anchors cycles)
@@ -1412,24 +1722,13 @@ __global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
 // The kernels that count sub-windows are compiled for 0, 1, 2 and MAX_SUB
 // of them, so the per-window counters live in registers.
 
-template <typename F>
-static void nsub_dispatch(int n, F&& f) {
-  if (n <= 0)
-    f(std::integral_constant<int, 0>{});
-  else if (n == 1)
-    f(std::integral_constant<int, 1>{});
-  else if (n == 2)
-    f(std::integral_constant<int, 2>{});
-  else
-    f(std::integral_constant<int, MAX_SUB>{});
-}
 
 void launch_leg_count(unsigned grid, int block, cudaStream_t s, const GraphView& g, int32_t delta,
-                      int32_t* L, const int2* crng, int32_t* L2, int32_t* L_new, int2* qwin,
-                      int32_t* qcb, const SubWindows& sub, const ZeroSink& Z) {
+                      int32_t* L, const int2* crng, const int2* ccl, int32_t* L2, int32_t* L_new,
+                      int2* qwin, int32_t* qcb, const SubWindows& sub, const ZeroSink& Z) {
   nsub_dispatch(sub.n, [&](auto ns) {
     AML_LAUNCH("k_leg_count", s,
-               k_leg_count<decltype(ns)::value><<<grid, block, 0, s>>>(g, delta, L, crng, L2,
+               k_leg_count<decltype(ns)::value><<<grid, block, 0, s>>>(g, delta, L, crng, ccl, L2,
                                                                       L_new, qwin, qcb, sub, Z));
   });
 }
@@ -1484,20 +1783,24 @@ void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
 
 void launch_cyc_level(unsigned grid, int block, cudaStream_t s, const GraphView& g,
                       int32_t delta, int K, int j, const CycFrontier& F, int64_t n,
-                      const int2* close_rng, const CycleSlots& slots, unsigned long long* acc,
-                      int32_t* cnt, int32_t* q0_out, int32_t close_scan_max,
-                      const SubWindows& sub, bool window_cycles) {
+                      const int2* close_rng, const int2* ccl, const int2* qwin,
+                      const CycleSlots& slots, unsigned long long* acc, int32_t* cnt,
+                      int32_t* q0_out, int32_t close_scan_max, const SubWindows& sub,
+                      bool window_cycles) {
+  const CycLevelArgs A{g, delta, K, close_rng, ccl, window_cycles ? nullptr : qwin, slots, acc,
+                       close_scan_max};
+  AML_REQUIRE(j >= (window_cycles ? 1 : 2) && j <= MAX_CYCLE - 1, AML_EINTERNAL,
+              "cycle level out of range");
   nsub_dispatch(sub.n, [&](auto ns) {
-    if (window_cycles)
-      AML_LAUNCH("k_cyc_level_win", s,
-                 k_cyc_level<decltype(ns)::value, true><<<grid, block, 0, s>>>(
-                     g, delta, K, j, F, n, close_rng, slots, acc, cnt, q0_out, close_scan_max,
-                     sub));
-    else
-      AML_LAUNCH("k_cyc_level", s,
-                 k_cyc_level<decltype(ns)::value, false><<<grid, block, 0, s>>>(
-                     g, delta, K, j, F, n, close_rng, slots, acc, cnt, q0_out, close_scan_max,
-                     sub));
+    level_dispatch(j, [&](auto jc) {
+      constexpr int NSV = decltype(ns)::value, J = decltype(jc)::value;
+      if (window_cycles)
+        AML_LAUNCH("k_cyc_level_win", s,
+                   k_cyc_level<NSV, true, J><<<grid, block, 0, s>>>(A, F, n, cnt, q0_out, sub));
+      else if constexpr (J >= 2)
+        AML_LAUNCH("k_cyc_level", s,
+                   k_cyc_level<NSV, false, J><<<grid, block, 0, s>>>(A, F, n, cnt, q0_out, sub));
+    });
   });
 }
 

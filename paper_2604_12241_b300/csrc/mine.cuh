@@ -159,7 +159,7 @@ __global__ void k_sg_new_keys(const LegRec* rec, int64_t n, int32_t new_from, Ke
 __global__ void k_sg_count_new(const LegRec* rec, int64_t n, int32_t new_from,
                                unsigned long long* count);
 __global__ void k_mark_nodes(const int32_t* node_of, int64_t from, int64_t E, uint32_t* mask);
-__global__ void k_close_range(GraphView g, int32_t delta, int2* rng);
+__global__ void k_close_range(GraphView g, int32_t delta, int2* rng, int2* last);
 __global__ void k_anchor_flags(const int2* crng, int64_t E, int32_t* flag);
 __global__ void k_compact_ids(const int32_t* flag, const int32_t* off, int64_t E, int32_t* items);
 // Buffers k_leg_count zeroes per edge: n_acc accumulator columns of E
@@ -172,8 +172,8 @@ struct ZeroSink {
 // Launchers of the kernels that also count sub-windows (instantiated for
 // the number of them in sub).
 void launch_leg_count(unsigned grid, int block, cudaStream_t s, const GraphView& g, int32_t delta,
-                      int32_t* L, const int2* crng, int32_t* L2, int32_t* L_new, int2* qwin,
-                      int32_t* qcb, const SubWindows& sub, const ZeroSink& Z);
+                      int32_t* L, const int2* crng, const int2* ccl, int32_t* L2, int32_t* L_new,
+                      int2* qwin, int32_t* qcb, const SubWindows& sub, const ZeroSink& Z);
 // Delta counting (new_from > 0): the legs a new instance can use (mine.cu);
 // first_new = each out-list's first new slot (k_first_new); mptr/mslot =
 // each node's out-list slots whose counterparty is a batch destination
@@ -199,13 +199,45 @@ void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
                        const uint32_t* bend, int32_t delta, const int32_t* dst, const int32_t* ts,
                        unsigned long long* acc, int32_t new_from, uint32_t* overflow,
                        const SubWindows& sub);
+// ccl, qwin: the closing ranges' latest edges and the leg windows of the
+// same window's leg pass (either null: the bounds are searched instead)
 void launch_cyc_level(unsigned grid, int block, cudaStream_t s, const GraphView& g,
                       int32_t delta, int K, int j, const CycFrontier& F, int64_t n,
-                      const int2* close_rng, const CycleSlots& slots, unsigned long long* acc,
-                      int32_t* cnt, int32_t* q0_out, int32_t close_scan_max,
-                      const SubWindows& sub, bool window_cycles = false);
+                      const int2* close_rng, const int2* ccl, const int2* qwin,
+                      const CycleSlots& slots, unsigned long long* acc, int32_t* cnt,
+                      int32_t* q0_out, int32_t close_scan_max, const SubWindows& sub,
+                      bool window_cycles = false);
 __global__ void k_cyc_emit(int64_t n, const int32_t* cnt, const int32_t* q0, const int64_t* off,
                            int32_t* par, int32_t* slot, int32_t own_max);
+
+// Grid-wide barrier state of a cooperative launch (zeroed before it).
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+// The fused cycle search: every level in one cooperative launch.  par/slot
+// of levels 3..K-1 hold cap[j] elements; cnt/q0 hold the largest level that
+// has children; bsum one value per block.
+struct FusedCycles {
+  CycFrontier F;  // base level (la, lb)
+  int64_t n2;
+  int64_t cap[MAX_CYCLE + 1];
+  int32_t* par[MAX_CYCLE + 1];
+  int32_t* slot[MAX_CYCLE + 1];
+  int32_t* cnt;
+  int32_t* q0;
+  long long* bsum;
+  GridBarrier* bar;
+  uint32_t* err;
+  long long wait_limit;  // SM clock cycles a barrier wait may take
+  int32_t own_max;       // child lists up to this long are written by one lane
+};
+// blocks of the fused launch on this device (all resident at once)
+int fused_cycle_grid(int n_sub);
+void launch_cyc_fused(int grid, cudaStream_t s, const GraphView& g, int32_t delta, int K,
+                      const int2* close_rng, const int2* ccl, const int2* qwin,
+                      const CycleSlots& slots, unsigned long long* acc, int32_t close_scan_max,
+                      const FusedCycles& P, const SubWindows& sub);
 __global__ void k_assemble(AssembleParams P);
 
 // Host pipeline: enqueue a full mine of `ps` on `g` into device `counts`.
@@ -227,8 +259,9 @@ void run_program(const GraphView& gv, const float* amount, const Prog& p,
 
 void level_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K,
                         const CycleSlots& slots, const SubWindows& sub,
-                        unsigned long long* acc, const int2* crng, const int32_t* la,
-                        const int32_t* lb, int64_t* front_cache, cudaStream_t s);
+                        unsigned long long* acc, const int2* crng, const int2* ccl,
+                        const int2* qwin, const int32_t* la, const int32_t* lb,
+                        int64_t* front_cache, cudaStream_t s);
 // Cycle search of one window split by estimated anchor cost (cost.cu): the
 // heaviest anchors' legs level by level on s, the other anchors by the
 // persistent kernel on `side` (forked from and joined back to s).

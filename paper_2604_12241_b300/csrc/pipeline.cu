@@ -68,7 +68,8 @@ void window_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K
   const int B = tn.block;
   LegCache& lc = g->legs[delta];
   DBuf<int2> crng((size_t)E, s);
-  AML_LAUNCH("k_close_range", s, k_close_range<<<grid_for(E, B), B, 0, s>>>(gv, delta, crng.p));
+  AML_LAUNCH("k_close_range", s,
+             k_close_range<<<grid_for(E, B), B, 0, s>>>(gv, delta, crng.p, nullptr));
   DBuf<int32_t> flag((size_t)E + 1, s), off((size_t)E + 1, s);
   AML_LAUNCH("k_anchor_flags", s,
              k_anchor_flags<<<grid_for(E, 256), 256, 0, s>>>(crng.p, E, flag.p));
@@ -94,8 +95,8 @@ void window_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K
   for (int j = 1; j <= K - 1 && n > 0; ++j) {
     const bool has_next = j + 1 <= K - 1;
     DBuf<int32_t> cnt(has_next ? n + 1 : 0, s), q0(has_next ? n : 0, s);
-    launch_cyc_level(grid_for(n, B), B, s, gv, delta, K, j, F, n, crng.p, slots, acc, cnt.p,
-                     q0.p, tn.close_scan_max, sw, true);
+    launch_cyc_level(grid_for(n, B), B, s, gv, delta, K, j, F, n, crng.p, nullptr, nullptr,
+                     slots, acc, cnt.p, q0.p, tn.close_scan_max, sw, true);
     if (!has_next) break;
     DBuf<int64_t> foff(n + 1, s);
     AML_CUDA(cudaMemsetAsync(cnt.p + n, 0, sizeof(int32_t), s));
@@ -128,8 +129,9 @@ void window_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K
 // with one wait per level).
 void level_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K,
                         const CycleSlots& slots, const SubWindows& sub,
-                        unsigned long long* acc, const int2* crng, const int32_t* la,
-                        const int32_t* lb, int64_t* front_cache, cudaStream_t s) {
+                        unsigned long long* acc, const int2* crng, const int2* ccl,
+                        const int2* qwin, const int32_t* la, const int32_t* lb,
+                        int64_t* front_cache, cudaStream_t s) {
   const Tuning tn = g->tune;
   const int B = tn.block;
   CycFrontier F;
@@ -143,8 +145,8 @@ void level_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K,
   for (int j = 2; j <= K - 1 && n > 0; ++j) {
     const bool has_next = j + 1 <= K - 1;
     DBuf<int32_t> cnt(has_next ? n + 1 : 0, s), q0(has_next ? n : 0, s);
-    launch_cyc_level(grid_for(n, B), B, s, gv, delta, K, j, F, n, crng, slots, acc, cnt.p,
-                     q0.p, tn.close_scan_max, sub);
+    launch_cyc_level(grid_for(n, B), B, s, gv, delta, K, j, F, n, crng, ccl, qwin, slots, acc,
+                     cnt.p, q0.p, tn.close_scan_max, sub);
     if (!has_next) break;
     DBuf<int64_t> foff(n + 1, s);
     AML_CUDA(cudaMemsetAsync(cnt.p + n, 0, sizeof(int32_t), s));
@@ -168,6 +170,54 @@ void level_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K,
     F.slot[j + 1] = slot;
     n = nn;
   }
+}
+
+// The same search in one cooperative launch (k_cyc_fused), once the sizes of
+// every level are known (a plain search learns them first).
+void level_cycle_search_fused(aml_graph* g, const GraphView& gv, int32_t delta, int K,
+                              const CycleSlots& slots, const SubWindows& sub,
+                              unsigned long long* acc, const int2* crng, const int2* ccl,
+                              const int2* qwin, const int32_t* la, const int32_t* lb,
+                              int64_t* front_cache, cudaStream_t s) {
+  for (int j = 3; j <= K - 1; ++j)
+    if (front_cache[j] < 0) {
+      level_cycle_search(g, gv, delta, K, slots, sub, acc, crng, ccl, qwin, la, lb, front_cache,
+                         s);
+      return;
+    }
+  const int64_t n2 = front_cache[2];
+  if (n2 <= 0 || K < 3) return;
+  FusedCycles P;
+  std::memset(&P, 0, sizeof(P));
+  P.F.base = 2;
+  P.F.la = la;
+  P.F.lb = lb;
+  P.n2 = n2;
+  std::vector<DBuf<int32_t>> front;
+  front.reserve(2 * MAX_CYCLE);
+  int64_t widest = 1;  // the largest level with children
+  for (int j = 2; j <= K - 2; ++j) widest = std::max(widest, front_cache[j]);
+  for (int j = 3; j <= K - 1; ++j) {
+    P.cap[j] = front_cache[j];
+    front.emplace_back((size_t)std::max<int64_t>(front_cache[j], 1), s);
+    P.par[j] = front.back().p;
+    front.emplace_back((size_t)std::max<int64_t>(front_cache[j], 1), s);
+    P.slot[j] = front.back().p;
+  }
+  const int grid = fused_cycle_grid(sub.n);
+  DBuf<int32_t> cnt((size_t)widest, s), q0((size_t)widest, s);
+  DBuf<long long> bsum((size_t)grid, s);
+  DBuf<GridBarrier> bar(1, s);
+  AML_CUDA(cudaMemsetAsync(bar.p, 0, sizeof(GridBarrier), s));
+  P.cnt = cnt.p;
+  P.q0 = q0.p;
+  P.bsum = bsum.p;
+  P.bar = bar.p;
+  P.err = g->err;
+  P.wait_limit = g->wait_limit;
+  P.own_max = g->tune.own_max;
+  launch_cyc_fused(grid, s, gv, delta, K, crng, ccl, qwin, slots, acc, g->tune.close_scan_max, P,
+                   sub);
 }
 
 void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
@@ -366,13 +416,14 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     // 2. legs (and, for the level-by-level cycle search, the legs that can
     // start a cycle: those of anchors with a closing range, before its end)
     const bool level_cycles = wp.K >= 3;
-    DBuf<int2> crng;
+    DBuf<int2> crng, ccl;
     DBuf<int32_t> L2;
     DBuf<int64_t> off2;
     if (level_cycles) {
       crng = DBuf<int2>((size_t)E, s);
+      ccl = DBuf<int2>((size_t)E, s);
       AML_LAUNCH("k_close_range", s,
-                 k_close_range<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, crng.p));
+                 k_close_range<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, crng.p, ccl.p));
       L2 = DBuf<int32_t>((size_t)E + 1, s);
       off2 = DBuf<int64_t>((size_t)E + 1, s);
     }
@@ -394,7 +445,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     ZeroSink Z{acc_zeroed ? nullptr : acc.p, acc_zeroed ? 0 : n_acc, gs_in};
     acc_zeroed = true;
     launch_leg_count(grid_for(E, B), B, s, gv, wp.delta, L.p, level_cycles ? crng.p : nullptr,
-                     level_cycles ? L2.p : nullptr, L_new, qwin.p, qcb.p, sub, Z);
+                     level_cycles ? ccl.p : nullptr, level_cycles ? L2.p : nullptr, L_new, qwin.p,
+                     qcb.p, sub, Z);
     AML_CUDA(cudaMemsetAsync(L.p + E, 0, sizeof(int32_t), s));
     keep64.emplace_back((size_t)(E + 1), s);
     int64_t* off = keep64.back().p;
@@ -568,9 +620,12 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     if (wp.K >= 3 && persistent) {
       cycles_hybrid(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, crng.p, la.p, lb.p,
                     (mode & AML_MINE_LEARNED) != 0, s, branches ? g->side[2] : s);
+    } else if (level_cycles && (mode & AML_MINE_FUSED)) {  // ... or all levels in one launch
+      level_cycle_search_fused(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, crng.p, ccl.p, qwin.p,
+                               la.p, lb.p, lc.n_front, s);
     } else if (level_cycles) {  // ... or level by level from the legs
-      level_cycle_search(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, crng.p, la.p, lb.p,
-                         lc.n_front, s);
+      level_cycle_search(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, crng.p, ccl.p, qwin.p, la.p,
+                         lb.p, lc.n_front, s);
     }
     // the window's buffers (rec, hist, ...) are freed on s after this join
     if (sg_branch) branch_wait(g->branch_ev[3], s_sg, s);
