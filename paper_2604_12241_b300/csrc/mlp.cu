@@ -30,13 +30,15 @@ __device__ __forceinline__ float bf16r(float x) {
 }
 
 // Per-sample forward/backward of a tile of samples into shared memory, then
-// the parameter gradients as dot products over the tile's samples.
-// grad must be zeroed; loss_sum accumulates the summed squared error.
+// the parameter gradients as dot products over the tile's samples.  Block b
+// takes tiles b, b + grid, ... and writes its partial sums to part[b] (the
+// MLP_NPARAM gradient entries, then its squared error); k_mlp_reduce adds
+// the blocks' partials in block order, so a gradient is the same bit for
+// bit on every run (no floating-point atomics).
 __global__ void __launch_bounds__(TR_THREADS) k_mlp_grad(const float* __restrict__ params,
                                                          const float* __restrict__ x,
                                                          const float* __restrict__ y, int64_t n,
-                                                         float scale, float* __restrict__ grad,
-                                                         float* __restrict__ loss_sum) {
+                                                         float scale, float* __restrict__ part) {
   extern __shared__ float sm[];
   float* w = sm;                              // bf16-rounded parameters [MLP_NPARAM]
   float* sx = w + MLP_NPARAM;                 // [TR_TILE][XS]
@@ -124,12 +126,31 @@ __global__ void __launch_bounds__(TR_THREADS) k_mlp_grad(const float* __restrict
     }
     __syncthreads();
   }
+  float* mine = part + (int64_t)blockIdx.x * (MLP_NPARAM + 1);
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     const int p = threadIdx.x + k * TR_THREADS;
-    if (p < MLP_NPARAM && acc[k] != 0.f) atomicAdd(grad + p, acc[k]);
+    if (p < MLP_NPARAM) mine[p] = acc[k];
   }
-  if (threadIdx.x < TR_TILE && my_loss != 0.f) atomicAdd(loss_sum, my_loss);
+  // the block's squared error, summed in thread order
+  sx[threadIdx.x] = threadIdx.x < TR_TILE ? my_loss : 0.f;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float l = 0.f;
+    for (int t = 0; t < TR_TILE; ++t) l += sx[t];
+    mine[MLP_NPARAM] = l;
+  }
+}
+
+// grad[p] = sum over blocks b (in order) of part[b][p]; loss likewise
+__global__ void k_mlp_reduce(const float* __restrict__ part, int blocks,
+                             float* __restrict__ grad, float* __restrict__ loss_sum) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > MLP_NPARAM) return;
+  float s = 0.f;
+  for (int b = 0; b < blocks; ++b) s += part[(int64_t)b * (MLP_NPARAM + 1) + p];
+  if (p < MLP_NPARAM) grad[p] = s;
+  else *loss_sum = s;
 }
 
 // Adam (Kingma & Ba) on the fp32 master parameters.
@@ -160,13 +181,15 @@ void mlp_grad(const float* params, const float* x, const float* y, int64_t n, fl
                                   (int)mlp_grad_smem()));
     if (dev < 64) attr[dev] = true;
   }
-  AML_CUDA(cudaMemsetAsync(grad, 0, MLP_NPARAM * sizeof(float), s));
-  AML_CUDA(cudaMemsetAsync(loss_sum, 0, sizeof(float), s));
   const int64_t tiles = (n + TR_TILE - 1) / TR_TILE;
   const unsigned blocks = (unsigned)std::min<int64_t>(std::max<int64_t>(tiles, 1), 296);
+  DBuf<float> part((size_t)blocks * (MLP_NPARAM + 1), s);
   AML_LAUNCH("k_mlp_grad", s,
-             k_mlp_grad<<<blocks, TR_THREADS, mlp_grad_smem(), s>>>(params, x, y, n, scale, grad,
-                                                                   loss_sum));
+             k_mlp_grad<<<blocks, TR_THREADS, mlp_grad_smem(), s>>>(params, x, y, n, scale,
+                                                                   part.p));
+  AML_LAUNCH("k_mlp_reduce", s,
+             k_mlp_reduce<<<grid_for(MLP_NPARAM + 1, 256), 256, 0, s>>>(part.p, (int)blocks, grad,
+                                                                        loss_sum));
 }
 
 void mlp_adam(float* p, const float* g, float* m, float* v, int n, int step, float lr, float b1,

@@ -45,6 +45,26 @@ def test_mlp_gradient_matches_fp64_reference():
         np.testing.assert_allclose(grad, want, rtol=0, atol=2e-4 * scale)
 
 
+def test_mlp_gradient_is_bitwise_reproducible():
+    """The blocks' partial gradients are added in a fixed order (no float
+    atomics), so the same inputs give the same bits on every call."""
+    rng = np.random.default_rng(11)
+    n = 100_000
+    p = _f32(R.random_params(rng))
+    x = _f32(rng.normal(0, 1, (n, R.IN)))
+    y = _f32(rng.normal(0, 1, n))
+    outs = []
+    for _ in range(3):
+        grad = np.zeros(R.NPARAM, np.float32)
+        loss = np.zeros(1, np.float32)
+        assert _lib.lib().aml_mlp_loss_grad(p.ctypes.data, x.ctypes.data, y.ctypes.data, n,
+                                            grad.ctypes.data, loss.ctypes.data) == 0
+        outs.append((grad.view(np.uint32).copy(), loss.view(np.uint32).copy()))
+    for g, l in outs[1:]:
+        np.testing.assert_array_equal(g, outs[0][0])
+        np.testing.assert_array_equal(l, outs[0][1])
+
+
 def test_adam_step_matches_reference():
     rng = np.random.default_rng(4)
     p = _f32(rng.normal(0, 1, R.NPARAM))
