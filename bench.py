@@ -181,10 +181,8 @@ def measured_peak():
 # full size, valid only for the kernel sources it was taken with:
 # KERNEL_DIGEST is the digest (kernel_digest()) of the files that define the
 # measured kernels.
-KERNEL_DIGEST = "c5d6358914ba8ac2"
-MEASURED_TRAFFIC = {"k_cyc_level": 267.0e6, "k_sg_bucket": 519.2e6, "k_leg_emit": 610.1e6,
-                    "k_sg_partition": 548.5e6, "k_fan_reduce": 230.5e6, "k_fan_scan": 314.4e6,
-                    "k_assemble": 1076.7e6, "k_leg_count": 698.2e6}
+KERNEL_DIGEST = "a5017b57799f61b3"
+MEASURED_TRAFFIC = {"k_cyc_level": 293.3e6, "k_sg_bucket": 521.6e6}
 
 
 TRAFFIC_SOURCES = ("aml_internal.cuh", "fan.cu", "mine.cu", "mine.cuh", "pipeline.cu", "prims.cu")
