@@ -228,3 +228,57 @@ def test_gather_scatter_n_brute_force():
             np.testing.assert_array_equal(got, want, err_msg=f"seed {seed}, delta {delta}")
             n_nonzero += int(want.any())
     assert n_nonzero >= 3
+
+
+def _brute_sg_sets(src, dst, ts, k, delta):
+    """Per edge, the k-intermediary scatter-gathers it belongs to, each
+    counted once as a set: k legs s -> m_i -> d (scatter before gather in
+    (t, id) order, s, d and the m_i distinct) with pairwise distinct
+    intermediaries and all 2k edges within delta.  Enumerated from the raw
+    edge list (no neighbour lists)."""
+    import itertools
+    E = len(src)
+    prec = lambda f, e: (int(ts[f]), f) < (int(ts[e]), e)
+    legs = [(a, b) for a in range(E) for b in range(E)
+            if src[a] != dst[a] and src[b] != dst[b] and dst[a] == src[b]
+            and src[a] != dst[b] and prec(a, b)]
+    out = np.zeros(E, dtype=np.uint64)
+    by_pair = {}
+    for a, b in legs:
+        by_pair.setdefault((int(src[a]), int(dst[b])), []).append((a, b))
+    for group in by_pair.values():
+        for combo in itertools.combinations(group, k):
+            mids = {int(dst[a]) for a, _ in combo}
+            if len(mids) != k:
+                continue
+            edges = [e for leg in combo for e in leg]
+            t = [int(ts[e]) for e in edges]
+            if max(t) - min(t) > delta:
+                continue
+            for e in edges:
+                out[e] += 1
+    return out
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_exact_size_scatter_gather_is_the_at_least_program_over_k_factorial(k):
+    """Exact-size bins: the k-intermediary scatter-gathers an edge belongs
+    to, each counted once (a set of k legs), equal the "at least k" program's
+    count (ordered k-tuples of legs) divided by k!, on small random graphs
+    with ties, parallel edges and self-loops (brute force over raw edges)."""
+    pat = P.scatter_gather_n(k, 0)
+    checked = 0
+    for seed in range(12):
+        rng = np.random.default_rng(4000 + seed)
+        n, E = 5, 24 + seed % 8
+        src = rng.integers(0, n, E).astype(np.int32)
+        dst = rng.integers(0, n, E).astype(np.int32)
+        ts = rng.integers(0, 7, E).astype(np.int32)
+        og = oracle.OracleGraph(src, dst, ts, n)
+        for delta in (2, 6):
+            got = og.program_count(_tuples(pat), pat.aggregate, delta, threads=1)
+            want = _brute_sg_sets(src, dst, ts, k, delta)
+            np.testing.assert_array_equal(got.astype(np.uint64),
+                                          want * np.uint64(math.factorial(k)))
+            checked += int((want > 0).sum())
+    assert checked > 20
