@@ -188,20 +188,21 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_reduce(const int32_t* __restr
   }
 }
 
+// edge e's row of df: the W (DEG, FAN) pairs and zero padding, 32 bytes in
+// two 16-byte stores (a whole sector, so no read-modify-write)
 template <int W>
 __device__ __forceinline__ void store_df(int2* __restrict__ df, int32_t e, const int2 (&v)[W]) {
-  int2* dst = df + (int64_t)e * W;
-  if constexpr (W % 2 == 0) {
+  static_assert(W <= DF_STRIDE, "window count");
+  int2 r[DF_STRIDE];
 #pragma unroll
-    for (int k = 0; k < W; k += 2)
-      reinterpret_cast<int4*>(dst)[k / 2] = make_int4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
-  } else {
-#pragma unroll
-    for (int k = 0; k < W; ++k) dst[k] = v[k];
-  }
+  for (int k = 0; k < DF_STRIDE; ++k) r[k] = k < W ? v[k] : make_int2(0, 0);
+  int4* dst = reinterpret_cast<int4*>(df + (int64_t)e * DF_STRIDE);
+  dst[0] = make_int4(r[0].x, r[0].y, r[1].x, r[1].y);
+  dst[1] = make_int4(r[2].x, r[2].y, r[3].x, r[3].y);
 }
 
-// df: [E][W] (DEG, FAN) pairs
+// df: [E][DF_STRIDE] (DEG, FAN) pairs in edge order, one whole 32-byte row
+// per edge
 template <int W>
 __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restrict__ rstart,
                                                         const int32_t* __restrict__ eid,
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restric
           const int32_t deg = deg_s[k * Ev + p];
           v[k] = make_int2(deg, deg - s_v[k][fpad(i)]);
         }
-        store_df<W>(df, eid[p], v);
+        store_df<W>(df, __ldg(eid + p), v);
       }
     }
     run = seg_combine(run, tile_total);

@@ -28,8 +28,8 @@ namespace aml {
 
 // Per slot p of one direction: DEG(p) = p - lb(p) + 1, lb(p) the start of
 // its trailing window, and, when FAN is wanted, the repeat delta above.
-// deg_s: DEG per slot; df: (DEG, 0) stored at the slot's edge id (the
-// DEG-only case: no FAN pass follows).  Each output may be null.
+// deg_s: DEG per slot; df: (DEG, 0) stored in the edge's 32-byte row of df
+// (the DEG-only case: no FAN pass follows).  Each output may be null.
 __global__ void __launch_bounds__(512) k_window_slots(const int32_t* __restrict__ rstart,
                                                       const int32_t* __restrict__ t,
                                                       const int32_t* __restrict__ eid,
@@ -47,7 +47,11 @@ __global__ void __launch_bounds__(512) k_window_slots(const int32_t* __restrict_
   const int32_t lbp = lower_t(t, rs, p + 1, (int64_t)tp - delta);
   const int32_t deg = p - lbp + 1;
   if (deg_s) deg_s[p] = deg;
-  if (df) df[__ldg(eid + p)] = make_int2(deg, 0);
+  if (df) {  // the whole 32-byte row: a full-sector store, no read-modify-write
+    int4* row = reinterpret_cast<int4*>(df + (int64_t)__ldg(eid + p) * DF_STRIDE);
+    row[0] = make_int4(deg, 0, 0, 0);
+    row[1] = make_int4(0, 0, 0, 0);
+  }
   if (!D) return;
   int32_t d = 0;
   if (p > rs) {
@@ -1627,9 +1631,9 @@ __global__ void __launch_bounds__(512) k_cyc_emit(int64_t n, const int32_t* __re
 // -------------------------------------------------------------- assemble
 //
 // One thread per edge computes the edge's whole output row from values the
-// earlier kernels left in edge order: DEG and FAN per window and direction,
-// GS = legs starting + legs ending at the edge, SG and CYC from the 64-bit
-// accumulators; saturated at the graph's count limit (2^32-1).  A streamed
+// earlier kernels left in edge order: DEG and FAN per window and direction
+// (a 32-byte row per edge and direction), GS = legs starting + legs ending
+// at the edge, SG and CYC from the 64-bit accumulators; saturated at the graph's count limit (2^32-1).  A streamed
 // old row adds its new instances to the stored value and saturates the sum:
 // min(min(old, B) + new, B) = min(old + new, B), so a clamped row stays
 // exact.
@@ -1641,13 +1645,13 @@ __device__ __forceinline__ uint64_t assemble_value(const AssembleParams& P, cons
   const int w = cd.didx;
   switch (cd.family) {
     case AML_FAM_DEG_OUT:
-      return (uint64_t)P.df_out[w][(int64_t)e * P.df_stride_out[w]].x;
+      return (uint64_t)P.df_out[w][(int64_t)e * DF_STRIDE].x;
     case AML_FAM_FAN_OUT:
-      return (uint64_t)P.df_out[w][(int64_t)e * P.df_stride_out[w]].y;
+      return (uint64_t)P.df_out[w][(int64_t)e * DF_STRIDE].y;
     case AML_FAM_DEG_IN:
-      return (uint64_t)P.df_in[w][(int64_t)e * P.df_stride_in[w]].x;
+      return (uint64_t)P.df_in[w][(int64_t)e * DF_STRIDE].x;
     case AML_FAM_FAN_IN:
-      return (uint64_t)P.df_in[w][(int64_t)e * P.df_stride_in[w]].y;
+      return (uint64_t)P.df_in[w][(int64_t)e * DF_STRIDE].y;
     case AML_FAM_GS: {
       const int32_t from =
           P.gs_from[w] ? P.gs_from[w][e] : (int32_t)(P.off[w][e + 1] - P.off[w][e]);

@@ -59,10 +59,8 @@ struct AssembleParams {
   GraphView g;
   ColDesc cols[MAX_COLS];
   int32_t ncols;
-  const int2* df_out[MAX_DELTAS];  // (DEG_OUT, FAN_OUT) of edge e at [e * stride]
+  const int2* df_out[MAX_DELTAS];  // (DEG_OUT, FAN_OUT) of edge e at [e * DF_STRIDE]
   const int2* df_in[MAX_DELTAS];   // (DEG_IN, FAN_IN) likewise
-  int32_t df_stride_out[MAX_DELTAS];
-  int32_t df_stride_in[MAX_DELTAS];
   const int64_t* off[MAX_DELTAS];     // leg offsets per edge (GS gather side)
   const int32_t* gs_from[MAX_DELTAS]; // delta counting: legs from each edge that are new
   const int32_t* gs_in[MAX_DELTAS];   // legs ending with each edge (GS scatter side)
@@ -136,10 +134,14 @@ __global__ void k_window_slots(const int32_t* rstart, const int32_t* t, const in
                                const int32_t* prev, const int32_t* next, int64_t Ev,
                                int32_t delta, int32_t* deg_s, int32_t* D, int2* df);
 // (DEG, FAN) of every edge for nw <= FAN_MAX_W windows of one direction
-// (deltas in descending order): df[e * nw + k] for window k, at the edge id
-// (self-loop entries untouched); two launches on s.  new_from > 0: only the
-// edges e >= new_from (delta counting), the other entries untouched.
+// (deltas in descending order): df[e * DF_STRIDE + k] for window k, at the
+// edge id (self-loop rows untouched); each edge's row is DF_STRIDE pairs =
+// 32 bytes, written whole, so that the stores scattered by edge id fill
+// whole sectors (a partial sector costs the memory a read-modify-write);
+// two launches on s.  new_from > 0: only the edges e >= new_from (delta
+// counting), the other rows untouched.
 constexpr int FAN_MAX_W = 4;
+constexpr int DF_STRIDE = 4;
 void fan_per_edge(const Adj& a, int64_t Ev, int64_t E, int64_t new_from, int nw,
                   const int32_t* deltas, int2* df, cudaStream_t s);
 __global__ void k_gs_into(GraphView g, int32_t delta, int32_t* gs_in);

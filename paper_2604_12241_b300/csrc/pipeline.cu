@@ -358,13 +358,12 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     for (size_t g0 = 0; g0 < ws.size(); g0 += group) {
       DfJob job{dir == 0 ? &g->out : &g->in, (int)std::min<size_t>(group, ws.size() - g0),
                 any_fan, {}, nullptr};
-      keep_df.emplace_back((size_t)E * job.nw, s);
+      keep_df.emplace_back((size_t)E * DF_STRIDE, s);
       job.df = keep_df.back().p;
       for (int k = 0; k < job.nw; ++k) {
         const int w = ws[g0 + k];
         job.deltas[k] = wins[w].delta;
         (dir == 0 ? P.df_out : P.df_in)[w] = job.df + k;
-        (dir == 0 ? P.df_stride_out : P.df_stride_in)[w] = job.nw;
       }
       df_jobs.push_back(job);
     }
@@ -572,17 +571,24 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       n_sg = (int64_t)kept;
       if (n_sg > 1) {
         size_buckets(n_sg);
-        // the set holds the new legs' keys: sized by their number, so it
-        // stays in L2 while every record is looked up in it
-        AML_CUDA(cudaMemsetAsync(n_rec.p, 0, 8, s));
-        AML_LAUNCH("k_sg_count_new", s,
-                   k_sg_count_new<<<grid_for(n_sg, 256), 256, 0, s>>>(rec.p, n_sg, new_from,
-                                                                     n_rec.p));
-        unsigned long long n_new_legs = 0;
-        const SmallRead rn{&n_new_legs, n_rec.p, 8};
-        read_small(&rn, 1, s);
+        // the set holds the new legs' keys and must stay in L2 while every
+        // record is looked up in it: sized from the record count already on
+        // the host (an upper bound on the new legs) while that gives at most
+        // 2^23 slots (64 MB), else from the new legs counted on the device
+        // (one more wait for the host)
+        uint64_t bound = (uint64_t)n_sg;
+        if (2 * bound > (1ull << 23)) {
+          AML_CUDA(cudaMemsetAsync(n_rec.p, 0, 8, s));
+          AML_LAUNCH("k_sg_count_new", s,
+                     k_sg_count_new<<<grid_for(n_sg, 256), 256, 0, s>>>(rec.p, n_sg, new_from,
+                                                                       n_rec.p));
+          unsigned long long n_new_legs = 0;
+          const SmallRead rn{&n_new_legs, n_rec.p, 8};
+          read_small(&rn, 1, s);
+          bound = n_new_legs;
+        }
         uint64_t slots = 1024;
-        while (slots < 2 * (uint64_t)n_new_legs) slots <<= 1;
+        while (slots < 2 * bound) slots <<= 1;
         key_tab = DBuf<unsigned long long>((size_t)slots, s);
         AML_CUDA(cudaMemsetAsync(key_tab.p, 0xff, (size_t)slots * 8, s));
         ks = KeySet{key_tab.p, slots - 1};
