@@ -33,9 +33,11 @@ namespace aml {
 namespace {
 
 constexpr int FAN_BLOCK = 256;
-constexpr int FAN_ITEMS = 8;
-constexpr int FAN_TILE = FAN_BLOCK * FAN_ITEMS;
-constexpr int FAN_SMEM = FAN_TILE + FAN_TILE / 32;  // one pad word per 32
+constexpr int FAN_ITEMS = 4;                         // slots per thread of k_fan_reduce
+constexpr int FAN_TILE = FAN_BLOCK * FAN_ITEMS;      // slots per block (chunk sums)
+constexpr int SCAN_ITEMS = 4;                        // slots per thread of a scan pass
+constexpr int SCAN_TILE = FAN_BLOCK * SCAN_ITEMS;    // a chunk is scanned in passes of this
+constexpr int FAN_SMEM = SCAN_TILE + SCAN_TILE / 32;  // one pad word per 32
 
 __device__ __forceinline__ int fpad(int i) { return i + (i >> 5); }
 
@@ -247,8 +249,8 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restric
   run.h = 0;
 #pragma unroll
   for (int k = 0; k < W; ++k) run.v[k] = s_carry[k];
-  for (int64_t base = c0; base < c1; base += FAN_TILE) {
-    for (int i = threadIdx.x; i < FAN_TILE; i += FAN_BLOCK) {
+  for (int64_t base = c0; base < c1; base += SCAN_TILE) {
+    for (int i = threadIdx.x; i < SCAN_TILE; i += FAN_BLOCK) {
       const int64_t p = base + i;
       const bool in = p < c1;
 #pragma unroll
@@ -258,8 +260,8 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restric
     __syncthreads();
     Seg<W> mine = seg_zero<W>();
 #pragma unroll
-    for (int it = 0; it < FAN_ITEMS; ++it) {
-      const int j = fpad(threadIdx.x * FAN_ITEMS + it);
+    for (int it = 0; it < SCAN_ITEMS; ++it) {
+      const int j = fpad(threadIdx.x * SCAN_ITEMS + it);
       Seg<W> x;
       x.h = s_h[j];
 #pragma unroll
@@ -270,8 +272,8 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restric
     const Seg<W> ex = seg_scan_block(mine, &tile_total);
     Seg<W> r = seg_combine(run, ex);
 #pragma unroll
-    for (int it = 0; it < FAN_ITEMS; ++it) {
-      const int j = fpad(threadIdx.x * FAN_ITEMS + it);
+    for (int it = 0; it < SCAN_ITEMS; ++it) {
+      const int j = fpad(threadIdx.x * SCAN_ITEMS + it);
       const bool h = s_h[j] != 0;
 #pragma unroll
       for (int k = 0; k < W; ++k) {
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(FAN_BLOCK) k_fan_scan(const int32_t* __restric
       }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < FAN_TILE; i += FAN_BLOCK) {
+    for (int i = threadIdx.x; i < SCAN_TILE; i += FAN_BLOCK) {
       const int64_t p = base + i;
       if (p < c1) {
         int2 v[W];

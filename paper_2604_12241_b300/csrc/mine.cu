@@ -1118,7 +1118,8 @@ __global__ void __launch_bounds__(SG_BIG_BLOCK, 1) k_sg_bucket_big(const LegRec*
 //     (the degree-ordered intersection of Sec. 6).
 
 // B1 of every edge a = u0 -> u1: slots of in(u0) after a with t <= t_a + delta;
-// with last, also (t, id) of B1's latest edge (any value when B1 is empty),
+// with last, also (t, id) of B1's latest edge (left unwritten when B1 is
+// empty),
 // so that a path reads its anchor's closing bound in the same round of
 // loads as the range instead of after it
 __global__ void __launch_bounds__(512) k_close_range(GraphView g, int32_t delta,
@@ -1137,9 +1138,8 @@ __global__ void __launch_bounds__(512) k_close_range(GraphView g, int32_t delta,
     if (g.new_from > 0) r.x = after_edge(g.it, g.ieid, r.x, r.y, g.t_new, g.new_from - 1);
   }
   rng[a] = r;
-  if (last)
-    last[a] = r.x < r.y ? make_int2(__ldg(g.it + r.y - 1), __ldg(g.ieid + r.y - 1))
-                        : make_int2(INT32_MIN, -1);
+  // readers look at the bound only when the range is not empty
+  if (last && r.x < r.y) last[a] = make_int2(__ldg(g.it + r.y - 1), __ldg(g.ieid + r.y - 1));
 }
 
 
