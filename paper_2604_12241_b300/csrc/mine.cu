@@ -752,6 +752,14 @@ __device__ __forceinline__ int64_t sg_span(const int4& r, const int4& o, int32_t
   return (int64_t)max(r.z, o.z) - (int64_t)min(r.y, o.y);
 }
 
+// sg_span in 32-bit arithmetic: the latest minus the earliest of int32 times
+// lies in [0, 2^32), exact as uint32; UINT32_MAX when the pair is no
+// instance (or spans 2^32 - 1 seconds: above every window either way)
+__device__ __forceinline__ uint32_t sg_span32(const int4& r, const int4& o, int32_t new_from) {
+  if (o.x == r.x || max(r.w, o.w) < new_from) return 0xffffffffu;
+  return (uint32_t)max(r.z, o.z) - (uint32_t)min(r.y, o.y);
+}
+
 // partners of `own` among group entries [j0, j1), per window, credited to
 // the leg's two edges
 template <int NS>
@@ -760,19 +768,26 @@ __device__ __forceinline__ void sg_count_partners(const int4* grp, uint32_t j0, 
                                                   int32_t delta, int32_t new_from,
                                                   unsigned long long* acc,
                                                   const SubWindows& sub) {
-  unsigned long long k = 0, ks[NS > 0 ? NS : 1] = {};
+  uint32_t k = 0, ks[NS > 0 ? NS : 1] = {};  // at most CAP partners
   for (uint32_t j = j0; j < j1; ++j) {
-    const int64_t span = sg_span(own, grp[j], new_from);
-    if (span > delta) continue;
+    const uint32_t span = sg_span32(own, grp[j], new_from);
+    if (span > (uint32_t)delta) continue;
     ++k;
 #pragma unroll
     for (int i = 0; i < NS; ++i)
-      if (i < sub.n && span <= sub.delta[i]) ++ks[i];
+      if (i < sub.n && span <= (uint32_t)sub.delta[i]) ++ks[i];
   }
   if (acc) sg_credit(acc, a, own.w, k);
 #pragma unroll
   for (int i = 0; i < NS; ++i)
     if (i < sub.n && sub.sg[i]) sg_credit(sub.sg[i], a, own.w, ks[i]);
+}
+
+// table slot of a key inside its bucket: a 32-bit mix of both halves (the
+// keys of one bucket already share the top bits of mix64, which picked it)
+__device__ __forceinline__ uint32_t slot_hash(uint64_t key) {
+  uint32_t h = (uint32_t)key * 0x9e3779b1u ^ (uint32_t)(key >> 32) * 0x85ebca77u;
+  return h ^ (h >> 15);
 }
 
 // Groups one bucket's records by key in a shared-memory hash table and
@@ -964,7 +979,7 @@ __device__ __forceinline__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRe
   for (int k = 0; k < PER; ++k) {
     if (threadIdx.x + k * BS >= n) break;
     const unsigned long long key = r[k].key;
-    uint32_t q = (uint32_t)mix64(key) & (uint32_t)(tab - 1);
+    uint32_t q = slot_hash(key) & (uint32_t)(tab - 1);
     for (int probe = 0; probe < tab; ++probe) {  // n < tab: a slot is always found
       const unsigned long long cur_key = S.key[q];
       if (cur_key == key) break;
