@@ -395,19 +395,17 @@ __global__ void __launch_bounds__(256) k_mark_heavy(const int32_t* __restrict__ 
 }
 
 // flag[i] = 1 for the cycle-capable legs of heavy anchors
-__global__ void __launch_bounds__(256) k_heavy_legs(const int32_t* __restrict__ la, int64_t n,
+__global__ void __launch_bounds__(256) k_heavy_legs(const int4* __restrict__ legs, int64_t n,
                                                     const int32_t* __restrict__ heavy,
                                                     int32_t* __restrict__ flag) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) flag[i] = heavy[la[i]];
+  if (i < n) flag[i] = heavy[legs[i].x];
 }
 
 __global__ void __launch_bounds__(256) k_gather_legs(const int32_t* __restrict__ flag,
                                                      const int32_t* __restrict__ off, int64_t n,
-                                                     const int32_t* __restrict__ la,
-                                                     const int32_t* __restrict__ lb,
-                                                     int32_t* __restrict__ la_h,
-                                                     int32_t* __restrict__ lb_h, int64_t cap,
+                                                     const int4* __restrict__ legs,
+                                                     int4* __restrict__ legs_h, int64_t cap,
                                                      uint32_t* __restrict__ err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n && flag[i]) {
@@ -415,18 +413,17 @@ __global__ void __launch_bounds__(256) k_gather_legs(const int32_t* __restrict__
       atomicOr(err, ERR_BOUNDS);
       return;
     }
-    la_h[off[i]] = la[i];
-    lb_h[off[i]] = lb[i];
+    legs_h[off[i]] = legs[i];
   }
 }
 
 void cycles_hybrid(aml_graph* g, const GraphView& gv, int32_t delta, int K,
                    const CycleSlots& slots, const SubWindows& sub, unsigned long long* acc,
-                   const int2* crng, const int32_t* la, const int32_t* lb, bool learned,
-                   cudaStream_t s, cudaStream_t side) {
+                   const int2* crng, const AnchorRec* anc, const int2* qwin, const int4* legs,
+                   bool learned, cudaStream_t s, cudaStream_t side) {
   const int64_t E = g->E;
   LegCache& lc = g->legs[delta];
-  const int64_t n2 = lc.n_front[2];  // all cycle-capable legs (la, lb)
+  const int64_t n2 = lc.n_front[2];  // all cycle-capable legs
   // anchors with cycle work and their estimated costs, one descending queue
   DBuf<int32_t> items(E, s), w2(E, s), nb(4, s), queue(E, s), hist(2 * N_BUCKETS + 1, s);
   cyc_items(g, gv, delta, crng, items.p, nb.p, w2.p, s);
@@ -464,7 +461,7 @@ void cycles_hybrid(aml_graph* g, const GraphView& gv, int32_t delta, int K,
   DBuf<int32_t> fl((size_t)n2 + 1, s), off((size_t)n2 + 1, s);
   if (n2 > 0)
     AML_LAUNCH("k_heavy_legs", s,
-               k_heavy_legs<<<grid_for(n2, 256), 256, 0, s>>>(la, n2, heavy.p, fl.p));
+               k_heavy_legs<<<grid_for(n2, 256), 256, 0, s>>>(legs, n2, heavy.p, fl.p));
   AML_CUDA(cudaMemsetAsync(fl.p + n2, 0, sizeof(int32_t), s));
   scan_i32(fl.p, off.p, n2 + 1, false, s);
   if (cache[2] < 0) {
@@ -474,13 +471,13 @@ void cycles_hybrid(aml_graph* g, const GraphView& gv, int32_t delta, int K,
     cache[2] = nh;
   }
   const int64_t cap = std::max<int64_t>(cache[2], 1);
-  DBuf<int32_t> la_h((size_t)cap, s), lb_h((size_t)cap, s);
-  AML_CUDA(cudaMemsetAsync(la_h.p, 0, (size_t)cap * 4, s));  // valid ids whatever happens
-  AML_CUDA(cudaMemsetAsync(lb_h.p, 0, (size_t)cap * 4, s));
+  DBuf<int4> legs_h((size_t)cap, s);
+  // valid edge and node ids whatever happens
+  AML_CUDA(cudaMemsetAsync(legs_h.p, 0, (size_t)cap * sizeof(int4), s));
   if (n2 > 0)
     AML_LAUNCH("k_gather_legs", s,
-               k_gather_legs<<<grid_for(n2, 256), 256, 0, s>>>(fl.p, off.p, n2, la, lb,
-                                                              la_h.p, lb_h.p, cache[2], g->err));
+               k_gather_legs<<<grid_for(n2, 256), 256, 0, s>>>(fl.p, off.p, n2, legs, legs_h.p,
+                                                              cache[2], g->err));
   AML_LAUNCH("k_check_count", s, k_check_count<<<1, 1, 0, s>>>(off.p + n2, cache[2], g->err));
   // the other anchors: one persistent launch beside the level-by-level search
   DBuf<unsigned long long> next(2, s);
@@ -507,8 +504,7 @@ void cycles_hybrid(aml_graph* g, const GraphView& gv, int32_t delta, int K,
   A.close_scan_max = g->tune.close_scan_max;
   AML_LAUNCH("k_cyc_persistent", side,
              k_cyc_persistent<<<persistent_grid(), 256, 0, side>>>(A));
-  level_cycle_search(g, gv, delta, K, slots, sub, acc, crng, nullptr, nullptr, la_h.p, lb_h.p,
-                     cache, s);
+  level_cycle_search(g, gv, delta, K, slots, sub, acc, anc, qwin, legs_h.p, cache, s);
   if (fork) {  // joined before the buffers above are released on s
     AML_CUDA(cudaEventRecord(g->branch_ev[5], side));
     AML_CUDA(cudaStreamWaitEvent(s, g->branch_ev[5], 0));

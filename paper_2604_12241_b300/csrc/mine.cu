@@ -130,18 +130,18 @@ __device__ __forceinline__ int32_t cycle_bound(const GraphView& g, int2 cr, int2
   return after_edge(g.ot, g.oeid, q0, q1, cl.x, cl.y - 1);  // first slot not before it
 }
 
-// L[a]: legs from a.  With crng: L2[a] = those that can start a cycle
-// (slots before the cycle bound, minus returns to src(a) among them).
+// L[a]: legs from a.  With anc (anchor records): L2[a] = those that can
+// start a cycle (slots before the cycle bound, minus returns to src(a) among
+// them).
 // With L_new (delta counting): L_new[a] = legs from a whose second edge is new.
-// qwin[a] = a's window slots [q0, q1) in dst(a)'s out-list and, with crng,
+// qwin[a] = a's window slots [q0, q1) in dst(a)'s out-list and, with anc,
 // qcb[a] = its cycle bound, kept for the emission.
 // Z: the accumulators the emission and later kernels add into, zeroed here
 // (element a of each) instead of by separate memsets.
 template <int NS>
 __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
                                                    int32_t* __restrict__ L,
-                                                   const int2* __restrict__ crng,
-                                                   const int2* __restrict__ ccl,
+                                                   const AnchorRec* __restrict__ anc,
                                                    int32_t* __restrict__ L2,
                                                    int32_t* __restrict__ L_new,
                                                    int2* __restrict__ qwin,
@@ -207,10 +207,8 @@ __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
     L_new[a] = (q1 - qn) - back;
   }
   if (!L2) return;
-  const int2 cr = crng[a];
-  const int2 cl = ccl ? ccl[a]
-                      : (cr.x < cr.y ? make_int2(__ldg(g.it + cr.y - 1), __ldg(g.ieid + cr.y - 1))
-                                     : make_int2(0, 0));
+  const int4 an = *reinterpret_cast<const int4*>(anc + a);
+  const int2 cr = make_int2(an.x, an.y), cl = make_int2(an.z, an.w);
   const int32_t qc = cycle_bound(g, cr, cl, q0, q1);
   qcb[a] = qc;
   int32_t back = 0;
@@ -339,7 +337,7 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit(GraphView g, const int2* __
   // off2[a] + their rank among a's legs
   int32_t qc = q0;
   int64_t o2 = 0;
-  if (S.la && q1 > q0) {
+  if (S.leg && q1 > q0) {
     qc = qcb[a];
     o2 = S.off2[a] - o;
   }
@@ -390,10 +388,7 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit(GraphView g, const int2* __
     if (NS > 0 && in) sub_leg_credit<NS>(sub, leg, sa, b, tb - sta, g.new_from);
     if (leg) {
       if (gs_in && b >= g.new_from) atomicAdd(gs_in + b, 1);
-      if (S.la && sq < sqc) {
-        S.la[sc2 + rank] = sa;
-        S.lb[sc2 + rank] = b;
-      }
+      if (S.leg && sq < sqc) S.leg[sc2 + rank] = make_int4(sa, b, y, tb);
     } else if (in && acc_cyc2 && b >= g.new_from) {  // a return: a 2-cycle
       atomicAdd(acc_cyc2 + b, 1ull);
       atomicAdd(acc_cyc2 + sa, 1ull);
@@ -435,11 +430,7 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit(GraphView g, const int2* __
         atomicAdd(acc_cyc2 + b, 1ull);
         ++hc2;
       }
-      if (S.la && leg && q < hqc) {
-        const int64_t pos = ho2 + ho + __popc(m & lt);
-        S.la[pos] = ha;
-        S.lb[pos] = b;
-      }
+      if (S.leg && leg && q < hqc) S.leg[ho2 + ho + __popc(m & lt)] = make_int4(ha, b, y, tb);
       ho += __popc(m);
     }
     if (acc_cyc2) {
@@ -549,7 +540,7 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit_delta(
       if (q1 > q0) {
         ta = g.ts[a];
         qn = min(max(__ldg(first_new + h), q0), q1);
-        if (S.la) {
+        if (S.leg) {
           qc = qcb[a];
           c2 = S.off2[a];
         }
@@ -591,16 +582,16 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit_delta(
       const int32_t tb = in ? __ldg(g.ot + q) : 0;
       sg_record(S, in && y != sx, 0, sa, b, sx, sh, y, sta, tb, g.N, S.bits);
     });
-  if (!S.la) return;
+  if (!S.leg) return;
   // cycle legs: the legs in [q0, qc), at off2[a] + their rank
   const bool own = qc - q0 <= own_max;
   int32_t q = q0;
   int64_t rank = 0;
   while (__any_sync(full, own && q < qc)) {
     if (own && q < qc) {
-      if (__ldg(g.onbr + q) != x) {
-        S.la[c2 + rank] = a;
-        S.lb[c2 + rank] = __ldg(g.oeid + q);
+      const int32_t y = __ldg(g.onbr + q);
+      if (y != x) {
+        S.leg[c2 + rank] = make_int4(a, __ldg(g.oeid + q), y, __ldg(g.ot + q));
         ++rank;
       }
       ++q;
@@ -617,13 +608,11 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit_delta(
     for (int32_t base = hq0; base < hqc; base += 32) {
       const int32_t qq = base + lane;
       const bool in = qq < hqc;
-      const bool leg = in && __ldg(g.onbr + qq) != hx;
+      const int32_t y = in ? __ldg(g.onbr + qq) : hx;
+      const bool leg = in && y != hx;
       const unsigned m = __ballot_sync(full, leg);
-      if (leg) {
-        const int64_t pos = hc2 + r + __popc(m & lt);
-        S.la[pos] = ha;
-        S.lb[pos] = __ldg(g.oeid + qq);
-      }
+      if (leg)
+        S.leg[hc2 + r + __popc(m & lt)] = make_int4(ha, __ldg(g.oeid + qq), y, __ldg(g.ot + qq));
       r += __popc(m);
     }
   }
@@ -1132,29 +1121,31 @@ __global__ void __launch_bounds__(SG_BIG_BLOCK, 1) k_sg_bucket_big(const LegRec*
 //     it is short, two binary searches in u0's (nbr, t, id) in-list otherwise
 //     (the degree-ordered intersection of Sec. 6).
 
-// B1 of every edge a = u0 -> u1: slots of in(u0) after a with t <= t_a + delta;
-// with last, also (t, id) of B1's latest edge (left unwritten when B1 is
-// empty),
-// so that a path reads its anchor's closing bound in the same round of
-// loads as the range instead of after it
+// B1 of every edge a = u0 -> u1: slots of in(u0) after a with t <= t_a + delta,
+// into rng and/or, with the (t, id) of B1's latest edge, u0, u1 and t_a, into
+// the anchor record anc[a]: a path then reads everything it needs of its
+// anchor in one sector, in one round of loads
 __global__ void __launch_bounds__(512) k_close_range(GraphView g, int32_t delta,
                                                      int2* __restrict__ rng,
-                                                     int2* __restrict__ last) {
+                                                     AnchorRec* __restrict__ anc) {
   int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a64 >= g.E) return;
   int32_t a = (int32_t)a64;
-  int32_t u0 = g.src[a];
+  const int32_t u0 = g.src[a], u1 = g.dst[a], ta = g.ts[a];
   int2 r = make_int2(0, 0);
-  if (u0 != g.dst[a]) {
+  if (u0 != u1) {
     int32_t is = g.iptr[u0], ie = g.iptr[u0 + 1];
-    int32_t ta = g.ts[a];
     after_edge_upto(g.it, g.ieid, is, ie, ta, a, (int64_t)ta + delta, r.x, r.y);
     // delta counting: a cycle is new iff its closing (latest) edge is new
     if (g.new_from > 0) r.x = after_edge(g.it, g.ieid, r.x, r.y, g.t_new, g.new_from - 1);
   }
-  rng[a] = r;
-  // readers look at the bound only when the range is not empty
-  if (last && r.x < r.y) last[a] = make_int2(__ldg(g.it + r.y - 1), __ldg(g.ieid + r.y - 1));
+  if (rng) rng[a] = r;
+  if (anc) {  // the whole 32-byte record, so the store fills its sector
+    int4* dst = reinterpret_cast<int4*>(anc + a);
+    const bool any = r.x < r.y;
+    dst[0] = make_int4(r.x, r.y, any ? __ldg(g.it + r.y - 1) : 0, any ? __ldg(g.ieid + r.y - 1) : 0);
+    dst[1] = make_int4(u0, u1, ta, 0);
+  }
 }
 
 
@@ -1198,17 +1189,18 @@ __device__ __forceinline__ void cyc_path(const GraphView& g, const CycFrontier& 
     }
     idx = F.par[lev][idx];
   }
-  edges[0] = F.la[idx];
-  nodes[0] = g.src[edges[0]];
-  nodes[1] = g.dst[edges[0]];
-  if constexpr (BASE == 2) {
-    edges[1] = F.lb[idx];
-    nodes[2] = g.dst[edges[1]];
-    const int32_t tb = g.ts[edges[1]];
-    t_late = max(t_late, tb);
-    if (J == 2) *tl = tb;
-  } else if (J == 1) {
-    *tl = g.ts[edges[0]];
+  if constexpr (BASE == 2) {  // the leg record; nodes[0..1] come with the anchor's record
+    const int4 lg = F.leg[idx];
+    edges[0] = lg.x;
+    edges[1] = lg.y;
+    nodes[2] = lg.z;
+    t_late = max(t_late, lg.w);
+    if (J == 2) *tl = lg.w;
+  } else {
+    edges[0] = F.la[idx];
+    nodes[0] = g.src[edges[0]];
+    nodes[1] = g.dst[edges[0]];
+    if (J == 1) *tl = g.ts[edges[0]];
   }
   if (tp) *tp = J == 1 ? g.ts[edges[0]] : t_late;
 }
@@ -1222,20 +1214,21 @@ __device__ __forceinline__ void cyc_path(const GraphView& g, const CycFrontier& 
 // the frontier starts at level 1 (the anchors); a cycle closes through any
 // edge of B1, and a smaller window keeps it only when the path's latest edge
 // also lies inside it.
-// With ccl (the closing ranges' latest edges) and qwin (the leg window of
-// every edge: its end node's out-slots after it, up to its time + delta),
-// the window of a path's children starts at qwin[last].x with no search,
-// and ends inside qwin[last] (the latest closing edge is at most delta after
-// the anchor, hence after the path's last edge); without them (window
-// cycles, or callers that keep neither) both bounds are searched.
+// Ordered cycles read a path's anchor (closing range and bound, its two
+// nodes and time) from one anchor record and the path's base leg from one
+// leg record; the window of a path's children starts at qwin[last].x (the
+// leg window of every edge: its end node's out-slots after it, up to its
+// time + delta) with no search, and ends inside it (the latest closing edge
+// is at most delta after the anchor, hence after the path's last edge).
+// Window cycles read the closing ranges and search both bounds.
 // Arguments of one level of the cycle search (see cyc_item).
 struct CycLevelArgs {
   GraphView g;
   int32_t delta;
   int K;
-  const int2* close_rng;
-  const int2* ccl;
-  const int2* qwin;
+  const int2* close_rng;  // window cycles
+  const AnchorRec* anc;   // ordered cycles
+  const int2* qwin;       // ordered cycles
   CycleSlots slots;
   unsigned long long* acc;
   int32_t close_scan_max;
@@ -1255,10 +1248,23 @@ __device__ __forceinline__ int32_t cyc_item(const CycLevelArgs& A, const CycFron
   int32_t nodes[J + 1];
   int32_t tp = 0, tl = 0;
   cyc_path<J, WIN ? 1 : 2>(g, F, i, edges, nodes, &tl, WIN ? &tp : nullptr);
-  const int2 cr = A.close_rng[edges[0]];
-  int2 cl = A.ccl ? A.ccl[edges[0]] : make_int2(0, 0);
-  if (cr.x >= cr.y) return 0;  // e1 starts no cycle
-  if (!A.ccl) cl = make_int2(__ldg(g.it + cr.y - 1), __ldg(g.ieid + cr.y - 1));
+  int2 cr, cl;
+  int32_t t1;
+  if constexpr (WIN) {
+    cr = A.close_rng[edges[0]];
+    if (cr.x >= cr.y) return 0;  // e1 starts no cycle
+    cl = make_int2(__ldg(g.it + cr.y - 1), __ldg(g.ieid + cr.y - 1));
+    t1 = g.ts[edges[0]];
+  } else {
+    const int4* rec = reinterpret_cast<const int4*>(A.anc + edges[0]);
+    const int4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
+    cr = make_int2(r0.x, r0.y);
+    if (cr.x >= cr.y) return 0;  // e1 starts no cycle
+    cl = make_int2(r0.z, r0.w);
+    nodes[0] = r1.x;
+    nodes[1] = r1.y;
+    t1 = r1.z;
+  }
   const int32_t t_cl = cl.x, id_cl = cl.y;
   const int32_t last = edges[j - 1];
   if (!WIN && !before(tl, last, t_cl, id_cl)) return 0;  // nothing can close after it
@@ -1272,7 +1278,7 @@ __device__ __forceinline__ int32_t cyc_item(const CycLevelArgs& A, const CycFron
   const CycleSlots& slots = A.slots;
   unsigned long long* acc = A.acc;
   const int32_t close_scan_max = A.close_scan_max;
-  const int32_t e1 = edges[0], t1 = g.ts[e1];
+  const int32_t e1 = edges[0];
   // cycles of length j+1: edges w -> u0 in B1 (after `last` unless WIN), for
   // this window and every smaller one whose delta the cycle keeps
   const int k = j + 1;
@@ -1334,7 +1340,7 @@ __device__ __forceinline__ int32_t cyc_item(const CycLevelArgs& A, const CycFron
   }
   if (!has_next) return 0;
   int32_t q0, q1;
-  if (!WIN && A.qwin) {
+  if constexpr (!WIN) {
     const int2 lw = A.qwin[last];
     q0 = lw.x;
     q1 = upper_t_short(g.ot, lw.x, lw.y, t_cl);
@@ -1572,10 +1578,10 @@ int fused_cycle_grid(int n_sub) {
 }
 
 void launch_cyc_fused(int grid, cudaStream_t s, const GraphView& g, int32_t delta, int K,
-                      const int2* close_rng, const int2* ccl, const int2* qwin,
-                      const CycleSlots& slots, unsigned long long* acc, int32_t close_scan_max,
-                      const FusedCycles& P, const SubWindows& sub) {
-  const CycLevelArgs A{g, delta, K, close_rng, ccl, qwin, slots, acc, close_scan_max};
+                      const AnchorRec* anc, const int2* qwin, const CycleSlots& slots,
+                      unsigned long long* acc, int32_t close_scan_max, const FusedCycles& P,
+                      const SubWindows& sub) {
+  const CycLevelArgs A{g, delta, K, nullptr, anc, qwin, slots, acc, close_scan_max};
   nsub_dispatch(sub.n, [&](auto ns) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -1743,11 +1749,11 @@ __global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
 
 
 void launch_leg_count(unsigned grid, int block, cudaStream_t s, const GraphView& g, int32_t delta,
-                      int32_t* L, const int2* crng, const int2* ccl, int32_t* L2, int32_t* L_new,
-                      int2* qwin, int32_t* qcb, const SubWindows& sub, const ZeroSink& Z) {
+                      int32_t* L, const AnchorRec* anc, int32_t* L2, int32_t* L_new, int2* qwin,
+                      int32_t* qcb, const SubWindows& sub, const ZeroSink& Z) {
   nsub_dispatch(sub.n, [&](auto ns) {
     AML_LAUNCH("k_leg_count", s,
-               k_leg_count<decltype(ns)::value><<<grid, block, 0, s>>>(g, delta, L, crng, ccl, L2,
+               k_leg_count<decltype(ns)::value><<<grid, block, 0, s>>>(g, delta, L, anc, L2,
                                                                       L_new, qwin, qcb, sub, Z));
   });
 }
@@ -1802,12 +1808,13 @@ void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
 
 void launch_cyc_level(unsigned grid, int block, cudaStream_t s, const GraphView& g,
                       int32_t delta, int K, int j, const CycFrontier& F, int64_t n,
-                      const int2* close_rng, const int2* ccl, const int2* qwin,
+                      const int2* close_rng, const AnchorRec* anc, const int2* qwin,
                       const CycleSlots& slots, unsigned long long* acc, int32_t* cnt,
                       int32_t* q0_out, int32_t close_scan_max, const SubWindows& sub,
                       bool window_cycles) {
-  const CycLevelArgs A{g, delta, K, close_rng, ccl, window_cycles ? nullptr : qwin, slots, acc,
-                       close_scan_max};
+  AML_REQUIRE(window_cycles ? close_rng != nullptr : (anc != nullptr && qwin != nullptr),
+              AML_EINTERNAL, "cycle level without its anchor data");
+  const CycLevelArgs A{g, delta, K, close_rng, anc, qwin, slots, acc, close_scan_max};
   AML_REQUIRE(j >= (window_cycles ? 1 : 2) && j <= MAX_CYCLE - 1, AML_EINTERNAL,
               "cycle level out of range");
   nsub_dispatch(sub.n, [&](auto ns) {

@@ -86,10 +86,10 @@ struct __align__(16) LegRec {
 // Where k_leg_emit writes the legs: (a, b) arrays for the cycle search
 // and/or records + bucket histogram for the SG grouping (null = not wanted).
 struct LegSink {
-  int32_t* la;      // legs that can start a cycle (closing range not empty and the
-  int32_t* lb;      // second edge before its last closing edge), compacted
+  int4* leg;        // legs that can start a cycle (closing range not empty and the
+                    // second edge before its last closing edge), compacted, as
+                    // {a, b, dst b, t_b}: what the cycle search reads of a leg
   const int64_t* off2;  // first cycle leg of each edge (scan of k_leg_count's L2)
-  const int2* crng;     // closing ranges (needed with la)
   LegRec* rec;
   uint32_t* hist;
   int bits;  // log2 of the number of SG buckets
@@ -124,10 +124,18 @@ struct SubWindows {
 // the out-slot slot[j][i].
 struct CycFrontier {
   int base;
-  const int32_t* la;
-  const int32_t* lb;
+  const int32_t* la;   // base 1: the anchor edges
+  const int4* leg;     // base 2: the legs {a, b, dst b, t_b}
   const int32_t* par[MAX_CYCLE + 1];
   const int32_t* slot[MAX_CYCLE + 1];
+};
+
+// What a cycle path reads of its anchor edge a = u0 -> u1, in one 32-byte
+// record (one sector): its closing range B1 = in(u0) slots [cr_x, cr_y),
+// the (t, id) of B1's latest edge (when B1 is not empty), u0, u1 and t_a.
+struct __align__(32) AnchorRec {
+  int32_t cr_x, cr_y, t_cl, id_cl;
+  int32_t u0, u1, t1, pad;
 };
 
 __global__ void k_window_slots(const int32_t* rstart, const int32_t* t, const int32_t* eid,
@@ -161,7 +169,9 @@ __global__ void k_sg_new_keys(const LegRec* rec, int64_t n, int32_t new_from, Ke
 __global__ void k_sg_count_new(const LegRec* rec, int64_t n, int32_t new_from,
                                unsigned long long* count);
 __global__ void k_mark_nodes(const int32_t* node_of, int64_t from, int64_t E, uint32_t* mask);
-__global__ void k_close_range(GraphView g, int32_t delta, int2* rng, int2* last);
+// closing ranges of every edge: into rng (int2) and/or anc (anchor records);
+// either may be null
+__global__ void k_close_range(GraphView g, int32_t delta, int2* rng, AnchorRec* anc);
 __global__ void k_anchor_flags(const int2* crng, int64_t E, int32_t* flag);
 __global__ void k_compact_ids(const int32_t* flag, const int32_t* off, int64_t E, int32_t* items);
 // Buffers k_leg_count zeroes per edge: n_acc accumulator columns of E
@@ -174,8 +184,8 @@ struct ZeroSink {
 // Launchers of the kernels that also count sub-windows (instantiated for
 // the number of them in sub).
 void launch_leg_count(unsigned grid, int block, cudaStream_t s, const GraphView& g, int32_t delta,
-                      int32_t* L, const int2* crng, const int2* ccl, int32_t* L2, int32_t* L_new,
-                      int2* qwin, int32_t* qcb, const SubWindows& sub, const ZeroSink& Z);
+                      int32_t* L, const AnchorRec* anc, int32_t* L2, int32_t* L_new, int2* qwin,
+                      int32_t* qcb, const SubWindows& sub, const ZeroSink& Z);
 // Delta counting (new_from > 0): the legs a new instance can use (mine.cu);
 // first_new = each out-list's first new slot (k_first_new); mptr/mslot =
 // each node's out-list slots whose counterparty is a batch destination
@@ -201,11 +211,12 @@ void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
                        const uint32_t* bend, int32_t delta, const int32_t* dst, const int32_t* ts,
                        unsigned long long* acc, int32_t new_from, uint32_t* overflow,
                        const SubWindows& sub);
-// ccl, qwin: the closing ranges' latest edges and the leg windows of the
-// same window's leg pass (either null: the bounds are searched instead)
+// Ordered cycles read their anchors from anc and their children's window
+// starts from qwin (the leg windows of the same window's leg pass); window
+// cycles (base 1) read close_rng and search their windows.
 void launch_cyc_level(unsigned grid, int block, cudaStream_t s, const GraphView& g,
                       int32_t delta, int K, int j, const CycFrontier& F, int64_t n,
-                      const int2* close_rng, const int2* ccl, const int2* qwin,
+                      const int2* close_rng, const AnchorRec* anc, const int2* qwin,
                       const CycleSlots& slots, unsigned long long* acc, int32_t* cnt,
                       int32_t* q0_out, int32_t close_scan_max, const SubWindows& sub,
                       bool window_cycles = false);
@@ -221,7 +232,7 @@ struct GridBarrier {
 // of levels 3..K-1 hold cap[j] elements; cnt/q0 hold the largest level that
 // has children; bsum one value per block.
 struct FusedCycles {
-  CycFrontier F;  // base level (la, lb)
+  CycFrontier F;  // base level (the legs)
   int64_t n2;
   int64_t cap[MAX_CYCLE + 1];
   int32_t* par[MAX_CYCLE + 1];
@@ -237,9 +248,9 @@ struct FusedCycles {
 // blocks of the fused launch on this device (all resident at once)
 int fused_cycle_grid(int n_sub);
 void launch_cyc_fused(int grid, cudaStream_t s, const GraphView& g, int32_t delta, int K,
-                      const int2* close_rng, const int2* ccl, const int2* qwin,
-                      const CycleSlots& slots, unsigned long long* acc, int32_t close_scan_max,
-                      const FusedCycles& P, const SubWindows& sub);
+                      const AnchorRec* anc, const int2* qwin, const CycleSlots& slots,
+                      unsigned long long* acc, int32_t close_scan_max, const FusedCycles& P,
+                      const SubWindows& sub);
 __global__ void k_assemble(AssembleParams P);
 
 // Host pipeline: enqueue a full mine of `ps` on `g` into device `counts`.
@@ -261,16 +272,15 @@ void run_program(const GraphView& gv, const float* amount, const Prog& p,
 
 void level_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K,
                         const CycleSlots& slots, const SubWindows& sub,
-                        unsigned long long* acc, const int2* crng, const int2* ccl,
-                        const int2* qwin, const int32_t* la, const int32_t* lb,
-                        int64_t* front_cache, cudaStream_t s);
+                        unsigned long long* acc, const AnchorRec* anc, const int2* qwin,
+                        const int4* legs, int64_t* front_cache, cudaStream_t s);
 // Cycle search of one window split by estimated anchor cost (cost.cu): the
 // heaviest anchors' legs level by level on s, the other anchors by the
 // persistent kernel on `side` (forked from and joined back to s).
 void cycles_hybrid(aml_graph* g, const GraphView& gv, int32_t delta, int K,
                    const CycleSlots& slots, const SubWindows& sub, unsigned long long* acc,
-                   const int2* crng, const int32_t* la, const int32_t* lb, bool learned,
-                   cudaStream_t s, cudaStream_t side);
+                   const int2* crng, const AnchorRec* anc, const int2* qwin, const int4* legs,
+                   bool learned, cudaStream_t s, cudaStream_t side);
 void drop_captured_mines(aml_graph* g);
 
 }  // namespace aml

@@ -96,7 +96,7 @@ void window_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K
     const bool has_next = j + 1 <= K - 1;
     DBuf<int32_t> cnt(has_next ? n + 1 : 0, s), q0(has_next ? n : 0, s);
     launch_cyc_level(grid_for(n, B), B, s, gv, delta, K, j, F, n, crng.p, nullptr, nullptr,
-                     slots, acc, cnt.p, q0.p, tn.close_scan_max, sw, true);
+                     slots, acc, cnt.p, q0.p, tn.close_scan_max, sw, true);  // window cycles
     if (!has_next) break;
     DBuf<int64_t> foff(n + 1, s);
     AML_CUDA(cudaMemsetAsync(cnt.p + n, 0, sizeof(int32_t), s));
@@ -129,23 +129,21 @@ void window_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K
 // with one wait per level).
 void level_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K,
                         const CycleSlots& slots, const SubWindows& sub,
-                        unsigned long long* acc, const int2* crng, const int2* ccl,
-                        const int2* qwin, const int32_t* la, const int32_t* lb,
-                        int64_t* front_cache, cudaStream_t s) {
+                        unsigned long long* acc, const AnchorRec* anc, const int2* qwin,
+                        const int4* legs, int64_t* front_cache, cudaStream_t s) {
   const Tuning tn = g->tune;
   const int B = tn.block;
   CycFrontier F;
   std::memset(&F, 0, sizeof(F));
   F.base = 2;
-  F.la = la;
-  F.lb = lb;
+  F.leg = legs;
   std::vector<DBuf<int32_t>> front;  // par/slot of levels >= 3
   front.reserve(2 * MAX_CYCLE);
   int64_t n = front_cache[2];
   for (int j = 2; j <= K - 1 && n > 0; ++j) {
     const bool has_next = j + 1 <= K - 1;
     DBuf<int32_t> cnt(has_next ? n + 1 : 0, s), q0(has_next ? n : 0, s);
-    launch_cyc_level(grid_for(n, B), B, s, gv, delta, K, j, F, n, crng, ccl, qwin, slots, acc,
+    launch_cyc_level(grid_for(n, B), B, s, gv, delta, K, j, F, n, nullptr, anc, qwin, slots, acc,
                      cnt.p, q0.p, tn.close_scan_max, sub);
     if (!has_next) break;
     DBuf<int64_t> foff(n + 1, s);
@@ -176,13 +174,12 @@ void level_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K,
 // every level are known (a plain search learns them first).
 void level_cycle_search_fused(aml_graph* g, const GraphView& gv, int32_t delta, int K,
                               const CycleSlots& slots, const SubWindows& sub,
-                              unsigned long long* acc, const int2* crng, const int2* ccl,
-                              const int2* qwin, const int32_t* la, const int32_t* lb,
-                              int64_t* front_cache, cudaStream_t s) {
+                              unsigned long long* acc, const AnchorRec* anc,
+                              const int2* qwin, const int4* legs, int64_t* front_cache,
+                              cudaStream_t s) {
   for (int j = 3; j <= K - 1; ++j)
     if (front_cache[j] < 0) {
-      level_cycle_search(g, gv, delta, K, slots, sub, acc, crng, ccl, qwin, la, lb, front_cache,
-                         s);
+      level_cycle_search(g, gv, delta, K, slots, sub, acc, anc, qwin, legs, front_cache, s);
       return;
     }
   const int64_t n2 = front_cache[2];
@@ -190,8 +187,7 @@ void level_cycle_search_fused(aml_graph* g, const GraphView& gv, int32_t delta, 
   FusedCycles P;
   std::memset(&P, 0, sizeof(P));
   P.F.base = 2;
-  P.F.la = la;
-  P.F.lb = lb;
+  P.F.leg = legs;
   P.n2 = n2;
   std::vector<DBuf<int32_t>> front;
   front.reserve(2 * MAX_CYCLE);
@@ -216,8 +212,7 @@ void level_cycle_search_fused(aml_graph* g, const GraphView& gv, int32_t delta, 
   P.err = g->err;
   P.wait_limit = g->wait_limit;
   P.own_max = g->tune.own_max;
-  launch_cyc_fused(grid, s, gv, delta, K, crng, ccl, qwin, slots, acc, g->tune.close_scan_max, P,
-                   sub);
+  launch_cyc_fused(grid, s, gv, delta, K, anc, qwin, slots, acc, g->tune.close_scan_max, P, sub);
 }
 
 void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
@@ -415,14 +410,17 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     // 2. legs (and, for the level-by-level cycle search, the legs that can
     // start a cycle: those of anchors with a closing range, before its end)
     const bool level_cycles = wp.K >= 3;
-    DBuf<int2> crng, ccl;
+    // closing ranges: anchor records for the level-by-level search, and the
+    // plain ranges for the persistent modes' kernels
+    DBuf<int2> crng;
+    DBuf<AnchorRec> anc;
     DBuf<int32_t> L2;
     DBuf<int64_t> off2;
     if (level_cycles) {
-      crng = DBuf<int2>((size_t)E, s);
-      ccl = DBuf<int2>((size_t)E, s);
+      if (persistent) crng = DBuf<int2>((size_t)E, s);
+      anc = DBuf<AnchorRec>((size_t)E, s);
       AML_LAUNCH("k_close_range", s,
-                 k_close_range<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, crng.p, ccl.p));
+                 k_close_range<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, crng.p, anc.p));
       L2 = DBuf<int32_t>((size_t)E + 1, s);
       off2 = DBuf<int64_t>((size_t)E + 1, s);
     }
@@ -443,9 +441,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     }
     ZeroSink Z{acc_zeroed ? nullptr : acc.p, acc_zeroed ? 0 : n_acc, gs_in};
     acc_zeroed = true;
-    launch_leg_count(grid_for(E, B), B, s, gv, wp.delta, L.p, level_cycles ? crng.p : nullptr,
-                     level_cycles ? ccl.p : nullptr, level_cycles ? L2.p : nullptr, L_new, qwin.p,
-                     qcb.p, sub, Z);
+    launch_leg_count(grid_for(E, B), B, s, gv, wp.delta, L.p, level_cycles ? anc.p : nullptr,
+                     level_cycles ? L2.p : nullptr, L_new, qwin.p, qcb.p, sub, Z);
     AML_CUDA(cudaMemsetAsync(L.p + E, 0, sizeof(int32_t), s));
     keep64.emplace_back((size_t)(E + 1), s);
     int64_t* off = keep64.back().p;
@@ -476,16 +473,13 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       if (level_cycles) lc.n_front[2] = total[1];
     }
     const int64_t nl = lc.n_legs;
-    LegSink S{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
-    DBuf<int32_t> la, lb;
+    LegSink S{nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
+    DBuf<int4> legs;
     if (level_cycles) {
       const int64_t n2 = lc.n_front[2];
-      la = DBuf<int32_t>((size_t)std::max<int64_t>(n2, 1), s);
-      lb = DBuf<int32_t>((size_t)std::max<int64_t>(n2, 1), s);
-      S.la = la.p;
-      S.lb = lb.p;
+      legs = DBuf<int4>((size_t)std::max<int64_t>(n2, 1), s);
+      S.leg = legs.p;
       S.off2 = off2.p;
-      S.crng = crng.p;
     }
     DBuf<LegRec> rec;
     DBuf<uint32_t> hist;
@@ -624,14 +618,14 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     // 4. cycles of length >= 3: the cost-binned hybrid (heaviest anchors
     // level by level, the rest in one persistent launch beside them) ...
     if (wp.K >= 3 && persistent) {
-      cycles_hybrid(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, crng.p, la.p, lb.p,
+      cycles_hybrid(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, crng.p, anc.p, qwin.p, legs.p,
                     (mode & AML_MINE_LEARNED) != 0, s, branches ? g->side[2] : s);
     } else if (level_cycles && (mode & AML_MINE_FUSED)) {  // ... or all levels in one launch
-      level_cycle_search_fused(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, crng.p, ccl.p, qwin.p,
-                               la.p, lb.p, lc.n_front, s);
+      level_cycle_search_fused(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, anc.p, qwin.p, legs.p,
+                               lc.n_front, s);
     } else if (level_cycles) {  // ... or level by level from the legs
-      level_cycle_search(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, crng.p, ccl.p, qwin.p, la.p,
-                         lb.p, lc.n_front, s);
+      level_cycle_search(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, anc.p, qwin.p, legs.p,
+                         lc.n_front, s);
     }
     // the window's buffers (rec, hist, ...) are freed on s after this join
     if (sg_branch) branch_wait(g->branch_ev[3], s_sg, s);
