@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit(GraphView g, const int2* __
       ta = g.ts[a];
     }
   }
-  // legs before the cycle bound can start a cycle: they go to la/lb at
+  // legs before the cycle bound can start a cycle: their records go to S.leg at
   // off2[a] + their rank among a's legs
   int32_t qc = q0;
   int64_t o2 = 0;

@@ -83,8 +83,9 @@ struct __align__(16) LegRec {
   int32_t a, b;
 };
 
-// Where k_leg_emit writes the legs: (a, b) arrays for the cycle search
-// and/or records + bucket histogram for the SG grouping (null = not wanted).
+// Where k_leg_emit writes the legs: one {a, b, dst of b, t_b} record per
+// cycle-starting leg for the cycle search and/or records + bucket histogram
+// for the SG grouping (null = not wanted).
 struct LegSink {
   int4* leg;        // legs that can start a cycle (closing range not empty and the
                     // second edge before its last closing edge), compacted, as
@@ -118,8 +119,8 @@ struct SubWindows {
   CycleSlots cyc[MAX_SUB];            // CYC_k accumulator slots, k >= 3
 };
 
-// Frontier of the level-by-level cycle search: the base level is the legs
-// (la, lb) (base 2) or, for window cycles, the anchor edges la (base 1);
+// Frontier of the level-by-level cycle search: the base level is the leg
+// records leg (base 2) or, for window cycles, the anchor edges la (base 1);
 // element i of a level j above it extends element par[j][i] of level j-1 by
 // the out-slot slot[j][i].
 struct CycFrontier {
