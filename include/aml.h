@@ -192,6 +192,21 @@ typedef struct aml_stage {
                              /* instance credited to all of its edges           */
                              /* (Sec. 5: an edge "increments counts for all     */
                              /* pattern instances it participates in")          */
+#define AML_AGG_SETS 3       /* # distinct edge sets of the instances that      */
+                             /* contain the edge: bindings that find one set of */
+                             /* edges from other triggers or in another order   */
+                             /* of their stages count once.  Counted for the    */
+                             /* scatter-gather of n intermediaries, 2 <= n <= 7 */
+                             /* (the trigger s->m1, N1.out -> d after it, then  */
+                             /* n-1 intersections N0.out with N2.in, each leg   */
+                             /* in order (LEG), each intermediary skipping N1   */
+                             /* and the ones before, every stage in the span    */
+                             /* window, no amount constraints): the exact       */
+                             /* n-intermediary motif (Sec. 4's variable number  */
+                             /* of intermediaries), n legs with one source and  */
+                             /* one destination, on each of its 2n edges; n = 2 */
+                             /* is the SG column.  Any other program with this  */
+                             /* aggregate: AML_EUNSUPPORTED.                    */
 
 #define AML_PAT_INTERPRET 0x1  /* run the program through the generic        */
                                /* interpreter even when a family matches it    */

@@ -46,7 +46,7 @@ OP_TRIGGER, OP_FOR_ALL, OP_INTERSECT = 0, 1, 2
 DIR_OUT, DIR_IN = 0, 1
 ORD_NONE, ORD_AFTER, ORD_BEFORE, ORD_LEG, ORD_AFTER_TRIGGER = 0, 1, 2, 3, 4
 WIN_TRAILING, WIN_SPAN = 0, 1
-AGG_EDGES, AGG_DISTINCT, AGG_INSTANCES = 0, 1, 2
+AGG_EDGES, AGG_DISTINCT, AGG_INSTANCES, AGG_SETS = 0, 1, 2, 3
 AMT_RANGE, AMT_RATIO = 1, 2
 
 

@@ -7,6 +7,7 @@
  * skip excluded nodes, and credit every edge of every instance found.
  * Counts accumulate in uint64 and are clamped to 2^32-1 on output.
  */
+#define _GNU_SOURCE /* qsort_r */
 #include "aml_oracle.h"
 
 #include <omp.h>
@@ -625,6 +626,8 @@ typedef struct {
   int32_t* seen;               /* DISTINCT: last-stage nodes met so far */
   int64_t nseen, capseen;
   uint64_t* acc;               /* INSTANCES: this thread's credits, E entries */
+  int64_t* sets;               /* SETS: this thread's instances, each its    */
+  int64_t nsets, capsets;      /* edge ids sorted, nedges entries apiece      */
 } pg_ctx;
 
 /* the list of node u in direction dir, and the node at the far end of edge f */
@@ -671,8 +674,33 @@ static void pg_complete(pg_ctx* c, int32_t x_last) {
     for (int i = 0; i < c->nedges; ++i)
       for (int j = i + 1; j < c->nedges; ++j)
         if (c->edges[i] == c->edges[j]) return;
-    for (int i = 0; i < c->nedges; ++i) c->acc[c->edges[i]]++;
+    if (c->agg == OG_AGG_INSTANCES) {
+      for (int i = 0; i < c->nedges; ++i) c->acc[c->edges[i]]++;
+      return;
+    }
+    /* SETS: keep the instance's edge set (sorted ids); duplicates found
+     * from other triggers or in other orders are removed at the end */
+    if (c->nsets == c->capsets) {
+      c->capsets = c->capsets ? 2 * c->capsets : 64;
+      c->sets = (int64_t*)realloc(c->sets, (size_t)c->capsets * c->nedges * 8);
+    }
+    int64_t* r = c->sets + c->nsets * c->nedges;
+    for (int i = 0; i < c->nedges; ++i) {
+      int j = i;
+      for (; j > 0 && r[j - 1] > c->edges[i]; --j) r[j] = r[j - 1];
+      r[j] = c->edges[i];
+    }
+    c->nsets++;
   }
+}
+
+/* lexicographic order of two edge sets of *width ids */
+static int pg_cmp_set(const void* a, const void* b, void* width) {
+  const int64_t* x = (const int64_t*)a;
+  const int64_t* y = (const int64_t*)b;
+  for (int i = 0; i < *(const int*)width; ++i)
+    if (x[i] != y[i]) return x[i] < y[i] ? -1 : 1;
+  return 0;
 }
 
 /* node x passes the stage's out_var and skip_eq conditions */
@@ -791,7 +819,7 @@ static void pg_stage(pg_ctx* c, int si, int bound) {
 }
 
 static int pg_check(const og_stage* st, int32_t n, int32_t agg) {
-  if (n < 1 || n > OG_MAXST || agg < OG_AGG_EDGES || agg > OG_AGG_INSTANCES) return -1;
+  if (n < 1 || n > OG_MAXST || agg < OG_AGG_EDGES || agg > OG_AGG_SETS) return -1;
   if (st[0].op != OG_OP_TRIGGER || st[0].out_var != 1) return -1;
   for (int s = 0; s < n; ++s) {
     const uint32_t allowed = s == 0 ? OG_AMT_RANGE : (OG_AMT_RANGE | OG_AMT_RATIO);
@@ -825,6 +853,13 @@ int og_program_count(const og_graph* g, const og_stage* st, int32_t n, int32_t a
   const int64_t E = g->E;
   if (nthreads <= 0) nthreads = omp_get_max_threads();
   uint64_t* total = (uint64_t*)calloc((size_t)(E > 0 ? E : 1), 8);
+  /* SETS: every thread's instances, gathered; every binding of a program
+   * has the same number of edges: the trigger, one per FOR_ALL stage, two
+   * per INTERSECT stage */
+  int width = 1;
+  for (int s = 1; s < n; ++s) width += st[s].op == OG_OP_INTERSECT ? 2 : 1;
+  int64_t* all_sets = NULL;
+  int64_t n_all = 0;
 #pragma omp parallel num_threads(nthreads)
   {
     pg_ctx c;
@@ -860,7 +895,26 @@ int og_program_count(const og_graph* g, const og_stage* st, int32_t n, int32_t a
       for (int64_t e = 0; e < E; ++e) total[e] += c.acc[e];
       free(c.acc);
     }
+    if (agg == OG_AGG_SETS && c.nsets) {
+#pragma omp critical
+      {
+        all_sets = (int64_t*)realloc(all_sets, (size_t)(n_all + c.nsets) * width * 8);
+        memcpy(all_sets + n_all * width, c.sets, (size_t)c.nsets * width * 8);
+        n_all += c.nsets;
+      }
+    }
+    free(c.sets);
     free(c.seen);
+  }
+  if (agg == OG_AGG_SETS) {
+    /* sort the sets, then credit each distinct one to its edges once */
+    qsort_r(all_sets, (size_t)n_all, (size_t)width * 8, pg_cmp_set, &width);
+    for (int64_t i = 0; i < n_all; ++i) {
+      const int64_t* r = all_sets + i * width;
+      if (i > 0 && pg_cmp_set(r - width, r, &width) == 0) continue;
+      for (int k = 0; k < width; ++k) total[r[k]]++;
+    }
+    free(all_sets);
   }
   clamp_out(total, out, (size_t)E, 0xffffffffu);
   free(total);

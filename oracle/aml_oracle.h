@@ -101,6 +101,12 @@ int og_count_edges_limit(const og_graph* g, const og_col* cols, int32_t ncols,
  *   INSTANCES  a binding whose edges (e0 and all stages') are pairwise
  *              distinct is an instance, and adds 1 to the row of each of its
  *              edges (credited from every trigger it is found from).
+ *   SETS       the distinct edge sets of the instances: each set adds 1 to
+ *              the row of each of its edges, once, however many bindings
+ *              (triggers, orders of its stages) find it.  For the
+ *              scatter-gather of n intermediaries (n - 1 intersections, each
+ *              a further intermediary) a set is n legs with one source and
+ *              one destination: the exact n-intermediary motif.
  * Every family above is one such program; e.g. the chain of AFTER stages
  * closing on N0 counts CYC_k, and SG's program finds each pair of legs
  * twice (once from each scatter edge). */
@@ -109,7 +115,7 @@ enum { OG_DIR_OUT = 0, OG_DIR_IN = 1 };
 enum { OG_ORD_NONE = 0, OG_ORD_AFTER = 1, OG_ORD_BEFORE = 2, OG_ORD_LEG = 3,
        OG_ORD_AFTER_TRIGGER = 4 };
 enum { OG_WIN_TRAILING = 0, OG_WIN_SPAN = 1 };
-enum { OG_AGG_EDGES = 0, OG_AGG_DISTINCT = 1, OG_AGG_INSTANCES = 2 };
+enum { OG_AGG_EDGES = 0, OG_AGG_DISTINCT = 1, OG_AGG_INSTANCES = 2, OG_AGG_SETS = 3 };
 
 /* Amount constraints (edge attributes as operands): RANGE = every edge g of
  * the stage has amount_min <= amount(g) <= amount_max; RATIO = every edge

@@ -252,8 +252,10 @@ struct ProgStage {
 struct Prog {
   ProgStage st[PROG_MAX_STAGES];
   int32_t n;      // stages, trigger included
-  int32_t agg;    // AML_AGG_*
+  int32_t agg;    // AML_AGG_* (EDGES, DISTINCT or INSTANCES)
   int32_t delta;
+  int32_t div;    // INSTANCES counts are divided by it (exactly): the
+                  // bindings per instance set of an AML_AGG_SETS column
 };
 
 }  // namespace aml

@@ -232,7 +232,8 @@ __global__ void __launch_bounds__(512) k_gs_into(GraphView g, int32_t delta,
 // A leg (a, b) of a scatter-gather candidate is filed under its (source,
 // destination) pair s*N + d.  Pairs are spread over `nb` buckets by the top
 // bits of a 64-bit mix of the key (MurmurHash3's finalizer, Appleby), so a
-// bucket holds ~1.5K legs and every leg of one pair lands in one bucket.
+// bucket holds about the tuned mean of legs (at most 512 on average) and
+// every leg of one pair lands in one bucket.
 
 __device__ __forceinline__ uint64_t mix64(uint64_t k) {
   k ^= k >> 33;

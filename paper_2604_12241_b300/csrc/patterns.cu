@@ -90,6 +90,22 @@ std::vector<Template> templates() {
   return t;
 }
 
+// The scatter-gather of n intermediaries with the scatter edge as trigger:
+// N1.out -> N2 (the destination, after the trigger), then n - 1
+// intersections N0.out with N2.in, each a further intermediary skipping N1
+// and the intersections' intermediaries before it, each leg in order.
+std::vector<aml_stage> scatter_gather_n(int n) {
+  const int O = AML_DIR_OUT, I = AML_DIR_IN, SP = AML_WIN_SPAN;
+  std::vector<aml_stage> v{trigger(),
+                           st(AML_OP_FOR_ALL, 1, O, -1, 0, 2, AML_ORDER_AFTER, SP, 1u << 0)};
+  for (int i = 0; i < n - 1; ++i) {
+    uint32_t skip = 1u << 1;
+    for (int j = 0; j < i; ++j) skip |= 1u << (3 + j);
+    v.push_back(st(AML_OP_INTERSECT, 0, O, 2, I, 3 + i, AML_ORDER_LEG, SP, skip));
+  }
+  return v;
+}
+
 bool same_stage(const aml_stage& a, const aml_stage& b) {
   if (a.op != b.op || a.out_var != b.out_var) return false;
   if (a.amount_flags != b.amount_flags) return false;  // families have no amount constraints
@@ -113,7 +129,7 @@ void validate(const aml_pattern& pat, int p) {
   AML_REQUIRE(pat.delta >= 0, AML_EINVAL, where(p, 0) + "delta must be >= 0");
   AML_REQUIRE((pat.flags & ~AML_PAT_INTERPRET) == 0, AML_EINVAL,
               where(p, 0) + "unknown pattern flag bits");
-  AML_REQUIRE(pat.aggregate >= AML_AGG_EDGES && pat.aggregate <= AML_AGG_INSTANCES, AML_EINVAL,
+  AML_REQUIRE(pat.aggregate >= AML_AGG_EDGES && pat.aggregate <= AML_AGG_SETS, AML_EINVAL,
               where(p, 0) + "unknown aggregate");
   const aml_stage& t = pat.stages[0];
   AML_REQUIRE(t.op == AML_OP_TRIGGER && t.out_var == 1, AML_EINVAL,
@@ -172,6 +188,7 @@ static Prog interpretable(const aml_pattern& pat, int p) {
   g.n = pat.n_stages;
   g.agg = pat.aggregate;
   g.delta = pat.delta;
+  g.div = 1;
   for (int s = 0; s < pat.n_stages; ++s) {
     const aml_stage& x = pat.stages[s];
     AML_REQUIRE(!(x.op == AML_OP_FOR_ALL && x.order == AML_ORDER_LEG), AML_EUNSUPPORTED,
@@ -204,6 +221,31 @@ std::vector<Column> plan_patterns(const aml_pattern* pats, int n, std::vector<Pr
   for (int p = 0; p < n; ++p) {
     validate(pats[p], p);
     const aml_pattern& pat = pats[p];
+    if (pat.aggregate == AML_AGG_SETS) {
+      // the scatter-gather of n intermediaries: every set of n legs is found
+      // from each of its n scatter edges with the other n - 1 legs in every
+      // order of the intersections, n! bindings that all credit its 2n edges
+      // (the distinct intermediaries make the legs of a set of edges unique)
+      const int n_int = pat.n_stages - 1;
+      bool ok = n_int >= 2 && n_int <= PROG_MAX_STAGES - 1;
+      if (ok) {
+        const std::vector<aml_stage> t = scatter_gather_n(n_int);
+        for (int s = 0; s < pat.n_stages && ok; ++s) ok = same_stage(pat.stages[s], t[s]);
+      }
+      AML_REQUIRE(ok, AML_EUNSUPPORTED,
+                  where(p, 0) + "AML_AGG_SETS is counted for the scatter-gather of n "
+                                "intermediaries (2 <= n <= 7) only");
+      if (n_int == 2 && !(pat.flags & AML_PAT_INTERPRET)) {
+        cols.push_back(Column{AML_FAM_SG, 0, pat.delta});  // a set of two legs: an SG pair
+        continue;
+      }
+      Prog g = interpretable(pat, p);
+      g.agg = AML_AGG_INSTANCES;
+      for (int i = 2; i <= n_int; ++i) g.div *= i;
+      progs->push_back(g);
+      cols.push_back(Column{AML_FAM_PROGRAM, 0, pat.delta, (int32_t)progs->size() - 1});
+      continue;
+    }
     int fam = -1, k = 0;
     for (const Template& t : tpl) {
       if (pat.flags & AML_PAT_INTERPRET) break;

@@ -365,6 +365,13 @@ __global__ void __launch_bounds__(PROG_BLOCK) k_program_warp(GraphView g, const 
   }
 }
 
+// v[i] / d for counts that are exact multiples of d (the bindings of an
+// instance set each credit it once)
+__global__ void k_div_exact(unsigned long long* __restrict__ v, int64_t n, uint32_t d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] /= d;
+}
+
 __global__ void k_sum_u64(const unsigned long long* __restrict__ v, int64_t n,
                           unsigned long long* __restrict__ total) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -407,6 +414,9 @@ void run_program(const GraphView& gv, const float* amount, const Prog& p,
   };
   if (p.agg == AML_AGG_INSTANCES) {
     pass(std::integral_constant<int, AGG_CREDIT>{}, nullptr, 0);
+    if (p.div > 1)
+      AML_LAUNCH("k_div_exact", s,
+                 k_div_exact<<<grid_for(E, 256), 256, 0, s>>>(out, E, (uint32_t)p.div));
   } else if (p.agg == AML_AGG_EDGES) {
     pass(std::integral_constant<int, AGG_COUNT>{}, nullptr, 0);
   } else {

@@ -15,7 +15,7 @@ OP_TRIGGER, OP_FOR_ALL, OP_INTERSECT = 0, 1, 2
 DIR_OUT, DIR_IN = 0, 1
 ORDER_NONE, ORDER_AFTER, ORDER_BEFORE, ORDER_LEG, ORDER_AFTER_TRIGGER = 0, 1, 2, 3, 4
 WIN_TRAILING, WIN_SPAN = 0, 1
-AGG_EDGES, AGG_DISTINCT, AGG_INSTANCES = 0, 1, 2
+AGG_EDGES, AGG_DISTINCT, AGG_INSTANCES, AGG_SETS = 0, 1, 2, 3
 AMT_RANGE, AMT_RATIO = 1, 2
 FAM_NAMES = {0: "DEG_OUT", 1: "DEG_IN", 2: "FAN_OUT", 3: "FAN_IN", 4: "GS", 5: "SG", 6: "CYC",
              7: "CYCW", 8: "PROGRAM"}
@@ -154,6 +154,18 @@ def scatter_gather_n(n: int, delta: int) -> Pattern:
                             order=ORDER_LEG, window=WIN_SPAN,
                             skip_eq=_skip(1, *range(3, 3 + i))))
     return Pattern(tuple(stages), AGG_INSTANCES, delta, f"SG{n}@{delta}", interpret=True)
+
+
+def scatter_gather_exact(n: int, delta: int, interpret: bool = False) -> Pattern:
+    """Exact-size scatter-gather bins: the scatter-gather program of n
+    intermediaries with the SETS aggregate, which counts every set of n legs
+    (one source, one destination, pairwise distinct intermediaries, each leg
+    in order, all 2n edges within delta) once on each of its 2n edges.
+    n = 2 is the SG column (mined by the SG family unless ``interpret``);
+    larger n run through the interpreter, whose ordered count holds every
+    set n! times and is divided by it."""
+    p = scatter_gather_n(n, delta)
+    return Pattern(p.stages, AGG_SETS, delta, f"SG{n}_EXACT@{delta}", interpret=interpret)
 
 
 def gather_scatter_n(n_in: int, n_out: int, delta: int) -> Pattern:

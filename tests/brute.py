@@ -179,7 +179,8 @@ def _amount_rule(st):
 def brute_program(src, dst, ts, stages, aggregate: int, delta: int, amount=None) -> np.ndarray:
     """A stage program's counts by enumerating every tuple of edges for the
     program's edge slots (one per FOR_ALL stage, two per INTERSECT stage) and
-    testing the definition on each; no neighbour lists.  uint64 [E]."""
+    testing the definition on each; no neighbour lists.  aggregate 3 (SETS)
+    credits each distinct edge set of the instances once.  uint64 [E]."""
     src = [int(x) for x in src]
     dst = [int(x) for x in dst]
     ts = [int(x) for x in ts]
@@ -207,6 +208,7 @@ def brute_program(src, dst, ts, stages, aggregate: int, delta: int, amount=None)
     def before(f, e):
         return _prec(ts, f, e)
 
+    sets = set()  # SETS: the distinct edge sets of the instances
     for e0 in valid:
         if not amount_ok(rules[0], e0, e0):  # the trigger's range (no ratio on it)
             continue
@@ -277,10 +279,16 @@ def brute_program(src, dst, ts, stages, aggregate: int, delta: int, amount=None)
             elif aggregate == 1:
                 lasts.add(x_last)
             elif len(set(edges)) == len(edges):
-                for g in edges:
-                    out[g] += 1
+                if aggregate == 3:
+                    sets.add(frozenset(edges))
+                else:
+                    for g in edges:
+                        out[g] += 1
         if aggregate == 0:
             out[e0] = n_bind
         elif aggregate == 1:
             out[e0] = len(lasts)
+    for inst in sets:
+        for g in inst:
+            out[g] += 1
     return out

@@ -2,6 +2,7 @@
 include/aml.h declares, and its host-only logic (status strings, stage-program
 validation and planning, argument checks) behaves as documented."""
 import ctypes
+import dataclasses
 import os
 import re
 
@@ -118,6 +119,24 @@ def test_planner_reports_programs_beyond_the_interpreter():
     arr[0].flags = 0x6
     h = ctypes.c_void_p()
     assert _lib.lib().aml_pattern_set_create(arr, 1, ctypes.byref(h)) == 1
+
+
+def test_planner_counts_sets_for_scatter_gathers_of_n_intermediaries_only():
+    T = P.TRIGGER
+    ps = _ps([P.scatter_gather_exact(2, 10), P.scatter_gather_exact(2, 10, interpret=True),
+              P.scatter_gather_exact(3, 10), P.scatter_gather_exact(7, 10)])
+    assert [c["family"] for c in ps.columns] == [5, 8, 8, 8]   # SG, then interpreted
+    # SETS of another program, or of a scatter-gather with amount constraints
+    # or a missing skip, has no definition here
+    assert _err([P.Pattern(P.gather_scatter(10).stages, P.AGG_SETS, 10)]) == "AML_EUNSUPPORTED"
+    assert "AML_AGG_SETS" in _lib.lib().aml_last_error().decode()
+    st = list(P.scatter_gather_n(3, 10).stages)
+    st[3] = dataclasses.replace(st[3], skip_eq=0b10)
+    assert _err([P.Pattern(tuple(st), P.AGG_SETS, 10)]) == "AML_EUNSUPPORTED"
+    st = list(P.scatter_gather_n(3, 10).stages)
+    st[2] = dataclasses.replace(st[2], amount_flags=1, amount_min=0.0, amount_max=5.0)
+    assert _err([P.Pattern(tuple(st), P.AGG_SETS, 10)]) == "AML_EUNSUPPORTED"
+    assert _err([P.Pattern((T,), P.AGG_SETS, 10)]) == "AML_EUNSUPPORTED"
 
 
 def test_argument_errors_need_no_device():

@@ -216,3 +216,45 @@ def test_programs_in_every_cycle_mode():
     graph.close()
     np.testing.assert_array_equal(outs[1], outs[0])
     np.testing.assert_array_equal(outs[2], outs[0])
+
+
+def _exact_sg(delta):
+    """Exact-size scatter-gather bins: n = 2 by the SG family and through the
+    interpreter, n = 3 and 4 through the interpreter (ordered count / n!)."""
+    return [P.scatter_gather_exact(2, delta), P.scatter_gather_exact(2, delta, interpret=True),
+            P.scatter_gather_exact(3, delta), P.scatter_gather_exact(4, delta)]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_exact_size_scatter_gathers_match_oracle_on_tiny_graphs(seed):
+    """The SETS columns against the oracle's distinct edge sets, on dense
+    small graphs with ties, parallel edges and self-loops."""
+    rng = np.random.default_rng(600 + seed)
+    n, E = 7 + seed, 90 + 20 * seed
+    src = rng.integers(0, n, E).astype(np.int32)
+    dst = rng.integers(0, n, E).astype(np.int32)
+    ts = rng.integers(0, 40, E).astype(np.int32)
+    from types import SimpleNamespace
+    g = SimpleNamespace(src=src, dst=dst, ts=ts, n_nodes=n)
+    og = oracle.OracleGraph(src, dst, ts, n)
+    reached = 0
+    for delta in (3, 8, 40):
+        pats = _exact_sg(delta)
+        got = _mine(g, pats)
+        for j, p in enumerate(pats):
+            want = og.program_count(_tuples(p), oracle.AGG_SETS, delta, threads=4)
+            np.testing.assert_array_equal(got[:, j], want, err_msg=f"{p.name}, delta {delta}")
+        reached += int((got[:, 3] > 0).sum())
+    assert reached > 0  # 4-intermediary motifs occur
+
+
+def test_exact_size_scatter_gathers_match_oracle_on_tiny10k():
+    g = aml_synth.workload("tiny-10k")
+    og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
+    pats = _exact_sg(P.DAY) + P.standard(P.DAY)
+    got = _mine(g, pats)
+    for j, p in enumerate(pats[:4]):
+        want = og.program_count(_tuples(p), oracle.AGG_SETS, p.delta)
+        np.testing.assert_array_equal(got[:, j], want, err_msg=p.name)
+        assert want.any(), p.name
+    np.testing.assert_array_equal(got[:, 4:], og.count_all(oracle_columns(P.standard(P.DAY))))

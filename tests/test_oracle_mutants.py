@@ -175,3 +175,50 @@ def test_amount_pins_reject_mutant(tmp_path, name, orig, mutated):
 
 def test_unmutated_oracle_passes_amount_pins():
     assert not _amount_pins_reject(oracle._load())
+
+
+# mistakes in the SETS aggregate (distinct edge sets of the instances),
+# caught by the brute-force set pins
+SETS_MUTANTS = [
+    ("sets-no-dedupe", "      if (i > 0 && pg_cmp_set(r - width, r, &width) == 0) continue;\n", ""),
+    ("sets-unsorted", "      for (; j > 0 && r[j - 1] > c->edges[i]; --j) r[j] = r[j - 1];\n", ""),
+    ("sets-compare-short", "  for (int i = 0; i < *(const int*)width; ++i)",
+     "  for (int i = 0; i + 1 < *(const int*)width; ++i)"),
+    ("sets-repeat-edges", "        if (c->edges[i] == c->edges[j]) return;\n", ""),
+]
+
+
+def _sets_pins_reject(lib) -> bool:
+    from paper_2604_12241_b300 import patterns as P
+    import dataclasses
+    programs = [NOVEL["fan_pairs"][0], NOVEL["common_out"][0], NOVEL["path3"][0]]
+    programs += [[dataclasses.astuple(s) for s in P.scatter_gather_n(n, 0).stages] for n in (2, 3)]
+    for seed in range(6):
+        n = 3 + seed % 4
+        g = aml_synth.tiny_random(n, 12 + seed % 3, 8 + seed % 5, 900 + seed,
+                                  self_loops=(seed % 2 == 0))
+        og = oracle.OracleGraph(g.src, g.dst, g.ts, n, lib=lib)
+        for stages in programs:
+            for delta in (3, 1000):
+                want = brute_program(g.src, g.dst, g.ts, stages, oracle.AGG_SETS, delta)
+                got = og.program_count(stages, oracle.AGG_SETS, delta, threads=1)
+                if not np.array_equal(got, want):
+                    return True
+    return False
+
+
+@pytest.mark.parametrize("name,orig,mutated", SETS_MUTANTS, ids=[m[0] for m in SETS_MUTANTS])
+def test_sets_pins_reject_mutant(tmp_path, name, orig, mutated):
+    text = open(SRC).read()
+    assert text.count(orig) == 1, f"mutation site for {name} not unique"
+    path = tmp_path / "mutant.c"
+    path.write_text(text.replace(orig, mutated))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-I", os.path.dirname(SRC), "-o", str(so), str(path)])
+    lib = oracle.load_library(str(so))
+    assert _sets_pins_reject(lib), f"mutant {name} survived the set pins"
+
+
+def test_unmutated_oracle_passes_sets_pins():
+    assert not _sets_pins_reject(oracle._load())

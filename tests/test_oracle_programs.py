@@ -282,3 +282,71 @@ def test_exact_size_scatter_gather_is_the_at_least_program_over_k_factorial(k):
                                           want * np.uint64(math.factorial(k)))
             checked += int((want > 0).sum())
     assert checked > 20
+
+
+# ---- the SETS aggregate: each distinct edge set of the instances once ----
+
+_SETS_NOVEL = ("path3", "gs_any_order", "common_out", "fan_pairs", "leg_triangle", "closing_in")
+
+
+def _sets_cases():
+    cases = {name: NOVEL[name][0] for name in _SETS_NOVEL}
+    for n in (2, 3):
+        cases[f"sg{n}"] = _tuples(P.scatter_gather_n(n, 0))
+    return cases
+
+
+@pytest.mark.parametrize("name", sorted(_sets_cases()))
+def test_sets_aggregate_matches_brute_force(name):
+    """SETS credits every distinct edge set of the program's instances once,
+    whichever triggers and stage orders find it (brute force over raw edge
+    tuples, collecting the sets)."""
+    stages = _sets_cases()[name]
+    width = sum(1 if s[0] == 1 else 2 for s in stages[1:])
+    for seed in range(10 if width <= 2 else 5):
+        n = 3 + seed % 4
+        E = (13 if width <= 2 else 10) + seed % 4
+        g = aml_synth.tiny_random(n, E, 8 + seed % 6, 7000 + seed, self_loops=(seed % 3 == 0))
+        og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
+        for delta in (0, 3, 1000):
+            want = brute_program(g.src, g.dst, g.ts, stages, oracle.AGG_SETS, delta)
+            got = og.program_count(stages, oracle.AGG_SETS, delta, threads=2)
+            np.testing.assert_array_equal(got, want, err_msg=f"{name}, seed {seed}, delta {delta}")
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_sets_of_the_k_intermediary_program_is_the_exact_motif(k):
+    """Exact-size bins as a column: the SETS aggregate of the k-intermediary
+    scatter-gather program counts every set of k legs (one source, one
+    destination, pairwise distinct intermediaries, each leg in order, all 2k
+    edges within delta) once on each of its edges: the raw-edge brute force
+    of exact k-intermediary motifs."""
+    pat = P.scatter_gather_n(k, 0)
+    checked = 0
+    for seed in range(10):
+        rng = np.random.default_rng(5000 + seed)
+        n, E = (5, 24 + seed % 8) if k < 4 else (6, 48 + seed % 6)
+        src = rng.integers(0, n, E).astype(np.int32)
+        dst = rng.integers(0, n, E).astype(np.int32)
+        ts = rng.integers(0, 7, E).astype(np.int32)
+        og = oracle.OracleGraph(src, dst, ts, n)
+        for delta in (2, 6):
+            got = og.program_count(_tuples(pat), oracle.AGG_SETS, delta, threads=1)
+            want = _brute_sg_sets(src, dst, ts, k, delta)
+            np.testing.assert_array_equal(got.astype(np.uint64), want)
+            checked += int((want > 0).sum())
+    assert checked > 20
+
+
+def test_sets_of_two_intermediaries_is_the_sg_column():
+    """The 2-intermediary set is an SG instance (an unordered pair of legs):
+    the SETS aggregate of that program equals the oracle's SG family
+    column, which its separate enumeration computes (pinned by brute force)."""
+    for seed, delta in ((1, 20), (2, 60), (3, 1000)):
+        g = aml_synth.tiny_random(12, 400, 200, 8100 + seed, self_loops=(seed == 2))
+        og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
+        pat = P.scatter_gather_n(2, delta)
+        got = og.program_count(_tuples(pat), oracle.AGG_SETS, delta)
+        want = og.count_all([("sg", delta)])[:, 0]
+        assert want.sum() > 0
+        np.testing.assert_array_equal(got, want)
