@@ -751,8 +751,8 @@ __device__ __forceinline__ uint32_t sg_span32(const int4& r, const int4& o, int3
 }
 
 // partners of `own` among group entries [j0, j1), per window, credited to
-// the leg's two edges
-template <int NS>
+// the leg's two edges (DC: delta counting, pairs need a new gather edge)
+template <int NS, bool DC>
 __device__ __forceinline__ void sg_count_partners(const int4* grp, uint32_t j0, uint32_t j1,
                                                   const int4& own, int32_t a,
                                                   int32_t delta, int32_t new_from,
@@ -760,7 +760,7 @@ __device__ __forceinline__ void sg_count_partners(const int4* grp, uint32_t j0, 
                                                   const SubWindows& sub) {
   uint32_t k = 0, ks[NS > 0 ? NS : 1] = {};  // at most CAP partners
   for (uint32_t j = j0; j < j1; ++j) {
-    const uint32_t span = sg_span32(own, grp[j], new_from);
+    const uint32_t span = sg_span32(own, grp[j], DC ? new_from : 0);
     if (span > (uint32_t)delta) continue;
     ++k;
 #pragma unroll
@@ -788,6 +788,14 @@ __device__ __forceinline__ uint32_t slot_hash(uint64_t key) {
 // table is needed.  Then the grouped legs' data are filed group by group
 // and consecutive threads take consecutive group members (a warp's threads
 // mostly walk the same group).
+// Groups are laid out by size class (2-4, 5-16, 17-64, more legs), so that
+// the threads of a warp, which take consecutive group entries and walk
+// their own group, walk groups of about one length.
+constexpr int SG_CLASSES = 4;
+__device__ __forceinline__ int sg_class(uint32_t c) {
+  return c <= 4 ? 0 : c <= 16 ? 1 : c <= 64 ? 2 : 3;
+}
+
 template <int CAP, int TAB>
 struct SgSmem {
   int4 grp[CAP];                 // leg_info of grouped legs, by group
@@ -796,6 +804,7 @@ struct SgSmem {
   unsigned long long key[TAB];   // filed keys; later (as uint32) group cursors
   uint32_t cnt[TAB];             // records per slot
   uint32_t n_grouped;
+  uint32_t cls_n[SG_CLASSES];    // grouped legs per size class, then the class's start
   uint32_t n_big;                // groups counted by sorting (sg_sorted_group)
   uint32_t n_valid;              // legs within the window being counted there
   uint32_t big_start[CAP / 64], big_n[CAP / 64];
@@ -957,10 +966,8 @@ __device__ __forceinline__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRe
     S.key[t] = ~0ull;
     S.cnt[t] = 0;
   }
-  if (threadIdx.x == 0) {
-    S.n_grouped = 0;
-    S.n_big = 0;
-  }
+  if (threadIdx.x < SG_CLASSES) S.cls_n[threadIdx.x] = 0;
+  if (threadIdx.x == 0) S.n_big = 0;
   __syncthreads();
   // file every record under its key; remember which keys this thread filed
   uint32_t lead = 0;
@@ -987,24 +994,37 @@ __device__ __forceinline__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRe
     atomicAdd(&S.cnt[q], 1u);
   }
   __syncthreads();
-  // group leaders reserve their group's range (keys are no longer read)
+  // group leaders reserve their group's range inside its size class (keys
+  // are no longer read); the classes' starts follow
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     if (threadIdx.x + k * BS >= n) break;
     if ((lead >> k) & 1u) {
       const uint32_t c = S.cnt[h[k]];
-      if (c >= 2) cur[h[k]] = atomicAdd(&S.n_grouped, c);
+      if (c >= 2) cur[h[k]] = atomicAdd(&S.cls_n[sg_class(c)], c);
     }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t at = 0;
+    for (int q = 0; q < SG_CLASSES; ++q) {
+      const uint32_t m = S.cls_n[q];
+      S.cls_n[q] = at;
+      at += m;
+    }
+    S.n_grouped = at;
   }
   __syncthreads();
   const uint32_t n_grouped = S.n_grouped;
   if (n_grouped == 0) return;
-  // the grouped legs' data, group by group (cursor ends at the group's end)
+  // the grouped legs' data, group by group (cursor ends at the group's end
+  // within its class)
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     if (threadIdx.x + k * BS >= n) break;
-    if (S.cnt[h[k]] >= 2) {
-      const uint32_t at = atomicAdd(&cur[h[k]], 1u);
+    const uint32_t c = S.cnt[h[k]];
+    if (c >= 2) {
+      const uint32_t at = S.cls_n[sg_class(c)] + atomicAdd(&cur[h[k]], 1u);
       S.grp[at] = leg_info(r[k], dst, ts);
       S.ga[at] = r[k].a;
       S.gslot[at] = h[k];
@@ -1015,7 +1035,7 @@ __device__ __forceinline__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRe
   for (uint32_t p = threadIdx.x; p < n_grouped; p += BS) {
     const uint32_t q = S.gslot[p];
     const uint32_t c = S.cnt[q];
-    const uint32_t end = cur[q];
+    const uint32_t end = S.cls_n[sg_class(c)] + cur[q];
     if (sort_big && c > SG_SORT_MIN) {  // listed by its first entry, counted below
       if (p == end - c) {
         const uint32_t k = atomicAdd(&S.n_big, 1u);
@@ -1024,7 +1044,11 @@ __device__ __forceinline__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRe
       }
       continue;
     }
-    sg_count_partners<NS>(S.grp, end - c, end, S.grp[p], S.ga[p], delta, new_from, acc, sub);
+    if (new_from > 0)
+      sg_count_partners<NS, true>(S.grp, end - c, end, S.grp[p], S.ga[p], delta, new_from, acc,
+                                  sub);
+    else
+      sg_count_partners<NS, false>(S.grp, end - c, end, S.grp[p], S.ga[p], delta, 0, acc, sub);
   }
   if (!sort_big) return;
   __syncthreads();  // the table's space becomes the sort buffers
