@@ -1030,25 +1030,83 @@ __device__ __forceinline__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRe
       S.gslot[at] = h[k];
     }
   }
-  __syncthreads();
   const bool sort_big = SORT_BIG && new_from == 0;
-  for (uint32_t p = threadIdx.x; p < n_grouped; p += BS) {
-    const uint32_t q = S.gslot[p];
-    const uint32_t c = S.cnt[q];
-    const uint32_t end = S.cls_n[sg_class(c)] + cur[q];
-    if (sort_big && c > SG_SORT_MIN) {  // listed by its first entry, counted below
-      if (p == end - c) {
-        const uint32_t k = atomicAdd(&S.n_big, 1u);
-        S.big_start[k] = end - c;
-        S.big_n[k] = c;
-      }
-      continue;
+  if constexpr (NS <= 1 && 2 * CAP <= TAB) {
+    // Every unordered pair once: entry i of a group of c walks the entries
+    // 1 .. (c-1)/2 places after it, cyclically (and, for even c, the lower
+    // half also the one c/2 places on), so a group's threads walk about
+    // (c-1)/2 entries each; a pair within a window adds 1 to both entries'
+    // counters (the key array's upper half: the cursors use its lower half).
+    uint32_t* pk0 = cur + TAB;  // partners within delta
+    uint32_t* pk1 = pk0 + CAP;  // partners within the sub-window
+    // (the filed entries and the final cursors are read after the barrier
+    // below; the counters lie outside both)
+    for (uint32_t p = threadIdx.x; p < n_grouped; p += BS) {
+      pk0[p] = 0;
+      pk1[p] = 0;
     }
-    if (new_from > 0)
-      sg_count_partners<NS, true>(S.grp, end - c, end, S.grp[p], S.ga[p], delta, new_from, acc,
-                                  sub);
-    else
-      sg_count_partners<NS, false>(S.grp, end - c, end, S.grp[p], S.ga[p], delta, 0, acc, sub);
+    __syncthreads();
+    const uint32_t d1 = NS > 0 && sub.n > 0 ? (uint32_t)sub.delta[0] : 0u;
+    for (uint32_t p = threadIdx.x; p < n_grouped; p += BS) {
+      const uint32_t q = S.gslot[p];
+      const uint32_t c = S.cnt[q];
+      const uint32_t g0 = S.cls_n[sg_class(c)] + cur[q] - c;
+      if (sort_big && c > SG_SORT_MIN) {  // listed by its first entry, counted below
+        if (p == g0) {
+          const uint32_t k = atomicAdd(&S.n_big, 1u);
+          S.big_start[k] = g0;
+          S.big_n[k] = c;
+        }
+        continue;
+      }
+      const int4 own = S.grp[p];
+      const uint32_t i = p - g0;
+      const uint32_t steps = (c - 1) / 2 + ((c & 1u) == 0 && i < c / 2 ? 1u : 0u);
+      uint32_t k0 = 0, k1 = 0;
+      uint32_t j = i;
+      for (uint32_t t = 0; t < steps; ++t) {
+        if (++j == c) j = 0;
+        const uint32_t span = sg_span32(own, S.grp[g0 + j], new_from);
+        if (span > (uint32_t)delta) continue;
+        ++k0;
+        atomicAdd(&pk0[g0 + j], 1u);
+        if (NS > 0 && span <= d1) {
+          ++k1;
+          atomicAdd(&pk1[g0 + j], 1u);
+        }
+      }
+      if (k0) atomicAdd(&pk0[p], k0);
+      if (k1) atomicAdd(&pk1[p], k1);
+    }
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < n_grouped; p += BS) {
+      const uint32_t c = S.cnt[S.gslot[p]];
+      if (sort_big && c > SG_SORT_MIN) continue;
+      const int32_t a = S.ga[p], b = S.grp[p].w;
+      if (acc) sg_credit(acc, a, b, pk0[p]);
+      if (NS > 0 && sub.n > 0 && sub.sg[0]) sg_credit(sub.sg[0], a, b, pk1[p]);
+    }
+  } else {
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < n_grouped; p += BS) {
+      const uint32_t q = S.gslot[p];
+      const uint32_t c = S.cnt[q];
+      const uint32_t end = S.cls_n[sg_class(c)] + cur[q];
+      if (sort_big && c > SG_SORT_MIN) {  // listed by its first entry, counted below
+        if (p == end - c) {
+          const uint32_t k = atomicAdd(&S.n_big, 1u);
+          S.big_start[k] = end - c;
+          S.big_n[k] = c;
+        }
+        continue;
+      }
+      if (new_from > 0)
+        sg_count_partners<NS, true>(S.grp, end - c, end, S.grp[p], S.ga[p], delta, new_from,
+                                    acc, sub);
+      else
+        sg_count_partners<NS, false>(S.grp, end - c, end, S.grp[p], S.ga[p], delta, 0, acc,
+                                     sub);
+    }
   }
   if (!sort_big) return;
   __syncthreads();  // the table's space becomes the sort buffers
