@@ -230,9 +230,18 @@ def algorithmic_bytes(kernel: str, E: int, Ev: int, pats, stats: dict) -> float:
     """Bytes per launch the kernel's definition must move (no probes, no re-reads).
 
     stats: the leg pass's window sizes (aml_graph_window_stats of the largest
-    window: every smaller window is counted inside its pass): legs = temporal
-    2-paths, front[j] = cycle-search paths of j edges.  A kernel launched once
-    per level reports the mean over its launches.
+    window with GS, SG or cycle columns: every smaller window is counted
+    inside its pass): legs = temporal 2-paths, front[j] = cycle-search paths
+    of j edges.  A kernel launched once per level reports the mean over its
+    launches.  None for a kernel without a byte model.
+      k_leg_count     per edge: src, dst, ts (12 B), its leg window's bounds and
+                      leg count written (12 B); with cycle columns the anchor's
+                      latest closing edge read (8 B) and the cycle-capable count
+                      and bound written (8 B); per SG/CYC column one uint64
+                      accumulator cleared (8 B); per GS column the gather-side
+                      count cleared (4 B)
+      k_close_range   per edge: src, dst, ts (12 B), its closing range and the
+                      range's latest edge written (16 B)
       k_assemble      per edge: src, dst (8 B); per window and direction with
                       DEG/FAN columns one (DEG, FAN) pair (8 B); per GS column
                       the two leg counts (8 B); per SG/CYC column one uint64
@@ -278,7 +287,12 @@ def algorithmic_bytes(kernel: str, E: int, Ev: int, pats, stats: dict) -> float:
         return Ev * (8 + 16 * W)
     if kernel == "k_cyc_level" and front:
         return 8.0 * sum(front.values()) / len(front)
-    return float("nan")
+    if kernel == "k_leg_count":
+        cyc = any(f.startswith("CYC") and not f.startswith("CYCW") for f in fam)
+        return E * (12 + 12 + (16 if cyc else 0) + 8 * n_acc + 4 * n_gs)
+    if kernel == "k_close_range":
+        return E * (12 + 16)
+    return None
 
 
 def time_window_cycles(graph, pats, E, use_graph, stream, flush, reps=5) -> dict:
@@ -678,17 +692,27 @@ def profiled_mines(graph, ps, out, stream, flush, mode, n) -> tuple:
     return total, _lib.profile_read(reset=True)
 
 
+def leg_pass_window(pats) -> int:
+    """The window whose leg pass counts every GS, SG and cycle column (the
+    largest such window; the smaller ones are counted inside its pass), or
+    the largest window when no column needs legs."""
+    fam_of = [(p.name.split("@")[0], int(p.name.split("@")[1])) for p in pats]
+    legs = [d for f, d in fam_of
+            if f == "GS" or f.startswith("SG") or (f.startswith("CYC") and not f.startswith("CYCW"))]
+    return max(legs) if legs else max(d for _, d in fam_of)
+
+
 def roofline_of(prof, total_ms, graph, pats, E, Ev) -> dict:
     """The dominant kernel's HBM roofline: algorithmic bytes per launch over
     its mean launch time (CUDA events), against the measured copy
     bandwidth."""
     dom_name, (dom_n, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    big = max(int(p.name.split("@")[1]) for p in pats)
+    big = leg_pass_window(pats)
     ws_stats = graph.window_stats(big)
     stats = {"legs": ws_stats["n_legs"], "front": ws_stats["n_front"]}
     peak, peak_src = measured_peak()
     alg = algorithmic_bytes(dom_name, E, Ev, pats, stats)
-    achieved = alg / (dom_ms / dom_n / 1000.0) / 1e9 if alg == alg else None
+    achieved = alg / (dom_ms / dom_n / 1000.0) / 1e9 if alg is not None else None
     return {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
             "peak_source": peak_src, "launch_ms": dom_ms / dom_n,
