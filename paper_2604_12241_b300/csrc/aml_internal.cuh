@@ -154,6 +154,7 @@ struct aml_graph {
   int32_t* dst = nullptr;
   int32_t* ts = nullptr;
   float* amount = nullptr;
+  int2* dts = nullptr;  // [E] (dst, ts) of every edge: one gather for both
   aml::Adj out, in;
   uint32_t* err = nullptr;  // device error word
   int64_t bytes = 0;

@@ -11,6 +11,7 @@
 #include <cstring>
 
 #include "aml_internal.cuh"
+#include "mine.cuh"
 #include "profile.cuh"
 
 namespace aml {
@@ -217,6 +218,9 @@ aml_graph* build_graph(const int32_t* src, const int32_t* dst, const int32_t* ts
       in(g->ts, ts);
       if (amount) in(g->amount, amount);
       else AML_CUDA(cudaMemsetAsync(g->amount, 0, E * 4, s));
+      g->dts = ga.get<int2>(E);
+      AML_LAUNCH("k_pack_dst_ts", s,
+                 k_pack_dst_ts<<<grid_for(E, 256), 256, 0, s>>>(g->dst, g->ts, E, g->dts));
     }
     AML_CUDA(cudaMemsetAsync(g->err, 0, 16, s));
     DBuf<unsigned long long> scal(4, s);
@@ -640,6 +644,9 @@ aml_graph* update_graph(const aml_graph* o, int64_t drop, const int32_t* src, co
       copy_d2d(g->ts, ts, E * 4, s);
       if (amount) copy_d2d(g->amount, amount, E * 4, s);
       else AML_CUDA(cudaMemsetAsync(g->amount, 0, E * 4, s));
+      g->dts = ga.get<int2>(E);
+      AML_LAUNCH("k_pack_dst_ts", s,
+                 k_pack_dst_ts<<<grid_for(E, 256), 256, 0, s>>>(g->dst, g->ts, E, g->dts));
     }
     AML_CUDA(cudaMemsetAsync(g->err, 0, 16, s));
     g->max_deg = ga.get<int32_t>(2);

@@ -138,6 +138,7 @@ __device__ __forceinline__ int32_t cycle_bound(const GraphView& g, int2 cr, int2
 // qcb[a] = its cycle bound, kept for the emission.
 // Z: the accumulators the emission and later kernels add into, zeroed here
 // (element a of each) instead of by separate memsets.
+constexpr int LEG_SCAN = 4;  // windows up to this many slots are scanned, not searched
 template <int NS>
 __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
                                                    int32_t* __restrict__ L,
@@ -174,6 +175,60 @@ __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
   int32_t q0, q1;
   after_edge_upto(g.ot, g.oeid, hs, he, ta, a, (int64_t)ta + delta, q0, q1);
   qwin[a] = make_int2(q0, q1);
+  const int32_t n = q1 - q0;
+  if (n <= LEG_SCAN) {
+    // a short window (most are): its slots are read at once and every count
+    // is taken from them -- the returns h -> x are the slots whose
+    // counterparty is x -- with no search of the (nbr, t, id) copy
+    const bool need_id = g.new_from > 0 || L2 != nullptr;
+    int32_t y[LEG_SCAN], tq[LEG_SCAN], iq[LEG_SCAN];
+#pragma unroll
+    for (int k = 0; k < LEG_SCAN; ++k) {
+      y[k] = k < n ? __ldg(g.onbr + q0 + k) : -1;
+      tq[k] = k < n ? __ldg(g.ot + q0 + k) : 0;
+      iq[k] = k < n && need_id ? __ldg(g.oeid + q0 + k) : 0;
+    }
+    int32_t back = 0;
+#pragma unroll
+    for (int k = 0; k < LEG_SCAN; ++k) back += y[k] == x ? 1 : 0;
+    L[a] = n - back;
+    // delta counting: a slot is new when it comes after (t_new, new_from - 1)
+    auto is_new = [&](int k) {
+      return g.new_from == 0 || before(g.t_new, g.new_from - 1, tq[k], iq[k]);
+    };
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+      if (i < sub.n && sub.gs_from[i]) {
+        const int64_t tmax = (int64_t)ta + sub.delta[i];
+        int32_t c = 0;
+#pragma unroll
+        for (int k = 0; k < LEG_SCAN; ++k)
+          if (k < n && (int64_t)tq[k] <= tmax && is_new(k) && y[k] != x) ++c;
+        sub.gs_from[i][a] = c;
+      }
+    if (L_new) {
+      int32_t c = 0;
+#pragma unroll
+      for (int k = 0; k < LEG_SCAN; ++k)
+        if (k < n && is_new(k) && y[k] != x) ++c;
+      L_new[a] = c;
+    }
+    if (!L2) return;
+    const int4 an = *reinterpret_cast<const int4*>(anc + a);
+    // the cycle bound: the window's slots before the latest closing edge
+    int32_t nc = 0, c2 = 0;
+    if (an.x < an.y) {
+#pragma unroll
+      for (int k = 0; k < LEG_SCAN; ++k)
+        if (k < n && before(tq[k], iq[k], an.z, an.w)) {
+          ++nc;
+          if (y[k] != x) ++c2;
+        }
+    }
+    qcb[a] = q0 + nc;
+    L2[a] = c2;
+    return;
+  }
   // returns h -> x inside the window: slots [b0, b1) of x's run [r0, r1) in
   // h's (nbr, t, id) list
   int32_t r0, r1, b0, b1;
@@ -727,9 +782,18 @@ __device__ __forceinline__ void sg_credit(unsigned long long* acc, int32_t a, in
   }
 }
 
-// (intermediary, scatter time, gather time, gather edge) of a leg
-__device__ __forceinline__ int4 leg_info(const LegRec& r, const int32_t* dst, const int32_t* ts) {
-  return make_int4(__ldg(dst + r.a), __ldg(ts + r.a), __ldg(ts + r.b), r.b);
+// (intermediary, scatter time, gather time, gather edge) of a leg; dts[a] =
+// (dst[a], ts[a]), so the scatter edge's two values come in one sector
+__device__ __forceinline__ int4 leg_info(const LegRec& r, const int2* dts, const int32_t* ts) {
+  const int2 sa = __ldg(dts + r.a);
+  return make_int4(sa.x, sa.y, __ldg(ts + r.b), r.b);
+}
+
+__global__ void __launch_bounds__(256) k_pack_dst_ts(const int32_t* __restrict__ dst,
+                                                     const int32_t* __restrict__ ts, int64_t E,
+                                                     int2* __restrict__ dts) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < E) dts[e] = make_int2(dst[e], ts[e]);
 }
 
 // two legs of one (s, d) key form an SG instance within a window when their
@@ -939,7 +1003,7 @@ __device__ __forceinline__ void sg_sorted_group(SgSmem<CAP, TAB>& S, uint32_t st
 
 template <int CAP, int TAB, int NS, int BS, bool SORT_BIG = false>
 __device__ __forceinline__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRec* __restrict__ R, int n,
-                                int32_t delta, const int32_t* __restrict__ dst,
+                                int32_t delta, const int2* __restrict__ dts,
                                 const int32_t* __restrict__ ts,
                                 unsigned long long* __restrict__ acc, int32_t new_from,
                                 const SubWindows& sub) {
@@ -1025,7 +1089,7 @@ __device__ __forceinline__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRe
     const uint32_t c = S.cnt[h[k]];
     if (c >= 2) {
       const uint32_t at = S.cls_n[sg_class(c)] + atomicAdd(&cur[h[k]], 1u);
-      S.grp[at] = leg_info(r[k], dst, ts);
+      S.grp[at] = leg_info(r[k], dts, ts);
       S.ga[at] = r[k].a;
       S.gslot[at] = h[k];
     }
@@ -1120,7 +1184,7 @@ __device__ __forceinline__ void sg_group_bucket(SgSmem<CAP, TAB>& S, const LegRe
 template <int NS>
 __global__ void __launch_bounds__(SG_BLOCK, 8) k_sg_bucket(const LegRec* __restrict__ rec,
                                                    const uint32_t* __restrict__ bend,
-                                                   int32_t delta, const int32_t* __restrict__ dst,
+                                                   int32_t delta, const int2* __restrict__ dts,
                                                    const int32_t* __restrict__ ts,
                                                    unsigned long long* __restrict__ acc,
                                                    int32_t new_from,
@@ -1134,7 +1198,7 @@ __global__ void __launch_bounds__(SG_BLOCK, 8) k_sg_bucket(const LegRec* __restr
     if (threadIdx.x == 0) overflow[1 + atomicAdd(overflow, 1u)] = blockIdx.x;
     return;
   }
-  sg_group_bucket<SG_CAP, SG_TAB, NS, SG_BLOCK>(S, rec + base, (int)n, delta, dst, ts, acc,
+  sg_group_bucket<SG_CAP, SG_TAB, NS, SG_BLOCK>(S, rec + base, (int)n, delta, dts, ts, acc,
                                                 new_from, sub);
 }
 
@@ -1144,7 +1208,7 @@ template <int NS>
 __global__ void __launch_bounds__(SG_BIG_BLOCK, 1) k_sg_bucket_big(const LegRec* __restrict__ rec,
                                                        const uint32_t* __restrict__ bend,
                                                        int32_t delta,
-                                                       const int32_t* __restrict__ dst,
+                                                       const int2* __restrict__ dts,
                                                        const int32_t* __restrict__ ts,
                                                        unsigned long long* __restrict__ acc,
                                                        int32_t new_from,
@@ -1159,17 +1223,17 @@ __global__ void __launch_bounds__(SG_BIG_BLOCK, 1) k_sg_bucket_big(const LegRec*
     const int64_t n = (int64_t)bend[b] - base;
     const LegRec* R = rec + base;
     if (n <= SG_CAP_BIG) {
-      sg_group_bucket<SG_CAP_BIG, SG_TAB_BIG, NS, SG_BIG_BLOCK, true>(S, R, (int)n, delta, dst,
+      sg_group_bucket<SG_CAP_BIG, SG_TAB_BIG, NS, SG_BIG_BLOCK, true>(S, R, (int)n, delta, dts,
                                                                       ts, acc, new_from, sub);
     } else {
       for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         const LegRec r = R[i];
-        const int4 ri = leg_info(r, dst, ts);
+        const int4 ri = leg_info(r, dts, ts);
         unsigned long long c = 0, cs[NS > 0 ? NS : 1] = {};
         for (int64_t j = 0; j < n; ++j) {
           const LegRec o = R[j];
           if (o.key != r.key) continue;
-          const int64_t span = sg_span(ri, leg_info(o, dst, ts), new_from);
+          const int64_t span = sg_span(ri, leg_info(o, dts, ts), new_from);
           if (span > delta) continue;
           ++c;
 #pragma unroll
@@ -1317,6 +1381,8 @@ struct CycLevelArgs {
   int32_t close_scan_max;
 };
 
+constexpr int CLOSE_BATCH = 4;
+
 // One element i of level j: closes its cycles and returns the window
 // [*q0, *q0 + count) of its children's slots (count 0: none).
 template <int NS, bool WIN, int J>
@@ -1383,16 +1449,25 @@ __device__ __forceinline__ int32_t cyc_item(const CycLevelArgs& A, const CycFron
     }
     if (any) {
       if (cr.y - cr.x <= close_scan_max) {
-        for (int32_t q = cr.x; q < cr.y; ++q) {
-          if (__ldg(g.inbr + q) != w) continue;
-          const int32_t cid = __ldg(g.ieid + q), tq = __ldg(g.it + q);
-          if (!WIN && !before(tl, last, tq, cid)) continue;
+        // CLOSE_BATCH counterparties are requested before any is compared,
+        // so a scan waits for one round of loads per batch, not per slot
+        for (int32_t qb = cr.x; qb < cr.y; qb += CLOSE_BATCH) {
+          int32_t nb[CLOSE_BATCH];
 #pragma unroll
-          for (int t = 0; t < NT; ++t)
-            if (col[t] && tq <= tmax[t]) {
-              atomicAdd(col[t] + cid, 1ull);
-              ++c[t];
-            }
+          for (int k = 0; k < CLOSE_BATCH; ++k) nb[k] = qb + k < cr.y ? __ldg(g.inbr + qb + k) : -1;
+#pragma unroll
+          for (int k = 0; k < CLOSE_BATCH; ++k) {
+            if (nb[k] != w) continue;
+            const int32_t q = qb + k;
+            const int32_t cid = __ldg(g.ieid + q), tq = __ldg(g.it + q);
+            if (!WIN && !before(tl, last, tq, cid)) continue;
+#pragma unroll
+            for (int t = 0; t < NT; ++t)
+              if (col[t] && tq <= tmax[t]) {
+                atomicAdd(col[t] + cid, 1ull);
+                ++c[t];
+              }
+          }
         }
       } else {
         const int32_t in_s = g.iptr[u0], in_e = g.iptr[u0 + 1];
@@ -1771,6 +1846,7 @@ __device__ __forceinline__ uint32_t saturate(uint64_t v, uint32_t limit) {
   return v > (uint64_t)limit ? limit : (uint32_t)v;
 }
 
+constexpr int ASM_BATCH = 8;
 __global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
   extern __shared__ uint32_t s_rows[];  // the block's rows, row-major
   const GraphView& g = P.g;
@@ -1812,8 +1888,17 @@ __global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
     if (u == v) {
       for (int c = 0; c < nc; ++c) row[c] = 0u;
     } else {
-      for (int c = 0; c < nc; ++c) {
-        row[c] = saturate(assemble_value(P, P.cols[c], e), P.limit);
+      // ASM_BATCH columns' loads are issued before the first of them is
+      // used, so a row waits for a few rounds of memory latency, not one
+      // per column
+      for (int c0 = 0; c0 < nc; c0 += ASM_BATCH) {
+        uint64_t val[ASM_BATCH];
+#pragma unroll
+        for (int k = 0; k < ASM_BATCH; ++k)
+          if (c0 + k < nc) val[k] = assemble_value(P, P.cols[c0 + k], e);
+#pragma unroll
+        for (int k = 0; k < ASM_BATCH; ++k)
+          if (c0 + k < nc) row[c0 + k] = saturate(val[k], P.limit);
       }
     }
   }
@@ -1866,7 +1951,7 @@ void launch_leg_emit(unsigned grid, int block, cudaStream_t s, const GraphView& 
 }
 
 void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
-                       const uint32_t* bend, int32_t delta, const int32_t* dst, const int32_t* ts,
+                       const uint32_t* bend, int32_t delta, const int2* dts, const int32_t* ts,
                        unsigned long long* acc, int32_t new_from, uint32_t* overflow,
                        const SubWindows& sub) {
   nsub_dispatch(sub.n, [&](auto ns) {
@@ -1881,11 +1966,11 @@ void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
       if (dev < 64) smem_set[dev][NS] = true;
     }
     AML_LAUNCH("k_sg_bucket", s,
-               k_sg_bucket<NS><<<n_buckets, SG_BLOCK, 0, s>>>(rec, bend, delta, dst, ts, acc,
+               k_sg_bucket<NS><<<n_buckets, SG_BLOCK, 0, s>>>(rec, bend, delta, dts, ts, acc,
                                                          new_from, overflow, sub));
     AML_LAUNCH("k_sg_bucket_big", s,
                k_sg_bucket_big<NS><<<(unsigned)sm_count(), SG_BIG_BLOCK, big, s>>>(
-                   rec, bend, delta, dst, ts, acc, new_from, overflow, sub));
+                   rec, bend, delta, dts, ts, acc, new_from, overflow, sub));
   });
 }
 

@@ -206,10 +206,12 @@ void launch_leg_emit(unsigned grid, int block, cudaStream_t s, const GraphView& 
                      const int2* qwin, const int32_t* qcb, const int64_t* off, const LegSink& S,
                      unsigned long long* acc_cyc2, int32_t* gs_in, int32_t own_max,
                      const SubWindows& sub);
+// (dst[e], ts[e]) of every edge in one int2, for the SG grouping's gathers
+__global__ void k_pack_dst_ts(const int32_t* dst, const int32_t* ts, int64_t E, int2* dts);
 // k_sg_bucket over all buckets (bucket b = records [bend[b-1], bend[b])),
-// then k_sg_bucket_big over the overflow list
+// then k_sg_bucket_big over the overflow list; dts from k_pack_dst_ts
 void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
-                       const uint32_t* bend, int32_t delta, const int32_t* dst, const int32_t* ts,
+                       const uint32_t* bend, int32_t delta, const int2* dts, const int32_t* ts,
                        unsigned long long* acc, int32_t new_from, uint32_t* overflow,
                        const SubWindows& sub);
 // Ordered cycles read their anchors from anc and their children's window

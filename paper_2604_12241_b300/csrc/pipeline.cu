@@ -612,7 +612,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       DBuf<uint32_t> overflow((size_t)nb + 1, t);
       AML_CUDA(cudaMemsetAsync(overflow.p, 0, sizeof(uint32_t), t));
       unsigned long long* acc_sg = wp.sg ? acc.p + (int64_t)wp.sg_slot * E : nullptr;
-      launch_sg_buckets((unsigned)nb, t, part.p, hist.p, wp.delta, gv.dst, gv.ts, acc_sg,
+      launch_sg_buckets((unsigned)nb, t, part.p, hist.p, wp.delta, g->dts, gv.ts, acc_sg,
                         new_from, overflow.p, sub);
     }
     // 4. cycles of length >= 3: the cost-binned hybrid (heaviest anchors

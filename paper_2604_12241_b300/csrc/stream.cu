@@ -387,6 +387,8 @@ aml_status aml_stream_check_graph(aml_stream* st, int64_t* n_mismatch) {
       cmp(f->src, g->src, E);
       cmp(f->dst, g->dst, E);
       cmp(f->ts, g->ts, E);
+      cmp(reinterpret_cast<const int32_t*>(f->dts), reinterpret_cast<const int32_t*>(g->dts),
+          2 * E);
       const Adj* fa[2] = {&f->out, &f->in};
       const Adj* ga[2] = {&g->out, &g->in};
       for (int d = 0; d < 2; ++d) {
