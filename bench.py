@@ -236,11 +236,11 @@ def algorithmic_bytes(kernel: str, E: int, Ev: int, pats, stats: dict) -> float:
     of j edges.  A kernel launched once per level reports the mean over its
     launches.  None for a kernel without a byte model.
       k_leg_count     per edge: src, dst, ts (12 B), its leg window's bounds and
-                      leg count written (12 B); with cycle columns the anchor's
-                      latest closing edge read (8 B) and the cycle-capable count
-                      and bound written (8 B); per SG/CYC column one uint64
-                      accumulator cleared (8 B); per GS column the gather-side
-                      count cleared (4 B)
+                      leg count written (12 B); with cycle columns its closing
+                      range and the range's latest edge (16 B) and the
+                      cycle-capable count and bound (8 B) written; per SG/CYC
+                      column one uint64 accumulator cleared (8 B); per GS
+                      column the gather-side count cleared (4 B)
       k_close_range   per edge: src, dst, ts (12 B), its closing range and the
                       range's latest edge written (16 B)
       k_assemble      per edge: src, dst (8 B); per window and direction with
@@ -290,7 +290,7 @@ def algorithmic_bytes(kernel: str, E: int, Ev: int, pats, stats: dict) -> float:
         return 8.0 * sum(front.values()) / len(front)
     if kernel == "k_leg_count":
         cyc = any(f.startswith("CYC") and not f.startswith("CYCW") for f in fam)
-        return E * (12 + 12 + (16 if cyc else 0) + 8 * n_acc + 4 * n_gs)
+        return E * (12 + 12 + (24 if cyc else 0) + 8 * n_acc + 4 * n_gs)
     if kernel == "k_close_range":
         return E * (12 + 16)
     return None

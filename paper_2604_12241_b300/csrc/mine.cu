@@ -130,19 +130,47 @@ __device__ __forceinline__ int32_t cycle_bound(const GraphView& g, int2 cr, int2
   return after_edge(g.ot, g.oeid, q0, q1, cl.x, cl.y - 1);  // first slot not before it
 }
 
+// The closing range B1 of edge a = x -> h (the slots of x's in-list after a,
+// up to t_a + delta; delta counting: only new closing edges) and the (t,
+// id) of its latest edge, as (B1 begin, B1 end, t, id); with rec, also
+// stored as a's whole 32-byte anchor record (one sector).
+__device__ __forceinline__ int4 close_anchor(const GraphView& g, int32_t a, int32_t x, int32_t h,
+                                             int32_t ta, int32_t delta, AnchorRec* rec) {
+  int2 r = make_int2(0, 0);
+  if (x != h) {
+    const int32_t is = g.iptr[x], ie = g.iptr[x + 1];
+    after_edge_upto(g.it, g.ieid, is, ie, ta, a, (int64_t)ta + delta, r.x, r.y);
+    // delta counting: a cycle is new iff its closing (latest) edge is new
+    if (g.new_from > 0) r.x = after_edge(g.it, g.ieid, r.x, r.y, g.t_new, g.new_from - 1);
+  }
+  const bool any = r.x < r.y;
+  const int4 an = make_int4(r.x, r.y, any ? __ldg(g.it + r.y - 1) : 0,
+                            any ? __ldg(g.ieid + r.y - 1) : 0);
+  if (rec) {
+    int4* dst = reinterpret_cast<int4*>(rec + a);
+    dst[0] = an;
+    dst[1] = make_int4(x, h, ta, 0);
+  }
+  return an;
+}
+
 // L[a]: legs from a.  With anc (anchor records): L2[a] = those that can
 // start a cycle (slots before the cycle bound, minus returns to src(a) among
 // them).
 // With L_new (delta counting): L_new[a] = legs from a whose second edge is new.
 // qwin[a] = a's window slots [q0, q1) in dst(a)'s out-list and, with anc,
 // qcb[a] = its cycle bound, kept for the emission.
+// close_here: the anchor record of every edge with legs is computed and
+// stored here (no separate k_close_range pass; an edge without legs starts
+// no cycle and its record is never read); else it is read from anc.
 // Z: the accumulators the emission and later kernels add into, zeroed here
 // (element a of each) instead of by separate memsets.
 constexpr int LEG_SCAN = 4;  // windows up to this many slots are scanned, not searched
 template <int NS>
-__global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
+__global__ void __launch_bounds__(512, 4) k_leg_count(GraphView g, int32_t delta,
                                                    int32_t* __restrict__ L,
-                                                   const AnchorRec* __restrict__ anc,
+                                                   AnchorRec* __restrict__ anc,
+                                                   int close_here,
                                                    int32_t* __restrict__ L2,
                                                    int32_t* __restrict__ L_new,
                                                    int2* __restrict__ qwin,
@@ -214,7 +242,13 @@ __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
       L_new[a] = c;
     }
     if (!L2) return;
-    const int4 an = *reinterpret_cast<const int4*>(anc + a);
+    if (n == 0) {  // no legs: no cycle starts at a
+      qcb[a] = q0;
+      L2[a] = 0;
+      return;
+    }
+    const int4 an = close_here ? close_anchor(g, a, x, h, ta, delta, anc)
+                               : *reinterpret_cast<const int4*>(anc + a);
     // the cycle bound: the window's slots before the latest closing edge
     int32_t nc = 0, c2 = 0;
     if (an.x < an.y) {
@@ -262,7 +296,8 @@ __global__ void __launch_bounds__(512) k_leg_count(GraphView g, int32_t delta,
     L_new[a] = (q1 - qn) - back;
   }
   if (!L2) return;
-  const int4 an = *reinterpret_cast<const int4*>(anc + a);
+  const int4 an = close_here ? close_anchor(g, a, x, h, ta, delta, anc)
+                             : *reinterpret_cast<const int4*>(anc + a);
   const int2 cr = make_int2(an.x, an.y), cl = make_int2(an.z, an.w);
   const int32_t qc = cycle_bound(g, cr, cl, q0, q1);
   qcb[a] = qc;
@@ -1279,20 +1314,8 @@ __global__ void __launch_bounds__(512) k_close_range(GraphView g, int32_t delta,
   if (a64 >= g.E) return;
   int32_t a = (int32_t)a64;
   const int32_t u0 = g.src[a], u1 = g.dst[a], ta = g.ts[a];
-  int2 r = make_int2(0, 0);
-  if (u0 != u1) {
-    int32_t is = g.iptr[u0], ie = g.iptr[u0 + 1];
-    after_edge_upto(g.it, g.ieid, is, ie, ta, a, (int64_t)ta + delta, r.x, r.y);
-    // delta counting: a cycle is new iff its closing (latest) edge is new
-    if (g.new_from > 0) r.x = after_edge(g.it, g.ieid, r.x, r.y, g.t_new, g.new_from - 1);
-  }
-  if (rng) rng[a] = r;
-  if (anc) {  // the whole 32-byte record, so the store fills its sector
-    int4* dst = reinterpret_cast<int4*>(anc + a);
-    const bool any = r.x < r.y;
-    dst[0] = make_int4(r.x, r.y, any ? __ldg(g.it + r.y - 1) : 0, any ? __ldg(g.ieid + r.y - 1) : 0);
-    dst[1] = make_int4(u0, u1, ta, 0);
-  }
+  const int4 an = close_anchor(g, a, u0, u1, ta, delta, anc);
+  if (rng) rng[a] = make_int2(an.x, an.y);
 }
 
 
@@ -1917,12 +1940,12 @@ __global__ void __launch_bounds__(ASM_BLOCK) k_assemble(AssembleParams P) {
 
 
 void launch_leg_count(unsigned grid, int block, cudaStream_t s, const GraphView& g, int32_t delta,
-                      int32_t* L, const AnchorRec* anc, int32_t* L2, int32_t* L_new, int2* qwin,
-                      int32_t* qcb, const SubWindows& sub, const ZeroSink& Z) {
+                      int32_t* L, AnchorRec* anc, bool close_here, int32_t* L2, int32_t* L_new,
+                      int2* qwin, int32_t* qcb, const SubWindows& sub, const ZeroSink& Z) {
   nsub_dispatch(sub.n, [&](auto ns) {
     AML_LAUNCH("k_leg_count", s,
-               k_leg_count<decltype(ns)::value><<<grid, block, 0, s>>>(g, delta, L, anc, L2,
-                                                                      L_new, qwin, qcb, sub, Z));
+               k_leg_count<decltype(ns)::value><<<grid, block, 0, s>>>(
+                   g, delta, L, anc, close_here ? 1 : 0, L2, L_new, qwin, qcb, sub, Z));
   });
 }
 

@@ -185,8 +185,8 @@ struct ZeroSink {
 // Launchers of the kernels that also count sub-windows (instantiated for
 // the number of them in sub).
 void launch_leg_count(unsigned grid, int block, cudaStream_t s, const GraphView& g, int32_t delta,
-                      int32_t* L, const AnchorRec* anc, int32_t* L2, int32_t* L_new, int2* qwin,
-                      int32_t* qcb, const SubWindows& sub, const ZeroSink& Z);
+                      int32_t* L, AnchorRec* anc, bool close_here, int32_t* L2, int32_t* L_new,
+                      int2* qwin, int32_t* qcb, const SubWindows& sub, const ZeroSink& Z);
 // Delta counting (new_from > 0): the legs a new instance can use (mine.cu);
 // first_new = each out-list's first new slot (k_first_new); mptr/mslot =
 // each node's out-list slots whose counterparty is a batch destination

@@ -410,17 +410,21 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     // 2. legs (and, for the level-by-level cycle search, the legs that can
     // start a cycle: those of anchors with a closing range, before its end)
     const bool level_cycles = wp.K >= 3;
-    // closing ranges: anchor records for the level-by-level search, and the
-    // plain ranges for the persistent modes' kernels
+    // closing ranges: anchor records for the level-by-level search (those
+    // of the edges with legs, computed by the leg count), and for the
+    // persistent modes' kernels the plain ranges of every edge (a pass of
+    // their own)
     DBuf<int2> crng;
     DBuf<AnchorRec> anc;
     DBuf<int32_t> L2;
     DBuf<int64_t> off2;
     if (level_cycles) {
-      if (persistent) crng = DBuf<int2>((size_t)E, s);
       anc = DBuf<AnchorRec>((size_t)E, s);
-      AML_LAUNCH("k_close_range", s,
-                 k_close_range<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, crng.p, anc.p));
+      if (persistent) {
+        crng = DBuf<int2>((size_t)E, s);
+        AML_LAUNCH("k_close_range", s,
+                   k_close_range<<<grid_for(E, B), B, 0, s>>>(gv, wp.delta, crng.p, anc.p));
+      }
       L2 = DBuf<int32_t>((size_t)E + 1, s);
       off2 = DBuf<int64_t>((size_t)E + 1, s);
     }
@@ -442,7 +446,8 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     ZeroSink Z{acc_zeroed ? nullptr : acc.p, acc_zeroed ? 0 : n_acc, gs_in};
     acc_zeroed = true;
     launch_leg_count(grid_for(E, B), B, s, gv, wp.delta, L.p, level_cycles ? anc.p : nullptr,
-                     level_cycles ? L2.p : nullptr, L_new, qwin.p, qcb.p, sub, Z);
+                     level_cycles && !persistent, level_cycles ? L2.p : nullptr, L_new, qwin.p,
+                     qcb.p, sub, Z);
     AML_CUDA(cudaMemsetAsync(L.p + E, 0, sizeof(int32_t), s));
     keep64.emplace_back((size_t)(E + 1), s);
     int64_t* off = keep64.back().p;

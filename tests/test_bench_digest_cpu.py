@@ -49,4 +49,4 @@ def test_byte_models_are_finite_or_none():
         b = bench.algorithmic_bytes(k, 100, 90, pats, stats)
         assert b is None or (math.isfinite(b) and b > 0), k
     # hi-large: SG + CYC3..6 accumulators, one GS column, cycle columns
-    assert bench.algorithmic_bytes("k_leg_count", 100, 90, pats, stats) == 100 * (40 + 40 + 4)
+    assert bench.algorithmic_bytes("k_leg_count", 100, 90, pats, stats) == 100 * (48 + 40 + 4)
