@@ -181,10 +181,10 @@ def measured_peak():
 # full size, valid only for the kernel sources it was taken with:
 # KERNEL_DIGEST is the digest (kernel_digest()) of the files that define the
 # measured kernels.
-KERNEL_DIGEST = "3f59e64a7c9c3927"
-MEASURED_TRAFFIC = {"k_sg_bucket": 569.6e6, "k_cyc_level": 246.3e6, "k_sg_partition": 553.0e6,
-                    "k_leg_emit": 660.2e6, "k_leg_count": 827.1e6, "k_assemble": 1256.8e6,
-                    "k_fan_scan": 265.2e6, "k_fan_reduce": 143.3e6}
+KERNEL_DIGEST = "90f2dbcd9eb8ec67"
+MEASURED_TRAFFIC = {"k_sg_bucket": 569.5e6, "k_cyc_level": 246.4e6, "k_sg_partition": 550.0e6,
+                    "k_leg_emit": 662.5e6, "k_leg_count": 858.0e6, "k_assemble": 1257.0e6,
+                    "k_fan_scan": 265.3e6, "k_fan_reduce": 143.1e6}
 
 
 TRAFFIC_SOURCES = ("aml_internal.cuh", "fan.cu", "mine.cu", "mine.cuh", "pipeline.cu", "prims.cu")
