@@ -322,18 +322,28 @@ aml_status aml_pattern_set_column(const aml_pattern_set* ps, int32_t col,
                                    /* cost model trained by aml_cost_train for   */
                                    /* that window (degree estimate when no model */
                                    /* exists)                                   */
-#define AML_MINE_FUSED 0x20u       /* the level-by-level cycle search in one      */
-                                   /* persistent cooperative launch: per level,   */
-                                   /* the blocks close their chunk's cycles, meet */
-                                   /* at a grid-wide barrier, place their chunk's */
-                                   /* children from all blocks' counts and meet   */
-                                   /* again (no per-level scan, emission or count */
-                                   /* arrays).  The first mine of a (graph,       */
-                                   /* window) runs the plain search to learn the  */
-                                   /* level sizes.  Not with PERSISTENT/LEARNED.  */
-                                   /* A barrier wait that runs out (see           */
+#define AML_MINE_FUSED 0x20u       /* the leg pass and the level-by-level cycle  */
+                                   /* search of a window in one persistent       */
+                                   /* cooperative launch (Sec. 4: the families   */
+                                   /* share their first hop): each block counts  */
+                                   /* the legs of its edge chunk, meets the      */
+                                   /* others at a grid-wide barrier, places its   */
+                                   /* chunk's legs from all blocks' sums, emits   */
+                                   /* them (GS, 2-cycle and SG records, cycle     */
+                                   /* legs), meets them again, then per cycle     */
+                                   /* level closes its chunk's cycles and places  */
+                                   /* its chunk's children between two barriers.  */
+                                   /* The SG grouping follows the launch and the  */
+                                   /* DEG/FAN pass runs beside it.  The first     */
+                                   /* mine of a (graph, window) runs the plain    */
+                                   /* sequence to learn the leg and level sizes.  */
+                                   /* Not with PERSISTENT/LEARNED.  A barrier     */
+                                   /* wait that runs out (see                     */
                                    /* aml_graph_set_wait_limit) ends the launch:  */
-                                   /* AML_ETIMEOUT at aml_sync, counts invalid.   */
+                                   /* AML_ETIMEOUT at aml_sync, that mine's       */
+                                   /* counts invalid.  While the graph's error    */
+                                   /* word is set (until aml_sync reports it) a   */
+                                   /* fused mine also skips its SG grouping.      */
 #define AML_MINE_HOST_ASYNC 0x10u  /* with HOST_OUTPUT: counts is page-locked    */
                                    /* host memory (cudaHostAlloc / registered),  */
                                    /* the copy back is enqueued on `stream` and  */

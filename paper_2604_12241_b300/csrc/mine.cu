@@ -166,19 +166,17 @@ __device__ __forceinline__ int4 close_anchor(const GraphView& g, int32_t a, int3
 // Z: the accumulators the emission and later kernels add into, zeroed here
 // (element a of each) instead of by separate memsets.
 constexpr int LEG_SCAN = 4;  // windows up to this many slots are scanned, not searched
+// the leg count of one edge a (every thread of k_leg_count, and the fused
+// mine's first phase)
 template <int NS>
-__global__ void __launch_bounds__(512, 4) k_leg_count(GraphView g, int32_t delta,
-                                                   int32_t* __restrict__ L,
-                                                   AnchorRec* __restrict__ anc,
-                                                   int close_here,
-                                                   int32_t* __restrict__ L2,
-                                                   int32_t* __restrict__ L_new,
-                                                   int2* __restrict__ qwin,
-                                                   int32_t* __restrict__ qcb,
-                                                   SubWindows sub, ZeroSink Z) {
-  int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a64 >= g.E) return;
-  int32_t a = (int32_t)a64;
+__device__ __forceinline__ void leg_count_item(const GraphView& g, int32_t delta, int32_t a,
+                                               int32_t* __restrict__ L,
+                                               AnchorRec* __restrict__ anc, int close_here,
+                                               int32_t* __restrict__ L2,
+                                               int32_t* __restrict__ L_new,
+                                               int2* __restrict__ qwin,
+                                               int32_t* __restrict__ qcb,
+                                               const SubWindows& sub, const ZeroSink& Z) {
   for (int c = 0; c < Z.n_acc; ++c) Z.acc[(int64_t)c * g.E + a] = 0ull;
   if (Z.gs_in) Z.gs_in[a] = 0;
 #pragma unroll
@@ -307,6 +305,21 @@ __global__ void __launch_bounds__(512, 4) k_leg_count(GraphView g, int32_t delta
   L2[a] = (qc - q0) - back;
 }
 
+template <int NS>
+__global__ void __launch_bounds__(512, 4) k_leg_count(GraphView g, int32_t delta,
+                                                   int32_t* __restrict__ L,
+                                                   AnchorRec* __restrict__ anc,
+                                                   int close_here,
+                                                   int32_t* __restrict__ L2,
+                                                   int32_t* __restrict__ L_new,
+                                                   int2* __restrict__ qwin,
+                                                   int32_t* __restrict__ qcb,
+                                                   SubWindows sub, ZeroSink Z) {
+  const int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a64 >= g.E) return;
+  leg_count_item<NS>(g, delta, (int32_t)a64, L, anc, close_here, L2, L_new, qwin, qcb, sub, Z);
+}
+
 // legs ending with each edge, by binary search (when no legs are emitted)
 __global__ void __launch_bounds__(512) k_gs_into(GraphView g, int32_t delta,
                                                  int32_t* __restrict__ gs_in) {
@@ -401,14 +414,16 @@ __device__ __forceinline__ void sub_leg_credit(const SubWindows& sub, bool leg, 
   }
 }
 
+// The emission of the warp's 32 edges, a64 this lane's (g.E or beyond:
+// none).  Every lane of the warp calls it together (k_leg_emit, and the
+// fused mine's emission phase).
 template <int NS>
-__global__ void __launch_bounds__(512, 3) k_leg_emit(GraphView g, const int2* __restrict__ qwin,
-                                                  const int32_t* __restrict__ qcb,
-                                                  const int64_t* __restrict__ off, LegSink S,
-                                                  unsigned long long* __restrict__ acc_cyc2,
-                                                  int32_t* __restrict__ gs_in, int32_t own_max,
-                                                  SubWindows sub) {
-  const int64_t a64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void leg_emit_warp(const GraphView& g, const int2* __restrict__ qwin,
+                                              const int32_t* __restrict__ qcb,
+                                              const int64_t* __restrict__ off, const LegSink& S,
+                                              unsigned long long* __restrict__ acc_cyc2,
+                                              int32_t* __restrict__ gs_in, int32_t own_max,
+                                              const SubWindows& sub, int64_t a64) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   int32_t a = (int32_t)a64, x = 0, q0 = 0, q1 = 0, h = 0, ta = 0;
@@ -529,6 +544,17 @@ __global__ void __launch_bounds__(512, 3) k_leg_emit(GraphView g, const int2* __
       if (lane == 0 && hc2) atomicAdd(acc_cyc2 + ha, hc2);
     }
   }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(512, 3) k_leg_emit(GraphView g, const int2* __restrict__ qwin,
+                                                  const int32_t* __restrict__ qcb,
+                                                  const int64_t* __restrict__ off, LegSink S,
+                                                  unsigned long long* __restrict__ acc_cyc2,
+                                                  int32_t* __restrict__ gs_in, int32_t own_max,
+                                                  SubWindows sub) {
+  leg_emit_warp<NS>(g, qwin, qcb, off, S, acc_cyc2, gs_in, own_max, sub,
+                    (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------- legs for delta counting
@@ -779,10 +805,14 @@ __global__ void __launch_bounds__(256) k_mark_nodes(const int32_t* __restrict__ 
 
 // SG_PART_ITEMS independent records per thread keep several cursor atomics
 // in flight at once (the kernel is bound by their latency)
+// (skip: a device error word; when it is set the records may be unwritten
+// and nothing is moved)
 __global__ void __launch_bounds__(256) k_sg_partition(const LegRec* __restrict__ rec, int64_t n,
                                                       int bits, KeySet ks,
                                                       uint32_t* __restrict__ cursor,
-                                                      LegRec* __restrict__ out) {
+                                                      LegRec* __restrict__ out,
+                                                      const uint32_t* __restrict__ skip) {
+  if (skip && *(volatile const uint32_t*)skip) return;
   const int64_t base = (int64_t)blockIdx.x * blockDim.x * SG_PART_ITEMS + threadIdx.x;
   LegRec r[SG_PART_ITEMS];
   uint32_t bkt[SG_PART_ITEMS];
@@ -1224,8 +1254,12 @@ __global__ void __launch_bounds__(SG_BLOCK, 8) k_sg_bucket(const LegRec* __restr
                                                    unsigned long long* __restrict__ acc,
                                                    int32_t new_from,
                                                    uint32_t* __restrict__ overflow,
-                                                   SubWindows sub) {
+                                                   SubWindows sub,
+                                                   const uint32_t* __restrict__ skip) {
   __shared__ SgSmem<SG_CAP, SG_TAB> S;
+  // (skip set: the records and bucket ends may be unwritten; nothing is
+  // grouped and no bucket is listed for k_sg_bucket_big)
+  if (skip && *(volatile const uint32_t*)skip) return;
   const int64_t base = blockIdx.x ? bend[blockIdx.x - 1] : 0;
   const int64_t n = (int64_t)bend[blockIdx.x] - base;
   if (n < 2) return;
@@ -1659,14 +1693,17 @@ __device__ __forceinline__ long long fused_block_excl(long long v, long long* s_
   return before + x - v;
 }
 
+// every level of the cycle search from the n2 cycle legs of P.F (the body
+// of k_cyc_fused, and the fused mine's last phase); false if a barrier wait
+// ran out or a level outgrew its buffers
 template <int NS>
-__global__ void __launch_bounds__(FUSED_BLOCK, 3) k_cyc_fused(CycLevelArgs A, FusedCycles P,
-                                                            SubWindows sub) {
-  __shared__ long long s_w[FUSED_BLOCK / 32];
+__device__ __forceinline__ bool cyc_fused_levels(const CycLevelArgs& A, const FusedCycles& P,
+                                                 const SubWindows& sub, int64_t n2,
+                                                 long long* s_w) {
   const int lane = threadIdx.x & 31;
   const unsigned G = gridDim.x;
   CycFrontier F = P.F;
-  int64_t n = P.n2;
+  int64_t n = n2;
   for (int j = 2; j <= A.K - 1 && n > 0; ++j) {
     const bool has_next = j + 1 <= A.K - 1;
     const int64_t C = (n + G - 1) / G;
@@ -1687,7 +1724,7 @@ __global__ void __launch_bounds__(FUSED_BLOCK, 3) k_cyc_fused(CycLevelArgs A, Fu
     if (!has_next) break;
     mine = fused_block_sum(mine, s_w);
     if (threadIdx.x == 0) P.bsum[blockIdx.x] = mine;
-    if (!grid_wait(P.bar, P.wait_limit, P.err)) return;
+    if (!grid_wait(P.bar, P.wait_limit, P.err)) return false;
     // this chunk's first child position and the level's total
     long long before = 0, total = 0;
     for (unsigned b = threadIdx.x; b < G; b += FUSED_BLOCK) {
@@ -1699,7 +1736,7 @@ __global__ void __launch_bounds__(FUSED_BLOCK, 3) k_cyc_fused(CycLevelArgs A, Fu
     total = fused_block_sum(total, s_w);
     if (total > P.cap[j + 1]) {  // cannot happen for the sizes the capacity came from
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(P.err, ERR_OVERFLOW);
-      return;  // every block sees the same total and leaves here
+      return false;  // every block sees the same total and leaves here
     }
     int32_t* par = P.par[j + 1];
     int32_t* slot = P.slot[j + 1];
@@ -1731,11 +1768,143 @@ __global__ void __launch_bounds__(FUSED_BLOCK, 3) k_cyc_fused(CycLevelArgs A, Fu
       }
       run += tile;
     }
-    if (!grid_wait(P.bar, P.wait_limit, P.err)) return;
+    if (!grid_wait(P.bar, P.wait_limit, P.err)) return false;
     F.par[j + 1] = par;
     F.slot[j + 1] = slot;
     n = total;
   }
+  return true;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(FUSED_BLOCK, 3) k_cyc_fused(CycLevelArgs A, FusedCycles P,
+                                                            SubWindows sub) {
+  __shared__ long long s_w[FUSED_BLOCK / 32];
+  cyc_fused_levels<NS>(A, P, sub, P.n2, s_w);
+}
+
+// The fused mine (FusedLegs): P.bar, P.err and P.wait_limit serve every
+// barrier; K >= 3 runs the cycle levels after the legs.
+#ifndef AML_FUSED_MIN_BLOCKS
+#define AML_FUSED_MIN_BLOCKS 3
+#endif
+template <int NS>
+__global__ void __launch_bounds__(FUSED_BLOCK, AML_FUSED_MIN_BLOCKS) k_mine_fused(GraphView g, FusedLegs Q,
+                                                             CycLevelArgs A, FusedCycles P,
+                                                             SubWindows sub) {
+  __shared__ long long s_w[FUSED_BLOCK / 32];
+  const unsigned G = gridDim.x;
+  const int64_t E = g.E;
+  const int64_t C = (E + G - 1) / G;
+  const int64_t c0 = min(E, (int64_t)blockIdx.x * C), c1 = min(E, c0 + C);
+  const bool cyc = Q.anc != nullptr;
+  // 1. leg count of the chunk (thread t takes edges c0 + t + k * FUSED_BLOCK
+  // in every phase, so it reads back its own writes)
+  long long nl = 0, nc = 0;
+  for (int64_t a = c0 + threadIdx.x; a < c1; a += FUSED_BLOCK) {
+    leg_count_item<NS>(g, Q.delta, (int32_t)a, Q.L, Q.anc, 1, Q.L2, nullptr, Q.qwin, Q.qcb,
+                       sub, Q.Z);
+    nl += Q.L[a];
+    if (cyc) nc += Q.L2[a];
+  }
+  nl = fused_block_sum(nl, s_w);
+  nc = fused_block_sum(nc, s_w);
+  if (threadIdx.x == 0) {
+    Q.bsum[2 * blockIdx.x] = nl;
+    Q.bsum[2 * blockIdx.x + 1] = nc;
+  }
+  if (!grid_wait(P.bar, P.wait_limit, P.err)) return;
+  // 2. the chunk's first leg and cycle-leg positions, and the totals
+  long long b1 = 0, b2 = 0, t1 = 0, t2 = 0;
+  for (unsigned b = threadIdx.x; b < G; b += FUSED_BLOCK) {
+    const long long v1 = __ldcg(Q.bsum + 2 * b), v2 = __ldcg(Q.bsum + 2 * b + 1);
+    t1 += v1;
+    t2 += v2;
+    if (b < blockIdx.x) {
+      b1 += v1;
+      b2 += v2;
+    }
+  }
+  b1 = fused_block_sum(b1, s_w);
+  b2 = fused_block_sum(b2, s_w);
+  t1 = fused_block_sum(t1, s_w);
+  t2 = fused_block_sum(t2, s_w);
+  if (t1 != Q.n_legs || (cyc && t2 != Q.n2)) {  // every block sees the same totals
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(P.err, ERR_OVERFLOW);
+    return;
+  }
+  for (int64_t t0 = c0; t0 < c1; t0 += FUSED_BLOCK) {
+    const int64_t a = t0 + threadIdx.x;
+    const int32_t l1 = a < c1 ? Q.L[a] : 0;
+    const int32_t l2 = cyc && a < c1 ? Q.L2[a] : 0;
+    long long tile1 = 0, tile2 = 0;
+    const long long o1 = b1 + fused_block_excl(l1, s_w, &tile1);
+    const long long o2 = b2 + fused_block_excl(l2, s_w, &tile2);
+    if (a < c1) {
+      Q.off[a] = o1;
+      if (cyc) Q.off2[a] = o2;
+    }
+    b1 += tile1;
+    b2 += tile2;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Q.off[E] = t1;
+    if (cyc) Q.off2[E] = t2;
+  }
+  // 3. leg emission of the chunk (its windows and offsets are this thread's
+  // own writes; static chunks spread the hubs' long windows over every
+  // warp, which balancing the chunks by legs would gather into a few); the
+  // accumulators it adds into were zeroed in phase 1, before the barrier
+  for (int64_t t0 = c0; t0 < c1; t0 += FUSED_BLOCK) {
+    const int64_t a = t0 + threadIdx.x;
+    leg_emit_warp<NS>(g, Q.qwin, Q.qcb, Q.off, Q.S, Q.acc_cyc2, Q.gs_in, Q.own_max, sub,
+                      a < c1 ? a : E);
+  }
+  if (!cyc || A.K < 3) return;
+  // 4. the cycle levels, once every block's cycle legs are written
+  if (!grid_wait(P.bar, P.wait_limit, P.err)) return;
+  cyc_fused_levels<NS>(A, P, sub, t2, s_w);
+}
+
+template <int NS>
+static void fused_mine_blocks(int* per_sm) {
+  AML_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_mine_fused<NS>, FUSED_BLOCK,
+                                                         0));
+}
+
+int fused_mine_grid(int n_sub) {
+  static int cached[64][MAX_SUB + 1] = {};
+  int dev = 0;
+  AML_CUDA(cudaGetDevice(&dev));
+  int per_sm = 0;
+  const int key = n_sub <= 0 ? 0 : n_sub == 1 ? 1 : n_sub == 2 ? 2 : MAX_SUB;
+  if (dev < 64 && cached[dev][key]) return cached[dev][key];
+  nsub_dispatch(n_sub, [&](auto ns) { fused_mine_blocks<decltype(ns)::value>(&per_sm); });
+  AML_REQUIRE(per_sm >= 1, AML_EUNSUPPORTED, "the fused mine kernel cannot be resident");
+  const int grid = per_sm * sm_count();
+  if (dev < 64) cached[dev][key] = grid;
+  return grid;
+}
+
+void launch_mine_fused(int grid, cudaStream_t s, const GraphView& g, const FusedLegs& Q, int K,
+                       const CycleSlots& slots, unsigned long long* acc, int32_t close_scan_max,
+                       const FusedCycles& P, const SubWindows& sub) {
+  const CycLevelArgs A{g, Q.delta, K, nullptr, Q.anc, Q.qwin, slots, acc, close_scan_max};
+  nsub_dispatch(sub.n, [&](auto ns) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(FUSED_BLOCK);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    AML_LAUNCH("k_mine_fused", s,
+               AML_CUDA(cudaLaunchKernelEx(&cfg, k_mine_fused<decltype(ns)::value>, g, Q, A, P,
+                                           sub)));
+  });
 }
 
 template <int NS>
@@ -1976,7 +2145,7 @@ void launch_leg_emit(unsigned grid, int block, cudaStream_t s, const GraphView& 
 void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
                        const uint32_t* bend, int32_t delta, const int2* dts, const int32_t* ts,
                        unsigned long long* acc, int32_t new_from, uint32_t* overflow,
-                       const SubWindows& sub) {
+                       const SubWindows& sub, const uint32_t* skip) {
   nsub_dispatch(sub.n, [&](auto ns) {
     constexpr int NS = decltype(ns)::value;
     static bool smem_set[64][MAX_SUB + 1] = {};  // per device and instantiation
@@ -1990,7 +2159,7 @@ void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
     }
     AML_LAUNCH("k_sg_bucket", s,
                k_sg_bucket<NS><<<n_buckets, SG_BLOCK, 0, s>>>(rec, bend, delta, dts, ts, acc,
-                                                         new_from, overflow, sub));
+                                                         new_from, overflow, sub, skip));
     AML_LAUNCH("k_sg_bucket_big", s,
                k_sg_bucket_big<NS><<<(unsigned)sm_count(), SG_BIG_BLOCK, big, s>>>(
                    rec, bend, delta, dts, ts, acc, new_from, overflow, sub));

@@ -164,7 +164,7 @@ struct KeySet {
 
 __global__ void k_sg_partition(const LegRec* rec, int64_t n, int bits, KeySet ks,
                                uint32_t* cursor,
-                               LegRec* out);
+                               LegRec* out, const uint32_t* skip);
 __global__ void k_sg_hist(const LegRec* rec, int64_t n, int bits, KeySet ks, uint32_t* hist);
 __global__ void k_sg_new_keys(const LegRec* rec, int64_t n, int32_t new_from, KeySet ks);
 __global__ void k_sg_count_new(const LegRec* rec, int64_t n, int32_t new_from,
@@ -213,7 +213,8 @@ __global__ void k_pack_dst_ts(const int32_t* dst, const int32_t* ts, int64_t E, 
 void launch_sg_buckets(unsigned n_buckets, cudaStream_t s, const LegRec* rec,
                        const uint32_t* bend, int32_t delta, const int2* dts, const int32_t* ts,
                        unsigned long long* acc, int32_t new_from, uint32_t* overflow,
-                       const SubWindows& sub);
+                       const SubWindows& sub,
+                       const uint32_t* skip = nullptr);
 // Ordered cycles read their anchors from anc and their children's window
 // starts from qwin (the leg windows of the same window's leg pass); window
 // cycles (base 1) read close_rng and search their windows.
@@ -248,8 +249,36 @@ struct FusedCycles {
   long long wait_limit;  // SM clock cycles a barrier wait may take
   int32_t own_max;       // child lists up to this long are written by one lane
 };
-// blocks of the fused launch on this device (all resident at once)
+// The fused mine of one window: the leg pass and the cycle search in one
+// cooperative launch (k_mine_fused).  Block b takes the contiguous edge chunk
+// b; phases: leg count of the chunk, grid barrier, the chunk's leg offsets
+// (off, off2 and their totals at [E]) from every block's sums, leg emission
+// of the chunk, grid barrier, then every cycle level (FusedCycles).  The
+// buffers are sized for n_legs legs and n2 cycle legs (the sizes of an
+// earlier mine of the same graph); other totals set ERR_OVERFLOW.
+struct FusedLegs {
+  int32_t delta;
+  int32_t* L;
+  AnchorRec* anc;  // null: no cycle search (L2, qcb, off2 unused)
+  int32_t* L2;
+  int2* qwin;
+  int32_t* qcb;
+  ZeroSink Z;
+  int64_t* off;
+  int64_t* off2;
+  LegSink S;
+  unsigned long long* acc_cyc2;
+  int32_t* gs_in;
+  int32_t own_max;
+  int64_t n_legs, n2;
+  long long* bsum;  // two values per block
+};
+// blocks of the fused launches on this device (all resident at once)
 int fused_cycle_grid(int n_sub);
+int fused_mine_grid(int n_sub);
+void launch_mine_fused(int grid, cudaStream_t s, const GraphView& g, const FusedLegs& Q, int K,
+                       const CycleSlots& slots, unsigned long long* acc, int32_t close_scan_max,
+                       const FusedCycles& P, const SubWindows& sub);
 void launch_cyc_fused(int grid, cudaStream_t s, const GraphView& g, int32_t delta, int K,
                       const AnchorRec* anc, const int2* qwin, const CycleSlots& slots,
                       unsigned long long* acc, int32_t close_scan_max, const FusedCycles& P,

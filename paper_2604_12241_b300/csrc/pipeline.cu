@@ -428,6 +428,137 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       L2 = DBuf<int32_t>((size_t)E + 1, s);
       off2 = DBuf<int64_t>((size_t)E + 1, s);
     }
+    // 3. scatter-gather: bucket the n_rec leg records, group each bucket by
+    // (s, d) (beside the cycle search: disjoint accumulator columns); true
+    // when that runs on the SG branch, which the caller joins back to s.
+    // skip: a device error word that, once set, leaves the records alone.
+    auto sg_group = [&](const LegRec* recp, uint32_t* histp, int64_t nbk, int bits,
+                        int64_t n_rec, KeySet ks, const uint32_t* skip) {
+      const bool on_branch = branches && sg_any && n_rec > 1;
+      if (on_branch) branch_wait(g->branch_ev[2], s, s_sg);
+      if (sg_any && n_rec > 1) {
+        cudaStream_t t = on_branch ? s_sg : s;
+        // bucket starts (the sizes sum to < 2^32, so the 32-bit scan is exact
+        // read as unsigned); the partition leaves the bucket ends
+        scan_i32(reinterpret_cast<const int32_t*>(histp), reinterpret_cast<int32_t*>(histp),
+                 nbk, false, t);
+        DBuf<LegRec> part((size_t)n_rec, t);
+        AML_LAUNCH("k_sg_partition", t,
+                   k_sg_partition<<<grid_for(n_rec, 256 * SG_PART_ITEMS), 256, 0, t>>>(
+                       recp, n_rec, bits, ks, histp, part.p, skip));
+        // buckets beyond SG_CAP records: listed by k_sg_bucket, grouped by
+        // k_sg_bucket_big (one large-table block per SM)
+        DBuf<uint32_t> overflow((size_t)nbk + 1, t);
+        AML_CUDA(cudaMemsetAsync(overflow.p, 0, sizeof(uint32_t), t));
+        unsigned long long* acc_sg = wp.sg ? acc.p + (int64_t)wp.sg_slot * E : nullptr;
+        launch_sg_buckets((unsigned)nbk, t, part.p, histp, wp.delta, g->dts, gv.ts, acc_sg,
+                          new_from, overflow.p, sub, skip);
+      }
+      return on_branch;
+    };
+    // SG buckets of about sg_bucket_mean records each
+    auto bucket_count = [&](int64_t n_records, int* bits) {
+      int64_t nbk = 1;
+      while (nbk * tn.sg_bucket_mean < n_records) nbk <<= 1;
+      *bits = 0;
+      while ((1ll << *bits) < nbk) ++*bits;
+      return nbk;
+    };
+
+    // The fused mine (AML_MINE_FUSED): leg count, leg offsets, leg emission
+    // and every cycle level in one cooperative launch, once an earlier mine
+    // of this graph has found the sizes of this window's legs and levels;
+    // the SG grouping follows it (the DEG/FAN branch runs beside it).
+    LegCache& lcf = g->legs[wp.delta];
+    bool fused_mine = (mode & AML_MINE_FUSED) && !persistent && new_from == 0 &&
+                      wp.emit_legs() && lcf.n_legs >= 0 &&
+                      (!level_cycles || lcf.n_front[2] >= 0);
+    for (int j = 3; fused_mine && level_cycles && j <= wp.K - 1; ++j)
+      fused_mine = lcf.n_front[j] >= 0;
+    if (fused_mine) {
+      const int64_t nl = lcf.n_legs, n2 = level_cycles ? lcf.n_front[2] : 0;
+      DBuf<int32_t> L((size_t)E + 1, s);
+      DBuf<int2> qwin((size_t)E, s);
+      DBuf<int32_t> qcb(level_cycles ? (size_t)E : 0, s);
+      int32_t* gs_in = nullptr;
+      if (wp.gs) {  // gather-side GS counts: zeroed by the count, added to by the emission
+        keep32.emplace_back((size_t)E, s);
+        gs_in = keep32.back().p;
+        P.gs_in[w] = gs_in;
+      }
+      keep64.emplace_back((size_t)(E + 1), s);
+      int64_t* off = keep64.back().p;
+      P.off[w] = off;
+      FusedLegs Q;
+      std::memset(&Q, 0, sizeof(Q));
+      Q.delta = wp.delta;
+      Q.L = L.p;
+      Q.qwin = qwin.p;
+      Q.qcb = qcb.p;
+      Q.Z = ZeroSink{acc_zeroed ? nullptr : acc.p, acc_zeroed ? 0 : n_acc, gs_in};
+      acc_zeroed = true;
+      Q.off = off;
+      DBuf<int4> legs;
+      if (level_cycles) {
+        legs = DBuf<int4>((size_t)std::max<int64_t>(n2, 1), s);
+        Q.anc = anc.p;
+        Q.L2 = L2.p;
+        Q.off2 = off2.p;
+        Q.S.leg = legs.p;
+        Q.S.off2 = off2.p;
+      }
+      DBuf<LegRec> rec;
+      DBuf<uint32_t> hist;
+      int64_t nb = 1;
+      if (sg_any) {
+        rec = DBuf<LegRec>((size_t)std::max<int64_t>(nl, 1), s);
+        nb = bucket_count(nl, &Q.S.bits);
+        hist = DBuf<uint32_t>((size_t)nb + 1, s);
+        AML_CUDA(cudaMemsetAsync(hist.p, 0, (size_t)(nb + 1) * 4, s));
+        Q.S.rec = rec.p;
+        Q.S.hist = hist.p;
+      }
+      Q.acc_cyc2 = wp.cyc.slot[2] >= 0 ? acc.p + (int64_t)wp.cyc.slot[2] * E : nullptr;
+      Q.gs_in = gs_in;
+      Q.own_max = tn.own_max;
+      Q.n_legs = nl;
+      Q.n2 = n2;
+      FusedCycles FC;
+      std::memset(&FC, 0, sizeof(FC));
+      FC.F.base = 2;
+      FC.F.leg = legs.p;
+      FC.n2 = n2;
+      std::vector<DBuf<int32_t>> front;
+      front.reserve(2 * MAX_CYCLE);
+      int64_t widest = 1;  // the largest level with children
+      for (int j = 2; level_cycles && j <= wp.K - 2; ++j) widest = std::max(widest, lcf.n_front[j]);
+      for (int j = 3; level_cycles && j <= wp.K - 1; ++j) {
+        FC.cap[j] = lcf.n_front[j];
+        front.emplace_back((size_t)std::max<int64_t>(lcf.n_front[j], 1), s);
+        FC.par[j] = front.back().p;
+        front.emplace_back((size_t)std::max<int64_t>(lcf.n_front[j], 1), s);
+        FC.slot[j] = front.back().p;
+      }
+      const int grid = fused_mine_grid(sub.n);
+      DBuf<int32_t> cnt((size_t)widest, s), q0b((size_t)widest, s);
+      DBuf<long long> bsum((size_t)2 * grid, s);
+      DBuf<GridBarrier> bar(1, s);
+      AML_CUDA(cudaMemsetAsync(bar.p, 0, sizeof(GridBarrier), s));
+      FC.cnt = cnt.p;
+      FC.q0 = q0b.p;
+      FC.bsum = bsum.p;
+      FC.bar = bar.p;
+      FC.err = g->err;
+      FC.wait_limit = g->wait_limit;
+      FC.own_max = tn.own_max;
+      Q.bsum = bsum.p;
+      launch_mine_fused(grid, s, gv, Q, wp.K, wp.cyc, acc.p, tn.close_scan_max, FC, sub);
+      // the records are complete only if every barrier of the launch was met
+      if (sg_group(rec.p, hist.p, nb, Q.S.bits, sg_any ? nl : 0, KeySet{nullptr, 0}, g->err))
+        branch_wait(g->branch_ev[3], s_sg, s);
+      continue;
+    }
+
     DBuf<int32_t> L(E + 1, s);
     int32_t* L_new = nullptr;
     if (new_from > 0 && wp.gs) {
@@ -495,10 +626,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     DBuf<uint32_t> dmask;
     DBuf<unsigned long long> n_rec;
     auto size_buckets = [&](int64_t n_records) {
-      nb = 1;
-      while (nb * tn.sg_bucket_mean < n_records) nb <<= 1;
-      S.bits = 0;
-      while ((1ll << S.bits) < nb) ++S.bits;
+      nb = bucket_count(n_records, &S.bits);
       hist = DBuf<uint32_t>((size_t)nb + 1, s);
       AML_CUDA(cudaMemsetAsync(hist.p, 0, (size_t)(nb + 1) * 4, s));
     };
@@ -597,29 +725,7 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
                    k_sg_hist<<<grid_for(n_sg, 256), 256, 0, s>>>(rec.p, n_sg, S.bits, ks, hist.p));
       }
     }
-    // 3. scatter-gather: bucket the leg records, group each bucket by (s, d)
-    // (beside the cycle search: disjoint accumulator columns)
-    const bool sg_branch = branches && sg_any && n_sg > 1;
-    if (sg_branch) branch_wait(g->branch_ev[2], s, s_sg);
-    if (sg_any && n_sg > 1) {
-      cudaStream_t t = sg_branch ? s_sg : s;
-      const int64_t nl = n_sg;
-      // bucket starts (the sizes sum to < 2^32, so the 32-bit scan is exact
-      // read as unsigned); the partition leaves the bucket ends
-      scan_i32(reinterpret_cast<const int32_t*>(hist.p), reinterpret_cast<int32_t*>(hist.p), nb,
-               false, t);
-      DBuf<LegRec> part((size_t)nl, t);
-      AML_LAUNCH("k_sg_partition", t,
-                 k_sg_partition<<<grid_for(nl, 256 * SG_PART_ITEMS), 256, 0, t>>>(
-                     rec.p, nl, S.bits, ks, hist.p, part.p));
-      // buckets beyond SG_CAP records: listed by k_sg_bucket, grouped by
-      // k_sg_bucket_big (one large-table block per SM)
-      DBuf<uint32_t> overflow((size_t)nb + 1, t);
-      AML_CUDA(cudaMemsetAsync(overflow.p, 0, sizeof(uint32_t), t));
-      unsigned long long* acc_sg = wp.sg ? acc.p + (int64_t)wp.sg_slot * E : nullptr;
-      launch_sg_buckets((unsigned)nb, t, part.p, hist.p, wp.delta, g->dts, gv.ts, acc_sg,
-                        new_from, overflow.p, sub);
-    }
+    const bool sg_branch = sg_group(rec.p, hist.p, nb, S.bits, n_sg, ks, nullptr);
     // 4. cycles of length >= 3: the cost-binned hybrid (heaviest anchors
     // level by level, the rest in one persistent launch beside them) ...
     if (wp.K >= 3 && persistent) {

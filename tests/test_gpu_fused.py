@@ -1,10 +1,12 @@
-"""The fused persistent cycle search (AML_MINE_FUSED): every level of the
-cycle search in one cooperative launch whose blocks meet at grid-wide
-barriers.  Its counts equal the oracle's and the plain mine's, replayed from
-a captured CUDA graph too, on tiny-10k, on a hub graph and at hi-small's
-full size (sampled oracle rows, every row against the plain mine); a
-barrier wait that runs out (wait limit 0) ends the launch with AML_ETIMEOUT
-at aml_sync and leaves the context usable."""
+"""The fused persistent mine (AML_MINE_FUSED): a window's leg pass (leg
+count, leg offsets, leg emission) and every level of its cycle search in one
+cooperative launch whose blocks meet at grid-wide barriers.  Its counts equal
+the oracle's and the plain mine's, replayed from a captured CUDA graph too,
+on tiny-10k, on a hub graph, on graphs with fewer edges than the launch has
+blocks, on pattern sets without cycles, and at hi-small's full size (sampled
+oracle rows, every row against the plain mine); the fused launch replaces the
+separate leg and cycle kernels; a barrier wait that runs out (wait limit 0)
+ends the launch with AML_ETIMEOUT at aml_sync and leaves the context usable."""
 import numpy as np
 import pytest
 
@@ -32,6 +34,65 @@ def test_fused_equals_oracle_tiny_10k(kmax):
         np.testing.assert_array_equal(_mine(graph, ps, mode="fused"), want)
     for _ in range(3):
         np.testing.assert_array_equal(_mine(graph, ps, mode="fused", use_graph=True), want)
+    graph.sync()
+    graph.close()
+
+
+def test_fused_launch_replaces_leg_and_cycle_kernels():
+    from paper_2604_12241_b300 import _lib
+    g = aml_synth.workload("tiny-10k")
+    pats = P.standard(P.DAY, 5)
+    ps = aml.PatternSet(pats)
+    graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes, assume_sorted=True)
+    want = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes).count_all(oracle_columns(pats))
+    np.testing.assert_array_equal(_mine(graph, ps, mode="fused"), want)  # learns the sizes
+    graph.sync()
+    _lib.profile_enable(True)
+    try:
+        _lib.profile_read(reset=True)
+        np.testing.assert_array_equal(_mine(graph, ps, mode="fused"), want)
+        graph.sync()
+        ran = _lib.profile_read(reset=True)
+    finally:
+        _lib.profile_enable(False)
+    assert ran.get("k_mine_fused", (0, 0.0))[0] == 1, ran
+    for k in ("k_leg_count", "k_leg_emit", "k_cyc_level", "k_cyc_emit", "k_cyc_fused"):
+        assert k not in ran, ran
+    assert "k_sg_bucket" in ran and "k_assemble" in ran
+    graph.close()
+
+
+@pytest.mark.parametrize("n_edges", [1, 37, 700, 5000])
+def test_fused_with_fewer_edges_than_blocks(n_edges):
+    """Chunks of zero or one edge: most blocks of the launch count and emit
+    nothing but still meet every barrier."""
+    rng = np.random.default_rng(n_edges)
+    N = max(4, n_edges // 6)
+    src = rng.integers(0, N, n_edges).astype(np.int32)
+    dst = rng.integers(0, N, n_edges).astype(np.int32)
+    ts = np.sort(rng.integers(0, 3 * 3600, n_edges)).astype(np.int32)
+    pats = P.standard(3600, 5)
+    ps = aml.PatternSet(pats)
+    graph = aml.Graph(src, dst, ts, N, assume_sorted=True)
+    want = oracle.OracleGraph(src, dst, ts, N).count_all(oracle_columns(pats))
+    for _ in range(3):
+        np.testing.assert_array_equal(_mine(graph, ps, mode="fused"), want)
+    np.testing.assert_array_equal(_mine(graph, ps, mode="fused", use_graph=True), want)
+    graph.sync()
+    graph.close()
+
+
+def test_fused_without_cycles():
+    """GS, SG and 2-cycles only: the launch ends after the leg emission."""
+    g = aml_synth.workload("tiny-10k")
+    pats = [p for p in P.standard(P.DAY, 2) + P.standard(P.WEEK, 2)]
+    ps = aml.PatternSet(pats)
+    graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes, assume_sorted=True)
+    want = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes).count_all(oracle_columns(pats))
+    assert want[:, [p.name.startswith("SG") for p in pats]].sum() > 0
+    for _ in range(3):
+        np.testing.assert_array_equal(_mine(graph, ps, mode="fused"), want)
+    np.testing.assert_array_equal(_mine(graph, ps, mode="fused", use_graph=True), want)
     graph.sync()
     graph.close()
 
