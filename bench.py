@@ -475,7 +475,7 @@ def cpu_baseline(g, pats, seconds: float) -> dict:
 
 # ---------------------------------------------------------------- streaming
 
-STREAM_DAYS = 24        # the stream's graph: hi-medium's shape and daily rate, 24 days
+STREAM_DAYS = 31        # the stream's graph: hi-medium's shape and daily rate, 31 days
 STREAM_PRE_DAYS = 9     # appended untimed before the measured batches
 STREAM_LOADS = (0.25, 0.5, 0.9)
 
@@ -483,13 +483,14 @@ STREAM_LOADS = (0.25, 0.5, 0.9)
 def run_stream(args, rank) -> dict:
     """Streaming serving (the fifth workload): a HI-Medium-shaped graph
     (2,032,095 accounts, Zipf 1.05, hubs to 1e5) at HI-Medium's rate of
-    about 2M transactions a day, generated over 24 days so that enough
+    about 2M transactions a day, generated over 31 days so that enough
     batches arrive; 20 columns, a 7-day resident window.  The first 9 days
     are appended in 2M-edge batches (untimed).  Then batches of log-uniform
     size in [1e3, 1e5] arrive: first back to back (service time, capacity),
     then as Poisson processes offered at 25%, 50% and 90% of the measured
     capacity (latency = queueing + service), ``--stream-batches`` batches at
-    each load."""
+    each load, served one batch per append and again with the queued
+    batches merged into one append."""
     import aml_synth
     import paper_2604_12241_b300 as aml
     from paper_2604_12241_b300 import patterns as P
@@ -529,33 +530,57 @@ def run_stream(args, rank) -> dict:
     cap_eps = sum(sizes) / sum(service)               # edges/s, back to back
     mean_n = float(np.mean(sizes))
     ms = lambda v, q: float(np.percentile(np.asarray(v) * 1e3, q)) if v else None
-    loads = {}
-    for load in STREAM_LOADS:
+    # Offered loads.  A batch's latency runs from its arrival to the end of
+    # the append that holds it.  "one batch per append" serves the queue in
+    # arrival order; "queued batches merged" appends, whenever the server
+    # is free, every batch that has arrived by then as one (consecutive
+    # batches are one time-ordered slice), so a burst costs one recount
+    # instead of one per batch.  Counts are the same either way.
+    def serve(load, merge):
         lam = load * cap_eps / mean_n                 # batches/s
-        lat, sizes2 = [], []
-        t_start = t_next = time.perf_counter()
+        arr, sl = [], []
+        t = 0.0
         for _ in range(args.stream_batches):
             if pos >= g.n_edges:
                 break
-            t_next += rng.exponential(1.0 / lam)
+            t += rng.exponential(1.0 / lam)
+            lo = pos
             b = next_batch()
-            now = time.perf_counter()
-            if now < t_next:
-                time.sleep(t_next - now)
-            st.append(*b)
-            lat.append(time.perf_counter() - t_next)
-            sizes2.append(len(b[0]))
+            arr.append(t)
+            sl.append((lo, lo + len(b[0])))
+        lat, appends = [], 0
+        t_start = time.perf_counter()
+        k = 0
+        while k < len(arr):
+            now = time.perf_counter() - t_start
+            if now < arr[k]:
+                time.sleep(arr[k] - now)
+                now = time.perf_counter() - t_start
+            j = k + 1
+            while merge and j < len(arr) and arr[j] <= now:
+                j += 1
+            lo, hi = sl[k][0], sl[j - 1][1]
+            st.append(g.src[lo:hi], g.dst[lo:hi], g.ts[lo:hi], g.amount[lo:hi])
+            done = time.perf_counter() - t_start
+            lat.extend(done - a for a in arr[k:j])
+            appends += 1
+            k = j
         span = time.perf_counter() - t_start
-        loads[f"load_{int(round(load * 100))}pct"] = {
-            "batches": len(lat), "p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99),
-            "max_ms": ms(lat, 100), "edges_per_s": sum(sizes2) / span if lat else None,
-            "arrivals": "Poisson, batches/s = %.2f" % lam}
+        return {"batches": len(lat), "appends": appends, "p50_ms": ms(lat, 50),
+                "p99_ms": ms(lat, 99), "max_ms": ms(lat, 100),
+                "edges_per_s": (sl[-1][1] - sl[0][0]) / span if lat else None,
+                "arrivals": "Poisson, batches/s = %.2f" % lam}
+
+    loads = {}
+    for load in STREAM_LOADS:
+        one = serve(load, False)
+        loads[f"load_{int(round(load * 100))}pct"] = dict(one, merged=serve(load, True))
     info = st.info()
     st.close()
     return {"workload": ("hi-medium shape (2,032,095 accounts, Zipf 1.05, hubs to 1e5) at "
-                         "~2.0M transactions/day over 24 days; 7-day resident window, 20 columns"),
+                         "~2.0M transactions/day over 31 days; 7-day resident window, 20 columns"),
             "resident_rows": info["resident_rows"], "batches": len(service) + sum(
-                v["batches"] for v in loads.values()),
+                v["batches"] + v["merged"]["batches"] for v in loads.values()),
             "batch_edges": "log-uniform in [1e3, 1e5]",
             "service_batches": len(service),
             "service_ms_p50": ms(service, 50), "service_ms_p99": ms(service, 99),
@@ -901,7 +926,9 @@ def run_ours(args, ws, rank, local):
         st = run_stream(args, rank)
         if line is not None:
             line["stream"] = st
-            line["p99_stream_latency_ms"] = st["load_50pct"]["p99_ms"]
+            # the serving loop merges queued batches; one append per batch beside it
+            line["p99_stream_latency_ms"] = st["load_50pct"]["merged"]["p99_ms"]
+            line["p99_stream_latency_ms_one_per_append"] = st["load_50pct"]["p99_ms"]
     if not args.no_large and args.workload != "hi-large":
         large = run_large(args, rank, local)
         if line is not None:

@@ -1693,9 +1693,9 @@ __device__ __forceinline__ long long fused_block_excl(long long v, long long* s_
   return before + x - v;
 }
 
-// every level of the cycle search from the n2 cycle legs of P.F (the body
-// of k_cyc_fused, and the fused mine's last phase); false if a barrier wait
-// ran out or a level outgrew its buffers
+// every level of the cycle search from the n2 cycle legs of P.F (the fused
+// mine's last phase); false if a barrier wait ran out or a level outgrew its
+// buffers
 template <int NS>
 __device__ __forceinline__ bool cyc_fused_levels(const CycLevelArgs& A, const FusedCycles& P,
                                                  const SubWindows& sub, int64_t n2,
@@ -1776,20 +1776,11 @@ __device__ __forceinline__ bool cyc_fused_levels(const CycLevelArgs& A, const Fu
   return true;
 }
 
-template <int NS>
-__global__ void __launch_bounds__(FUSED_BLOCK, 3) k_cyc_fused(CycLevelArgs A, FusedCycles P,
-                                                            SubWindows sub) {
-  __shared__ long long s_w[FUSED_BLOCK / 32];
-  cyc_fused_levels<NS>(A, P, sub, P.n2, s_w);
-}
-
 // The fused mine (FusedLegs): P.bar, P.err and P.wait_limit serve every
-// barrier; K >= 3 runs the cycle levels after the legs.
-#ifndef AML_FUSED_MIN_BLOCKS
-#define AML_FUSED_MIN_BLOCKS 3
-#endif
+// barrier; K >= 3 runs the cycle levels after the legs.  3 blocks of 512
+// per SM at 40 registers (with spills) measured faster than 2 at 64.
 template <int NS>
-__global__ void __launch_bounds__(FUSED_BLOCK, AML_FUSED_MIN_BLOCKS) k_mine_fused(GraphView g, FusedLegs Q,
+__global__ void __launch_bounds__(FUSED_BLOCK, 3) k_mine_fused(GraphView g, FusedLegs Q,
                                                              CycLevelArgs A, FusedCycles P,
                                                              SubWindows sub) {
   __shared__ long long s_w[FUSED_BLOCK / 32];
@@ -1904,47 +1895,6 @@ void launch_mine_fused(int grid, cudaStream_t s, const GraphView& g, const Fused
     AML_LAUNCH("k_mine_fused", s,
                AML_CUDA(cudaLaunchKernelEx(&cfg, k_mine_fused<decltype(ns)::value>, g, Q, A, P,
                                            sub)));
-  });
-}
-
-template <int NS>
-static void fused_smem_blocks(int* per_sm) {
-  AML_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_cyc_fused<NS>, FUSED_BLOCK,
-                                                         0));
-}
-
-int fused_cycle_grid(int n_sub) {
-  static int cached[64][MAX_SUB + 1] = {};
-  int dev = 0;
-  AML_CUDA(cudaGetDevice(&dev));
-  int per_sm = 0;
-  const int key = n_sub <= 0 ? 0 : n_sub == 1 ? 1 : n_sub == 2 ? 2 : MAX_SUB;
-  if (dev < 64 && cached[dev][key]) return cached[dev][key];
-  nsub_dispatch(n_sub, [&](auto ns) { fused_smem_blocks<decltype(ns)::value>(&per_sm); });
-  AML_REQUIRE(per_sm >= 1, AML_EUNSUPPORTED, "the fused cycle kernel cannot be resident");
-  const int grid = per_sm * sm_count();
-  if (dev < 64) cached[dev][key] = grid;
-  return grid;
-}
-
-void launch_cyc_fused(int grid, cudaStream_t s, const GraphView& g, int32_t delta, int K,
-                      const AnchorRec* anc, const int2* qwin, const CycleSlots& slots,
-                      unsigned long long* acc, int32_t close_scan_max, const FusedCycles& P,
-                      const SubWindows& sub) {
-  const CycLevelArgs A{g, delta, K, nullptr, anc, qwin, slots, acc, close_scan_max};
-  nsub_dispatch(sub.n, [&](auto ns) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(FUSED_BLOCK);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    AML_LAUNCH("k_cyc_fused", s,
-               AML_CUDA(cudaLaunchKernelEx(&cfg, k_cyc_fused<decltype(ns)::value>, A, P, sub)));
   });
 }
 

@@ -232,12 +232,11 @@ struct GridBarrier {
   unsigned int count;
   unsigned int gen;
 };
-// The fused cycle search: every level in one cooperative launch.  par/slot
-// of levels 3..K-1 hold cap[j] elements; cnt/q0 hold the largest level that
-// has children; bsum one value per block.
+// The cycle levels of the fused mine.  par/slot of levels 3..K-1 hold
+// cap[j] elements; cnt/q0 hold the largest level that has children; bsum
+// one value per block.
 struct FusedCycles {
   CycFrontier F;  // base level (the legs)
-  int64_t n2;
   int64_t cap[MAX_CYCLE + 1];
   int32_t* par[MAX_CYCLE + 1];
   int32_t* slot[MAX_CYCLE + 1];
@@ -274,15 +273,10 @@ struct FusedLegs {
   long long* bsum;  // two values per block
 };
 // blocks of the fused launches on this device (all resident at once)
-int fused_cycle_grid(int n_sub);
 int fused_mine_grid(int n_sub);
 void launch_mine_fused(int grid, cudaStream_t s, const GraphView& g, const FusedLegs& Q, int K,
                        const CycleSlots& slots, unsigned long long* acc, int32_t close_scan_max,
                        const FusedCycles& P, const SubWindows& sub);
-void launch_cyc_fused(int grid, cudaStream_t s, const GraphView& g, int32_t delta, int K,
-                      const AnchorRec* anc, const int2* qwin, const CycleSlots& slots,
-                      unsigned long long* acc, int32_t close_scan_max, const FusedCycles& P,
-                      const SubWindows& sub);
 __global__ void k_assemble(AssembleParams P);
 
 // Host pipeline: enqueue a full mine of `ps` on `g` into device `counts`.

@@ -170,51 +170,6 @@ void level_cycle_search(aml_graph* g, const GraphView& gv, int32_t delta, int K,
   }
 }
 
-// The same search in one cooperative launch (k_cyc_fused), once the sizes of
-// every level are known (a plain search learns them first).
-void level_cycle_search_fused(aml_graph* g, const GraphView& gv, int32_t delta, int K,
-                              const CycleSlots& slots, const SubWindows& sub,
-                              unsigned long long* acc, const AnchorRec* anc,
-                              const int2* qwin, const int4* legs, int64_t* front_cache,
-                              cudaStream_t s) {
-  for (int j = 3; j <= K - 1; ++j)
-    if (front_cache[j] < 0) {
-      level_cycle_search(g, gv, delta, K, slots, sub, acc, anc, qwin, legs, front_cache, s);
-      return;
-    }
-  const int64_t n2 = front_cache[2];
-  if (n2 <= 0 || K < 3) return;
-  FusedCycles P;
-  std::memset(&P, 0, sizeof(P));
-  P.F.base = 2;
-  P.F.leg = legs;
-  P.n2 = n2;
-  std::vector<DBuf<int32_t>> front;
-  front.reserve(2 * MAX_CYCLE);
-  int64_t widest = 1;  // the largest level with children
-  for (int j = 2; j <= K - 2; ++j) widest = std::max(widest, front_cache[j]);
-  for (int j = 3; j <= K - 1; ++j) {
-    P.cap[j] = front_cache[j];
-    front.emplace_back((size_t)std::max<int64_t>(front_cache[j], 1), s);
-    P.par[j] = front.back().p;
-    front.emplace_back((size_t)std::max<int64_t>(front_cache[j], 1), s);
-    P.slot[j] = front.back().p;
-  }
-  const int grid = fused_cycle_grid(sub.n);
-  DBuf<int32_t> cnt((size_t)widest, s), q0((size_t)widest, s);
-  DBuf<long long> bsum((size_t)grid, s);
-  DBuf<GridBarrier> bar(1, s);
-  AML_CUDA(cudaMemsetAsync(bar.p, 0, sizeof(GridBarrier), s));
-  P.cnt = cnt.p;
-  P.q0 = q0.p;
-  P.bsum = bsum.p;
-  P.bar = bar.p;
-  P.err = g->err;
-  P.wait_limit = g->wait_limit;
-  P.own_max = g->tune.own_max;
-  launch_cyc_fused(grid, s, gv, delta, K, anc, qwin, slots, acc, g->tune.close_scan_max, P, sub);
-}
-
 void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64_t ld,
                 cudaStream_t s, uint32_t mode, int32_t new_from, int32_t t_new, bool accumulate) {
   const bool persistent = (mode & (AML_MINE_PERSISTENT | AML_MINE_LEARNED)) != 0;
@@ -527,7 +482,6 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       std::memset(&FC, 0, sizeof(FC));
       FC.F.base = 2;
       FC.F.leg = legs.p;
-      FC.n2 = n2;
       std::vector<DBuf<int32_t>> front;
       front.reserve(2 * MAX_CYCLE);
       int64_t widest = 1;  // the largest level with children
@@ -731,9 +685,6 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
     if (wp.K >= 3 && persistent) {
       cycles_hybrid(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, crng.p, anc.p, qwin.p, legs.p,
                     (mode & AML_MINE_LEARNED) != 0, s, branches ? g->side[2] : s);
-    } else if (level_cycles && (mode & AML_MINE_FUSED)) {  // ... or all levels in one launch
-      level_cycle_search_fused(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, anc.p, qwin.p, legs.p,
-                               lc.n_front, s);
     } else if (level_cycles) {  // ... or level by level from the legs
       level_cycle_search(g, gv, wp.delta, wp.K, wp.cyc, sub, acc.p, anc.p, qwin.p, legs.p,
                          lc.n_front, s);
