@@ -97,6 +97,23 @@ def test_fused_without_cycles():
     graph.close()
 
 
+def test_fused_with_two_leg_passes():
+    """A 24-hour window with longer cycles than the 7-day one gets a leg
+    pass (and a fused launch) of its own; the second launch finds the
+    accumulators already zeroed by the first and runs beside the first
+    window's SG grouping."""
+    g = aml_synth.workload("tiny-10k")
+    pats = P.standard(P.DAY, 5) + P.standard(P.WEEK, 3)
+    ps = aml.PatternSet(pats)
+    graph = aml.Graph(g.src, g.dst, g.ts, g.n_nodes, assume_sorted=True)
+    want = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes).count_all(oracle_columns(pats))
+    for _ in range(3):
+        np.testing.assert_array_equal(_mine(graph, ps, mode="fused"), want)
+    np.testing.assert_array_equal(_mine(graph, ps, mode="fused", use_graph=True), want)
+    graph.sync()
+    graph.close()
+
+
 def test_fused_on_hub_graph():
     """A few accounts with most of the edges: long child lists written by
     whole warps, and chunks of the frontier that start inside one path's
