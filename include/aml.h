@@ -205,8 +205,16 @@ typedef struct aml_stage {
                              /* n-intermediary motif (Sec. 4's variable number  */
                              /* of intermediaries), n legs with one source and  */
                              /* one destination, on each of its 2n edges; n = 2 */
-                             /* is the SG column.  Any other program with this  */
-                             /* aggregate: AML_EUNSUPPORTED.                    */
+                             /* is the SG column.  Also counted for the stacked  */
+                             /* bipartite read for Sec. 8's "Stack" pattern     */
+                             /* (the trigger s1->m1, N0.out -> m2, N1.in        */
+                             /* intersected with N2.in -> s2, then N1.out       */
+                             /* intersected with N2.out -> r1 and again -> r2,  */
+                             /* each new account skipping those bound before    */
+                             /* it, no order, every stage in the span window):  */
+                             /* each instance of eight edges once on each of    */
+                             /* them.  Any other program with this aggregate:   */
+                             /* AML_EUNSUPPORTED.                               */
 
 #define AML_PAT_INTERPRET 0x1  /* run the program through the generic        */
                                /* interpreter even when a family matches it    */

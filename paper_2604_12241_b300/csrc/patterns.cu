@@ -106,6 +106,19 @@ std::vector<aml_stage> scatter_gather_n(int n) {
   return v;
 }
 
+// The stacked bipartite ("Stack"): trigger s1 -> m1, s1.out -> m2, then
+// s2 from m1.in intersected with m2.in, r1 and r2 from m1.out intersected
+// with m2.out, each new account skipping the ones bound before it, every
+// stage in the span window, no order.
+std::vector<aml_stage> stack_stages() {
+  const int O = AML_DIR_OUT, I = AML_DIR_IN, SP = AML_WIN_SPAN;
+  const int F = AML_OP_FOR_ALL, X = AML_OP_INTERSECT;
+  return {trigger(), st(F, 0, O, -1, 0, 2, AML_ORDER_NONE, SP, bits_upto(1)),
+          st(X, 1, I, 2, I, 3, AML_ORDER_NONE, SP, bits_upto(2)),
+          st(X, 1, O, 2, O, 4, AML_ORDER_NONE, SP, bits_upto(3)),
+          st(X, 1, O, 2, O, 5, AML_ORDER_NONE, SP, bits_upto(4))};
+}
+
 bool same_stage(const aml_stage& a, const aml_stage& b) {
   if (a.op != b.op || a.out_var != b.out_var) return false;
   if (a.amount_flags != b.amount_flags) return false;  // families have no amount constraints
@@ -222,6 +235,22 @@ std::vector<Column> plan_patterns(const aml_pattern* pats, int n, std::vector<Pr
     validate(pats[p], p);
     const aml_pattern& pat = pats[p];
     if (pat.aggregate == AML_AGG_SETS) {
+      // the stacked bipartite: every instance (eight edges) is found from
+      // each of its four first-layer edges, with its two receivers in both
+      // orders: 8 bindings that all credit its eight edges
+      {
+        const std::vector<aml_stage> t = stack_stages();
+        bool is_stack = pat.n_stages == (int)t.size();
+        for (int s = 0; s < pat.n_stages && is_stack; ++s) is_stack = same_stage(pat.stages[s], t[s]);
+        if (is_stack) {
+          Prog g = interpretable(pat, p);
+          g.agg = AML_AGG_INSTANCES;
+          g.div = 8;
+          progs->push_back(g);
+          cols.push_back(Column{AML_FAM_PROGRAM, 0, pat.delta, (int32_t)progs->size() - 1});
+          continue;
+        }
+      }
       // the scatter-gather of n intermediaries: every set of n legs is found
       // from each of its n scatter edges with the other n - 1 legs in every
       // order of the intersections, n! bindings that all credit its 2n edges
@@ -234,7 +263,7 @@ std::vector<Column> plan_patterns(const aml_pattern* pats, int n, std::vector<Pr
       }
       AML_REQUIRE(ok, AML_EUNSUPPORTED,
                   where(p, 0) + "AML_AGG_SETS is counted for the scatter-gather of n "
-                                "intermediaries (2 <= n <= 7) only");
+                                "intermediaries (2 <= n <= 7) and the stacked bipartite only");
       if (n_int == 2 && !(pat.flags & AML_PAT_INTERPRET)) {
         cols.push_back(Column{AML_FAM_SG, 0, pat.delta});  // a set of two legs: an SG pair
         continue;

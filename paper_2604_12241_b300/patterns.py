@@ -209,6 +209,29 @@ def scatter_gather_nodes(delta: int) -> Pattern:
     return Pattern(p.stages, AGG_DISTINCT, delta, f"SG_NODES@{delta}", interpret=True)
 
 
+def stack(delta: int) -> Pattern:
+    """The "Stack" pattern (benchmarked in Sec. 8, Fig. 9, never defined in
+    the text), read as the stacked bipartite of the laundering-pattern
+    catalogue that the paper's Fig. 2 draws on: two senders s1, s2 that each
+    pay both of two middle accounts m1, m2 (a complete first layer), and
+    m1, m2 that each pay both of two receivers r1, r2 (a complete second
+    layer); six distinct accounts, eight transfers, all within delta (no
+    order inside the instance beyond the window).  The program: trigger
+    s1 -> m1, s1's out-edge to m2, s2 from m1.in intersected with m2.in, then
+    r1 and r2 from m1.out intersected with m2.out.  With the SETS aggregate
+    each instance (its set of eight edges) counts once on each of its edges.
+    Every instance is found by 8 bindings (any of its 4 first-layer edges as
+    trigger, times the 2 orders of r1, r2), so the interpreter's per-binding
+    count is divided by 8."""
+    O, I, X, F, SP = DIR_OUT, DIR_IN, OP_INTERSECT, OP_FOR_ALL, WIN_SPAN
+    stages = (TRIGGER,
+              Stage(F, 0, O, out_var=2, window=SP, skip_eq=_skip(0, 1)),
+              Stage(X, 1, I, 2, I, out_var=3, window=SP, skip_eq=_skip(0, 1, 2)),
+              Stage(X, 1, O, 2, O, out_var=4, window=SP, skip_eq=_skip(0, 1, 2, 3)),
+              Stage(X, 1, O, 2, O, out_var=5, window=SP, skip_eq=_skip(0, 1, 2, 3, 4)))
+    return Pattern(stages, AGG_SETS, delta, f"STACK@{delta}", interpret=True)
+
+
 def cycle(k: int, delta: int, closing: str = "for_all") -> Pattern:
     """k-cycle: trigger N0 -> N1, then N_i.out -> N_{i+1} (later, new node),
     closed by an edge back into N0 -- or, for k >= 3, by intersecting

@@ -258,3 +258,40 @@ def test_exact_size_scatter_gathers_match_oracle_on_tiny10k():
         np.testing.assert_array_equal(got[:, j], want, err_msg=p.name)
         assert want.any(), p.name
     np.testing.assert_array_equal(got[:, 4:], og.count_all(oracle_columns(P.standard(P.DAY))))
+
+
+# ---- the stacked bipartite ("Stack", Sec. 8): SETS = bindings / 8 ----
+
+@pytest.mark.parametrize("seed", range(3))
+def test_stack_matches_oracle_on_dense_graphs(seed):
+    """The interpreter's per-binding count divided by the 8 bindings of every
+    instance, against the oracle's distinct edge sets, on dense small graphs
+    (parallel edges, ties, self-loops)."""
+    rng = np.random.default_rng(9300 + seed)
+    n, E = 7 + seed, 60 + 20 * seed
+    src = rng.integers(0, n, E).astype(np.int32)
+    dst = rng.integers(0, n, E).astype(np.int32)
+    ts = rng.integers(0, 20, E).astype(np.int32)
+    from types import SimpleNamespace
+    g = SimpleNamespace(src=src, dst=dst, ts=ts, n_nodes=n)
+    og = oracle.OracleGraph(src, dst, ts, n)
+    reached = 0
+    for delta in (3, 8, 40):
+        p = P.stack(delta)
+        got = _mine(g, [p])[:, 0]
+        want = og.program_count(_tuples(p), oracle.AGG_SETS, delta, threads=4)
+        np.testing.assert_array_equal(got, want, err_msg=f"delta {delta}")
+        reached += int((want > 0).sum())
+    assert reached > 0
+
+
+def test_stack_matches_oracle_on_tiny10k():
+    g = aml_synth.workload("tiny-10k")
+    og = oracle.OracleGraph(g.src, g.dst, g.ts, g.n_nodes)
+    pats = [P.stack(P.DAY), P.stack(3 * 3600)] + P.standard(P.DAY, 3)
+    got = _mine(g, pats)
+    for j, p in enumerate(pats[:2]):
+        want = og.program_count(_tuples(p), oracle.AGG_SETS, p.delta)
+        np.testing.assert_array_equal(got[:, j], want, err_msg=p.name)
+    assert got[:, 0].any()
+    np.testing.assert_array_equal(got[:, 2:], og.count_all(oracle_columns(P.standard(P.DAY, 3))))
