@@ -140,6 +140,9 @@ __device__ __forceinline__ unsigned long long walk(const GraphView& g, const flo
   unsigned long long found = 0;
   int work = 0;
   bool stopped = false;
+  // bit s: intersection stage s walks its b-side window and searches the
+  // a-side (degree-ordered intersection: the shorter window is walked)
+  uint32_t swp = 0;
 
   auto tick = [&]() {
     if (++work < PROG_FLUSH) return;
@@ -204,11 +207,27 @@ __device__ __forceinline__ unsigned long long walk(const GraphView& g, const flo
     else if (q.order == AML_ORDER_BEFORE) th = min(th, (int64_t)reach_t[A]);
     else if (q.order == AML_ORDER_AFTER_TRIGGER) tl = max(tl, (int64_t)t0);
     const int32_t lo = L.ptr[node[A]], end = L.ptr[node[A] + 1];
+    swp &= ~(1u << s);
     if (tl > th) {
       cur[s] = hi[s] = lo;
     } else {
       cur[s] = lower_t(L.t, lo, end, tl);
       hi[s] = lower_t(L.t, cur[s], end, th + 1);
+      // an intersection without order or amount constraints is symmetric in
+      // its two sides: walk the shorter window, search the other side's
+      // (counterparty, t, id) copy (Sec. 6's degree-ordered intersection);
+      // the bindings are the same pairs of edges either way
+      if (q.op == AML_OP_INTERSECT && q.order == AML_ORDER_NONE && !q.amt) {
+        const ListView LB = list_of(g, q.b_dir);
+        const int32_t lob = LB.ptr[node[q.b_var]], endb = LB.ptr[node[q.b_var] + 1];
+        const int32_t cb = lower_t(LB.t, lob, endb, tl);
+        const int32_t hb = lower_t(LB.t, cb, endb, th + 1);
+        if (hb - cb < hi[s] - cur[s]) {
+          swp |= 1u << s;
+          cur[s] = cb;
+          hi[s] = hb;
+        }
+      }
     }
     bcur[s] = bhi[s] = 0;
   };
@@ -241,25 +260,35 @@ __device__ __forceinline__ unsigned long long walk(const GraphView& g, const flo
       }
       return false;
     }
-    const ListView LB = list_of(g, q.b_dir);
+    // an intersection: the outer loop walks one side's time window (the
+    // a-side, or the b-side when swapped), the inner loop the other side's
+    // edges with the outer edge's far end x, from its (counterparty, t, id)
+    // copy
+    const bool sw = (swp >> s) & 1u;
+    const ListView LO = list_of(g, sw ? q.b_dir : q.a_dir);
+    const ListView LI = list_of(g, sw ? q.a_dir : q.b_dir);
+    const int32_t inode = node[sw ? q.a_var : q.b_var];
     while (true) {
       while (bcur[s] < bhi[s]) {
         tick();
         if (stopped) return false;
         const int32_t j = bcur[s]++;
-        const int32_t fb = LB.neid[j], tb = LB.nt[j];
-        const int32_t fa = ea[s], tfa = ta[s];
-        if ((q.order == AML_ORDER_AFTER || q.order == AML_ORDER_LEG) && !before(tfa, fa, tb, fb))
-          continue;
-        if (q.order == AML_ORDER_BEFORE && !before(tb, fb, tfa, fa)) continue;
-        if (q.order == AML_ORDER_AFTER_TRIGGER && !before(t0, e0, tb, fb)) continue;
-        if (!span && before(t0, e0, tb, fb)) continue;
-        if (!amount_ok(q, amount, fb, fa)) continue;
-        if (MODE == AGG_CREDIT && (fb == fa || used(fb, s))) continue;
-        eb[s] = fb;
-        tmin = span ? min(min(smin[s], tfa), tb) : smin[s];
-        tmax = span ? max(max(smax[s], tfa), tb) : smax[s];
-        bind(q, s, xa[s], fb, tb);
+        const int32_t fi = LI.neid[j], ti = LI.nt[j];
+        const int32_t fo = sw ? eb[s] : ea[s], to = ta[s];
+        if (!sw) {  // fo = fa (a-side), fi = fb (b-side)
+          if ((q.order == AML_ORDER_AFTER || q.order == AML_ORDER_LEG) && !before(to, fo, ti, fi))
+            continue;
+          if (q.order == AML_ORDER_BEFORE && !before(ti, fi, to, fo)) continue;
+          if (q.order == AML_ORDER_AFTER_TRIGGER && !before(t0, e0, ti, fi)) continue;
+          if (!amount_ok(q, amount, fi, fo)) continue;
+        }
+        if (!span && before(t0, e0, ti, fi)) continue;
+        if (MODE == AGG_CREDIT && (fi == fo || used(fi, s))) continue;
+        if (sw) ea[s] = fi; else eb[s] = fi;
+        tmin = span ? min(min(smin[s], to), ti) : smin[s];
+        tmax = span ? max(max(smax[s], to), ti) : smax[s];
+        // the new variable is reached by the b-side edge
+        if (sw) bind(q, s, xa[s], fo, to); else bind(q, s, xa[s], fi, ti);
         return true;
       }
       if (cur[s] >= hi[s]) return false;
@@ -267,35 +296,39 @@ __device__ __forceinline__ unsigned long long walk(const GraphView& g, const flo
       if (stopped) return false;
       const int32_t i = cur[s];
       cur[s] += (WARP && s == 1) ? 32 : 1;
-      const int32_t fa = LA.eid[i], x = LA.nbr[i], tfa = LA.t[i];
+      const int32_t fo = LO.eid[i], x = LO.nbr[i], to = LO.t[i];
       bhi[s] = bcur[s] = 0;
-      if (q.order == AML_ORDER_AFTER && !before(reach_t[A], reach_e[A], tfa, fa)) continue;
-      if (q.order == AML_ORDER_BEFORE && !before(tfa, fa, reach_t[A], reach_e[A])) continue;
-      if (q.order == AML_ORDER_AFTER_TRIGGER && !before(t0, e0, tfa, fa)) continue;
-      if (!span && before(t0, e0, tfa, fa)) continue;
+      if (!sw) {  // the a-side edge's order and amount constraints
+        if (q.order == AML_ORDER_AFTER && !before(reach_t[A], reach_e[A], to, fo)) continue;
+        if (q.order == AML_ORDER_BEFORE && !before(to, fo, reach_t[A], reach_e[A])) continue;
+        if (q.order == AML_ORDER_AFTER_TRIGGER && !before(t0, e0, to, fo)) continue;
+        if (!amount_ok(q, amount, fo, reach_e[A])) continue;
+      }
+      if (!span && before(t0, e0, to, fo)) continue;
       if (!node_ok(q, s, x)) continue;
-      if (!amount_ok(q, amount, fa, reach_e[A])) continue;
-      if (MODE == AGG_CREDIT && used(fa, s)) continue;
-      ea[s] = fa;
+      if (MODE == AGG_CREDIT && used(fo, s)) continue;
+      if (sw) eb[s] = fo; else ea[s] = fo;
       xa[s] = x;
-      ta[s] = tfa;
-      // the b-side edges: far end x, inside the window with fa in the span
+      ta[s] = to;
+      // the inner side's edges: far end x, inside the window with the outer
+      // edge in the span
       int64_t tl, th;
       if (span) {
-        tl = (int64_t)max(smax[s], tfa) - delta;
-        th = (int64_t)min(smin[s], tfa) + delta;
+        tl = (int64_t)max(smax[s], to) - delta;
+        th = (int64_t)min(smin[s], to) + delta;
       } else {
         tl = (int64_t)t0 - delta;
         th = t0;
       }
-      if (q.order == AML_ORDER_AFTER || q.order == AML_ORDER_LEG) tl = max(tl, (int64_t)tfa);
-      else if (q.order == AML_ORDER_BEFORE) th = min(th, (int64_t)tfa);
-      else if (q.order == AML_ORDER_AFTER_TRIGGER) tl = max(tl, (int64_t)t0);
+      if (!sw) {
+        if (q.order == AML_ORDER_AFTER || q.order == AML_ORDER_LEG) tl = max(tl, (int64_t)to);
+        else if (q.order == AML_ORDER_BEFORE) th = min(th, (int64_t)to);
+        else if (q.order == AML_ORDER_AFTER_TRIGGER) tl = max(tl, (int64_t)t0);
+      }
       if (tl > th) continue;
-      const int32_t nbv = node[q.b_var];
-      const int32_t lo = LB.ptr[nbv], end = LB.ptr[nbv + 1];
-      bcur[s] = lower_nbr_t(LB.nnbr, LB.nt, lo, end, x, tl);
-      bhi[s] = lower_nbr_t(LB.nnbr, LB.nt, bcur[s], end, x, th + 1);
+      const int32_t lo = LI.ptr[inode], end = LI.ptr[inode + 1];
+      bcur[s] = lower_nbr_t(LI.nnbr, LI.nt, lo, end, x, tl);
+      bhi[s] = lower_nbr_t(LI.nnbr, LI.nt, bcur[s], end, x, th + 1);
     }
   };
 

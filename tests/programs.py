@@ -55,6 +55,12 @@ NOVEL = {
     "fan_pairs": ([T, F(0, OUT, 2, NONE, SPAN)], INSTANCES),
     # the trigger alone
     "trigger_only": ([T], INSTANCES),
+    # common senders of N0 and N1 inside the trailing window (an intersection
+    # without order: the interpreter walks the shorter side)
+    "common_in_trailing": ([T, X(0, IN, 1, IN, 2, NONE, TRAILING, mask(0, 1))], EDGES),
+    # after a later hop N1 -> N2, the distinct accounts that pay both N1 and N2
+    "hop_then_common_payer": ([T, F(1, OUT, 2, AFTER, SPAN, mask(0)),
+                               X(1, IN, 2, IN, 3, NONE, SPAN, mask(0, 1, 2))], DISTINCT),
 }
 
 RANGE, RATIO = 1, 2
