@@ -1625,6 +1625,7 @@ static void nsub_dispatch(int n, F&& f) {
 // every block resident, so in normal operation no wait runs out.
 
 constexpr int FUSED_BLOCK = 512;
+constexpr int FUSED_WARP_TILE = 256;  // edges a warp takes from the fused mine's work queues
 
 // Sense-reversing grid barrier: the last block to arrive resets the count
 // and advances the generation the others wait on.  False if the wait ran out.
@@ -1708,20 +1709,35 @@ __device__ __forceinline__ bool cyc_fused_levels(const CycLevelArgs& A, const Fu
     const bool has_next = j + 1 <= A.K - 1;
     const int64_t C = (n + G - 1) / G;
     const int64_t c0 = min(n, (int64_t)blockIdx.x * C), c1 = min(n, c0 + C);
-    long long mine = 0;
+    // the level's paths from a work queue of warp tiles (the paths of a hub
+    // anchor are contiguous, and a static chunk of them would set the
+    // level's end); each path's child count and first child slot are stored
+    const long long n_wt = (n + FUSED_WARP_TILE - 1) / FUSED_WARP_TILE;
     level_dispatch(j, [&](auto jc) {
       constexpr int JJ = decltype(jc)::value < 2 ? 2 : decltype(jc)::value;
-      for (int64_t i = c0 + threadIdx.x; i < c1; i += FUSED_BLOCK) {
-        int32_t q0 = 0;
-        const int32_t c = cyc_item<NS, false, JJ>(A, F, sub, i, &q0);
-        if (has_next) {
-          P.cnt[i] = c;
-          P.q0[i] = q0;
-          mine += c;
+      for (;;) {
+        long long t = 0;
+        if (lane == 0) t = (long long)atomicAdd(P.ctr + j, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= n_wt) break;
+        for (int k = 0; k < FUSED_WARP_TILE / 32; ++k) {
+          const int64_t i = t * FUSED_WARP_TILE + k * 32 + lane;
+          if (i >= n) continue;
+          int32_t q0 = 0;
+          const int32_t c = cyc_item<NS, false, JJ>(A, F, sub, i, &q0);
+          if (has_next) {
+            P.cnt[i] = c;
+            P.q0[i] = q0;
+          }
         }
       }
     });
     if (!has_next) break;
+    // the children of block b's contiguous chunk of paths, once all counts
+    // are stored
+    if (!grid_wait(P.bar, P.wait_limit, P.err)) return false;
+    long long mine = 0;
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += FUSED_BLOCK) mine += __ldcg(P.cnt + i);
     mine = fused_block_sum(mine, s_w);
     if (threadIdx.x == 0) P.bsum[blockIdx.x] = mine;
     if (!grid_wait(P.bar, P.wait_limit, P.err)) return false;
@@ -1789,14 +1805,31 @@ __global__ void __launch_bounds__(FUSED_BLOCK, 3) k_mine_fused(GraphView g, Fuse
   const int64_t C = (E + G - 1) / G;
   const int64_t c0 = min(E, (int64_t)blockIdx.x * C), c1 = min(E, c0 + C);
   const bool cyc = Q.anc != nullptr;
-  // 1. leg count of the chunk (thread t takes edges c0 + t + k * FUSED_BLOCK
-  // in every phase, so it reads back its own writes)
+  const int lane = threadIdx.x & 31;
+  const long long n_wt = (E + FUSED_WARP_TILE - 1) / FUSED_WARP_TILE;
+  // 1. leg count: a work queue of warp tiles (FUSED_WARP_TILE consecutive
+  // edges a warp takes from a counter), so the blocks whose edges have long
+  // windows do not set the phase's end
+  for (;;) {
+    long long t = 0;
+    if (lane == 0) t = (long long)atomicAdd(Q.ctr, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= n_wt) break;
+    for (int k = 0; k < FUSED_WARP_TILE / 32; ++k) {
+      const int64_t a = t * FUSED_WARP_TILE + k * 32 + lane;
+      if (a < E)
+        leg_count_item<NS>(g, Q.delta, (int32_t)a, Q.L, Q.anc, 1, Q.L2, nullptr, Q.qwin, Q.qcb,
+                           sub, Q.Z);
+    }
+  }
+  if (!grid_wait(P.bar, P.wait_limit, P.err)) return;
+  // 2. the leg offsets: block b sums the legs of its contiguous chunk, meets
+  // the others, and places the chunk's legs and cycle legs from every
+  // block's sums; the totals go to off[E], off2[E]
   long long nl = 0, nc = 0;
   for (int64_t a = c0 + threadIdx.x; a < c1; a += FUSED_BLOCK) {
-    leg_count_item<NS>(g, Q.delta, (int32_t)a, Q.L, Q.anc, 1, Q.L2, nullptr, Q.qwin, Q.qcb,
-                       sub, Q.Z);
-    nl += Q.L[a];
-    if (cyc) nc += Q.L2[a];
+    nl += __ldcg(Q.L + a);
+    if (cyc) nc += __ldcg(Q.L2 + a);
   }
   nl = fused_block_sum(nl, s_w);
   nc = fused_block_sum(nc, s_w);
@@ -1805,7 +1838,6 @@ __global__ void __launch_bounds__(FUSED_BLOCK, 3) k_mine_fused(GraphView g, Fuse
     Q.bsum[2 * blockIdx.x + 1] = nc;
   }
   if (!grid_wait(P.bar, P.wait_limit, P.err)) return;
-  // 2. the chunk's first leg and cycle-leg positions, and the totals
   long long b1 = 0, b2 = 0, t1 = 0, t2 = 0;
   for (unsigned b = threadIdx.x; b < G; b += FUSED_BLOCK) {
     const long long v1 = __ldcg(Q.bsum + 2 * b), v2 = __ldcg(Q.bsum + 2 * b + 1);
@@ -1826,8 +1858,8 @@ __global__ void __launch_bounds__(FUSED_BLOCK, 3) k_mine_fused(GraphView g, Fuse
   }
   for (int64_t t0 = c0; t0 < c1; t0 += FUSED_BLOCK) {
     const int64_t a = t0 + threadIdx.x;
-    const int32_t l1 = a < c1 ? Q.L[a] : 0;
-    const int32_t l2 = cyc && a < c1 ? Q.L2[a] : 0;
+    const int32_t l1 = a < c1 ? __ldcg(Q.L + a) : 0;
+    const int32_t l2 = cyc && a < c1 ? __ldcg(Q.L2 + a) : 0;
     long long tile1 = 0, tile2 = 0;
     const long long o1 = b1 + fused_block_excl(l1, s_w, &tile1);
     const long long o2 = b2 + fused_block_excl(l2, s_w, &tile2);
@@ -1842,14 +1874,19 @@ __global__ void __launch_bounds__(FUSED_BLOCK, 3) k_mine_fused(GraphView g, Fuse
     Q.off[E] = t1;
     if (cyc) Q.off2[E] = t2;
   }
-  // 3. leg emission of the chunk (its windows and offsets are this thread's
-  // own writes; static chunks spread the hubs' long windows over every
-  // warp, which balancing the chunks by legs would gather into a few); the
-  // accumulators it adds into were zeroed in phase 1, before the barrier
-  for (int64_t t0 = c0; t0 < c1; t0 += FUSED_BLOCK) {
-    const int64_t a = t0 + threadIdx.x;
-    leg_emit_warp<NS>(g, Q.qwin, Q.qcb, Q.off, Q.S, Q.acc_cyc2, Q.gs_in, Q.own_max, sub,
-                      a < c1 ? a : E);
+  // 3. leg emission, from a second work queue of warp tiles once every
+  // offset is placed; the accumulators it adds into were zeroed in phase 1
+  if (!grid_wait(P.bar, P.wait_limit, P.err)) return;
+  for (;;) {
+    long long t = 0;
+    if (lane == 0) t = (long long)atomicAdd(Q.ctr + 1, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= n_wt) break;
+    for (int k = 0; k < FUSED_WARP_TILE / 32; ++k) {
+      const int64_t a = t * FUSED_WARP_TILE + k * 32 + lane;
+      leg_emit_warp<NS>(g, Q.qwin, Q.qcb, Q.off, Q.S, Q.acc_cyc2, Q.gs_in, Q.own_max, sub,
+                        a < E ? a : E);
+    }
   }
   if (!cyc || A.K < 3) return;
   // 4. the cycle levels, once every block's cycle legs are written

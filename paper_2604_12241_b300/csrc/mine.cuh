@@ -244,15 +244,17 @@ struct FusedCycles {
   int32_t* q0;
   long long* bsum;
   GridBarrier* bar;
+  unsigned long long* ctr;  // per level, the work queue's counter (zeroed before the launch)
   uint32_t* err;
   long long wait_limit;  // SM clock cycles a barrier wait may take
   int32_t own_max;       // child lists up to this long are written by one lane
 };
 // The fused mine of one window: the leg pass and the cycle search in one
-// cooperative launch (k_mine_fused).  Block b takes the contiguous edge chunk
-// b; phases: leg count of the chunk, grid barrier, the chunk's leg offsets
-// (off, off2 and their totals at [E]) from every block's sums, leg emission
-// of the chunk, grid barrier, then every cycle level (FusedCycles).  The
+// cooperative launch (k_mine_fused).  Phases, between grid barriers: leg
+// count (warps take tiles of edges from a work queue), the legs of block b's
+// contiguous edge chunk summed, the chunk's leg offsets (off, off2 and their
+// totals at [E]) from every block's sums, leg emission (a second work
+// queue), then every cycle level (FusedCycles).  The
 // buffers are sized for n_legs legs and n2 cycle legs (the sizes of an
 // earlier mine of the same graph); other totals set ERR_OVERFLOW.
 struct FusedLegs {
@@ -270,7 +272,8 @@ struct FusedLegs {
   int32_t* gs_in;
   int32_t own_max;
   int64_t n_legs, n2;
-  long long* bsum;  // two values per block
+  long long* bsum;               // two values per block
+  unsigned long long* ctr;       // the two work queues' counters, zeroed before the launch
 };
 // blocks of the fused launches on this device (all resident at once)
 int fused_mine_grid(int n_sub);

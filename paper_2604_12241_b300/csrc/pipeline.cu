@@ -498,6 +498,11 @@ void mine_plain(aml_graph* g, const aml_pattern_set* ps, uint32_t* counts, int64
       DBuf<long long> bsum((size_t)2 * grid, s);
       DBuf<GridBarrier> bar(1, s);
       AML_CUDA(cudaMemsetAsync(bar.p, 0, sizeof(GridBarrier), s));
+      // the work queues' counters: leg count, emission, then one per cycle level
+      DBuf<unsigned long long> ctr(2 + MAX_CYCLE + 1, s);
+      AML_CUDA(cudaMemsetAsync(ctr.p, 0, (2 + MAX_CYCLE + 1) * sizeof(unsigned long long), s));
+      Q.ctr = ctr.p;
+      FC.ctr = ctr.p + 2;
       FC.cnt = cnt.p;
       FC.q0 = q0b.p;
       FC.bsum = bsum.p;
