@@ -333,15 +333,16 @@ aml_status aml_pattern_set_column(const aml_pattern_set* ps, int32_t col,
 #define AML_MINE_FUSED 0x20u       /* the leg pass and the level-by-level cycle  */
                                    /* search of a window in one persistent       */
                                    /* cooperative launch (Sec. 4: the families   */
-                                   /* share their first hop): each block counts  */
-                                   /* the legs of its edge chunk, meets the      */
-                                   /* others at a grid-wide barrier, places its   */
-                                   /* chunk's legs from all blocks' sums, emits   */
-                                   /* them (GS, 2-cycle and SG records, cycle     */
-                                   /* legs), meets them again, then per cycle     */
-                                   /* level closes its chunk's cycles and places  */
-                                   /* its chunk's children between two barriers.  */
-                                   /* The SG grouping follows the launch and the  */
+                                   /* share their first hop): warps take tiles    */
+                                   /* of edges from a work queue and count their  */
+                                   /* legs; after a grid-wide barrier each block  */
+                                   /* places its chunk's legs from all blocks'    */
+                                   /* sums; warps take tiles again and emit the   */
+                                   /* legs (GS, 2-cycle and SG records, cycle     */
+                                   /* legs); then per cycle level warps close     */
+                                   /* tiles of paths and each block places its   */
+                                   /* chunk's children, barriers between.  The    */
+                                   /* SG grouping follows the launch and the      */
                                    /* DEG/FAN pass runs beside it.  The first     */
                                    /* mine of a (graph, window) runs the plain    */
                                    /* sequence to learn the leg and level sizes.  */

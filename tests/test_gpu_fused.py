@@ -1,6 +1,7 @@
 """The fused persistent mine (AML_MINE_FUSED): a window's leg pass (leg
 count, leg offsets, leg emission) and every level of its cycle search in one
-cooperative launch whose blocks meet at grid-wide barriers.  Its counts equal
+cooperative launch whose warps take tiles of work from queues and whose
+blocks meet at grid-wide barriers.  Its counts equal
 the oracle's and the plain mine's, replayed from a captured CUDA graph too,
 on tiny-10k, on a hub graph, on graphs with fewer edges than the launch has
 blocks, on pattern sets without cycles, and at hi-small's full size (sampled
@@ -64,8 +65,9 @@ def test_fused_launch_replaces_leg_and_cycle_kernels():
 
 @pytest.mark.parametrize("n_edges", [1, 37, 700, 5000])
 def test_fused_with_fewer_edges_than_blocks(n_edges):
-    """Chunks of zero or one edge: most blocks of the launch count and emit
-    nothing but still meet every barrier."""
+    """Fewer edge tiles than the launch has warps, and chunks of zero or one
+    edge for the offsets: most blocks of the launch count and emit nothing
+    but still meet every barrier."""
     rng = np.random.default_rng(n_edges)
     N = max(4, n_edges // 6)
     src = rng.integers(0, N, n_edges).astype(np.int32)
