@@ -197,8 +197,9 @@ def mine(graph: Graph, pset: PatternSet, out=None, stream=None, host_output: boo
     be page-locked, e.g. a pinned torch tensor's ``.numpy()``) and the caller
     synchronizes ``stream`` before reading it.  ``use_graph``
     replays the whole mine as one captured CUDA graph (AML_MINE_GRAPH).
-    ``mode``: "plain" (level-by-level cycle search), "fused" (the same
-    search in one cooperative persistent launch), "persistent" (one
+    ``mode``: "plain" (level-by-level cycle search), "fused" (a window's
+    leg pass and cycle search in one cooperative persistent launch with
+    work queues), "persistent" (one
     persistent launch, degree-binned queues) or "learned" (queues from the
     trained cost model).  All modes give identical counts.
     """

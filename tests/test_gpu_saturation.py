@@ -25,8 +25,9 @@ COLS = [("deg_out", 5), ("deg_in", 5), ("fan_out", 5), ("fan_in", 5), ("gs", 5),
         ("sg", 100), ("cyc", 2, 6), ("cyc", 3, 6), ("cyc", 4, 8), ("cyc", 5, 9)]
 
 
-def _mine(graph, pats, use_graph=False):
-    out = aml.mine(graph, aml.PatternSet(pats), use_graph=use_graph)
+def _mine(graph, pats, use_graph=False, mode=None):
+    kw = {} if mode is None else {"mode": mode}
+    out = aml.mine(graph, aml.PatternSet(pats), use_graph=use_graph, **kw)
     return out.cpu().numpy().view(np.uint32)
 
 
@@ -49,7 +50,7 @@ def test_tiny_graphs_saturate_like_the_oracle(limit):
     assert reached > 20   # the limit is really reached, on many edges
 
 
-def test_tiny_10k_saturates_plain_and_captured():
+def test_tiny_10k_saturates_plain_captured_and_fused():
     g = aml_synth.workload("tiny-10k")
     pats = P.standard(P.DAY)
     cols = oracle_columns(pats)
@@ -63,6 +64,8 @@ def test_tiny_10k_saturates_plain_and_captured():
         assert (want != og.count_all(cols)).any()
         np.testing.assert_array_equal(_mine(graph, pats), want)
         np.testing.assert_array_equal(_mine(graph, pats, use_graph=True), want)
+        for _ in range(2):  # the fused mine (the first learns its sizes)
+            np.testing.assert_array_equal(_mine(graph, pats, mode="fused"), want)
     graph.set_count_limit(0xFFFFFFFF)
     np.testing.assert_array_equal(_mine(graph, pats, use_graph=True), full)
     with pytest.raises(aml.AmlError):
