@@ -477,32 +477,42 @@ struct BatchRows {
         bnbr(n, s), cnt((size_t)N + 1, s), kdrop((size_t)N, s) {}
 };
 
-// A small batch (up to SMALL_SORT edges) sorted in one block: a bitonic sort
-// of (row, counterparty, index) triples in shared memory, rows as
-// k_row_keys gives them (N for a self-loop) and the counterparty 0 when only
-// (row, index) order is wanted.  The triples are unique (the index), so the
-// order equals the stable radix sorts' order.
-constexpr int SMALL_SORT = 2048;
+// A batch of up to SMALL_SORT edges is sorted in shared memory: one block
+// per (direction, order), all four in one launch, each a bitonic sort of
+// 64-bit keys (row << 36 | counterparty << 14 | index), rows as k_row_keys
+// gives them (N for a self-loop) and the counterparty 0 when only (row,
+// index) order is wanted.  The keys are unique (the index), so the order
+// equals the stable radix sorts' order.  It needs N < 2^22 (rows up to N in
+// 28 bits, counterparties in 22); a larger batch or graph takes the radix
+// passes (three launches each) instead.
+constexpr int SMALL_SORT = 16384;
+constexpr int SMALL_SORT_THREADS = 1024;
+constexpr int32_t SMALL_SORT_MAX_N = 1 << 22;
 
-template <bool BY_NBR>
-__global__ void __launch_bounds__(SMALL_SORT / 2) k_sort_small(const int32_t* __restrict__ row_of,
-                                                               const int32_t* __restrict__ other,
-                                                               int n, int32_t N,
-                                                               uint32_t* __restrict__ key,
-                                                               uint32_t* __restrict__ perm) {
-  __shared__ uint32_t s_row[SMALL_SORT], s_nbr[SMALL_SORT], s_idx[SMALL_SORT];
-  int m = 2;
-  while (m < n) m <<= 1;
+struct SmallSortJob {
+  const int32_t* row_of;
+  const int32_t* other;
+  uint32_t* key;   // sorted rows
+  uint32_t* perm;  // the batch index of each
+  int by_nbr;
+};
+struct SmallSortJobs {
+  SmallSortJob job[4];
+};
+
+__global__ void __launch_bounds__(SMALL_SORT_THREADS) k_sort_small(SmallSortJobs J, int n, int m,
+                                                                   int32_t N) {
+  extern __shared__ unsigned long long s_sort[];  // m keys
+  const SmallSortJob q = J.job[blockIdx.x];
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    unsigned long long k = ~0ull;  // padding sorts last
     if (i < n) {
-      const int32_t r = row_of[i], o = other[i];
-      s_row[i] = r == o ? (uint32_t)N : (uint32_t)r;
-      s_nbr[i] = BY_NBR ? (uint32_t)o : 0u;
-    } else {
-      s_row[i] = 0xffffffffu;  // padding sorts last
-      s_nbr[i] = 0xffffffffu;
+      const int32_t r = q.row_of[i], o = q.other[i];
+      const unsigned long long row = r == o ? (unsigned long long)N : (unsigned long long)r;
+      const unsigned long long nbr = q.by_nbr ? (unsigned long long)o : 0ull;
+      k = (row << 36) | (nbr << 14) | (unsigned long long)i;
     }
-    s_idx[i] = (uint32_t)i;
+    s_sort[i] = k;
   }
   __syncthreads();
   for (int k = 2; k <= m; k <<= 1) {
@@ -510,40 +520,59 @@ __global__ void __launch_bounds__(SMALL_SORT / 2) k_sort_small(const int32_t* __
       for (int t = threadIdx.x; t < m / 2; t += blockDim.x) {
         const int i = 2 * t - (t & (j - 1));  // the lower element of a pair
         const int l = i + j;
-        const bool up = (i & k) == 0;
-        const bool gt = s_row[i] != s_row[l] ? s_row[i] > s_row[l]
-                        : s_nbr[i] != s_nbr[l] ? s_nbr[i] > s_nbr[l] : s_idx[i] > s_idx[l];
-        if (gt == up) {
-          uint32_t x = s_row[i]; s_row[i] = s_row[l]; s_row[l] = x;
-          x = s_nbr[i]; s_nbr[i] = s_nbr[l]; s_nbr[l] = x;
-          x = s_idx[i]; s_idx[i] = s_idx[l]; s_idx[l] = x;
+        const unsigned long long x = s_sort[i], y = s_sort[l];
+        if ((x > y) == ((i & k) == 0)) {
+          s_sort[i] = y;
+          s_sort[l] = x;
         }
       }
       __syncthreads();
     }
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    key[i] = s_row[i];
-    perm[i] = s_idx[i];
+    const unsigned long long k = s_sort[i];
+    q.key[i] = (uint32_t)(k >> 36);
+    q.perm[i] = (uint32_t)(k & 0x3fffull);
   }
+}
+
+// Both directions' batch orders at once when the batch and the graph are
+// small enough for k_sort_small; false (nothing done) otherwise.
+static bool upd_sort_batches_small(BatchRows& bo, BatchRows& bi, const int32_t* src,
+                                   const int32_t* dst, int64_t n, int32_t N, cudaStream_t s) {
+  if (n > SMALL_SORT || N >= SMALL_SORT_MAX_N) return false;
+  const int B = 256;
+  int m = 2;
+  while (m < n) m <<= 1;
+  const int smem = m * (int)sizeof(unsigned long long);
+  static bool attr_set[64] = {};  // per device: the large shared-memory opt-in
+  int dev = 0;
+  AML_CUDA(cudaGetDevice(&dev));
+  if (smem > 48 * 1024 && (dev >= 64 || !attr_set[dev])) {
+    AML_CUDA(cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  SMALL_SORT * (int)sizeof(unsigned long long)));
+    if (dev < 64) attr_set[dev] = true;
+  }
+  SmallSortJobs J;
+  J.job[0] = SmallSortJob{src, dst, bo.bkey.p, bo.bperm.p, 0};
+  J.job[1] = SmallSortJob{src, dst, bo.nkey.p, bo.nperm.p, 1};
+  J.job[2] = SmallSortJob{dst, src, bi.bkey.p, bi.bperm.p, 0};
+  J.job[3] = SmallSortJob{dst, src, bi.nkey.p, bi.nperm.p, 1};
+  AML_LAUNCH("k_sort_small", s,
+             k_sort_small<<<4, SMALL_SORT_THREADS, smem, s>>>(J, (int)n, m, N));
+  for (BatchRows* b : {&bo, &bi}) {
+    const int32_t* other = b == &bo ? dst : src;
+    AML_LAUNCH("k_row_ptr", s,
+               k_row_ptr<<<grid_for((int64_t)N + 1, B), B, 0, s>>>(b->bkey.p, n, N, b->bptr.p));
+    AML_LAUNCH("k_upd_batch_nbr", s,
+               k_upd_batch_nbr<<<grid_for(n, B), B, 0, s>>>(b->nperm.p, other, 0, n, b->bnbr.p));
+  }
+  return true;
 }
 
 static void upd_sort_batch(BatchRows& b, const int32_t* row_of, const int32_t* other, int64_t n,
                            int32_t N, int nbits, cudaStream_t s) {
   const int B = 256;
-  if (n <= SMALL_SORT) {  // one block per order instead of radix passes
-    AML_LAUNCH("k_sort_small", s,
-               k_sort_small<false><<<1, SMALL_SORT / 2, 0, s>>>(row_of, other, (int)n, N,
-                                                               b.bkey.p, b.bperm.p));
-    AML_LAUNCH("k_row_ptr", s,
-               k_row_ptr<<<grid_for((int64_t)N + 1, B), B, 0, s>>>(b.bkey.p, n, N, b.bptr.p));
-    AML_LAUNCH("k_sort_small", s,
-               k_sort_small<true><<<1, SMALL_SORT / 2, 0, s>>>(row_of, other, (int)n, N,
-                                                              b.nkey.p, b.nperm.p));
-    AML_LAUNCH("k_upd_batch_nbr", s,
-               k_upd_batch_nbr<<<grid_for(n, B), B, 0, s>>>(b.nperm.p, other, 0, n, b.bnbr.p));
-    return;
-  }
   DBuf<uint32_t> kt(n, s), vt(n, s);
   iota_i32(reinterpret_cast<int32_t*>(b.bperm.p), n, s);
   AML_LAUNCH("k_row_keys", s,
@@ -657,8 +686,10 @@ aml_graph* update_graph(const aml_graph* o, int64_t drop, const int32_t* src, co
     const int64_t nb = n_new ? n_new : 1;
     BatchRows bo(nb, N, s), bi(nb, N, s);
     if (n_new) {
-      upd_sort_batch(bo, g->src + b0, g->dst + b0, n_new, N, nbits, s);
-      upd_sort_batch(bi, g->dst + b0, g->src + b0, n_new, N, nbits, s);
+      if (!upd_sort_batches_small(bo, bi, g->src + b0, g->dst + b0, n_new, N, s)) {
+        upd_sort_batch(bo, g->src + b0, g->dst + b0, n_new, N, nbits, s);
+        upd_sort_batch(bi, g->dst + b0, g->src + b0, n_new, N, nbits, s);
+      }
     } else {
       AML_CUDA(cudaMemsetAsync(bo.bptr.p, 0, ((size_t)N + 1) * 4, s));
       AML_CUDA(cudaMemsetAsync(bi.bptr.p, 0, ((size_t)N + 1) * 4, s));

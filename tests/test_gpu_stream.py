@@ -249,3 +249,23 @@ def test_stream_column_subsets(kind):
     assert check_resident(st, g, E, pats, full_mine(g, E, pats)) > 0
     assert st.check_graph() == 0
     st.close()
+
+
+def test_stream_batches_at_the_one_block_sort_limit():
+    """Batches of up to 16,384 edges are sorted by one block in shared
+    memory, larger ones by radix passes: batches on both sides of the limit
+    (and of the power of two below it) give the same window graph as a fresh
+    build and the same counts as a full mine."""
+    g = aml_synth.workload("tiny-10k")
+    pats = P.standard(P.DAY)
+    st = aml.Stream(aml.PatternSet(pats), g.n_nodes, resident_window=30 * P.DAY,
+                    mem_budget=1 << 30)
+    pos, E = 0, g.n_edges
+    for n in (16384, 16385, 8192, 8193, 1, 2049):
+        st.append(g.src[pos:pos + n], g.dst[pos:pos + n], g.ts[pos:pos + n])
+        pos += n
+        assert st.check_graph() == 0
+    st.append(g.src[pos:], g.dst[pos:], g.ts[pos:])
+    assert st.check_graph() == 0
+    check_resident(st, g, E, pats, full_mine(g, E, pats))
+    st.close()
